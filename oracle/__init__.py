@@ -1,0 +1,189 @@
+"""FP64 CPU oracle for PRADMM (arXiv 2601.15684) -- TEST INFRASTRUCTURE.
+
+Only the test suite, the smoke check and the benchmark's CPU-baseline leg may
+import this package.  It shares no code with the CUDA library and the library
+never calls it.
+
+`pradmm_oracle.c` holds the iteration itself (Section 3.2 Eq. (3),
+Algorithm 1, Appendix B closed forms, Appendix E.1 residual) as plain double
+precision loops; this module only loads it and marshals numpy arrays.
+`matrix_form.py` is a second, independent statement of the same iteration
+built from the literal 4x4 matrices M(.), W(.), D of Appendix A.2/B.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pradmm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("tau", ctypes.c_double),
+                ("gamma", ctypes.c_double * 4)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C11, -O2, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-fno-fast-math",
+                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            P = ctypes.POINTER
+            d, i32, i64 = P(ctypes.c_double), P(ctypes.c_int32), ctypes.c_int64
+            L.orc_iterate.restype = ctypes.c_int64
+            L.orc_iterate.argtypes = [i64, i64, i32, i32, d, d, d, d, P(Params), d, d, d, d, d, d, d]
+            L.orc_solve.restype = ctypes.c_int64
+            L.orc_solve.argtypes = [i64, i64, i32, i32, d, d, d, d, P(Params), i64, ctypes.c_double,
+                                    d, d, d, d, d, d, d, d]
+            L.orc_objective.restype = ctypes.c_double
+            L.orc_objective.argtypes = [i64, i64, i32, i32, d, d, d, d, d, d]
+            L.orc_split_objective.restype = None
+            L.orc_split_objective.argtypes = [i64, i64, i32, i32, d, d, d, d, d, d, d, d, d, d]
+            L.orc_lagrangian.restype = ctypes.c_double
+            L.orc_lagrangian.argtypes = [i64, i64, i32, i32, d, d, d, d, P(Params), d, d, d, d, d, d]
+            L.orc_init_odometry.restype = ctypes.c_int
+            L.orc_init_odometry.argtypes = [i64, i64, i32, i32, d, d, d, d]
+            L.orc_qmul.restype = None
+            L.orc_qmul.argtypes = [d, d, d]
+            L.orc_qrotate.restype = None
+            L.orc_qrotate.argtypes = [d, d, d]
+            _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _i(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def make_params(beta1=10.0, beta2=10.0, tau=1.5, gamma=(1.0, 1e-3, 1e-3, 1e-3)) -> Params:
+    p = Params()
+    p.beta1, p.beta2, p.tau = beta1, beta2, tau
+    for k in range(4):
+        p.gamma[k] = gamma[k]
+    return p
+
+
+def _graph_args(g):
+    src = np.ascontiguousarray(g.src, dtype=np.int32)
+    dst = np.ascontiguousarray(g.dst, dtype=np.int32)
+    qe = _f64(g.q_meas)
+    te = _f64(g.t_meas)
+    ka = _f64(g.kappa)
+    om = _f64(g.omega)
+    keep = (src, dst, qe, te, ka, om)
+    return keep, (g.n, src.shape[0], _i(src), _i(dst), _d(qe), _d(te), _d(ka), _d(om))
+
+
+def init_state(q0, t0):
+    """Initial ADMM state of reading R8: p = q = q0, s = t = t0, multipliers zero."""
+    q0, t0 = _f64(q0), _f64(t0)
+    n = q0.shape[0]
+    return {"p": q0.copy(), "q": q0.copy(), "t": t0.copy(), "s": t0.copy(),
+            "lam": np.zeros((n, 4)), "z": np.zeros((n, 3))}
+
+
+def copy_state(st):
+    return {k: _f64(v).copy() for k, v in st.items()}
+
+
+def init_odometry(g):
+    keep, a = _graph_args(g)
+    q = np.zeros((g.n, 4))
+    t = np.zeros((g.n, 3))
+    rc = lib().orc_init_odometry(*a[:6], _d(q), _d(t))
+    if rc != 0:
+        raise MemoryError("oracle init_odometry")
+    return q, t
+
+
+def iterate(g, params: Params, state: dict, iters: int = 1):
+    """Runs `iters` iterations of Algorithm 1 in place on a copy of `state`.
+    Returns (new_state, residual parts [e, |dlam|^2, |dz|^2, |dq|^2, |dt|^2] of
+    the last iteration, number of zero-|u| vertices over all iterations)."""
+    st = copy_state(state)
+    keep, a = _graph_args(g)
+    res = np.zeros(5)
+    nz = 0
+    for _ in range(iters):
+        r = lib().orc_iterate(*a, ctypes.byref(params), _d(st["p"]), _d(st["q"]), _d(st["t"]),
+                              _d(st["s"]), _d(st["lam"]), _d(st["z"]), _d(res))
+        if r < 0:
+            raise MemoryError("oracle iterate")
+        nz += int(r)
+    return st, res.copy(), nz
+
+
+def solve(g, params: Params, state: dict, max_iter: int, tol: float):
+    st = copy_state(state)
+    keep, a = _graph_args(g)
+    e = np.zeros(1)
+    trace = np.zeros(max(max_iter, 1))
+    k = lib().orc_solve(*a, ctypes.byref(params), int(max_iter), float(tol), _d(st["p"]), _d(st["q"]),
+                        _d(st["t"]), _d(st["s"]), _d(st["lam"]), _d(st["z"]), _d(e), _d(trace))
+    return st, int(k), float(e[0]), trace[:k].copy()
+
+
+def objective(g, q, t) -> float:
+    """Eq. (1) at (q, t)."""
+    keep, a = _graph_args(g)
+    q, t = _f64(q), _f64(t)
+    return float(lib().orc_objective(*a, _d(q), _d(t)))
+
+
+def split_objective(g, st) -> tuple[float, float]:
+    keep, a = _graph_args(g)
+    f = np.zeros(1)
+    gg = np.zeros(1)
+    s = copy_state(st)
+    lib().orc_split_objective(*a, _d(s["p"]), _d(s["q"]), _d(s["t"]), _d(s["s"]), _d(f), _d(gg))
+    return float(f[0]), float(gg[0])
+
+
+def lagrangian(g, params: Params, st) -> float:
+    keep, a = _graph_args(g)
+    s = copy_state(st)
+    return float(lib().orc_lagrangian(*a, ctypes.byref(params), _d(s["p"]), _d(s["q"]), _d(s["t"]),
+                                      _d(s["s"]), _d(s["lam"]), _d(s["z"])))
+
+
+def qmul(a, b):
+    a, b = _f64(a), _f64(b)
+    o = np.zeros(4)
+    lib().orc_qmul(_d(a), _d(b), _d(o))
+    return o
+
+
+def qrotate(q, t):
+    q, t = _f64(q), _f64(t)
+    o = np.zeros(3)
+    lib().orc_qrotate(_d(q), _d(t), _d(o))
+    return o

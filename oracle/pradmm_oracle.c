@@ -1,0 +1,447 @@
+/*
+ * PRADMM oracle -- plain, slow, FP64 CPU implementation of one PRADMM
+ * iteration (Chen, Cui, Han, Qi, "Parallelizable Riemannian ADMM for
+ * Non-convex Pose Graph Optimization", arXiv 2601.15684).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the checker the CUDA library is
+ * compared against.  Only the test suite, the smoke check and the benchmark's
+ * CPU-baseline leg may load it.  It shares no code, header, table or helper
+ * with the CUDA library, and the library never calls it.
+ *
+ * Everything is double precision, single threaded, with loops written in the
+ * order the paper states the steps:
+ *   - quaternion algebra .................. Appendix A.2
+ *   - model (1) objective F ............... Section 2, Eq. (1)
+ *   - split model (2), f and g ............ Section 3.1, Eq. (2)
+ *   - augmented Lagrangian L_beta ......... Section 3.2
+ *   - one iteration (3a)-(3f) ............. Section 3.2 Eq. (3), Algorithm 1,
+ *                                           closed forms of Appendix B
+ *   - residual e^{k+1} and stopping ....... Appendix E.1
+ *
+ * Readings of passages that are garbled or silent (the same readings the CUDA
+ * path follows):
+ *   R1  the in-edge matrix of the p-block is W(q_li) W(q_l) D (the printed
+ *       form drops D); in product form its transpose times 1~ is q_l q_li.
+ *   R2  x = A^{-1} b with b as printed for the q, t, s blocks; p = -b1/|b1|.
+ *   R3  c_e = Im(q_tail t~_e p_tail^*) for e = (tail, head).
+ *   R4  proximal anchors x^{k+1/2} are read as x^k.
+ *   R5  z lives in R^{3n}.
+ *   R6  e^{k+1} uses beta1 for the lambda / q terms and beta2 for z / t.
+ *   R8  lambda^0 = z^0 = 0, p^0 = q^0, s^0 = t^0 (set by the caller).
+ *   R9  Sigma_1 = omega_e I_4 and Sigma_2 = kappa_e I_4 per edge.
+ *   R11 if |u_i| == 0 the p-block keeps p_i^k.
+ *   R13 Jacobi inside a block: every vertex reads pre-block values.
+ *
+ * Quaternions are scalar first, [q0, q1, q2, q3] (Appendix A.2).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    double beta1, beta2; /* penalties beta_1, beta_2 (Section 3.2) */
+    double tau;          /* relaxed dual step tau in (0,2), Eq. (3e,f) */
+    double gamma[4];     /* H_{s,i} = gamma_s I (Section 3.2) */
+} orc_params;
+
+/* ---- quaternion algebra, Appendix A.2 -------------------------------- */
+
+/* p q = [p0 q0 - p.q, p0 q + q0 p + p x q] */
+static void qmul(const double* a, const double* b, double* o) {
+    double r0 = a[0] * b[0] - (a[1] * b[1] + a[2] * b[2] + a[3] * b[3]);
+    double r1 = a[0] * b[1] + b[0] * a[1] + (a[2] * b[3] - a[3] * b[2]);
+    double r2 = a[0] * b[2] + b[0] * a[2] + (a[3] * b[1] - a[1] * b[3]);
+    double r3 = a[0] * b[3] + b[0] * a[3] + (a[1] * b[2] - a[2] * b[1]);
+    o[0] = r0; o[1] = r1; o[2] = r2; o[3] = r3;
+}
+
+/* q^* = [q0, -q] */
+static void qconj(const double* a, double* o) {
+    o[0] = a[0]; o[1] = -a[1]; o[2] = -a[2]; o[3] = -a[3];
+}
+
+/* pure quaternion t~ = [0, t] (Section 2) */
+static void qpure(const double* t3, double* o) {
+    o[0] = 0.0; o[1] = t3[0]; o[2] = t3[1]; o[3] = t3[2];
+}
+
+static double dot4(const double* a, const double* b) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + a[3] * b[3];
+}
+
+/* [0, R(q) t] = q [0, t] q^*  (Appendix A.2) */
+static void qrotate(const double* q, const double* t3, double* out3) {
+    double tp[4], a[4], qc[4], r[4];
+    qpure(t3, tp);
+    qmul(q, tp, a);
+    qconj(q, qc);
+    qmul(a, qc, r);
+    out3[0] = r[1]; out3[1] = r[2]; out3[2] = r[3];
+}
+
+/* Exported for the oracle's own unit tests (Lemma MW, R(q) identities). */
+void orc_qmul(const double* a, const double* b, double* o) { qmul(a, b, o); }
+void orc_qrotate(const double* q, const double* t3, double* o) { qrotate(q, t3, o); }
+
+/* ---- odometry initialisation --------------------------------------------
+ * The paper starts every method from a chordal initialisation that it does
+ * not define (Section 5).  The initial point used here is odometry
+ * composition along a spanning forest: edges are taken in input order and an
+ * edge joins the forest when it links two components (Kruskal by edge
+ * index).  The lowest vertex of each component gets the identity pose, and
+ * every other vertex is composed from its forest parent with the generative
+ * relation of Section 2, q_j = q_i q_ij and t_j = t_i + R_i t_ij.
+ */
+static int64_t uf_find(int64_t* par, int64_t x) {
+    while (par[x] != x) { par[x] = par[par[x]]; x = par[x]; }
+    return x;
+}
+
+int orc_init_odometry(int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                      const double* qe, const double* te, double* q, double* t) {
+    int64_t* par = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t* deg = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    int64_t* tree = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+    if (!par || !deg || !tree) { free(par); free(deg); free(tree); return -1; }
+    for (int64_t i = 0; i < n; ++i) par[i] = i;
+    int64_t nt = 0;
+    for (int64_t e = 0; e < m; ++e) {
+        int64_t a = uf_find(par, src[e]), b = uf_find(par, dst[e]);
+        if (a == b) continue;
+        if (a < b) par[b] = a; else par[a] = b;
+        tree[nt++] = e;
+    }
+    /* adjacency of the forest (CSR over both endpoints) */
+    for (int64_t k = 0; k < nt; ++k) { deg[src[tree[k]] + 1]++; deg[dst[tree[k]] + 1]++; }
+    for (int64_t i = 0; i < n; ++i) deg[i + 1] += deg[i];
+    int64_t* adj = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * nt + 1));
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    char* done = (char*)calloc((size_t)n + 1, 1);
+    int64_t* queue = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    if (!adj || !fill || !done || !queue) {
+        free(par); free(deg); free(tree); free(adj); free(fill); free(done); free(queue);
+        return -1;
+    }
+    for (int64_t i = 0; i < n; ++i) fill[i] = deg[i];
+    for (int64_t k = 0; k < nt; ++k) {
+        int64_t e = tree[k];
+        adj[fill[src[e]]++] = e;
+        adj[fill[dst[e]]++] = e;
+    }
+    for (int64_t r = 0; r < n; ++r) {
+        if (done[r]) continue;
+        /* r is the lowest vertex of a component not yet reached */
+        q[4 * r] = 1.0; q[4 * r + 1] = q[4 * r + 2] = q[4 * r + 3] = 0.0;
+        t[3 * r] = t[3 * r + 1] = t[3 * r + 2] = 0.0;
+        done[r] = 1;
+        int64_t head = 0, tail = 0;
+        queue[tail++] = r;
+        while (head < tail) {
+            int64_t v = queue[head++];
+            for (int64_t k = deg[v]; k < deg[v + 1]; ++k) {
+                int64_t e = adj[k];
+                int64_t a = src[e], b = dst[e];
+                if (a == v && !done[b]) {
+                    /* q_b = q_a q_e ; t_b = t_a + R(q_a) t_e */
+                    double rt[3];
+                    qmul(&q[4 * a], &qe[4 * e], &q[4 * b]);
+                    qrotate(&q[4 * a], &te[3 * e], rt);
+                    for (int c = 0; c < 3; ++c) t[3 * b + c] = t[3 * a + c] + rt[c];
+                    done[b] = 1;
+                    queue[tail++] = b;
+                } else if (b == v && !done[a]) {
+                    /* q_a = q_b q_e^* ; t_a = t_b - R(q_a) t_e */
+                    double qc[4], rt[3];
+                    qconj(&qe[4 * e], qc);
+                    qmul(&q[4 * b], qc, &q[4 * a]);
+                    qrotate(&q[4 * a], &te[3 * e], rt);
+                    for (int c = 0; c < 3; ++c) t[3 * a + c] = t[3 * b + c] - rt[c];
+                    done[a] = 1;
+                    queue[tail++] = a;
+                }
+            }
+        }
+    }
+    free(par); free(deg); free(tree); free(adj); free(fill); free(done); free(queue);
+    return 0;
+}
+
+/* ---- objectives --------------------------------------------------------- */
+
+/* Model (1), Eq. (1), at (q, t) with Sigma_1 = omega_e I_4, Sigma_2 = kappa_e I_4:
+ * F = sum_e omega_e |t~_j - t~_i - q_i t~_ij q_i^*|^2 + kappa_e |q_j^* q_i q_ij - 1|^2 */
+double orc_objective(int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                     const double* qe, const double* te, const double* kappa,
+                     const double* omega, const double* q, const double* t) {
+    (void)n;
+    double F = 0.0;
+    for (int64_t e = 0; e < m; ++e) {
+        int64_t i = src[e], j = dst[e];
+        double tp[4], a[4], qc[4], rot[4], r[4];
+        qpure(&te[3 * e], tp);
+        qmul(&q[4 * i], tp, a);
+        qconj(&q[4 * i], qc);
+        qmul(a, qc, rot);
+        r[0] = -rot[0];
+        for (int c = 0; c < 3; ++c) r[c + 1] = t[3 * j + c] - t[3 * i + c] - rot[c + 1];
+        double w = omega ? omega[e] : 1.0;
+        F += w * dot4(r, r);
+        double qjc[4], b[4], g[4];
+        qconj(&q[4 * j], qjc);
+        qmul(qjc, &q[4 * i], b);
+        qmul(b, &qe[4 * e], g);
+        g[0] -= 1.0;
+        double k = kappa ? kappa[e] : 1.0;
+        F += k * dot4(g, g);
+    }
+    return F;
+}
+
+/* Split model (2): f = sum_e omega_e |t~_j - s~_i - q_i t~_ij p_i^*|^2,
+ * g = sum_e kappa_e |p_j^* q_i q_ij - 1|^2.  Writes f and g. */
+void orc_split_objective(int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                         const double* qe, const double* te, const double* kappa,
+                         const double* omega, const double* p, const double* q,
+                         const double* t, const double* s, double* f_out, double* g_out) {
+    (void)n;
+    double f = 0.0, g = 0.0;
+    for (int64_t e = 0; e < m; ++e) {
+        int64_t i = src[e], j = dst[e];
+        double tp[4], a[4], pc[4], c[4], r[4];
+        qpure(&te[3 * e], tp);
+        qmul(&q[4 * i], tp, a);
+        qconj(&p[4 * i], pc);
+        qmul(a, pc, c);
+        r[0] = -c[0];
+        for (int k = 0; k < 3; ++k) r[k + 1] = t[3 * j + k] - s[3 * i + k] - c[k + 1];
+        f += (omega ? omega[e] : 1.0) * dot4(r, r);
+        double pjc[4], b[4], h[4];
+        qconj(&p[4 * j], pjc);
+        qmul(pjc, &q[4 * i], b);
+        qmul(b, &qe[4 * e], h);
+        h[0] -= 1.0;
+        g += (kappa ? kappa[e] : 1.0) * dot4(h, h);
+    }
+    *f_out = f;
+    *g_out = g;
+}
+
+/* Augmented Lagrangian L_beta of Section 3.2. */
+double orc_lagrangian(int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                      const double* qe, const double* te, const double* kappa,
+                      const double* omega, const orc_params* prm, const double* p,
+                      const double* q, const double* t, const double* s,
+                      const double* lam, const double* z) {
+    double f, g;
+    orc_split_objective(n, m, src, dst, qe, te, kappa, omega, p, q, t, s, &f, &g);
+    double L = f + g;
+    for (int64_t i = 0; i < n; ++i) {
+        double d2 = 0.0, ld = 0.0;
+        for (int c = 0; c < 4; ++c) {
+            double d = p[4 * i + c] - q[4 * i + c];
+            ld += lam[4 * i + c] * d;
+            d2 += d * d;
+        }
+        L += -ld + 0.5 * prm->beta1 * d2;
+        double e2 = 0.0, zd = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            double d = t[3 * i + c] - s[3 * i + c];
+            zd += z[3 * i + c] * d;
+            e2 += d * d;
+        }
+        L += -zd + 0.5 * prm->beta2 * e2;
+    }
+    return L;
+}
+
+/* ---- one PRADMM iteration, Eq. (3a)-(3f) / Algorithm 1 --------------------
+ * Updates (p, q, t, s, lam, z) in place from x^k to x^{k+1}.
+ * res_out (nullable) receives 5 numbers: e^{k+1} (Appendix E.1, reading R6),
+ * then |dlam|^2, |dz|^2, |dq|^2, |dt|^2.
+ * Returns the number of vertices whose p-block hit |u_i| == 0 (R11).
+ */
+int64_t orc_iterate(int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                    const double* qe, const double* te, const double* kappa,
+                    const double* omega, const orc_params* prm, double* p, double* q,
+                    double* t, double* s, double* lam, double* z, double* res_out) {
+    const double b1 = prm->beta1, b2 = prm->beta2, tau = prm->tau;
+    const double g1 = prm->gamma[0], g2 = prm->gamma[1], g3 = prm->gamma[2], g4 = prm->gamma[3];
+    double* u = (double*)calloc((size_t)(4 * n + 1), sizeof(double));
+    double* qn = (double*)calloc((size_t)(4 * n + 1), sizeof(double));
+    double* a2 = (double*)calloc((size_t)(n + 1), sizeof(double));
+    double* tn = (double*)calloc((size_t)(3 * n + 1), sizeof(double));
+    double* a3 = (double*)calloc((size_t)(n + 1), sizeof(double));
+    double* sn = (double*)calloc((size_t)(3 * n + 1), sizeof(double));
+    double* a4 = (double*)calloc((size_t)(n + 1), sizeof(double));
+    double* c = (double*)calloc((size_t)(3 * m + 1), sizeof(double));
+    double* qold = (double*)malloc(sizeof(double) * (size_t)(4 * n + 1));
+    double* told = (double*)malloc(sizeof(double) * (size_t)(3 * n + 1));
+    double* lold = (double*)malloc(sizeof(double) * (size_t)(4 * n + 1));
+    double* zold = (double*)malloc(sizeof(double) * (size_t)(3 * n + 1));
+    int64_t nzero = 0;
+    if (!u || !qn || !a2 || !tn || !a3 || !sn || !a4 || !c || !qold || !told || !lold || !zold) {
+        nzero = -1;
+        goto out;
+    }
+    memcpy(qold, q, sizeof(double) * (size_t)(4 * n));
+    memcpy(told, t, sizeof(double) * (size_t)(3 * n));
+    memcpy(lold, lam, sizeof(double) * (size_t)(4 * n));
+    memcpy(zold, z, sizeof(double) * (size_t)(3 * n));
+
+    /* (3a) p-block, Appendix B.1.  With scalar Sigma the quadratic form A_1 is
+     * a multiple of I_4 (Lemma MW(c)) and the minimiser of the linear term on
+     * the unit sphere is p = -b_1/|b_1| = u/|u|, where
+     *   u_i = sum_{out} 2 w_e G1^T r_e + sum_{in} 2 k_e G2^T 1~ + b1 q_i + lam_i + g1 p_i,
+     * G1^T r = r^* q_i t~_e  (G1 = M(q_i) M(t~_e) D),
+     * G2^T 1~ = q_l q_e      (G2 = W(q_e) W(q_l) D, reading R1),
+     * r_e = t~_j - s~_i.                                                    */
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < 4; ++k)
+            u[4 * i + k] = b1 * q[4 * i + k] + lam[4 * i + k] + g1 * p[4 * i + k];
+    for (int64_t e = 0; e < m; ++e) { /* out-edge sums: e = (i, j) */
+        int64_t i = src[e], j = dst[e];
+        double r[4], rc[4], tp[4], a[4], v[4];
+        r[0] = 0.0;
+        for (int k = 0; k < 3; ++k) r[k + 1] = t[3 * j + k] - s[3 * i + k];
+        qconj(r, rc);
+        qpure(&te[3 * e], tp);
+        qmul(rc, &q[4 * i], a);
+        qmul(a, tp, v);
+        double w = 2.0 * (omega ? omega[e] : 1.0);
+        for (int k = 0; k < 4; ++k) u[4 * i + k] += w * v[k];
+    }
+    for (int64_t e = 0; e < m; ++e) { /* in-edge sums: e = (l, i) */
+        int64_t l = src[e], i = dst[e];
+        double v[4];
+        qmul(&q[4 * l], &qe[4 * e], v);
+        double w = 2.0 * (kappa ? kappa[e] : 1.0);
+        for (int k = 0; k < 4; ++k) u[4 * i + k] += w * v[k];
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        double nu = sqrt(dot4(&u[4 * i], &u[4 * i]));
+        if (nu > 0.0) {
+            for (int k = 0; k < 4; ++k) p[4 * i + k] = u[4 * i + k] / nu;
+        } else {
+            nzero++; /* R11: keep p_i^k */
+        }
+    }
+
+    /* (3b) q-block, Appendix B.2: q_i = b_2 / A_2 with
+     *   A_2 = sum_{out} 2 (w_e |p_i|^2 |t_e|^2 + k_e |p_j|^2 |q_e|^2) + b1 + g2,
+     *   b_2 = sum_{out} 2 (w_e G3^T r_e + k_e G4^T 1~) + b1 p_i - lam_i + g2 q_i,
+     * G3^T r = r p_i t~_e^*   (G3 = W(p_i)^T W(t~_e)),
+     * G4^T 1~ = p_j q_e^*     (G4 = W(q_e) M(p_j)^T).                        */
+    for (int64_t i = 0; i < n; ++i) {
+        a2[i] = b1 + g2;
+        for (int k = 0; k < 4; ++k) qn[4 * i + k] = b1 * p[4 * i + k] - lam[4 * i + k] + g2 * q[4 * i + k];
+    }
+    for (int64_t e = 0; e < m; ++e) {
+        int64_t i = src[e], j = dst[e];
+        double w = omega ? omega[e] : 1.0, kk = kappa ? kappa[e] : 1.0;
+        double r[4], tp[4], tc[4], a[4], v[4], qc[4], h[4];
+        r[0] = 0.0;
+        for (int k = 0; k < 3; ++k) r[k + 1] = t[3 * j + k] - s[3 * i + k];
+        qpure(&te[3 * e], tp);
+        qconj(tp, tc);
+        qmul(r, &p[4 * i], a);
+        qmul(a, tc, v);
+        qconj(&qe[4 * e], qc);
+        qmul(&p[4 * j], qc, h);
+        double tn2 = dot4(tp, tp);
+        a2[i] += 2.0 * (w * dot4(&p[4 * i], &p[4 * i]) * tn2 +
+                        kk * dot4(&p[4 * j], &p[4 * j]) * dot4(&qe[4 * e], &qe[4 * e]));
+        for (int k = 0; k < 4; ++k) qn[4 * i + k] += 2.0 * (w * v[k] + kk * h[k]);
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < 4; ++k) q[4 * i + k] = qn[4 * i + k] / a2[i];
+
+    /* c_e = Im(q_i^{k+1} t~_e (p_i^{k+1})^*) for e = (i, j) (reading R3) */
+    for (int64_t e = 0; e < m; ++e) {
+        int64_t i = src[e];
+        double tp[4], a[4], pc[4], v[4];
+        qpure(&te[3 * e], tp);
+        qmul(&q[4 * i], tp, a);
+        qconj(&p[4 * i], pc);
+        qmul(a, pc, v);
+        c[3 * e] = v[1]; c[3 * e + 1] = v[2]; c[3 * e + 2] = v[3];
+    }
+
+    /* (3c) t-block, Appendix B.3 with hat-Sigma_1 = w_e I_3:
+     *   t_i = [sum_{in} 2 w_e (s_l + c_e) + b2 s_i + z_i + g3 t_i] / [sum_{in} 2 w_e + b2 + g3] */
+    for (int64_t i = 0; i < n; ++i) {
+        a3[i] = b2 + g3;
+        for (int k = 0; k < 3; ++k) tn[3 * i + k] = b2 * s[3 * i + k] + z[3 * i + k] + g3 * t[3 * i + k];
+    }
+    for (int64_t e = 0; e < m; ++e) {
+        int64_t l = src[e], i = dst[e];
+        double w = omega ? omega[e] : 1.0;
+        a3[i] += 2.0 * w;
+        for (int k = 0; k < 3; ++k) tn[3 * i + k] += 2.0 * w * (s[3 * l + k] + c[3 * e + k]);
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) t[3 * i + k] = tn[3 * i + k] / a3[i];
+
+    /* (3d) s-block, Appendix B.4 (the section's variable is s_i):
+     *   s_i = [sum_{out} 2 w_e (t_j - c_e) + b2 t_i - z_i + g4 s_i] / [sum_{out} 2 w_e + b2 + g4] */
+    for (int64_t i = 0; i < n; ++i) {
+        a4[i] = b2 + g4;
+        for (int k = 0; k < 3; ++k) sn[3 * i + k] = b2 * t[3 * i + k] - z[3 * i + k] + g4 * s[3 * i + k];
+    }
+    for (int64_t e = 0; e < m; ++e) {
+        int64_t i = src[e], j = dst[e];
+        double w = omega ? omega[e] : 1.0;
+        a4[i] += 2.0 * w;
+        for (int k = 0; k < 3; ++k) sn[3 * i + k] += 2.0 * w * (t[3 * j + k] - c[3 * e + k]);
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) s[3 * i + k] = sn[3 * i + k] / a4[i];
+
+    /* (3e), (3f) relaxed dual updates */
+    for (int64_t i = 0; i < n; ++i) {
+        for (int k = 0; k < 4; ++k) lam[4 * i + k] -= tau * b1 * (p[4 * i + k] - q[4 * i + k]);
+        for (int k = 0; k < 3; ++k) z[3 * i + k] -= tau * b2 * (t[3 * i + k] - s[3 * i + k]);
+    }
+
+    /* residual of Appendix E.1 (reading R6) */
+    if (res_out) {
+        double dl = 0.0, dz = 0.0, dq = 0.0, dt = 0.0;
+        for (int64_t k = 0; k < 4 * n; ++k) {
+            double a = lam[k] - lold[k], b = q[k] - qold[k];
+            dl += a * a;
+            dq += b * b;
+        }
+        for (int64_t k = 0; k < 3 * n; ++k) {
+            double a = z[k] - zold[k], b = t[k] - told[k];
+            dz += a * a;
+            dt += b * b;
+        }
+        res_out[0] = dl / b1 + dz / b2 + b1 * dq + b2 * dt;
+        res_out[1] = dl; res_out[2] = dz; res_out[3] = dq; res_out[4] = dt;
+    }
+out:
+    free(u); free(qn); free(a2); free(tn); free(a3); free(sn); free(a4); free(c);
+    free(qold); free(told); free(lold); free(zold);
+    return nzero;
+}
+
+/* Algorithm 1 with the stopping rule of Appendix E.1: iterate until
+ * e^{k+1} < tol or max_iter iterations.  Returns the iterations done;
+ * e_out receives the last residual, trace (nullable, max_iter entries)
+ * every residual. */
+int64_t orc_solve(int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                  const double* qe, const double* te, const double* kappa,
+                  const double* omega, const orc_params* prm, int64_t max_iter, double tol,
+                  double* p, double* q, double* t, double* s, double* lam, double* z,
+                  double* e_out, double* trace) {
+    double res[5] = {0, 0, 0, 0, 0};
+    int64_t k = 0;
+    while (k < max_iter) {
+        orc_iterate(n, m, src, dst, qe, te, kappa, omega, prm, p, q, t, s, lam, z, res);
+        if (trace) trace[k] = res[0];
+        ++k;
+        if (res[0] < tol) break;
+    }
+    if (e_out) *e_out = res[0];
+    return k;
+}
