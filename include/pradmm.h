@@ -1,0 +1,192 @@
+/*
+ * libpradmm -- C ABI of a GB300 (sm_103a) implementation of PRADMM, the
+ * parallelizable Riemannian ADMM for non-convex pose graph optimization
+ * (Chen, Cui, Han, Qi, arXiv 2601.15684).
+ *
+ * The problem (Section 2, Eq. (1)): a directed graph of n poses
+ * (q_i unit quaternion, t_i in R^3) and m relative measurements
+ * (q_ij, t_ij) on edges (i, j); minimise
+ *   F = sum_{(i,j)} omega_e |t~_j - t~_i - q_i t~_ij q_i^*|^2
+ *                 + kappa_e |q_j^* q_i q_ij - 1|^2 ,  q_i in U (unit sphere),
+ * where t~ = [0, t] and Sigma_1 = omega_e I_4, Sigma_2 = kappa_e I_4 are
+ * per-edge scalar weights.  The solver runs the PRADMM iteration of
+ * Section 3.2 Eq. (3a)-(3f) / Algorithm 1 on the split model (2): closed-form
+ * per-vertex updates of the rotation copy p (projection onto S^3), the
+ * quaternion copy q, the translations t and s (Appendix B), the relaxed
+ * multiplier updates with step tau in (0,2), and the residual e^k of
+ * Appendix E.1 with the stopping test e^k < tol.
+ *
+ * Conventions
+ *  - Quaternions are scalar first, [q0, q1, q2, q3] (Appendix A.2).
+ *  - Arrays are row major and C contiguous: an "n x 4" array holds
+ *    q_0[0..3], q_1[0..3], ...
+ *  - Vertex indices are int32 in [0, n); self-loops are rejected; repeated
+ *    edges are allowed and summed.
+ *  - Unless a name ends in _device, pointers are HOST memory.  The library
+ *    copies every input it is given and owns all device memory it allocates;
+ *    callers own their buffers.
+ *  - All GPU work of a handle runs on the CUDA stream given to create (NULL:
+ *    the library makes a private non-blocking stream).  Calls on one handle
+ *    are not thread safe; distinct handles are independent.
+ *  - No function aborts or prints.  Each returns a status; after a failure
+ *    pradmm_last_error() gives a one-line message for the calling thread.
+ *  - Precision: PRADMM_FP64 runs everything in double.  PRADMM_FP32 keeps the
+ *    pose state and bulk arithmetic in float, and does the residual, the
+ *    stopping test, the objective and the fallback of the p-update in double.
+ *
+ * Readings of passages the paper leaves open (also used by the test oracle):
+ *  - the in-edge matrix of the p-subproblem is W(q_li) W(q_l) D (Appendix B.1
+ *    prints it without D, which would make noise-free ground truth not a
+ *    fixed point);
+ *  - c_e = Im(q_tail t~_e p_tail^*) for an edge e = (tail, head)
+ *    (Appendix B.3 prints garbled indices);
+ *  - proximal anchors x^{k+1/2} of Appendix B are x^k;
+ *  - e^{k+1} = |dlambda|^2/beta1 + |dz|^2/beta2 + beta1 |dq|^2 + beta2 |dt|^2
+ *    (Appendix E.1 uses a single beta);
+ *  - lambda^0 = z^0 = 0, p^0 = q^0, s^0 = t^0;
+ *  - if |u_i| = 0 in the p-update (p = u/|u| = -b_1/|b_1|, Section 3.3) the
+ *    vertex keeps p_i^k.
+ */
+#ifndef PRADMM_H
+#define PRADMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pradmm_s* pradmm_t;
+
+typedef enum {
+    PRADMM_OK = 0,
+    PRADMM_ERR_ARG = 1,            /* null pointer, bad size or bad parameter   */
+    PRADMM_ERR_INDEX = 2,          /* edge endpoint outside [0, n)              */
+    PRADMM_ERR_SELFLOOP = 3,       /* edge (i, i)                               */
+    PRADMM_ERR_NONFINITE = 4,      /* NaN/Inf in an input or in the iteration  */
+    PRADMM_ERR_NOMEM = 5,          /* host or device allocation failed          */
+    PRADMM_ERR_CUDA = 6,           /* a CUDA runtime call failed                */
+    PRADMM_ERR_TIMEOUT = 7,        /* a bounded device wait ran out             */
+    PRADMM_ERR_NOT_CONVERGED = 8,  /* solve hit max_iter with e >= tol (state valid) */
+    PRADMM_ERR_QUATERNION = 9,     /* |q_meas| differs from 1 by more than 1e-6 */
+    PRADMM_ERR_STATE = 10          /* operation needs a state that was never set */
+} pradmm_status;
+
+enum { PRADMM_FP64 = 0, PRADMM_FP32 = 1 };
+
+typedef struct {
+    double beta1;        /* penalty beta_1 of the p = q constraint (Section 3.2)   */
+    double beta2;        /* penalty beta_2 of the t = s constraint                 */
+    double relax;        /* relaxed dual step tau in (0, 2), Eq. (3e)-(3f)         */
+    double gamma[4];     /* proximal weights: H_s = gamma[s-1] I, s = 1..4         */
+    double tol;          /* stop when e^k < tol (Appendix E.1)                     */
+    int32_t max_iter;    /* iteration cap of pradmm_solve                          */
+    int32_t precision;   /* PRADMM_FP64 or PRADMM_FP32                             */
+    double fallback_eps; /* FP32: recompute u_i in FP64 when |u_i| < eps (beta1+gamma1) */
+    int32_t use_graph;   /* 1: loop inside a CUDA graph with a device-side while node;
+                            0: plain stream launches                               */
+    int32_t block;       /* threads per CTA of the sweeps: 0 (default 256) or a
+                            multiple of 32 in [32, 256]                            */
+} pradmm_params;
+
+/* Defaults: beta1 = beta2 = 1, relax = 1.5, gamma = {1, 1e-3, 1e-3, 1e-3},
+ * tol = 1e-4, max_iter = 300 (Section 5 settings; beta is not given in the
+ * paper and is fixed here by a sweep on the 128-pose walk), FP32,
+ * fallback_eps = 1e-6, use_graph = 1, block = 0. */
+void pradmm_default_params(pradmm_params* prm);
+
+/* Builds a solver for one pose graph (Section 2): validates the edges
+ * (ERR_INDEX, ERR_SELFLOOP, ERR_NONFINITE, ERR_QUATERNION), renormalises
+ * q_meas, sorts the edges by tail and by head, packs structure-of-arrays
+ * device buffers and uploads them on `cuda_stream` (a cudaStream_t or NULL).
+ *   src, dst     m int32 edge endpoints (tail i, head j)
+ *   q_meas       m x 4 relative rotations q_ij
+ *   t_meas       m x 3 relative translations t_ij
+ *   kappa, omega m per-edge weights (> 0); NULL means all ones
+ * n >= 1, m >= 0.  The state is unset until pradmm_set_state* or
+ * pradmm_init_odometry.  On failure *out is NULL. */
+pradmm_status pradmm_create(int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                            const double* q_meas, const double* t_meas, const double* kappa,
+                            const double* omega, const pradmm_params* prm, void* cuda_stream,
+                            pradmm_t* out);
+
+/* Same as pradmm_create with every array in device memory (e.g. torch
+ * tensors); they are read once on the handle's stream before return. */
+pradmm_status pradmm_create_device(int64_t n, int64_t m, const int32_t* src_d, const int32_t* dst_d,
+                                   const double* q_meas_d, const double* t_meas_d,
+                                   const double* kappa_d, const double* omega_d,
+                                   const pradmm_params* prm, void* cuda_stream, pradmm_t* out);
+
+/* Initial point of Algorithm 1 from poses (q: n x 4, t: n x 3):
+ * p = q, s = t, lambda = z = 0 (reading of the unspecified initial multipliers). */
+pradmm_status pradmm_set_state(pradmm_t h, const double* q, const double* t);
+
+/* Full ADMM state (checkpoint/resume): p, q, lam n x 4; t, s, z n x 3. */
+pradmm_status pradmm_set_state_full(pradmm_t h, const double* p, const double* q, const double* t,
+                                    const double* s, const double* lam, const double* z);
+
+/* Initial poses by odometry composition along a spanning forest: edges are
+ * taken in input order, an edge joins the forest when it links two
+ * components, the lowest vertex of each component gets the identity, and the
+ * others follow q_j = q_i q_ij, t_j = t_i + R(q_i) t_ij (Section 2).  Then as
+ * pradmm_set_state.  (The paper starts from a chordal initialisation it does
+ * not define.) */
+pradmm_status pradmm_init_odometry(pradmm_t h);
+
+/* Runs `iters` >= 0 iterations of Algorithm 1 (no stopping test).
+ * e_last (nullable) receives e^k of the last iteration. */
+pradmm_status pradmm_step(pradmm_t h, int32_t iters, double* e_last);
+
+/* Runs Algorithm 1 until e^k < prm.tol or prm.max_iter iterations of this call.
+ * Returns PRADMM_OK on convergence, PRADMM_ERR_NOT_CONVERGED otherwise (the
+ * state stays valid).  iters_done, e_final are nullable. */
+pradmm_status pradmm_solve(pradmm_t h, int32_t* iters_done, double* e_final);
+
+/* F of Eq. (1) at (p, t) in double precision (Appendix E.1 reports p, since
+ * |q_i| != 1 during the iteration). */
+pradmm_status pradmm_objective(pradmm_t h, double* F);
+
+/* Copies the state to host arrays (any pointer may be NULL):
+ * p, q, lam n x 4; t, s, z n x 3. */
+pradmm_status pradmm_get_state(pradmm_t h, double* p, double* q, double* t, double* s, double* lam,
+                               double* z);
+
+/* Same with device destination arrays (double, same shapes). */
+pradmm_status pradmm_get_state_device(pradmm_t h, double* p, double* q, double* t, double* s,
+                                      double* lam, double* z);
+
+/* Output of Algorithm 1: rotations p (n x 4, unit) and translations t (n x 3). */
+pradmm_status pradmm_get_poses(pradmm_t h, double* q_out, double* t_out);
+
+/* Iterations run since the state was last set. */
+int64_t pradmm_iterations(pradmm_t h);
+
+/* Counters: [0] p-updates recomputed in FP64, [1] p-updates with |u| = 0
+ * that kept p^k, [2] iterations, [3] stop flag.  out has 4 entries. */
+pradmm_status pradmm_counters(pradmm_t h, int64_t* out);
+
+/* Algorithmic bytes of one iteration and of each sweep kernel under the
+ * byte model of the library's roofline report (FP32 words of every array a
+ * sweep needs, counted once per sweep):
+ *   out[0] total, out[1] q/lambda sweep, out[2] t sweep, out[3] s/z + next p sweep. */
+pradmm_status pradmm_bytes_per_iteration(pradmm_t h, double* out);
+
+/* Times `iters` iterations launched kernel by kernel on the handle's stream
+ * with CUDA events around each sweep kernel; ms_out[0..2] receive the mean
+ * duration (ms) of the q/lambda, t and s/z+p kernels, ms_out[3] the mean
+ * iteration time.  The state advances by `iters` iterations. */
+pradmm_status pradmm_profile_sweeps(pradmm_t h, int32_t iters, double* ms_out);
+
+/* Frees every resource of the handle (NULL is a no-op). */
+void pradmm_destroy(pradmm_t h);
+
+const char* pradmm_status_string(pradmm_status st);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* pradmm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PRADMM_H */

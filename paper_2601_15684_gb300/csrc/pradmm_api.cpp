@@ -1,0 +1,939 @@
+// C ABI of libpradmm (include/pradmm.h): input validation, the edge-sorted
+// structure-of-arrays graph builder, device memory, and the launch schedule
+// of the PRADMM iteration (Section 3.2 Eq. (3), Algorithm 1) on one GPU.
+#include "pradmm.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pradmm_internal.h"
+
+using pradmm::Ctrl;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+pradmm_status fail(pradmm_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define CU(call)                                                                                         \
+    do {                                                                                                 \
+        cudaError_t _e = (call);                                                                         \
+        if (_e != cudaSuccess)                                                                           \
+            return fail(_e == cudaErrorMemoryAllocation ? PRADMM_ERR_NOMEM : PRADMM_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(_e), __FILE__, __LINE__);                              \
+    } while (0)
+
+}  // namespace
+
+struct pradmm_s {
+    int64_t n = 0, m = 0;
+    pradmm_params prm{};
+    bool fp64 = false;
+    size_t rsize = 4;  // bytes per real
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int grid = 1, block = 256, obj_grid = 1;
+
+    // host copies (input order) for the odometry initialisation
+    std::vector<int32_t> src, dst;
+    std::vector<double> qe, te;
+    std::vector<double> inv2, inv3, inv4;  // 1/A_2, 1/A_3, 1/A_4 per vertex
+
+    std::vector<void*> allocs;
+    int32_t *out_ptr = nullptr, *out_dst = nullptr, *in_ptr = nullptr, *in_src = nullptr;
+    void *out_te = nullptr, *out_qk = nullptr, *in_te = nullptr, *in_qk = nullptr;
+    double *qe64 = nullptr, *te64 = nullptr, *ka64 = nullptr, *om64 = nullptr;
+    void *p[2] = {nullptr, nullptr}, *q = nullptr, *lam = nullptr, *t = nullptr, *s = nullptr, *z = nullptr;
+    double *inv2_d = nullptr, *inv3_d = nullptr, *inv4_d = nullptr;
+    double* stage = nullptr;  // 4n doubles
+    double* zeros = nullptr;  // 4n doubles of zero
+    double* part = nullptr;   // 4 * grid
+    double* obj_part = nullptr;
+    unsigned int* obj_ticket = nullptr;
+    double* F_dev = nullptr;
+    Ctrl* ctrl = nullptr;
+    Ctrl* ctrl_h = nullptr;   // pinned mirror
+
+    bool state_set = false;
+    bool pending = false;     // p^{k+1} already computed ahead
+
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaGraphConditionalHandle cond = 0;
+    bool graph_ready = false;
+
+    template <typename R>
+    pradmm::GraphDev<R> gdev() const {
+        pradmm::GraphDev<R> g;
+        g.n = n;
+        g.m = m;
+        g.out_ptr = out_ptr;
+        g.out_dst = out_dst;
+        g.out_te = static_cast<const R*>(out_te);
+        g.out_qk = static_cast<const R*>(out_qk);
+        g.in_ptr = in_ptr;
+        g.in_src = in_src;
+        g.in_te = static_cast<const R*>(in_te);
+        g.in_qk = static_cast<const R*>(in_qk);
+        return g;
+    }
+    template <typename R>
+    pradmm::StateDev<R> sdev() const {
+        pradmm::StateDev<R> S;
+        S.p[0] = static_cast<R*>(p[0]);
+        S.p[1] = static_cast<R*>(p[1]);
+        S.q = static_cast<R*>(q);
+        S.lam = static_cast<R*>(lam);
+        S.t = static_cast<R*>(t);
+        S.s = static_cast<R*>(s);
+        S.z = static_cast<R*>(z);
+        return S;
+    }
+    template <typename R>
+    pradmm::Coef<R> coef() const {
+        pradmm::Coef<R> c;
+        c.beta1 = R(prm.beta1);
+        c.beta2 = R(prm.beta2);
+        c.tb1 = R(prm.relax * prm.beta1);
+        c.tb2 = R(prm.relax * prm.beta2);
+        c.g1 = R(prm.gamma[0]);
+        c.g2 = R(prm.gamma[1]);
+        c.g3 = R(prm.gamma[2]);
+        c.g4 = R(prm.gamma[3]);
+        c.b1d = prm.beta1;
+        c.b2d = prm.beta2;
+        c.fb_thresh = prm.fallback_eps * (prm.beta1 + prm.gamma[0]);
+        return c;
+    }
+    pradmm::Launch launch(bool with_cond) const {
+        pradmm::Launch L;
+        L.grid = grid;
+        L.block = block;
+        L.stream = stream;
+        L.ctrl = ctrl;
+        L.part = part;
+        L.cond = cond;
+        L.has_cond = with_cond ? 1 : 0;
+        return L;
+    }
+};
+
+namespace {
+
+template <typename T>
+pradmm_status dalloc(pradmm_s* h, T** ptr, size_t count) {
+    void* v = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&v, bytes);
+    if (e != cudaSuccess)
+        return fail(e == cudaErrorMemoryAllocation ? PRADMM_ERR_NOMEM : PRADMM_ERR_CUDA, "cudaMalloc(%zu): %s",
+                    bytes, cudaGetErrorString(e));
+    h->allocs.push_back(v);
+    *ptr = static_cast<T*>(v);
+    return PRADMM_OK;
+}
+
+pradmm_status valloc(pradmm_s* h, void** ptr, size_t reals) {
+    if (h->fp64) {
+        double* d = nullptr;
+        pradmm_status st = dalloc(h, &d, reals);
+        *ptr = d;
+        return st;
+    }
+    float* f = nullptr;
+    pradmm_status st = dalloc(h, &f, reals);
+    *ptr = f;
+    return st;
+}
+
+#define ST(call)                          \
+    do {                                  \
+        pradmm_status _s = (call);        \
+        if (_s != PRADMM_OK) return _s;   \
+    } while (0)
+
+pradmm_status check_params(const pradmm_params* p) {
+    if (!(p->beta1 > 0) || !(p->beta2 > 0) || !std::isfinite(p->beta1) || !std::isfinite(p->beta2))
+        return fail(PRADMM_ERR_ARG, "beta1, beta2 must be finite and > 0");
+    if (!(p->relax > 0 && p->relax < 2)) return fail(PRADMM_ERR_ARG, "relax (tau) must lie in (0, 2)");
+    for (int k = 0; k < 4; ++k)
+        if (!(p->gamma[k] >= 0) || !std::isfinite(p->gamma[k]))
+            return fail(PRADMM_ERR_ARG, "gamma[%d] must be finite and >= 0", k);
+    if (!(p->tol >= 0)) return fail(PRADMM_ERR_ARG, "tol must be >= 0");
+    if (p->max_iter < 0) return fail(PRADMM_ERR_ARG, "max_iter must be >= 0");
+    if (p->precision != PRADMM_FP64 && p->precision != PRADMM_FP32)
+        return fail(PRADMM_ERR_ARG, "precision must be PRADMM_FP64 or PRADMM_FP32");
+    if (!(p->fallback_eps >= 0)) return fail(PRADMM_ERR_ARG, "fallback_eps must be >= 0");
+    if (p->block != 0 && (p->block < 32 || p->block > 256 || p->block % 32 != 0))
+        return fail(PRADMM_ERR_ARG, "block must be 0 or a multiple of 32 in [32, 256]");
+    return PRADMM_OK;
+}
+
+// Stable counting sort of edge ids by key; returns ptr[n+1] and perm (sorted
+// position -> input edge).
+void counting_sort(int64_t n, int64_t m, const int32_t* key, std::vector<int32_t>& ptr, std::vector<int32_t>& perm) {
+    ptr.assign(n + 1, 0);
+    for (int64_t e = 0; e < m; ++e) ptr[key[e] + 1]++;
+    for (int64_t i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
+    std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
+    perm.assign(m, 0);
+    for (int64_t e = 0; e < m; ++e) perm[fill[key[e]]++] = (int32_t)e;
+}
+
+template <typename R>
+void pack_edges(const pradmm_s* h, const std::vector<int32_t>& perm, const std::vector<double>& ka,
+                const std::vector<double>& om, std::vector<R>& te_o, std::vector<R>& qk_o) {
+    te_o.resize(4 * h->m);
+    qk_o.resize(4 * h->m);
+    for (int64_t k = 0; k < h->m; ++k) {
+        const int64_t e = perm[k];
+        te_o[4 * k + 0] = R(h->te[3 * e + 0]);
+        te_o[4 * k + 1] = R(h->te[3 * e + 1]);
+        te_o[4 * k + 2] = R(h->te[3 * e + 2]);
+        te_o[4 * k + 3] = R(om[e]);
+        for (int c = 0; c < 4; ++c) qk_o[4 * k + c] = R(ka[e] * h->qe[4 * e + c]);
+    }
+}
+
+template <typename R>
+pradmm_status upload_edges(pradmm_s* h, const std::vector<int32_t>& perm_out, const std::vector<int32_t>& perm_in,
+                           const std::vector<double>& ka, const std::vector<double>& om) {
+    std::vector<R> te_o, qk_o;
+    pack_edges<R>(h, perm_out, ka, om, te_o, qk_o);
+    CU(cudaMemcpy(h->out_te, te_o.data(), sizeof(R) * te_o.size(), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->out_qk, qk_o.data(), sizeof(R) * qk_o.size(), cudaMemcpyHostToDevice));
+    pack_edges<R>(h, perm_in, ka, om, te_o, qk_o);
+    CU(cudaMemcpy(h->in_te, te_o.data(), sizeof(R) * te_o.size(), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->in_qk, qk_o.data(), sizeof(R) * qk_o.size(), cudaMemcpyHostToDevice));
+    return PRADMM_OK;
+}
+
+pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const double* q_meas, const double* t_meas,
+                    const double* kappa, const double* omega) {
+    const int64_t n = h->n, m = h->m;
+    // ---- validation (never trust the caller's graph) ----
+    std::vector<double> ka(m, 1.0), om(m, 1.0);
+    h->src.assign(src, src + m);
+    h->dst.assign(dst, dst + m);
+    h->qe.assign(q_meas, q_meas + 4 * m);
+    h->te.assign(t_meas, t_meas + 3 * m);
+    for (int64_t e = 0; e < m; ++e) {
+        if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n)
+            return fail(PRADMM_ERR_INDEX, "edge %lld = (%d, %d) has an endpoint outside [0, %lld)", (long long)e,
+                        src[e], dst[e], (long long)n);
+        if (src[e] == dst[e]) return fail(PRADMM_ERR_SELFLOOP, "edge %lld is a self-loop (%d, %d)", (long long)e, src[e], dst[e]);
+        if (kappa) ka[e] = kappa[e];
+        if (omega) om[e] = omega[e];
+        if (!std::isfinite(ka[e]) || !std::isfinite(om[e]) || !(ka[e] > 0) || !(om[e] > 0))
+            return fail(ka[e] > 0 && om[e] > 0 ? PRADMM_ERR_NONFINITE : PRADMM_ERR_ARG,
+                        "edge %lld: weights must be finite and > 0", (long long)e);
+        double nn = 0.0;
+        for (int c = 0; c < 4; ++c) {
+            if (!std::isfinite(q_meas[4 * e + c])) return fail(PRADMM_ERR_NONFINITE, "edge %lld: q_meas not finite", (long long)e);
+            nn += q_meas[4 * e + c] * q_meas[4 * e + c];
+        }
+        for (int c = 0; c < 3; ++c)
+            if (!std::isfinite(t_meas[3 * e + c])) return fail(PRADMM_ERR_NONFINITE, "edge %lld: t_meas not finite", (long long)e);
+        nn = std::sqrt(nn);
+        if (std::fabs(nn - 1.0) > 1e-6)
+            return fail(PRADMM_ERR_QUATERNION, "edge %lld: |q_meas| = %.17g is not 1", (long long)e, nn);
+        for (int c = 0; c < 4; ++c) h->qe[4 * e + c] /= nn;
+    }
+    // ---- CSR by tail (out) and by head (in) ----
+    std::vector<int32_t> optr, operm, iptr, iperm;
+    counting_sort(n, m, src, optr, operm);
+    counting_sort(n, m, dst, iptr, iperm);
+    // ---- iteration-invariant scalar block matrices (Appendix B, scalar Sigma) ----
+    std::vector<double> A2(n, h->prm.beta1 + h->prm.gamma[1]), A3(n, h->prm.beta2 + h->prm.gamma[2]),
+        A4(n, h->prm.beta2 + h->prm.gamma[3]);
+    for (int64_t e = 0; e < m; ++e) {
+        const double* tv = &h->te[3 * e];
+        const double tn2 = tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2];
+        A2[src[e]] += 2.0 * (om[e] * tn2 + ka[e]);  // |p_i| = |p_j| = |q_e| = 1
+        A3[dst[e]] += 2.0 * om[e];
+        A4[src[e]] += 2.0 * om[e];
+    }
+    h->inv2.resize(n);
+    h->inv3.resize(n);
+    h->inv4.resize(n);
+    for (int64_t i = 0; i < n; ++i) {
+        h->inv2[i] = 1.0 / A2[i];
+        h->inv3[i] = 1.0 / A3[i];
+        h->inv4[i] = 1.0 / A4[i];
+    }
+    // ---- device buffers ----
+    ST(dalloc(h, &h->out_ptr, n + 1));
+    ST(dalloc(h, &h->in_ptr, n + 1));
+    ST(dalloc(h, &h->out_dst, m));
+    ST(dalloc(h, &h->in_src, m));
+    ST(valloc(h, &h->out_te, 4 * m));
+    ST(valloc(h, &h->out_qk, 4 * m));
+    ST(valloc(h, &h->in_te, 4 * m));
+    ST(valloc(h, &h->in_qk, 4 * m));
+    ST(dalloc(h, &h->qe64, 4 * m));
+    ST(dalloc(h, &h->te64, 3 * m));
+    ST(dalloc(h, &h->ka64, m));
+    ST(dalloc(h, &h->om64, m));
+    for (int b = 0; b < 2; ++b) ST(valloc(h, &h->p[b], 4 * n));
+    ST(valloc(h, &h->q, 4 * n));
+    ST(valloc(h, &h->lam, 4 * n));
+    ST(valloc(h, &h->t, 4 * n));
+    ST(valloc(h, &h->s, 4 * n));
+    ST(valloc(h, &h->z, 4 * n));
+    ST(dalloc(h, &h->inv2_d, n));
+    ST(dalloc(h, &h->inv3_d, n));
+    ST(dalloc(h, &h->inv4_d, n));
+    ST(dalloc(h, &h->stage, 4 * n));
+    ST(dalloc(h, &h->zeros, 4 * n));
+    ST(dalloc(h, &h->part, 4 * (size_t)h->grid));
+    ST(dalloc(h, &h->obj_part, (size_t)h->obj_grid));
+    ST(dalloc(h, &h->obj_ticket, 1));
+    ST(dalloc(h, &h->F_dev, 1));
+    ST(dalloc(h, &h->ctrl, 1));
+    {
+        void* hp = nullptr;
+        CU(cudaMallocHost(&hp, sizeof(Ctrl)));
+        h->ctrl_h = static_cast<Ctrl*>(hp);
+        std::memset(h->ctrl_h, 0, sizeof(Ctrl));
+    }
+    // uploads (pageable, synchronous with respect to the host buffers)
+    std::vector<int32_t> tmp(m);
+    CU(cudaMemcpy(h->out_ptr, optr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->in_ptr, iptr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
+    for (int64_t k = 0; k < m; ++k) tmp[k] = dst[operm[k]];
+    CU(cudaMemcpy(h->out_dst, tmp.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
+    for (int64_t k = 0; k < m; ++k) tmp[k] = src[iperm[k]];
+    CU(cudaMemcpy(h->in_src, tmp.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
+    if (h->fp64) {
+        ST(upload_edges<double>(h, operm, iperm, ka, om));
+    } else {
+        ST(upload_edges<float>(h, operm, iperm, ka, om));
+    }
+    {
+        std::vector<double> b4(4 * m), b3(3 * m), b1k(m), b1o(m);
+        for (int64_t k = 0; k < m; ++k) {
+            const int64_t e = operm[k];
+            for (int c = 0; c < 4; ++c) b4[4 * k + c] = h->qe[4 * e + c];
+            for (int c = 0; c < 3; ++c) b3[3 * k + c] = h->te[3 * e + c];
+            b1k[k] = ka[e];
+            b1o[k] = om[e];
+        }
+        CU(cudaMemcpy(h->qe64, b4.data(), sizeof(double) * 4 * m, cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(h->te64, b3.data(), sizeof(double) * 3 * m, cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(h->ka64, b1k.data(), sizeof(double) * m, cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(h->om64, b1o.data(), sizeof(double) * m, cudaMemcpyHostToDevice));
+    }
+    CU(cudaMemcpy(h->inv2_d, h->inv2.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->inv3_d, h->inv3.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->inv4_d, h->inv4.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    CU(cudaMemsetAsync(h->zeros, 0, sizeof(double) * 4 * n, h->stream));
+    CU(cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream));
+    CU(cudaMemsetAsync(h->obj_ticket, 0, sizeof(unsigned int), h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return PRADMM_OK;
+}
+
+void free_all(pradmm_s* h) {
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    for (void* v : h->allocs) cudaFree(v);
+    h->allocs.clear();
+    if (h->ctrl_h) cudaFreeHost(h->ctrl_h);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+pradmm_status create_common(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const double* q_meas,
+                            const double* t_meas, const double* kappa, const double* omega, const pradmm_params* prm,
+                            void* stream, pradmm_t* out) {
+    if (!out) return fail(PRADMM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || m < 0 || n > INT32_MAX - 1 || m > INT32_MAX - 1)
+        return fail(PRADMM_ERR_ARG, "need 1 <= n < 2^31 - 1 and 0 <= m < 2^31 - 1");
+    if (m > 0 && (!src || !dst || !q_meas || !t_meas)) return fail(PRADMM_ERR_ARG, "edge arrays must not be NULL");
+    pradmm_params p;
+    if (prm) {
+        p = *prm;
+    } else {
+        pradmm_default_params(&p);
+    }
+    ST(check_params(&p));
+    pradmm_s* h = new (std::nothrow) pradmm_s();
+    if (!h) return fail(PRADMM_ERR_NOMEM, "host allocation failed");
+    h->n = n;
+    h->m = m;
+    h->prm = p;
+    h->fp64 = p.precision == PRADMM_FP64;
+    h->rsize = h->fp64 ? 8 : 4;
+    h->block = p.block > 0 ? p.block : 256;
+    pradmm_status st = PRADMM_OK;
+    do {
+        cudaError_t e;
+        if (stream) {
+            h->stream = static_cast<cudaStream_t>(stream);
+        } else {
+            e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) {
+                st = fail(PRADMM_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+                break;
+            }
+            h->own_stream = true;
+        }
+        int dev = 0, sms = 0, bps = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+            (e = pradmm::sweep_occupancy(h->fp64 ? 1 : 0, h->block, &bps)) != cudaSuccess) {
+            st = fail(PRADMM_ERR_CUDA, "device query: %s", cudaGetErrorString(e));
+            break;
+        }
+        if (bps < 1) bps = 1;
+        const int64_t need = (n + h->block - 1) / h->block;
+        const int64_t cap = (int64_t)sms * bps;
+        h->grid = (int)std::max<int64_t>(1, std::min(need, cap));
+        h->obj_grid = h->grid;
+        st = build(h, src, dst, q_meas, t_meas, kappa, omega);
+    } while (0);
+    if (st != PRADMM_OK) {
+        free_all(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return PRADMM_OK;
+}
+
+template <typename R>
+pradmm_status set_state_dev(pradmm_s* h, const double* p, const double* q, const double* t, const double* s,
+                            const double* lam, const double* z, bool device_src) {
+    // p, q, lam: n x 4; t, s, z: n x 3 (host or device doubles); NULL lam/z mean zero.
+    const int64_t n = h->n;
+    cudaStream_t st = h->stream;
+    auto put4 = [&](const double* src, void* dst) -> pradmm_status {
+        const double* d = src;
+        if (!src) {
+            d = h->zeros;
+        } else if (!device_src) {
+            CU(cudaMemcpyAsync(h->stage, src, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, st));
+            d = h->stage;
+        }
+        CU(pradmm::launch_pack4<R>(d, static_cast<R*>(dst), n, st));
+        if (src && !device_src) CU(cudaStreamSynchronize(st));  // stage is reused
+        return PRADMM_OK;
+    };
+    auto put3 = [&](const double* src, const double* inv, void* dst) -> pradmm_status {
+        const double* d = src;
+        if (!src) {
+            d = h->zeros;
+        } else if (!device_src) {
+            CU(cudaMemcpyAsync(h->stage, src, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+            d = h->stage;
+        }
+        CU(pradmm::launch_pack3<R>(d, inv, static_cast<R*>(dst), n, st));
+        if (src && !device_src) CU(cudaStreamSynchronize(st));
+        return PRADMM_OK;
+    };
+    CU(cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), st));  // k = 0: p^0 lives in p[0]
+    ST(put4(p, h->p[0]));
+    ST(put4(q, h->q));
+    ST(put4(lam, h->lam));
+    ST(put3(t, h->inv3_d, h->t));
+    ST(put3(s, h->inv2_d, h->s));
+    ST(put3(z, h->inv4_d, h->z));
+    CU(cudaStreamSynchronize(st));
+    h->state_set = true;
+    h->pending = false;
+    return PRADMM_OK;
+}
+
+pradmm_status set_state_any(pradmm_s* h, const double* p, const double* q, const double* t, const double* s,
+                            const double* lam, const double* z, bool device_src) {
+    if (h->fp64) return set_state_dev<double>(h, p, q, t, s, lam, z, device_src);
+    return set_state_dev<float>(h, p, q, t, s, lam, z, device_src);
+}
+
+pradmm_status read_ctrl(pradmm_s* h) {
+    CU(cudaMemcpyAsync(h->ctrl_h, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return PRADMM_OK;
+}
+
+template <typename R>
+pradmm_status launch_iters_plain(pradmm_s* h, long long iters) {
+    const auto g = h->gdev<R>();
+    const auto S = h->sdev<R>();
+    const auto c = h->coef<R>();
+    const auto L = h->launch(false);
+    for (long long k = 0; k < iters; ++k) {
+        CU(pradmm::launch_q<R>(g, S, c, L));
+        CU(pradmm::launch_t<R>(g, S, c, L));
+        CU(pradmm::launch_sp<R>(g, S, c, L));
+    }
+    return PRADMM_OK;
+}
+
+template <typename R>
+pradmm_status ensure_graph(pradmm_s* h) {
+    if (h->graph_ready) return PRADMM_OK;
+    CU(cudaGraphCreate(&h->graph, 0));
+    CU(cudaGraphConditionalHandleCreate(&h->cond, h->graph, 1u, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h->cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CU(cudaGraphAddNode(&node, h->graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CU(cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const auto g = h->gdev<R>();
+    const auto S = h->sdev<R>();
+    const auto c = h->coef<R>();
+    const auto L = h->launch(true);
+    cudaError_t e1 = pradmm::launch_q<R>(g, S, c, L);
+    cudaError_t e2 = pradmm::launch_t<R>(g, S, c, L);
+    cudaError_t e3 = pradmm::launch_sp<R>(g, S, c, L);
+    cudaGraph_t captured = nullptr;
+    cudaError_t e4 = cudaStreamEndCapture(h->stream, &captured);
+    CU(e1);
+    CU(e2);
+    CU(e3);
+    CU(e4);
+    CU(cudaGraphInstantiate(&h->graph_exec, h->graph, 0));
+    h->graph_ready = true;
+    return PRADMM_OK;
+}
+
+template <typename R>
+pradmm_status run(pradmm_s* h, long long iters, bool use_tol) {
+    if (!h->state_set) return fail(PRADMM_ERR_STATE, "state is not set (pradmm_set_state or pradmm_init_odometry)");
+    if (iters <= 0) return read_ctrl(h);
+    CU(pradmm::launch_arm(h->ctrl, iters, use_tol ? 1 : 0, h->prm.tol, h->stream));
+    if (!h->pending) {
+        CU(pradmm::launch_p<R>(h->gdev<R>(), h->sdev<R>(), h->coef<R>(), h->launch(false)));
+        h->pending = true;
+    }
+    if (h->prm.use_graph) {
+        ST(ensure_graph<R>(h));
+        CU(cudaGraphLaunch(h->graph_exec, h->stream));
+    } else {
+        ST(launch_iters_plain<R>(h, iters));
+    }
+    ST(read_ctrl(h));
+    if (h->ctrl_h->nonfinite) return fail(PRADMM_ERR_NONFINITE, "the iteration produced a non-finite residual");
+    return PRADMM_OK;
+}
+
+pradmm_status run_any(pradmm_s* h, long long iters, bool use_tol) {
+    return h->fp64 ? run<double>(h, iters, use_tol) : run<float>(h, iters, use_tol);
+}
+
+// ---- odometry initialisation (host): spanning forest by edge order --------
+struct UF {
+    std::vector<int64_t> par;
+    explicit UF(int64_t n) : par(n) {
+        for (int64_t i = 0; i < n; ++i) par[i] = i;
+    }
+    int64_t find(int64_t x) {
+        while (par[x] != x) {
+            par[x] = par[par[x]];
+            x = par[x];
+        }
+        return x;
+    }
+};
+
+inline void hmul(const double* a, const double* b, double* o) {
+    const double w = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    const double x = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    const double y = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    const double z = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+    o[0] = w;
+    o[1] = x;
+    o[2] = y;
+    o[3] = z;
+}
+
+// R(q) v via the rotation matrix of a unit quaternion
+inline void hrot(const double* q, const double* v, double* o) {
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    const double r00 = 1 - 2 * (y * y + z * z), r01 = 2 * (x * y - w * z), r02 = 2 * (x * z + w * y);
+    const double r10 = 2 * (x * y + w * z), r11 = 1 - 2 * (x * x + z * z), r12 = 2 * (y * z - w * x);
+    const double r20 = 2 * (x * z - w * y), r21 = 2 * (y * z + w * x), r22 = 1 - 2 * (x * x + y * y);
+    o[0] = r00 * v[0] + r01 * v[1] + r02 * v[2];
+    o[1] = r10 * v[0] + r11 * v[1] + r12 * v[2];
+    o[2] = r20 * v[0] + r21 * v[1] + r22 * v[2];
+}
+
+void odometry(const pradmm_s* h, std::vector<double>& q, std::vector<double>& t) {
+    const int64_t n = h->n, m = h->m;
+    UF uf(n);
+    std::vector<int32_t> tree;
+    tree.reserve(n);
+    for (int64_t e = 0; e < m; ++e) {
+        const int64_t a = uf.find(h->src[e]), b = uf.find(h->dst[e]);
+        if (a == b) continue;
+        if (a < b) uf.par[b] = a; else uf.par[a] = b;
+        tree.push_back((int32_t)e);
+    }
+    std::vector<int64_t> ptr(n + 1, 0);
+    for (int32_t e : tree) {
+        ptr[h->src[e] + 1]++;
+        ptr[h->dst[e] + 1]++;
+    }
+    for (int64_t i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
+    std::vector<int32_t> adj(2 * tree.size());
+    std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int32_t e : tree) {
+        adj[fill[h->src[e]]++] = e;
+        adj[fill[h->dst[e]]++] = e;
+    }
+    q.assign(4 * n, 0.0);
+    t.assign(3 * n, 0.0);
+    std::vector<char> seen(n, 0);
+    std::vector<int64_t> queue;
+    queue.reserve(n);
+    for (int64_t r = 0; r < n; ++r) {
+        if (seen[r]) continue;
+        seen[r] = 1;
+        q[4 * r] = 1.0;
+        queue.clear();
+        queue.push_back(r);
+        for (size_t head = 0; head < queue.size(); ++head) {
+            const int64_t v = queue[head];
+            for (int64_t k = ptr[v]; k < ptr[v + 1]; ++k) {
+                const int32_t e = adj[k];
+                const int64_t a = h->src[e], b = h->dst[e];
+                double rt[3];
+                if (a == v && !seen[b]) {
+                    hmul(&q[4 * a], &h->qe[4 * e], &q[4 * b]);
+                    hrot(&q[4 * a], &h->te[3 * e], rt);
+                    for (int c = 0; c < 3; ++c) t[3 * b + c] = t[3 * a + c] + rt[c];
+                    seen[b] = 1;
+                    queue.push_back(b);
+                } else if (b == v && !seen[a]) {
+                    const double qc[4] = {h->qe[4 * e], -h->qe[4 * e + 1], -h->qe[4 * e + 2], -h->qe[4 * e + 3]};
+                    hmul(&q[4 * b], qc, &q[4 * a]);
+                    hrot(&q[4 * a], &h->te[3 * e], rt);
+                    for (int c = 0; c < 3; ++c) t[3 * a + c] = t[3 * b + c] - rt[c];
+                    seen[a] = 1;
+                    queue.push_back(a);
+                }
+            }
+        }
+    }
+}
+
+template <typename R>
+pradmm_status get_state_impl(pradmm_s* h, double* p, double* q, double* t, double* s, double* lam, double* z,
+                             bool device_dst) {
+    if (!h->state_set) return fail(PRADMM_ERR_STATE, "state is not set");
+    ST(read_ctrl(h));
+    const int64_t n = h->n;
+    const long long k = h->ctrl_h->iter;
+    cudaStream_t st = h->stream;
+    auto get4 = [&](const void* src, double* dst) -> pradmm_status {
+        if (!dst) return PRADMM_OK;
+        double* d = device_dst ? dst : h->stage;
+        CU(pradmm::launch_unpack4<R>(static_cast<const R*>(src), d, n, st));
+        if (!device_dst) CU(cudaMemcpyAsync(dst, h->stage, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        return PRADMM_OK;
+    };
+    auto get3 = [&](const void* src, double* dst) -> pradmm_status {
+        if (!dst) return PRADMM_OK;
+        double* d = device_dst ? dst : h->stage;
+        CU(pradmm::launch_unpack3<R>(static_cast<const R*>(src), d, n, st));
+        if (!device_dst) CU(cudaMemcpyAsync(dst, h->stage, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        return PRADMM_OK;
+    };
+    ST(get4(h->p[k & 1], p));
+    ST(get4(h->q, q));
+    ST(get4(h->lam, lam));
+    ST(get3(h->t, t));
+    ST(get3(h->s, s));
+    ST(get3(h->z, z));
+    return PRADMM_OK;
+}
+
+template <typename R>
+pradmm_status profile_impl(pradmm_s* h, int32_t iters, double* ms_out) {
+    if (!h->state_set) return fail(PRADMM_ERR_STATE, "state is not set");
+    if (iters < 1) return fail(PRADMM_ERR_ARG, "iters must be >= 1");
+    const auto g = h->gdev<R>();
+    const auto S = h->sdev<R>();
+    const auto c = h->coef<R>();
+    const auto L = h->launch(false);
+    CU(pradmm::launch_arm(h->ctrl, iters, 0, 0.0, h->stream));
+    if (!h->pending) {
+        CU(pradmm::launch_p<R>(g, S, c, L));
+        h->pending = true;
+    }
+    std::vector<cudaEvent_t> ev(4 * (size_t)iters);
+    for (auto& e : ev) CU(cudaEventCreate(&e));
+    pradmm_status st = PRADMM_OK;
+    for (int32_t k = 0; k < iters && st == PRADMM_OK; ++k) {
+        cudaEvent_t* E = &ev[4 * (size_t)k];
+        cudaError_t err = cudaEventRecord(E[0], h->stream);
+        if (!err) err = pradmm::launch_q<R>(g, S, c, L);
+        if (!err) err = cudaEventRecord(E[1], h->stream);
+        if (!err) err = pradmm::launch_t<R>(g, S, c, L);
+        if (!err) err = cudaEventRecord(E[2], h->stream);
+        if (!err) err = pradmm::launch_sp<R>(g, S, c, L);
+        if (!err) err = cudaEventRecord(E[3], h->stream);
+        if (err) st = fail(PRADMM_ERR_CUDA, "profile launch: %s", cudaGetErrorString(err));
+    }
+    if (st == PRADMM_OK) {
+        cudaError_t err = cudaStreamSynchronize(h->stream);
+        if (err) st = fail(PRADMM_ERR_CUDA, "profile sync: %s", cudaGetErrorString(err));
+    }
+    if (st == PRADMM_OK) {
+        double acc[4] = {0, 0, 0, 0};
+        for (int32_t k = 0; k < iters; ++k) {
+            cudaEvent_t* E = &ev[4 * (size_t)k];
+            float a = 0, b = 0, cc = 0, d = 0;
+            cudaEventElapsedTime(&a, E[0], E[1]);
+            cudaEventElapsedTime(&b, E[1], E[2]);
+            cudaEventElapsedTime(&cc, E[2], E[3]);
+            cudaEventElapsedTime(&d, E[0], E[3]);
+            acc[0] += a;
+            acc[1] += b;
+            acc[2] += cc;
+            acc[3] += d;
+        }
+        for (int j = 0; j < 4; ++j) ms_out[j] = acc[j] / iters;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    if (st == PRADMM_OK) st = read_ctrl(h);
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pradmm_default_params(pradmm_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->beta1 = 1.0;
+    p->beta2 = 1.0;
+    p->relax = 1.5;
+    p->gamma[0] = 1.0;
+    p->gamma[1] = 1e-3;
+    p->gamma[2] = 1e-3;
+    p->gamma[3] = 1e-3;
+    p->tol = 1e-4;
+    p->max_iter = 300;
+    p->precision = PRADMM_FP32;
+    p->fallback_eps = 1e-6;
+    p->use_graph = 1;
+    p->block = 0;
+}
+
+pradmm_status pradmm_create(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const double* q_meas,
+                            const double* t_meas, const double* kappa, const double* omega, const pradmm_params* prm,
+                            void* cuda_stream, pradmm_t* out) {
+    try {
+        return create_common(n, m, src, dst, q_meas, t_meas, kappa, omega, prm, cuda_stream, out);
+    } catch (const std::bad_alloc&) {
+        return fail(PRADMM_ERR_NOMEM, "host allocation failed");
+    }
+}
+
+pradmm_status pradmm_create_device(int64_t n, int64_t m, const int32_t* src_d, const int32_t* dst_d,
+                                   const double* q_meas_d, const double* t_meas_d, const double* kappa_d,
+                                   const double* omega_d, const pradmm_params* prm, void* cuda_stream,
+                                   pradmm_t* out) {
+    if (!out) return fail(PRADMM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (m < 0 || m > INT32_MAX - 1) return fail(PRADMM_ERR_ARG, "bad m");
+    if (m > 0 && (!src_d || !dst_d || !q_meas_d || !t_meas_d)) return fail(PRADMM_ERR_ARG, "edge arrays must not be NULL");
+    try {
+        // the graph builder validates and sorts on the host: bring the edges over once
+        std::vector<int32_t> src(m), dst(m);
+        std::vector<double> qm(4 * m), tm(3 * m), ka, om;
+        cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+        if (m > 0) {
+            CU(cudaMemcpyAsync(src.data(), src_d, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, st));
+            CU(cudaMemcpyAsync(dst.data(), dst_d, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, st));
+            CU(cudaMemcpyAsync(qm.data(), q_meas_d, sizeof(double) * 4 * m, cudaMemcpyDeviceToHost, st));
+            CU(cudaMemcpyAsync(tm.data(), t_meas_d, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, st));
+            if (kappa_d) {
+                ka.resize(m);
+                CU(cudaMemcpyAsync(ka.data(), kappa_d, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+            }
+            if (omega_d) {
+                om.resize(m);
+                CU(cudaMemcpyAsync(om.data(), omega_d, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+            }
+            CU(cudaStreamSynchronize(st));
+        }
+        return create_common(n, m, src.data(), dst.data(), qm.data(), tm.data(), kappa_d ? ka.data() : nullptr,
+                             omega_d ? om.data() : nullptr, prm, cuda_stream, out);
+    } catch (const std::bad_alloc&) {
+        return fail(PRADMM_ERR_NOMEM, "host allocation failed");
+    }
+}
+
+pradmm_status pradmm_set_state(pradmm_t h, const double* q, const double* t) {
+    if (!h || !q || !t) return fail(PRADMM_ERR_ARG, "NULL argument");
+    for (int64_t k = 0; k < 4 * h->n; ++k)
+        if (!std::isfinite(q[k])) return fail(PRADMM_ERR_NONFINITE, "q not finite");
+    for (int64_t k = 0; k < 3 * h->n; ++k)
+        if (!std::isfinite(t[k])) return fail(PRADMM_ERR_NONFINITE, "t not finite");
+    return set_state_any(h, q, q, t, t, nullptr, nullptr, false);
+}
+
+pradmm_status pradmm_set_state_full(pradmm_t h, const double* p, const double* q, const double* t, const double* s,
+                                    const double* lam, const double* z) {
+    if (!h || !p || !q || !t || !s || !lam || !z) return fail(PRADMM_ERR_ARG, "NULL argument");
+    const double* a4[3] = {p, q, lam};
+    const double* a3[3] = {t, s, z};
+    for (auto a : a4)
+        for (int64_t k = 0; k < 4 * h->n; ++k)
+            if (!std::isfinite(a[k])) return fail(PRADMM_ERR_NONFINITE, "state not finite");
+    for (auto a : a3)
+        for (int64_t k = 0; k < 3 * h->n; ++k)
+            if (!std::isfinite(a[k])) return fail(PRADMM_ERR_NONFINITE, "state not finite");
+    return set_state_any(h, p, q, t, s, lam, z, false);
+}
+
+pradmm_status pradmm_init_odometry(pradmm_t h) {
+    if (!h) return fail(PRADMM_ERR_ARG, "NULL handle");
+    try {
+        std::vector<double> q, t;
+        odometry(h, q, t);
+        return set_state_any(h, q.data(), q.data(), t.data(), t.data(), nullptr, nullptr, false);
+    } catch (const std::bad_alloc&) {
+        return fail(PRADMM_ERR_NOMEM, "host allocation failed");
+    }
+}
+
+pradmm_status pradmm_step(pradmm_t h, int32_t iters, double* e_last) {
+    if (!h) return fail(PRADMM_ERR_ARG, "NULL handle");
+    if (iters < 0) return fail(PRADMM_ERR_ARG, "iters must be >= 0");
+    ST(run_any(h, iters, false));
+    if (e_last) *e_last = h->ctrl_h->e_last;
+    return PRADMM_OK;
+}
+
+pradmm_status pradmm_solve(pradmm_t h, int32_t* iters_done, double* e_final) {
+    if (!h) return fail(PRADMM_ERR_ARG, "NULL handle");
+    if (!h->state_set) return fail(PRADMM_ERR_STATE, "state is not set");
+    ST(read_ctrl(h));
+    const long long k0 = h->ctrl_h->iter;
+    ST(run_any(h, h->prm.max_iter, true));
+    if (iters_done) *iters_done = (int32_t)(h->ctrl_h->iter - k0);
+    if (e_final) *e_final = h->ctrl_h->e_last;
+    if (h->prm.max_iter > 0 && h->ctrl_h->stop) return PRADMM_OK;
+    return fail(PRADMM_ERR_NOT_CONVERGED, "e = %.6g >= tol = %.6g after %d iterations", h->ctrl_h->e_last, h->prm.tol,
+                (int)(h->ctrl_h->iter - k0));
+}
+
+pradmm_status pradmm_objective(pradmm_t h, double* F) {
+    if (!h || !F) return fail(PRADMM_ERR_ARG, "NULL argument");
+    if (!h->state_set) return fail(PRADMM_ERR_STATE, "state is not set");
+    cudaError_t e;
+    if (h->fp64)
+        e = pradmm::launch_objective<double>(h->gdev<double>(), h->sdev<double>(), h->out_ptr, h->out_dst, h->qe64,
+                                             h->te64, h->ka64, h->om64, h->ctrl, h->obj_part, h->obj_ticket, h->F_dev,
+                                             h->obj_grid, h->block, h->stream);
+    else
+        e = pradmm::launch_objective<float>(h->gdev<float>(), h->sdev<float>(), h->out_ptr, h->out_dst, h->qe64,
+                                            h->te64, h->ka64, h->om64, h->ctrl, h->obj_part, h->obj_ticket, h->F_dev,
+                                            h->obj_grid, h->block, h->stream);
+    CU(e);
+    CU(cudaMemcpyAsync(F, h->F_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return PRADMM_OK;
+}
+
+pradmm_status pradmm_get_state(pradmm_t h, double* p, double* q, double* t, double* s, double* lam, double* z) {
+    if (!h) return fail(PRADMM_ERR_ARG, "NULL handle");
+    return h->fp64 ? get_state_impl<double>(h, p, q, t, s, lam, z, false)
+                   : get_state_impl<float>(h, p, q, t, s, lam, z, false);
+}
+
+pradmm_status pradmm_get_state_device(pradmm_t h, double* p, double* q, double* t, double* s, double* lam, double* z) {
+    if (!h) return fail(PRADMM_ERR_ARG, "NULL handle");
+    return h->fp64 ? get_state_impl<double>(h, p, q, t, s, lam, z, true)
+                   : get_state_impl<float>(h, p, q, t, s, lam, z, true);
+}
+
+pradmm_status pradmm_get_poses(pradmm_t h, double* q_out, double* t_out) {
+    return pradmm_get_state(h, q_out, nullptr, t_out, nullptr, nullptr, nullptr);
+}
+
+int64_t pradmm_iterations(pradmm_t h) {
+    if (!h || read_ctrl(h) != PRADMM_OK) return -1;
+    return h->ctrl_h->iter;
+}
+
+pradmm_status pradmm_counters(pradmm_t h, int64_t* out) {
+    if (!h || !out) return fail(PRADMM_ERR_ARG, "NULL argument");
+    ST(read_ctrl(h));
+    out[0] = (int64_t)h->ctrl_h->fallbacks;
+    out[1] = (int64_t)h->ctrl_h->zero_u;
+    out[2] = h->ctrl_h->iter;
+    out[3] = h->ctrl_h->stop;
+    return PRADMM_OK;
+}
+
+pradmm_status pradmm_bytes_per_iteration(pradmm_t h, double* out) {
+    if (!h || !out) return fail(PRADMM_ERR_ARG, "NULL argument");
+    // words per vertex / per edge of each sweep (FP32 words; indices count one word)
+    const double w = (double)h->rsize, n = (double)h->n, m = (double)h->m;
+    out[1] = w * (28.0 * n + 13.0 * m);           // q-block + lambda
+    out[2] = w * (14.0 * n + 5.0 * m);            // t-block
+    out[3] = w * ((17.0 + 24.0) * n + (5.0 + 11.0) * m);  // s-block + z, then p-block
+    out[0] = out[1] + out[2] + out[3];
+    return PRADMM_OK;
+}
+
+pradmm_status pradmm_profile_sweeps(pradmm_t h, int32_t iters, double* ms_out) {
+    if (!h || !ms_out) return fail(PRADMM_ERR_ARG, "NULL argument");
+    return h->fp64 ? profile_impl<double>(h, iters, ms_out) : profile_impl<float>(h, iters, ms_out);
+}
+
+void pradmm_destroy(pradmm_t h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+const char* pradmm_status_string(pradmm_status st) {
+    switch (st) {
+        case PRADMM_OK: return "ok";
+        case PRADMM_ERR_ARG: return "invalid argument";
+        case PRADMM_ERR_INDEX: return "edge endpoint out of range";
+        case PRADMM_ERR_SELFLOOP: return "self-loop edge";
+        case PRADMM_ERR_NONFINITE: return "non-finite value";
+        case PRADMM_ERR_NOMEM: return "out of memory";
+        case PRADMM_ERR_CUDA: return "CUDA error";
+        case PRADMM_ERR_TIMEOUT: return "device wait timed out";
+        case PRADMM_ERR_NOT_CONVERGED: return "not converged";
+        case PRADMM_ERR_QUATERNION: return "measurement quaternion not unit";
+        case PRADMM_ERR_STATE: return "state not set";
+    }
+    return "unknown status";
+}
+
+const char* pradmm_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,120 @@
+// Internal declarations shared by the host side and the sweep kernels of
+// libpradmm.  Not part of the public ABI (include/pradmm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace pradmm {
+
+// Device-resident control block of one handle.  The last CTA of every
+// s/z + p sweep reduces the residual partials, advances `iter` and decides
+// whether the next iteration runs (`halt`), so a whole solve needs no
+// host round trip.
+struct Ctrl {
+    long long iter;        // completed iterations k (state is x^k)
+    long long target;      // halt once iter reaches target
+    double e_last;         // e^k (Appendix E.1, reading R6)
+    double parts[4];       // |dlam|^2, |dz|^2, |dq|^2, |dt|^2 of the last iteration
+    double tol;            // stopping tolerance when use_tol
+    unsigned int ticket;   // CTA arrival counter of the last-block reduction
+    int halt;              // 1: sweep kernels return at once
+    int stop;              // 1: e^k < tol was met
+    int use_tol;           // 1: solve (stopping test on), 0: step
+    int nonfinite;         // 1: e^k was NaN or Inf
+    int pad0;
+    unsigned long long fallbacks;  // p-updates recomputed in FP64
+    unsigned long long zero_u;     // p-updates with |u| == 0 (kept p^k)
+};
+
+// Residual partial slots (double part[4 * grid]).
+enum { SLOT_DLAM = 0, SLOT_DZ = 1, SLOT_DQ = 2, SLOT_DT = 3 };
+
+// Structure-of-arrays graph in device memory.  Every 4-wide record is one
+// aligned vector load (float4 in FP32, two double2 in FP64).
+//   out order: edges sorted by tail (stable), CSR out_ptr[n+1]
+//   in order:  edges sorted by head (stable), CSR in_ptr[n+1]
+template <typename R>
+struct GraphDev {
+    int64_t n, m;
+    const int32_t* out_ptr;  // n+1
+    const int32_t* out_dst;  // m   head j of out-edge
+    const R* out_te;         // 4m  (t_e x, y, z, omega_e)
+    const R* out_qk;         // 4m  kappa_e * q_e
+    const int32_t* in_ptr;   // n+1
+    const int32_t* in_src;   // m   tail l of in-edge
+    const R* in_te;          // 4m  (t_e x, y, z, omega_e)
+    const R* in_qk;          // 4m  kappa_e * q_e
+};
+
+// Pose / multiplier state.  p is double buffered: p[k & 1] holds p^k and
+// p[(k+1) & 1] the p^{k+1} that the s/z sweep of iteration k-1 (or the
+// first p sweep) computed ahead.  3-vectors are padded to 4; the padding
+// carries the iteration-invariant inverse block matrices (Appendix B with
+// scalar Sigma): s.w = 1/A_2, t.w = 1/A_3, z.w = 1/A_4.
+template <typename R>
+struct StateDev {
+    R* p[2];
+    R* q;
+    R* lam;
+    R* t;
+    R* s;
+    R* z;
+};
+
+template <typename R>
+struct Coef {
+    R beta1, beta2;      // penalties
+    R tb1, tb2;          // tau * beta1, tau * beta2
+    R g1, g2, g3, g4;    // proximal weights
+    double b1d, b2d;     // penalties in double (residual)
+    double fb_thresh;    // FP64 recompute of the p-update below this |u|
+};
+
+struct Launch {
+    int grid;                 // CTAs of every sweep (fixed: partial slots)
+    int block;                // threads per CTA
+    cudaStream_t stream;
+    Ctrl* ctrl;
+    double* part;             // 4 * grid doubles
+    cudaGraphConditionalHandle cond;
+    int has_cond;
+};
+
+template <typename R>
+cudaError_t launch_p(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const Launch& L);
+template <typename R>
+cudaError_t launch_q(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const Launch& L);
+template <typename R>
+cudaError_t launch_t(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const Launch& L);
+template <typename R>
+cudaError_t launch_sp(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const Launch& L);
+
+// Smallest resident-CTA count per SM over the sweep kernels at `block` threads.
+cudaError_t sweep_occupancy(int is_double, int block, int* blocks_per_sm);
+
+// Sets target = iter + iters, halt = (iters <= 0), stop = 0, use_tol, tol.
+cudaError_t launch_arm(Ctrl* ctrl, long long iters, int use_tol, double tol, cudaStream_t st);
+
+// F of Eq. (1) at (p^k, t^k) in double: per-CTA partials, then the last CTA
+// sums them in a fixed order into *F_dev.
+template <typename R>
+cudaError_t launch_objective(const GraphDev<R>& g, const StateDev<R>& s, const int32_t* out_ptr,
+                             const int32_t* out_dst, const double* qe64, const double* te64,
+                             const double* kappa64, const double* omega64, Ctrl* ctrl,
+                             double* part, unsigned int* ticket, double* F_dev, int grid, int block,
+                             cudaStream_t st);
+
+// Packs double host-layout arrays (n x 4 / n x 3) into the padded device
+// layout (and back).  `inv` supplies the padding constants of a 3-vector.
+template <typename R>
+cudaError_t launch_pack4(const double* src, R* dst, int64_t n, cudaStream_t st);
+template <typename R>
+cudaError_t launch_pack3(const double* src, const double* inv, R* dst, int64_t n, cudaStream_t st);
+template <typename R>
+cudaError_t launch_unpack4(const R* src, double* dst, int64_t n, cudaStream_t st);
+template <typename R>
+cudaError_t launch_unpack3(const R* src, double* dst, int64_t n, cudaStream_t st);
+
+}  // namespace pradmm

@@ -1,0 +1,318 @@
+"""Python binding of libpradmm (include/pradmm.h).
+
+Argument marshalling only: every function here forwards to the C ABI of the
+same name, and all arithmetic of the solver runs in the library's CUDA
+kernels.  Importing this module does not load the library; the first call
+does, and raises if `libpradmm.so` has not been built (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpradmm.so")
+
+PRADMM_OK = 0
+PRADMM_ERR_ARG = 1
+PRADMM_ERR_INDEX = 2
+PRADMM_ERR_SELFLOOP = 3
+PRADMM_ERR_NONFINITE = 4
+PRADMM_ERR_NOMEM = 5
+PRADMM_ERR_CUDA = 6
+PRADMM_ERR_TIMEOUT = 7
+PRADMM_ERR_NOT_CONVERGED = 8
+PRADMM_ERR_QUATERNION = 9
+PRADMM_ERR_STATE = 10
+PRADMM_FP64 = 0
+PRADMM_FP32 = 1
+
+
+class pradmm_params(ctypes.Structure):
+    _fields_ = [("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("relax", ctypes.c_double),
+                ("gamma", ctypes.c_double * 4), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("fallback_eps", ctypes.c_double), ("use_graph", ctypes.c_int32),
+                ("block", ctypes.c_int32)]
+
+
+class PRADMMError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: status {status} ({message})")
+        self.status = status
+        self.message = message
+
+
+_lock = threading.Lock()
+_lib = None
+
+_P = ctypes.POINTER
+_d = _P(ctypes.c_double)
+_i32 = _P(ctypes.c_int32)
+_i64 = _P(ctypes.c_int64)
+_h = ctypes.c_void_p
+
+_SIGS = {
+    "pradmm_default_params": (None, [_P(pradmm_params)]),
+    "pradmm_create": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, _i32, _i32, _d, _d, _d, _d, _P(pradmm_params),
+                                     ctypes.c_void_p, _P(ctypes.c_void_p)]),
+    "pradmm_create_device": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            _P(pradmm_params), ctypes.c_void_p, _P(ctypes.c_void_p)]),
+    "pradmm_set_state": (ctypes.c_int, [_h, _d, _d]),
+    "pradmm_set_state_full": (ctypes.c_int, [_h, _d, _d, _d, _d, _d, _d]),
+    "pradmm_init_odometry": (ctypes.c_int, [_h]),
+    "pradmm_step": (ctypes.c_int, [_h, ctypes.c_int32, _d]),
+    "pradmm_solve": (ctypes.c_int, [_h, _i32, _d]),
+    "pradmm_objective": (ctypes.c_int, [_h, _d]),
+    "pradmm_get_state": (ctypes.c_int, [_h, _d, _d, _d, _d, _d, _d]),
+    "pradmm_get_state_device": (ctypes.c_int, [_h, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "pradmm_get_poses": (ctypes.c_int, [_h, _d, _d]),
+    "pradmm_iterations": (ctypes.c_int64, [_h]),
+    "pradmm_counters": (ctypes.c_int, [_h, _i64]),
+    "pradmm_bytes_per_iteration": (ctypes.c_int, [_h, _d]),
+    "pradmm_profile_sweeps": (ctypes.c_int, [_h, ctypes.c_int32, _d]),
+    "pradmm_destroy": (None, [_h]),
+    "pradmm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "pradmm_last_error": (ctypes.c_char_p, []),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Loads libpradmm.so (built by `paper_2601_15684_gb300.build_lib.build()`)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"libpradmm.so not built at {path}; run __graft_entry__.build()")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != PRADMM_OK:
+        lib = load()
+        msg = lib.pradmm_last_error().decode() or lib.pradmm_status_string(status).decode()
+        raise PRADMMError(status, where, msg)
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(_d)
+
+
+def _f64(a, shape=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.shape != shape:
+        a = a.reshape(shape)
+    return a
+
+
+# ---- same-name wrappers of the C ABI ---------------------------------------------
+
+def pradmm_default_params() -> pradmm_params:
+    p = pradmm_params()
+    load().pradmm_default_params(ctypes.byref(p))
+    return p
+
+
+def pradmm_create(n, src, dst, q_meas, t_meas, kappa=None, omega=None, params=None, stream=None):
+    """Returns a handle (int).  Arrays are host numpy arrays; see pradmm.h."""
+    lib = load()
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    m = int(src.shape[0])
+    q_meas = _f64(q_meas, (m, 4))
+    t_meas = _f64(t_meas, (m, 3))
+    kappa = _f64(kappa)
+    omega = _f64(omega)
+    prm = params if params is not None else pradmm_default_params()
+    h = ctypes.c_void_p()
+    st = lib.pradmm_create(int(n), m, src.ctypes.data_as(_i32), dst.ctypes.data_as(_i32), _dp(q_meas), _dp(t_meas),
+                           _dp(kappa), _dp(omega), ctypes.byref(prm), ctypes.c_void_p(stream or 0), ctypes.byref(h))
+    _check(st, "pradmm_create")
+    return h.value
+
+
+def pradmm_create_device(n, m, src_ptr, dst_ptr, q_ptr, t_ptr, kappa_ptr=0, omega_ptr=0, params=None, stream=None):
+    """Device-pointer variant (e.g. torch tensors' data_ptr())."""
+    lib = load()
+    prm = params if params is not None else pradmm_default_params()
+    h = ctypes.c_void_p()
+    st = lib.pradmm_create_device(int(n), int(m), ctypes.c_void_p(src_ptr), ctypes.c_void_p(dst_ptr),
+                                  ctypes.c_void_p(q_ptr), ctypes.c_void_p(t_ptr), ctypes.c_void_p(kappa_ptr or 0),
+                                  ctypes.c_void_p(omega_ptr or 0), ctypes.byref(prm), ctypes.c_void_p(stream or 0),
+                                  ctypes.byref(h))
+    _check(st, "pradmm_create_device")
+    return h.value
+
+
+def pradmm_set_state(h, q, t, n):
+    q, t = _f64(q, (n, 4)), _f64(t, (n, 3))
+    _check(load().pradmm_set_state(h, _dp(q), _dp(t)), "pradmm_set_state")
+
+
+def pradmm_set_state_full(h, st: dict, n):
+    a = {k: _f64(st[k], (n, 4) if k in ("p", "q", "lam") else (n, 3)) for k in ("p", "q", "t", "s", "lam", "z")}
+    _check(load().pradmm_set_state_full(h, _dp(a["p"]), _dp(a["q"]), _dp(a["t"]), _dp(a["s"]), _dp(a["lam"]),
+                                        _dp(a["z"])), "pradmm_set_state_full")
+
+
+def pradmm_init_odometry(h):
+    _check(load().pradmm_init_odometry(h), "pradmm_init_odometry")
+
+
+def pradmm_step(h, iters: int) -> float:
+    e = ctypes.c_double(0.0)
+    _check(load().pradmm_step(h, int(iters), ctypes.byref(e)), "pradmm_step")
+    return e.value
+
+
+def pradmm_solve(h):
+    """Returns (converged, iterations, e_final)."""
+    it = ctypes.c_int32(0)
+    e = ctypes.c_double(0.0)
+    st = load().pradmm_solve(h, ctypes.byref(it), ctypes.byref(e))
+    if st not in (PRADMM_OK, PRADMM_ERR_NOT_CONVERGED):
+        _check(st, "pradmm_solve")
+    return st == PRADMM_OK, it.value, e.value
+
+
+def pradmm_objective(h) -> float:
+    F = ctypes.c_double(0.0)
+    _check(load().pradmm_objective(h, ctypes.byref(F)), "pradmm_objective")
+    return F.value
+
+
+def pradmm_get_state(h, n) -> dict:
+    out = {"p": np.zeros((n, 4)), "q": np.zeros((n, 4)), "t": np.zeros((n, 3)), "s": np.zeros((n, 3)),
+           "lam": np.zeros((n, 4)), "z": np.zeros((n, 3))}
+    _check(load().pradmm_get_state(h, _dp(out["p"]), _dp(out["q"]), _dp(out["t"]), _dp(out["s"]), _dp(out["lam"]),
+                                   _dp(out["z"])), "pradmm_get_state")
+    return out
+
+
+def pradmm_get_state_device(h, p=0, q=0, t=0, s=0, lam=0, z=0):
+    _check(load().pradmm_get_state_device(h, ctypes.c_void_p(p), ctypes.c_void_p(q), ctypes.c_void_p(t),
+                                          ctypes.c_void_p(s), ctypes.c_void_p(lam), ctypes.c_void_p(z)),
+           "pradmm_get_state_device")
+
+
+def pradmm_get_poses(h, n, q_out=None, t_out=None):
+    q = q_out if q_out is not None else np.zeros((n, 4))
+    t = t_out if t_out is not None else np.zeros((n, 3))
+    _check(load().pradmm_get_poses(h, _dp(q), _dp(t)), "pradmm_get_poses")
+    return q, t
+
+
+def pradmm_iterations(h) -> int:
+    return int(load().pradmm_iterations(h))
+
+
+def pradmm_counters(h) -> dict:
+    out = np.zeros(4, dtype=np.int64)
+    _check(load().pradmm_counters(h, out.ctypes.data_as(_i64)), "pradmm_counters")
+    return {"fallbacks": int(out[0]), "zero_u": int(out[1]), "iterations": int(out[2]), "stopped": int(out[3])}
+
+
+def pradmm_bytes_per_iteration(h) -> dict:
+    out = np.zeros(4)
+    _check(load().pradmm_bytes_per_iteration(h, _dp(out)), "pradmm_bytes_per_iteration")
+    return {"total": out[0], "k_q": out[1], "k_t": out[2], "k_sp": out[3]}
+
+
+def pradmm_profile_sweeps(h, iters: int) -> dict:
+    out = np.zeros(4)
+    _check(load().pradmm_profile_sweeps(h, int(iters), _dp(out)), "pradmm_profile_sweeps")
+    return {"k_q": out[0], "k_t": out[1], "k_sp": out[2], "iteration": out[3]}
+
+
+def pradmm_destroy(h):
+    if h:
+        load().pradmm_destroy(h)
+
+
+def pradmm_status_string(st: int) -> str:
+    return load().pradmm_status_string(int(st)).decode()
+
+
+# ---- convenience object ------------------------------------------------------------
+
+class Solver:
+    """Owns one handle for a `synth.PoseGraph`-like object (fields n, src, dst,
+    q_meas, t_meas, kappa, omega)."""
+
+    def __init__(self, graph, params: pradmm_params | None = None, stream=None, **overrides):
+        prm = params if params is not None else pradmm_default_params()
+        for k, v in overrides.items():
+            if k == "gamma":
+                for i in range(4):
+                    prm.gamma[i] = v[i]
+            else:
+                setattr(prm, k, v)
+        self.params = prm
+        self.n = int(graph.n)
+        self.h = pradmm_create(graph.n, graph.src, graph.dst, graph.q_meas, graph.t_meas, graph.kappa, graph.omega,
+                               prm, stream)
+
+    def close(self):
+        if self.h:
+            pradmm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_state(self, q, t):
+        pradmm_set_state(self.h, q, t, self.n)
+
+    def set_state_full(self, st):
+        pradmm_set_state_full(self.h, st, self.n)
+
+    def init_odometry(self):
+        pradmm_init_odometry(self.h)
+
+    def step(self, iters=1):
+        return pradmm_step(self.h, iters)
+
+    def solve(self):
+        return pradmm_solve(self.h)
+
+    def objective(self):
+        return pradmm_objective(self.h)
+
+    def state(self):
+        return pradmm_get_state(self.h, self.n)
+
+    def poses(self):
+        return pradmm_get_poses(self.h, self.n)
+
+    def iterations(self):
+        return pradmm_iterations(self.h)
+
+    def counters(self):
+        return pradmm_counters(self.h)
+
+    def bytes_per_iteration(self):
+        return pradmm_bytes_per_iteration(self.h)
+
+    def profile(self, iters):
+        return pradmm_profile_sweeps(self.h, iters)

@@ -1,0 +1,290 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (relerr(X) = |X_gpu - X_oracle|_2 / |X_oracle|_2 per state array):
+  FP64 path: 1e-10 after 1 and 10 iterations (rounding-order differences only;
+             measured ~1e-15), final objective within 1e-6 relative.
+  FP32 path: p, q, t, s within 1e-5 relative after 1 and 10 iterations.  The
+             multipliers are sums of tau*beta*(p - q) and tau*beta*(t - s),
+             differences of nearly equal stored values, so their error is
+             measured against the scale they are formed from:
+             |dlam| <= 1e-5 * tau*beta1*|p|,  |dz| <= 1e-5 * tau*beta2*|t|
+             (FP32 unit roundoff 6e-8 times the few-term sums of one update,
+             with margin).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_15684_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("p", "q", "t", "s", "lam", "z")
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2601_15684_gb300 import build_lib
+    from paper_2601_15684_gb300 import pradmm
+    build_lib.build()
+    pradmm.load()
+    return pradmm
+
+
+def relerr(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _params(P, precision, beta1=1.0, beta2=1.0, tau=1.5, gamma=(1.0, 1e-3, 1e-3, 1e-3), use_graph=1, block=0,
+            tol=1e-4, max_iter=300):
+    prm = P.pradmm_default_params()
+    prm.beta1, prm.beta2, prm.relax = beta1, beta2, tau
+    for k in range(4):
+        prm.gamma[k] = gamma[k]
+    prm.precision = precision
+    prm.use_graph = use_graph
+    prm.block = block
+    prm.tol = tol
+    prm.max_iter = max_iter
+    return prm
+
+
+def _oparams(beta1=1.0, beta2=1.0, tau=1.5, gamma=(1.0, 1e-3, 1e-3, 1e-3)):
+    return oracle.make_params(beta1=beta1, beta2=beta2, tau=tau, gamma=gamma)
+
+
+def check_state(gpu, orc, fp64, prm):
+    if fp64:
+        for k in KEYS:
+            assert relerr(gpu[k], orc[k]) <= 1e-10, (k, relerr(gpu[k], orc[k]))
+        return
+    for k in ("p", "q", "t", "s"):
+        assert relerr(gpu[k], orc[k]) <= 1e-5, (k, relerr(gpu[k], orc[k]))
+    assert np.linalg.norm(gpu["lam"] - orc["lam"]) <= 1e-5 * prm.relax * prm.beta1 * np.linalg.norm(orc["p"])
+    assert np.linalg.norm(gpu["z"] - orc["z"]) <= 1e-5 * prm.relax * prm.beta2 * np.linalg.norm(orc["t"])
+
+
+def _run_pair(P, g, st0, prm, iters_list=(1, 10)):
+    op = _oparams(prm.beta1, prm.beta2, prm.relax, tuple(prm.gamma))
+    with P.Solver(g, prm) as S:
+        S.set_state_full(st0)
+        done = 0
+        orc = st0
+        for it in iters_list:
+            e_gpu = S.step(it - done)
+            orc, res, _ = oracle.iterate(g, op, orc, it - done)
+            done = it
+            gpu = S.state()
+            check_state(gpu, orc, prm.precision == P.PRADMM_FP64, prm)
+            assert abs(e_gpu - res[0]) <= (1e-9 if prm.precision == P.PRADMM_FP64 else 1e-3) * max(res[0], 1e-30)
+            assert S.iterations() == it
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("case", ["ragged", "hubs", "isolated", "tail"])
+def test_random_graphs_one_and_ten_iterations(P, precision, case):
+    if case == "ragged":
+        g = synth.random_graph(3000, 9000, seed=1)
+    elif case == "hubs":
+        g = synth.random_graph(700, 6000, seed=2)  # pareto-skewed tails: high-degree hubs
+    elif case == "isolated":
+        g = synth.random_graph(1200, 2500, seed=3, isolated=300)
+    else:
+        g = synth.random_graph(257, 700, seed=4)  # one vertex past a 256-thread CTA
+    st0 = synth.random_state(np.random.default_rng(10), g.n)
+    prm = _params(P, precision, beta1=3.0, beta2=5.0, tau=1.3, gamma=(0.7, 0.01, 0.02, 0.03))
+    _run_pair(P, g, st0, prm)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_walk128_odometry_and_iterates(P, precision):
+    g = synth.workload("walk128")
+    prm = _params(P, precision)
+    q0, t0 = oracle.init_odometry(g)
+    with P.Solver(g, prm) as S:
+        S.init_odometry()
+        st = S.state()
+        tq = 1e-12 if precision == 0 else 1e-6
+        tt = 1e-10 if precision == 0 else 1e-6 * max(1.0, np.abs(t0).max())
+        assert np.abs(st["q"] - q0).max() < tq
+        assert np.abs(st["t"] - t0).max() < tt
+    _run_pair(P, g, oracle.init_state(q0, t0), prm)
+
+
+def test_walk128_fp64_solve_500_objective(P):
+    """Config: 128-pose walk, FP64, 500 iterations; final objective within 1e-6."""
+    g = synth.workload("walk128")
+    prm = _params(P, 0)
+    q0, t0 = oracle.init_odometry(g)
+    with P.Solver(g, prm) as S:
+        S.set_state(q0, t0)
+        S.step(500)
+        F_gpu = S.objective()
+        gpu = S.state()
+    orc, _, _ = oracle.iterate(g, _oparams(), oracle.init_state(q0, t0), 500)
+    F_orc = oracle.objective(g, orc["p"], orc["t"])
+    assert abs(F_gpu - F_orc) <= 1e-6 * F_orc
+    assert abs(oracle.objective(g, gpu["p"], gpu["t"]) - F_gpu) <= 1e-12 * F_orc
+    for k in KEYS:
+        assert relerr(gpu[k], orc[k]) <= 1e-8, k
+
+
+def test_solve_stops_like_the_oracle(P):
+    g = synth.workload("walk128")
+    prm = _params(P, 0, tol=3e-4, max_iter=400)
+    q0, t0 = oracle.init_odometry(g)
+    orc, k_orc, e_orc, trace = oracle.solve(g, _oparams(), oracle.init_state(q0, t0), 400, 3e-4)
+    assert k_orc < 400 and abs(trace[k_orc - 2] - 3e-4) > 1e-8  # not a borderline crossing
+    for use_graph in (1, 0):
+        prm.use_graph = use_graph
+        with P.Solver(g, prm) as S:
+            S.set_state(q0, t0)
+            conv, k, e = S.solve()
+            assert conv and k == k_orc
+            assert abs(e - e_orc) <= 1e-9 * e_orc
+            gpu = S.state()
+            for key in KEYS:
+                assert relerr(gpu[key], orc[key]) <= 1e-10, key
+
+
+def test_solve_not_converged_keeps_state(P):
+    g = synth.workload("walk128")
+    prm = _params(P, 0, tol=1e-30, max_iter=7)
+    q0, t0 = oracle.init_odometry(g)
+    with P.Solver(g, prm) as S:
+        S.set_state(q0, t0)
+        conv, k, e = S.solve()
+        assert not conv and k == 7 and S.iterations() == 7
+        orc, res, _ = oracle.iterate(g, _oparams(), oracle.init_state(q0, t0), 7)
+        for key in KEYS:
+            assert relerr(S.state()[key], orc[key]) <= 1e-10
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_and_plain_launches_bit_identical_and_deterministic(P, precision):
+    g = synth.random_graph(5000, 20000, seed=7)
+    st0 = synth.random_state(np.random.default_rng(8), g.n)
+    outs = []
+    for use_graph in (1, 0, 1):
+        prm = _params(P, precision, use_graph=use_graph)
+        with P.Solver(g, prm) as S:
+            S.set_state_full(st0)
+            e = S.step(6)
+            outs.append((e, S.state(), S.objective()))
+    for e, st, F in outs[1:]:
+        assert e == outs[0][0] and F == outs[0][2]
+        for k in KEYS:
+            np.testing.assert_array_equal(st[k], outs[0][1][k])
+
+
+def test_checkpoint_resume_matches_uninterrupted(P):
+    g = synth.workload("helix25k")
+    prm = _params(P, 1)
+    q0, t0 = oracle.init_odometry(g)
+    with P.Solver(g, prm) as A:
+        A.set_state(q0, t0)
+        A.step(20)
+        full = A.state()
+    with P.Solver(g, prm) as B:
+        B.set_state(q0, t0)
+        B.step(8)
+        ck = B.state()
+    with P.Solver(g, prm) as C:
+        C.set_state_full(ck)
+        C.step(12)
+        res = C.state()
+    for k in KEYS:
+        # the checkpoint round-trips through double and back: exact for FP32 values
+        np.testing.assert_array_equal(res[k], full[k])
+
+
+def test_block_sizes_agree(P):
+    g = synth.random_graph(4000, 12000, seed=9, isolated=7)
+    st0 = synth.random_state(np.random.default_rng(3), g.n)
+    ref = None
+    for block in (64, 96, 160, 256):
+        prm = _params(P, 0, block=block)
+        with P.Solver(g, prm) as S:
+            S.set_state_full(st0)
+            S.step(3)
+            st = S.state()
+        if ref is None:
+            ref = st
+        for k in KEYS:
+            assert relerr(st[k], ref[k]) <= 1e-13
+
+
+def test_edge_cases(P):
+    # no edges at all: every vertex is isolated; n = 1
+    for n in (1, 5):
+        g = synth.PoseGraph(n=n, src=np.zeros(0, np.int32), dst=np.zeros(0, np.int32), q_meas=np.zeros((0, 4)),
+                            t_meas=np.zeros((0, 3)), kappa=np.zeros(0), omega=np.zeros(0))
+        st0 = synth.random_state(np.random.default_rng(n), n)
+        for precision in (0, 1):
+            prm = _params(P, precision)
+            with P.Solver(g, prm) as S:
+                S.set_state_full(st0)
+                S.step(4)
+                gpu = S.state()
+                assert S.objective() == 0.0
+            orc, _, _ = oracle.iterate(g, _oparams(), st0, 4)
+            check_state(gpu, orc, precision == 0, prm)
+    # |u| = 0 keeps p (reading of the undefined normalisation)
+    g = synth.random_graph(6, 10, seed=31, isolated=1)
+    st = synth.random_state(np.random.default_rng(32), g.n)
+    st["p"][5] = st["q"][5] = [1.0, 0, 0, 0]
+    st["lam"][5] = [-2.0, 0, 0, 0]
+    for precision in (0, 1):
+        with P.Solver(g, _params(P, precision)) as S:
+            S.set_state_full(st)
+            S.step(1)
+            c = S.counters()
+            assert c["zero_u"] == 1
+            assert c["fallbacks"] == (1 if precision == 1 else 0)
+            np.testing.assert_array_equal(S.state()["p"][5], [1.0, 0, 0, 0])
+
+
+def test_input_errors(P):
+    g = synth.random_graph(10, 20, seed=5)
+    bad = [
+        dict(dst=np.where(np.arange(20) == 3, 10, g.dst)),  # out of range
+        dict(dst=np.where(np.arange(20) == 3, g.src, g.dst)),  # self-loop
+    ]
+    codes = [P.PRADMM_ERR_INDEX, P.PRADMM_ERR_SELFLOOP]
+    for kw, code in zip(bad, codes):
+        with pytest.raises(P.PRADMMError) as ei:
+            P.pradmm_create(g.n, kw.get("src", g.src), kw["dst"], g.q_meas, g.t_meas)
+        assert ei.value.status == code
+    qm = g.q_meas.copy()
+    qm[2] *= 1.01
+    with pytest.raises(P.PRADMMError) as ei:
+        P.pradmm_create(g.n, g.src, g.dst, qm, g.t_meas)
+    assert ei.value.status == P.PRADMM_ERR_QUATERNION
+    tm = g.t_meas.copy()
+    tm[4, 1] = np.nan
+    with pytest.raises(P.PRADMMError) as ei:
+        P.pradmm_create(g.n, g.src, g.dst, g.q_meas, tm)
+    assert ei.value.status == P.PRADMM_ERR_NONFINITE
+    prm = _params(P, 1, tau=2.0)
+    with pytest.raises(P.PRADMMError) as ei:
+        P.pradmm_create(g.n, g.src, g.dst, g.q_meas, g.t_meas, params=prm)
+    assert ei.value.status == P.PRADMM_ERR_ARG
+    h = P.pradmm_create(g.n, g.src, g.dst, g.q_meas, g.t_meas)
+    try:
+        with pytest.raises(P.PRADMMError) as ei:
+            P.pradmm_step(h, 1)
+        assert ei.value.status == P.PRADMM_ERR_STATE
+    finally:
+        P.pradmm_destroy(h)
+
+
+def test_nonfinite_state_is_reported(P):
+    g = synth.random_graph(50, 120, seed=6)
+    st = synth.random_state(np.random.default_rng(6), g.n)
+    with P.Solver(g, _params(P, 1)) as S:
+        st["t"][3] = 3.3e38  # finite inputs whose products overflow FP32
+        st["s"][3] = 3.3e38
+        S.set_state_full(st)
+        with pytest.raises(P.PRADMMError) as ei:
+            S.step(3)
+        assert ei.value.status == P.PRADMM_ERR_NONFINITE
