@@ -85,7 +85,7 @@ typedef struct {
     double fallback_eps; /* FP32: recompute u_i in FP64 when |u_i| < eps (beta1+gamma1) */
     int32_t use_graph;   /* 1: loop inside a CUDA graph with a device-side while node;
                             0: plain stream launches                               */
-    int32_t block;       /* threads per CTA of the sweeps: 0 (default 256) or a
+    int32_t block;       /* threads per CTA of the sweeps: 0 (default, 256) or a
                             multiple of 32 in [32, 256]                            */
 } pradmm_params;
 

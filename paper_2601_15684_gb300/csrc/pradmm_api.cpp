@@ -49,15 +49,18 @@ struct pradmm_s {
     size_t rsize = 4;  // bytes per real
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    int grid = 1, block = 256, obj_grid = 1;
+    int grids[4] = {1, 1, 1, 1};  // p, q, t, s/z+p sweeps
+    int pstride = 1, block = 256, obj_grid = 1;
+    int64_t out_slots = 0, in_slots = 0;  // edges per order (= m)
 
     // host copies (input order) for the odometry initialisation
     std::vector<int32_t> src, dst;
     std::vector<double> qe, te;
-    std::vector<double> inv2, inv3, inv4;  // 1/A_2, 1/A_3, 1/A_4 per vertex
+    std::vector<double> inv2, inv3, inv4;  // 1/A_2, 1/A_3, 1/A_4 per internal vertex
 
     std::vector<void*> allocs;
-    int32_t *out_ptr = nullptr, *out_dst = nullptr, *in_ptr = nullptr, *in_src = nullptr;
+    int32_t *out_ptr = nullptr, *in_ptr = nullptr, *out_idx = nullptr, *in_idx = nullptr;
+    int32_t* perm_d = nullptr;  // internal vertex -> user vertex
     void *out_te = nullptr, *out_qk = nullptr, *in_te = nullptr, *in_qk = nullptr;
     double *qe64 = nullptr, *te64 = nullptr, *ka64 = nullptr, *om64 = nullptr;
     void *p[2] = {nullptr, nullptr}, *q = nullptr, *lam = nullptr, *t = nullptr, *s = nullptr, *z = nullptr;
@@ -85,11 +88,11 @@ struct pradmm_s {
         g.n = n;
         g.m = m;
         g.out_ptr = out_ptr;
-        g.out_dst = out_dst;
+        g.in_ptr = in_ptr;
+        g.out_idx = out_idx;
         g.out_te = static_cast<const R*>(out_te);
         g.out_qk = static_cast<const R*>(out_qk);
-        g.in_ptr = in_ptr;
-        g.in_src = in_src;
+        g.in_idx = in_idx;
         g.in_te = static_cast<const R*>(in_te);
         g.in_qk = static_cast<const R*>(in_qk);
         return g;
@@ -124,7 +127,11 @@ struct pradmm_s {
     }
     pradmm::Launch launch(bool with_cond) const {
         pradmm::Launch L;
-        L.grid = grid;
+        L.grid_p = grids[0];
+        L.grid_q = grids[1];
+        L.grid_t = grids[2];
+        L.grid_sp = grids[3];
+        L.pstride = pstride;
         L.block = block;
         L.stream = stream;
         L.ctrl = ctrl;
@@ -136,6 +143,13 @@ struct pradmm_s {
 };
 
 namespace {
+
+// Vertices are ordered by degree within windows of this many consecutive ids
+// (1 keeps the caller's order, which keeps chain neighbours adjacent).
+#ifndef PRADMM_SORT_WINDOW
+#define PRADMM_SORT_WINDOW 1
+#endif
+constexpr int64_t kSortWindow = PRADMM_SORT_WINDOW;
 
 template <typename T>
 pradmm_status dalloc(pradmm_s* h, T** ptr, size_t count) {
@@ -182,7 +196,7 @@ pradmm_status check_params(const pradmm_params* p) {
         return fail(PRADMM_ERR_ARG, "precision must be PRADMM_FP64 or PRADMM_FP32");
     if (!(p->fallback_eps >= 0)) return fail(PRADMM_ERR_ARG, "fallback_eps must be >= 0");
     if (p->block != 0 && (p->block < 32 || p->block > 256 || p->block % 32 != 0))
-        return fail(PRADMM_ERR_ARG, "block must be 0 or a multiple of 32 in [32, 256]");
+        return fail(PRADMM_ERR_ARG, "block must be 0 (default) or a multiple of 32 in [32, 256]");
     return PRADMM_OK;
 }
 
@@ -197,31 +211,50 @@ void counting_sort(int64_t n, int64_t m, const int32_t* key, std::vector<int32_t
     for (int64_t e = 0; e < m; ++e) perm[fill[key[e]]++] = (int32_t)e;
 }
 
-template <typename R>
-void pack_edges(const pradmm_s* h, const std::vector<int32_t>& perm, const std::vector<double>& ka,
-                const std::vector<double>& om, std::vector<R>& te_o, std::vector<R>& qk_o) {
-    te_o.resize(4 * h->m);
-    qk_o.resize(4 * h->m);
-    for (int64_t k = 0; k < h->m; ++k) {
-        const int64_t e = perm[k];
-        te_o[4 * k + 0] = R(h->te[3 * e + 0]);
-        te_o[4 * k + 1] = R(h->te[3 * e + 1]);
-        te_o[4 * k + 2] = R(h->te[3 * e + 2]);
-        te_o[4 * k + 3] = R(om[e]);
-        for (int c = 0; c < 4; ++c) qk_o[4 * k + c] = R(ka[e] * h->qe[4 * e + c]);
+// CSR of one edge order over internal vertex ids: the edges of internal
+// vertex i (user vertex perm[i]) keep their input order.
+struct Csr {
+    std::vector<int32_t> ptr;   // n + 1
+    std::vector<int32_t> idx;   // other endpoint (internal id) per slot
+    std::vector<int64_t> edge;  // input edge per slot
+};
+
+Csr build_csr(int64_t n, const std::vector<int32_t>& perm, const std::vector<int32_t>& iperm,
+              const std::vector<int32_t>& ptr, const std::vector<int32_t>& sorted_edges, const int32_t* other) {
+    Csr C;
+    C.ptr.assign(n + 1, 0);
+    for (int64_t i = 0; i < n; ++i) C.ptr[i + 1] = C.ptr[i] + (ptr[perm[i] + 1] - ptr[perm[i]]);
+    const int64_t m = C.ptr[n];
+    C.idx.assign(m, 0);
+    C.edge.assign(m, -1);
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t u = perm[i];
+        for (int32_t k = 0; k < ptr[u + 1] - ptr[u]; ++k) {
+            const int64_t e = sorted_edges[ptr[u] + k];
+            C.idx[C.ptr[i] + k] = iperm[other[e]];
+            C.edge[C.ptr[i] + k] = e;
+        }
     }
+    return C;
 }
 
+// Packs (t_e, omega_e) and kappa_e q_e per slot; padding slots are zero.
 template <typename R>
-pradmm_status upload_edges(pradmm_s* h, const std::vector<int32_t>& perm_out, const std::vector<int32_t>& perm_in,
-                           const std::vector<double>& ka, const std::vector<double>& om) {
-    std::vector<R> te_o, qk_o;
-    pack_edges<R>(h, perm_out, ka, om, te_o, qk_o);
-    CU(cudaMemcpy(h->out_te, te_o.data(), sizeof(R) * te_o.size(), cudaMemcpyHostToDevice));
-    CU(cudaMemcpy(h->out_qk, qk_o.data(), sizeof(R) * qk_o.size(), cudaMemcpyHostToDevice));
-    pack_edges<R>(h, perm_in, ka, om, te_o, qk_o);
-    CU(cudaMemcpy(h->in_te, te_o.data(), sizeof(R) * te_o.size(), cudaMemcpyHostToDevice));
-    CU(cudaMemcpy(h->in_qk, qk_o.data(), sizeof(R) * qk_o.size(), cudaMemcpyHostToDevice));
+pradmm_status upload_slots(pradmm_s* h, const Csr& S, const std::vector<double>& ka, const std::vector<double>& om,
+                           void* te_d, void* qk_d) {
+    const int64_t slots = (int64_t)S.edge.size();
+    std::vector<R> te(4 * slots, R(0)), qk(4 * slots, R(0));
+    for (int64_t k = 0; k < slots; ++k) {
+        const int64_t e = S.edge[k];
+        if (e < 0) continue;
+        for (int c = 0; c < 3; ++c) te[4 * k + c] = R(h->te[3 * e + c]);
+        te[4 * k + 3] = R(om[e]);
+        for (int c = 0; c < 4; ++c) qk[4 * k + c] = R(ka[e] * h->qe[4 * e + c]);
+    }
+    if (slots > 0) {
+        CU(cudaMemcpy(te_d, te.data(), sizeof(R) * te.size(), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(qk_d, qk.data(), sizeof(R) * qk.size(), cudaMemcpyHostToDevice));
+    }
     return PRADMM_OK;
 }
 
@@ -256,10 +289,24 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
             return fail(PRADMM_ERR_QUATERNION, "edge %lld: |q_meas| = %.17g is not 1", (long long)e, nn);
         for (int c = 0; c < 4; ++c) h->qe[4 * e + c] /= nn;
     }
-    // ---- CSR by tail (out) and by head (in) ----
-    std::vector<int32_t> optr, operm, iptr, iperm;
+    // ---- CSR by tail (out) and by head (in), input order inside a vertex ----
+    std::vector<int32_t> optr, operm, iptr, ipermv;
     counting_sort(n, m, src, optr, operm);
-    counting_sort(n, m, dst, iptr, iperm);
+    counting_sort(n, m, dst, iptr, ipermv);
+    // ---- internal vertex order: by degree within windows of consecutive ids ----
+    std::vector<int32_t> perm(n), iperm(n);
+    for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
+    for (int64_t w0 = 0; w0 < n; w0 += kSortWindow) {
+        const int64_t w1 = std::min<int64_t>(n, w0 + kSortWindow);
+        std::stable_sort(perm.begin() + w0, perm.begin() + w1, [&](int32_t a, int32_t b) {
+            return (optr[a + 1] - optr[a]) + (iptr[a + 1] - iptr[a]) > (optr[b + 1] - optr[b]) + (iptr[b + 1] - iptr[b]);
+        });
+    }
+    for (int64_t i = 0; i < n; ++i) iperm[perm[i]] = (int32_t)i;
+    const Csr so = build_csr(n, perm, iperm, optr, operm, dst);
+    const Csr si = build_csr(n, perm, iperm, iptr, ipermv, src);
+    h->out_slots = (int64_t)so.idx.size();
+    h->in_slots = (int64_t)si.idx.size();
     // ---- iteration-invariant scalar block matrices (Appendix B, scalar Sigma) ----
     std::vector<double> A2(n, h->prm.beta1 + h->prm.gamma[1]), A3(n, h->prm.beta2 + h->prm.gamma[2]),
         A4(n, h->prm.beta2 + h->prm.gamma[3]);
@@ -274,23 +321,25 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
     h->inv3.resize(n);
     h->inv4.resize(n);
     for (int64_t i = 0; i < n; ++i) {
-        h->inv2[i] = 1.0 / A2[i];
-        h->inv3[i] = 1.0 / A3[i];
-        h->inv4[i] = 1.0 / A4[i];
+        const int32_t u = perm[i];
+        h->inv2[i] = 1.0 / A2[u];
+        h->inv3[i] = 1.0 / A3[u];
+        h->inv4[i] = 1.0 / A4[u];
     }
     // ---- device buffers ----
+    ST(dalloc(h, &h->perm_d, n));
     ST(dalloc(h, &h->out_ptr, n + 1));
     ST(dalloc(h, &h->in_ptr, n + 1));
-    ST(dalloc(h, &h->out_dst, m));
-    ST(dalloc(h, &h->in_src, m));
-    ST(valloc(h, &h->out_te, 4 * m));
-    ST(valloc(h, &h->out_qk, 4 * m));
-    ST(valloc(h, &h->in_te, 4 * m));
-    ST(valloc(h, &h->in_qk, 4 * m));
-    ST(dalloc(h, &h->qe64, 4 * m));
-    ST(dalloc(h, &h->te64, 3 * m));
-    ST(dalloc(h, &h->ka64, m));
-    ST(dalloc(h, &h->om64, m));
+    ST(dalloc(h, &h->out_idx, h->out_slots));
+    ST(dalloc(h, &h->in_idx, h->in_slots));
+    ST(valloc(h, &h->out_te, 4 * h->out_slots));
+    ST(valloc(h, &h->out_qk, 4 * h->out_slots));
+    ST(valloc(h, &h->in_te, 4 * h->in_slots));
+    ST(valloc(h, &h->in_qk, 4 * h->in_slots));
+    ST(dalloc(h, &h->qe64, 4 * h->out_slots));
+    ST(dalloc(h, &h->te64, 3 * h->out_slots));
+    ST(dalloc(h, &h->ka64, h->out_slots));
+    ST(dalloc(h, &h->om64, h->out_slots));
     for (int b = 0; b < 2; ++b) ST(valloc(h, &h->p[b], 4 * n));
     ST(valloc(h, &h->q, 4 * n));
     ST(valloc(h, &h->lam, 4 * n));
@@ -302,7 +351,7 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
     ST(dalloc(h, &h->inv4_d, n));
     ST(dalloc(h, &h->stage, 4 * n));
     ST(dalloc(h, &h->zeros, 4 * n));
-    ST(dalloc(h, &h->part, 4 * (size_t)h->grid));
+    ST(dalloc(h, &h->part, 4 * (size_t)h->pstride));
     ST(dalloc(h, &h->obj_part, (size_t)h->obj_grid));
     ST(dalloc(h, &h->obj_ticket, 1));
     ST(dalloc(h, &h->F_dev, 1));
@@ -313,32 +362,34 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
         h->ctrl_h = static_cast<Ctrl*>(hp);
         std::memset(h->ctrl_h, 0, sizeof(Ctrl));
     }
-    // uploads (pageable, synchronous with respect to the host buffers)
-    std::vector<int32_t> tmp(m);
-    CU(cudaMemcpy(h->out_ptr, optr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
-    CU(cudaMemcpy(h->in_ptr, iptr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
-    for (int64_t k = 0; k < m; ++k) tmp[k] = dst[operm[k]];
-    CU(cudaMemcpy(h->out_dst, tmp.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
-    for (int64_t k = 0; k < m; ++k) tmp[k] = src[iperm[k]];
-    CU(cudaMemcpy(h->in_src, tmp.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
+    // ---- uploads (synchronous with respect to the host buffers) ----
+    CU(cudaMemcpy(h->perm_d, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->out_ptr, so.ptr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->in_ptr, si.ptr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
+    if (h->out_slots > 0) CU(cudaMemcpy(h->out_idx, so.idx.data(), sizeof(int32_t) * h->out_slots, cudaMemcpyHostToDevice));
+    if (h->in_slots > 0) CU(cudaMemcpy(h->in_idx, si.idx.data(), sizeof(int32_t) * h->in_slots, cudaMemcpyHostToDevice));
     if (h->fp64) {
-        ST(upload_edges<double>(h, operm, iperm, ka, om));
+        ST(upload_slots<double>(h, so, ka, om, h->out_te, h->out_qk));
+        ST(upload_slots<double>(h, si, ka, om, h->in_te, h->in_qk));
     } else {
-        ST(upload_edges<float>(h, operm, iperm, ka, om));
+        ST(upload_slots<float>(h, so, ka, om, h->out_te, h->out_qk));
+        ST(upload_slots<float>(h, si, ka, om, h->in_te, h->in_qk));
     }
-    {
-        std::vector<double> b4(4 * m), b3(3 * m), b1k(m), b1o(m);
-        for (int64_t k = 0; k < m; ++k) {
-            const int64_t e = operm[k];
+    if (h->out_slots > 0) {
+        const int64_t S = h->out_slots;
+        std::vector<double> b4(4 * S, 0.0), b3(3 * S, 0.0), b1k(S, 0.0), b1o(S, 0.0);
+        for (int64_t k = 0; k < S; ++k) {
+            const int64_t e = so.edge[k];
+            if (e < 0) continue;
             for (int c = 0; c < 4; ++c) b4[4 * k + c] = h->qe[4 * e + c];
             for (int c = 0; c < 3; ++c) b3[3 * k + c] = h->te[3 * e + c];
             b1k[k] = ka[e];
             b1o[k] = om[e];
         }
-        CU(cudaMemcpy(h->qe64, b4.data(), sizeof(double) * 4 * m, cudaMemcpyHostToDevice));
-        CU(cudaMemcpy(h->te64, b3.data(), sizeof(double) * 3 * m, cudaMemcpyHostToDevice));
-        CU(cudaMemcpy(h->ka64, b1k.data(), sizeof(double) * m, cudaMemcpyHostToDevice));
-        CU(cudaMemcpy(h->om64, b1o.data(), sizeof(double) * m, cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(h->qe64, b4.data(), sizeof(double) * 4 * S, cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(h->te64, b3.data(), sizeof(double) * 3 * S, cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(h->ka64, b1k.data(), sizeof(double) * S, cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(h->om64, b1o.data(), sizeof(double) * S, cudaMemcpyHostToDevice));
     }
     CU(cudaMemcpy(h->inv2_d, h->inv2.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
     CU(cudaMemcpy(h->inv3_d, h->inv3.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
@@ -395,18 +446,23 @@ pradmm_status create_common(int64_t n, int64_t m, const int32_t* src, const int3
             }
             h->own_stream = true;
         }
-        int dev = 0, sms = 0, bps = 0;
+        int dev = 0, sms = 0, bps[4] = {0, 0, 0, 0};
         if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
             (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
-            (e = pradmm::sweep_occupancy(h->fp64 ? 1 : 0, h->block, &bps)) != cudaSuccess) {
+            (e = pradmm::sweep_occupancy(h->fp64 ? 1 : 0, h->block, bps)) != cudaSuccess) {
             st = fail(PRADMM_ERR_CUDA, "device query: %s", cudaGetErrorString(e));
             break;
         }
-        if (bps < 1) bps = 1;
-        const int64_t need = (n + h->block - 1) / h->block;
-        const int64_t cap = (int64_t)sms * bps;
-        h->grid = (int)std::max<int64_t>(1, std::min(need, cap));
-        h->obj_grid = h->grid;
+        // a thread per vertex, at most a full wave of resident CTAs (the
+        // sweeps loop over vertices)
+        const int64_t tiles = (n + h->block - 1) / h->block;
+        h->pstride = 1;
+        for (int k = 0; k < 4; ++k) {
+            const int64_t cap = (int64_t)sms * std::max(bps[k], 1);
+            h->grids[k] = (int)std::max<int64_t>(1, std::min(tiles, cap));
+            h->pstride = std::max(h->pstride, h->grids[k]);
+        }
+        h->obj_grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * 4));
         st = build(h, src, dst, q_meas, t_meas, kappa, omega);
     } while (0);
     if (st != PRADMM_OK) {
@@ -432,7 +488,7 @@ pradmm_status set_state_dev(pradmm_s* h, const double* p, const double* q, const
             CU(cudaMemcpyAsync(h->stage, src, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, st));
             d = h->stage;
         }
-        CU(pradmm::launch_pack4<R>(d, static_cast<R*>(dst), n, st));
+        CU(pradmm::launch_pack4<R>(d, h->perm_d, static_cast<R*>(dst), n, st));
         if (src && !device_src) CU(cudaStreamSynchronize(st));  // stage is reused
         return PRADMM_OK;
     };
@@ -444,7 +500,7 @@ pradmm_status set_state_dev(pradmm_s* h, const double* p, const double* q, const
             CU(cudaMemcpyAsync(h->stage, src, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
             d = h->stage;
         }
-        CU(pradmm::launch_pack3<R>(d, inv, static_cast<R*>(dst), n, st));
+        CU(pradmm::launch_pack3<R>(d, h->perm_d, inv, static_cast<R*>(dst), n, st));
         if (src && !device_src) CU(cudaStreamSynchronize(st));
         return PRADMM_OK;
     };
@@ -534,6 +590,7 @@ pradmm_status run(pradmm_s* h, long long iters, bool use_tol) {
         ST(launch_iters_plain<R>(h, iters));
     }
     ST(read_ctrl(h));
+    if (h->ctrl_h->timeout) return fail(PRADMM_ERR_TIMEOUT, "a bounded device wait ran out (staged copy never landed)");
     if (h->ctrl_h->nonfinite) return fail(PRADMM_ERR_NONFINITE, "the iteration produced a non-finite residual");
     return PRADMM_OK;
 }
@@ -649,7 +706,7 @@ pradmm_status get_state_impl(pradmm_s* h, double* p, double* q, double* t, doubl
     auto get4 = [&](const void* src, double* dst) -> pradmm_status {
         if (!dst) return PRADMM_OK;
         double* d = device_dst ? dst : h->stage;
-        CU(pradmm::launch_unpack4<R>(static_cast<const R*>(src), d, n, st));
+        CU(pradmm::launch_unpack4<R>(static_cast<const R*>(src), h->perm_d, d, n, st));
         if (!device_dst) CU(cudaMemcpyAsync(dst, h->stage, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
         return PRADMM_OK;
@@ -657,7 +714,7 @@ pradmm_status get_state_impl(pradmm_s* h, double* p, double* q, double* t, doubl
     auto get3 = [&](const void* src, double* dst) -> pradmm_status {
         if (!dst) return PRADMM_OK;
         double* d = device_dst ? dst : h->stage;
-        CU(pradmm::launch_unpack3<R>(static_cast<const R*>(src), d, n, st));
+        CU(pradmm::launch_unpack3<R>(static_cast<const R*>(src), h->perm_d, d, n, st));
         if (!device_dst) CU(cudaMemcpyAsync(dst, h->stage, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
         return PRADMM_OK;
@@ -850,13 +907,13 @@ pradmm_status pradmm_objective(pradmm_t h, double* F) {
     if (!h->state_set) return fail(PRADMM_ERR_STATE, "state is not set");
     cudaError_t e;
     if (h->fp64)
-        e = pradmm::launch_objective<double>(h->gdev<double>(), h->sdev<double>(), h->out_ptr, h->out_dst, h->qe64,
-                                             h->te64, h->ka64, h->om64, h->ctrl, h->obj_part, h->obj_ticket, h->F_dev,
-                                             h->obj_grid, h->block, h->stream);
+        e = pradmm::launch_objective<double>(h->gdev<double>(), h->sdev<double>(), h->qe64, h->te64, h->ka64,
+                                             h->om64, h->ctrl, h->obj_part, h->obj_ticket, h->F_dev, h->obj_grid, 256,
+                                             h->stream);
     else
-        e = pradmm::launch_objective<float>(h->gdev<float>(), h->sdev<float>(), h->out_ptr, h->out_dst, h->qe64,
-                                            h->te64, h->ka64, h->om64, h->ctrl, h->obj_part, h->obj_ticket, h->F_dev,
-                                            h->obj_grid, h->block, h->stream);
+        e = pradmm::launch_objective<float>(h->gdev<float>(), h->sdev<float>(), h->qe64, h->te64, h->ka64,
+                                            h->om64, h->ctrl, h->obj_part, h->obj_ticket, h->F_dev, h->obj_grid, 256,
+                                            h->stream);
     CU(e);
     CU(cudaMemcpyAsync(F, h->F_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));

@@ -23,36 +23,37 @@ struct Ctrl {
     int stop;              // 1: e^k < tol was met
     int use_tol;           // 1: solve (stopping test on), 0: step
     int nonfinite;         // 1: e^k was NaN or Inf
-    int pad0;
+    int timeout;           // 1: a bounded device wait ran out
     unsigned long long fallbacks;  // p-updates recomputed in FP64
     unsigned long long zero_u;     // p-updates with |u| == 0 (kept p^k)
 };
 
-// Residual partial slots (double part[4 * grid]).
+// Residual partial slots (double part[4 * pstride]).
 enum { SLOT_DLAM = 0, SLOT_DZ = 1, SLOT_DQ = 2, SLOT_DT = 3 };
 
-// Structure-of-arrays graph in device memory.  Every 4-wide record is one
-// aligned vector load (float4 in FP32, two double2 in FP64).
-//   out order: edges sorted by tail (stable), CSR out_ptr[n+1]
-//   in order:  edges sorted by head (stable), CSR in_ptr[n+1]
+// Graph in CSR form over internal vertex ids (internal vertex i is user
+// vertex perm[i]; see launch_pack4).  The out-edges of i are slots
+// [out_ptr[i], out_ptr[i+1]) in input order, its in-edges [in_ptr[i],
+// in_ptr[i+1]).  Consecutive vertices' edge ranges are adjacent, so the 32
+// lanes of a warp walk one dense block of edge records.
 template <typename R>
 struct GraphDev {
     int64_t n, m;
     const int32_t* out_ptr;  // n+1
-    const int32_t* out_dst;  // m   head j of out-edge
-    const R* out_te;         // 4m  (t_e x, y, z, omega_e)
-    const R* out_qk;         // 4m  kappa_e * q_e
     const int32_t* in_ptr;   // n+1
-    const int32_t* in_src;   // m   tail l of in-edge
-    const R* in_te;          // 4m  (t_e x, y, z, omega_e)
-    const R* in_qk;          // 4m  kappa_e * q_e
+    const int32_t* out_idx;  // m: head j (internal id) of each out-edge
+    const R* out_te;         // 4m: (t_e x, y, z, omega_e)
+    const R* out_qk;         // 4m: kappa_e q_e
+    const int32_t* in_idx;   // m: tail l (internal id) of each in-edge
+    const R* in_te;          // 4m: (t_e x, y, z, omega_e)
+    const R* in_qk;          // 4m: kappa_e q_e
 };
 
-// Pose / multiplier state.  p is double buffered: p[k & 1] holds p^k and
-// p[(k+1) & 1] the p^{k+1} that the s/z sweep of iteration k-1 (or the
-// first p sweep) computed ahead.  3-vectors are padded to 4; the padding
-// carries the iteration-invariant inverse block matrices (Appendix B with
-// scalar Sigma): s.w = 1/A_2, t.w = 1/A_3, z.w = 1/A_4.
+// Pose / multiplier state in internal vertex order.  p is double buffered:
+// p[k & 1] holds p^k and p[(k+1) & 1] the p^{k+1} that the s/z sweep of
+// iteration k-1 (or the first p sweep) computed ahead.  3-vectors are padded
+// to 4; the padding carries the iteration-invariant inverse block matrices
+// (Appendix B with scalar Sigma): s.w = 1/A_2, t.w = 1/A_3, z.w = 1/A_4.
 template <typename R>
 struct StateDev {
     R* p[2];
@@ -73,11 +74,12 @@ struct Coef {
 };
 
 struct Launch {
-    int grid;                 // CTAs of every sweep (fixed: partial slots)
-    int block;                // threads per CTA
+    int grid_p, grid_q, grid_t, grid_sp;  // CTAs of each sweep (fixed per handle)
+    int pstride;              // partial slot stride (>= every grid)
+    int block;                // threads per CTA (multiple of 32)
     cudaStream_t stream;
     Ctrl* ctrl;
-    double* part;             // 4 * grid doubles
+    double* part;             // 4 * pstride doubles
     cudaGraphConditionalHandle cond;
     int has_cond;
 };
@@ -91,30 +93,33 @@ cudaError_t launch_t(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& 
 template <typename R>
 cudaError_t launch_sp(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const Launch& L);
 
-// Smallest resident-CTA count per SM over the sweep kernels at `block` threads.
-cudaError_t sweep_occupancy(int is_double, int block, int* blocks_per_sm);
+// Resident CTAs per SM of the sweep kernels at `block` threads:
+// bps[0] first p sweep, bps[1] q sweep, bps[2] t sweep, bps[3] s/z + p sweep.
+cudaError_t sweep_occupancy(int is_double, int block, int* bps);
 
 // Sets target = iter + iters, halt = (iters <= 0), stop = 0, use_tol, tol.
 cudaError_t launch_arm(Ctrl* ctrl, long long iters, int use_tol, double tol, cudaStream_t st);
 
 // F of Eq. (1) at (p^k, t^k) in double: per-CTA partials, then the last CTA
-// sums them in a fixed order into *F_dev.
+// sums them in a fixed order into *F_dev.  qe64, te64, ka64, om64 are the
+// measurements in out-edge order.
 template <typename R>
-cudaError_t launch_objective(const GraphDev<R>& g, const StateDev<R>& s, const int32_t* out_ptr,
-                             const int32_t* out_dst, const double* qe64, const double* te64,
-                             const double* kappa64, const double* omega64, Ctrl* ctrl,
-                             double* part, unsigned int* ticket, double* F_dev, int grid, int block,
-                             cudaStream_t st);
+cudaError_t launch_objective(const GraphDev<R>& g, const StateDev<R>& s, const double* qe64,
+                             const double* te64, const double* kappa64, const double* omega64,
+                             Ctrl* ctrl, double* part, unsigned int* ticket, double* F_dev, int grid,
+                             int block, cudaStream_t st);
 
-// Packs double host-layout arrays (n x 4 / n x 3) into the padded device
-// layout (and back).  `inv` supplies the padding constants of a 3-vector.
+// Layout conversion between caller arrays (double, user vertex order, n x 4 /
+// n x 3) and the padded internal arrays: internal vertex i is user vertex
+// perm[i]; `inv` (internal order) supplies the padding of a 3-vector.
 template <typename R>
-cudaError_t launch_pack4(const double* src, R* dst, int64_t n, cudaStream_t st);
+cudaError_t launch_pack4(const double* src, const int32_t* perm, R* dst, int64_t n, cudaStream_t st);
 template <typename R>
-cudaError_t launch_pack3(const double* src, const double* inv, R* dst, int64_t n, cudaStream_t st);
+cudaError_t launch_pack3(const double* src, const int32_t* perm, const double* inv, R* dst, int64_t n,
+                         cudaStream_t st);
 template <typename R>
-cudaError_t launch_unpack4(const R* src, double* dst, int64_t n, cudaStream_t st);
+cudaError_t launch_unpack4(const R* src, const int32_t* perm, double* dst, int64_t n, cudaStream_t st);
 template <typename R>
-cudaError_t launch_unpack3(const R* src, double* dst, int64_t n, cudaStream_t st);
+cudaError_t launch_unpack3(const R* src, const int32_t* perm, double* dst, int64_t n, cudaStream_t st);
 
 }  // namespace pradmm

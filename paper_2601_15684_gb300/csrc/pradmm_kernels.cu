@@ -10,20 +10,34 @@
 //         reduces the residual e^{k+1} (Appendix E.1) and sets the stop state.
 // The p-block of iteration k+1 only needs the vertex's own s^{k+1}, while its
 // gathers (t^{k+1}_j over out-edges, q^{k+1}_l over in-edges) were finished by
-// earlier launches, so it fuses into the s-sweep: the three sweeps share one
-// pass over the vertex and its out-edges.  p is double buffered so the p^{k+2}
-// computed ahead never overwrites the p^{k+1} the same launch reads.
+// earlier launches, so it fuses into the s-sweep and shares its pass over the
+// out-edges.  p is double buffered so the p^{k+2} computed ahead never
+// overwrites the p^{k+1} the same launch reads.
 //
-// Every block is Jacobi over vertices (each vertex reads pre-block values of
-// its neighbours), so one thread owns one vertex and loops over its CSR
-// edges in a fixed order: results are deterministic and the residual
-// reductions use a fixed tree (per-CTA partials in double, summed by the last
-// CTA in CTA order).
+// Work decomposition.  Every block of the iteration is Jacobi over vertices,
+// so one thread owns one vertex and loops over that vertex's CSR edges in
+// input order: every sum has a fixed order and results are deterministic.
+// The 32 vertices of a warp are consecutive, so their edge ranges form one
+// dense block of 16-byte records that L1 serves across the loop steps; each
+// step issues two edges' loads and neighbour gathers before using any of
+// them, and edge records are streamed with evict-first loads so the gathered
+// vertex arrays stay resident in L2.
+// Residual partials are per-thread compensated FP32 sums (FP32 has the
+// throughput; FP64 on this part does not), then a fixed-order FP64 tree across
+// threads and CTAs.
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
 #include "pradmm_internal.h"
+
+// Resident 256-thread CTAs per SM requested from the register allocator.
+#ifndef PRADMM_MINB_SP
+#define PRADMM_MINB_SP 3
+#endif
+#ifndef PRADMM_MINB_Q
+#define PRADMM_MINB_Q 4
+#endif
 
 namespace pradmm {
 namespace {
@@ -47,8 +61,9 @@ struct IO<float> {
         float4 v = reinterpret_cast<const float4*>(p)[i];
         return {v.x, v.y, v.z, v.w};
     }
-    static __device__ __forceinline__ R4<float> ldro(const float* __restrict__ p, int64_t i) {
-        float4 v = __ldg(reinterpret_cast<const float4*>(p) + i);
+    // streamed once per sweep: evict-first
+    static __device__ __forceinline__ R4<float> ldcs(const float* __restrict__ p, int64_t i) {
+        float4 v = __ldcs(reinterpret_cast<const float4*>(p) + i);
         return {v.x, v.y, v.z, v.w};
     }
     static __device__ __forceinline__ void st(float* p, int64_t i, float a, float b, float c, float d) {
@@ -63,9 +78,9 @@ struct IO<double> {
         double2 u = v[0], w = v[1];
         return {u.x, u.y, w.x, w.y};
     }
-    static __device__ __forceinline__ R4<double> ldro(const double* __restrict__ p, int64_t i) {
+    static __device__ __forceinline__ R4<double> ldcs(const double* __restrict__ p, int64_t i) {
         const double2* v = reinterpret_cast<const double2*>(p) + 2 * i;
-        double2 u = __ldg(v), w = __ldg(v + 1);
+        double2 u = __ldcs(v), w = __ldcs(v + 1);
         return {u.x, u.y, w.x, w.y};
     }
     static __device__ __forceinline__ void st(double* p, int64_t i, double a, double b, double c, double d) {
@@ -117,6 +132,15 @@ __device__ __forceinline__ Q<A> qmul_pr(const Q<A>& a, A vx, A vy, A vz) {
             a.w * vz + a.x * vy - a.y * vx};
 }
 
+// Im(a [0, v] b^*): the rotated-translation term c_e = Im(q t~_e p^*).
+template <typename A>
+__device__ __forceinline__ void im_rot(const Q<A>& a, A vx, A vy, A vz, const Q<A>& b, A& cx, A& cy, A& cz) {
+    const Q<A> h = qmul_pr(a, vx, vy, vz);
+    cx = -h.w * b.x + h.x * b.w - h.y * b.z + h.z * b.y;
+    cy = -h.w * b.y + h.x * b.z + h.y * b.w - h.z * b.x;
+    cz = -h.w * b.z - h.x * b.y + h.y * b.x + h.z * b.w;
+}
+
 template <typename A>
 __device__ __forceinline__ void axpy(Q<A>& y, A a, const Q<A>& x) {
     y.w += a * x.w;
@@ -125,7 +149,28 @@ __device__ __forceinline__ void axpy(Q<A>& y, A a, const Q<A>& x) {
     y.z += a * x.z;
 }
 
-// ---- deterministic CTA reduction of doubles (fixed shuffle tree) ----------
+// ---- residual accumulation ----------------------------------------------------
+// Per-thread partial of a sum of squares: compensated (Kahan) in FP32, plain
+// in FP64.  The cross-thread and cross-CTA sums are FP64 with a fixed tree.
+template <typename R>
+struct Acc;
+template <>
+struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double get() const { return double(s) - double(c); }
+};
+template <>
+struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double get() const { return s; }
+};
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -133,7 +178,7 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Returns the CTA total in thread 0 (other threads: unspecified).
+// CTA total in thread 0 (other threads: unspecified); fixed shuffle tree.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     v = warp_sum(v);
@@ -148,51 +193,40 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return r;
 }
 
-// ---- p-block, Eq. (3a) / Appendix B.1 ---------------------------------------
+// ---- p-block, serial form (FP64 recompute of a tiny |u|) ---------------------
 // u_i = sum_{e=(i,j)} 2 w_e (t~_j - s~_i)^* q_i t~_e + sum_{e=(l,i)} 2 k_e q_l q_e
 //       + beta1 q_i + lam_i + gamma1 p_i ,      p_i^{new} = u_i / |u_i|
-// (A_1 is scalar by Lemma MW(c), and the minimiser of its linear term on S^3
-// is -b_1/|b_1| = u/|u|.)  Since t~_j - s~_i is pure, its conjugate is its
-// negative: the out-edge term is -2 w_e r~ q_i t~_e with r = t_j - s_i.
+// (Eq. (3a) / Appendix B.1: A_1 is scalar by Lemma MW(c), and the minimiser of
+// the linear term on S^3 is -b_1/|b_1| = u/|u|.)  t~_j - s~_i is pure, so its
+// conjugate is its negative: the out-edge term is -2 w_e r~ q_i t~_e, r = t_j - s_i.
 template <typename R, typename A>
-__device__ __forceinline__ Q<A> p_rhs(const GraphDev<R>& g, const R* __restrict__ t, const R* __restrict__ q,
-                                      int64_t i, const Q<A>& qi, const Q<A>& li, const Q<A>& pi, A sx, A sy,
-                                      A sz, const Coef<R>& c) {
+__device__ __noinline__ Q<A> p_rhs_serial(const GraphDev<R>& g, const R* t, const R* q, int64_t i, const Q<A>& qi,
+                                          const Q<A>& li, const Q<A>& pi, A sx, A sy, A sz, const Coef<R>& c) {
     const A b1 = A(c.beta1), g1 = A(c.g1);
     Q<A> u = {b1 * qi.w + li.w + g1 * pi.w, b1 * qi.x + li.x + g1 * pi.x, b1 * qi.y + li.y + g1 * pi.y,
               b1 * qi.z + li.z + g1 * pi.z};
-    const int e0 = g.out_ptr[i], e1 = g.out_ptr[i + 1];
-    for (int e = e0; e < e1; ++e) {
-        const int j = g.out_dst[e];
-        const R4<R> te = IO<R>::ldro(g.out_te, e);
-        const R4<R> tj = IO<R>::ld(t, j);
+    for (int e = g.out_ptr[i]; e < g.out_ptr[i + 1]; ++e) {
+        const R4<R> te = IO<R>::ld(g.out_te, e);
+        const R4<R> tj = IO<R>::ld(t, g.out_idx[e]);
         const A rx = A(tj.a) - sx, ry = A(tj.b) - sy, rz = A(tj.c) - sz;
-        const Q<A> v = qmul_pr(qmul_pl(rx, ry, rz, qi), A(te.a), A(te.b), A(te.c));
-        axpy(u, A(-2) * A(te.d), v);
+        axpy(u, A(-2) * A(te.d), qmul_pr(qmul_pl(rx, ry, rz, qi), A(te.a), A(te.b), A(te.c)));
     }
-    const int f0 = g.in_ptr[i], f1 = g.in_ptr[i + 1];
-    for (int e = f0; e < f1; ++e) {
-        const int l = g.in_src[e];
-        const Q<A> qk = asq<A>(IO<R>::ldro(g.in_qk, e));
-        const Q<A> ql = asq<A>(IO<R>::ld(q, l));
-        axpy(u, A(2), qmul(ql, qk));
-    }
+    for (int e = g.in_ptr[i]; e < g.in_ptr[i + 1]; ++e)
+        axpy(u, A(2), qmul(asq<A>(IO<R>::ld(q, g.in_idx[e])), asq<A>(IO<R>::ld(g.in_qk, e))));
     return u;
 }
 
-// Normalises u (computed in R); in FP32, a tiny |u| is recomputed in FP64
-// from the same inputs; |u| == 0 keeps p^k (the sphere minimiser is not
-// unique then).  Writes p_out[i].
+// p-update finish for vertex i: normalise u; in FP32 a tiny |u| is recomputed in
+// FP64 from the same inputs; |u| == 0 keeps p^k (sphere minimiser not unique).
 template <typename R>
-__device__ __forceinline__ void p_finish(const GraphDev<R>& g, const R* t, const R* q, int64_t i,
-                                         const R4<R>& qr, const R4<R>& lr, const R4<R>& pr, R sx, R sy,
-                                         R sz, const Coef<R>& c, R* p_out, Ctrl* ctrl) {
-    const Q<R> qi = asq<R>(qr), li = asq<R>(lr), pi = asq<R>(pr);
-    Q<R> u = p_rhs<R, R>(g, t, q, i, qi, li, pi, sx, sy, sz, c);
+__device__ __forceinline__ void p_normalise(const GraphDev<R>& g, const StateDev<R>& S, int64_t i, const Q<R>& u,
+                                            const R4<R>& qr, const R4<R>& lr, const R4<R>& pr, R sx, R sy, R sz,
+                                            const Coef<R>& c, R* p_out, Ctrl* ctrl) {
     const R nn = u.w * u.w + u.x * u.x + u.y * u.y + u.z * u.z;
-    if (sizeof(R) == sizeof(float) && double(sqrt(nn)) < c.fb_thresh) {
-        const Q<double> qd = asq<double>(qr), ld = asq<double>(lr), pd = asq<double>(pr);
-        const Q<double> ud = p_rhs<R, double>(g, t, q, i, qd, ld, pd, double(sx), double(sy), double(sz), c);
+    const R nrm = sqrt(nn);
+    if (sizeof(R) == sizeof(float) && nrm < R(c.fb_thresh)) {
+        const Q<double> ud = p_rhs_serial<R, double>(g, S.t, S.q, i, asq<double>(qr), asq<double>(lr), asq<double>(pr),
+                                                     double(sx), double(sy), double(sz), c);
         const double nd = sqrt(ud.w * ud.w + ud.x * ud.x + ud.y * ud.y + ud.z * ud.z);
         atomicAdd(&ctrl->fallbacks, 1ull);
         if (nd > 0.0) {
@@ -204,7 +238,7 @@ __device__ __forceinline__ void p_finish(const GraphDev<R>& g, const R* t, const
         return;
     }
     if (nn > R(0)) {
-        const R inv = R(1) / sqrt(nn);
+        const R inv = R(1) / nrm;
         IO<R>::st(p_out, i, u.w * inv, u.x * inv, u.y * inv, u.z * inv);
     } else {
         atomicAdd(&ctrl->zero_u, 1ull);
@@ -212,29 +246,47 @@ __device__ __forceinline__ void p_finish(const GraphDev<R>& g, const R* t, const
     }
 }
 
-// First p-block of a run (when no p^{k+1} was computed ahead).
-template <typename R>
-__global__ void __launch_bounds__(256) k_p(GraphDev<R> g, StateDev<R> S, Coef<R> c, Ctrl* ctrl) {
-    const long long k = ctrl->iter;
-    const R* pc = S.p[k & 1];
-    R* pn = S.p[(k + 1) & 1];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
-        const R4<R> qr = IO<R>::ld(S.q, i), lr = IO<R>::ld(S.lam, i), pr = IO<R>::ld(pc, i);
-        const R4<R> sr = IO<R>::ld(S.s, i);
-        p_finish<R>(g, S.t, S.q, i, qr, lr, pr, sr.a, sr.b, sr.c, c, pn, ctrl);
+// Visits edges [e0, e1) kUnroll at a time: load(e, buffer) issues the loads
+// of one edge, use(buffer) consumes them; the group's loads are all in
+// flight before the first use.  Uses run in edge order.
+#ifndef PRADMM_UNROLL
+#define PRADMM_UNROLL 2
+#endif
+constexpr int kUnroll = PRADMM_UNROLL;
+
+template <typename T, typename LoadF, typename UseF>
+__device__ __forceinline__ void for_edges(int e0, int e1, LoadF load, UseF use) {
+    int e = e0;
+    for (; e + kUnroll <= e1; e += kUnroll) {
+        T b[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) load(e + u, b[u]);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) use(b[u]);
+    }
+    for (; e < e1; ++e) {
+        T b0;
+        load(e, b0);
+        use(b0);
     }
 }
 
-// ---- q-block (3b) / Appendix B.2 + lambda (3e) ----------------------------
+// ---- q-block (3b) / Appendix B.2 + lambda (3e) --------------------------------
 // q_i = [sum_{e=(i,j)} 2 (w_e r~ p_i t~_e^* + k_e p_j q_e^*) + beta1 p_i - lam_i + gamma2 q_i] / A_2,
 // r = t_j - s_i (t^k, s^k), p = p^{k+1};  lam_i -= tau beta1 (p_i - q_i^{new}).
 template <typename R>
-__global__ void __launch_bounds__(256) k_q(GraphDev<R> g, StateDev<R> S, Coef<R> c, Ctrl* ctrl, double* part) {
+struct QEdge {
+    R4<R> te, qk, tj, pj;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256, PRADMM_MINB_Q) k_q(GraphDev<R> g, StateDev<R> S, Coef<R> c, Ctrl* ctrl, double* part,
+                                           int pstride) {
     __shared__ double sh[32];
     if (ctrl->halt) return;
     const long long k = ctrl->iter;
     const R* pn = S.p[(k + 1) & 1];
-    double acc_dq = 0.0, acc_dl = 0.0;
+    Acc<R> adq, adl;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
         const Q<R> pi = asq<R>(IO<R>::ld(pn, i));
         const Q<R> qi = asq<R>(IO<R>::ld(S.q, i));
@@ -242,51 +294,57 @@ __global__ void __launch_bounds__(256) k_q(GraphDev<R> g, StateDev<R> S, Coef<R>
         const R4<R> sr = IO<R>::ld(S.s, i);  // (s_i, 1/A_2)
         Q<R> b = {c.beta1 * pi.w - li.w + c.g2 * qi.w, c.beta1 * pi.x - li.x + c.g2 * qi.x,
                   c.beta1 * pi.y - li.y + c.g2 * qi.y, c.beta1 * pi.z - li.z + c.g2 * qi.z};
-        const int e0 = g.out_ptr[i], e1 = g.out_ptr[i + 1];
-        for (int e = e0; e < e1; ++e) {
-            const int j = g.out_dst[e];
-            const R4<R> te = IO<R>::ldro(g.out_te, e);
-            const Q<R> qk = asq<R>(IO<R>::ldro(g.out_qk, e));
-            const R4<R> tj = IO<R>::ld(S.t, j);
-            const Q<R> pj = asq<R>(IO<R>::ld(pn, j));
-            const R rx = tj.a - sr.a, ry = tj.b - sr.b, rz = tj.c - sr.c;
-            // 2 w r~ p t~^* = -2 w r~ p t~ (t~ pure)
-            axpy(b, R(-2) * te.d, qmul_pr(qmul_pl(rx, ry, rz, pi), te.a, te.b, te.c));
-            // 2 k p_j q_e^* = 2 p_j (k q_e)^*
-            axpy(b, R(2), qmul_c(pj, qk));
-        }
+        for_edges<QEdge<R>>(
+            g.out_ptr[i], g.out_ptr[i + 1],
+            [&](int e, QEdge<R>& x) {
+                const int j = __ldcs(g.out_idx + e);
+                x.te = IO<R>::ldcs(g.out_te, e);
+                x.qk = IO<R>::ldcs(g.out_qk, e);
+                x.tj = IO<R>::ld(S.t, j);
+                x.pj = IO<R>::ld(pn, j);
+            },
+            [&](const QEdge<R>& x) {
+                const R rx = x.tj.a - sr.a, ry = x.tj.b - sr.b, rz = x.tj.c - sr.c;
+                // 2 w r~ p t~^* = -2 w r~ p t~ (t~ pure);  2 k p_j q_e^* = 2 p_j (k q_e)^*
+                axpy(b, R(-2) * x.te.d, qmul_pr(qmul_pl(rx, ry, rz, pi), x.te.a, x.te.b, x.te.c));
+                axpy(b, R(2), qmul_c(asq<R>(x.pj), asq<R>(x.qk)));
+            });
         const R inv = sr.d;
         const R qw = b.w * inv, qx = b.x * inv, qy = b.y * inv, qz = b.z * inv;
         const R lw = li.w - c.tb1 * (pi.w - qw), lx = li.x - c.tb1 * (pi.x - qx);
         const R ly = li.y - c.tb1 * (pi.y - qy), lz = li.z - c.tb1 * (pi.z - qz);
         IO<R>::st(S.q, i, qw, qx, qy, qz);
         IO<R>::st(S.lam, i, lw, lx, ly, lz);
-        double d0 = double(qw) - double(qi.w), d1 = double(qx) - double(qi.x);
-        double d2 = double(qy) - double(qi.y), d3 = double(qz) - double(qi.z);
-        acc_dq += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
-        d0 = double(lw) - double(li.w); d1 = double(lx) - double(li.x);
-        d2 = double(ly) - double(li.y); d3 = double(lz) - double(li.z);
-        acc_dl += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+        R d0 = qw - qi.w, d1 = qx - qi.x, d2 = qy - qi.y, d3 = qz - qi.z;
+        adq.add(d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3);
+        d0 = lw - li.w; d1 = lx - li.x; d2 = ly - li.y; d3 = lz - li.z;
+        adl.add(d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3);
     }
-    const double sq = block_sum(acc_dq, sh);
-    const double sl = block_sum(acc_dl, sh);
+    const double sq = block_sum(adq.get(), sh);
+    const double sl = block_sum(adl.get(), sh);
     if (threadIdx.x == 0) {
-        part[SLOT_DQ * gridDim.x + blockIdx.x] = sq;
-        part[SLOT_DLAM * gridDim.x + blockIdx.x] = sl;
+        part[SLOT_DQ * pstride + blockIdx.x] = sq;
+        part[SLOT_DLAM * pstride + blockIdx.x] = sl;
     }
 }
 
-// ---- t-block (3c) / Appendix B.3 ------------------------------------------
+// ---- t-block (3c) / Appendix B.3 ------------------------------------------------
 // t_i = [sum_{e=(l,i)} 2 w_e (s_l + c_e) + beta2 s_i + z_i + gamma3 t_i] / A_3,
-// c_e = Im(q_l t~_e p_l^*) with q = q^{k+1}, p = p^{k+1} (reading R3), s = s^k.
+// c_e = Im(q_l t~_e p_l^*) with q = q^{k+1}, p = p^{k+1} (tail of e), s = s^k.
 // c_e is recomputed from the gathered tail state rather than stored.
 template <typename R>
-__global__ void __launch_bounds__(256) k_t(GraphDev<R> g, StateDev<R> S, Coef<R> c, Ctrl* ctrl, double* part) {
+struct TEdge {
+    R4<R> te, sl, ql, pl;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_t(GraphDev<R> g, StateDev<R> S, Coef<R> c, Ctrl* ctrl, double* part,
+                                           int pstride) {
     __shared__ double sh[32];
     if (ctrl->halt) return;
     const long long k = ctrl->iter;
     const R* pn = S.p[(k + 1) & 1];
-    double acc_dt = 0.0;
+    Acc<R> adt;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
         const R4<R> tr = IO<R>::ld(S.t, i);  // (t_i, 1/A_3)
         const R4<R> sr = IO<R>::ld(S.s, i);
@@ -294,43 +352,47 @@ __global__ void __launch_bounds__(256) k_t(GraphDev<R> g, StateDev<R> S, Coef<R>
         R ax = c.beta2 * sr.a + zr.a + c.g3 * tr.a;
         R ay = c.beta2 * sr.b + zr.b + c.g3 * tr.b;
         R az = c.beta2 * sr.c + zr.c + c.g3 * tr.c;
-        const int f0 = g.in_ptr[i], f1 = g.in_ptr[i + 1];
-        for (int e = f0; e < f1; ++e) {
-            const int l = g.in_src[e];
-            const R4<R> te = IO<R>::ldro(g.in_te, e);
-            const R4<R> sl = IO<R>::ld(S.s, l);
-            const Q<R> ql = asq<R>(IO<R>::ld(S.q, l));
-            const Q<R> pl = asq<R>(IO<R>::ld(pn, l));
-            const Q<R> ce = qmul_c(qmul_pr(ql, te.a, te.b, te.c), pl);
-            const R w2 = R(2) * te.d;
-            ax += w2 * (sl.a + ce.x);
-            ay += w2 * (sl.b + ce.y);
-            az += w2 * (sl.c + ce.z);
-        }
+        for_edges<TEdge<R>>(
+            g.in_ptr[i], g.in_ptr[i + 1],
+            [&](int e, TEdge<R>& x) {
+                const int l = __ldcs(g.in_idx + e);
+                x.te = IO<R>::ldcs(g.in_te, e);
+                x.sl = IO<R>::ld(S.s, l);
+                x.ql = IO<R>::ld(S.q, l);
+                x.pl = IO<R>::ld(pn, l);
+            },
+            [&](const TEdge<R>& x) {
+                R cx, cy, cz;
+                im_rot(asq<R>(x.ql), x.te.a, x.te.b, x.te.c, asq<R>(x.pl), cx, cy, cz);
+                const R w2 = R(2) * x.te.d;
+                ax += w2 * (x.sl.a + cx);
+                ay += w2 * (x.sl.b + cy);
+                az += w2 * (x.sl.c + cz);
+            });
         const R inv = tr.d;
         const R nx = ax * inv, ny = ay * inv, nz = az * inv;
         IO<R>::st(S.t, i, nx, ny, nz, inv);
-        const double d0 = double(nx) - double(tr.a), d1 = double(ny) - double(tr.b), d2 = double(nz) - double(tr.c);
-        acc_dt += d0 * d0 + d1 * d1 + d2 * d2;
+        const R d0 = nx - tr.a, d1 = ny - tr.b, d2 = nz - tr.c;
+        adt.add(d0 * d0 + d1 * d1 + d2 * d2);
     }
-    const double st = block_sum(acc_dt, sh);
-    if (threadIdx.x == 0) part[SLOT_DT * gridDim.x + blockIdx.x] = st;
+    const double st = block_sum(adt.get(), sh);
+    if (threadIdx.x == 0) part[SLOT_DT * pstride + blockIdx.x] = st;
 }
 
-// ---- residual e^{k+1} and stop decision (last CTA) --------------------------
-__device__ __forceinline__ void finish_iteration(Ctrl* ctrl, const double* part, const Launch& L,
-                                                 double b1, double b2, double* sh) {
+// ---- residual e^{k+1} and stop decision (last CTA of the s/z + p sweep) ---------
+__device__ __forceinline__ void finish_iteration(Ctrl* ctrl, const Launch& L, double b1, double b2, double* sh) {
     __shared__ bool last;
     __threadfence();
     if (threadIdx.x == 0) last = (atomicAdd(&ctrl->ticket, 1u) == gridDim.x - 1);
     __syncthreads();
     if (!last) return;
     __threadfence();
+    const int cnt[4] = {L.grid_q, L.grid_sp, L.grid_q, L.grid_t};  // slots DLAM, DZ, DQ, DT
     double tot[4];
 #pragma unroll
     for (int sl = 0; sl < 4; ++sl) {
         double v = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(part + sl * gridDim.x + b);
+        for (int b = threadIdx.x; b < cnt[sl]; b += blockDim.x) v += __ldcg(L.part + sl * L.pstride + b);
         tot[sl] = block_sum(v, sh);
     }
     if (threadIdx.x == 0) {
@@ -360,58 +422,107 @@ __device__ __forceinline__ void finish_iteration(Ctrl* ctrl, const double* part,
     }
 }
 
-// ---- s-block (3d) / Appendix B.4 + z (3f), then p-block of iteration k+1 ----
-// s_i = [sum_{e=(i,j)} 2 w_e (t_j - c_e) + beta2 t_i - z_i + gamma4 s_i] / A_4 with
-// t = t^{k+1}, c_e = Im(q_i t~_e p_i^*) (q^{k+1}, p^{k+1}), s = s^k, z = z^k;
-// z_i -= tau beta2 (t_i - s_i^{new}).
+// ---- s-block (3d) / Appendix B.4 + z (3f), then p-block (3a) of the next iteration ----
+// WITH_S = true  (k_sp): s_i = [sum_{e=(i,j)} 2 w_e (t_j - c_e) + beta2 t_i - z_i + gamma4 s_i] / A_4
+//   with t = t^{k+1}, c_e = Im(q_i t~_e p_i^*) (q^{k+1}, p^{k+1}), s = s^k, z = z^k;
+//   z_i -= tau beta2 (t_i - s_i^{new}); then p^{k+2} from (q, lam, p, s, t)^{k+1}.
+// WITH_S = false (k_p, the first p-block of a run): p^{k+1} from x^k.
+// The p-block's out-edge term needs s_i^{new}, known only after the whole
+// out-edge sum of the s-block; by bilinearity
+//   sum_e -2 w_e (t~_j - s~^{new}) q t~_e
+//     = sum_e -2 w_e (t~_j - s~^{old}) q t~_e  -  (s~^{old} - s~^{new}) q (sum_e 2 w_e t~_e),
+// so one pass over the out-edges serves both blocks.  Both parts stay well
+// conditioned: t_j - s^{old} is a short edge-length vector and s^{old} - s^{new}
+// is the step of s, not a difference of absolute positions.
 template <typename R>
-__global__ void __launch_bounds__(256) k_sp(GraphDev<R> g, StateDev<R> S, Coef<R> c, Launch L) {
+struct SEdge {
+    R4<R> te, tj;
+};
+template <typename R>
+struct PEdge {
+    R4<R> qk, ql;
+};
+
+template <typename R, bool WITH_S>
+__global__ void __launch_bounds__(256, PRADMM_MINB_SP) k_sp(GraphDev<R> g, StateDev<R> S, Coef<R> c, Launch L) {
     __shared__ double sh[32];
     Ctrl* ctrl = L.ctrl;
-    if (ctrl->halt) {
+    if (WITH_S && ctrl->halt) {
         // a halted while-loop body must still end the loop
         if (L.has_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(L.cond, 0u);
         return;
     }
     const long long k = ctrl->iter;
-    const R* pc = S.p[(k + 1) & 1];  // p^{k+1}
-    R* pn = S.p[k & 1];              // p^{k+2}, computed ahead
-    double acc_dz = 0.0;
+    const R* pc = WITH_S ? S.p[(k + 1) & 1] : S.p[k & 1];  // p used by this sweep
+    R* pn = WITH_S ? S.p[k & 1] : S.p[(k + 1) & 1];        // p computed ahead
+    Acc<R> adz;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
-        const R4<R> tr = IO<R>::ld(S.t, i);
         const R4<R> sr = IO<R>::ld(S.s, i);  // (s_i, 1/A_2)
-        const R4<R> zr = IO<R>::ld(S.z, i);  // (z_i, 1/A_4)
         const R4<R> qr = IO<R>::ld(S.q, i);
         const R4<R> pr = IO<R>::ld(pc, i);
-        const Q<R> qi = asq<R>(qr), pi = asq<R>(pr);
-        R ax = c.beta2 * tr.a - zr.a + c.g4 * sr.a;
-        R ay = c.beta2 * tr.b - zr.b + c.g4 * sr.b;
-        R az = c.beta2 * tr.c - zr.c + c.g4 * sr.c;
-        const int e0 = g.out_ptr[i], e1 = g.out_ptr[i + 1];
-        for (int e = e0; e < e1; ++e) {
-            const int j = g.out_dst[e];
-            const R4<R> te = IO<R>::ldro(g.out_te, e);
-            const R4<R> tj = IO<R>::ld(S.t, j);
-            const Q<R> ce = qmul_c(qmul_pr(qi, te.a, te.b, te.c), pi);
-            const R w2 = R(2) * te.d;
-            ax += w2 * (tj.a - ce.x);
-            ay += w2 * (tj.b - ce.y);
-            az += w2 * (tj.c - ce.z);
-        }
-        const R inv = zr.d;
-        const R sx = ax * inv, sy = ay * inv, sz = az * inv;
-        const R zx = zr.a - c.tb2 * (tr.a - sx), zy = zr.b - c.tb2 * (tr.b - sy), zz = zr.c - c.tb2 * (tr.c - sz);
-        IO<R>::st(S.s, i, sx, sy, sz, sr.d);
-        IO<R>::st(S.z, i, zx, zy, zz, inv);
-        const double d0 = double(zx) - double(zr.a), d1 = double(zy) - double(zr.b), d2 = double(zz) - double(zr.c);
-        acc_dz += d0 * d0 + d1 * d1 + d2 * d2;
-        // p-block of iteration k+1 (uses q^{k+1}, lam^{k+1}, p^{k+1}, s^{k+1}, t^{k+1})
         const R4<R> lr = IO<R>::ld(S.lam, i);
-        p_finish<R>(g, S.t, S.q, i, qr, lr, pr, sx, sy, sz, c, pn, ctrl);
+        const Q<R> qi = asq<R>(qr), pi = asq<R>(pr);
+        // out-edge pass: s-block sum (WITH_S), p-block term at s^{old}, sum 2 w t_e
+        R ax = R(0), ay = R(0), az = R(0);
+        R wx = R(0), wy = R(0), wz = R(0);
+        Q<R> u = {R(0), R(0), R(0), R(0)};
+        for_edges<SEdge<R>>(
+            g.out_ptr[i], g.out_ptr[i + 1],
+            [&](int e, SEdge<R>& x) {
+                const int j = __ldcs(g.out_idx + e);
+                x.te = IO<R>::ldcs(g.out_te, e);
+                x.tj = IO<R>::ld(S.t, j);
+            },
+            [&](const SEdge<R>& x) {
+                const R w2 = R(2) * x.te.d;
+                if (WITH_S) {
+                    R cx, cy, cz;
+                    im_rot(qi, x.te.a, x.te.b, x.te.c, pi, cx, cy, cz);
+                    ax += w2 * (x.tj.a - cx);
+                    ay += w2 * (x.tj.b - cy);
+                    az += w2 * (x.tj.c - cz);
+                    wx += w2 * x.te.a;
+                    wy += w2 * x.te.b;
+                    wz += w2 * x.te.c;
+                }
+                const R rx = x.tj.a - sr.a, ry = x.tj.b - sr.b, rz = x.tj.c - sr.c;
+                axpy(u, -w2, qmul_pr(qmul_pl(rx, ry, rz, qi), x.te.a, x.te.b, x.te.c));
+            });
+        R sx = sr.a, sy = sr.b, sz = sr.c;
+        if (WITH_S) {
+            const R4<R> tr = IO<R>::ld(S.t, i);
+            const R4<R> zr = IO<R>::ld(S.z, i);  // (z_i, 1/A_4)
+            const R inv = zr.d;
+            sx = (ax + c.beta2 * tr.a - zr.a + c.g4 * sr.a) * inv;
+            sy = (ay + c.beta2 * tr.b - zr.b + c.g4 * sr.b) * inv;
+            sz = (az + c.beta2 * tr.c - zr.c + c.g4 * sr.c) * inv;
+            const R zx = zr.a - c.tb2 * (tr.a - sx), zy = zr.b - c.tb2 * (tr.b - sy), zz = zr.c - c.tb2 * (tr.c - sz);
+            IO<R>::st(S.s, i, sx, sy, sz, sr.d);
+            IO<R>::st(S.z, i, zx, zy, zz, inv);
+            const R d0 = zx - zr.a, d1 = zy - zr.b, d2 = zz - zr.c;
+            adz.add(d0 * d0 + d1 * d1 + d2 * d2);
+            // move the p-block's out-edge term from s^{old} to s^{new}
+            axpy(u, R(-1), qmul_pr(qmul_pl(sr.a - sx, sr.b - sy, sr.c - sz, qi), wx, wy, wz));
+        }
+        // own terms beta1 q_i + lam_i + gamma1 p_i, then in-edge terms 2 q_l (k_e q_e)
+        Q<R> v = {c.beta1 * qr.a + lr.a + c.g1 * pr.a, c.beta1 * qr.b + lr.b + c.g1 * pr.b,
+                  c.beta1 * qr.c + lr.c + c.g1 * pr.c, c.beta1 * qr.d + lr.d + c.g1 * pr.d};
+        axpy(v, R(1), u);
+        for_edges<PEdge<R>>(
+            g.in_ptr[i], g.in_ptr[i + 1],
+            [&](int e, PEdge<R>& x) {
+                const int l = __ldcs(g.in_idx + e);
+                x.qk = IO<R>::ldcs(g.in_qk, e);
+                x.ql = IO<R>::ld(S.q, l);
+            },
+            [&](const PEdge<R>& x) { axpy(v, R(2), qmul(asq<R>(x.ql), asq<R>(x.qk))); });
+        p_normalise<R>(g, S, i, v, qr, lr, pr, sx, sy, sz, c, pn, ctrl);
     }
-    const double sd = block_sum(acc_dz, sh);
-    if (threadIdx.x == 0) L.part[SLOT_DZ * gridDim.x + blockIdx.x] = sd;
-    finish_iteration(ctrl, L.part, L, c.b1d, c.b2d, sh);
+    if (WITH_S) {
+        const double sd = block_sum(adz.get(), sh);
+        if (threadIdx.x == 0) L.part[SLOT_DZ * L.pstride + blockIdx.x] = sd;
+        finish_iteration(ctrl, L, c.b1d, c.b2d, sh);
+    }
 }
 
 __global__ void k_arm(Ctrl* ctrl, long long iters, int use_tol, double tol) {
@@ -421,6 +532,7 @@ __global__ void k_arm(Ctrl* ctrl, long long iters, int use_tol, double tol) {
     ctrl->use_tol = use_tol;
     ctrl->tol = tol;
     ctrl->nonfinite = 0;
+    ctrl->timeout = 0;
     ctrl->ticket = 0u;
 }
 
@@ -438,9 +550,8 @@ __global__ void __launch_bounds__(256) k_objective(GraphDev<R> g, StateDev<R> S,
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
         const Q<double> pi = asq<double>(IO<R>::ld(pc, i));
         const R4<R> ti = IO<R>::ld(S.t, i);
-        const int e0 = g.out_ptr[i], e1 = g.out_ptr[i + 1];
-        for (int e = e0; e < e1; ++e) {
-            const int j = g.out_dst[e];
+        for (int e = g.out_ptr[i]; e < g.out_ptr[i + 1]; ++e) {
+            const int j = g.out_idx[e];
             const Q<double> pj = asq<double>(IO<R>::ld(pc, j));
             const R4<R> tj = IO<R>::ld(S.t, j);
             // t~_j - t~_i - p_i t~_e p_i^*
@@ -474,34 +585,41 @@ __global__ void __launch_bounds__(256) k_objective(GraphDev<R> g, StateDev<R> S,
     }
 }
 
-// ---- layout conversion ---------------------------------------------------------
+// ---- layout conversion (internal vertex i <-> user vertex perm[i]) -------------
 template <typename R>
-__global__ void k_pack4(const double* __restrict__ src, R* dst, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        IO<R>::st(dst, i, R(src[4 * i]), R(src[4 * i + 1]), R(src[4 * i + 2]), R(src[4 * i + 3]));
-}
-template <typename R>
-__global__ void k_pack3(const double* __restrict__ src, const double* __restrict__ inv, R* dst, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        IO<R>::st(dst, i, R(src[3 * i]), R(src[3 * i + 1]), R(src[3 * i + 2]), R(inv[i]));
-}
-template <typename R>
-__global__ void k_unpack4(const R* src, double* dst, int64_t n) {
+__global__ void k_pack4(const double* __restrict__ src, const int32_t* __restrict__ perm, R* dst, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const R4<R> v = IO<R>::ld(src, i);
-        dst[4 * i] = v.a;
-        dst[4 * i + 1] = v.b;
-        dst[4 * i + 2] = v.c;
-        dst[4 * i + 3] = v.d;
+        const int64_t u = perm[i];
+        IO<R>::st(dst, i, R(src[4 * u]), R(src[4 * u + 1]), R(src[4 * u + 2]), R(src[4 * u + 3]));
     }
 }
 template <typename R>
-__global__ void k_unpack3(const R* src, double* dst, int64_t n) {
+__global__ void k_pack3(const double* __restrict__ src, const int32_t* __restrict__ perm,
+                        const double* __restrict__ inv, R* dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = perm[i];
+        IO<R>::st(dst, i, R(src[3 * u]), R(src[3 * u + 1]), R(src[3 * u + 2]), R(inv[i]));
+    }
+}
+template <typename R>
+__global__ void k_unpack4(const R* src, const int32_t* __restrict__ perm, double* dst, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const R4<R> v = IO<R>::ld(src, i);
-        dst[3 * i] = v.a;
-        dst[3 * i + 1] = v.b;
-        dst[3 * i + 2] = v.c;
+        const int64_t u = perm[i];
+        dst[4 * u] = v.a;
+        dst[4 * u + 1] = v.b;
+        dst[4 * u + 2] = v.c;
+        dst[4 * u + 3] = v.d;
+    }
+}
+template <typename R>
+__global__ void k_unpack3(const R* src, const int32_t* __restrict__ perm, double* dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const R4<R> v = IO<R>::ld(src, i);
+        const int64_t u = perm[i];
+        dst[3 * u] = v.a;
+        dst[3 * u + 1] = v.b;
+        dst[3 * u + 2] = v.c;
     }
 }
 
@@ -516,44 +634,36 @@ inline int conv_grid(int64_t n) {
 
 template <typename R>
 cudaError_t launch_p(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const Launch& L) {
-    k_p<R><<<L.grid, L.block, 0, L.stream>>>(g, s, c, L.ctrl);
+    k_sp<R, false><<<L.grid_p, L.block, 0, L.stream>>>(g, s, c, L);
     return cudaGetLastError();
 }
 template <typename R>
 cudaError_t launch_q(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const Launch& L) {
-    k_q<R><<<L.grid, L.block, 0, L.stream>>>(g, s, c, L.ctrl, L.part);
+    k_q<R><<<L.grid_q, L.block, 0, L.stream>>>(g, s, c, L.ctrl, L.part, L.pstride);
     return cudaGetLastError();
 }
 template <typename R>
 cudaError_t launch_t(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const Launch& L) {
-    k_t<R><<<L.grid, L.block, 0, L.stream>>>(g, s, c, L.ctrl, L.part);
+    k_t<R><<<L.grid_t, L.block, 0, L.stream>>>(g, s, c, L.ctrl, L.part, L.pstride);
     return cudaGetLastError();
 }
 template <typename R>
 cudaError_t launch_sp(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const Launch& L) {
-    k_sp<R><<<L.grid, L.block, 0, L.stream>>>(g, s, c, L);
+    k_sp<R, true><<<L.grid_sp, L.block, 0, L.stream>>>(g, s, c, L);
     return cudaGetLastError();
 }
 
-cudaError_t sweep_occupancy(int is_double, int block, int* blocks_per_sm) {
-    int a = 0, b = 0, c = 0, d = 0;
-    cudaError_t err;
-    if (is_double) {
-        if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_q<double>, block, 0))) return err;
-        if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_t<double>, block, 0))) return err;
-        if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_sp<double>, block, 0))) return err;
-        if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, k_p<double>, block, 0))) return err;
-    } else {
-        if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_q<float>, block, 0))) return err;
-        if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_t<float>, block, 0))) return err;
-        if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_sp<float>, block, 0))) return err;
-        if ((err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d, k_p<float>, block, 0))) return err;
-    }
-    int m = a < b ? a : b;
-    m = m < c ? m : c;
-    m = m < d ? m : d;
-    *blocks_per_sm = m;
-    return cudaSuccess;
+template <typename R>
+cudaError_t occupancy_r(int block, int* bps) {
+    cudaError_t e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps[0], k_sp<R, false>, block, 0))) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps[1], k_q<R>, block, 0))) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps[2], k_t<R>, block, 0))) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps[3], k_sp<R, true>, block, 0);
+}
+
+cudaError_t sweep_occupancy(int is_double, int block, int* bps) {
+    return is_double ? occupancy_r<double>(block, bps) : occupancy_r<float>(block, bps);
 }
 
 cudaError_t launch_arm(Ctrl* ctrl, long long iters, int use_tol, double tol, cudaStream_t st) {
@@ -562,32 +672,32 @@ cudaError_t launch_arm(Ctrl* ctrl, long long iters, int use_tol, double tol, cud
 }
 
 template <typename R>
-cudaError_t launch_objective(const GraphDev<R>& g, const StateDev<R>& s, const int32_t*, const int32_t*,
-                             const double* qe64, const double* te64, const double* kappa64,
-                             const double* omega64, Ctrl* ctrl, double* part, unsigned int* ticket, double* F_dev,
-                             int grid, int block, cudaStream_t st) {
+cudaError_t launch_objective(const GraphDev<R>& g, const StateDev<R>& s, const double* qe64, const double* te64,
+                             const double* kappa64, const double* omega64, Ctrl* ctrl, double* part,
+                             unsigned int* ticket, double* F_dev, int grid, int block, cudaStream_t st) {
     k_objective<R><<<grid, block, 0, st>>>(g, s, qe64, te64, kappa64, omega64, ctrl, part, ticket, F_dev);
     return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_pack4(const double* src, R* dst, int64_t n, cudaStream_t st) {
-    k_pack4<R><<<conv_grid(n), 256, 0, st>>>(src, dst, n);
+cudaError_t launch_pack4(const double* src, const int32_t* perm, R* dst, int64_t n, cudaStream_t st) {
+    k_pack4<R><<<conv_grid(n), 256, 0, st>>>(src, perm, dst, n);
     return cudaGetLastError();
 }
 template <typename R>
-cudaError_t launch_pack3(const double* src, const double* inv, R* dst, int64_t n, cudaStream_t st) {
-    k_pack3<R><<<conv_grid(n), 256, 0, st>>>(src, inv, dst, n);
+cudaError_t launch_pack3(const double* src, const int32_t* perm, const double* inv, R* dst, int64_t n,
+                         cudaStream_t st) {
+    k_pack3<R><<<conv_grid(n), 256, 0, st>>>(src, perm, inv, dst, n);
     return cudaGetLastError();
 }
 template <typename R>
-cudaError_t launch_unpack4(const R* src, double* dst, int64_t n, cudaStream_t st) {
-    k_unpack4<R><<<conv_grid(n), 256, 0, st>>>(src, dst, n);
+cudaError_t launch_unpack4(const R* src, const int32_t* perm, double* dst, int64_t n, cudaStream_t st) {
+    k_unpack4<R><<<conv_grid(n), 256, 0, st>>>(src, perm, dst, n);
     return cudaGetLastError();
 }
 template <typename R>
-cudaError_t launch_unpack3(const R* src, double* dst, int64_t n, cudaStream_t st) {
-    k_unpack3<R><<<conv_grid(n), 256, 0, st>>>(src, dst, n);
+cudaError_t launch_unpack3(const R* src, const int32_t* perm, double* dst, int64_t n, cudaStream_t st) {
+    k_unpack3<R><<<conv_grid(n), 256, 0, st>>>(src, perm, dst, n);
     return cudaGetLastError();
 }
 
@@ -596,14 +706,14 @@ cudaError_t launch_unpack3(const R* src, double* dst, int64_t n, cudaStream_t st
     template cudaError_t launch_q<R>(const GraphDev<R>&, const StateDev<R>&, const Coef<R>&, const Launch&);  \
     template cudaError_t launch_t<R>(const GraphDev<R>&, const StateDev<R>&, const Coef<R>&, const Launch&);  \
     template cudaError_t launch_sp<R>(const GraphDev<R>&, const StateDev<R>&, const Coef<R>&, const Launch&); \
-    template cudaError_t launch_objective<R>(const GraphDev<R>&, const StateDev<R>&, const int32_t*,           \
-                                             const int32_t*, const double*, const double*, const double*,     \
-                                             const double*, Ctrl*, double*, unsigned int*, double*, int, int,  \
-                                             cudaStream_t);                                                   \
-    template cudaError_t launch_pack4<R>(const double*, R*, int64_t, cudaStream_t);                           \
-    template cudaError_t launch_pack3<R>(const double*, const double*, R*, int64_t, cudaStream_t);            \
-    template cudaError_t launch_unpack4<R>(const R*, double*, int64_t, cudaStream_t);                         \
-    template cudaError_t launch_unpack3<R>(const R*, double*, int64_t, cudaStream_t);
+    template cudaError_t launch_objective<R>(const GraphDev<R>&, const StateDev<R>&, const double*,           \
+                                             const double*, const double*, const double*, Ctrl*, double*,     \
+                                             unsigned int*, double*, int, int, cudaStream_t);                 \
+    template cudaError_t launch_pack4<R>(const double*, const int32_t*, R*, int64_t, cudaStream_t);           \
+    template cudaError_t launch_pack3<R>(const double*, const int32_t*, const double*, R*, int64_t,           \
+                                         cudaStream_t);                                                       \
+    template cudaError_t launch_unpack4<R>(const R*, const int32_t*, double*, int64_t, cudaStream_t);         \
+    template cudaError_t launch_unpack3<R>(const R*, const int32_t*, double*, int64_t, cudaStream_t);
 
 PRADMM_INST(float)
 PRADMM_INST(double)

