@@ -177,6 +177,34 @@ pradmm_status pradmm_bytes_per_iteration(pradmm_t h, double* out);
  * iteration time.  The state advances by `iters` iterations. */
 pradmm_status pradmm_profile_sweeps(pradmm_t h, int32_t iters, double* ms_out);
 
+/* F of Eq. (1) for poses already in device memory, written to the device
+ * double *F_d, without allocating any memory.  There is no counterpart in the
+ * paper: it serves callers that cannot allocate device memory when they need
+ * the objective (for example a real-time process that reserves all of its GPU
+ * memory at start-up and forbids allocation afterwards, since an allocation
+ * can synchronise the device and stall the loop), and that therefore cannot
+ * create a handle.
+ *   src_d, dst_d     m int32 edge endpoints in [0, n) (not validated)
+ *   q_meas_d         m x 4 relative rotations (used as given, not renormalised)
+ *   t_meas_d         m x 3 relative translations
+ *   kappa_d, omega_d m weights, or NULL for all ones
+ *   q_d, t_d         n x 4 rotations and n x 3 translations to evaluate
+ *   F_d              one double, written on `cuda_stream`
+ * All pointers are device memory; the call is asynchronous on cuda_stream.
+ * Scratch: one FP64 partial per chunk of 1024 edges and a counter live in a
+ * 32 KiB static device array that every GPU loading the library keeps until
+ * process exit; m above 4,194,304 is rejected with PRADMM_ERR_ARG.  The first
+ * call on a device looks up that array's device address (with the device
+ * current); make that first call before any stream capture.  Every call on
+ * a device shares that device's array and leaves its contents behind, so
+ * calls that may overlap on the same GPU (for example on different streams)
+ * race: serialise them.  Each call clears the counter before its kernel
+ * runs and rewrites every partial it reads. */
+pradmm_status pradmm_objective_noalloc(int64_t n, int64_t m, const int32_t* src_d, const int32_t* dst_d,
+                                       const double* q_meas_d, const double* t_meas_d,
+                                       const double* kappa_d, const double* omega_d, const double* q_d,
+                                       const double* t_d, double* F_d, void* cuda_stream);
+
 /* Frees every resource of the handle (NULL is a no-op). */
 void pradmm_destroy(pradmm_t h);
 

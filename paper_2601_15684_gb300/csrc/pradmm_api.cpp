@@ -42,6 +42,8 @@ pradmm_status fail(pradmm_status st, const char* fmt, ...) {
 
 }  // namespace
 
+void pradmm::set_last_error(const char* msg) { g_last_error = msg; }
+
 struct pradmm_s {
     int64_t n = 0, m = 0;
     pradmm_params prm{};

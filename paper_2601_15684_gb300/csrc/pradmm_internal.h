@@ -122,4 +122,7 @@ cudaError_t launch_unpack4(const R* src, const int32_t* perm, double* dst, int64
 template <typename R>
 cudaError_t launch_unpack3(const R* src, const int32_t* perm, double* dst, int64_t n, cudaStream_t st);
 
+// Records the message pradmm_last_error() returns on the calling thread.
+void set_last_error(const char* msg);
+
 }  // namespace pradmm

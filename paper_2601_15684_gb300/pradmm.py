@@ -75,6 +75,7 @@ _SIGS = {
     "pradmm_counters": (ctypes.c_int, [_h, _i64]),
     "pradmm_bytes_per_iteration": (ctypes.c_int, [_h, _d]),
     "pradmm_profile_sweeps": (ctypes.c_int, [_h, ctypes.c_int32, _d]),
+    "pradmm_objective_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 10),
     "pradmm_destroy": (None, [_h]),
     "pradmm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pradmm_last_error": (ctypes.c_char_p, []),
@@ -234,6 +235,17 @@ def pradmm_profile_sweeps(h, iters: int) -> dict:
     out = np.zeros(4)
     _check(load().pradmm_profile_sweeps(h, int(iters), _dp(out)), "pradmm_profile_sweeps")
     return {"k_q": out[0], "k_t": out[1], "k_sp": out[2], "iteration": out[3]}
+
+
+def pradmm_objective_noalloc(n, m, src_ptr, dst_ptr, q_meas_ptr, t_meas_ptr, kappa_ptr, omega_ptr, q_ptr, t_ptr,
+                             F_ptr, stream=None):
+    """F of Eq. (1) from device arrays into the device double at F_ptr, with no
+    allocation (for callers that cannot allocate device memory at that point;
+    see pradmm.h).  Pointers are raw device addresses (e.g. tensor.data_ptr());
+    kappa_ptr / omega_ptr may be 0 for unit weights."""
+    args = [ctypes.c_void_p(x or 0) for x in (src_ptr, dst_ptr, q_meas_ptr, t_meas_ptr, kappa_ptr, omega_ptr, q_ptr,
+                                              t_ptr, F_ptr, stream)]
+    _check(load().pradmm_objective_noalloc(int(n), int(m), *args), "pradmm_objective_noalloc")
 
 
 def pradmm_destroy(h):
