@@ -213,6 +213,59 @@ const char* pradmm_status_string(pradmm_status st);
 /* Message of the last failure on the calling thread ("" if none). */
 const char* pradmm_last_error(void);
 
+/* ---- batched solver ---------------------------------------------------------
+ * Many independent pose graphs (each a problem of the form of Eq. (1)) solved
+ * by Algorithm 1 in one persistent launch captured in a CUDA graph.  The batch
+ * is stored as one disjoint-union graph; a work queue ordered largest first
+ * gives each large graph a whole CTA and packs small graphs one per warp.
+ * Each graph stops on its own: when e^k <= rel_tol * e^1 (the ratio of its
+ * Appendix E.1 residual to the first iteration's), when e^k is not finite,
+ * or after max_iter iterations.  Results of a graph are bitwise those of
+ * the plain solver run for the same number of iterations. */
+typedef struct pradmm_batch_s* pradmm_batch_t;
+
+/* G graphs; graph g has n_g[g] >= 1 vertices and m_g[g] >= 0 edges.  Edge
+ * arrays are concatenated in graph order with GRAPH-LOCAL endpoints in
+ * [0, n_g[g]); layouts and validation as pradmm_create.  The schedule starts
+ * at block 256, warp_max_n 256. */
+pradmm_status pradmm_batch_create(int32_t G, const int64_t* n_g, const int64_t* m_g, const int32_t* src,
+                                  const int32_t* dst, const double* q_meas, const double* t_meas,
+                                  const double* kappa, const double* omega, const pradmm_params* prm,
+                                  void* cuda_stream, pradmm_batch_t* out);
+
+/* Schedule: `block` threads per CTA of the persistent kernel (64, 128, 256,
+ * 512); graphs with at most warp_max_n vertices are solved one per warp,
+ * larger ones one per CTA. */
+pradmm_status pradmm_batch_set_schedule(pradmm_batch_t b, int32_t block, int32_t warp_max_n);
+pradmm_status pradmm_batch_get_schedule(pradmm_batch_t b, int32_t* block, int32_t* warp_max_n);
+
+/* Times `iters` iterations of every candidate schedule (block 128/256/512 x
+ * warp_max_n 0/64/256/1024) from the current state, keeps the fastest and
+ * restores the state.  Outputs are nullable. */
+pradmm_status pradmm_batch_autotune(pradmm_batch_t b, int32_t iters, int32_t* block_out,
+                                    int32_t* warp_max_n_out);
+
+/* Initial states, all graphs at once (q: N x 4, t: N x 3 with N = sum n_g, in
+ * graph order): odometry composition per graph, or given poses. */
+pradmm_status pradmm_batch_init_odometry(pradmm_batch_t b);
+pradmm_status pradmm_batch_set_state(pradmm_batch_t b, const double* q, const double* t);
+
+/* Runs every graph from the current state until its stopping rule.  Per-graph
+ * outputs (G entries each, nullable): iterations, e^1, last e^k, and the
+ * outcome (PRADMM_OK converged, PRADMM_ERR_NOT_CONVERGED max_iter reached,
+ * PRADMM_ERR_NONFINITE).  Returns PRADMM_OK when every graph converged. */
+pradmm_status pradmm_batch_solve(pradmm_batch_t b, double rel_tol, int32_t max_iter, int32_t* iters,
+                                 double* e_first, double* e_last, int32_t* status);
+
+/* F of Eq. (1) of each graph at its (p, t), double precision: F has G entries. */
+pradmm_status pradmm_batch_objectives(pradmm_batch_t b, double* F);
+
+/* State of all graphs (N rows each, graph order); any pointer may be NULL. */
+pradmm_status pradmm_batch_get_state(pradmm_batch_t b, double* p, double* q, double* t, double* s,
+                                     double* lam, double* z);
+
+void pradmm_batch_destroy(pradmm_batch_t b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -996,3 +996,313 @@ const char* pradmm_status_string(pradmm_status st) {
 const char* pradmm_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
+
+// ---- batched solver (many independent graphs, one persistent launch) ----------
+
+struct pradmm_batch_s {
+    pradmm_s* h = nullptr;  // the disjoint-union graph: graph g owns vertices [off[g], off[g+1])
+    int32_t G = 0;
+    std::vector<int64_t> off;  // G + 1 vertex offsets
+    std::vector<int64_t> n_g;
+    int64_t* gv_d = nullptr;
+    int32_t* order_d = nullptr;
+    int2* items_d = nullptr;
+    int* next_d = nullptr;
+    int32_t* iters_d = nullptr;
+    double* e_first_d = nullptr;
+    double* e_last_d = nullptr;
+    int32_t* status_d = nullptr;
+    double* F_d = nullptr;
+    double* save_d = nullptr;  // 24 n doubles: state snapshot for the autotuner
+    int n_items = 0;
+    int block = 256;        // threads per CTA of the persistent kernel
+    int warp_max_n = 256;   // graphs up to this many vertices are solved by one warp
+    int grid = 1;
+};
+
+namespace {
+
+void batch_free(pradmm_batch_s* b) {
+    if (!b) return;
+    if (b->h) {
+        free_all(b->h);
+        delete b->h;
+    }
+    delete b;
+}
+
+// Work items: graphs larger than warp_max_n get a whole CTA each (largest
+// first); the others are packed, in decreasing size, block/32 per CTA.
+pradmm_status batch_schedule(pradmm_batch_s* b, int block, int warp_max_n) {
+    if (block != 64 && block != 128 && block != 256 && block != 512)
+        return fail(PRADMM_ERR_ARG, "batch block must be 64, 128, 256 or 512");
+    if (warp_max_n < 0) return fail(PRADMM_ERR_ARG, "warp_max_n must be >= 0");
+    std::vector<int32_t> order(b->G);
+    for (int32_t g = 0; g < b->G; ++g) order[g] = g;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t c) { return b->n_g[a] > b->n_g[c]; });
+    std::vector<int2> items;
+    const int wpb = block / 32;
+    int32_t pos = 0;
+    while (pos < b->G && b->n_g[order[pos]] > warp_max_n) items.push_back(make_int2(pos++, -1));
+    while (pos < b->G) {
+        const int cnt = std::min<int32_t>(wpb, b->G - pos);
+        items.push_back(make_int2(pos, cnt));
+        pos += cnt;
+    }
+    pradmm_s* h = b->h;
+    CU(cudaMemcpyAsync(b->order_d, order.data(), sizeof(int32_t) * b->G, cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemcpyAsync(b->items_d, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    int dev = 0, sms = 0, bps = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CU(h->fp64 ? pradmm::batch_occupancy<double>(block, &bps) : pradmm::batch_occupancy<float>(block, &bps));
+    b->n_items = (int)items.size();
+    b->block = block;
+    b->warp_max_n = warp_max_n;
+    b->grid = std::max(1, std::min(b->n_items, sms * std::max(bps, 1)));
+    return PRADMM_OK;
+}
+
+pradmm::BatchDev batch_dev(const pradmm_batch_s* b, double rel_tol, double abs_tol, int max_iter) {
+    pradmm::BatchDev d;
+    d.gv = b->gv_d;
+    d.order = b->order_d;
+    d.items = b->items_d;
+    d.n_items = b->n_items;
+    d.next = b->next_d;
+    d.iters = b->iters_d;
+    d.e_first = b->e_first_d;
+    d.e_last = b->e_last_d;
+    d.status = b->status_d;
+    d.rel_tol = rel_tol;
+    d.abs_tol = abs_tol;
+    d.max_iter = max_iter;
+    return d;
+}
+
+// One persistent launch, captured in a CUDA graph and replayed once.
+template <typename R>
+pradmm_status batch_run(pradmm_batch_s* b, double rel_tol, double abs_tol, int max_iter) {
+    pradmm_s* h = b->h;
+    if (!h->state_set) return fail(PRADMM_ERR_STATE, "batch state is not set");
+    const pradmm::BatchDev d = batch_dev(b, rel_tol, abs_tol, max_iter);
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e1 = pradmm::launch_batch<R>(h->gdev<R>(), h->sdev<R>(), h->coef<R>(), d, h->ctrl, b->grid, b->block,
+                                             h->stream);
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
+    CU(e1);
+    CU(e2);
+    cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
+    if (e3 == cudaSuccess) e3 = cudaGraphLaunch(exec, h->stream);
+    if (e3 == cudaSuccess) e3 = cudaStreamSynchronize(h->stream);
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    CU(e3);
+    return PRADMM_OK;
+}
+
+pradmm_status batch_run_any(pradmm_batch_s* b, double rel_tol, double abs_tol, int max_iter) {
+    return b->h->fp64 ? batch_run<double>(b, rel_tol, abs_tol, max_iter) : batch_run<float>(b, rel_tol, abs_tol, max_iter);
+}
+
+}  // namespace
+
+extern "C" {
+
+pradmm_status pradmm_batch_create(int32_t G, const int64_t* n_g, const int64_t* m_g, const int32_t* src,
+                                  const int32_t* dst, const double* q_meas, const double* t_meas, const double* kappa,
+                                  const double* omega, const pradmm_params* prm, void* cuda_stream,
+                                  pradmm_batch_t* out) {
+    if (!out) return fail(PRADMM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (G < 1 || !n_g || !m_g) return fail(PRADMM_ERR_ARG, "need G >= 1 and the size arrays");
+    try {
+        pradmm_batch_s* b = new pradmm_batch_s();
+        b->G = G;
+        b->off.assign(G + 1, 0);
+        b->n_g.assign(n_g, n_g + G);
+        int64_t m = 0;
+        for (int32_t g = 0; g < G; ++g) {
+            if (n_g[g] < 1 || m_g[g] < 0) {
+                delete b;
+                return fail(PRADMM_ERR_ARG, "graph %d: need n >= 1 and m >= 0", g);
+            }
+            b->off[g + 1] = b->off[g] + n_g[g];
+            m += m_g[g];
+        }
+        const int64_t n = b->off[G];
+        if (n > INT32_MAX - 1 || m > INT32_MAX - 1) {
+            delete b;
+            return fail(PRADMM_ERR_ARG, "batch too large for int32 vertex / edge indices");
+        }
+        // union graph: shift each graph's local endpoints by its vertex offset
+        std::vector<int32_t> us(m), ud(m);
+        int64_t e = 0;
+        for (int32_t g = 0; g < G; ++g) {
+            for (int64_t k = 0; k < m_g[g]; ++k, ++e) {
+                if (src[e] < 0 || src[e] >= n_g[g] || dst[e] < 0 || dst[e] >= n_g[g]) {
+                    delete b;
+                    return fail(PRADMM_ERR_INDEX, "graph %d edge %lld: endpoint outside [0, %lld)", g, (long long)k,
+                                (long long)n_g[g]);
+                }
+                us[e] = (int32_t)(src[e] + b->off[g]);
+                ud[e] = (int32_t)(dst[e] + b->off[g]);
+            }
+        }
+        pradmm_t h = nullptr;
+        pradmm_status st = create_common(n, m, us.data(), ud.data(), q_meas, t_meas, kappa, omega, prm, cuda_stream, &h);
+        if (st != PRADMM_OK) {
+            delete b;
+            return st;
+        }
+        b->h = h;
+        st = dalloc(h, &b->gv_d, G + 1);
+        if (st == PRADMM_OK) st = dalloc(h, &b->order_d, G);
+        if (st == PRADMM_OK) st = dalloc(h, &b->items_d, G);
+        if (st == PRADMM_OK) st = dalloc(h, &b->next_d, 1);
+        if (st == PRADMM_OK) st = dalloc(h, &b->iters_d, G);
+        if (st == PRADMM_OK) st = dalloc(h, &b->e_first_d, G);
+        if (st == PRADMM_OK) st = dalloc(h, &b->e_last_d, G);
+        if (st == PRADMM_OK) st = dalloc(h, &b->status_d, G);
+        if (st == PRADMM_OK) st = dalloc(h, &b->F_d, G);
+        if (st == PRADMM_OK) {
+            cudaError_t ce = cudaMemcpy(b->gv_d, b->off.data(), sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice);
+            if (ce != cudaSuccess) st = fail(PRADMM_ERR_CUDA, "upload: %s", cudaGetErrorString(ce));
+        }
+        if (st == PRADMM_OK) st = batch_schedule(b, 256, 256);
+        if (st != PRADMM_OK) {
+            batch_free(b);
+            return st;
+        }
+        *out = b;
+        return PRADMM_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(PRADMM_ERR_NOMEM, "host allocation failed");
+    }
+}
+
+pradmm_status pradmm_batch_set_schedule(pradmm_batch_t b, int32_t block, int32_t warp_max_n) {
+    if (!b) return fail(PRADMM_ERR_ARG, "NULL handle");
+    return batch_schedule(b, block, warp_max_n);
+}
+
+pradmm_status pradmm_batch_get_schedule(pradmm_batch_t b, int32_t* block, int32_t* warp_max_n) {
+    if (!b) return fail(PRADMM_ERR_ARG, "NULL handle");
+    if (block) *block = b->block;
+    if (warp_max_n) *warp_max_n = b->warp_max_n;
+    return PRADMM_OK;
+}
+
+pradmm_status pradmm_batch_init_odometry(pradmm_batch_t b) {
+    if (!b) return fail(PRADMM_ERR_ARG, "NULL handle");
+    return pradmm_init_odometry(b->h);
+}
+
+pradmm_status pradmm_batch_set_state(pradmm_batch_t b, const double* q, const double* t) {
+    if (!b) return fail(PRADMM_ERR_ARG, "NULL handle");
+    return pradmm_set_state(b->h, q, t);
+}
+
+pradmm_status pradmm_batch_solve(pradmm_batch_t b, double rel_tol, int32_t max_iter, int32_t* iters, double* e_first,
+                                 double* e_last, int32_t* status) {
+    if (!b) return fail(PRADMM_ERR_ARG, "NULL handle");
+    if (!(rel_tol >= 0) || max_iter < 0) return fail(PRADMM_ERR_ARG, "need rel_tol >= 0 and max_iter >= 0");
+    ST(batch_run_any(b, rel_tol, 0.0, max_iter));
+    const size_t G = (size_t)b->G;
+    std::vector<int32_t> st(G);
+    cudaStream_t s = b->h->stream;
+    if (iters) CU(cudaMemcpyAsync(iters, b->iters_d, sizeof(int32_t) * G, cudaMemcpyDeviceToHost, s));
+    if (e_first) CU(cudaMemcpyAsync(e_first, b->e_first_d, sizeof(double) * G, cudaMemcpyDeviceToHost, s));
+    if (e_last) CU(cudaMemcpyAsync(e_last, b->e_last_d, sizeof(double) * G, cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(st.data(), b->status_d, sizeof(int32_t) * G, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (status) std::memcpy(status, st.data(), sizeof(int32_t) * G);
+    bool nonfinite = false, all = true;
+    for (int32_t v : st) {
+        nonfinite |= v == pradmm::PRADMM_BATCH_NONFINITE;
+        all &= v == pradmm::PRADMM_BATCH_CONVERGED;
+    }
+    if (nonfinite) return fail(PRADMM_ERR_NONFINITE, "a graph produced a non-finite residual");
+    if (!all) return fail(PRADMM_ERR_NOT_CONVERGED, "some graphs reached max_iter before the stopping rule");
+    return PRADMM_OK;
+}
+
+pradmm_status pradmm_batch_objectives(pradmm_batch_t b, double* F) {
+    if (!b || !F) return fail(PRADMM_ERR_ARG, "NULL argument");
+    pradmm_s* h = b->h;
+    if (!h->state_set) return fail(PRADMM_ERR_STATE, "batch state is not set");
+    const pradmm::BatchDev d = batch_dev(b, 0.0, 0.0, 0);
+    cudaError_t e = h->fp64 ? pradmm::launch_batch_objective<double>(h->gdev<double>(), h->sdev<double>(), h->qe64,
+                                                                    h->te64, h->ka64, h->om64, d, b->F_d, b->G, h->stream)
+                            : pradmm::launch_batch_objective<float>(h->gdev<float>(), h->sdev<float>(), h->qe64,
+                                                                   h->te64, h->ka64, h->om64, d, b->F_d, b->G, h->stream);
+    CU(e);
+    CU(cudaMemcpyAsync(F, b->F_d, sizeof(double) * b->G, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return PRADMM_OK;
+}
+
+pradmm_status pradmm_batch_get_state(pradmm_batch_t b, double* p, double* q, double* t, double* s, double* lam,
+                                     double* z) {
+    if (!b) return fail(PRADMM_ERR_ARG, "NULL handle");
+    return pradmm_get_state(b->h, p, q, t, s, lam, z);
+}
+
+pradmm_status pradmm_batch_autotune(pradmm_batch_t b, int32_t iters, int32_t* block_out, int32_t* warp_max_n_out) {
+    if (!b) return fail(PRADMM_ERR_ARG, "NULL handle");
+    if (iters < 1) return fail(PRADMM_ERR_ARG, "iters must be >= 1");
+    pradmm_s* h = b->h;
+    if (!h->state_set) return fail(PRADMM_ERR_STATE, "batch state is not set");
+    const int64_t n = h->n;
+    if (!b->save_d) ST(dalloc(h, &b->save_d, 24 * n));
+    double* sv = b->save_d;
+    // snapshot the state; every candidate starts from it, and it is restored after
+    ST(h->fp64 ? get_state_impl<double>(h, sv, sv + 4 * n, sv + 8 * n, sv + 11 * n, sv + 14 * n, sv + 18 * n, true)
+               : get_state_impl<float>(h, sv, sv + 4 * n, sv + 8 * n, sv + 11 * n, sv + 14 * n, sv + 18 * n, true));
+    const int blocks[3] = {128, 256, 512};
+    const int warp_ns[4] = {0, 64, 256, 1024};
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_b = b->block, best_w = b->warp_max_n;
+    pradmm_status st = PRADMM_OK;
+    for (int bi = 0; bi < 3 && st == PRADMM_OK; ++bi) {
+        for (int wi = 0; wi < 4 && st == PRADMM_OK; ++wi) {
+            st = batch_schedule(b, blocks[bi], warp_ns[wi]);
+            if (st != PRADMM_OK) break;
+            st = set_state_any(h, sv, sv + 4 * n, sv + 8 * n, sv + 11 * n, sv + 14 * n, sv + 18 * n, true);
+            if (st != PRADMM_OK) break;
+            cudaEventRecord(e0, h->stream);
+            st = batch_run_any(b, 0.0, 0.0, iters);  // fixed iterations: rel_tol 0 never stops early
+            cudaEventRecord(e1, h->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (st == PRADMM_OK && ms < best) {
+                best = ms;
+                best_b = blocks[bi];
+                best_w = warp_ns[wi];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == PRADMM_OK) st = batch_schedule(b, best_b, best_w);
+    if (st == PRADMM_OK) st = set_state_any(h, sv, sv + 4 * n, sv + 8 * n, sv + 11 * n, sv + 14 * n, sv + 18 * n, true);
+    if (st != PRADMM_OK) return st;
+    if (block_out) *block_out = best_b;
+    if (warp_max_n_out) *warp_max_n_out = best_w;
+    return PRADMM_OK;
+}
+
+void pradmm_batch_destroy(pradmm_batch_t b) {
+    if (!b) return;
+    if (b->h && b->h->stream) cudaStreamSynchronize(b->h->stream);
+    batch_free(b);
+}
+
+}  // extern "C"

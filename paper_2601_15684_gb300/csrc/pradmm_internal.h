@@ -122,6 +122,39 @@ cudaError_t launch_unpack4(const R* src, const int32_t* perm, double* dst, int64
 template <typename R>
 cudaError_t launch_unpack3(const R* src, const int32_t* perm, double* dst, int64_t n, cudaStream_t st);
 
+// ---- batched solver ------------------------------------------------------------
+
+// Per-graph outcome codes (the pradmm_status values of the same meaning).
+enum { PRADMM_BATCH_CONVERGED = 0, PRADMM_BATCH_NONFINITE = 4, PRADMM_BATCH_MAXITER = 8 };
+
+// Device view of a batch: graph g owns internal vertices [gv[g], gv[g+1]) of
+// the union graph.  Work items (order positions, count): count < 0 is one
+// graph solved by a whole CTA, count > 0 a pack of that many small graphs
+// solved by one warp each.  `next` is the queue counter.
+struct BatchDev {
+    const int64_t* gv;    // G + 1
+    const int32_t* order; // graphs by size, largest first
+    const int2* items;    // n_items
+    int n_items;
+    int* next;
+    int32_t* iters;       // G outputs
+    double* e_first;
+    double* e_last;
+    int32_t* status;
+    double rel_tol, abs_tol;
+    int max_iter;
+};
+
+template <typename R>
+cudaError_t launch_batch(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const BatchDev& b,
+                         Ctrl* ctrl, int grid, int block, cudaStream_t st);
+template <typename R>
+cudaError_t batch_occupancy(int block, int* bps);
+template <typename R>
+cudaError_t launch_batch_objective(const GraphDev<R>& g, const StateDev<R>& s, const double* qe64,
+                                   const double* te64, const double* ka64, const double* om64,
+                                   const BatchDev& b, double* F, int G, cudaStream_t st);
+
 // Records the message pradmm_last_error() returns on the calling thread.
 void set_last_error(const char* msg);
 

@@ -29,6 +29,7 @@
 
 #include <cstdint>
 
+#include "pradmm_device.cuh"
 #include "pradmm_internal.h"
 
 // Resident 256-thread CTAs per SM requested from the register allocator.
@@ -42,242 +43,7 @@
 namespace pradmm {
 namespace {
 
-template <typename R>
-struct Q {
-    R w, x, y, z;
-};
-
-template <typename R>
-struct R4 {
-    R a, b, c, d;
-};
-
-template <typename R>
-struct IO;
-
-template <>
-struct IO<float> {
-    static __device__ __forceinline__ R4<float> ld(const float* p, int64_t i) {
-        float4 v = reinterpret_cast<const float4*>(p)[i];
-        return {v.x, v.y, v.z, v.w};
-    }
-    // streamed once per sweep: evict-first
-    static __device__ __forceinline__ R4<float> ldcs(const float* __restrict__ p, int64_t i) {
-        float4 v = __ldcs(reinterpret_cast<const float4*>(p) + i);
-        return {v.x, v.y, v.z, v.w};
-    }
-    static __device__ __forceinline__ void st(float* p, int64_t i, float a, float b, float c, float d) {
-        reinterpret_cast<float4*>(p)[i] = make_float4(a, b, c, d);
-    }
-};
-
-template <>
-struct IO<double> {
-    static __device__ __forceinline__ R4<double> ld(const double* p, int64_t i) {
-        const double2* v = reinterpret_cast<const double2*>(p) + 2 * i;
-        double2 u = v[0], w = v[1];
-        return {u.x, u.y, w.x, w.y};
-    }
-    static __device__ __forceinline__ R4<double> ldcs(const double* __restrict__ p, int64_t i) {
-        const double2* v = reinterpret_cast<const double2*>(p) + 2 * i;
-        double2 u = __ldcs(v), w = __ldcs(v + 1);
-        return {u.x, u.y, w.x, w.y};
-    }
-    static __device__ __forceinline__ void st(double* p, int64_t i, double a, double b, double c, double d) {
-        double2* v = reinterpret_cast<double2*>(p) + 2 * i;
-        v[0] = make_double2(a, b);
-        v[1] = make_double2(c, d);
-    }
-};
-
-template <typename A, typename R>
-__device__ __forceinline__ Q<A> asq(const R4<R>& v) {
-    return {A(v.a), A(v.b), A(v.c), A(v.d)};
-}
-
-// ---- quaternion algebra (Appendix A.2): pq = [p0 q0 - p.q, p0 q + q0 p + p x q]
-
-template <typename A>
-__device__ __forceinline__ Q<A> qmul(const Q<A>& a, const Q<A>& b) {
-    return {a.w * b.w - a.x * b.x - a.y * b.y - a.z * b.z,
-            a.w * b.x + a.x * b.w + a.y * b.z - a.z * b.y,
-            a.w * b.y - a.x * b.z + a.y * b.w + a.z * b.x,
-            a.w * b.z + a.x * b.y - a.y * b.x + a.z * b.w};
-}
-
-// a b^*
-template <typename A>
-__device__ __forceinline__ Q<A> qmul_c(const Q<A>& a, const Q<A>& b) {
-    return {a.w * b.w + a.x * b.x + a.y * b.y + a.z * b.z,
-            -a.w * b.x + a.x * b.w - a.y * b.z + a.z * b.y,
-            -a.w * b.y + a.x * b.z + a.y * b.w - a.z * b.x,
-            -a.w * b.z - a.x * b.y + a.y * b.x + a.z * b.w};
-}
-
-// [0, v] b
-template <typename A>
-__device__ __forceinline__ Q<A> qmul_pl(A vx, A vy, A vz, const Q<A>& b) {
-    return {-vx * b.x - vy * b.y - vz * b.z,
-            vx * b.w + vy * b.z - vz * b.y,
-            -vx * b.z + vy * b.w + vz * b.x,
-            vx * b.y - vy * b.x + vz * b.w};
-}
-
-// a [0, v]
-template <typename A>
-__device__ __forceinline__ Q<A> qmul_pr(const Q<A>& a, A vx, A vy, A vz) {
-    return {-a.x * vx - a.y * vy - a.z * vz,
-            a.w * vx + a.y * vz - a.z * vy,
-            a.w * vy - a.x * vz + a.z * vx,
-            a.w * vz + a.x * vy - a.y * vx};
-}
-
-// Im(a [0, v] b^*): the rotated-translation term c_e = Im(q t~_e p^*).
-template <typename A>
-__device__ __forceinline__ void im_rot(const Q<A>& a, A vx, A vy, A vz, const Q<A>& b, A& cx, A& cy, A& cz) {
-    const Q<A> h = qmul_pr(a, vx, vy, vz);
-    cx = -h.w * b.x + h.x * b.w - h.y * b.z + h.z * b.y;
-    cy = -h.w * b.y + h.x * b.z + h.y * b.w - h.z * b.x;
-    cz = -h.w * b.z - h.x * b.y + h.y * b.x + h.z * b.w;
-}
-
-template <typename A>
-__device__ __forceinline__ void axpy(Q<A>& y, A a, const Q<A>& x) {
-    y.w += a * x.w;
-    y.x += a * x.x;
-    y.y += a * x.y;
-    y.z += a * x.z;
-}
-
-// ---- residual accumulation ----------------------------------------------------
-// Per-thread partial of a sum of squares: compensated (Kahan) in FP32, plain
-// in FP64.  The cross-thread and cross-CTA sums are FP64 with a fixed tree.
-template <typename R>
-struct Acc;
-template <>
-struct Acc<float> {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float x) {
-        const float y = x - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-    __device__ __forceinline__ double get() const { return double(s) - double(c); }
-};
-template <>
-struct Acc<double> {
-    double s = 0.0;
-    __device__ __forceinline__ void add(double x) { s += x; }
-    __device__ __forceinline__ double get() const { return s; }
-};
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// CTA total in thread 0 (other threads: unspecified); fixed shuffle tree.
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    v = warp_sum(v);
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (wid == 0) {
-        r = lane < nw ? sh[lane] : 0.0;
-        r = warp_sum(r);
-    }
-    __syncthreads();
-    return r;
-}
-
-// ---- p-block, serial form (FP64 recompute of a tiny |u|) ---------------------
-// u_i = sum_{e=(i,j)} 2 w_e (t~_j - s~_i)^* q_i t~_e + sum_{e=(l,i)} 2 k_e q_l q_e
-//       + beta1 q_i + lam_i + gamma1 p_i ,      p_i^{new} = u_i / |u_i|
-// (Eq. (3a) / Appendix B.1: A_1 is scalar by Lemma MW(c), and the minimiser of
-// the linear term on S^3 is -b_1/|b_1| = u/|u|.)  t~_j - s~_i is pure, so its
-// conjugate is its negative: the out-edge term is -2 w_e r~ q_i t~_e, r = t_j - s_i.
-template <typename R, typename A>
-__device__ __noinline__ Q<A> p_rhs_serial(const GraphDev<R>& g, const R* t, const R* q, int64_t i, const Q<A>& qi,
-                                          const Q<A>& li, const Q<A>& pi, A sx, A sy, A sz, const Coef<R>& c) {
-    const A b1 = A(c.beta1), g1 = A(c.g1);
-    Q<A> u = {b1 * qi.w + li.w + g1 * pi.w, b1 * qi.x + li.x + g1 * pi.x, b1 * qi.y + li.y + g1 * pi.y,
-              b1 * qi.z + li.z + g1 * pi.z};
-    for (int e = g.out_ptr[i]; e < g.out_ptr[i + 1]; ++e) {
-        const R4<R> te = IO<R>::ld(g.out_te, e);
-        const R4<R> tj = IO<R>::ld(t, g.out_idx[e]);
-        const A rx = A(tj.a) - sx, ry = A(tj.b) - sy, rz = A(tj.c) - sz;
-        axpy(u, A(-2) * A(te.d), qmul_pr(qmul_pl(rx, ry, rz, qi), A(te.a), A(te.b), A(te.c)));
-    }
-    for (int e = g.in_ptr[i]; e < g.in_ptr[i + 1]; ++e)
-        axpy(u, A(2), qmul(asq<A>(IO<R>::ld(q, g.in_idx[e])), asq<A>(IO<R>::ld(g.in_qk, e))));
-    return u;
-}
-
-// p-update finish for vertex i: normalise u; in FP32 a tiny |u| is recomputed in
-// FP64 from the same inputs; |u| == 0 keeps p^k (sphere minimiser not unique).
-template <typename R>
-__device__ __forceinline__ void p_normalise(const GraphDev<R>& g, const StateDev<R>& S, int64_t i, const Q<R>& u,
-                                            const R4<R>& qr, const R4<R>& lr, const R4<R>& pr, R sx, R sy, R sz,
-                                            const Coef<R>& c, R* p_out, Ctrl* ctrl) {
-    const R nn = u.w * u.w + u.x * u.x + u.y * u.y + u.z * u.z;
-    const R nrm = sqrt(nn);
-    if (sizeof(R) == sizeof(float) && nrm < R(c.fb_thresh)) {
-        const Q<double> ud = p_rhs_serial<R, double>(g, S.t, S.q, i, asq<double>(qr), asq<double>(lr), asq<double>(pr),
-                                                     double(sx), double(sy), double(sz), c);
-        const double nd = sqrt(ud.w * ud.w + ud.x * ud.x + ud.y * ud.y + ud.z * ud.z);
-        atomicAdd(&ctrl->fallbacks, 1ull);
-        if (nd > 0.0) {
-            IO<R>::st(p_out, i, R(ud.w / nd), R(ud.x / nd), R(ud.y / nd), R(ud.z / nd));
-        } else {
-            atomicAdd(&ctrl->zero_u, 1ull);
-            IO<R>::st(p_out, i, pr.a, pr.b, pr.c, pr.d);
-        }
-        return;
-    }
-    if (nn > R(0)) {
-        const R inv = R(1) / nrm;
-        IO<R>::st(p_out, i, u.w * inv, u.x * inv, u.y * inv, u.z * inv);
-    } else {
-        atomicAdd(&ctrl->zero_u, 1ull);
-        IO<R>::st(p_out, i, pr.a, pr.b, pr.c, pr.d);
-    }
-}
-
-// Visits edges [e0, e1) kUnroll at a time: load(e, buffer) issues the loads
-// of one edge, use(buffer) consumes them; the group's loads are all in
-// flight before the first use.  Uses run in edge order.
-#ifndef PRADMM_UNROLL
-#define PRADMM_UNROLL 2
-#endif
-constexpr int kUnroll = PRADMM_UNROLL;
-
-template <typename T, typename LoadF, typename UseF>
-__device__ __forceinline__ void for_edges(int e0, int e1, LoadF load, UseF use) {
-    int e = e0;
-    for (; e + kUnroll <= e1; e += kUnroll) {
-        T b[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) load(e + u, b[u]);
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) use(b[u]);
-    }
-    for (; e < e1; ++e) {
-        T b0;
-        load(e, b0);
-        use(b0);
-    }
-}
-
-// ---- q-block (3b) / Appendix B.2 + lambda (3e) --------------------------------
-// q_i = [sum_{e=(i,j)} 2 (w_e r~ p_i t~_e^* + k_e p_j q_e^*) + beta1 p_i - lam_i + gamma2 q_i] / A_2,
-// r = t_j - s_i (t^k, s^k), p = p^{k+1};  lam_i -= tau beta1 (p_i - q_i^{new}).
-template <typename R>
-struct QEdge {
-    R4<R> te, qk, tj, pj;
-};
+using namespace dev;
 
 template <typename R>
 __global__ void __launch_bounds__(256, PRADMM_MINB_Q) k_q(GraphDev<R> g, StateDev<R> S, Coef<R> c, Ctrl* ctrl, double* part,
@@ -287,39 +53,8 @@ __global__ void __launch_bounds__(256, PRADMM_MINB_Q) k_q(GraphDev<R> g, StateDe
     const long long k = ctrl->iter;
     const R* pn = S.p[(k + 1) & 1];
     Acc<R> adq, adl;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
-        const Q<R> pi = asq<R>(IO<R>::ld(pn, i));
-        const Q<R> qi = asq<R>(IO<R>::ld(S.q, i));
-        const Q<R> li = asq<R>(IO<R>::ld(S.lam, i));
-        const R4<R> sr = IO<R>::ld(S.s, i);  // (s_i, 1/A_2)
-        Q<R> b = {c.beta1 * pi.w - li.w + c.g2 * qi.w, c.beta1 * pi.x - li.x + c.g2 * qi.x,
-                  c.beta1 * pi.y - li.y + c.g2 * qi.y, c.beta1 * pi.z - li.z + c.g2 * qi.z};
-        for_edges<QEdge<R>>(
-            g.out_ptr[i], g.out_ptr[i + 1],
-            [&](int e, QEdge<R>& x) {
-                const int j = __ldcs(g.out_idx + e);
-                x.te = IO<R>::ldcs(g.out_te, e);
-                x.qk = IO<R>::ldcs(g.out_qk, e);
-                x.tj = IO<R>::ld(S.t, j);
-                x.pj = IO<R>::ld(pn, j);
-            },
-            [&](const QEdge<R>& x) {
-                const R rx = x.tj.a - sr.a, ry = x.tj.b - sr.b, rz = x.tj.c - sr.c;
-                // 2 w r~ p t~^* = -2 w r~ p t~ (t~ pure);  2 k p_j q_e^* = 2 p_j (k q_e)^*
-                axpy(b, R(-2) * x.te.d, qmul_pr(qmul_pl(rx, ry, rz, pi), x.te.a, x.te.b, x.te.c));
-                axpy(b, R(2), qmul_c(asq<R>(x.pj), asq<R>(x.qk)));
-            });
-        const R inv = sr.d;
-        const R qw = b.w * inv, qx = b.x * inv, qy = b.y * inv, qz = b.z * inv;
-        const R lw = li.w - c.tb1 * (pi.w - qw), lx = li.x - c.tb1 * (pi.x - qx);
-        const R ly = li.y - c.tb1 * (pi.y - qy), lz = li.z - c.tb1 * (pi.z - qz);
-        IO<R>::st(S.q, i, qw, qx, qy, qz);
-        IO<R>::st(S.lam, i, lw, lx, ly, lz);
-        R d0 = qw - qi.w, d1 = qx - qi.x, d2 = qy - qi.y, d3 = qz - qi.z;
-        adq.add(d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3);
-        d0 = lw - li.w; d1 = lx - li.x; d2 = ly - li.y; d3 = lz - li.z;
-        adl.add(d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3);
-    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x)
+        q_vertex<R>(g, S, c, pn, i, adq, adl);
     const double sq = block_sum(adq.get(), sh);
     const double sl = block_sum(adl.get(), sh);
     if (threadIdx.x == 0) {
@@ -327,15 +62,6 @@ __global__ void __launch_bounds__(256, PRADMM_MINB_Q) k_q(GraphDev<R> g, StateDe
         part[SLOT_DLAM * pstride + blockIdx.x] = sl;
     }
 }
-
-// ---- t-block (3c) / Appendix B.3 ------------------------------------------------
-// t_i = [sum_{e=(l,i)} 2 w_e (s_l + c_e) + beta2 s_i + z_i + gamma3 t_i] / A_3,
-// c_e = Im(q_l t~_e p_l^*) with q = q^{k+1}, p = p^{k+1} (tail of e), s = s^k.
-// c_e is recomputed from the gathered tail state rather than stored.
-template <typename R>
-struct TEdge {
-    R4<R> te, sl, ql, pl;
-};
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_t(GraphDev<R> g, StateDev<R> S, Coef<R> c, Ctrl* ctrl, double* part,
@@ -345,36 +71,8 @@ __global__ void __launch_bounds__(256) k_t(GraphDev<R> g, StateDev<R> S, Coef<R>
     const long long k = ctrl->iter;
     const R* pn = S.p[(k + 1) & 1];
     Acc<R> adt;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
-        const R4<R> tr = IO<R>::ld(S.t, i);  // (t_i, 1/A_3)
-        const R4<R> sr = IO<R>::ld(S.s, i);
-        const R4<R> zr = IO<R>::ld(S.z, i);
-        R ax = c.beta2 * sr.a + zr.a + c.g3 * tr.a;
-        R ay = c.beta2 * sr.b + zr.b + c.g3 * tr.b;
-        R az = c.beta2 * sr.c + zr.c + c.g3 * tr.c;
-        for_edges<TEdge<R>>(
-            g.in_ptr[i], g.in_ptr[i + 1],
-            [&](int e, TEdge<R>& x) {
-                const int l = __ldcs(g.in_idx + e);
-                x.te = IO<R>::ldcs(g.in_te, e);
-                x.sl = IO<R>::ld(S.s, l);
-                x.ql = IO<R>::ld(S.q, l);
-                x.pl = IO<R>::ld(pn, l);
-            },
-            [&](const TEdge<R>& x) {
-                R cx, cy, cz;
-                im_rot(asq<R>(x.ql), x.te.a, x.te.b, x.te.c, asq<R>(x.pl), cx, cy, cz);
-                const R w2 = R(2) * x.te.d;
-                ax += w2 * (x.sl.a + cx);
-                ay += w2 * (x.sl.b + cy);
-                az += w2 * (x.sl.c + cz);
-            });
-        const R inv = tr.d;
-        const R nx = ax * inv, ny = ay * inv, nz = az * inv;
-        IO<R>::st(S.t, i, nx, ny, nz, inv);
-        const R d0 = nx - tr.a, d1 = ny - tr.b, d2 = nz - tr.c;
-        adt.add(d0 * d0 + d1 * d1 + d2 * d2);
-    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x)
+        t_vertex<R>(g, S, c, pn, i, adt);
     const double st = block_sum(adt.get(), sh);
     if (threadIdx.x == 0) part[SLOT_DT * pstride + blockIdx.x] = st;
 }
@@ -422,27 +120,6 @@ __device__ __forceinline__ void finish_iteration(Ctrl* ctrl, const Launch& L, do
     }
 }
 
-// ---- s-block (3d) / Appendix B.4 + z (3f), then p-block (3a) of the next iteration ----
-// WITH_S = true  (k_sp): s_i = [sum_{e=(i,j)} 2 w_e (t_j - c_e) + beta2 t_i - z_i + gamma4 s_i] / A_4
-//   with t = t^{k+1}, c_e = Im(q_i t~_e p_i^*) (q^{k+1}, p^{k+1}), s = s^k, z = z^k;
-//   z_i -= tau beta2 (t_i - s_i^{new}); then p^{k+2} from (q, lam, p, s, t)^{k+1}.
-// WITH_S = false (k_p, the first p-block of a run): p^{k+1} from x^k.
-// The p-block's out-edge term needs s_i^{new}, known only after the whole
-// out-edge sum of the s-block; by bilinearity
-//   sum_e -2 w_e (t~_j - s~^{new}) q t~_e
-//     = sum_e -2 w_e (t~_j - s~^{old}) q t~_e  -  (s~^{old} - s~^{new}) q (sum_e 2 w_e t~_e),
-// so one pass over the out-edges serves both blocks.  Both parts stay well
-// conditioned: t_j - s^{old} is a short edge-length vector and s^{old} - s^{new}
-// is the step of s, not a difference of absolute positions.
-template <typename R>
-struct SEdge {
-    R4<R> te, tj;
-};
-template <typename R>
-struct PEdge {
-    R4<R> qk, ql;
-};
-
 template <typename R, bool WITH_S>
 __global__ void __launch_bounds__(256, PRADMM_MINB_SP) k_sp(GraphDev<R> g, StateDev<R> S, Coef<R> c, Launch L) {
     __shared__ double sh[32];
@@ -456,68 +133,8 @@ __global__ void __launch_bounds__(256, PRADMM_MINB_SP) k_sp(GraphDev<R> g, State
     const R* pc = WITH_S ? S.p[(k + 1) & 1] : S.p[k & 1];  // p used by this sweep
     R* pn = WITH_S ? S.p[k & 1] : S.p[(k + 1) & 1];        // p computed ahead
     Acc<R> adz;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
-        const R4<R> sr = IO<R>::ld(S.s, i);  // (s_i, 1/A_2)
-        const R4<R> qr = IO<R>::ld(S.q, i);
-        const R4<R> pr = IO<R>::ld(pc, i);
-        const R4<R> lr = IO<R>::ld(S.lam, i);
-        const Q<R> qi = asq<R>(qr), pi = asq<R>(pr);
-        // out-edge pass: s-block sum (WITH_S), p-block term at s^{old}, sum 2 w t_e
-        R ax = R(0), ay = R(0), az = R(0);
-        R wx = R(0), wy = R(0), wz = R(0);
-        Q<R> u = {R(0), R(0), R(0), R(0)};
-        for_edges<SEdge<R>>(
-            g.out_ptr[i], g.out_ptr[i + 1],
-            [&](int e, SEdge<R>& x) {
-                const int j = __ldcs(g.out_idx + e);
-                x.te = IO<R>::ldcs(g.out_te, e);
-                x.tj = IO<R>::ld(S.t, j);
-            },
-            [&](const SEdge<R>& x) {
-                const R w2 = R(2) * x.te.d;
-                if (WITH_S) {
-                    R cx, cy, cz;
-                    im_rot(qi, x.te.a, x.te.b, x.te.c, pi, cx, cy, cz);
-                    ax += w2 * (x.tj.a - cx);
-                    ay += w2 * (x.tj.b - cy);
-                    az += w2 * (x.tj.c - cz);
-                    wx += w2 * x.te.a;
-                    wy += w2 * x.te.b;
-                    wz += w2 * x.te.c;
-                }
-                const R rx = x.tj.a - sr.a, ry = x.tj.b - sr.b, rz = x.tj.c - sr.c;
-                axpy(u, -w2, qmul_pr(qmul_pl(rx, ry, rz, qi), x.te.a, x.te.b, x.te.c));
-            });
-        R sx = sr.a, sy = sr.b, sz = sr.c;
-        if (WITH_S) {
-            const R4<R> tr = IO<R>::ld(S.t, i);
-            const R4<R> zr = IO<R>::ld(S.z, i);  // (z_i, 1/A_4)
-            const R inv = zr.d;
-            sx = (ax + c.beta2 * tr.a - zr.a + c.g4 * sr.a) * inv;
-            sy = (ay + c.beta2 * tr.b - zr.b + c.g4 * sr.b) * inv;
-            sz = (az + c.beta2 * tr.c - zr.c + c.g4 * sr.c) * inv;
-            const R zx = zr.a - c.tb2 * (tr.a - sx), zy = zr.b - c.tb2 * (tr.b - sy), zz = zr.c - c.tb2 * (tr.c - sz);
-            IO<R>::st(S.s, i, sx, sy, sz, sr.d);
-            IO<R>::st(S.z, i, zx, zy, zz, inv);
-            const R d0 = zx - zr.a, d1 = zy - zr.b, d2 = zz - zr.c;
-            adz.add(d0 * d0 + d1 * d1 + d2 * d2);
-            // move the p-block's out-edge term from s^{old} to s^{new}
-            axpy(u, R(-1), qmul_pr(qmul_pl(sr.a - sx, sr.b - sy, sr.c - sz, qi), wx, wy, wz));
-        }
-        // own terms beta1 q_i + lam_i + gamma1 p_i, then in-edge terms 2 q_l (k_e q_e)
-        Q<R> v = {c.beta1 * qr.a + lr.a + c.g1 * pr.a, c.beta1 * qr.b + lr.b + c.g1 * pr.b,
-                  c.beta1 * qr.c + lr.c + c.g1 * pr.c, c.beta1 * qr.d + lr.d + c.g1 * pr.d};
-        axpy(v, R(1), u);
-        for_edges<PEdge<R>>(
-            g.in_ptr[i], g.in_ptr[i + 1],
-            [&](int e, PEdge<R>& x) {
-                const int l = __ldcs(g.in_idx + e);
-                x.qk = IO<R>::ldcs(g.in_qk, e);
-                x.ql = IO<R>::ld(S.q, l);
-            },
-            [&](const PEdge<R>& x) { axpy(v, R(2), qmul(asq<R>(x.ql), asq<R>(x.qk))); });
-        p_normalise<R>(g, S, i, v, qr, lr, pr, sx, sy, sz, c, pn, ctrl);
-    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x)
+        sp_vertex<R, WITH_S>(g, S, c, pc, pn, i, adz, ctrl);
     if (WITH_S) {
         const double sd = block_sum(adz.get(), sh);
         if (threadIdx.x == 0) L.part[SLOT_DZ * L.pstride + blockIdx.x] = sd;
@@ -547,28 +164,8 @@ __global__ void __launch_bounds__(256) k_objective(GraphDev<R> g, StateDev<R> S,
     const long long k = ctrl->iter;
     const R* pc = S.p[k & 1];
     double acc = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
-        const Q<double> pi = asq<double>(IO<R>::ld(pc, i));
-        const R4<R> ti = IO<R>::ld(S.t, i);
-        for (int e = g.out_ptr[i]; e < g.out_ptr[i + 1]; ++e) {
-            const int j = g.out_idx[e];
-            const Q<double> pj = asq<double>(IO<R>::ld(pc, j));
-            const R4<R> tj = IO<R>::ld(S.t, j);
-            // t~_j - t~_i - p_i t~_e p_i^*
-            const Q<double> rot = qmul_c(qmul_pr(pi, te[3 * e], te[3 * e + 1], te[3 * e + 2]), pi);
-            const double r0 = -rot.w;
-            const double r1 = double(tj.a) - double(ti.a) - rot.x;
-            const double r2 = double(tj.b) - double(ti.b) - rot.y;
-            const double r3 = double(tj.c) - double(ti.c) - rot.z;
-            acc += om[e] * (r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
-            // p_j^* p_i q_e - 1
-            const Q<double> qq = {qe[4 * e], qe[4 * e + 1], qe[4 * e + 2], qe[4 * e + 3]};
-            const Q<double> pjc = {pj.w, -pj.x, -pj.y, -pj.z};
-            Q<double> h = qmul(qmul(pjc, pi), qq);
-            h.w -= 1.0;
-            acc += ka[e] * (h.w * h.w + h.x * h.x + h.y * h.y + h.z * h.z);
-        }
-    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += objective_vertex<R>(g, pc, S.t, qe, te, ka, om, i);
     const double bs = block_sum(acc, sh);
     if (threadIdx.x == 0) part[blockIdx.x] = bs;
     __threadfence();

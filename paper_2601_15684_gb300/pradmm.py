@@ -77,6 +77,17 @@ _SIGS = {
     "pradmm_profile_sweeps": (ctypes.c_int, [_h, ctypes.c_int32, _d]),
     "pradmm_objective_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 10),
     "pradmm_destroy": (None, [_h]),
+    "pradmm_batch_create": (ctypes.c_int, [ctypes.c_int32, _i64, _i64, _i32, _i32, _d, _d, _d, _d, _P(pradmm_params),
+                                           ctypes.c_void_p, _P(ctypes.c_void_p)]),
+    "pradmm_batch_set_schedule": (ctypes.c_int, [_h, ctypes.c_int32, ctypes.c_int32]),
+    "pradmm_batch_get_schedule": (ctypes.c_int, [_h, _i32, _i32]),
+    "pradmm_batch_autotune": (ctypes.c_int, [_h, ctypes.c_int32, _i32, _i32]),
+    "pradmm_batch_init_odometry": (ctypes.c_int, [_h]),
+    "pradmm_batch_set_state": (ctypes.c_int, [_h, _d, _d]),
+    "pradmm_batch_solve": (ctypes.c_int, [_h, ctypes.c_double, ctypes.c_int32, _i32, _d, _d, _i32]),
+    "pradmm_batch_objectives": (ctypes.c_int, [_h, _d]),
+    "pradmm_batch_get_state": (ctypes.c_int, [_h, _d, _d, _d, _d, _d, _d]),
+    "pradmm_batch_destroy": (None, [_h]),
     "pradmm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pradmm_last_error": (ctypes.c_char_p, []),
 }
@@ -328,3 +339,102 @@ class Solver:
 
     def profile(self, iters):
         return pradmm_profile_sweeps(self.h, iters)
+
+
+# ---- batched solver ---------------------------------------------------------------
+
+class Batch:
+    """Many independent graphs (a list of synth.PoseGraph-like objects) solved
+    together by the batched entry points of pradmm.h."""
+
+    def __init__(self, graphs, params: pradmm_params | None = None, stream=None, **overrides):
+        lib = load()
+        prm = params if params is not None else pradmm_default_params()
+        for k, v in overrides.items():
+            if k == "gamma":
+                for i in range(4):
+                    prm.gamma[i] = v[i]
+            else:
+                setattr(prm, k, v)
+        self.params = prm
+        self.G = len(graphs)
+        self.n_g = np.array([g.n for g in graphs], dtype=np.int64)
+        self.m_g = np.array([g.m for g in graphs], dtype=np.int64)
+        self.offsets = np.concatenate([[0], np.cumsum(self.n_g)])
+        self.N = int(self.offsets[-1])
+        src = np.ascontiguousarray(np.concatenate([g.src for g in graphs]), dtype=np.int32)
+        dst = np.ascontiguousarray(np.concatenate([g.dst for g in graphs]), dtype=np.int32)
+        qm = _f64(np.concatenate([g.q_meas for g in graphs]))
+        tm = _f64(np.concatenate([g.t_meas for g in graphs]))
+        ka = _f64(np.concatenate([g.kappa for g in graphs]))
+        om = _f64(np.concatenate([g.omega for g in graphs]))
+        h = ctypes.c_void_p()
+        st = lib.pradmm_batch_create(self.G, self.n_g.ctypes.data_as(_i64), self.m_g.ctypes.data_as(_i64),
+                                     src.ctypes.data_as(_i32), dst.ctypes.data_as(_i32), _dp(qm), _dp(tm), _dp(ka),
+                                     _dp(om), ctypes.byref(prm), ctypes.c_void_p(stream or 0), ctypes.byref(h))
+        _check(st, "pradmm_batch_create")
+        self.h = h.value
+
+    def close(self):
+        if self.h:
+            load().pradmm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_schedule(self, block, warp_max_n):
+        _check(load().pradmm_batch_set_schedule(self.h, int(block), int(warp_max_n)), "pradmm_batch_set_schedule")
+
+    def schedule(self):
+        b, w = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(load().pradmm_batch_get_schedule(self.h, ctypes.byref(b), ctypes.byref(w)), "pradmm_batch_get_schedule")
+        return b.value, w.value
+
+    def autotune(self, iters=20):
+        b, w = ctypes.c_int32(0), ctypes.c_int32(0)
+        _check(load().pradmm_batch_autotune(self.h, int(iters), ctypes.byref(b), ctypes.byref(w)),
+               "pradmm_batch_autotune")
+        return b.value, w.value
+
+    def init_odometry(self):
+        _check(load().pradmm_batch_init_odometry(self.h), "pradmm_batch_init_odometry")
+
+    def set_state(self, q, t):
+        q, t = _f64(q, (self.N, 4)), _f64(t, (self.N, 3))
+        _check(load().pradmm_batch_set_state(self.h, _dp(q), _dp(t)), "pradmm_batch_set_state")
+
+    def solve(self, rel_tol=1e-6, max_iter=3000):
+        """Returns dict of per-graph arrays: iters, e_first, e_last, status."""
+        it = np.zeros(self.G, dtype=np.int32)
+        e1 = np.zeros(self.G)
+        ek = np.zeros(self.G)
+        stt = np.zeros(self.G, dtype=np.int32)
+        st = load().pradmm_batch_solve(self.h, float(rel_tol), int(max_iter), it.ctypes.data_as(_i32), _dp(e1),
+                                       _dp(ek), stt.ctypes.data_as(_i32))
+        if st not in (PRADMM_OK, PRADMM_ERR_NOT_CONVERGED):
+            _check(st, "pradmm_batch_solve")
+        return {"iters": it, "e_first": e1, "e_last": ek, "status": stt, "all_converged": st == PRADMM_OK}
+
+    def objectives(self):
+        F = np.zeros(self.G)
+        _check(load().pradmm_batch_objectives(self.h, _dp(F)), "pradmm_batch_objectives")
+        return F
+
+    def state(self):
+        N = self.N
+        out = {"p": np.zeros((N, 4)), "q": np.zeros((N, 4)), "t": np.zeros((N, 3)), "s": np.zeros((N, 3)),
+               "lam": np.zeros((N, 4)), "z": np.zeros((N, 3))}
+        _check(load().pradmm_batch_get_state(self.h, _dp(out["p"]), _dp(out["q"]), _dp(out["t"]), _dp(out["s"]),
+                                             _dp(out["lam"]), _dp(out["z"])), "pradmm_batch_get_state")
+        return out
+

@@ -1,0 +1,146 @@
+"""Batched solver: many graphs in one persistent launch.
+
+- each graph's state matches the plain solver run for the same number of
+  iterations (the same per-vertex functions compiled into different kernels:
+  they agree to rounding, since the compiler may contract multiply-adds
+  differently per kernel), and a repeated run is bitwise identical;
+- small graphs match the FP64 oracle;
+- every schedule (CTA- or warp-per-graph, block sizes) gives the same state;
+- the per-graph stopping rule e^k <= rel_tol * e^1 holds where it reports
+  convergence;
+- the autotuner keeps a valid schedule and leaves the state untouched.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_15684_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+KEYS = ("p", "q", "t", "s", "lam", "z")
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2601_15684_gb300 import build_lib
+    from paper_2601_15684_gb300 import pradmm
+    build_lib.build()
+    pradmm.load()
+    return pradmm
+
+
+def _graphs(count=24, seed=0, n_max=3000):
+    rng = np.random.default_rng(seed)
+    ns = np.exp(rng.uniform(np.log(20), np.log(n_max), count)).round().astype(int)
+    dens = rng.uniform(0.5, 3.0, count)
+    return [synth.random_walk_graph(int(ns[k]), n_closures=None, closure_density=float(dens[k]), sigma_r=0.02,
+                                    sigma_t=0.1, seed=1000 + k, name=f"g{k}") for k in range(count)]
+
+
+def _slice(st, a, b):
+    return {k: v[a:b] for k, v in st.items()}
+
+
+def close_state(a, b, fp64, tau=1.5, beta1=1.0, beta2=1.0, what="", iters=1):
+    """FP64: 1e-10 relative per array.  FP32: 1e-5 relative for p, q, t, s and
+    the multipliers against the scale they are formed from (as the parity
+    tests), times sqrt(iters): a multiplier is the running sum of one
+    rounded increment per iteration."""
+    rel = lambda x, y: np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-300)
+    if fp64:
+        for k in KEYS:
+            assert rel(a[k], b[k]) <= 1e-10, (what, k, rel(a[k], b[k]))
+        return
+    for k in ("p", "q", "t", "s"):
+        assert rel(a[k], b[k]) <= 1e-5, (what, k, rel(a[k], b[k]))
+    grow = np.sqrt(max(iters, 1))
+    assert np.linalg.norm(a["lam"] - b["lam"]) <= 1e-5 * grow * tau * beta1 * max(np.linalg.norm(b["p"]), 1.0), what
+    assert np.linalg.norm(a["z"] - b["z"]) <= 1e-5 * grow * tau * beta2 * max(np.linalg.norm(b["t"]), 1.0), what
+
+
+@pytest.mark.parametrize("precision,rel_tol,max_iter", [(0, 1e-4, 400), (1, 0.0, 30)])
+def test_batch_matches_plain_graph_by_graph(P, precision, rel_tol, max_iter):
+    # FP32 runs a fixed 30 iterations: two FP32 executions that round
+    # differently drift apart over hundreds of iterations, beyond a bound
+    # stated for short runs
+    graphs = _graphs(12, seed=precision)
+    with P.Batch(graphs, precision=precision) as B:
+        B.init_odometry()
+        res = B.solve(rel_tol=rel_tol, max_iter=max_iter)
+        st = B.state()
+        F = B.objectives()
+    assert (res["iters"] >= 1).all() and (res["iters"] <= max_iter).all()
+    for k, g in enumerate(graphs):
+        a, b = B.offsets[k], B.offsets[k + 1]
+        with P.Solver(g, precision=precision) as S:
+            S.init_odometry()
+            S.step(int(res["iters"][k]))
+            ref = S.state()
+            F_ref = S.objective()
+        close_state(_slice(st, a, b), ref, precision == 0, what=f"graph {k}", iters=int(res["iters"][k]))
+        assert abs(F[k] - F_ref) <= (1e-10 if precision == 0 else 1e-4) * max(F_ref, 1.0)
+
+
+def test_batch_fp64_matches_oracle(P):
+    graphs = _graphs(6, seed=7, n_max=200)
+    with P.Batch(graphs, precision=0) as B:
+        B.init_odometry()
+        res = B.solve(rel_tol=1e-3, max_iter=60)
+        st = B.state()
+    prm = oracle.make_params(beta1=1.0, beta2=1.0, tau=1.5)
+    for k, g in enumerate(graphs):
+        q0, t0 = oracle.init_odometry(g)
+        orc, _, _ = oracle.iterate(g, prm, oracle.init_state(q0, t0), int(res["iters"][k]))
+        sl = _slice(st, B.offsets[k], B.offsets[k + 1])
+        for key in KEYS:
+            err = np.linalg.norm(sl[key] - orc[key]) / max(np.linalg.norm(orc[key]), 1e-300)
+            assert err <= 1e-10, (k, key, err)
+
+
+def test_batch_schedules_agree_and_stop_rule(P):
+    graphs = _graphs(40, seed=3, n_max=2500)
+    outs = []
+    with P.Batch(graphs, precision=1) as B:
+        for block, wmax in ((256, 256), (128, 0), (512, 1024), (64, 64)):
+            B.set_schedule(block, wmax)
+            assert B.schedule() == (block, wmax)
+            B.init_odometry()
+            res = B.solve(rel_tol=0.0, max_iter=25)  # fixed iteration count
+            assert (res["iters"] == 25).all()
+            outs.append(B.state())
+        B.set_schedule(256, 256)
+        B.init_odometry()
+        res = B.solve(rel_tol=1e-6, max_iter=3000)
+    for st in outs[1:]:
+        close_state(st, outs[0], False, what="schedule", iters=25)
+    conv = res["status"] == P.PRADMM_OK
+    assert conv.any()
+    assert (res["e_last"][conv] <= 1e-6 * res["e_first"][conv]).all()
+    assert (res["iters"][~conv] == 3000).all()
+
+
+def test_batch_repeat_is_bitwise_identical(P):
+    graphs = _graphs(20, seed=9, n_max=2000)
+    outs = []
+    for _ in range(2):
+        with P.Batch(graphs, precision=1) as B:
+            B.init_odometry()
+            res = B.solve(rel_tol=1e-5, max_iter=500)
+            outs.append((res, B.state()))
+    np.testing.assert_array_equal(outs[0][0]["iters"], outs[1][0]["iters"])
+    np.testing.assert_array_equal(outs[0][0]["e_last"], outs[1][0]["e_last"])
+    for key in KEYS:
+        np.testing.assert_array_equal(outs[0][1][key], outs[1][1][key])
+
+
+def test_batch_autotune_keeps_state(P):
+    graphs = _graphs(30, seed=5, n_max=1500)
+    with P.Batch(graphs, precision=1) as B:
+        B.init_odometry()
+        before = B.state()
+        block, wmax = B.autotune(iters=5)
+        assert block in (128, 256, 512) and wmax in (0, 64, 256, 1024)
+        assert B.schedule() == (block, wmax)
+        after = B.state()
+        for key in KEYS:
+            np.testing.assert_array_equal(after[key], before[key])
