@@ -64,6 +64,9 @@ def lib():
             L.orc_lagrangian.argtypes = [i64, i64, i32, i32, d, d, d, d, P(Params), d, d, d, d, d, d]
             L.orc_init_odometry.restype = ctypes.c_int
             L.orc_init_odometry.argtypes = [i64, i64, i32, i32, d, d, d, d]
+            L.orc_adjoint.restype = ctypes.c_int
+            L.orc_adjoint.argtypes = [i64, i64, i32, i32, d, d, d, d, P(Params), i64, d, d, d, d, d, d, d, d,
+                                      d, d, d, d, d, d, d]
             L.orc_qmul.restype = None
             L.orc_qmul.argtypes = [d, d, d]
             L.orc_qrotate.restype = None
@@ -150,6 +153,34 @@ def solve(g, params: Params, state: dict, max_iter: int, tol: float):
     k = lib().orc_solve(*a, ctypes.byref(params), int(max_iter), float(tol), _d(st["p"]), _d(st["q"]),
                         _d(st["t"]), _d(st["s"]), _d(st["lam"]), _d(st["z"]), _d(e), _d(trace))
     return st, int(k), float(e[0]), trace[:k].copy()
+
+
+def adjoint(g, params: Params, state: dict, iters: int, p_bar, t_bar):
+    """Reverse-mode gradient of a loss L(p^K, t^K) through `iters` iterations
+    of Algorithm 1 started at `state` (held fixed), given p_bar = dL/dp^K
+    (n x 4) and t_bar = dL/dt^K (n x 3).  Returns a dict with the gradients
+    with respect to the measurements ("q_meas" m x 4, "t_meas" m x 3,
+    "kappa" m, "omega" m), the adjoint of the initial state ("x0": dict of
+    p, q, t, s, lam, z) and the final "p", "t"."""
+    n, m = g.n, g.m
+    st = copy_state(state)
+    keep, a = _graph_args(g)
+    pb, tb = _f64(p_bar), _f64(t_bar)
+    out = {"p": np.zeros((n, 4)), "t": np.zeros((n, 3)), "q_meas": np.zeros((m, 4)), "t_meas": np.zeros((m, 3)),
+           "kappa": np.zeros(m), "omega": np.zeros(m)}
+    x0 = np.zeros(21 * n)
+    rc = lib().orc_adjoint(*a, ctypes.byref(params), int(iters), _d(st["p"]), _d(st["q"]), _d(st["t"]),
+                           _d(st["s"]), _d(st["lam"]), _d(st["z"]), _d(pb), _d(tb), _d(out["p"]), _d(out["t"]),
+                           _d(out["q_meas"]), _d(out["t_meas"]), _d(out["kappa"]), _d(out["omega"]), _d(x0))
+    if rc != 0:
+        raise MemoryError("oracle adjoint")
+    sizes = (("p", 4), ("q", 4), ("t", 3), ("s", 3), ("lam", 4), ("z", 3))
+    o, x0d = 0, {}
+    for key, w in sizes:
+        x0d[key] = x0[o:o + w * n].reshape(n, w)
+        o += w * n
+    out["x0"] = x0d
+    return out
 
 
 def objective(g, q, t) -> float:

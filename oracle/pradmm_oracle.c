@@ -17,6 +17,8 @@
  *   - one iteration (3a)-(3f) ............. Section 3.2 Eq. (3), Algorithm 1,
  *                                           closed forms of Appendix B
  *   - residual e^{k+1} and stopping ....... Appendix E.1
+ *   - reverse mode of the unrolled ........ derivative of Eq. (3a)-(3f) with
+ *     iteration (adjoint)                   respect to the measurements and x^0
  *
  * Readings of passages that are garbled or silent (the same readings the CUDA
  * path follows):
@@ -31,6 +33,9 @@
  *   R9  Sigma_1 = omega_e I_4 and Sigma_2 = kappa_e I_4 per edge.
  *   R11 if |u_i| == 0 the p-block keeps p_i^k.
  *   R13 Jacobi inside a block: every vertex reads pre-block values.
+ *   R21 the adjoint differentiates the unrolled map x^0 -> x^K with x^0 held
+ *       fixed; q_e is a point of R^4 (no renormalisation inside the map);
+ *       where |u_i| == 0 (R11) the adjoint of p_i^{k+1} passes to p_i^k.
  *
  * Quaternions are scalar first, [q0, q1, q2, q3] (Appendix A.2).
  */
@@ -444,4 +449,385 @@ int64_t orc_solve(int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
     }
     if (e_out) *e_out = res[0];
     return k;
+}
+
+/* ---- reverse mode of one iteration ------------------------------------------
+ * Vector-Jacobian product of the map x^k -> x^{k+1} of orc_iterate (Eq. (3a)-
+ * (3f) with the Appendix B closed forms), written by hand step by step in
+ * reverse order.  For a quaternion product V = a x b the adjoint of x is
+ * a^* V_bar b^* (Lemma MW: left/right multiplication matrices are orthogonal
+ * up to scale, M(a)^T = M(a^*), W(b)^T = W(b^*)); a conjugate x^* = D x
+ * contributes the conjugate of that adjoint; the normalisation p = u/|u| has
+ * adjoint u_bar = (I - p p^T) p_bar / |u|.
+ *
+ * in:  x^k (p, q, t, s, lam, z) and the adjoints of x^{k+1} (pb1 .. zb1)
+ * out: adjoints of x^k (pb .. zb, overwritten) and of the measurements,
+ *      ACCUMULATED: qeb (m x 4), teb (m x 3), kab (m), omb (m).
+ * Returns 0, or -1 on allocation failure.
+ */
+static void qadd(double* a, const double* b, double s) {
+    for (int k = 0; k < 4; ++k) a[k] += s * b[k];
+}
+
+int orc_iterate_adjoint(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const double* qe,
+                        const double* te, const double* kappa, const double* omega, const orc_params* prm,
+                        const double* p, const double* q, const double* t, const double* s, const double* lam,
+                        const double* z, const double* pb1, const double* qb1, const double* tb1,
+                        const double* sb1, const double* lb1, const double* zb1, double* pb, double* qb,
+                        double* tb, double* sb, double* lb, double* zb, double* qeb, double* teb, double* kab,
+                        double* omb) {
+    const double b1 = prm->beta1, b2 = prm->beta2, tau = prm->tau;
+    const double g1 = prm->gamma[0], g2 = prm->gamma[1], g3 = prm->gamma[2], g4 = prm->gamma[3];
+    /* forward intermediates, recomputed exactly as orc_iterate does */
+    double* P = (double*)malloc(sizeof(double) * (size_t)(4 * n + 1));
+    double* Qn = (double*)malloc(sizeof(double) * (size_t)(4 * n + 1));
+    double* Tn = (double*)malloc(sizeof(double) * (size_t)(3 * n + 1));
+    double* Sn = (double*)malloc(sizeof(double) * (size_t)(3 * n + 1));
+    double* L = (double*)malloc(sizeof(double) * (size_t)(4 * n + 1));
+    double* Z = (double*)malloc(sizeof(double) * (size_t)(3 * n + 1));
+    double* u = (double*)calloc((size_t)(4 * n + 1), sizeof(double));
+    double* nu = (double*)calloc((size_t)(n + 1), sizeof(double));
+    double* a2 = (double*)calloc((size_t)(n + 1), sizeof(double));
+    double* a3 = (double*)calloc((size_t)(n + 1), sizeof(double));
+    double* a4 = (double*)calloc((size_t)(n + 1), sizeof(double));
+    double* c = (double*)calloc((size_t)(3 * m + 1), sizeof(double));
+    /* adjoint accumulators */
+    double* pba = (double*)calloc((size_t)(4 * n + 1), sizeof(double)); /* of p^{k+1} */
+    double* qba = (double*)calloc((size_t)(4 * n + 1), sizeof(double)); /* of q^{k+1} */
+    double* tba = (double*)calloc((size_t)(3 * n + 1), sizeof(double)); /* of t^{k+1} */
+    double* sba = (double*)calloc((size_t)(3 * n + 1), sizeof(double)); /* of s^{k+1} */
+    double* cb = (double*)calloc((size_t)(3 * m + 1), sizeof(double));
+    double* gs = (double*)calloc((size_t)(3 * n + 1), sizeof(double));
+    double* gt = (double*)calloc((size_t)(3 * n + 1), sizeof(double));
+    double* gq = (double*)calloc((size_t)(4 * n + 1), sizeof(double));
+    double* ub = (double*)calloc((size_t)(4 * n + 1), sizeof(double));
+    int rc = 0;
+    if (!P || !Qn || !Tn || !Sn || !L || !Z || !u || !nu || !a2 || !a3 || !a4 || !c || !pba || !qba || !tba ||
+        !sba || !cb || !gs || !gt || !gq || !ub) {
+        rc = -1;
+        goto out;
+    }
+    memcpy(P, p, sizeof(double) * (size_t)(4 * n));
+    memcpy(Qn, q, sizeof(double) * (size_t)(4 * n));
+    memcpy(Tn, t, sizeof(double) * (size_t)(3 * n));
+    memcpy(Sn, s, sizeof(double) * (size_t)(3 * n));
+    memcpy(L, lam, sizeof(double) * (size_t)(4 * n));
+    memcpy(Z, z, sizeof(double) * (size_t)(3 * n));
+    if (orc_iterate(n, m, src, dst, qe, te, kappa, omega, prm, P, Qn, Tn, Sn, L, Z, NULL) < 0) {
+        rc = -1;
+        goto out;
+    }
+    /* u and |u| of the p-block (same order of operations as orc_iterate) */
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < 4; ++k) u[4 * i + k] = b1 * q[4 * i + k] + lam[4 * i + k] + g1 * p[4 * i + k];
+    for (int64_t e = 0; e < m; ++e) {
+        int64_t i = src[e], j = dst[e];
+        double r[4], rc_[4], tp[4], a[4], v[4];
+        r[0] = 0.0;
+        for (int k = 0; k < 3; ++k) r[k + 1] = t[3 * j + k] - s[3 * i + k];
+        qconj(r, rc_);
+        qpure(&te[3 * e], tp);
+        qmul(rc_, &q[4 * i], a);
+        qmul(a, tp, v);
+        qadd(&u[4 * i], v, 2.0 * (omega ? omega[e] : 1.0));
+    }
+    for (int64_t e = 0; e < m; ++e) {
+        double v[4];
+        qmul(&q[4 * src[e]], &qe[4 * e], v);
+        qadd(&u[4 * dst[e]], v, 2.0 * (kappa ? kappa[e] : 1.0));
+    }
+    for (int64_t i = 0; i < n; ++i) nu[i] = sqrt(dot4(&u[4 * i], &u[4 * i]));
+    for (int64_t i = 0; i < n; ++i) {
+        a2[i] = b1 + g2;
+        a3[i] = b2 + g3;
+        a4[i] = b2 + g4;
+    }
+    for (int64_t e = 0; e < m; ++e) {
+        int64_t i = src[e], j = dst[e];
+        double w = omega ? omega[e] : 1.0, kk = kappa ? kappa[e] : 1.0, tp[4];
+        qpure(&te[3 * e], tp);
+        a2[i] += 2.0 * (w * dot4(&P[4 * i], &P[4 * i]) * dot4(tp, tp) + kk * dot4(&P[4 * j], &P[4 * j]) * dot4(&qe[4 * e], &qe[4 * e]));
+        a3[j] += 2.0 * w;
+        a4[i] += 2.0 * w;
+        double a[4], pc[4], v[4];
+        qmul(&Qn[4 * i], tp, a);
+        qconj(&P[4 * i], pc);
+        qmul(a, pc, v);
+        c[3 * e] = v[1]; c[3 * e + 1] = v[2]; c[3 * e + 2] = v[3];
+    }
+    memset(pb, 0, sizeof(double) * (size_t)(4 * n));
+    memset(qb, 0, sizeof(double) * (size_t)(4 * n));
+    memset(tb, 0, sizeof(double) * (size_t)(3 * n));
+    memset(sb, 0, sizeof(double) * (size_t)(3 * n));
+    memset(lb, 0, sizeof(double) * (size_t)(4 * n));
+    memset(zb, 0, sizeof(double) * (size_t)(3 * n));
+    /* (3e), (3f) */
+    for (int64_t i = 0; i < n; ++i) {
+        for (int k = 0; k < 4; ++k) {
+            lb[4 * i + k] += lb1[4 * i + k];
+            pba[4 * i + k] = pb1[4 * i + k] - tau * b1 * lb1[4 * i + k];
+            qba[4 * i + k] = qb1[4 * i + k] + tau * b1 * lb1[4 * i + k];
+        }
+        for (int k = 0; k < 3; ++k) {
+            zb[3 * i + k] += zb1[3 * i + k];
+            tba[3 * i + k] = tb1[3 * i + k] - tau * b2 * zb1[3 * i + k];
+            sba[3 * i + k] = sb1[3 * i + k] + tau * b2 * zb1[3 * i + k];
+        }
+    }
+    /* (3d) s = sn / a4 */
+    for (int64_t i = 0; i < n; ++i) {
+        double a4b = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            gs[3 * i + k] = sba[3 * i + k] / a4[i];
+            a4b -= gs[3 * i + k] * Sn[3 * i + k];
+            tba[3 * i + k] += b2 * gs[3 * i + k];
+            zb[3 * i + k] -= gs[3 * i + k];
+            sb[3 * i + k] += g4 * gs[3 * i + k];
+        }
+        a4[i] = a4b; /* reuse: adjoint of A_4 */
+    }
+    for (int64_t e = 0; e < m; ++e) {
+        int64_t i = src[e], j = dst[e];
+        double w = omega ? omega[e] : 1.0, dot = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            tba[3 * j + k] += 2.0 * w * gs[3 * i + k];
+            cb[3 * e + k] -= 2.0 * w * gs[3 * i + k];
+            dot += (Tn[3 * j + k] - c[3 * e + k]) * gs[3 * i + k];
+        }
+        omb[e] += 2.0 * dot + 2.0 * a4[i];
+    }
+    /* (3c) t = tn / a3 */
+    for (int64_t i = 0; i < n; ++i) {
+        double a3b = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            gt[3 * i + k] = tba[3 * i + k] / a3[i];
+            a3b -= gt[3 * i + k] * Tn[3 * i + k];
+            sb[3 * i + k] += b2 * gt[3 * i + k];
+            zb[3 * i + k] += gt[3 * i + k];
+            tb[3 * i + k] += g3 * gt[3 * i + k];
+        }
+        a3[i] = a3b;
+    }
+    for (int64_t e = 0; e < m; ++e) {
+        int64_t l = src[e], i = dst[e];
+        double w = omega ? omega[e] : 1.0, dot = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            sb[3 * l + k] += 2.0 * w * gt[3 * i + k];
+            cb[3 * e + k] += 2.0 * w * gt[3 * i + k];
+            dot += (s[3 * l + k] + c[3 * e + k]) * gt[3 * i + k];
+        }
+        omb[e] += 2.0 * dot + 2.0 * a3[i];
+    }
+    /* c_e = Im(q'_i t~_e p'_i^*) */
+    for (int64_t e = 0; e < m; ++e) {
+        int64_t i = src[e];
+        double hb[4] = {0.0, cb[3 * e], cb[3 * e + 1], cb[3 * e + 2]}, tp[4], tc[4], a[4], v[4], qc[4];
+        qpure(&te[3 * e], tp);
+        qconj(tp, tc);
+        /* q' adjoint: hb (t~ p'^*)^* = hb p' t~^* */
+        qmul(hb, &P[4 * i], a);
+        qmul(a, tc, v);
+        qadd(&qba[4 * i], v, 1.0);
+        /* p' adjoint: hb^* (q' t~) */
+        double hc[4];
+        qconj(hb, hc);
+        qmul(&Qn[4 * i], tp, a);
+        qmul(hc, a, v);
+        qadd(&pba[4 * i], v, 1.0);
+        /* t~ adjoint: q'^* hb p' */
+        qconj(&Qn[4 * i], qc);
+        qmul(qc, hb, a);
+        qmul(a, &P[4 * i], v);
+        for (int k = 0; k < 3; ++k) teb[3 * e + k] += v[k + 1];
+    }
+    /* (3b) q = qn / a2 */
+    for (int64_t i = 0; i < n; ++i) {
+        double a2b = 0.0;
+        for (int k = 0; k < 4; ++k) {
+            gq[4 * i + k] = qba[4 * i + k] / a2[i];
+            a2b -= gq[4 * i + k] * Qn[4 * i + k];
+            pba[4 * i + k] += b1 * gq[4 * i + k];
+            lb[4 * i + k] -= gq[4 * i + k];
+            qb[4 * i + k] += g2 * gq[4 * i + k];
+        }
+        a2[i] = a2b;
+    }
+    for (int64_t e = 0; e < m; ++e) {
+        int64_t i = src[e], j = dst[e];
+        double w = omega ? omega[e] : 1.0, kk = kappa ? kappa[e] : 1.0;
+        double r[4], tp[4], tc[4], a[4], v[4], g[4];
+        r[0] = 0.0;
+        for (int k = 0; k < 3; ++k) r[k + 1] = t[3 * j + k] - s[3 * i + k];
+        qpure(&te[3 * e], tp);
+        qconj(tp, tc);
+        memcpy(g, &gq[4 * i], sizeof(g));
+        /* term 2 w r p'_i t~^* */
+        qmul(g, tp, a); /* g t~ */
+        double pc[4];
+        qconj(&P[4 * i], pc);
+        qmul(a, pc, v); /* g t~ p'^*  = adjoint of r (times 2w) */
+        for (int k = 0; k < 3; ++k) {
+            tb[3 * j + k] += 2.0 * w * v[k + 1];
+            sb[3 * i + k] -= 2.0 * w * v[k + 1];
+        }
+        double rcj[4];
+        qconj(r, rcj);
+        qmul(rcj, g, a); /* r^* g */
+        qmul(a, tp, v);  /* r^* g t~ = (r)^* g (t~^*)^* */
+        qadd(&pba[4 * i], v, 2.0 * w);
+        double gc[4], rp[4];
+        qconj(g, gc);
+        qmul(r, &P[4 * i], rp);
+        qmul(gc, rp, v); /* g^* (r p') */
+        for (int k = 0; k < 3; ++k) teb[3 * e + k] += 2.0 * w * v[k + 1];
+        double tv[4];
+        qmul(rp, tc, tv);
+        omb[e] += 2.0 * dot4(g, tv);
+        /* term 2 k p'_j q_e^* */
+        qmul(g, &qe[4 * e], v); /* g (q_e^*)^* */
+        qadd(&pba[4 * j], v, 2.0 * kk);
+        qmul(gc, &P[4 * j], v); /* g^* p'_j */
+        qadd(&qeb[4 * e], v, 2.0 * kk);
+        double qc[4];
+        qconj(&qe[4 * e], qc);
+        qmul(&P[4 * j], qc, v);
+        kab[e] += 2.0 * dot4(g, v);
+        /* A_2 = ... + 2 (w |p'_i|^2 |t_e|^2 + k |p'_j|^2 |q_e|^2) */
+        double pn2 = dot4(&P[4 * i], &P[4 * i]), pj2 = dot4(&P[4 * j], &P[4 * j]);
+        double tn2 = dot4(tp, tp), qn2 = dot4(&qe[4 * e], &qe[4 * e]);
+        omb[e] += 2.0 * pn2 * tn2 * a2[i];
+        kab[e] += 2.0 * pj2 * qn2 * a2[i];
+        for (int k = 0; k < 3; ++k) teb[3 * e + k] += 4.0 * w * pn2 * te[3 * e + k] * a2[i];
+        qadd(&qeb[4 * e], &qe[4 * e], 4.0 * kk * pj2 * a2[i]);
+        qadd(&pba[4 * i], &P[4 * i], 4.0 * w * tn2 * a2[i]);
+        qadd(&pba[4 * j], &P[4 * j], 4.0 * kk * qn2 * a2[i]);
+    }
+    /* (3a) p = u / |u|  (|u| = 0 keeps p^k: p' = p) */
+    for (int64_t i = 0; i < n; ++i) {
+        if (nu[i] > 0.0) {
+            double pp = dot4(&P[4 * i], &pba[4 * i]);
+            for (int k = 0; k < 4; ++k) ub[4 * i + k] = (pba[4 * i + k] - P[4 * i + k] * pp) / nu[i];
+        } else {
+            for (int k = 0; k < 4; ++k) pb[4 * i + k] += pba[4 * i + k];
+        }
+        for (int k = 0; k < 4; ++k) {
+            qb[4 * i + k] += b1 * ub[4 * i + k];
+            lb[4 * i + k] += ub[4 * i + k];
+            pb[4 * i + k] += g1 * ub[4 * i + k];
+        }
+    }
+    for (int64_t e = 0; e < m; ++e) {
+        int64_t i = src[e], j = dst[e];
+        double w = 2.0 * (omega ? omega[e] : 1.0);
+        double r[4], rcj[4], tp[4], tc[4], qt[4], a[4], v[4], g[4];
+        r[0] = 0.0;
+        for (int k = 0; k < 3; ++k) r[k + 1] = t[3 * j + k] - s[3 * i + k];
+        qconj(r, rcj);
+        qpure(&te[3 * e], tp);
+        qconj(tp, tc);
+        memcpy(g, &ub[4 * i], sizeof(g));
+        /* V = w r^* q_i t~ : adjoint of r^* is w g (q_i t~)^*, of r its conjugate */
+        qmul(&q[4 * i], tp, qt);
+        double qtc[4];
+        qconj(qt, qtc);
+        qmul(g, qtc, a);
+        for (int k = 0; k < 3; ++k) {
+            tb[3 * j + k] -= w * a[k + 1];
+            sb[3 * i + k] += w * a[k + 1];
+        }
+        /* q_i: (w r^*)^* g t~^* = w r g t~^* */
+        qmul(r, g, a);
+        qmul(a, tc, v);
+        qadd(&qb[4 * i], v, w);
+        /* t~: (w r^* q_i)^* g */
+        double rq[4], rqc[4];
+        qmul(rcj, &q[4 * i], rq);
+        qconj(rq, rqc);
+        qmul(rqc, g, v);
+        for (int k = 0; k < 3; ++k) teb[3 * e + k] += w * v[k + 1];
+        qmul(rq, tp, v);
+        omb[e] += 2.0 * dot4(g, v);
+    }
+    for (int64_t e = 0; e < m; ++e) {
+        int64_t l = src[e], i = dst[e];
+        double kk = 2.0 * (kappa ? kappa[e] : 1.0), g[4], qc[4], ql[4], v[4];
+        memcpy(g, &ub[4 * i], sizeof(g));
+        qconj(&qe[4 * e], qc);
+        qmul(g, qc, v); /* g q_e^* */
+        qadd(&qb[4 * l], v, kk);
+        qconj(&q[4 * l], ql);
+        qmul(ql, g, v); /* q_l^* g */
+        qadd(&qeb[4 * e], v, kk);
+        qmul(&q[4 * l], &qe[4 * e], v);
+        kab[e] += 2.0 * dot4(g, v);
+    }
+out:
+    free(P); free(Qn); free(Tn); free(Sn); free(L); free(Z); free(u); free(nu); free(a2); free(a3); free(a4);
+    free(c); free(pba); free(qba); free(tba); free(sba); free(cb); free(gs); free(gt); free(gq); free(ub);
+    return rc;
+}
+
+/* Gradient of a terminal loss through `iters` iterations of Algorithm 1 from
+ * a fixed x^0 (reverse mode: every state x^0 .. x^{iters} is kept, then
+ * orc_iterate_adjoint runs from the last iteration back to the first).
+ * pbK, tbK: dL/dp^K (n x 4) and dL/dt^K (n x 3); the loss depends on no
+ * other part of x^K.  Outputs dL/dq_e (m x 4), dL/dt_e (m x 3), dL/dkappa_e,
+ * dL/domega_e (each overwritten), x^K's p and t (nullable), and the adjoint
+ * of x^0 packed as (p, q, t, s, lam, z), 21 n values (nullable).
+ * Returns 0, or -1 on allocation failure. */
+int orc_adjoint(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const double* qe, const double* te,
+                const double* kappa, const double* omega, const orc_params* prm, int64_t iters, const double* p0,
+                const double* q0, const double* t0, const double* s0, const double* lam0, const double* z0,
+                const double* pbK, const double* tbK, double* pK, double* tK, double* qeb, double* teb,
+                double* kab, double* omb, double* x0b) {
+    const int64_t W = 21 * n; /* one state: p 4n, q 4n, t 3n, s 3n, lam 4n, z 3n */
+    const int64_t off[6] = {0, 4 * n, 8 * n, 11 * n, 14 * n, 18 * n};
+    double* tape = (double*)malloc(sizeof(double) * (size_t)(W * (iters + 1) + 1));
+    double* bar = (double*)calloc((size_t)(2 * W + 1), sizeof(double));
+    int rc = 0;
+    if (!tape || !bar) {
+        rc = -1;
+        goto out;
+    }
+    memcpy(tape + off[0], p0, sizeof(double) * (size_t)(4 * n));
+    memcpy(tape + off[1], q0, sizeof(double) * (size_t)(4 * n));
+    memcpy(tape + off[2], t0, sizeof(double) * (size_t)(3 * n));
+    memcpy(tape + off[3], s0, sizeof(double) * (size_t)(3 * n));
+    memcpy(tape + off[4], lam0, sizeof(double) * (size_t)(4 * n));
+    memcpy(tape + off[5], z0, sizeof(double) * (size_t)(3 * n));
+    for (int64_t k = 0; k < iters; ++k) {
+        double* x = tape + W * (k + 1);
+        memcpy(x, tape + W * k, sizeof(double) * (size_t)W);
+        if (orc_iterate(n, m, src, dst, qe, te, kappa, omega, prm, x + off[0], x + off[1], x + off[2], x + off[3],
+                        x + off[4], x + off[5], NULL) < 0) {
+            rc = -1;
+            goto out;
+        }
+    }
+    if (pK) memcpy(pK, tape + W * iters + off[0], sizeof(double) * (size_t)(4 * n));
+    if (tK) memcpy(tK, tape + W * iters + off[2], sizeof(double) * (size_t)(3 * n));
+    memset(qeb, 0, sizeof(double) * (size_t)(4 * m));
+    memset(teb, 0, sizeof(double) * (size_t)(3 * m));
+    memset(kab, 0, sizeof(double) * (size_t)m);
+    memset(omb, 0, sizeof(double) * (size_t)m);
+    /* bar[0 .. W) holds the adjoint of x^{k+1}, bar[W .. 2W) receives that of x^k */
+    memcpy(bar + off[0], pbK, sizeof(double) * (size_t)(4 * n));
+    memcpy(bar + off[2], tbK, sizeof(double) * (size_t)(3 * n));
+    for (int64_t k = iters - 1; k >= 0; --k) {
+        const double* x = tape + W * k;
+        double *a1 = bar, *a0 = bar + W;
+        if (orc_iterate_adjoint(n, m, src, dst, qe, te, kappa, omega, prm, x + off[0], x + off[1], x + off[2],
+                                x + off[3], x + off[4], x + off[5], a1 + off[0], a1 + off[1], a1 + off[2],
+                                a1 + off[3], a1 + off[4], a1 + off[5], a0 + off[0], a0 + off[1], a0 + off[2],
+                                a0 + off[3], a0 + off[4], a0 + off[5], qeb, teb, kab, omb) < 0) {
+            rc = -1;
+            goto out;
+        }
+        memcpy(a1, a0, sizeof(double) * (size_t)W);
+    }
+    if (x0b) memcpy(x0b, bar, sizeof(double) * (size_t)W);
+out:
+    free(tape);
+    free(bar);
+    return rc;
 }

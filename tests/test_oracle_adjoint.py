@@ -1,0 +1,174 @@
+"""Reverse mode of the oracle iteration, pinned by central finite differences.
+
+The oracle's adjoint (a hand-written vector-Jacobian product of every block
+of Eq. (3a)-(3f), run backwards through the unrolled iterations) must agree
+with FP64 central differences of the forward oracle itself, on measurement
+coordinates (q_e, t_e, kappa_e, omega_e) and on the initial state.  Central
+differences with h = 1e-6 are accurate to about 1e-9 relative here, so a
+dropped term, a wrong sign or a transposed product fails at once.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_15684_gb300 import synth
+
+H = 1e-6
+KEYS = ("p", "q", "t", "s", "lam", "z")
+
+
+def _qmul(a, b):
+    w1, x1, y1, z1 = np.moveaxis(a, -1, 0)
+    w2, x2, y2, z2 = np.moveaxis(b, -1, 0)
+    return np.stack([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                     w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2], -1)
+
+
+def _conj(a):
+    return a * np.array([1.0, -1.0, -1.0, -1.0])
+
+
+def _pure(v):
+    return np.concatenate([np.zeros(v.shape[:-1] + (1,)), v], -1)
+
+
+def anchor_loss(p, t, q_gt, t_gt):
+    """L = sum_i |R(p_0)^T (t_i - t_0) - R(q0_gt)^T (t_i_gt - t0_gt)|^2 with
+    R(p)^T v = Im(p^* v~ p): translations expressed in the frame of pose 0,
+    which removes the global gauge of Eq. (1).  Returns (L, dL/dp, dL/dt)."""
+    d = _qmul(_qmul(_conj(q_gt[0]), _pure(t_gt - t_gt[0])), q_gt[0])[:, 1:]
+    v = t - t[0]
+    y = _qmul(_qmul(_conj(p[0]), _pure(v)), p[0])[:, 1:] - d
+    L = float((y * y).sum())
+    Yb = _pure(2.0 * y)
+    gt = _qmul(_qmul(p[0], Yb), _conj(p[0]))[:, 1:]
+    dt = gt.copy()
+    dt[0] -= gt.sum(0)
+    dp = np.zeros_like(p)
+    dp[0] = (-2.0 * _qmul(_qmul(_pure(v), p[0]), Yb)).sum(0)
+    return L, dp, dt
+
+
+@pytest.fixture(scope="module")
+def case():
+    g = synth.random_graph(16, 40, seed=11)
+    st = synth.random_state(np.random.default_rng(4), g.n)
+    prm = oracle.make_params(beta1=1.0, beta2=1.0, tau=1.5)
+    rng = np.random.default_rng(21)
+    a, b = rng.normal(size=(g.n, 4)), rng.normal(size=(g.n, 3))
+    return g, st, prm, a, b
+
+
+def _linear(g, prm, st, K, a, b):
+    x, _, _ = oracle.iterate(g, prm, st, K)
+    return float((a * x["p"]).sum() + (b * x["t"]).sum())
+
+
+def _fd_measurement(g, key, idx, f):
+    vals = []
+    for sgn in (1.0, -1.0):
+        arr = getattr(g, key).copy()
+        arr[idx] += sgn * H
+        vals.append(f(dataclasses.replace(g, **{key: arr})))
+    return (vals[0] - vals[1]) / (2 * H)
+
+
+def test_adjoint_matches_central_differences_on_measurements(case):
+    g, st, prm, a, b = case
+    K = 8
+    res = oracle.adjoint(g, prm, st, K, a, b)
+    rng = np.random.default_rng(5)
+    fd, ad = [], []
+    for key, name in (("q_meas", "q_meas"), ("t_meas", "t_meas"), ("kappa", "kappa"), ("omega", "omega")):
+        shape = getattr(g, key).shape
+        for _ in range(16):  # 64 coordinates in all
+            idx = tuple(int(rng.integers(0, s)) for s in shape)
+            fd.append(_fd_measurement(g, key, idx, lambda gg: _linear(gg, prm, st, K, a, b)))
+            ad.append(res[name][idx])
+    fd, ad = np.array(fd), np.array(ad)
+    assert np.linalg.norm(fd - ad) <= 1e-6 * np.linalg.norm(ad)
+    assert np.abs(fd - ad).max() <= 1e-6 * np.abs(ad).max()
+    # and the forward part returns x^K itself
+    x, _, _ = oracle.iterate(g, prm, st, K)
+    np.testing.assert_array_equal(res["p"], x["p"])
+    np.testing.assert_array_equal(res["t"], x["t"])
+
+
+def test_adjoint_matches_central_differences_on_initial_state(case):
+    g, st, prm, a, b = case
+    K = 5
+    res = oracle.adjoint(g, prm, st, K, a, b)
+    rng = np.random.default_rng(8)
+    for key in KEYS:
+        for _ in range(4):
+            idx = (int(rng.integers(0, g.n)), int(rng.integers(0, st[key].shape[1])))
+            vals = []
+            for sgn in (1.0, -1.0):
+                s2 = oracle.copy_state(st)
+                s2[key][idx] += sgn * H
+                vals.append(_linear(g, prm, s2, K, a, b))
+            fd = (vals[0] - vals[1]) / (2 * H)
+            ad = res["x0"][key][idx]
+            assert abs(fd - ad) <= 1e-6 * max(1.0, abs(ad)), (key, idx, fd, ad)
+
+
+def test_anchor_loss_gradient_by_differences():
+    rng = np.random.default_rng(2)
+    n = 7
+    p = rng.normal(size=(n, 4))
+    p /= np.linalg.norm(p, axis=1, keepdims=True)
+    t = rng.normal(size=(n, 3)) * 3
+    q_gt = rng.normal(size=(n, 4))
+    q_gt /= np.linalg.norm(q_gt, axis=1, keepdims=True)
+    t_gt = t + rng.normal(size=(n, 3)) * 0.3
+    L, dp, dt = anchor_loss(p, t, q_gt, t_gt)
+    for arr, grad in ((p, dp), (t, dt)):
+        for idx in np.ndindex(arr.shape):
+            if arr is p and idx[0] > 0:
+                assert grad[idx] == 0.0
+                continue
+            a1, a2 = arr.copy(), arr.copy()
+            a1[idx] += H
+            a2[idx] -= H
+            f1 = anchor_loss(a1, t, q_gt, t_gt)[0] if arr is p else anchor_loss(p, a1, q_gt, t_gt)[0]
+            f2 = anchor_loss(a2, t, q_gt, t_gt)[0] if arr is p else anchor_loss(p, a2, q_gt, t_gt)[0]
+            assert abs((f1 - f2) / (2 * H) - grad[idx]) <= 1e-6 * max(1.0, abs(grad[idx]))
+    # zero at the ground truth moved by any global rigid motion (gauge of Eq. (1))
+    g = np.array([np.cos(0.3), 0.0, np.sin(0.3), 0.0])
+    moved = _qmul(_qmul(g[None], _pure(t_gt)), _conj(g)[None])[:, 1:] + np.array([5.0, -2.0, 1.0])
+    assert anchor_loss(_qmul(g[None], q_gt), moved, q_gt, t_gt)[0] < 1e-20
+
+
+def test_anchor_loss_through_iterations_by_differences():
+    g = synth.random_walk_graph(40, n_closures=None, closure_density=1.0, sigma_r=0.02, sigma_t=0.1, seed=3)
+    q0, t0 = oracle.init_odometry(g)
+    st = oracle.init_state(q0, t0)
+    prm = oracle.make_params(beta1=1.0, beta2=1.0, tau=1.5)
+    K = 12
+    x, _, _ = oracle.iterate(g, prm, st, K)
+    _, dp, dt = anchor_loss(x["p"], x["t"], g.q_gt, g.t_gt)
+    res = oracle.adjoint(g, prm, st, K, dp, dt)
+
+    def f(gg):
+        xx, _, _ = oracle.iterate(gg, prm, st, K)
+        return anchor_loss(xx["p"], xx["t"], g.q_gt, g.t_gt)[0]
+
+    rng = np.random.default_rng(1)
+    for key in ("q_meas", "t_meas", "kappa", "omega"):
+        for _ in range(3):
+            idx = tuple(int(rng.integers(0, s)) for s in getattr(g, key).shape)
+            fd = _fd_measurement(g, key, idx, f)
+            assert abs(fd - res[key][idx]) <= 1e-6 * max(1.0, np.abs(res[key]).max()), (key, idx)
+
+
+def test_adjoint_of_zero_iterations_is_the_cotangent(case):
+    g, st, prm, a, b = case
+    res = oracle.adjoint(g, prm, st, 0, a, b)
+    for key in ("q_meas", "t_meas", "kappa", "omega"):
+        assert not res[key].any()
+    np.testing.assert_array_equal(res["x0"]["p"], a)
+    np.testing.assert_array_equal(res["x0"]["t"], b)
+    for key in ("q", "s", "lam", "z"):
+        assert not res["x0"][key].any()
