@@ -177,6 +177,43 @@ pradmm_status pradmm_bytes_per_iteration(pradmm_t h, double* out);
  * iteration time.  The state advances by `iters` iterations. */
 pradmm_status pradmm_profile_sweeps(pradmm_t h, int32_t iters, double* ms_out);
 
+/* ---- reverse mode -------------------------------------------------------------
+ * Gradients of a loss L(p^K, t^K) of the poses after K iterations of
+ * Algorithm 1 with respect to the measurements q_e, t_e and the weights
+ * kappa_e, omega_e of Eq. (1), through the unrolled iterations (3a)-(3f)
+ * with the closed forms of Appendix B.  The starting state x^0 is held fixed
+ * (its own dependence on the measurements, e.g. through odometry, is not
+ * differentiated); its adjoint is available as an output.  q_e is treated as
+ * a point of R^4: the gradient is not projected onto the tangent space of
+ * the unit sphere.  Where a p-update met |u_i| = 0 and kept p_i^k, the
+ * adjoint of p_i^{k+1} passes to p_i^k.  Derivatives of A_2 with respect to
+ * p are dropped: they point along p and the sphere projection removes them.
+ *
+ * pradmm_adjoint_record runs `iters` iterations from the current state x^0
+ * (like pradmm_step) and keeps a checkpoint of the full state every
+ * `ckpt_every` iterations (>= 1; device memory for ceil(iters/ckpt_every)+1
+ * checkpoints plus ckpt_every-1 recompute slots, 28 n reals each).  The
+ * tape stays valid until the state changes (set_state, init_odometry, step,
+ * solve, another record). */
+pradmm_status pradmm_adjoint_record(pradmm_t h, int32_t iters, int32_t ckpt_every);
+
+/* Runs the reverse sweeps over the recorded iterations for the cotangent
+ * (p_bar = dL/dp^K, n x 4; t_bar = dL/dt^K, n x 3; NULL means zero) and
+ * writes, in the caller's edge order, dL/dq_meas (m x 4), dL/dt_meas (m x 3),
+ * dL/dkappa (m), dL/domega (m), and, if x0_bar is not NULL, the adjoint of
+ * x^0 as 21 n doubles: p (n x 4), q (n x 4), t (n x 3), s (n x 3),
+ * lam (n x 4), z (n x 3).  Any output pointer may be NULL.  Segments between
+ * checkpoints are recomputed with the forward sweep kernels, bitwise as
+ * recorded.  The tape stays valid, so several cotangents may be run. */
+pradmm_status pradmm_adjoint(pradmm_t h, const double* p_bar, const double* t_bar, double* q_meas_bar,
+                             double* t_meas_bar, double* kappa_bar, double* omega_bar, double* x0_bar);
+
+/* Same with every array in device memory (double).  The work runs on the
+ * handle's stream and has finished when the call returns. */
+pradmm_status pradmm_adjoint_device(pradmm_t h, const double* p_bar_d, const double* t_bar_d,
+                                    double* q_meas_bar_d, double* t_meas_bar_d, double* kappa_bar_d,
+                                    double* omega_bar_d, double* x0_bar_d);
+
 /* F of Eq. (1) for poses already in device memory, written to the device
  * double *F_d, without allocating any memory.  There is no counterpart in the
  * paper: it serves callers that cannot allocate device memory when they need
@@ -220,8 +257,10 @@ const char* pradmm_last_error(void);
  * gives each large graph a whole CTA and packs small graphs one per warp.
  * Each graph stops on its own: when e^k <= rel_tol * e^1 (the ratio of its
  * Appendix E.1 residual to the first iteration's), when e^k is not finite,
- * or after max_iter iterations.  Results of a graph are bitwise those of
- * the plain solver run for the same number of iterations. */
+ * or after max_iter iterations.  A graph's results agree with the plain
+ * solver run for the same number of iterations to rounding (the same
+ * per-vertex updates, compiled into a different kernel), and a repeated
+ * solve is bitwise identical. */
 typedef struct pradmm_batch_s* pradmm_batch_t;
 
 /* G graphs; graph g has n_g[g] >= 1 vertices and m_g[g] >= 0 edges.  Edge

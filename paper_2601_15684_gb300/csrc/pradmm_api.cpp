@@ -84,6 +84,22 @@ struct pradmm_s {
     cudaGraphConditionalHandle cond = 0;
     bool graph_ready = false;
 
+    uint64_t epoch = 0;                // bumped by every change of the state
+    std::vector<int32_t> out_edge;     // out-slot -> input edge
+
+    // reverse mode: checkpoints + recompute slots, 28 n reals per slot
+    void* tape = nullptr;
+    size_t tape_bytes = 0;
+    bool tape_valid = false;
+    uint64_t tape_epoch = 0;
+    long long tape_k0 = 0;             // iteration counter at x^0
+    int tape_K = 0, tape_C = 1, tape_nck = 0;
+    void* adj = nullptr;               // per-vertex adjoint arrays + per-slot q_e, kappa_e
+    double* adj_g = nullptr;           // 9 m: per-slot gradients
+    int32_t* out_edge_d = nullptr;
+    double* adj_stage = nullptr;       // max(9 m, 21 n) doubles
+    Ctrl* tape_ctrl = nullptr;
+
     template <typename R>
     pradmm::GraphDev<R> gdev() const {
         pradmm::GraphDev<R> g;
@@ -309,6 +325,7 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
     const Csr si = build_csr(n, perm, iperm, iptr, ipermv, src);
     h->out_slots = (int64_t)so.idx.size();
     h->in_slots = (int64_t)si.idx.size();
+    h->out_edge.assign(so.edge.begin(), so.edge.end());
     // ---- iteration-invariant scalar block matrices (Appendix B, scalar Sigma) ----
     std::vector<double> A2(n, h->prm.beta1 + h->prm.gamma[1]), A3(n, h->prm.beta2 + h->prm.gamma[2]),
         A4(n, h->prm.beta2 + h->prm.gamma[3]);
@@ -404,6 +421,8 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
 }
 
 void free_all(pradmm_s* h) {
+    if (h->tape) cudaFree(h->tape);
+    h->tape = nullptr;
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     if (h->graph) cudaGraphDestroy(h->graph);
     for (void* v : h->allocs) cudaFree(v);
@@ -516,6 +535,7 @@ pradmm_status set_state_dev(pradmm_s* h, const double* p, const double* q, const
     CU(cudaStreamSynchronize(st));
     h->state_set = true;
     h->pending = false;
+    h->epoch++;
     return PRADMM_OK;
 }
 
@@ -580,6 +600,7 @@ template <typename R>
 pradmm_status run(pradmm_s* h, long long iters, bool use_tol) {
     if (!h->state_set) return fail(PRADMM_ERR_STATE, "state is not set (pradmm_set_state or pradmm_init_odometry)");
     if (iters <= 0) return read_ctrl(h);
+    h->epoch++;
     CU(pradmm::launch_arm(h->ctrl, iters, use_tol ? 1 : 0, h->prm.tol, h->stream));
     if (!h->pending) {
         CU(pradmm::launch_p<R>(h->gdev<R>(), h->sdev<R>(), h->coef<R>(), h->launch(false)));
@@ -738,6 +759,7 @@ pradmm_status profile_impl(pradmm_s* h, int32_t iters, double* ms_out) {
     const auto S = h->sdev<R>();
     const auto c = h->coef<R>();
     const auto L = h->launch(false);
+    h->epoch++;
     CU(pradmm::launch_arm(h->ctrl, iters, 0, 0.0, h->stream));
     if (!h->pending) {
         CU(pradmm::launch_p<R>(g, S, c, L));
@@ -780,6 +802,225 @@ pradmm_status profile_impl(pradmm_s* h, int32_t iters, double* ms_out) {
     for (auto& e : ev) cudaEventDestroy(e);
     if (st == PRADMM_OK) st = read_ctrl(h);
     return st;
+}
+
+// ---- reverse mode ------------------------------------------------------------
+// Tape slot: p[0], p[1], q, lam, t, s, z, each 4 n reals, contiguous.  A slot
+// at iteration k holds p^k in p[k & 1] and p^{k+1} in p[(k+1) & 1], exactly
+// as the handle's own state does, so the forward sweep kernels run on a slot
+// unchanged.
+template <typename R>
+pradmm::StateDev<R> slot_state(void* base, int64_t n) {
+    R* b = static_cast<R*>(base);
+    pradmm::StateDev<R> S;
+    S.p[0] = b;
+    S.p[1] = b + 4 * n;
+    S.q = b + 8 * n;
+    S.lam = b + 12 * n;
+    S.t = b + 16 * n;
+    S.s = b + 20 * n;
+    S.z = b + 24 * n;
+    return S;
+}
+
+// n rounded up to a multiple of 4, so that an array following n scalars
+// still starts on a 16-byte boundary for float4 / double2 accesses.
+int64_t pad4(int64_t n) { return (n + 3) & ~int64_t(3); }
+
+size_t slot_bytes(const pradmm_s* h) { return 28 * (size_t)h->n * h->rsize; }
+
+void* tape_slot(pradmm_s* h, int64_t idx) { return static_cast<char*>(h->tape) + (size_t)idx * slot_bytes(h); }
+
+pradmm_status snapshot(pradmm_s* h, void* dst) {
+    const size_t b = 4 * (size_t)h->n * h->rsize;
+    char* d = static_cast<char*>(dst);
+    const void* src[7] = {h->p[0], h->p[1], h->q, h->lam, h->t, h->s, h->z};
+    for (int k = 0; k < 7; ++k) CU(cudaMemcpyAsync(d + k * b, src[k], b, cudaMemcpyDeviceToDevice, h->stream));
+    return PRADMM_OK;
+}
+
+template <typename R>
+pradmm_status adjoint_record(pradmm_s* h, int32_t iters, int32_t ckpt_every) {
+    if (!h->state_set) return fail(PRADMM_ERR_STATE, "state is not set (pradmm_set_state or pradmm_init_odometry)");
+    if (iters < 0) return fail(PRADMM_ERR_ARG, "iters must be >= 0");
+    if (ckpt_every < 1) return fail(PRADMM_ERR_ARG, "ckpt_every must be >= 1");
+    h->tape_valid = false;
+    const int C = iters == 0 ? 1 : std::min(ckpt_every, iters);
+    const int nck = iters == 0 ? 1 : (iters + C - 1) / C + 1;
+    const size_t need = (size_t)(nck + C - 1) * slot_bytes(h);
+    if (need > h->tape_bytes) {
+        if (h->tape) CU(cudaFree(h->tape));
+        h->tape = nullptr;
+        h->tape_bytes = 0;
+        cudaError_t e = cudaMalloc(&h->tape, need);
+        if (e != cudaSuccess) {
+            h->tape = nullptr;
+            return fail(e == cudaErrorMemoryAllocation ? PRADMM_ERR_NOMEM : PRADMM_ERR_CUDA,
+                        "tape of %zu bytes: %s", need, cudaGetErrorString(e));
+        }
+        h->tape_bytes = need;
+    }
+    if (!h->pending) {
+        CU(pradmm::launch_p<R>(h->gdev<R>(), h->sdev<R>(), h->coef<R>(), h->launch(false)));
+        h->pending = true;
+    }
+    ST(read_ctrl(h));
+    const long long k0 = h->ctrl_h->iter;
+    ST(snapshot(h, tape_slot(h, 0)));
+    for (int c = 0; c + 1 < nck; ++c) {
+        const int L = std::min(C, iters - c * C);
+        ST(run<R>(h, L, false));
+        ST(snapshot(h, tape_slot(h, c + 1)));
+    }
+    CU(cudaStreamSynchronize(h->stream));
+    h->tape_k0 = k0;
+    h->tape_K = iters;
+    h->tape_C = C;
+    h->tape_nck = nck;
+    h->tape_epoch = h->epoch;
+    h->tape_valid = true;
+    return PRADMM_OK;
+}
+
+template <typename R>
+pradmm_status ensure_adjoint(pradmm_s* h) {
+    const int64_t n = h->n, m = h->out_slots;
+    if (!h->adj) {
+        ST(valloc(h, &h->adj, 13 * 4 * (size_t)n + (size_t)pad4(n) + 4 * (size_t)m + (size_t)m));
+        ST(dalloc(h, &h->adj_g, 9 * (size_t)m));
+        ST(dalloc(h, &h->out_edge_d, (size_t)m));
+        ST(dalloc(h, &h->adj_stage, std::max<size_t>(9 * (size_t)m, 21 * (size_t)n)));
+        ST(dalloc(h, &h->tape_ctrl, 1));
+        if (m > 0)
+            CU(cudaMemcpy(h->out_edge_d, h->out_edge.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
+        R* b = static_cast<R*>(h->adj);
+        R* eq = b + 13 * 4 * n + pad4(n);
+        CU(pradmm::launch_adj_edges<R>(h->qe64, h->ka64, m, eq, eq + 4 * m, h->stream));
+        CU(cudaMemsetAsync(h->tape_ctrl, 0, sizeof(Ctrl), h->stream));
+    }
+    return PRADMM_OK;
+}
+
+template <typename R>
+pradmm::AdjDev<R> adj_dev(pradmm_s* h) {
+    const int64_t n = h->n, m = h->out_slots;
+    R* b = static_cast<R*>(h->adj);
+    pradmm::AdjDev<R> A;
+    R** v[13] = {&A.gs, &A.gt, &A.gq, &A.pb, &A.qb, &A.tb, &A.ub, &A.op, &A.oq, &A.ot, &A.os, &A.ol, &A.oz};
+    for (int k = 0; k < 13; ++k) *v[k] = b + 4 * n * k;
+    A.a2b = b + 4 * n * 13;
+    A.eq = A.a2b + pad4(n);  // 4-real records need 16-byte alignment
+    A.ek = A.eq + 4 * m;
+    A.g_te = h->adj_g;
+    A.g_qe = h->adj_g + 4 * m;
+    A.g_ka = h->adj_g + 8 * m;
+    return A;
+}
+
+template <typename R>
+pradmm_status adjoint_impl(pradmm_s* h, const double* p_bar, const double* t_bar, double* qe_bar, double* te_bar,
+                           double* ka_bar, double* om_bar, double* x0_bar, bool device) {
+    if (!h->tape_valid || h->tape_epoch != h->epoch)
+        return fail(PRADMM_ERR_STATE, "no recorded iterations: call pradmm_adjoint_record after the last state change");
+    ST(ensure_adjoint<R>(h));
+    const int64_t n = h->n, m = h->out_slots;
+    cudaStream_t st = h->stream;
+    const auto g = h->gdev<R>();
+    const auto c = h->coef<R>();
+    const pradmm::AdjDev<R> A = adj_dev<R>(h);
+    // cotangent of x^K: pbar -> op, tbar -> ot (internal order)
+    const double* pb = h->zeros;
+    const double* tb = h->zeros;
+    if (p_bar) {
+        if (device) {
+            pb = p_bar;
+        } else {
+            CU(cudaMemcpyAsync(h->adj_stage, p_bar, sizeof(double) * 4 * n, cudaMemcpyHostToDevice, st));
+            pb = h->adj_stage;
+        }
+    }
+    if (t_bar) {
+        if (device) {
+            tb = t_bar;
+        } else {
+            CU(cudaMemcpyAsync(h->adj_stage + 4 * n, t_bar, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+            tb = h->adj_stage + 4 * n;
+        }
+    }
+    CU(pradmm::launch_pack4<R>(pb, h->perm_d, A.op, n, st));
+    CU(pradmm::launch_pack3<R>(tb, h->perm_d, h->zeros, A.ot, n, st));
+    CU(cudaMemsetAsync(h->adj_g, 0, sizeof(double) * 9 * (size_t)m, st));
+    const int K = h->tape_K, C = h->tape_C, nck = h->tape_nck;
+    if (K == 0) {
+        for (R* a : {A.oq, A.os, A.ol, A.oz}) CU(cudaMemsetAsync(a, 0, 4 * (size_t)n * sizeof(R), st));
+    } else {
+        const auto SK = slot_state<R>(tape_slot(h, nck - 1), n);
+        CU(pradmm::launch_adj_seed<R>(g, A, c, SK.s, SK.z, st));
+        const int64_t seg0 = nck;  // first recompute slot
+        pradmm::Launch L = h->launch(false);
+        L.ctrl = h->tape_ctrl;
+        for (int ci = nck - 2; ci >= 0; --ci) {
+            const long long kc = h->tape_k0 + (long long)ci * C;
+            const int len = std::min(C, K - ci * C);
+            std::vector<void*> slot(len + 1);
+            slot[0] = tape_slot(h, ci);
+            slot[len] = tape_slot(h, ci + 1);
+            for (int j = 1; j < len; ++j) slot[j] = tape_slot(h, seg0 + j - 1);
+            if (len > 1) {
+                CU(pradmm::launch_tape_arm(h->tape_ctrl, kc, st));
+                for (int j = 0; j + 1 < len; ++j) {
+                    CU(cudaMemcpyAsync(slot[j + 1], slot[j], slot_bytes(h), cudaMemcpyDeviceToDevice, st));
+                    const auto S = slot_state<R>(slot[j + 1], n);
+                    CU(pradmm::launch_q<R>(g, S, c, L));
+                    CU(pradmm::launch_t<R>(g, S, c, L));
+                    CU(pradmm::launch_sp<R>(g, S, c, L));
+                }
+            }
+            for (int j = len - 1; j >= 0; --j) {
+                const long long k = kc + j;
+                const auto S0 = slot_state<R>(slot[j], n);
+                const auto S1 = slot_state<R>(slot[j + 1], n);
+                pradmm::AdjStep<R> X;
+                X.pc = S0.p[k & 1];
+                X.pn = S0.p[(k + 1) & 1];
+                X.q = S0.q;
+                X.lam = S0.lam;
+                X.t = S0.t;
+                X.s = S0.s;
+                X.z = S0.z;
+                X.qn = S1.q;
+                X.tn = S1.t;
+                CU(pradmm::launch_adj_iteration<R>(g, A, X, c, (ci == 0 && j == 0) ? 0 : 1, st));
+            }
+        }
+    }
+    // measurement gradients in the caller's edge order
+    if (device) {
+        CU(pradmm::launch_adj_scatter(A.g_qe, A.g_te, A.g_ka, h->out_edge_d, m, qe_bar, te_bar, ka_bar, om_bar, st));
+    } else if (m > 0 && (qe_bar || te_bar || ka_bar || om_bar)) {
+        double* sq = h->adj_stage;
+        double* stt = sq + 4 * m;
+        double* sk = stt + 3 * m;
+        double* so = sk + m;
+        CU(pradmm::launch_adj_scatter(A.g_qe, A.g_te, A.g_ka, h->out_edge_d, m, sq, stt, sk, so, st));
+        if (qe_bar) CU(cudaMemcpyAsync(qe_bar, sq, sizeof(double) * 4 * m, cudaMemcpyDeviceToHost, st));
+        if (te_bar) CU(cudaMemcpyAsync(te_bar, stt, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, st));
+        if (ka_bar) CU(cudaMemcpyAsync(ka_bar, sk, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+        if (om_bar) CU(cudaMemcpyAsync(om_bar, so, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+    }
+    if (x0_bar) {
+        double* d = device ? x0_bar : h->adj_stage;
+        CU(pradmm::launch_unpack4<R>(A.op, h->perm_d, d, n, st));
+        CU(pradmm::launch_unpack4<R>(A.oq, h->perm_d, d + 4 * n, n, st));
+        CU(pradmm::launch_unpack3<R>(A.ot, h->perm_d, d + 8 * n, n, st));
+        CU(pradmm::launch_unpack3<R>(A.os, h->perm_d, d + 11 * n, n, st));
+        CU(pradmm::launch_unpack4<R>(A.ol, h->perm_d, d + 14 * n, n, st));
+        CU(pradmm::launch_unpack3<R>(A.oz, h->perm_d, d + 18 * n, n, st));
+        if (!device) CU(cudaMemcpyAsync(x0_bar, d, sizeof(double) * 21 * n, cudaMemcpyDeviceToHost, st));
+    }
+    CU(cudaStreamSynchronize(st));
+    return PRADMM_OK;
 }
 
 }  // namespace
@@ -902,6 +1143,27 @@ pradmm_status pradmm_solve(pradmm_t h, int32_t* iters_done, double* e_final) {
     if (h->prm.max_iter > 0 && h->ctrl_h->stop) return PRADMM_OK;
     return fail(PRADMM_ERR_NOT_CONVERGED, "e = %.6g >= tol = %.6g after %d iterations", h->ctrl_h->e_last, h->prm.tol,
                 (int)(h->ctrl_h->iter - k0));
+}
+
+pradmm_status pradmm_adjoint_record(pradmm_t h, int32_t iters, int32_t ckpt_every) {
+    if (!h) return fail(PRADMM_ERR_ARG, "handle is NULL");
+    return h->fp64 ? adjoint_record<double>(h, iters, ckpt_every) : adjoint_record<float>(h, iters, ckpt_every);
+}
+
+pradmm_status pradmm_adjoint(pradmm_t h, const double* p_bar, const double* t_bar, double* q_meas_bar,
+                             double* t_meas_bar, double* kappa_bar, double* omega_bar, double* x0_bar) {
+    if (!h) return fail(PRADMM_ERR_ARG, "handle is NULL");
+    return h->fp64 ? adjoint_impl<double>(h, p_bar, t_bar, q_meas_bar, t_meas_bar, kappa_bar, omega_bar, x0_bar, false)
+                   : adjoint_impl<float>(h, p_bar, t_bar, q_meas_bar, t_meas_bar, kappa_bar, omega_bar, x0_bar, false);
+}
+
+pradmm_status pradmm_adjoint_device(pradmm_t h, const double* p_bar_d, const double* t_bar_d, double* q_meas_bar_d,
+                                    double* t_meas_bar_d, double* kappa_bar_d, double* omega_bar_d, double* x0_bar_d) {
+    if (!h) return fail(PRADMM_ERR_ARG, "handle is NULL");
+    return h->fp64 ? adjoint_impl<double>(h, p_bar_d, t_bar_d, q_meas_bar_d, t_meas_bar_d, kappa_bar_d, omega_bar_d,
+                                          x0_bar_d, true)
+                   : adjoint_impl<float>(h, p_bar_d, t_bar_d, q_meas_bar_d, t_meas_bar_d, kappa_bar_d, omega_bar_d,
+                                         x0_bar_d, true);
 }
 
 pradmm_status pradmm_objective(pradmm_t h, double* F) {

@@ -155,6 +155,52 @@ cudaError_t launch_batch_objective(const GraphDev<R>& g, const StateDev<R>& s, c
                                    const double* te64, const double* ka64, const double* om64,
                                    const BatchDev& b, double* F, int G, cudaStream_t st);
 
+// ---- reverse mode (adjoint) ------------------------------------------------------
+
+// Per-vertex adjoint arrays (internal vertex order, 4 reals per vertex unless
+// noted) and the per-out-slot measurement gradients.
+template <typename R>
+struct AdjDev {
+    R* gs;   // (gs, A_4bar): adjoint of the s-block numerator / A_4, and of A_4
+    R* gt;   // (gt, A_3bar)
+    R* gq;   // gq = qbar / A_2
+    R* a2b;  // n: A_2bar
+    R* pb;   // adjoint of p^{k+1} (accumulating)
+    R* qb;   // adjoint of q^{k+1}
+    R* tb;   // adjoint of t^{k+1}
+    R* ub;   // adjoint of u (sphere projection)
+    R *op, *oq, *ot, *os, *ol, *oz;  // adjoint of x^k (p, q, t, s, lam, z)
+    const R* eq;     // 4m: q_e per out-slot (unscaled)
+    const R* ek;     // m: kappa_e per out-slot
+    double* g_te;    // 4m: (dL/dt_e, dL/domega_e) per out-slot
+    double* g_qe;    // 4m: dL/dq_e
+    double* g_ka;    // m: dL/dkappa_e
+};
+
+// State of one unrolled iteration k -> k+1 (tape slots; pads as in StateDev).
+template <typename R>
+struct AdjStep {
+    const R* pc;   // p^k
+    const R* pn;   // p^{k+1}
+    const R *q, *lam, *t, *s, *z;  // x^k
+    const R *qn, *tn;              // q^{k+1}, t^{k+1}
+};
+
+template <typename R>
+cudaError_t launch_adj_seed(const GraphDev<R>& g, const AdjDev<R>& A, const Coef<R>& c, const R* s_K, const R* z_K,
+                            cudaStream_t st);
+// The four reverse sweeps of iteration k; `more` = 1 starts iteration k-1.
+template <typename R>
+cudaError_t launch_adj_iteration(const GraphDev<R>& g, const AdjDev<R>& A, const AdjStep<R>& X, const Coef<R>& c,
+                                 int more, cudaStream_t st);
+template <typename R>
+cudaError_t launch_adj_edges(const double* qe64, const double* ka64, int64_t m, R* eq, R* ek, cudaStream_t st);
+cudaError_t launch_adj_scatter(const double* g_qe, const double* g_te, const double* g_ka, const int32_t* eidx,
+                               int64_t m, double* qe_bar, double* te_bar, double* ka_bar, double* om_bar,
+                               cudaStream_t st);
+// Sets a tape control block to iteration `iter` with no halt and no target.
+cudaError_t launch_tape_arm(Ctrl* ctrl, long long iter, cudaStream_t st);
+
 // Records the message pradmm_last_error() returns on the calling thread.
 void set_last_error(const char* msg);
 

@@ -75,6 +75,9 @@ _SIGS = {
     "pradmm_counters": (ctypes.c_int, [_h, _i64]),
     "pradmm_bytes_per_iteration": (ctypes.c_int, [_h, _d]),
     "pradmm_profile_sweeps": (ctypes.c_int, [_h, ctypes.c_int32, _d]),
+    "pradmm_adjoint_record": (ctypes.c_int, [_h, ctypes.c_int32, ctypes.c_int32]),
+    "pradmm_adjoint": (ctypes.c_int, [_h, _d, _d, _d, _d, _d, _d, _d]),
+    "pradmm_adjoint_device": (ctypes.c_int, [_h] + [ctypes.c_void_p] * 7),
     "pradmm_objective_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 10),
     "pradmm_destroy": (None, [_h]),
     "pradmm_batch_create": (ctypes.c_int, [ctypes.c_int32, _i64, _i64, _i32, _i32, _d, _d, _d, _d, _P(pradmm_params),
@@ -248,6 +251,39 @@ def pradmm_profile_sweeps(h, iters: int) -> dict:
     return {"k_q": out[0], "k_t": out[1], "k_sp": out[2], "iteration": out[3]}
 
 
+def pradmm_adjoint_record(h, iters: int, ckpt_every: int = 20):
+    _check(load().pradmm_adjoint_record(h, int(iters), int(ckpt_every)), "pradmm_adjoint_record")
+
+
+_X0 = (("p", 4), ("q", 4), ("t", 3), ("s", 3), ("lam", 4), ("z", 3))
+
+
+def pradmm_adjoint(h, n, m, p_bar=None, t_bar=None, x0=False) -> dict:
+    """Gradients of L(p^K, t^K) given p_bar = dL/dp^K, t_bar = dL/dt^K (host
+    arrays): dict with q_meas (m x 4), t_meas (m x 3), kappa (m), omega (m)
+    and, if x0, the adjoint of the recorded initial state (dict of p .. z)."""
+    pb = _f64(p_bar, (n, 4)) if p_bar is not None else None
+    tb = _f64(t_bar, (n, 3)) if t_bar is not None else None
+    out = {"q_meas": np.zeros((m, 4)), "t_meas": np.zeros((m, 3)), "kappa": np.zeros(m), "omega": np.zeros(m)}
+    x0buf = np.zeros(21 * n) if x0 else None
+    _check(load().pradmm_adjoint(h, _dp(pb), _dp(tb), _dp(out["q_meas"]), _dp(out["t_meas"]), _dp(out["kappa"]),
+                                 _dp(out["omega"]), _dp(x0buf)), "pradmm_adjoint")
+    if x0:
+        o, d = 0, {}
+        for key, w in _X0:
+            d[key] = x0buf[o:o + w * n].reshape(n, w)
+            o += w * n
+        out["x0"] = d
+    return out
+
+
+def pradmm_adjoint_device(h, p_bar_ptr, t_bar_ptr, q_meas_bar_ptr, t_meas_bar_ptr, kappa_bar_ptr, omega_bar_ptr,
+                          x0_bar_ptr=0):
+    args = [ctypes.c_void_p(x or 0) for x in (p_bar_ptr, t_bar_ptr, q_meas_bar_ptr, t_meas_bar_ptr, kappa_bar_ptr,
+                                              omega_bar_ptr, x0_bar_ptr)]
+    _check(load().pradmm_adjoint_device(h, *args), "pradmm_adjoint_device")
+
+
 def pradmm_objective_noalloc(n, m, src_ptr, dst_ptr, q_meas_ptr, t_meas_ptr, kappa_ptr, omega_ptr, q_ptr, t_ptr,
                              F_ptr, stream=None):
     """F of Eq. (1) from device arrays into the device double at F_ptr, with no
@@ -284,6 +320,7 @@ class Solver:
                 setattr(prm, k, v)
         self.params = prm
         self.n = int(graph.n)
+        self.m = int(len(graph.src))
         self.h = pradmm_create(graph.n, graph.src, graph.dst, graph.q_meas, graph.t_meas, graph.kappa, graph.omega,
                                prm, stream)
 
@@ -327,6 +364,12 @@ class Solver:
 
     def poses(self):
         return pradmm_get_poses(self.h, self.n)
+
+    def adjoint_record(self, iters, ckpt_every=20):
+        pradmm_adjoint_record(self.h, iters, ckpt_every)
+
+    def adjoint(self, p_bar=None, t_bar=None, x0=False):
+        return pradmm_adjoint(self.h, self.n, self.m, p_bar, t_bar, x0)
 
     def iterations(self):
         return pradmm_iterations(self.h)
@@ -438,3 +481,70 @@ class Batch:
                                              _dp(out["lam"]), _dp(out["z"])), "pradmm_batch_get_state")
         return out
 
+
+
+# ---- torch autograd wrapper of the reverse mode ---------------------------------------
+
+class _Handle:
+    """Destroys its handle when the autograd graph that holds it is freed."""
+
+    def __init__(self, h):
+        self.h = h
+
+    def __del__(self):
+        try:
+            pradmm_destroy(self.h)
+        except Exception:
+            pass
+
+
+def unrolled_poses(n, src, dst, q_meas, t_meas, kappa=None, omega=None, iters=200, ckpt_every=20, params=None,
+                   init=None):
+    """(p^K, t^K) after `iters` iterations of Algorithm 1, differentiable with
+    respect to q_meas (m x 4), t_meas (m x 3), kappa (m), omega (m): CUDA
+    float64 tensors; src, dst CUDA int32 tensors.  The start is the odometry
+    initialisation (init=None) or init=(q0, t0) host arrays, held fixed.
+    Forward and backward run in libpradmm's kernels on torch's current stream
+    (pradmm_adjoint_record / pradmm_adjoint_device)."""
+    import torch
+
+    class _Unrolled(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, qm, tm, ka, om):
+            m = int(qm.shape[0])
+            stream = torch.cuda.current_stream(qm.device).cuda_stream
+            h = pradmm_create_device(n, m, src.data_ptr(), dst.data_ptr(), qm.data_ptr(), tm.data_ptr(),
+                                     ka.data_ptr(), om.data_ptr(), params, stream)
+            hold = _Handle(h)
+            if init is None:
+                pradmm_init_odometry(h)
+            else:
+                pradmm_set_state(h, init[0], init[1], n)
+            pradmm_adjoint_record(h, iters, ckpt_every)
+            p = torch.empty((n, 4), dtype=torch.float64, device=qm.device)
+            t = torch.empty((n, 3), dtype=torch.float64, device=qm.device)
+            pradmm_get_state_device(h, p=p.data_ptr(), t=t.data_ptr())
+            ctx.hold = hold
+            ctx.m = m
+            return p, t
+
+        @staticmethod
+        def backward(ctx, gp, gt):
+            dev = gp.device if gp is not None else gt.device
+            gp = None if gp is None else gp.contiguous().to(torch.float64)
+            gt = None if gt is None else gt.contiguous().to(torch.float64)
+            m = ctx.m
+            dq = torch.empty((m, 4), dtype=torch.float64, device=dev)
+            dt = torch.empty((m, 3), dtype=torch.float64, device=dev)
+            dk = torch.empty((m,), dtype=torch.float64, device=dev)
+            do = torch.empty((m,), dtype=torch.float64, device=dev)
+            pradmm_adjoint_device(ctx.hold.h, 0 if gp is None else gp.data_ptr(), 0 if gt is None else gt.data_ptr(),
+                                  dq.data_ptr(), dt.data_ptr(), dk.data_ptr(), do.data_ptr())
+            return dq, dt, dk, do
+
+    m = int(q_meas.shape[0])
+    ones = None
+    if kappa is None or omega is None:
+        ones = torch.ones(m, dtype=torch.float64, device=q_meas.device)
+    return _Unrolled.apply(q_meas.contiguous(), t_meas.contiguous(), ones if kappa is None else kappa.contiguous(),
+                           ones if omega is None else omega.contiguous())

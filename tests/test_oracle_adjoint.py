@@ -13,42 +13,11 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle.anchor import _conj, _pure, _qmul, anchor_loss
 from paper_2601_15684_gb300 import synth
 
 H = 1e-6
 KEYS = ("p", "q", "t", "s", "lam", "z")
-
-
-def _qmul(a, b):
-    w1, x1, y1, z1 = np.moveaxis(a, -1, 0)
-    w2, x2, y2, z2 = np.moveaxis(b, -1, 0)
-    return np.stack([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
-                     w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2], -1)
-
-
-def _conj(a):
-    return a * np.array([1.0, -1.0, -1.0, -1.0])
-
-
-def _pure(v):
-    return np.concatenate([np.zeros(v.shape[:-1] + (1,)), v], -1)
-
-
-def anchor_loss(p, t, q_gt, t_gt):
-    """L = sum_i |R(p_0)^T (t_i - t_0) - R(q0_gt)^T (t_i_gt - t0_gt)|^2 with
-    R(p)^T v = Im(p^* v~ p): translations expressed in the frame of pose 0,
-    which removes the global gauge of Eq. (1).  Returns (L, dL/dp, dL/dt)."""
-    d = _qmul(_qmul(_conj(q_gt[0]), _pure(t_gt - t_gt[0])), q_gt[0])[:, 1:]
-    v = t - t[0]
-    y = _qmul(_qmul(_conj(p[0]), _pure(v)), p[0])[:, 1:] - d
-    L = float((y * y).sum())
-    Yb = _pure(2.0 * y)
-    gt = _qmul(_qmul(p[0], Yb), _conj(p[0]))[:, 1:]
-    dt = gt.copy()
-    dt[0] -= gt.sum(0)
-    dp = np.zeros_like(p)
-    dp[0] = (-2.0 * _qmul(_qmul(_pure(v), p[0]), Yb)).sum(0)
-    return L, dp, dt
 
 
 @pytest.fixture(scope="module")
