@@ -33,7 +33,9 @@ if ROOT not in sys.path:
 METRIC = "PRADMM edge-updates/s at 1M poses (% HBM roofline); batched & adjoint vs plain"
 UNIT = "edge-updates/s"
 WORKLOAD = "lattice1m"
-KERNEL_SRC = os.path.join(ROOT, "paper_2601_15684_gb300", "csrc", "pradmm_kernels.cu")
+# the sweep kernels and the per-vertex updates they run
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2601_15684_gb300", "csrc", f) for f in ("pradmm_kernels.cu",
+                                                                                  "pradmm_device.cuh")]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_sp_lattice1m.md")
 
 
@@ -54,6 +56,13 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def kernel_source_sha256() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SRCS:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
 def _traffic_from_profile():
     """Per-launch DRAM bytes of the dominant kernel from the committed ncu
     summary, if it was taken on the current kernel source."""
@@ -65,7 +74,7 @@ def _traffic_from_profile():
     m_traf = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     if not m_hash or not m_traf:
         return None, None
-    cur = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    cur = kernel_source_sha256()
     if cur != m_hash.group(1):
         return None, "stale"
     return float(m_traf.group(1)), "ncu"
@@ -181,6 +190,55 @@ def run_batched(P, sample=32):
             "plain": {"sample_graphs": int(len(pick)), "sample_time_s": t_plain, "estimated_total_s": plain_total,
                       "method": "plain solver, graph by graph, same iteration counts, scaled by edge-iterations"},
             "speedup_vs_plain": plain_total / t_batch, "objective_max_rel_diff_vs_plain": rel_F}
+
+
+def run_adjoint(P, K=200, ckpt=20, reps=5):
+    """Reverse mode vs the plain forward on the 10,000-pose walk (~30k edges):
+    K unrolled iterations from the odometry start, checkpoint every `ckpt`.
+    forward = K iterations (pradmm_step); record = the same iterations with
+    checkpoints (pradmm_adjoint_record); backward = pradmm_adjoint_device for
+    the anchor-pose loss's cotangent already on the device (recomputes the
+    segments and runs the reverse sweeps).  Medians of `reps` wall-clock runs,
+    each call synchronised."""
+    import torch
+    from paper_2601_15684_gb300 import synth
+    from paper_2601_15684_gb300.anchor import anchor_loss
+
+    g = synth.workload("walk10k")
+    dev = torch.device("cuda:0")
+    fwd, rec, bwd = [], [], []
+    with P.Solver(g, precision=P.PRADMM_FP32) as S:
+        for r in range(reps + 1):
+            S.init_odometry()
+            t0 = time.perf_counter()
+            S.step(K)
+            t1 = time.perf_counter()
+            S.init_odometry()
+            t2 = time.perf_counter()
+            S.adjoint_record(K, ckpt)
+            t3 = time.perf_counter()
+            if r == 0:
+                p, t = S.poses()
+                pt = torch.tensor(p, device=dev, requires_grad=True)
+                tt = torch.tensor(t, device=dev, requires_grad=True)
+                anchor_loss(pt, tt, torch.tensor(g.q_gt, device=dev), torch.tensor(g.t_gt, device=dev)).backward()
+                gp, gt = pt.grad.contiguous(), tt.grad.contiguous()
+                outs = [torch.empty(s, dtype=torch.float64, device=dev) for s in ((g.m, 4), (g.m, 3), (g.m,), (g.m,))]
+                torch.cuda.synchronize()
+            t4 = time.perf_counter()
+            P.pradmm_adjoint_device(S.h, gp.data_ptr(), gt.data_ptr(), *[o.data_ptr() for o in outs])
+            t5 = time.perf_counter()
+            if r > 0:  # the first round warms up
+                fwd.append(t1 - t0)
+                rec.append(t3 - t2)
+                bwd.append(t5 - t4)
+    f, rr, b = float(np.median(fwd)), float(np.median(rec)), float(np.median(bwd))
+    return {"workload": "walk10k: 10,000-pose random walk with 20,000 loop closures within 3 m, FP32 state",
+            "n": g.n, "m": g.m, "iterations": K, "ckpt_every": ckpt,
+            "forward_ms": 1e3 * f, "record_ms": 1e3 * rr, "backward_ms": 1e3 * b,
+            "forward_plus_backward_over_forward": (rr + b) / f,
+            "backward_edge_updates_per_s": g.m * K / b,
+            "loss": "anchor-pose translation loss; gradients w.r.t. q_e, t_e, kappa_e, omega_e"}
 
 
 def _workload():
@@ -358,6 +416,9 @@ def run_ours(args):
     batched = None
     if rank == 0 and ws == 1 and not args.no_batched:
         batched = run_batched(P)
+    adjoint = None
+    if rank == 0 and ws == 1 and not args.no_adjoint:
+        adjoint = run_adjoint(P)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = _cpu_baseline(g)
@@ -390,6 +451,8 @@ def run_ours(args):
     }
     if batched is not None:
         line["batched"] = batched
+    if adjoint is not None:
+        line["adjoint"] = adjoint
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
@@ -407,6 +470,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -5,6 +5,9 @@ few PRADMM iterations with plain stream launches (one kernel per launch,
 so `ncu -k regex:... -s ... -c ...` can pick single sweeps), then exits.
 
     python -m paper_2601_15684_gb300.prof_run --workload lattice1m --iters 12
+
+With --adjoint K it records K iterations (checkpoint every --ckpt) and runs
+the reverse sweeps once for a seeded cotangent.
 """
 from __future__ import annotations
 
@@ -20,6 +23,8 @@ def main(argv=None) -> int:
     ap.add_argument("--precision", type=int, default=1)
     ap.add_argument("--graph", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--adjoint", type=int, default=0)
+    ap.add_argument("--ckpt", type=int, default=20)
     a = ap.parse_args(argv)
     from paper_2601_15684_gb300 import build_lib, pradmm, synth
 
@@ -32,6 +37,15 @@ def main(argv=None) -> int:
         dt = time.perf_counter() - t0
         print(f"{a.workload}: n={g.n} m={g.m} iters={a.iters} e={e:.6e} wall={dt * 1e3:.2f} ms "
               f"bytes/iter={S.bytes_per_iteration()['total']:.4e}")
+        if a.adjoint > 0:
+            import numpy as np
+            rng = np.random.default_rng(0)
+            S.adjoint_record(a.adjoint, a.ckpt)
+            t0 = time.perf_counter()
+            out = S.adjoint(rng.normal(size=(g.n, 4)), rng.normal(size=(g.n, 3)))
+            dt = time.perf_counter() - t0
+            print(f"adjoint: iters={a.adjoint} ckpt={a.ckpt} wall={dt * 1e3:.2f} ms "
+                  f"|dL/dt_meas|={np.linalg.norm(out['t_meas']):.6e}")
     return 0
 
 
