@@ -87,12 +87,19 @@ typedef struct {
                             0: plain stream launches                               */
     int32_t block;       /* threads per CTA of the sweeps: 0 (default, 256) or a
                             multiple of 32 in [32, 256]                            */
+    int32_t l2_window;   /* 1: the sweep launches mark the vertex arrays they
+                            gather (t, s, q, both p buffers; one contiguous block)
+                            as persisting in L2, and the library sets aside that
+                            much L2 for the process while a handle using it
+                            lives (restored when the last one is destroyed);
+                            0: plain caching                                       */
+    int32_t reserved;    /* 0 */
 } pradmm_params;
 
 /* Defaults: beta1 = beta2 = 1, relax = 1.5, gamma = {1, 1e-3, 1e-3, 1e-3},
  * tol = 1e-4, max_iter = 300 (Section 5 settings; beta is not given in the
  * paper and is fixed here by a sweep on the 128-pose walk), FP32,
- * fallback_eps = 1e-6, use_graph = 1, block = 0. */
+ * fallback_eps = 1e-6, use_graph = 1, block = 0, l2_window = 1. */
 void pradmm_default_params(pradmm_params* prm);
 
 /* Builds a solver for one pose graph (Section 2): validates the edges
@@ -170,6 +177,10 @@ pradmm_status pradmm_counters(pradmm_t h, int64_t* out);
  * sweep needs, counted once per sweep):
  *   out[0] total, out[1] q/lambda sweep, out[2] t sweep, out[3] s/z + next p sweep. */
 pradmm_status pradmm_bytes_per_iteration(pradmm_t h, double* out);
+
+/* L2 persistence of the handle (params.l2_window): out[0] window bytes (0 if
+ * off), out[1] its hit ratio, out[2] the process's current L2 set-aside bytes. */
+pradmm_status pradmm_l2_window_info(pradmm_t h, double* out);
 
 /* Times `iters` iterations launched kernel by kernel on the handle's stream
  * with CUDA events around each sweep kernel; ms_out[0..2] receive the mean

@@ -12,6 +12,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "pradmm_internal.h"
@@ -84,6 +85,9 @@ struct pradmm_s {
     cudaGraphConditionalHandle cond = 0;
     bool graph_ready = false;
 
+    void* state_block = nullptr;       // t, s, q, p[0], p[1], lam, z: 28 n reals, contiguous
+    bool l2_on = false;                // this handle holds an L2 set-aside
+    cudaAccessPolicyWindow window{};   // persisting window over t, s, q, p[0], p[1]
     uint64_t epoch = 0;                // bumped by every change of the state
     std::vector<int32_t> out_edge;     // out-slot -> input edge
 
@@ -156,6 +160,8 @@ struct pradmm_s {
         L.part = part;
         L.cond = cond;
         L.has_cond = with_cond ? 1 : 0;
+        L.window = window;
+        L.has_window = l2_on ? 1 : 0;
         return L;
     }
 };
@@ -213,6 +219,7 @@ pradmm_status check_params(const pradmm_params* p) {
     if (p->precision != PRADMM_FP64 && p->precision != PRADMM_FP32)
         return fail(PRADMM_ERR_ARG, "precision must be PRADMM_FP64 or PRADMM_FP32");
     if (!(p->fallback_eps >= 0)) return fail(PRADMM_ERR_ARG, "fallback_eps must be >= 0");
+    if (p->l2_window != 0 && p->l2_window != 1) return fail(PRADMM_ERR_ARG, "l2_window must be 0 or 1");
     if (p->block != 0 && (p->block < 32 || p->block > 256 || p->block % 32 != 0))
         return fail(PRADMM_ERR_ARG, "block must be 0 (default) or a multiple of 32 in [32, 256]");
     return PRADMM_OK;
@@ -359,12 +366,19 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
     ST(dalloc(h, &h->te64, 3 * h->out_slots));
     ST(dalloc(h, &h->ka64, h->out_slots));
     ST(dalloc(h, &h->om64, h->out_slots));
-    for (int b = 0; b < 2; ++b) ST(valloc(h, &h->p[b], 4 * n));
-    ST(valloc(h, &h->q, 4 * n));
-    ST(valloc(h, &h->lam, 4 * n));
-    ST(valloc(h, &h->t, 4 * n));
-    ST(valloc(h, &h->s, 4 * n));
-    ST(valloc(h, &h->z, 4 * n));
+    // one block, gathered arrays first (the L2 persistence window covers them)
+    ST(valloc(h, &h->state_block, 28 * (size_t)n));
+    {
+        char* b = static_cast<char*>(h->state_block);
+        const size_t a = 4 * (size_t)n * h->rsize;
+        h->t = b;
+        h->s = b + a;
+        h->q = b + 2 * a;
+        h->p[0] = b + 3 * a;
+        h->p[1] = b + 4 * a;
+        h->lam = b + 5 * a;
+        h->z = b + 6 * a;
+    }
     ST(dalloc(h, &h->inv2_d, n));
     ST(dalloc(h, &h->inv3_d, n));
     ST(dalloc(h, &h->inv4_d, n));
@@ -420,7 +434,11 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
     return PRADMM_OK;
 }
 
+void l2_window_off(pradmm_s* h);
+
 void free_all(pradmm_s* h) {
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    l2_window_off(h);
     if (h->tape) cudaFree(h->tape);
     h->tape = nullptr;
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
@@ -429,6 +447,52 @@ void free_all(pradmm_s* h) {
     h->allocs.clear();
     if (h->ctrl_h) cudaFreeHost(h->ctrl_h);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+// ---- L2 persistence of the gathered vertex arrays ------------------------------
+// The set-aside (cudaLimitPersistingL2CacheSize) belongs to this process's
+// context; it is raised while at least one handle uses a window and put back
+// to its previous value when the last one is destroyed.
+std::mutex g_l2_mu;
+int g_l2_users = 0;
+size_t g_l2_prev = 0;
+
+void l2_window_on(pradmm_s* h, int dev) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return;
+    const size_t want = 20 * (size_t)h->n * h->rsize;  // t, s, q, p[0], p[1]
+    const size_t win = std::min(want, (size_t)std::max(prop.accessPolicyMaxWindowSize, 0));
+    const size_t aside = std::min(win, (size_t)std::max(prop.persistingL2CacheMaxSize, 0));
+    if (win == 0 || aside == 0) return;
+    std::lock_guard<std::mutex> lk(g_l2_mu);
+    if (g_l2_users == 0) {
+        if (cudaDeviceGetLimit(&g_l2_prev, cudaLimitPersistingL2CacheSize) != cudaSuccess) return;
+    }
+    size_t cur = 0;
+    if (cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize) != cudaSuccess) return;
+    if (cur < aside && cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, aside) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    size_t got = 0;
+    cudaDeviceGetLimit(&got, cudaLimitPersistingL2CacheSize);
+    h->window.base_ptr = h->state_block;
+    h->window.num_bytes = win;
+    h->window.hitRatio = (float)std::min(1.0, (double)std::max(got, (size_t)1) / (double)win);
+    h->window.hitProp = cudaAccessPropertyPersisting;
+    h->window.missProp = cudaAccessPropertyStreaming;
+    h->l2_on = true;
+    ++g_l2_users;
+}
+
+void l2_window_off(pradmm_s* h) {
+    if (!h->l2_on) return;
+    h->l2_on = false;
+    std::lock_guard<std::mutex> lk(g_l2_mu);
+    if (--g_l2_users == 0) {
+        cudaCtxResetPersistingL2Cache();
+        cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, g_l2_prev);
+    }
 }
 
 pradmm_status create_common(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const double* q_meas,
@@ -485,6 +549,7 @@ pradmm_status create_common(int64_t n, int64_t m, const int32_t* src, const int3
         }
         h->obj_grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * 4));
         st = build(h, src, dst, q_meas, t_meas, kappa, omega);
+        if (st == PRADMM_OK && p.l2_window) l2_window_on(h, dev);
     } while (0);
     if (st != PRADMM_OK) {
         free_all(h);
@@ -1043,6 +1108,8 @@ void pradmm_default_params(pradmm_params* p) {
     p->fallback_eps = 1e-6;
     p->use_graph = 1;
     p->block = 0;
+    p->l2_window = 1;
+    p->reserved = 0;
 }
 
 pradmm_status pradmm_create(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const double* q_meas,
@@ -1223,6 +1290,16 @@ pradmm_status pradmm_bytes_per_iteration(pradmm_t h, double* out) {
     out[2] = w * (14.0 * n + 5.0 * m);            // t-block
     out[3] = w * ((17.0 + 24.0) * n + (5.0 + 11.0) * m);  // s-block + z, then p-block
     out[0] = out[1] + out[2] + out[3];
+    return PRADMM_OK;
+}
+
+pradmm_status pradmm_l2_window_info(pradmm_t h, double* out) {
+    if (!h || !out) return fail(PRADMM_ERR_ARG, "handle or out is NULL");
+    size_t aside = 0;
+    cudaDeviceGetLimit(&aside, cudaLimitPersistingL2CacheSize);
+    out[0] = h->l2_on ? (double)h->window.num_bytes : 0.0;
+    out[1] = h->l2_on ? (double)h->window.hitRatio : 0.0;
+    out[2] = (double)aside;
     return PRADMM_OK;
 }
 
@@ -1415,7 +1492,14 @@ pradmm_status pradmm_batch_create(int32_t G, const int64_t* n_g, const int64_t* 
             }
         }
         pradmm_t h = nullptr;
-        pradmm_status st = create_common(n, m, us.data(), ud.data(), q_meas, t_meas, kappa, omega, prm, cuda_stream, &h);
+        pradmm_params bp;
+        if (prm) {
+            bp = *prm;
+        } else {
+            pradmm_default_params(&bp);
+        }
+        bp.l2_window = 0;  // the persistent batch kernel takes no access-policy window
+        pradmm_status st = create_common(n, m, us.data(), ud.data(), q_meas, t_meas, kappa, omega, &bp, cuda_stream, &h);
         if (st != PRADMM_OK) {
             delete b;
             return st;

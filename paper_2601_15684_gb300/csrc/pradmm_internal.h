@@ -82,6 +82,8 @@ struct Launch {
     double* part;             // 4 * pstride doubles
     cudaGraphConditionalHandle cond;
     int has_cond;
+    cudaAccessPolicyWindow window;  // L2 persistence of the gathered vertex arrays
+    int has_window;
 };
 
 template <typename R>

@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <utility>
 
 #include "pradmm_device.cuh"
 #include "pradmm_internal.h"
@@ -38,6 +39,14 @@
 #endif
 #ifndef PRADMM_MINB_Q
 #define PRADMM_MINB_Q 4
+#endif
+#ifndef PRADMM_MINB_T
+#define PRADMM_MINB_T 0
+#endif
+#if PRADMM_MINB_T > 0
+#define PRADMM_BOUNDS_T __launch_bounds__(256, PRADMM_MINB_T)
+#else
+#define PRADMM_BOUNDS_T __launch_bounds__(256)
 #endif
 
 namespace pradmm {
@@ -64,7 +73,7 @@ __global__ void __launch_bounds__(256, PRADMM_MINB_Q) k_q(GraphDev<R> g, StateDe
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) k_t(GraphDev<R> g, StateDev<R> S, Coef<R> c, Ctrl* ctrl, double* part,
+__global__ void PRADMM_BOUNDS_T k_t(GraphDev<R> g, StateDev<R> S, Coef<R> c, Ctrl* ctrl, double* part,
                                            int pstride) {
     __shared__ double sh[32];
     if (ctrl->halt) return;
@@ -229,25 +238,40 @@ inline int conv_grid(int64_t n) {
 
 }  // namespace
 
+// Sweep launch with the handle's L2 access-policy window as a launch
+// attribute (captured into the CUDA graph with the kernel node).
+template <typename... P, typename... A>
+cudaError_t launch_sweep(const Launch& L, int grid, void (*kern)(P...), A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)L.block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = L.stream;
+    cudaLaunchAttribute at[1];
+    if (L.has_window) {
+        at[0].id = cudaLaunchAttributeAccessPolicyWindow;
+        at[0].val.accessPolicyWindow = L.window;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
+
 template <typename R>
 cudaError_t launch_p(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const Launch& L) {
-    k_sp<R, false><<<L.grid_p, L.block, 0, L.stream>>>(g, s, c, L);
-    return cudaGetLastError();
+    return launch_sweep(L, L.grid_p, k_sp<R, false>, g, s, c, L);
 }
 template <typename R>
 cudaError_t launch_q(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const Launch& L) {
-    k_q<R><<<L.grid_q, L.block, 0, L.stream>>>(g, s, c, L.ctrl, L.part, L.pstride);
-    return cudaGetLastError();
+    return launch_sweep(L, L.grid_q, k_q<R>, g, s, c, L.ctrl, L.part, L.pstride);
 }
 template <typename R>
 cudaError_t launch_t(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const Launch& L) {
-    k_t<R><<<L.grid_t, L.block, 0, L.stream>>>(g, s, c, L.ctrl, L.part, L.pstride);
-    return cudaGetLastError();
+    return launch_sweep(L, L.grid_t, k_t<R>, g, s, c, L.ctrl, L.part, L.pstride);
 }
 template <typename R>
 cudaError_t launch_sp(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const Launch& L) {
-    k_sp<R, true><<<L.grid_sp, L.block, 0, L.stream>>>(g, s, c, L);
-    return cudaGetLastError();
+    return launch_sweep(L, L.grid_sp, k_sp<R, true>, g, s, c, L);
 }
 
 template <typename R>

@@ -35,7 +35,7 @@ class pradmm_params(ctypes.Structure):
     _fields_ = [("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("relax", ctypes.c_double),
                 ("gamma", ctypes.c_double * 4), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("fallback_eps", ctypes.c_double), ("use_graph", ctypes.c_int32),
-                ("block", ctypes.c_int32)]
+                ("block", ctypes.c_int32), ("l2_window", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class PRADMMError(RuntimeError):
@@ -75,6 +75,7 @@ _SIGS = {
     "pradmm_counters": (ctypes.c_int, [_h, _i64]),
     "pradmm_bytes_per_iteration": (ctypes.c_int, [_h, _d]),
     "pradmm_profile_sweeps": (ctypes.c_int, [_h, ctypes.c_int32, _d]),
+    "pradmm_l2_window_info": (ctypes.c_int, [_h, _d]),
     "pradmm_adjoint_record": (ctypes.c_int, [_h, ctypes.c_int32, ctypes.c_int32]),
     "pradmm_adjoint": (ctypes.c_int, [_h, _d, _d, _d, _d, _d, _d, _d]),
     "pradmm_adjoint_device": (ctypes.c_int, [_h] + [ctypes.c_void_p] * 7),
@@ -243,6 +244,12 @@ def pradmm_bytes_per_iteration(h) -> dict:
     out = np.zeros(4)
     _check(load().pradmm_bytes_per_iteration(h, _dp(out)), "pradmm_bytes_per_iteration")
     return {"total": out[0], "k_q": out[1], "k_t": out[2], "k_sp": out[3]}
+
+
+def pradmm_l2_window_info(h) -> dict:
+    out = np.zeros(3)
+    _check(load().pradmm_l2_window_info(h, _dp(out)), "pradmm_l2_window_info")
+    return {"window_bytes": out[0], "hit_ratio": out[1], "set_aside_bytes": out[2]}
 
 
 def pradmm_profile_sweeps(h, iters: int) -> dict:
