@@ -85,8 +85,9 @@ typedef struct {
     double fallback_eps; /* FP32: recompute u_i in FP64 when |u_i| < eps (beta1+gamma1) */
     int32_t use_graph;   /* 1: loop inside a CUDA graph with a device-side while node;
                             0: plain stream launches                               */
-    int32_t block;       /* threads per CTA of the sweeps: 0 (default, 256) or a
-                            multiple of 32 in [32, 256]                            */
+    int32_t block;       /* threads per CTA of the sweeps: a multiple of 32 in
+                            [32, 256], or 0: 256, halved (to 32 at least) while
+                            n / block is below half the number of SMs         */
     int32_t l2_window;   /* 1: the sweep launches mark the vertex arrays they
                             gather (t, s, q, both p buffers; one contiguous block)
                             as persisting in L2, and the library sets aside that

@@ -2,7 +2,7 @@
 //
 // Given the adjoint xbar^{k+1} of the state after iteration k (the map
 // x^k -> x^{k+1} of Eq. (3a)-(3f), Appendix B closed forms with scalar
-// Sigma), the four sweeps below produce xbar^k and add iteration k's share of
+// Sigma), the sweeps below produce xbar^k and add iteration k's share of
 // dL/dq_e, dL/dt_e, dL/dkappa_e, dL/domega_e.  The forward blocks run
 // p -> q -> t -> s -> (lambda, z); their adjoints run in the opposite order:
 //
@@ -11,8 +11,9 @@
 //   k_adj_q   c_e = Im(q_i t~_e p_i^*) and the q-block (3b): out-edges
 //   k_adj_p   p-block (3a) with the sphere projection p = u / |u|, whose
 //             adjoint is ubar = (I - p p^T) pbar / |u|: out- and in-edges
-//   k_adj_e   the p-block's edge terms, the measurement gradients of every
-//             block, and step A of the next (earlier) iteration
+//   k_adj_grad the measurement gradients of every block (one thread per edge)
+//   k_adj_v   the p-block's edge terms of the state adjoints, and step A of
+//             the next (earlier) iteration
 //
 // For a quaternion product V = a x b the adjoint of x is a^* Vbar b^*
 // (Lemma MW: M(a)^T = M(a^*), W(b)^T = W(b^*)), and a conjugated operand
@@ -265,96 +266,99 @@ __global__ void __launch_bounds__(256) k_adj_p(GraphDev<R> g, AdjDev<R> A, AdjSt
     }
 }
 
-// p-block edge terms, measurement gradients, and step A of iteration k-1.
-// Out-edges e = (i, j), r = t_j^k - s_i^k, c_e = Im(q_i^{k+1} t~_e p_i^{k+1*}):
-//   qbar_i += 2 k_e ub_j q_e^* + 2 w_e r~ ub_i t~_e^*
-//   sbar_i += 2 w_e Im(ub_i (q_i t~_e)^*)
+// Measurement gradients of iteration k, one thread per out-slot e = (i, j)
+// (r = t_j^k - s_i^k, c_e = Im(q_i^{k+1} t~_e p_i^{k+1*}), h = [0, 2 w_e (gt_j - gs_i)]):
 //   dL/dw_e += 2 (t_j^{k+1} - c_e).gs_i + 2 A_4bar_i + 2 (s_i + c_e).gt_j + 2 A_3bar_j
 //              + 2 gq_i.(r~ p_i t~_e^*) + 2 |t_e|^2 A_2bar_i + 2 ub_i.(r~^* q_i t~_e)
 //   dL/dk_e += 2 gq_i.(p_j q_e^*) + 2 |q_e|^2 A_2bar_i + 2 ub_j.(q_i q_e)
 //   dL/dt_e += Im(q_i^{k+1*} h p_i) + 2 w_e Im(gq_i^* r~ p_i) + 4 w_e A_2bar_i t_e
 //              + 2 w_e Im(q_i^* r~ ub_i)
 //   dL/dq_e += 2 k_e gq_i^* p_j + 4 k_e A_2bar_i q_e + 2 k_e q_i^* ub_j
-// In-edges e = (l, i): tbar_i -= 2 w_e Im(ub_l (q_l t~_e)^*).
+// Each slot has one writer; the sums over iterations are FP64.
 template <typename R>
-__global__ void __launch_bounds__(256) k_adj_e(GraphDev<R> g, AdjDev<R> A, AdjStep<R> X, Coef<R> c, int more) {
-    VERTEX_LOOP(g.n) {
-        const Q<R> qi = ldq(X.q, i);
-        const R4<R> sr = IO<R>::ld(X.s, i);
-        const V3<R> si = v3(sr);
-        const Q<R> P = ldq(X.pn, i), Qn = ldq(X.qn, i), gq = ldq(A.gq, i), ub = ldq(A.ub, i);
+__global__ void __launch_bounds__(256) k_adj_grad(GraphDev<R> g, AdjDev<R> A, AdjStep<R> X, const int32_t* __restrict__ out_src) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < g.m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = out_src[e], j = g.out_idx[e];
+        const R4<R> te = IO<R>::ld(g.out_te, e);
+        const V3<R> tv = {te.a, te.b, te.c};
+        const R w = te.d, w2 = R(2) * te.d;
+        const Q<R> qe = ldq(A.eq, e);
+        const R ka = A.ek[e];
+        const Q<R> qi = ldq(X.q, i), P = ldq(X.pn, i), Qn = ldq(X.qn, i), gq = ldq(A.gq, i), ub = ldq(A.ub, i);
+        const V3<R> si = v3(IO<R>::ld(X.s, i));
         const R4<R> gsr = IO<R>::ld(A.gs, i);
         const V3<R> gs = v3(gsr);
         const R a4b = gsr.d, a2b = A.a2b[i];
+        const V3<R> tj = v3(IO<R>::ld(X.t, j));
+        const V3<R> tnj = v3(IO<R>::ld(X.tn, j));
+        const Q<R> Pj = ldq(X.pn, j), ubj = ldq(A.ub, j);
+        const R4<R> gtr = IO<R>::ld(A.gt, j);
+        const V3<R> gt = v3(gtr);
+        const V3<R> r = {tj.x - si.x, tj.y - si.y, tj.z - si.z};
+        R cx, cy, cz;
+        im_rot(Qn, te.a, te.b, te.c, P, cx, cy, cz);
+        const V3<R> ce = {cx, cy, cz};
+        const V3<R> h = {w2 * (gt.x - gs.x), w2 * (gt.y - gs.y), w2 * (gt.z - gs.z)};
+        const Q<R> rpt = pr(pl(r, P), tv);   // r~ p t~ = -(r~ p t~^*)
+        const Q<R> rqt = pr(pl(r, qi), tv);  // r~ q t~ = -(r~^* q t~)
+        const V3<R> tmc = {tnj.x - ce.x, tnj.y - ce.y, tnj.z - ce.z};
+        const V3<R> spc = {si.x + ce.x, si.y + ce.y, si.z + ce.z};
+        const R tn2 = vdot(tv, tv), qn2 = qdot(qe, qe);
+        const R dw = R(2) * vdot(tmc, gs) + R(2) * a4b + R(2) * vdot(spc, gt) + R(2) * gtr.d -
+                     R(2) * qdot(gq, rpt) + R(2) * tn2 * a2b - R(2) * qdot(ub, rqt);
+        const R dk = R(2) * qdot(gq, qmul_c(Pj, qe)) + R(2) * qn2 * a2b + R(2) * qdot(ubj, qmul(qi, qe));
+        const V3<R> t1 = im(qmul(qconj(Qn), pl(h, P)));
+        const V3<R> t2 = im(qmul(qconj(gq), pl(r, P)));
+        const V3<R> t3 = im(qmul(qconj(qi), pl(r, ub)));
+        const R f2 = R(4) * w * a2b;
+        const Q<R> m1 = qmul(qconj(gq), Pj), m3 = qmul(qconj(qi), ubj);
+        const R k2 = R(2) * ka, f4 = R(4) * ka * a2b;
+        double* gte = A.g_te + 4 * e;
+        double* gqe = A.g_qe + 4 * e;
+        gte[0] += double(t1.x + w2 * (t2.x + t3.x) + f2 * tv.x);
+        gte[1] += double(t1.y + w2 * (t2.y + t3.y) + f2 * tv.y);
+        gte[2] += double(t1.z + w2 * (t2.z + t3.z) + f2 * tv.z);
+        gte[3] += double(dw);
+        gqe[0] += double(k2 * (m1.w + m3.w) + f4 * qe.w);
+        gqe[1] += double(k2 * (m1.x + m3.x) + f4 * qe.x);
+        gqe[2] += double(k2 * (m1.y + m3.y) + f4 * qe.y);
+        gqe[3] += double(k2 * (m1.z + m3.z) + f4 * qe.z);
+        A.g_ka[e] += double(dk);
+    }
+}
+
+// p-block edge terms of the state adjoints, then step A of iteration k-1.
+// Out-edges e = (i, j), r = t_j^k - s_i^k:
+//   qbar_i += 2 k_e ub_j q_e^* + 2 w_e r~ ub_i t~_e^*,  sbar_i += 2 w_e Im(ub_i (q_i t~_e)^*)
+// In-edges e = (l, i): tbar_i -= 2 w_e Im(ub_l (q_l t~_e)^*).
+template <typename R>
+__global__ void __launch_bounds__(256) k_adj_v(GraphDev<R> g, AdjDev<R> A, AdjStep<R> X, Coef<R> c, int more) {
+    VERTEX_LOOP(g.n) {
+        const Q<R> qi = ldq(X.q, i), ub = ldq(A.ub, i);
+        const V3<R> si = v3(IO<R>::ld(X.s, i));
         Q<R> oq = ldq(A.oq, i);
         V3<R> os = v3(IO<R>::ld(A.os, i)), ot = v3(IO<R>::ld(A.ot, i));
-        const Q<R> qnc = qconj(Qn), gqc = qconj(gq), qic = qconj(qi);
         for (int e = g.out_ptr[i]; e < g.out_ptr[i + 1]; ++e) {
             const int j = g.out_idx[e];
             const R4<R> te = IO<R>::ld(g.out_te, e);
             const V3<R> tv = {te.a, te.b, te.c};
-            const R w = te.d, w2 = R(2) * te.d;
-            const Q<R> qe = ldq(A.eq, e);
-            const R ka = A.ek[e];
+            const R w2 = R(2) * te.d;
             const V3<R> tj = v3(IO<R>::ld(X.t, j));
-            const V3<R> tnj = v3(IO<R>::ld(X.tn, j));
-            const Q<R> Pj = ldq(X.pn, j);
-            const R4<R> gtr = IO<R>::ld(A.gt, j);
-            const V3<R> gt = v3(gtr);
-            const Q<R> ubj = ldq(A.ub, j);
             const V3<R> r = {tj.x - si.x, tj.y - si.y, tj.z - si.z};
-            // state adjoints
-            axpy(oq, R(2) * ka, qmul_c(ubj, qe));
+            axpy(oq, R(2) * A.ek[e], qmul_c(ldq(A.ub, j), ldq(A.eq, e)));
             axpy(oq, -w2, pr(pl(r, ub), tv));  // r~ ub t~^* = -r~ ub t~
-            const V3<R> a = im(qmul_c(ub, pr(qi, tv)));
-            vaxpy(os, w2, a);
-            // measurement gradients
-            R cx, cy, cz;
-            im_rot(Qn, te.a, te.b, te.c, P, cx, cy, cz);
-            const V3<R> ce = {cx, cy, cz};
-            const V3<R> h = {w2 * (gt.x - gs.x), w2 * (gt.y - gs.y), w2 * (gt.z - gs.z)};
-            const Q<R> rpt = pr(pl(r, P), tv);  // r~ p t~ = -(r~ p t~^*)
-            const Q<R> rqt = pr(pl(r, qi), tv); // r~ q t~ = -(r~^* q t~)
-            const V3<R> tmc = {tnj.x - ce.x, tnj.y - ce.y, tnj.z - ce.z};
-            const V3<R> spc = {si.x + ce.x, si.y + ce.y, si.z + ce.z};
-            const R tn2 = vdot(tv, tv), qn2 = qdot(qe, qe);
-            const R dw = R(2) * vdot(tmc, gs) + R(2) * a4b + R(2) * vdot(spc, gt) + R(2) * gtr.d -
-                         R(2) * qdot(gq, rpt) + R(2) * tn2 * a2b - R(2) * qdot(ub, rqt);
-            const R dk = R(2) * qdot(gq, qmul_c(Pj, qe)) + R(2) * qn2 * a2b + R(2) * qdot(ubj, qmul(qi, qe));
-            const V3<R> t1 = im(qmul(qnc, pl(h, P)));
-            const V3<R> t2 = im(qmul(gqc, pl(r, P)));
-            const V3<R> t3 = im(qmul(qic, pl(r, ub)));
-            const R f2 = R(4) * w * a2b;
-            const V3<R> dt = {t1.x + w2 * (t2.x + t3.x) + f2 * tv.x, t1.y + w2 * (t2.y + t3.y) + f2 * tv.y,
-                              t1.z + w2 * (t2.z + t3.z) + f2 * tv.z};
-            const Q<R> m1 = qmul(gqc, Pj), m3 = qmul(qic, ubj);
-            const R k2 = R(2) * ka, f4 = R(4) * ka * a2b;
-            const Q<R> dq = {k2 * (m1.w + m3.w) + f4 * qe.w, k2 * (m1.x + m3.x) + f4 * qe.x,
-                             k2 * (m1.y + m3.y) + f4 * qe.y, k2 * (m1.z + m3.z) + f4 * qe.z};
-            double* gte = A.g_te + 4 * (int64_t)e;
-            double* gqe = A.g_qe + 4 * (int64_t)e;
-            gte[0] += double(dt.x);
-            gte[1] += double(dt.y);
-            gte[2] += double(dt.z);
-            gte[3] += double(dw);
-            gqe[0] += double(dq.w);
-            gqe[1] += double(dq.x);
-            gqe[2] += double(dq.y);
-            gqe[3] += double(dq.z);
-            A.g_ka[e] += double(dk);
+            vaxpy(os, w2, im(qmul_c(ub, pr(qi, tv))));
         }
         for (int e = g.in_ptr[i]; e < g.in_ptr[i + 1]; ++e) {
             const int l = g.in_idx[e];
             const R4<R> te = IO<R>::ld(g.in_te, e);
             const V3<R> tv = {te.a, te.b, te.c};
-            const V3<R> a = im(qmul_c(ldq(A.ub, l), pr(ldq(X.q, l), tv)));
-            vaxpy(ot, R(-2) * te.d, a);
+            vaxpy(ot, R(-2) * te.d, im(qmul_c(ldq(A.ub, l), pr(ldq(X.q, l), tv))));
         }
-        const Q<R> op = ldq(A.op, i), ol = ldq(A.ol, i);
-        const V3<R> oz = v3(IO<R>::ld(A.oz, i));
         if (more) {
             // xbar^k is the xbar^{k+1} of iteration k-1, whose s^{k+1} is s^k here
-            step_a<R>(A, c, i, op, oq, ot, os, ol, oz, si, IO<R>::ld(X.z, i).d);
+            step_a<R>(A, c, i, ldq(A.op, i), oq, ot, os, ldq(A.ol, i), v3(IO<R>::ld(A.oz, i)), si,
+                      IO<R>::ld(X.z, i).d);
         } else {
             stq(A.oq, i, oq);
             stv(A.os, i, os, R(0));
@@ -410,19 +414,20 @@ int grid_for(int64_t n, int block) {
 
 template <typename R>
 cudaError_t launch_adj_seed(const GraphDev<R>& g, const AdjDev<R>& A, const Coef<R>& c, const R* s_K, const R* z_K,
-                            cudaStream_t st) {
-    k_adj_seed<R><<<grid_for(g.n, 256), 256, 0, st>>>(g, A, c, s_K, z_K);
+                            int block, cudaStream_t st) {
+    k_adj_seed<R><<<grid_for(g.n, block), block, 0, st>>>(g, A, c, s_K, z_K);
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_adj_iteration(const GraphDev<R>& g, const AdjDev<R>& A, const AdjStep<R>& X, const Coef<R>& c,
-                                 int more, cudaStream_t st) {
-    const int grid = grid_for(g.n, 256);
-    k_adj_t<R><<<grid, 256, 0, st>>>(g, A, X, c);
-    k_adj_q<R><<<grid, 256, 0, st>>>(g, A, X, c);
-    k_adj_p<R><<<grid, 256, 0, st>>>(g, A, X, c);
-    k_adj_e<R><<<grid, 256, 0, st>>>(g, A, X, c, more);
+                                 const int32_t* out_src, int more, int block, cudaStream_t st) {
+    const int grid = grid_for(g.n, block);
+    k_adj_t<R><<<grid, block, 0, st>>>(g, A, X, c);
+    k_adj_q<R><<<grid, block, 0, st>>>(g, A, X, c);
+    k_adj_p<R><<<grid, block, 0, st>>>(g, A, X, c);
+    if (g.m > 0) k_adj_grad<R><<<grid_for(g.m, 256), 256, 0, st>>>(g, A, X, out_src);
+    k_adj_v<R><<<grid, block, 0, st>>>(g, A, X, c, more);
     return cudaGetLastError();
 }
 
@@ -448,9 +453,9 @@ cudaError_t launch_tape_arm(Ctrl* ctrl, long long iter, cudaStream_t st) {
 
 #define PRADMM_ADJ_INST(R)                                                                                           \
     template cudaError_t launch_adj_seed<R>(const GraphDev<R>&, const AdjDev<R>&, const Coef<R>&, const R*, const R*, \
-                                            cudaStream_t);                                                         \
+                                            int, cudaStream_t);                                                    \
     template cudaError_t launch_adj_iteration<R>(const GraphDev<R>&, const AdjDev<R>&, const AdjStep<R>&,             \
-                                                 const Coef<R>&, int, cudaStream_t);                               \
+                                                 const Coef<R>&, const int32_t*, int, int, cudaStream_t);          \
     template cudaError_t launch_adj_edges<R>(const double*, const double*, int64_t, R*, R*, cudaStream_t);
 
 PRADMM_ADJ_INST(float)

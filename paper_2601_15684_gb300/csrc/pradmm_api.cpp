@@ -90,6 +90,7 @@ struct pradmm_s {
     cudaAccessPolicyWindow window{};   // persisting window over t, s, q, p[0], p[1]
     uint64_t epoch = 0;                // bumped by every change of the state
     std::vector<int32_t> out_edge;     // out-slot -> input edge
+    std::vector<int32_t> out_src;      // out-slot -> tail (internal id)
 
     // reverse mode: checkpoints + recompute slots, 28 n reals per slot
     void* tape = nullptr;
@@ -101,8 +102,11 @@ struct pradmm_s {
     void* adj = nullptr;               // per-vertex adjoint arrays + per-slot q_e, kappa_e
     double* adj_g = nullptr;           // 9 m: per-slot gradients
     int32_t* out_edge_d = nullptr;
+    int32_t* out_src_d = nullptr;
     double* adj_stage = nullptr;       // max(9 m, 21 n) doubles
     Ctrl* tape_ctrl = nullptr;
+    cudaGraphExec_t adj_exec = nullptr;  // reverse pass of the current tape geometry
+    long long adj_key[5] = {0, 0, 0, 0, 0};
 
     template <typename R>
     pradmm::GraphDev<R> gdev() const {
@@ -333,6 +337,9 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
     h->out_slots = (int64_t)so.idx.size();
     h->in_slots = (int64_t)si.idx.size();
     h->out_edge.assign(so.edge.begin(), so.edge.end());
+    h->out_src.assign(h->out_slots, 0);
+    for (int64_t i = 0; i < n; ++i)
+        for (int32_t k = so.ptr[i]; k < so.ptr[i + 1]; ++k) h->out_src[k] = (int32_t)i;
     // ---- iteration-invariant scalar block matrices (Appendix B, scalar Sigma) ----
     std::vector<double> A2(n, h->prm.beta1 + h->prm.gamma[1]), A3(n, h->prm.beta2 + h->prm.gamma[2]),
         A4(n, h->prm.beta2 + h->prm.gamma[3]);
@@ -438,6 +445,8 @@ void l2_window_off(pradmm_s* h);
 
 void free_all(pradmm_s* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->adj_exec) cudaGraphExecDestroy(h->adj_exec);
+    h->adj_exec = nullptr;
     l2_window_off(h);
     if (h->tape) cudaFree(h->tape);
     h->tape = nullptr;
@@ -533,8 +542,18 @@ pradmm_status create_common(int64_t n, int64_t m, const int32_t* src, const int3
         }
         int dev = 0, sms = 0, bps[4] = {0, 0, 0, 0};
         if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
-            (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
-            (e = pradmm::sweep_occupancy(h->fp64 ? 1 : 0, h->block, bps)) != cudaSuccess) {
+            (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) {
+            st = fail(PRADMM_ERR_CUDA, "device query: %s", cudaGetErrorString(e));
+            break;
+        }
+        if (p.block == 0) {
+            // default: 256 threads, halved (down to one warp) while a thread per
+            // vertex gives fewer CTAs than half the SMs, so a small graph spreads
+            // over the GPU (measured on a 10,000-pose walk: 128 threads beat
+            // 256, 64 and 32 for both the forward and the reverse sweeps)
+            while (h->block > 32 && 2 * ((n + h->block - 1) / h->block) < sms) h->block /= 2;
+        }
+        if ((e = pradmm::sweep_occupancy(h->fp64 ? 1 : 0, h->block, bps)) != cudaSuccess) {
             st = fail(PRADMM_ERR_CUDA, "device query: %s", cudaGetErrorString(e));
             break;
         }
@@ -954,10 +973,13 @@ pradmm_status ensure_adjoint(pradmm_s* h) {
         ST(valloc(h, &h->adj, 13 * 4 * (size_t)n + (size_t)pad4(n) + 4 * (size_t)m + (size_t)m));
         ST(dalloc(h, &h->adj_g, 9 * (size_t)m));
         ST(dalloc(h, &h->out_edge_d, (size_t)m));
+        ST(dalloc(h, &h->out_src_d, (size_t)m));
         ST(dalloc(h, &h->adj_stage, std::max<size_t>(9 * (size_t)m, 21 * (size_t)n)));
         ST(dalloc(h, &h->tape_ctrl, 1));
-        if (m > 0)
+        if (m > 0) {
             CU(cudaMemcpy(h->out_edge_d, h->out_edge.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
+            CU(cudaMemcpy(h->out_src_d, h->out_src.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
+        }
         R* b = static_cast<R*>(h->adj);
         R* eq = b + 13 * 4 * n + pad4(n);
         CU(pradmm::launch_adj_edges<R>(h->qe64, h->ka64, m, eq, eq + 4 * m, h->stream));
@@ -982,6 +1004,90 @@ pradmm::AdjDev<R> adj_dev(pradmm_s* h) {
     return A;
 }
 
+// Seed + every segment (recompute from its checkpoint, then the reverse
+// sweeps from its last iteration back to its first), in stream order.
+template <typename R>
+cudaError_t enqueue_reverse(pradmm_s* h, const pradmm::AdjDev<R>& A) {
+    const int64_t n = h->n;
+    cudaStream_t st = h->stream;
+    const auto g = h->gdev<R>();
+    const auto c = h->coef<R>();
+    const int K = h->tape_K, C = h->tape_C, nck = h->tape_nck;
+    cudaError_t e;
+#define RQ(call)                            \
+    do {                                    \
+        if ((e = (call)) != cudaSuccess) return e; \
+    } while (0)
+    const auto SK = slot_state<R>(tape_slot(h, nck - 1), n);
+    RQ(pradmm::launch_adj_seed<R>(g, A, c, SK.s, SK.z, h->block, st));
+    const int64_t seg0 = nck;  // first recompute slot
+    pradmm::Launch L = h->launch(false);
+    L.ctrl = h->tape_ctrl;
+    for (int ci = nck - 2; ci >= 0; --ci) {
+        const long long kc = h->tape_k0 + (long long)ci * C;
+        const int len = std::min(C, K - ci * C);
+        std::vector<void*> slot(len + 1);
+        slot[0] = tape_slot(h, ci);
+        slot[len] = tape_slot(h, ci + 1);
+        for (int j = 1; j < len; ++j) slot[j] = tape_slot(h, seg0 + j - 1);
+        if (len > 1) {
+            RQ(pradmm::launch_tape_arm(h->tape_ctrl, kc, st));
+            for (int j = 0; j + 1 < len; ++j) {
+                RQ(cudaMemcpyAsync(slot[j + 1], slot[j], slot_bytes(h), cudaMemcpyDeviceToDevice, st));
+                const auto S = slot_state<R>(slot[j + 1], n);
+                RQ(pradmm::launch_q<R>(g, S, c, L));
+                RQ(pradmm::launch_t<R>(g, S, c, L));
+                RQ(pradmm::launch_sp<R>(g, S, c, L));
+            }
+        }
+        for (int j = len - 1; j >= 0; --j) {
+            const long long k = kc + j;
+            const auto S0 = slot_state<R>(slot[j], n);
+            const auto S1 = slot_state<R>(slot[j + 1], n);
+            pradmm::AdjStep<R> X;
+            X.pc = S0.p[k & 1];
+            X.pn = S0.p[(k + 1) & 1];
+            X.q = S0.q;
+            X.lam = S0.lam;
+            X.t = S0.t;
+            X.s = S0.s;
+            X.z = S0.z;
+            X.qn = S1.q;
+            X.tn = S1.t;
+            RQ(pradmm::launch_adj_iteration<R>(g, A, X, c, h->out_src_d, (ci == 0 && j == 0) ? 0 : 1, h->block, st));
+        }
+    }
+#undef RQ
+    return cudaSuccess;
+}
+
+// The reverse pass captured once as a CUDA graph and kept while the tape's
+// geometry (parity of k0, K, ckpt spacing, tape memory) is unchanged: a new
+// recording of the same shape, as in a training loop, reuses it.
+template <typename R>
+pradmm_status ensure_reverse_graph(pradmm_s* h, const pradmm::AdjDev<R>& A) {
+    const long long key[5] = {h->tape_k0 & 1, h->tape_K, h->tape_C, h->tape_nck, (long long)(uintptr_t)h->tape};
+    if (h->adj_exec && std::equal(key, key + 5, h->adj_key)) return PRADMM_OK;
+    if (h->adj_exec) {
+        cudaGraphExecDestroy(h->adj_exec);
+        h->adj_exec = nullptr;
+    }
+    CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    const cudaError_t e1 = enqueue_reverse<R>(h, A);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
+    CU(e1);
+    CU(e2);
+    const cudaError_t e3 = cudaGraphInstantiate(&h->adj_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e3 != cudaSuccess) {
+        h->adj_exec = nullptr;
+        CU(e3);
+    }
+    std::copy(key, key + 5, h->adj_key);
+    return PRADMM_OK;
+}
+
 template <typename R>
 pradmm_status adjoint_impl(pradmm_s* h, const double* p_bar, const double* t_bar, double* qe_bar, double* te_bar,
                            double* ka_bar, double* om_bar, double* x0_bar, bool device) {
@@ -990,8 +1096,6 @@ pradmm_status adjoint_impl(pradmm_s* h, const double* p_bar, const double* t_bar
     ST(ensure_adjoint<R>(h));
     const int64_t n = h->n, m = h->out_slots;
     cudaStream_t st = h->stream;
-    const auto g = h->gdev<R>();
-    const auto c = h->coef<R>();
     const pradmm::AdjDev<R> A = adj_dev<R>(h);
     // cotangent of x^K: pbar -> op, tbar -> ot (internal order)
     const double* pb = h->zeros;
@@ -1015,48 +1119,15 @@ pradmm_status adjoint_impl(pradmm_s* h, const double* p_bar, const double* t_bar
     CU(pradmm::launch_pack4<R>(pb, h->perm_d, A.op, n, st));
     CU(pradmm::launch_pack3<R>(tb, h->perm_d, h->zeros, A.ot, n, st));
     CU(cudaMemsetAsync(h->adj_g, 0, sizeof(double) * 9 * (size_t)m, st));
-    const int K = h->tape_K, C = h->tape_C, nck = h->tape_nck;
+    const int K = h->tape_K;
     if (K == 0) {
         for (R* a : {A.oq, A.os, A.ol, A.oz}) CU(cudaMemsetAsync(a, 0, 4 * (size_t)n * sizeof(R), st));
     } else {
-        const auto SK = slot_state<R>(tape_slot(h, nck - 1), n);
-        CU(pradmm::launch_adj_seed<R>(g, A, c, SK.s, SK.z, st));
-        const int64_t seg0 = nck;  // first recompute slot
-        pradmm::Launch L = h->launch(false);
-        L.ctrl = h->tape_ctrl;
-        for (int ci = nck - 2; ci >= 0; --ci) {
-            const long long kc = h->tape_k0 + (long long)ci * C;
-            const int len = std::min(C, K - ci * C);
-            std::vector<void*> slot(len + 1);
-            slot[0] = tape_slot(h, ci);
-            slot[len] = tape_slot(h, ci + 1);
-            for (int j = 1; j < len; ++j) slot[j] = tape_slot(h, seg0 + j - 1);
-            if (len > 1) {
-                CU(pradmm::launch_tape_arm(h->tape_ctrl, kc, st));
-                for (int j = 0; j + 1 < len; ++j) {
-                    CU(cudaMemcpyAsync(slot[j + 1], slot[j], slot_bytes(h), cudaMemcpyDeviceToDevice, st));
-                    const auto S = slot_state<R>(slot[j + 1], n);
-                    CU(pradmm::launch_q<R>(g, S, c, L));
-                    CU(pradmm::launch_t<R>(g, S, c, L));
-                    CU(pradmm::launch_sp<R>(g, S, c, L));
-                }
-            }
-            for (int j = len - 1; j >= 0; --j) {
-                const long long k = kc + j;
-                const auto S0 = slot_state<R>(slot[j], n);
-                const auto S1 = slot_state<R>(slot[j + 1], n);
-                pradmm::AdjStep<R> X;
-                X.pc = S0.p[k & 1];
-                X.pn = S0.p[(k + 1) & 1];
-                X.q = S0.q;
-                X.lam = S0.lam;
-                X.t = S0.t;
-                X.s = S0.s;
-                X.z = S0.z;
-                X.qn = S1.q;
-                X.tn = S1.t;
-                CU(pradmm::launch_adj_iteration<R>(g, A, X, c, (ci == 0 && j == 0) ? 0 : 1, st));
-            }
+        if (h->prm.use_graph) {
+            ST(ensure_reverse_graph<R>(h, A));
+            CU(cudaGraphLaunch(h->adj_exec, st));
+        } else {
+            CU(enqueue_reverse<R>(h, A));
         }
     }
     // measurement gradients in the caller's edge order

@@ -190,11 +190,12 @@ struct AdjStep {
 
 template <typename R>
 cudaError_t launch_adj_seed(const GraphDev<R>& g, const AdjDev<R>& A, const Coef<R>& c, const R* s_K, const R* z_K,
-                            cudaStream_t st);
-// The four reverse sweeps of iteration k; `more` = 1 starts iteration k-1.
+                            int block, cudaStream_t st);
+// The reverse sweeps of iteration k (out_src: tail of each out-slot); `more`
+// = 1 starts iteration k-1.
 template <typename R>
 cudaError_t launch_adj_iteration(const GraphDev<R>& g, const AdjDev<R>& A, const AdjStep<R>& X, const Coef<R>& c,
-                                 int more, cudaStream_t st);
+                                 const int32_t* out_src, int more, int block, cudaStream_t st);
 template <typename R>
 cudaError_t launch_adj_edges(const double* qe64, const double* ka64, int64_t m, R* eq, R* ek, cudaStream_t st);
 cudaError_t launch_adj_scatter(const double* g_qe, const double* g_te, const double* g_ka, const int32_t* eidx,

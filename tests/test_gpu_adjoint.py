@@ -204,3 +204,29 @@ def test_adjoint_full_size_walk10k_fp32(P):
         got = S.adjoint(dp, dt)
     for key in GRADS:
         assert relerr(got[key], ref[key]) <= 1e-3, (key, relerr(got[key], ref[key]))
+
+
+def test_reverse_graph_is_reused_and_matches_plain_launches(P):
+    # the reverse pass is captured once per tape geometry; a second recording
+    # of the same shape from another state reuses the graph
+    g = synth.random_graph(180, 500, seed=21)
+    st1 = synth.random_state(np.random.default_rng(11), g.n)
+    st2 = synth.random_state(np.random.default_rng(12), g.n)
+    pb, tb = _cotangent(g.n, 9)
+    outs = {}
+    for use_graph in (1, 0):
+        with P.Solver(g, precision=1, use_graph=use_graph) as S:
+            res = []
+            for st in (st1, st2, st1):
+                S.set_state_full(st)
+                S.adjoint_record(17, 5)
+                res.append(S.adjoint(pb, tb, x0=True))
+            outs[use_graph] = res
+    for a, b in zip(outs[1], outs[0]):
+        for key in GRADS:
+            np.testing.assert_array_equal(a[key], b[key])
+        for key in KEYS:
+            np.testing.assert_array_equal(a["x0"][key], b["x0"][key])
+    for key in GRADS:
+        np.testing.assert_array_equal(outs[1][0][key], outs[1][2][key])
+        assert not np.array_equal(outs[1][0][key], outs[1][1][key])
