@@ -186,7 +186,8 @@ def run_batched(P, sample=32):
             "rel_tol": rel_tol, "max_iter": max_iter, "time_s": t_batch, "graphs_per_s": len(graphs) / t_batch,
             "edge_updates_per_s": float(work.sum()) / t_batch, "iters_mean": float(res["iters"].mean()),
             "iters_max": int(res["iters"].max()), "converged_fraction": float((res["status"] == 0).mean()),
-            "schedule": {"block": schedule[0], "warp_max_n": schedule[1], "autotuned": True},
+            "schedule": {"block": schedule[0], "warp_max_n": schedule[1], "cluster": schedule[2],
+                         "cluster_min_n": schedule[3], "autotuned": True},
             "plain": {"sample_graphs": int(len(pick)), "sample_time_s": t_plain, "estimated_total_s": plain_total,
                       "method": "plain solver, graph by graph, same iteration counts, scaled by edge-iterations"},
             "speedup_vs_plain": plain_total / t_batch, "objective_max_rel_diff_vs_plain": rel_F}

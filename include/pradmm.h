@@ -278,7 +278,7 @@ typedef struct pradmm_batch_s* pradmm_batch_t;
 /* G graphs; graph g has n_g[g] >= 1 vertices and m_g[g] >= 0 edges.  Edge
  * arrays are concatenated in graph order with GRAPH-LOCAL endpoints in
  * [0, n_g[g]); layouts and validation as pradmm_create.  The schedule starts
- * at block 256, warp_max_n 256. */
+ * at block 256, warp_max_n 256, no clusters. */
 pradmm_status pradmm_batch_create(int32_t G, const int64_t* n_g, const int64_t* m_g, const int32_t* src,
                                   const int32_t* dst, const double* q_meas, const double* t_meas,
                                   const double* kappa, const double* omega, const pradmm_params* prm,
@@ -286,15 +286,27 @@ pradmm_status pradmm_batch_create(int32_t G, const int64_t* n_g, const int64_t* 
 
 /* Schedule: `block` threads per CTA of the persistent kernel (64, 128, 256,
  * 512); graphs with at most warp_max_n vertices are solved one per warp,
- * larger ones one per CTA. */
-pradmm_status pradmm_batch_set_schedule(pradmm_batch_t b, int32_t block, int32_t warp_max_n);
-pradmm_status pradmm_batch_get_schedule(pradmm_batch_t b, int32_t* block, int32_t* warp_max_n);
+ * larger ones one per CTA.  With `cluster` = 2, 4 or 8, graphs with more than
+ * cluster_min_n vertices are solved by a thread-block cluster of that many
+ * CTAs (the hardware co-schedules them; the sweeps of an iteration are
+ * separated by cluster barriers and the residual parts are exchanged through
+ * distributed shared memory); cluster = 1 uses no clusters.  PRADMM_ERR_ARG
+ * if a value is out of range or no cluster of that shape fits the GPU. */
+pradmm_status pradmm_batch_set_schedule(pradmm_batch_t b, int32_t block, int32_t warp_max_n, int32_t cluster,
+                                        int32_t cluster_min_n);
+pradmm_status pradmm_batch_get_schedule(pradmm_batch_t b, int32_t* block, int32_t* warp_max_n, int32_t* cluster,
+                                        int32_t* cluster_min_n);
 
-/* Times `iters` iterations of every candidate schedule (block 128/256/512 x
- * warp_max_n 0/64/256/1024) from the current state, keeps the fastest and
- * restores the state.  Outputs are nullable. */
+/* Runs `iters` iterations of candidate schedules from the current state in
+ * two stages -- block 128/256/512 x warp_max_n 0/64/256/1024 without clusters,
+ * then clusters (cluster, cluster_min_n) = (4, 2048), (8, 2048), (8, 8192),
+ * (4, 8192) at the best CTA shape -- scores each by the batch's time plus 4x
+ * the largest graph's own duration (a solve to a relative residual runs its
+ * slowest graphs several times the mean iteration count, so that graph's
+ * group sets the makespan), keeps the best and restores the state.  Outputs
+ * are nullable. */
 pradmm_status pradmm_batch_autotune(pradmm_batch_t b, int32_t iters, int32_t* block_out,
-                                    int32_t* warp_max_n_out);
+                                    int32_t* warp_max_n_out, int32_t* cluster_out, int32_t* cluster_min_n_out);
 
 /* Initial states, all graphs at once (q: N x 4, t: N x 3 with N = sum n_g, in
  * graph order): odometry composition per graph, or given poses. */

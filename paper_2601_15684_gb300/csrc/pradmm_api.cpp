@@ -1422,11 +1422,16 @@ struct pradmm_batch_s {
     double* e_first_d = nullptr;
     double* e_last_d = nullptr;
     int32_t* status_d = nullptr;
+    unsigned long long* t_span_d = nullptr;
     double* F_d = nullptr;
     double* save_d = nullptr;  // 24 n doubles: state snapshot for the autotuner
     int n_items = 0;
     int block = 256;        // threads per CTA of the persistent kernel
     int warp_max_n = 256;   // graphs up to this many vertices are solved by one warp
+    int cluster = 1;        // CTAs per cluster (1: no cluster items)
+    int cluster_min_n = 0;  // graphs above this many vertices are solved by a cluster
+    int n_big = 0;          // cluster items
+    int* next_big_d = nullptr;
     int grid = 1;
 };
 
@@ -1443,16 +1448,22 @@ void batch_free(pradmm_batch_s* b) {
 
 // Work items: graphs larger than warp_max_n get a whole CTA each (largest
 // first); the others are packed, in decreasing size, block/32 per CTA.
-pradmm_status batch_schedule(pradmm_batch_s* b, int block, int warp_max_n) {
+pradmm_status batch_schedule(pradmm_batch_s* b, int block, int warp_max_n, int cluster, int cluster_min_n) {
     if (block != 64 && block != 128 && block != 256 && block != 512)
         return fail(PRADMM_ERR_ARG, "batch block must be 64, 128, 256 or 512");
     if (warp_max_n < 0) return fail(PRADMM_ERR_ARG, "warp_max_n must be >= 0");
+    if (cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8)
+        return fail(PRADMM_ERR_ARG, "cluster must be 1, 2, 4 or 8");
+    if (cluster_min_n < 0) return fail(PRADMM_ERR_ARG, "cluster_min_n must be >= 0");
     std::vector<int32_t> order(b->G);
     for (int32_t g = 0; g < b->G; ++g) order[g] = g;
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t c) { return b->n_g[a] > b->n_g[c]; });
     std::vector<int2> items;
     const int wpb = block / 32;
     int32_t pos = 0;
+    if (cluster > 1)
+        while (pos < b->G && b->n_g[order[pos]] > cluster_min_n) ++pos;  // cluster items: order [0, pos)
+    const int32_t n_big = pos;
     while (pos < b->G && b->n_g[order[pos]] > warp_max_n) items.push_back(make_int2(pos++, -1));
     while (pos < b->G) {
         const int cnt = std::min<int32_t>(wpb, b->G - pos);
@@ -1461,16 +1472,28 @@ pradmm_status batch_schedule(pradmm_batch_s* b, int block, int warp_max_n) {
     }
     pradmm_s* h = b->h;
     CU(cudaMemcpyAsync(b->order_d, order.data(), sizeof(int32_t) * b->G, cudaMemcpyHostToDevice, h->stream));
-    CU(cudaMemcpyAsync(b->items_d, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, h->stream));
+    if (!items.empty())
+        CU(cudaMemcpyAsync(b->items_d, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, h->stream));
     CU(cudaStreamSynchronize(h->stream));
     int dev = 0, sms = 0, bps = 0;
     CU(cudaGetDevice(&dev));
     CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    CU(h->fp64 ? pradmm::batch_occupancy<double>(block, &bps) : pradmm::batch_occupancy<float>(block, &bps));
     b->n_items = (int)items.size();
+    b->n_big = n_big;
     b->block = block;
     b->warp_max_n = warp_max_n;
-    b->grid = std::max(1, std::min(b->n_items, sms * std::max(bps, 1)));
+    b->cluster = cluster;
+    b->cluster_min_n = cluster_min_n;
+    if (cluster > 1) {
+        int clusters = 0;
+        CU(h->fp64 ? pradmm::batch_cluster_occupancy<double>(block, cluster, &clusters)
+                   : pradmm::batch_cluster_occupancy<float>(block, cluster, &clusters));
+        if (clusters < 1) return fail(PRADMM_ERR_ARG, "no cluster of %d CTAs of %d threads fits the GPU", cluster, block);
+        b->grid = clusters * cluster;
+    } else {
+        CU(h->fp64 ? pradmm::batch_occupancy<double>(block, &bps) : pradmm::batch_occupancy<float>(block, &bps));
+        b->grid = std::max(1, std::min(b->n_items, sms * std::max(bps, 1)));
+    }
     return PRADMM_OK;
 }
 
@@ -1481,10 +1504,13 @@ pradmm::BatchDev batch_dev(const pradmm_batch_s* b, double rel_tol, double abs_t
     d.items = b->items_d;
     d.n_items = b->n_items;
     d.next = b->next_d;
+    d.n_big = b->n_big;
+    d.next_big = b->next_big_d;
     d.iters = b->iters_d;
     d.e_first = b->e_first_d;
     d.e_last = b->e_last_d;
     d.status = b->status_d;
+    d.t_span = b->t_span_d;
     d.rel_tol = rel_tol;
     d.abs_tol = abs_tol;
     d.max_iter = max_iter;
@@ -1501,7 +1527,7 @@ pradmm_status batch_run(pradmm_batch_s* b, double rel_tol, double abs_tol, int m
     cudaGraphExec_t exec = nullptr;
     CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e1 = pradmm::launch_batch<R>(h->gdev<R>(), h->sdev<R>(), h->coef<R>(), d, h->ctrl, b->grid, b->block,
-                                             h->stream);
+                                             b->cluster, h->stream);
     cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
     CU(e1);
     CU(e2);
@@ -1580,16 +1606,18 @@ pradmm_status pradmm_batch_create(int32_t G, const int64_t* n_g, const int64_t* 
         if (st == PRADMM_OK) st = dalloc(h, &b->order_d, G);
         if (st == PRADMM_OK) st = dalloc(h, &b->items_d, G);
         if (st == PRADMM_OK) st = dalloc(h, &b->next_d, 1);
+        if (st == PRADMM_OK) st = dalloc(h, &b->next_big_d, 1);
         if (st == PRADMM_OK) st = dalloc(h, &b->iters_d, G);
         if (st == PRADMM_OK) st = dalloc(h, &b->e_first_d, G);
         if (st == PRADMM_OK) st = dalloc(h, &b->e_last_d, G);
         if (st == PRADMM_OK) st = dalloc(h, &b->status_d, G);
+        if (st == PRADMM_OK) st = dalloc(h, &b->t_span_d, 2 * (size_t)G);
         if (st == PRADMM_OK) st = dalloc(h, &b->F_d, G);
         if (st == PRADMM_OK) {
             cudaError_t ce = cudaMemcpy(b->gv_d, b->off.data(), sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice);
             if (ce != cudaSuccess) st = fail(PRADMM_ERR_CUDA, "upload: %s", cudaGetErrorString(ce));
         }
-        if (st == PRADMM_OK) st = batch_schedule(b, 256, 256);
+        if (st == PRADMM_OK) st = batch_schedule(b, 256, 256, 1, 0);
         if (st != PRADMM_OK) {
             batch_free(b);
             return st;
@@ -1601,15 +1629,19 @@ pradmm_status pradmm_batch_create(int32_t G, const int64_t* n_g, const int64_t* 
     }
 }
 
-pradmm_status pradmm_batch_set_schedule(pradmm_batch_t b, int32_t block, int32_t warp_max_n) {
+pradmm_status pradmm_batch_set_schedule(pradmm_batch_t b, int32_t block, int32_t warp_max_n, int32_t cluster,
+                                        int32_t cluster_min_n) {
     if (!b) return fail(PRADMM_ERR_ARG, "NULL handle");
-    return batch_schedule(b, block, warp_max_n);
+    return batch_schedule(b, block, warp_max_n, cluster, cluster_min_n);
 }
 
-pradmm_status pradmm_batch_get_schedule(pradmm_batch_t b, int32_t* block, int32_t* warp_max_n) {
+pradmm_status pradmm_batch_get_schedule(pradmm_batch_t b, int32_t* block, int32_t* warp_max_n, int32_t* cluster,
+                                        int32_t* cluster_min_n) {
     if (!b) return fail(PRADMM_ERR_ARG, "NULL handle");
     if (block) *block = b->block;
     if (warp_max_n) *warp_max_n = b->warp_max_n;
+    if (cluster) *cluster = b->cluster;
+    if (cluster_min_n) *cluster_min_n = b->cluster_min_n;
     return PRADMM_OK;
 }
 
@@ -1668,7 +1700,8 @@ pradmm_status pradmm_batch_get_state(pradmm_batch_t b, double* p, double* q, dou
     return pradmm_get_state(b->h, p, q, t, s, lam, z);
 }
 
-pradmm_status pradmm_batch_autotune(pradmm_batch_t b, int32_t iters, int32_t* block_out, int32_t* warp_max_n_out) {
+pradmm_status pradmm_batch_autotune(pradmm_batch_t b, int32_t iters, int32_t* block_out, int32_t* warp_max_n_out,
+                                    int32_t* cluster_out, int32_t* cluster_min_n_out) {
     if (!b) return fail(PRADMM_ERR_ARG, "NULL handle");
     if (iters < 1) return fail(PRADMM_ERR_ARG, "iters must be >= 1");
     pradmm_s* h = b->h;
@@ -1679,40 +1712,70 @@ pradmm_status pradmm_batch_autotune(pradmm_batch_t b, int32_t iters, int32_t* bl
     // snapshot the state; every candidate starts from it, and it is restored after
     ST(h->fp64 ? get_state_impl<double>(h, sv, sv + 4 * n, sv + 8 * n, sv + 11 * n, sv + 14 * n, sv + 18 * n, true)
                : get_state_impl<float>(h, sv, sv + 4 * n, sv + 8 * n, sv + 11 * n, sv + 14 * n, sv + 18 * n, true));
-    const int blocks[3] = {128, 256, 512};
-    const int warp_ns[4] = {0, 64, 256, 1024};
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_b = b->block, best_w = b->warp_max_n;
+    int best_s[4] = {b->block, b->warp_max_n, b->cluster, b->cluster_min_n};
     pradmm_status st = PRADMM_OK;
-    for (int bi = 0; bi < 3 && st == PRADMM_OK; ++bi) {
-        for (int wi = 0; wi < 4 && st == PRADMM_OK; ++wi) {
-            st = batch_schedule(b, blocks[bi], warp_ns[wi]);
-            if (st != PRADMM_OK) break;
-            st = set_state_any(h, sv, sv + 4 * n, sv + 8 * n, sv + 11 * n, sv + 14 * n, sv + 18 * n, true);
-            if (st != PRADMM_OK) break;
-            cudaEventRecord(e0, h->stream);
-            st = batch_run_any(b, 0.0, 0.0, iters);  // fixed iterations: rel_tol 0 never stops early
-            cudaEventRecord(e1, h->stream);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (st == PRADMM_OK && ms < best) {
-                best = ms;
-                best_b = blocks[bi];
-                best_w = warp_ns[wi];
-            }
+    // Score = time of `iters` iterations of the whole batch + kCritWeight x the
+    // largest graph's own duration.  A solve to a relative residual runs its
+    // slowest graphs several times the mean iteration count (3000 vs 607 on
+    // 4,096 walks), so the largest graph's group sets the makespan once the
+    // others have stopped; a fixed-iteration probe alone measures only
+    // throughput.
+    constexpr double kCritWeight = 4.0;
+    int32_t largest = 0;
+    for (int32_t g = 1; g < b->G; ++g)
+        if (b->n_g[g] > b->n_g[largest]) largest = g;
+    auto trial = [&](int blk, int wn, int cl, int cmin) {
+        if (st != PRADMM_OK) return;
+        pradmm_status ts = batch_schedule(b, blk, wn, cl, cmin);
+        if (ts == PRADMM_ERR_ARG) return;  // a cluster shape that does not fit: skip it
+        st = ts;
+        if (st != PRADMM_OK) return;
+        st = set_state_any(h, sv, sv + 4 * n, sv + 8 * n, sv + 11 * n, sv + 14 * n, sv + 18 * n, true);
+        if (st != PRADMM_OK) return;
+        cudaEventRecord(e0, h->stream);
+        st = batch_run_any(b, 0.0, 0.0, iters);  // fixed iterations: rel_tol 0 never stops early
+        cudaEventRecord(e1, h->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        // the largest graph's own duration: its group's critical path
+        unsigned long long span[2] = {0, 0};
+        if (st == PRADMM_OK) {
+            cudaError_t ce = cudaMemcpy(span, b->t_span_d + 2 * (size_t)largest, sizeof(span), cudaMemcpyDeviceToHost);
+            if (ce != cudaSuccess) st = fail(PRADMM_ERR_CUDA, "autotune: %s", cudaGetErrorString(ce));
         }
-    }
+        const double crit_ms = span[1] > span[0] ? (double)(span[1] - span[0]) * 1e-6 : 0.0;
+        const float score = (float)(ms + kCritWeight * crit_ms);
+        if (st == PRADMM_OK && score < best) {
+            best = score;
+            best_s[0] = blk;
+            best_s[1] = wn;
+            best_s[2] = cl;
+            best_s[3] = cmin;
+        }
+    };
+    // stage 1: CTA size x warp-pack limit, no clusters
+    const int blocks[3] = {128, 256, 512};
+    const int warp_ns[4] = {0, 64, 256, 1024};
+    for (int bi = 0; bi < 3; ++bi)
+        for (int wi = 0; wi < 4; ++wi) trial(blocks[bi], warp_ns[wi], 1, 0);
+    // stage 2: clusters for the large graphs at the best CTA shape
+    const int b1 = best_s[0], w1 = best_s[1];
+    const int cl_shape[4][2] = {{4, 2048}, {8, 2048}, {8, 8192}, {4, 8192}};
+    for (int k = 0; k < 4; ++k) trial(b1, w1, cl_shape[k][0], cl_shape[k][1]);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (st == PRADMM_OK) st = batch_schedule(b, best_b, best_w);
+    if (st == PRADMM_OK) st = batch_schedule(b, best_s[0], best_s[1], best_s[2], best_s[3]);
     if (st == PRADMM_OK) st = set_state_any(h, sv, sv + 4 * n, sv + 8 * n, sv + 11 * n, sv + 14 * n, sv + 18 * n, true);
     if (st != PRADMM_OK) return st;
-    if (block_out) *block_out = best_b;
-    if (warp_max_n_out) *warp_max_n_out = best_w;
+    if (block_out) *block_out = best_s[0];
+    if (warp_max_n_out) *warp_max_n_out = best_s[1];
+    if (cluster_out) *cluster_out = best_s[2];
+    if (cluster_min_n_out) *cluster_min_n_out = best_s[3];
     return PRADMM_OK;
 }
 

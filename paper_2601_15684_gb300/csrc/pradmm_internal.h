@@ -139,19 +139,25 @@ struct BatchDev {
     const int2* items;    // n_items
     int n_items;
     int* next;
+    int n_big;            // cluster items: order positions [0, n_big) (k_batch_cl)
+    int* next_big;
     int32_t* iters;       // G outputs
     double* e_first;
     double* e_last;
     int32_t* status;
+    unsigned long long* t_span;  // 2 G: device clock (ns) at each graph's start and end
     double rel_tol, abs_tol;
     int max_iter;
 };
 
+// cluster > 1: the cluster kernel (grid a multiple of cluster); 1: k_batch.
 template <typename R>
 cudaError_t launch_batch(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const BatchDev& b,
-                         Ctrl* ctrl, int grid, int block, cudaStream_t st);
+                         Ctrl* ctrl, int grid, int block, int cluster, cudaStream_t st);
 template <typename R>
 cudaError_t batch_occupancy(int block, int* bps);
+template <typename R>
+cudaError_t batch_cluster_occupancy(int block, int cluster, int* clusters);
 template <typename R>
 cudaError_t launch_batch_objective(const GraphDev<R>& g, const StateDev<R>& s, const double* qe64,
                                    const double* te64, const double* ka64, const double* om64,

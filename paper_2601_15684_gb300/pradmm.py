@@ -83,9 +83,10 @@ _SIGS = {
     "pradmm_destroy": (None, [_h]),
     "pradmm_batch_create": (ctypes.c_int, [ctypes.c_int32, _i64, _i64, _i32, _i32, _d, _d, _d, _d, _P(pradmm_params),
                                            ctypes.c_void_p, _P(ctypes.c_void_p)]),
-    "pradmm_batch_set_schedule": (ctypes.c_int, [_h, ctypes.c_int32, ctypes.c_int32]),
-    "pradmm_batch_get_schedule": (ctypes.c_int, [_h, _i32, _i32]),
-    "pradmm_batch_autotune": (ctypes.c_int, [_h, ctypes.c_int32, _i32, _i32]),
+    "pradmm_batch_set_schedule": (ctypes.c_int, [_h, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                 ctypes.c_int32]),
+    "pradmm_batch_get_schedule": (ctypes.c_int, [_h, _i32, _i32, _i32, _i32]),
+    "pradmm_batch_autotune": (ctypes.c_int, [_h, ctypes.c_int32, _i32, _i32, _i32, _i32]),
     "pradmm_batch_init_odometry": (ctypes.c_int, [_h]),
     "pradmm_batch_set_state": (ctypes.c_int, [_h, _d, _d]),
     "pradmm_batch_solve": (ctypes.c_int, [_h, ctypes.c_double, ctypes.c_int32, _i32, _d, _d, _i32]),
@@ -442,19 +443,22 @@ class Batch:
     def __exit__(self, *a):
         self.close()
 
-    def set_schedule(self, block, warp_max_n):
-        _check(load().pradmm_batch_set_schedule(self.h, int(block), int(warp_max_n)), "pradmm_batch_set_schedule")
+    def set_schedule(self, block, warp_max_n, cluster=1, cluster_min_n=0):
+        _check(load().pradmm_batch_set_schedule(self.h, int(block), int(warp_max_n), int(cluster), int(cluster_min_n)),
+               "pradmm_batch_set_schedule")
 
     def schedule(self):
-        b, w = ctypes.c_int32(0), ctypes.c_int32(0)
-        _check(load().pradmm_batch_get_schedule(self.h, ctypes.byref(b), ctypes.byref(w)), "pradmm_batch_get_schedule")
-        return b.value, w.value
+        """(block, warp_max_n, cluster, cluster_min_n)"""
+        v = [ctypes.c_int32(0) for _ in range(4)]
+        _check(load().pradmm_batch_get_schedule(self.h, *[ctypes.byref(x) for x in v]), "pradmm_batch_get_schedule")
+        return tuple(x.value for x in v)
 
     def autotune(self, iters=20):
-        b, w = ctypes.c_int32(0), ctypes.c_int32(0)
-        _check(load().pradmm_batch_autotune(self.h, int(iters), ctypes.byref(b), ctypes.byref(w)),
+        """Returns the chosen (block, warp_max_n, cluster, cluster_min_n)."""
+        v = [ctypes.c_int32(0) for _ in range(4)]
+        _check(load().pradmm_batch_autotune(self.h, int(iters), *[ctypes.byref(x) for x in v]),
                "pradmm_batch_autotune")
-        return b.value, w.value
+        return tuple(x.value for x in v)
 
     def init_odometry(self):
         _check(load().pradmm_batch_init_odometry(self.h), "pradmm_batch_init_odometry")

@@ -5,7 +5,8 @@
   they agree to rounding, since the compiler may contract multiply-adds
   differently per kernel), and a repeated run is bitwise identical;
 - small graphs match the FP64 oracle;
-- every schedule (CTA- or warp-per-graph, block sizes) gives the same state;
+- every schedule (cluster-, CTA- or warp-per-graph, block sizes) gives the
+  same state to rounding;
 - the per-graph stopping rule e^k <= rel_tol * e^1 holds where it reports
   convergence;
 - the autotuner keeps a valid schedule and leaves the state untouched.
@@ -100,10 +101,12 @@ def test_batch_fp64_matches_oracle(P):
 def test_batch_schedules_agree_and_stop_rule(P):
     graphs = _graphs(40, seed=3, n_max=2500)
     outs = []
+    schedules = ((256, 256, 1, 0), (128, 0, 1, 0), (512, 1024, 1, 0), (64, 64, 1, 0),
+                 (256, 64, 8, 1000), (128, 64, 4, 300), (256, 0, 2, 0))
     with P.Batch(graphs, precision=1) as B:
-        for block, wmax in ((256, 256), (128, 0), (512, 1024), (64, 64)):
-            B.set_schedule(block, wmax)
-            assert B.schedule() == (block, wmax)
+        for sch in schedules:
+            B.set_schedule(*sch)
+            assert B.schedule() == sch
             B.init_odometry()
             res = B.solve(rel_tol=0.0, max_iter=25)  # fixed iteration count
             assert (res["iters"] == 25).all()
@@ -111,12 +114,43 @@ def test_batch_schedules_agree_and_stop_rule(P):
         B.set_schedule(256, 256)
         B.init_odometry()
         res = B.solve(rel_tol=1e-6, max_iter=3000)
-    for st in outs[1:]:
-        close_state(st, outs[0], False, what="schedule", iters=25)
+    for sch, st in zip(schedules[1:], outs[1:]):
+        close_state(st, outs[0], False, what=f"schedule {sch}", iters=25)
     conv = res["status"] == P.PRADMM_OK
     assert conv.any()
     assert (res["e_last"][conv] <= 1e-6 * res["e_first"][conv]).all()
     assert (res["iters"][~conv] == 3000).all()
+
+
+def test_batch_cluster_schedule_matches_oracle_fp64_and_stops(P):
+    # graphs large enough to go to clusters, FP64 against the oracle; the
+    # cluster's residual is one FP64 sum in rank order, so the stopping rule
+    # is applied to the same e^k in every CTA of the cluster
+    graphs = _graphs(5, seed=13, n_max=400)
+    with P.Batch(graphs, precision=0) as B:
+        B.set_schedule(128, 0, 8, 50)
+        B.init_odometry()
+        res = B.solve(rel_tol=1e-3, max_iter=60)
+        st = B.state()
+    prm = oracle.make_params(beta1=1.0, beta2=1.0, tau=1.5)
+    for k, g in enumerate(graphs):
+        q0, t0 = oracle.init_odometry(g)
+        orc, _, _ = oracle.iterate(g, prm, oracle.init_state(q0, t0), int(res["iters"][k]))
+        sl = _slice(st, B.offsets[k], B.offsets[k + 1])
+        for key in KEYS:
+            err = np.linalg.norm(sl[key] - orc[key]) / max(np.linalg.norm(orc[key]), 1e-300)
+            assert err <= 1e-10, (k, key, err)
+    conv = res["status"] == P.PRADMM_OK
+    assert (res["e_last"][conv] <= 1e-3 * res["e_first"][conv]).all()
+
+
+def test_batch_schedule_rejects_bad_values(P):
+    graphs = _graphs(3, seed=1, n_max=100)
+    with P.Batch(graphs, precision=1) as B:
+        for bad in ((100, 64, 1, 0), (256, -1, 1, 0), (256, 64, 3, 0), (256, 64, 16, 0), (256, 64, 4, -1)):
+            with pytest.raises(P.PRADMMError) as ei:
+                B.set_schedule(*bad)
+            assert ei.value.status == P.PRADMM_ERR_ARG
 
 
 def test_batch_repeat_is_bitwise_identical(P):
@@ -138,9 +172,10 @@ def test_batch_autotune_keeps_state(P):
     with P.Batch(graphs, precision=1) as B:
         B.init_odometry()
         before = B.state()
-        block, wmax = B.autotune(iters=5)
+        block, wmax, cl, cmin = B.autotune(iters=5)
         assert block in (128, 256, 512) and wmax in (0, 64, 256, 1024)
-        assert B.schedule() == (block, wmax)
+        assert (cl, cmin) in ((1, 0), (4, 2048), (8, 2048), (8, 8192), (4, 8192))
+        assert B.schedule() == (block, wmax, cl, cmin)
         after = B.state()
         for key in KEYS:
             np.testing.assert_array_equal(after[key], before[key])
