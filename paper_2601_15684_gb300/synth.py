@@ -183,6 +183,62 @@ def helix_graph(n: int = 25000, radius: float = 10.0, pitch: float = 0.5, per_tu
     return _finish("helix", n, src, dst, q_gt, t_gt, rng, sigma_r, sigma_t)
 
 
+def ring_graph(n: int = 100, radius: float = 2.0, sigma_r: float = 0.01, sigma_t: float = 0.01,
+               seed: int = 7) -> PoseGraph:
+    """The circular ring of the paper's synthetic experiments (Section 5): n
+    poses on one planar loop of the given radius, orientation tangent to the
+    loop, odometry edges (i, i+1) and the closing edge (n-1, 0), so m = n."""
+    rng = np.random.default_rng(seed)
+    phi = 2.0 * math.pi * np.arange(n, dtype=np.float64) / n
+    t_gt = np.stack([radius * np.cos(phi), radius * np.sin(phi), np.zeros(n)], axis=1)
+    Y = phi + math.pi / 2
+    q_gt = np.stack([np.cos(Y / 2), np.zeros(n), np.zeros(n), np.sin(Y / 2)], axis=1)
+    src = np.arange(n)
+    dst = (src + 1) % n
+    return _finish(f"ring{n}", n, src, dst, q_gt, t_gt, rng, sigma_r, sigma_t,
+                   info={"radius": radius, "sigma_r": sigma_r, "sigma_t": sigma_t})
+
+
+def cube_graph(side: int = 7, p_cube: float = 0.3, extent: float = 2.0, sigma_r: float = 0.1,
+               sigma_t: float = 0.1, seed: int = 11) -> PoseGraph:
+    """The cube dataset of the paper's synthetic experiments (Section 5): a
+    robot visits every node of a side^3 grid spanning an extent^3 world along
+    a serpentine path (odometry, side^3 - 1 edges); every pair of grid
+    neighbours the path does not join gets each of its two directed closures
+    independently with probability p_cube, which gives the paper's expected
+    edge count E(m) = 2 (2 side^3 - 3 side^2 + 1) p_cube + side^3 - 1.
+    Ground-truth orientations are uniform on SO(3)."""
+    rng = np.random.default_rng(seed)
+    # serpentine order: x varies fastest, reversing on alternate rows; rows
+    # reverse on alternate layers, so consecutive nodes are grid neighbours
+    order = []
+    for z in range(side):
+        ys = range(side) if z % 2 == 0 else range(side - 1, -1, -1)
+        for row, y in enumerate(ys):
+            xs = range(side) if (row + z * side) % 2 == 0 else range(side - 1, -1, -1)
+            for x in xs:
+                order.append((x, y, z))
+    coords = np.array(order, dtype=np.float64)
+    n = side ** 3
+    step = extent / max(side - 1, 1)
+    t_gt = coords * step
+    q_gt = random_unit_quaternions(rng, n)
+    pos = {c: k for k, c in enumerate(order)}
+    path = {(k, k + 1) for k in range(n - 1)}
+    src, dst = list(range(n - 1)), list(range(1, n))
+    for (x, y, z), a in pos.items():
+        for dx, dy, dz in ((1, 0, 0), (0, 1, 0), (0, 0, 1)):
+            b = pos.get((x + dx, y + dy, z + dz))
+            if b is None or (min(a, b), max(a, b)) in path:
+                continue
+            for u, v in ((a, b), (b, a)):
+                if rng.random() < p_cube:
+                    src.append(u)
+                    dst.append(v)
+    return _finish(f"cube{side}", n, np.array(src), np.array(dst), q_gt, t_gt, rng, sigma_r, sigma_t,
+                   info={"side": side, "p_cube": p_cube, "extent": extent})
+
+
 # axis-aligned headings of a lattice walk: +x, -x, +y, -y, +z, -z
 _LATTICE_STEP = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]])
 _H = math.sqrt(0.5)
@@ -310,4 +366,12 @@ def workload(name: str) -> PoseGraph:
         return lattice_walk_graph()
     if name == "walk10k":
         return random_walk_graph(10000, n_closures=20000, sigma_r=0.02, sigma_t=0.1, seed=5, name="walk10k")
+    if name == "ring100":
+        return ring_graph(100)
+    if name == "ring5000":
+        return ring_graph(5000)
+    if name == "cube7":
+        return cube_graph(7, 0.3)
+    if name == "cube10":
+        return cube_graph(10, 0.9)
     raise KeyError(name)
