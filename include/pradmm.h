@@ -189,6 +189,22 @@ pradmm_status pradmm_l2_window_info(pradmm_t h, double* out);
  * iteration time.  The state advances by `iters` iterations. */
 pradmm_status pradmm_profile_sweeps(pradmm_t h, int32_t iters, double* ms_out);
 
+/* General weight matrices (Lemma 1, Algorithm 1's branch for non-scalar
+ * Sigma): edge e weighs its translation residual with omega_e Sigma1 and its
+ * rotation residual with kappa_e Sigma2, Sigma1 and Sigma2 symmetric positive
+ * definite 4x4 (row-major, 16 doubles each, copied).  The p-update then solves
+ * min_{|p|=1} 1/2 p^T A_1 p + b_1^T p per vertex through the eigen-
+ * decomposition of A_1 and the secular equation of Lemma 1 (hard case
+ * included: of the two minimisers the one closer to p^k is kept); FP32
+ * handles repeat that solve in FP64 when the eigen-gap or the component of
+ * b_1 on the bottom eigenvector is tiny (counted in pradmm_counters out[0]).
+ * The q, t and s blocks solve 4x4 / 3x3 systems.  Both NULL returns to the
+ * scalar model (Sigma = I).  PRADMM_ERR_ARG if only one is given or one is
+ * not symmetric positive definite, PRADMM_ERR_NONFINITE for non-finite
+ * entries.  Keeps the state (the next iteration recomputes p^{k+1}); the
+ * reverse mode and pradmm_profile_sweeps need the scalar model. */
+pradmm_status pradmm_set_sigma(pradmm_t h, const double* Sigma1, const double* Sigma2);
+
 /* ---- reverse mode -------------------------------------------------------------
  * Gradients of a loss L(p^K, t^K) of the poses after K iterations of
  * Algorithm 1 with respect to the measurements q_e, t_e and the weights

@@ -85,6 +85,9 @@ struct pradmm_s {
     cudaGraphConditionalHandle cond = 0;
     bool graph_ready = false;
 
+    bool general = false;              // general Sigma_1, Sigma_2 (pradmm_set_sigma)
+    double S1[16] = {}, S2[16] = {}, U[9] = {}, mu[3] = {};
+    double* sigma_d = nullptr;         // 32 doubles: S1, S2 (objective)
     void* state_block = nullptr;       // t, s, q, p[0], p[1], lam, z: 28 n reals, contiguous
     bool l2_on = false;                // this handle holds an L2 set-aside
     cudaAccessPolicyWindow window{};   // persisting window over t, s, q, p[0], p[1]
@@ -134,6 +137,17 @@ struct pradmm_s {
         S.s = static_cast<R*>(s);
         S.z = static_cast<R*>(z);
         return S;
+    }
+    template <typename R>
+    pradmm::SigmaDev<R> sigma() const {
+        pradmm::SigmaDev<R> sg;
+        for (int k = 0; k < 16; ++k) {
+            sg.S1[k] = R(S1[k]);
+            sg.S2[k] = R(S2[k]);
+        }
+        for (int k = 0; k < 9; ++k) sg.U[k] = R(U[k]);
+        for (int k = 0; k < 3; ++k) sg.mu[k] = R(mu[k]);
+        return sg;
     }
     template <typename R>
     pradmm::Coef<R> coef() const {
@@ -642,6 +656,10 @@ pradmm_status launch_iters_plain(pradmm_s* h, long long iters) {
     const auto c = h->coef<R>();
     const auto L = h->launch(false);
     for (long long k = 0; k < iters; ++k) {
+        if (h->general) {
+            CU(pradmm::launch_sigma_iteration<R>(g, S, c, h->sigma<R>(), L));
+            continue;
+        }
         CU(pradmm::launch_q<R>(g, S, c, L));
         CU(pradmm::launch_t<R>(g, S, c, L));
         CU(pradmm::launch_sp<R>(g, S, c, L));
@@ -666,9 +684,14 @@ pradmm_status ensure_graph(pradmm_s* h) {
     const auto S = h->sdev<R>();
     const auto c = h->coef<R>();
     const auto L = h->launch(true);
-    cudaError_t e1 = pradmm::launch_q<R>(g, S, c, L);
-    cudaError_t e2 = pradmm::launch_t<R>(g, S, c, L);
-    cudaError_t e3 = pradmm::launch_sp<R>(g, S, c, L);
+    cudaError_t e1 = cudaSuccess, e2 = cudaSuccess, e3 = cudaSuccess;
+    if (h->general) {
+        e1 = pradmm::launch_sigma_iteration<R>(g, S, c, h->sigma<R>(), L);
+    } else {
+        e1 = pradmm::launch_q<R>(g, S, c, L);
+        e2 = pradmm::launch_t<R>(g, S, c, L);
+        e3 = pradmm::launch_sp<R>(g, S, c, L);
+    }
     cudaGraph_t captured = nullptr;
     cudaError_t e4 = cudaStreamEndCapture(h->stream, &captured);
     CU(e1);
@@ -686,7 +709,7 @@ pradmm_status run(pradmm_s* h, long long iters, bool use_tol) {
     if (iters <= 0) return read_ctrl(h);
     h->epoch++;
     CU(pradmm::launch_arm(h->ctrl, iters, use_tol ? 1 : 0, h->prm.tol, h->stream));
-    if (!h->pending) {
+    if (!h->pending && !h->general) {  // the general-Sigma iteration starts with its own p sweep
         CU(pradmm::launch_p<R>(h->gdev<R>(), h->sdev<R>(), h->coef<R>(), h->launch(false)));
         h->pending = true;
     }
@@ -838,6 +861,7 @@ pradmm_status get_state_impl(pradmm_s* h, double* p, double* q, double* t, doubl
 template <typename R>
 pradmm_status profile_impl(pradmm_s* h, int32_t iters, double* ms_out) {
     if (!h->state_set) return fail(PRADMM_ERR_STATE, "state is not set");
+    if (h->general) return fail(PRADMM_ERR_STATE, "the per-sweep profile covers the scalar-Sigma sweeps");
     if (iters < 1) return fail(PRADMM_ERR_ARG, "iters must be >= 1");
     const auto g = h->gdev<R>();
     const auto S = h->sdev<R>();
@@ -926,6 +950,7 @@ pradmm_status snapshot(pradmm_s* h, void* dst) {
 template <typename R>
 pradmm_status adjoint_record(pradmm_s* h, int32_t iters, int32_t ckpt_every) {
     if (!h->state_set) return fail(PRADMM_ERR_STATE, "state is not set (pradmm_set_state or pradmm_init_odometry)");
+    if (h->general) return fail(PRADMM_ERR_STATE, "the reverse mode supports scalar Sigma only");
     if (iters < 0) return fail(PRADMM_ERR_ARG, "iters must be >= 0");
     if (ckpt_every < 1) return fail(PRADMM_ERR_ARG, "ckpt_every must be >= 1");
     h->tape_valid = false;
@@ -1159,6 +1184,100 @@ pradmm_status adjoint_impl(pradmm_s* h, const double* p_bar, const double* t_bar
     return PRADMM_OK;
 }
 
+// ---- general Sigma ------------------------------------------------------------
+// Symmetric positive definite check by Cholesky.
+bool spd4(const double* S) {
+    double L[4][4] = {};
+    for (int j = 0; j < 4; ++j) {
+        double d = S[4 * j + j];
+        for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+        if (!(d > 0.0)) return false;
+        L[j][j] = std::sqrt(d);
+        for (int i = j + 1; i < 4; ++i) {
+            double v = S[4 * i + j];
+            for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+            L[i][j] = v / L[j][j];
+        }
+    }
+    return true;
+}
+
+// Eigen-decomposition of a symmetric 3x3 matrix by cyclic Jacobi: A = U diag(mu) U^T.
+void eig3_host(const double A0[3][3], double U[9], double mu[3]) {
+    double a[3][3], v[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    std::memcpy(a, A0, sizeof(a));
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        const double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+        if (off < 1e-300) break;
+        const int P[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+        for (const auto& pq : P) {
+            const int p = pq[0], q = pq[1];
+            if (a[p][q] == 0.0) continue;
+            const double th = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+            const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+            const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+            for (int k = 0; k < 3; ++k) {
+                const double kp = a[k][p], kq = a[k][q];
+                a[k][p] = c * kp - sn * kq;
+                a[k][q] = sn * kp + c * kq;
+            }
+            for (int k = 0; k < 3; ++k) {
+                const double pk = a[p][k], qk = a[q][k];
+                a[p][k] = c * pk - sn * qk;
+                a[q][k] = sn * pk + c * qk;
+            }
+            for (int k = 0; k < 3; ++k) {
+                const double kp = v[k][p], kq = v[k][q];
+                v[k][p] = c * kp - sn * kq;
+                v[k][q] = sn * kp + c * kq;
+            }
+        }
+    }
+    for (int r = 0; r < 3; ++r) {
+        mu[r] = a[r][r];
+        for (int c = 0; c < 3; ++c) U[3 * r + c] = v[r][c];
+    }
+}
+
+pradmm_status set_sigma_impl(pradmm_s* h, const double* S1, const double* S2) {
+    if (!S1 && !S2) {
+        h->general = false;
+    } else {
+        if (!S1 || !S2) return fail(PRADMM_ERR_ARG, "give both Sigma_1 and Sigma_2, or neither");
+        for (const double* S : {S1, S2}) {
+            double mx = 0.0;
+            for (int k = 0; k < 16; ++k) {
+                if (!std::isfinite(S[k])) return fail(PRADMM_ERR_NONFINITE, "Sigma has a non-finite entry");
+                mx = std::max(mx, std::fabs(S[k]));
+            }
+            for (int r = 0; r < 4; ++r)
+                for (int c = r + 1; c < 4; ++c)
+                    if (std::fabs(S[4 * r + c] - S[4 * c + r]) > 1e-12 * mx)
+                        return fail(PRADMM_ERR_ARG, "Sigma is not symmetric");
+            if (!spd4(S)) return fail(PRADMM_ERR_ARG, "Sigma is not positive definite");
+        }
+        std::memcpy(h->S1, S1, sizeof(h->S1));
+        std::memcpy(h->S2, S2, sizeof(h->S2));
+        double hat[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) hat[r][c] = S1[4 * (r + 1) + (c + 1)];
+        eig3_host(hat, h->U, h->mu);
+        if (!h->sigma_d) ST(dalloc(h, &h->sigma_d, 32));
+        CU(cudaMemcpy(h->sigma_d, h->S1, sizeof(double) * 16, cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(h->sigma_d + 16, h->S2, sizeof(double) * 16, cudaMemcpyHostToDevice));
+        h->general = true;
+    }
+    // the captured loop and any precomputed p^{k+1} belong to the other form
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->graph_exec = nullptr;
+    h->graph = nullptr;
+    h->graph_ready = false;
+    h->pending = false;
+    h->epoch++;
+    return PRADMM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1304,18 +1423,32 @@ pradmm_status pradmm_adjoint_device(pradmm_t h, const double* p_bar_d, const dou
                                          x0_bar_d, true);
 }
 
+pradmm_status pradmm_set_sigma(pradmm_t h, const double* Sigma1, const double* Sigma2) {
+    if (!h) return fail(PRADMM_ERR_ARG, "handle is NULL");
+    return set_sigma_impl(h, Sigma1, Sigma2);
+}
+
 pradmm_status pradmm_objective(pradmm_t h, double* F) {
     if (!h || !F) return fail(PRADMM_ERR_ARG, "NULL argument");
     if (!h->state_set) return fail(PRADMM_ERR_STATE, "state is not set");
     cudaError_t e;
-    if (h->fp64)
+    if (h->general) {
+        const double *S1 = h->sigma_d, *S2 = h->sigma_d + 16;
+        e = h->fp64 ? pradmm::launch_objective_sigma<double>(h->gdev<double>(), h->sdev<double>(), h->qe64, h->te64,
+                                                             h->ka64, h->om64, S1, S2, h->ctrl, h->obj_part,
+                                                             h->obj_ticket, h->F_dev, h->obj_grid, 256, h->stream)
+                    : pradmm::launch_objective_sigma<float>(h->gdev<float>(), h->sdev<float>(), h->qe64, h->te64,
+                                                            h->ka64, h->om64, S1, S2, h->ctrl, h->obj_part,
+                                                            h->obj_ticket, h->F_dev, h->obj_grid, 256, h->stream);
+    } else if (h->fp64) {
         e = pradmm::launch_objective<double>(h->gdev<double>(), h->sdev<double>(), h->qe64, h->te64, h->ka64,
                                              h->om64, h->ctrl, h->obj_part, h->obj_ticket, h->F_dev, h->obj_grid, 256,
                                              h->stream);
-    else
+    } else {
         e = pradmm::launch_objective<float>(h->gdev<float>(), h->sdev<float>(), h->qe64, h->te64, h->ka64,
                                             h->om64, h->ctrl, h->obj_part, h->obj_ticket, h->F_dev, h->obj_grid, 256,
                                             h->stream);
+    }
     CU(e);
     CU(cudaMemcpyAsync(F, h->F_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));

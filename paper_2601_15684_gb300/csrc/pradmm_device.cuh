@@ -166,6 +166,52 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return r;
 }
 
+// ---- residual e^{k+1} and stop decision (last CTA of the s/z + p sweep) ---------
+// Called by every CTA of the last sweep of an iteration after writing its
+// partials; the last CTA to arrive forms e^{k+1}, advances the iteration and
+// sets the stop state and the while-node condition.
+__device__ __forceinline__ void finish_iteration(Ctrl* ctrl, const Launch& L, double b1, double b2, double* sh) {
+    __shared__ bool last;
+    __threadfence();
+    if (threadIdx.x == 0) last = (atomicAdd(&ctrl->ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int cnt[4] = {L.grid_q, L.grid_sp, L.grid_q, L.grid_t};  // slots DLAM, DZ, DQ, DT
+    double tot[4];
+#pragma unroll
+    for (int sl = 0; sl < 4; ++sl) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < cnt[sl]; b += blockDim.x) v += __ldcg(L.part + sl * L.pstride + b);
+        tot[sl] = block_sum(v, sh);
+    }
+    if (threadIdx.x == 0) {
+        const double dl = tot[SLOT_DLAM], dz = tot[SLOT_DZ], dq = tot[SLOT_DQ], dt = tot[SLOT_DT];
+        const double e = dl / b1 + dz / b2 + b1 * dq + b2 * dt;
+        ctrl->parts[0] = dl;
+        ctrl->parts[1] = dz;
+        ctrl->parts[2] = dq;
+        ctrl->parts[3] = dt;
+        ctrl->e_last = e;
+        const long long it = ctrl->iter + 1;
+        ctrl->iter = it;
+        int halt = 0;
+        if (!isfinite(e)) {
+            ctrl->nonfinite = 1;
+            halt = 1;
+        }
+        if (ctrl->use_tol && e < ctrl->tol) {
+            ctrl->stop = 1;
+            halt = 1;
+        }
+        if (it >= ctrl->target) halt = 1;
+        ctrl->halt = halt;
+        ctrl->ticket = 0u;
+        __threadfence();
+        if (L.has_cond) cudaGraphSetConditional(L.cond, halt ? 0u : 1u);
+    }
+}
+
 // ---- p-block, serial form (FP64 recompute of a tiny |u|) ---------------------
 // u_i = sum_{e=(i,j)} 2 w_e (t~_j - s~_i)^* q_i t~_e + sum_{e=(l,i)} 2 k_e q_l q_e
 //       + beta1 q_i + lam_i + gamma1 p_i ,      p_i^{new} = u_i / |u_i|

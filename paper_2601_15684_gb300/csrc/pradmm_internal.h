@@ -124,6 +124,31 @@ cudaError_t launch_unpack4(const R* src, const int32_t* perm, double* dst, int64
 template <typename R>
 cudaError_t launch_unpack3(const R* src, const int32_t* perm, double* dst, int64_t n, cudaStream_t st);
 
+// ---- general weight matrices (Sigma_1, Sigma_2 not scalar) ------------------------
+
+// Passed by value as a kernel parameter.  S1, S2 row-major 4x4; U (row-major
+// 3x3, columns the eigenvectors) and mu the eigen-decomposition of the
+// translation block Sigma1_hat = S1[1..3][1..3].
+template <typename R>
+struct SigmaDev {
+    R S1[16];
+    R S2[16];
+    R U[9];
+    R mu[3];
+};
+
+// One iteration with general Sigma: p, q, t sweeps and the s/z sweep with the
+// residual and stop state (the same partial slots and control block as the
+// scalar sweeps).
+template <typename R>
+cudaError_t launch_sigma_iteration(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c,
+                                   const SigmaDev<R>& sg, const Launch& L);
+template <typename R>
+cudaError_t launch_objective_sigma(const GraphDev<R>& g, const StateDev<R>& s, const double* qe64,
+                                   const double* te64, const double* ka64, const double* om64, const double* S1,
+                                   const double* S2, Ctrl* ctrl, double* part, unsigned int* ticket, double* F_dev,
+                                   int grid, int block, cudaStream_t st);
+
 // ---- batched solver ------------------------------------------------------------
 
 // Per-graph outcome codes (the pradmm_status values of the same meaning).

@@ -1,0 +1,634 @@
+// PRADMM sweeps with general weight matrices Sigma_1, Sigma_2 for sm_103a.
+//
+// Edge e = (i, j) weighs the translation residual with omega_e Sigma_1 and
+// the rotation residual with kappa_e Sigma_2 (symmetric positive definite
+// 4x4, shared by all edges).  The block matrices of Appendix B are then no
+// longer scalar:
+//   k_p_sig  p-block (3a): A_1, b_1 assembled per vertex, then the sphere-
+//            constrained quadratic min_{|p|=1} 1/2 p^T A_1 p + b_1^T p of
+//            Lemma 1, solved through the eigen-decomposition of A_1 (cyclic
+//            Jacobi) and the secular equation sum_k g_k^2 / (a_k + lambda)^2
+//            = 1 for lambda > -a_min (the characterisation of the Appendix C
+//            lemma), with its hard case; FP32 handles re-solve in FP64 when
+//            the eigen-gap or the component of b_1 on the bottom eigenvector
+//            is tiny
+//   k_q_sig  q-block (3b) + lambda: A_2 (4x4) by Cholesky
+//   k_t_sig  t-block (3c): A_3 = a Sigma1_hat + (beta2 + gamma3) I, solved in
+//            the eigenbasis of Sigma1_hat (the translation block of Sigma_1)
+//   k_s_sig  s-block (3d) + z, residual and stop (last CTA)
+// With
+//   G1 = M(q_i t~_e) D,  G2 = W(q_l q_e) D,  G3 = W(t~_e p_i^*),  G4 = M(p_j^*) W(q_e),
+//   c~_e = q_i t~_e p_i^* (whole quaternion; its real part couples to the
+//   translation through Sigma_1's off-diagonal entries).
+// One thread per vertex, CSR gathers in edge order: deterministic.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "pradmm_device.cuh"
+#include "pradmm_internal.h"
+
+namespace pradmm {
+namespace {
+
+using namespace dev;
+
+template <typename T>
+struct Tol;
+template <>
+struct Tol<float> {
+    static __device__ __forceinline__ float jac() { return 1e-7f; }
+    static __device__ __forceinline__ float newton() { return 2e-7f; }
+};
+template <>
+struct Tol<double> {
+    static __device__ __forceinline__ double jac() { return 1e-15; }
+    static __device__ __forceinline__ double newton() { return 1e-15; }
+};
+
+// 4x4 matrices of quaternion multiplication (Appendix A.2): M(a) b = a b, W(b) a = a b.
+template <typename T>
+__device__ __forceinline__ void mat_M(const Q<T>& a, T m[4][4]) {
+    m[0][0] = a.w; m[0][1] = -a.x; m[0][2] = -a.y; m[0][3] = -a.z;
+    m[1][0] = a.x; m[1][1] = a.w;  m[1][2] = -a.z; m[1][3] = a.y;
+    m[2][0] = a.y; m[2][1] = a.z;  m[2][2] = a.w;  m[2][3] = -a.x;
+    m[3][0] = a.z; m[3][1] = -a.y; m[3][2] = a.x;  m[3][3] = a.w;
+}
+template <typename T>
+__device__ __forceinline__ void mat_W(const Q<T>& a, T m[4][4]) {
+    m[0][0] = a.w; m[0][1] = -a.x; m[0][2] = -a.y; m[0][3] = -a.z;
+    m[1][0] = a.x; m[1][1] = a.w;  m[1][2] = a.z;  m[1][3] = -a.y;
+    m[2][0] = a.y; m[2][1] = -a.z; m[2][2] = a.w;  m[2][3] = a.x;
+    m[3][0] = a.z; m[3][1] = a.y;  m[3][2] = -a.x; m[3][3] = a.w;
+}
+
+// A += w G^T S G (upper triangle of A is all that is read later, but the
+// full matrix is kept for the Jacobi sweeps)
+template <typename T, typename R>
+__device__ __forceinline__ void add_sandwich(T A[4][4], const T G[4][4], const R* S, T w) {
+    T X[4][4];  // S G
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            T v = T(0);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v += T(S[4 * r + k]) * G[k][c];
+            X[r][c] = v;
+        }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = r; c < 4; ++c) {
+            T v = T(0);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v += G[k][r] * X[k][c];
+            A[r][c] += w * v;
+            if (c != r) A[c][r] += w * v;
+        }
+}
+
+// y += w G^T (S v)
+template <typename T, typename R>
+__device__ __forceinline__ void add_gts(T y[4], const T G[4][4], const R* S, const T v[4], T w) {
+    T sv[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) sv[r] = T(S[4 * r]) * v[0] + T(S[4 * r + 1]) * v[1] + T(S[4 * r + 2]) * v[2] + T(S[4 * r + 3]) * v[3];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) y[c] += w * (G[0][c] * sv[0] + G[1][c] * sv[1] + G[2][c] * sv[2] + G[3][c] * sv[3]);
+}
+
+// D X D with D = diag(1, -1, -1, -1)
+template <typename T>
+__device__ __forceinline__ T dsign(int r) {
+    return r == 0 ? T(1) : T(-1);
+}
+
+// ---- Lemma 1: min_{|x| = 1} 1/2 x^T A x + b^T x ------------------------------
+
+template <typename T>
+__device__ __forceinline__ void jacobi_rotate(T a[4][4], T v[4][4], int p, int q) {
+    const T apq = a[p][q];
+    if (apq == T(0)) return;
+    const T theta = (a[q][q] - a[p][p]) / (T(2) * apq);
+    const T at = fabs(theta);
+    T t = at > T(1e15) ? T(0.5) / theta : (theta >= T(0) ? T(1) : T(-1)) / (at + sqrt(theta * theta + T(1)));
+    const T cs = T(1) / sqrt(t * t + T(1)), sn = t * cs;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const T kp = a[k][p], kq = a[k][q];
+        a[k][p] = cs * kp - sn * kq;
+        a[k][q] = sn * kp + cs * kq;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const T pk = a[p][k], qk = a[q][k];
+        a[p][k] = cs * pk - sn * qk;
+        a[q][k] = sn * pk + cs * qk;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const T kp = v[k][p], kq = v[k][q];
+        v[k][p] = cs * kp - sn * kq;
+        v[k][q] = sn * kp + cs * kq;
+    }
+}
+
+// Cyclic Jacobi: a -> diag (eigenvalues), v columns the eigenvectors, sorted ascending.
+template <typename T>
+__device__ void eig4(T a[4][4], T ev[4], T v[4][4]) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[r][c] = r == c ? T(1) : T(0);
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        T off = T(0), dg = T(0);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            dg += a[r][r] * a[r][r];
+#pragma unroll
+            for (int c = r + 1; c < 4; ++c) off += a[r][c] * a[r][c];
+        }
+        if (off <= Tol<T>::jac() * Tol<T>::jac() * dg) break;
+        jacobi_rotate(a, v, 0, 1);
+        jacobi_rotate(a, v, 0, 2);
+        jacobi_rotate(a, v, 0, 3);
+        jacobi_rotate(a, v, 1, 2);
+        jacobi_rotate(a, v, 1, 3);
+        jacobi_rotate(a, v, 2, 3);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ev[k] = a[k][k];
+    // sort ascending with the columns (selection, 4 elements)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        int mn = i;
+#pragma unroll
+        for (int j = i + 1; j < 4; ++j)
+            if (ev[j] < ev[mn]) mn = j;
+        if (mn != i) {
+            const T e = ev[i];
+            ev[i] = ev[mn];
+            ev[mn] = e;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const T x = v[r][i];
+                v[r][i] = v[r][mn];
+                v[r][mn] = x;
+            }
+        }
+    }
+}
+
+// Returns 1 if the solve should be repeated in FP64 (FP32 only: tiny eigen-gap or
+// a near-hard case), else writes x (unit) and returns 0.
+template <typename T>
+__device__ int trs4(const T A0[4][4], const T b[4], const T pk[4], T x[4], bool want_fallback) {
+    T a[4][4], v[4][4], ev[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) a[r][c] = A0[r][c];
+    eig4(a, ev, v);
+    T g[4], gn2 = T(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        g[k] = v[0][k] * b[0] + v[1][k] * b[1] + v[2][k] * b[2] + v[3][k] * b[3];
+        gn2 += g[k] * g[k];
+    }
+    const T scale = fmax(fmax(fabs(ev[0]), fabs(ev[3])), T(1e-30));
+    const T gn = sqrt(gn2);
+    if (want_fallback && ((ev[1] - ev[0]) < T(1e-3) * scale || fabs(g[0]) < T(1e-3) * gn)) return 1;
+    T y[4];
+    // hard case: no component of b on the bottom eigenvector, and the rest of
+    // the secular sum at lambda = -a_min is below 1
+    bool hard = fabs(g[0]) <= T(64) * Tol<T>::jac() * fmax(gn, scale);
+    if (hard) {
+        T rest = T(0);
+#pragma unroll
+        for (int k = 1; k < 4; ++k) {
+            const T d = ev[k] - ev[0];
+            if (d > T(64) * Tol<T>::jac() * scale) rest += g[k] * g[k] / (d * d);
+            else if (fabs(g[k]) > T(64) * Tol<T>::jac() * fmax(gn, scale)) rest = T(2);  // degenerate, not hard
+        }
+        hard = rest < T(1);
+        if (hard) {
+            y[0] = T(0);
+#pragma unroll
+            for (int k = 1; k < 4; ++k) {
+                const T d = ev[k] - ev[0];
+                y[k] = d > T(64) * Tol<T>::jac() * scale ? -g[k] / d : T(0);
+            }
+            const T alpha = sqrt(fmax(T(0), T(1) - (y[1] * y[1] + y[2] * y[2] + y[3] * y[3])));
+            // of the two signs keep the one closer to p^k: sign of v0 . (p^k - x_particular)
+            T xp[4], dot = T(0);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                xp[r] = v[r][1] * y[1] + v[r][2] * y[2] + v[r][3] * y[3];
+                dot += v[r][0] * (pk[r] - xp[r]);
+            }
+            const T sg = dot < T(0) ? T(-1) : T(1);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) x[r] = xp[r] + sg * alpha * v[r][0];
+            return 0;
+        }
+    }
+    // secular equation phi(lambda) = sum g_k^2 / (a_k + lambda)^2 = 1 on
+    // [-a_min + |g_0|, -a_min + |g|], Newton on 1/|x(lambda)| from the left
+    // (monotone), clamped to the bracket
+    const T lo = -ev[0] + fabs(g[0]), hi = -ev[0] + gn;
+    T lam = lo;
+    for (int it = 0; it < 60; ++it) {
+        T phi = T(0), w2 = T(0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const T d = T(1) / (ev[k] + lam);
+            const T gd = g[k] * d;
+            phi += gd * gd;
+            w2 += gd * gd * d;
+        }
+        const T nx = sqrt(phi);
+        if (fabs(nx - T(1)) <= Tol<T>::newton() || w2 <= T(0)) break;
+        T nl = lam + (nx - T(1)) * phi / w2;
+        nl = fmin(fmax(nl, lo), hi);
+        if (nl == lam) break;
+        lam = nl;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) y[k] = -g[k] / (ev[k] + lam);
+    T nn = T(0);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        x[r] = v[r][0] * y[0] + v[r][1] * y[1] + v[r][2] * y[2] + v[r][3] * y[3];
+        nn += x[r] * x[r];
+    }
+    const T inv = T(1) / sqrt(nn);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) x[r] *= inv;
+    return 0;
+}
+
+// ---- kernels --------------------------------------------------------------------
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_p_sig(GraphDev<R> g, StateDev<R> S, Coef<R> c, SigmaDev<R> sg, Ctrl* ctrl) {
+    if (ctrl->halt) return;
+    const long long k = ctrl->iter;
+    const R* pc = S.p[k & 1];
+    R* pn = S.p[(k + 1) & 1];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const Q<R> qi = asq<R>(IO<R>::ld(S.q, i)), li = asq<R>(IO<R>::ld(S.lam, i)), pk = asq<R>(IO<R>::ld(pc, i));
+        const R4<R> sr = IO<R>::ld(S.s, i);
+        R A[4][4], b[4] = {-c.beta1 * qi.w - li.w - c.g1 * pk.w, -c.beta1 * qi.x - li.x - c.g1 * pk.x,
+                           -c.beta1 * qi.y - li.y - c.g1 * pk.y, -c.beta1 * qi.z - li.z - c.g1 * pk.z};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) A[r][cc] = r == cc ? c.beta1 + c.g1 : R(0);
+        R G[4][4], bo[4] = {R(0), R(0), R(0), R(0)};
+        // out-edges: G1 = M(q_i t~_e) D (the D is applied once at the end)
+        for (int e = g.out_ptr[i]; e < g.out_ptr[i + 1]; ++e) {
+            const R4<R> te = IO<R>::ld(g.out_te, e);
+            const R4<R> tj = IO<R>::ld(S.t, g.out_idx[e]);
+            mat_M(qmul_pr(qi, te.a, te.b, te.c), G);
+            const R r4[4] = {R(0), tj.a - sr.a, tj.b - sr.b, tj.c - sr.c};
+            R Ao[4][4] = {};
+            add_sandwich(Ao, G, sg.S1, R(2) * te.d);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) A[r][cc] += dsign<R>(r) * dsign<R>(cc) * Ao[r][cc];
+            add_gts(bo, G, sg.S1, r4, R(-2) * te.d);
+        }
+        // in-edges: G2 = W(q_l q_e) D; the stored record is k_e q_e, so
+        // k_e G2^T S2 G2 = (1/k_e) W(h)^T S2 W(h) D-conjugated with h = q_l (k_e q_e),
+        // and -2 k_e G2^T S2 1~ = -2 D (sigma2 h^*) with sigma2 the first column of S2
+        Q<R> hs = {R(0), R(0), R(0), R(0)};
+        for (int e = g.in_ptr[i]; e < g.in_ptr[i + 1]; ++e) {
+            const Q<R> qk = asq<R>(IO<R>::ld(g.in_qk, e));
+            const R kap = sqrt(qk.w * qk.w + qk.x * qk.x + qk.y * qk.y + qk.z * qk.z);
+            const Q<R> h = qmul(asq<R>(IO<R>::ld(S.q, g.in_idx[e])), qk);
+            mat_W(h, G);
+            R Ai[4][4] = {};
+            add_sandwich(Ai, G, sg.S2, R(2) / kap);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) A[r][cc] += dsign<R>(r) * dsign<R>(cc) * Ai[r][cc];
+            hs.w += h.w;
+            hs.x += h.x;
+            hs.y += h.y;
+            hs.z += h.z;
+        }
+        // b_1 = own - 2 D (sum G1-part) - 2 D (sigma2 (sum h)^*)
+        const Q<R> s2 = {sg.S2[0], sg.S2[4], sg.S2[8], sg.S2[12]};
+        const Q<R> sh = qmul_c(s2, hs);
+        const R bi[4] = {sh.w, sh.x, sh.y, sh.z};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) b[r] += dsign<R>(r) * bo[r] - R(2) * dsign<R>(r) * bi[r];
+        const R pkv[4] = {pk.w, pk.x, pk.y, pk.z};
+        R x[4];
+        if (trs4<R>(A, b, pkv, x, sizeof(R) == sizeof(float))) {
+            double Ad[4][4], bd[4], pd[4], xd[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                bd[r] = double(b[r]);
+                pd[r] = double(pkv[r]);
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) Ad[r][cc] = double(A[r][cc]);
+            }
+            trs4<double>(Ad, bd, pd, xd, false);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) x[r] = R(xd[r]);
+            atomicAdd(&ctrl->fallbacks, 1ull);
+        }
+        IO<R>::st(pn, i, x[0], x[1], x[2], x[3]);
+    }
+}
+
+// 4x4 SPD solve by Cholesky (A = L L^T)
+template <typename T>
+__device__ __forceinline__ void chol_solve4(T A[4][4], T b[4], T x[4]) {
+    T L[4][4] = {};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        T d = A[j][j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+        const T ljj = sqrt(d);
+        L[j][j] = ljj;
+#pragma unroll
+        for (int i = j + 1; i < 4; ++i) {
+            T v = A[i][j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+            L[i][j] = v / ljj;
+        }
+    }
+    T y[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        T v = b[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) v -= L[i][k] * y[k];
+        y[i] = v / L[i][i];
+    }
+#pragma unroll
+    for (int i = 3; i >= 0; --i) {
+        T v = y[i];
+#pragma unroll
+        for (int k = i + 1; k < 4; ++k) v -= L[k][i] * x[k];
+        x[i] = v / L[i][i];
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_q_sig(GraphDev<R> g, StateDev<R> S, Coef<R> c, SigmaDev<R> sg, Ctrl* ctrl,
+                                               double* part, int pstride) {
+    __shared__ double sh[32];
+    if (ctrl->halt) return;
+    const long long k = ctrl->iter;
+    const R* pn = S.p[(k + 1) & 1];
+    Acc<R> adq, adl;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const Q<R> P = asq<R>(IO<R>::ld(pn, i)), qi = asq<R>(IO<R>::ld(S.q, i)), li = asq<R>(IO<R>::ld(S.lam, i));
+        const R4<R> sr = IO<R>::ld(S.s, i);
+        R A[4][4], b[4] = {c.beta1 * P.w - li.w + c.g2 * qi.w, c.beta1 * P.x - li.x + c.g2 * qi.x,
+                           c.beta1 * P.y - li.y + c.g2 * qi.y, c.beta1 * P.z - li.z + c.g2 * qi.z};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) A[r][cc] = r == cc ? c.beta1 + c.g2 : R(0);
+        const Q<R> Pc = {P.w, -P.x, -P.y, -P.z};
+        const Q<R> s2 = {sg.S2[0], sg.S2[4], sg.S2[8], sg.S2[12]};
+        for (int e = g.out_ptr[i]; e < g.out_ptr[i + 1]; ++e) {
+            const int j = g.out_idx[e];
+            const R4<R> te = IO<R>::ld(g.out_te, e);
+            const R4<R> tj = IO<R>::ld(S.t, j);
+            const Q<R> Pj = asq<R>(IO<R>::ld(pn, j));
+            const Q<R> qk = asq<R>(IO<R>::ld(g.out_qk, e));  // k_e q_e
+            const R kap = sqrt(qk.w * qk.w + qk.x * qk.x + qk.y * qk.y + qk.z * qk.z);
+            // G3 = W(t~_e p_i^*)
+            R G[4][4];
+            mat_W(qmul_pl(te.a, te.b, te.c, Pc), G);
+            add_sandwich(A, G, sg.S1, R(2) * te.d);
+            const R r4[4] = {R(0), tj.a - sr.a, tj.b - sr.b, tj.c - sr.c};
+            add_gts(b, G, sg.S1, r4, R(2) * te.d);
+            // G4' = M(p_j^*) W(k_e q_e) = k_e G4: k_e G4^T S2 G4 = (1/k_e) G4'^T S2 G4',
+            // 2 k_e G4^T S2 1~ = 2 G4'^T sigma2 = 2 (p_j sigma2) (k_e q_e)^*
+            R Mp[4][4], Wq[4][4];
+            mat_M(Q<R>{Pj.w, -Pj.x, -Pj.y, -Pj.z}, Mp);
+            mat_W(qk, Wq);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc)
+                    G[r][cc] = Mp[r][0] * Wq[0][cc] + Mp[r][1] * Wq[1][cc] + Mp[r][2] * Wq[2][cc] + Mp[r][3] * Wq[3][cc];
+            add_sandwich(A, G, sg.S2, R(2) / kap);
+            const Q<R> v = qmul_c(qmul(Pj, s2), qk);
+            b[0] += R(2) * v.w;
+            b[1] += R(2) * v.x;
+            b[2] += R(2) * v.y;
+            b[3] += R(2) * v.z;
+        }
+        R x[4];
+        chol_solve4(A, b, x);
+        const R lw = li.w - c.tb1 * (P.w - x[0]), lx = li.x - c.tb1 * (P.x - x[1]);
+        const R ly = li.y - c.tb1 * (P.y - x[2]), lz = li.z - c.tb1 * (P.z - x[3]);
+        IO<R>::st(S.q, i, x[0], x[1], x[2], x[3]);
+        IO<R>::st(S.lam, i, lw, lx, ly, lz);
+        R d0 = x[0] - qi.w, d1 = x[1] - qi.x, d2 = x[2] - qi.y, d3 = x[3] - qi.z;
+        adq.add(d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3);
+        d0 = lw - li.w; d1 = lx - li.x; d2 = ly - li.y; d3 = lz - li.z;
+        adl.add(d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3);
+    }
+    const double sq = block_sum(adq.get(), sh);
+    const double sl = block_sum(adl.get(), sh);
+    if (threadIdx.x == 0) {
+        part[SLOT_DQ * pstride + blockIdx.x] = sq;
+        part[SLOT_DLAM * pstride + blockIdx.x] = sl;
+    }
+}
+
+// E^T S1 w for a 4-vector w (rows 1..3 of S1)
+template <typename R>
+__device__ __forceinline__ void et_s1(const SigmaDev<R>& sg, const R w[4], R out[3]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        out[r] = sg.S1[4 * (r + 1)] * w[0] + sg.S1[4 * (r + 1) + 1] * w[1] + sg.S1[4 * (r + 1) + 2] * w[2] +
+                 sg.S1[4 * (r + 1) + 3] * w[3];
+}
+
+// (a Sigma1_hat + c I)^{-1} v through Sigma1_hat = U diag(mu) U^T
+template <typename R>
+__device__ __forceinline__ void solve_hat(const SigmaDev<R>& sg, R a, R cI, const R v[3], R x[3]) {
+    R y[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        y[k] = (sg.U[k] * v[0] + sg.U[3 + k] * v[1] + sg.U[6 + k] * v[2]) / (a * sg.mu[k] + cI);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) x[r] = sg.U[3 * r] * y[0] + sg.U[3 * r + 1] * y[1] + sg.U[3 * r + 2] * y[2];
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_t_sig(GraphDev<R> g, StateDev<R> S, Coef<R> c, SigmaDev<R> sg, Ctrl* ctrl,
+                                               double* part, int pstride) {
+    __shared__ double sh[32];
+    if (ctrl->halt) return;
+    const long long k = ctrl->iter;
+    const R* pn = S.p[(k + 1) & 1];
+    Acc<R> adt;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const R4<R> tr = IO<R>::ld(S.t, i), sr = IO<R>::ld(S.s, i), zr = IO<R>::ld(S.z, i);
+        R bv[3] = {c.beta2 * sr.a + zr.a + c.g3 * tr.a, c.beta2 * sr.b + zr.b + c.g3 * tr.b,
+                   c.beta2 * sr.c + zr.c + c.g3 * tr.c};
+        R a = R(0);
+        for (int e = g.in_ptr[i]; e < g.in_ptr[i + 1]; ++e) {
+            const int l = g.in_idx[e];
+            const R4<R> te = IO<R>::ld(g.in_te, e);
+            const R4<R> sl = IO<R>::ld(S.s, l);
+            const Q<R> cq = qmul_c(qmul_pr(asq<R>(IO<R>::ld(S.q, l)), te.a, te.b, te.c), asq<R>(IO<R>::ld(pn, l)));
+            const R w[4] = {cq.w, sl.a + cq.x, sl.b + cq.y, sl.c + cq.z};
+            R o[3];
+            et_s1(sg, w, o);
+            const R w2 = R(2) * te.d;
+            bv[0] += w2 * o[0];
+            bv[1] += w2 * o[1];
+            bv[2] += w2 * o[2];
+            a += w2;
+        }
+        R x[3];
+        solve_hat(sg, a, c.beta2 + c.g3, bv, x);
+        IO<R>::st(S.t, i, x[0], x[1], x[2], tr.d);
+        const R d0 = x[0] - tr.a, d1 = x[1] - tr.b, d2 = x[2] - tr.c;
+        adt.add(d0 * d0 + d1 * d1 + d2 * d2);
+    }
+    const double st = block_sum(adt.get(), sh);
+    if (threadIdx.x == 0) part[SLOT_DT * pstride + blockIdx.x] = st;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_s_sig(GraphDev<R> g, StateDev<R> S, Coef<R> c, SigmaDev<R> sg, Launch L) {
+    __shared__ double sh[32];
+    Ctrl* ctrl = L.ctrl;
+    if (ctrl->halt) {
+        if (L.has_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(L.cond, 0u);
+        return;
+    }
+    const long long k = ctrl->iter;
+    const R* pn = S.p[(k + 1) & 1];
+    Acc<R> adz;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const R4<R> tr = IO<R>::ld(S.t, i), sr = IO<R>::ld(S.s, i), zr = IO<R>::ld(S.z, i);
+        const Q<R> qi = asq<R>(IO<R>::ld(S.q, i)), P = asq<R>(IO<R>::ld(pn, i));
+        R bv[3] = {c.beta2 * tr.a - zr.a + c.g4 * sr.a, c.beta2 * tr.b - zr.b + c.g4 * sr.b,
+                   c.beta2 * tr.c - zr.c + c.g4 * sr.c};
+        R a = R(0);
+        for (int e = g.out_ptr[i]; e < g.out_ptr[i + 1]; ++e) {
+            const R4<R> te = IO<R>::ld(g.out_te, e);
+            const R4<R> tj = IO<R>::ld(S.t, g.out_idx[e]);
+            const Q<R> cq = qmul_c(qmul_pr(qi, te.a, te.b, te.c), P);
+            const R w[4] = {-cq.w, tj.a - cq.x, tj.b - cq.y, tj.c - cq.z};
+            R o[3];
+            et_s1(sg, w, o);
+            const R w2 = R(2) * te.d;
+            bv[0] += w2 * o[0];
+            bv[1] += w2 * o[1];
+            bv[2] += w2 * o[2];
+            a += w2;
+        }
+        R x[3];
+        solve_hat(sg, a, c.beta2 + c.g4, bv, x);
+        const R zx = zr.a - c.tb2 * (tr.a - x[0]), zy = zr.b - c.tb2 * (tr.b - x[1]), zz = zr.c - c.tb2 * (tr.c - x[2]);
+        IO<R>::st(S.s, i, x[0], x[1], x[2], sr.d);
+        IO<R>::st(S.z, i, zx, zy, zz, zr.d);
+        const R d0 = zx - zr.a, d1 = zy - zr.b, d2 = zz - zr.c;
+        adz.add(d0 * d0 + d1 * d1 + d2 * d2);
+    }
+    const double sd = block_sum(adz.get(), sh);
+    if (threadIdx.x == 0) L.part[SLOT_DZ * L.pstride + blockIdx.x] = sd;
+    finish_iteration(ctrl, L, c.b1d, c.b2d, sh);
+}
+
+// F of Eq. (1) with Sigma-weighted norms at (p^k, t^k), in double.
+template <typename R>
+__global__ void __launch_bounds__(256) k_objective_sig(GraphDev<R> g, StateDev<R> S, const double* __restrict__ qe,
+                                                       const double* __restrict__ te, const double* __restrict__ ka,
+                                                       const double* __restrict__ om, const double* __restrict__ S1,
+                                                       const double* __restrict__ S2, Ctrl* ctrl, double* part,
+                                                       unsigned int* ticket, double* F) {
+    __shared__ double sh[32];
+    __shared__ bool last;
+    const R* pc = S.p[ctrl->iter & 1];
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const Q<double> pi = asq<double>(IO<R>::ld(pc, i));
+        const R4<R> ti = IO<R>::ld(S.t, i);
+        for (int e = g.out_ptr[i]; e < g.out_ptr[i + 1]; ++e) {
+            const int j = g.out_idx[e];
+            const Q<double> pj = asq<double>(IO<R>::ld(pc, j));
+            const R4<R> tj = IO<R>::ld(S.t, j);
+            const Q<double> rot = qmul_c(qmul_pr(pi, te[3 * e], te[3 * e + 1], te[3 * e + 2]), pi);
+            const double rho[4] = {-rot.w, double(tj.a) - double(ti.a) - rot.x, double(tj.b) - double(ti.b) - rot.y,
+                                   double(tj.c) - double(ti.c) - rot.z};
+            const Q<double> qq = {qe[4 * e], qe[4 * e + 1], qe[4 * e + 2], qe[4 * e + 3]};
+            Q<double> h = qmul(qmul(Q<double>{pj.w, -pj.x, -pj.y, -pj.z}, pi), qq);
+            const double eta[4] = {h.w - 1.0, h.x, h.y, h.z};
+            double f1 = 0.0, f2 = 0.0;
+            for (int r = 0; r < 4; ++r)
+                for (int cc = 0; cc < 4; ++cc) {
+                    f1 += rho[r] * S1[4 * r + cc] * rho[cc];
+                    f2 += eta[r] * S2[4 * r + cc] * eta[cc];
+                }
+            acc += om[e] * f1 + ka[e] * f2;
+        }
+    }
+    const double bs = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = bs;
+    __threadfence();
+    if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double v = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) v += __ldcg(part + b);
+    const double tot = block_sum(v, sh);
+    if (threadIdx.x == 0) {
+        *F = tot;
+        *ticket = 0u;
+    }
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_sigma_iteration(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c,
+                                   const SigmaDev<R>& sg, const Launch& L) {
+    k_p_sig<R><<<L.grid_p, L.block, 0, L.stream>>>(g, s, c, sg, L.ctrl);
+    k_q_sig<R><<<L.grid_q, L.block, 0, L.stream>>>(g, s, c, sg, L.ctrl, L.part, L.pstride);
+    k_t_sig<R><<<L.grid_t, L.block, 0, L.stream>>>(g, s, c, sg, L.ctrl, L.part, L.pstride);
+    k_s_sig<R><<<L.grid_sp, L.block, 0, L.stream>>>(g, s, c, sg, L);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_objective_sigma(const GraphDev<R>& g, const StateDev<R>& s, const double* qe64,
+                                   const double* te64, const double* ka64, const double* om64, const double* S1,
+                                   const double* S2, Ctrl* ctrl, double* part, unsigned int* ticket, double* F_dev,
+                                   int grid, int block, cudaStream_t st) {
+    k_objective_sig<R><<<grid, block, 0, st>>>(g, s, qe64, te64, ka64, om64, S1, S2, ctrl, part, ticket, F_dev);
+    return cudaGetLastError();
+}
+
+#define PRADMM_SIGMA_INST(R)                                                                                      \
+    template cudaError_t launch_sigma_iteration<R>(const GraphDev<R>&, const StateDev<R>&, const Coef<R>&,         \
+                                                   const SigmaDev<R>&, const Launch&);                            \
+    template cudaError_t launch_objective_sigma<R>(const GraphDev<R>&, const StateDev<R>&, const double*,         \
+                                                   const double*, const double*, const double*, const double*,    \
+                                                   const double*, Ctrl*, double*, unsigned int*, double*, int, int, \
+                                                   cudaStream_t);
+
+PRADMM_SIGMA_INST(float)
+PRADMM_SIGMA_INST(double)
+
+}  // namespace pradmm

@@ -76,6 +76,7 @@ _SIGS = {
     "pradmm_bytes_per_iteration": (ctypes.c_int, [_h, _d]),
     "pradmm_profile_sweeps": (ctypes.c_int, [_h, ctypes.c_int32, _d]),
     "pradmm_l2_window_info": (ctypes.c_int, [_h, _d]),
+    "pradmm_set_sigma": (ctypes.c_int, [_h, _d, _d]),
     "pradmm_adjoint_record": (ctypes.c_int, [_h, ctypes.c_int32, ctypes.c_int32]),
     "pradmm_adjoint": (ctypes.c_int, [_h, _d, _d, _d, _d, _d, _d, _d]),
     "pradmm_adjoint_device": (ctypes.c_int, [_h] + [ctypes.c_void_p] * 7),
@@ -259,6 +260,13 @@ def pradmm_profile_sweeps(h, iters: int) -> dict:
     return {"k_q": out[0], "k_t": out[1], "k_sp": out[2], "iteration": out[3]}
 
 
+def pradmm_set_sigma(h, Sigma1=None, Sigma2=None):
+    """General 4x4 weight matrices (row-major); both None returns to Sigma = I."""
+    S1 = None if Sigma1 is None else _f64(Sigma1, (4, 4))
+    S2 = None if Sigma2 is None else _f64(Sigma2, (4, 4))
+    _check(load().pradmm_set_sigma(h, _dp(S1), _dp(S2)), "pradmm_set_sigma")
+
+
 def pradmm_adjoint_record(h, iters: int, ckpt_every: int = 20):
     _check(load().pradmm_adjoint_record(h, int(iters), int(ckpt_every)), "pradmm_adjoint_record")
 
@@ -372,6 +380,9 @@ class Solver:
 
     def poses(self):
         return pradmm_get_poses(self.h, self.n)
+
+    def set_sigma(self, Sigma1=None, Sigma2=None):
+        pradmm_set_sigma(self.h, Sigma1, Sigma2)
 
     def adjoint_record(self, iters, ckpt_every=20):
         pradmm_adjoint_record(self.h, iters, ckpt_every)

@@ -1,0 +1,129 @@
+"""General weight matrices on the GPU (pradmm_set_sigma) against the
+general-Sigma oracle (itself pinned by brute force on S^3, the scalar
+reduction and block minimality).
+
+Tolerances, relerr per state array: FP64 1e-9 (the p-update's sphere-
+constrained solve goes through an eigen-decomposition and a secular equation
+on both sides, by different algorithms: Jacobi + Newton here, the
+8x8 eigenproblem of Algorithm 2 in the oracle); FP32 1e-4 for p, q, t, s.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import general_sigma as gs
+from paper_2601_15684_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+KEYS = ("p", "q", "t", "s", "lam", "z")
+PARAMS = (1.0, 1.0, 1.5, (1.0, 1e-3, 1e-3, 1e-3))
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2601_15684_gb300 import build_lib
+    from paper_2601_15684_gb300 import pradmm
+    build_lib.build()
+    pradmm.load()
+    return pradmm
+
+
+def relerr(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _spd(rng, cond=8.0):
+    Q, _ = np.linalg.qr(rng.normal(size=(4, 4)))
+    return Q @ np.diag(np.exp(rng.uniform(0, np.log(cond), 4))) @ Q.T
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-9), (1, 1e-4)])
+def test_general_sigma_matches_oracle(P, precision, tol):
+    rng = np.random.default_rng(3)
+    g = synth.random_graph(97, 300, seed=5, isolated=2)
+    st = synth.random_state(rng, g.n)
+    S1, S2 = _spd(rng), _spd(rng)
+    orc = st
+    with P.Solver(g, precision=precision) as S:
+        S.set_sigma(S1, S2)
+        S.set_state_full(st)
+        done = 0
+        for it in (1, 10):
+            S.step(it - done)
+            for _ in range(it - done):
+                orc, _, _ = gs.iterate(g, PARAMS, S1, S2, orc)
+            done = it
+            gpu = S.state()
+            for key in ("p", "q", "t", "s"):
+                assert relerr(gpu[key], orc[key]) <= tol, (it, key, relerr(gpu[key], orc[key]))
+            if precision == 0:
+                for key in ("lam", "z"):
+                    assert relerr(gpu[key], orc[key]) <= tol, (it, key)
+        F = S.objective()
+    assert abs(F - gs.objective(g, S1, S2, orc["p"], orc["t"])) <= (1e-10 if precision == 0 else 1e-4) * max(F, 1.0)
+
+
+def test_identity_sigma_equals_scalar_path(P):
+    g = synth.random_graph(120, 360, seed=8)
+    st = synth.random_state(np.random.default_rng(2), g.n)
+    out = []
+    for use_sigma in (False, True):
+        with P.Solver(g, precision=0) as S:
+            if use_sigma:
+                S.set_sigma(np.eye(4), np.eye(4))
+            S.set_state_full(st)
+            S.step(12)
+            out.append(S.state())
+    for key in KEYS:
+        assert relerr(out[1][key], out[0][key]) <= 1e-12, key
+
+
+def test_walk_with_anisotropic_weights_converges_like_oracle(P):
+    rng = np.random.default_rng(1)
+    g = synth.random_walk_graph(60, n_closures=40, sigma_r=0.02, sigma_t=0.1, seed=4)
+    S1 = np.diag([1.0, 4.0, 1.0, 0.25])
+    S2 = _spd(rng, 3.0)
+    q0, t0 = oracle.init_odometry(g)
+    orc = oracle.init_state(q0, t0)
+    es = []
+    for _ in range(60):
+        orc, e, _ = gs.iterate(g, PARAMS, S1, S2, orc)
+        es.append(e)
+    with P.Solver(g, precision=0) as S:
+        S.set_sigma(S1, S2)
+        S.init_odometry()
+        e_gpu = S.step(60)
+        gpu = S.state()
+    assert abs(e_gpu - es[-1]) <= 1e-7 * max(es[-1], 1e-30)
+    assert es[-1] < 1e-2 * es[0]  # the residual falls (3e-3 of the first after 60 iterations)
+    for key in KEYS:
+        assert relerr(gpu[key], orc[key]) <= 1e-8, key
+
+
+def test_set_sigma_validation_and_reset(P):
+    g = synth.random_graph(30, 80, seed=1)
+    st = synth.random_state(np.random.default_rng(0), g.n)
+    with P.Solver(g, precision=0) as S:
+        bad = np.eye(4)
+        bad[0, 1] = 0.5  # not symmetric
+        for S1, S2 in ((bad, np.eye(4)), (np.eye(4), -np.eye(4)), (np.eye(4), None)):
+            with pytest.raises(P.PRADMMError) as ei:
+                S.set_sigma(S1, S2)
+            assert ei.value.status == P.PRADMM_ERR_ARG
+        nan = np.eye(4)
+        nan[2, 2] = np.nan
+        with pytest.raises(P.PRADMMError) as ei:
+            S.set_sigma(nan, np.eye(4))
+        assert ei.value.status == P.PRADMM_ERR_NONFINITE
+        S.set_sigma(2.0 * np.eye(4), np.eye(4))
+        S.set_state_full(st)
+        with pytest.raises(P.PRADMMError) as ei:
+            S.adjoint_record(3, 1)
+        assert ei.value.status == P.PRADMM_ERR_STATE
+        S.set_sigma(None, None)  # back to the scalar model
+        S.set_state_full(st)
+        S.step(5)
+        a = S.state()
+    ref, _, _ = oracle.iterate(g, oracle.make_params(beta1=1.0, beta2=1.0, tau=1.5), st, 5)
+    for key in KEYS:
+        assert relerr(a[key], ref[key]) <= 1e-10, key
