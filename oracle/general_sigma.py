@@ -84,6 +84,26 @@ def trs_sphere(A, b, x_prev=None):
     return x1, lam, True
 
 
+def p_system(g, params, Sigma1, Sigma2, st, i):
+    """A_1 and b_1 of the p-block of vertex i (Appendix B.1), as assembled in
+    `iterate`."""
+    beta1, _, _, gam = params
+    S1, S2 = np.asarray(Sigma1, dtype=np.float64), np.asarray(Sigma2, dtype=np.float64)
+    p, q, t, s, lam = st["p"], st["q"], st["t"], st["s"], st["lam"]
+    A1 = (beta1 + gam[0]) * np.eye(4)
+    b1 = -beta1 * q[i] - lam[i] - gam[0] * p[i]
+    for e in np.nonzero(g.src == i)[0]:
+        G1 = M(q[i]) @ M(pure(g.t_meas[e])) @ D
+        r = pure(t[g.dst[e]]) - pure(s[i])
+        A1 += 2.0 * g.omega[e] * G1.T @ S1 @ G1
+        b1 -= 2.0 * g.omega[e] * G1.T @ S1 @ r
+    for e in np.nonzero(g.dst == i)[0]:
+        G2 = W(g.q_meas[e]) @ W(q[g.src[e]]) @ D
+        A1 += 2.0 * g.kappa[e] * G2.T @ S2 @ G2
+        b1 -= 2.0 * g.kappa[e] * G2.T @ S2 @ ONE
+    return A1, b1
+
+
 def iterate(g, params, Sigma1, Sigma2, st):
     """One iteration of Eq. (3a)-(3f) with weights omega_e Sigma1, kappa_e Sigma2.
     params: (beta1, beta2, tau, (gamma1..gamma4)).  Returns (new_state, e^{k+1},

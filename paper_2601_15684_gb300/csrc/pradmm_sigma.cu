@@ -181,9 +181,13 @@ __device__ void eig4(T a[4][4], T ev[4], T v[4][4]) {
 }
 
 // Returns 1 if the solve should be repeated in FP64 (FP32 only: tiny eigen-gap or
-// a near-hard case), else writes x (unit) and returns 0.
+// a near-hard case), else writes x (unit) and returns 0.  hard_eps: relative
+// size below which b's component on the bottom eigenvector counts as zero --
+// the accuracy of the data A and b, not of the arithmetic (FP32 data re-solved
+// in FP64 keeps the FP32 threshold, so the hard case and its sign rule apply
+// as they would to exact data).
 template <typename T>
-__device__ int trs4(const T A0[4][4], const T b[4], const T pk[4], T x[4], bool want_fallback) {
+__device__ int trs4(const T A0[4][4], const T b[4], const T pk[4], T x[4], bool want_fallback, T hard_eps) {
     T a[4][4], v[4][4], ev[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
@@ -202,14 +206,14 @@ __device__ int trs4(const T A0[4][4], const T b[4], const T pk[4], T x[4], bool 
     T y[4];
     // hard case: no component of b on the bottom eigenvector, and the rest of
     // the secular sum at lambda = -a_min is below 1
-    bool hard = fabs(g[0]) <= T(64) * Tol<T>::jac() * fmax(gn, scale);
+    bool hard = fabs(g[0]) <= hard_eps * fmax(gn, scale);
     if (hard) {
         T rest = T(0);
 #pragma unroll
         for (int k = 1; k < 4; ++k) {
             const T d = ev[k] - ev[0];
             if (d > T(64) * Tol<T>::jac() * scale) rest += g[k] * g[k] / (d * d);
-            else if (fabs(g[k]) > T(64) * Tol<T>::jac() * fmax(gn, scale)) rest = T(2);  // degenerate, not hard
+            else if (fabs(g[k]) > hard_eps * fmax(gn, scale)) rest = T(2);  // degenerate, not hard
         }
         hard = rest < T(1);
         if (hard) {
@@ -236,7 +240,8 @@ __device__ int trs4(const T A0[4][4], const T b[4], const T pk[4], T x[4], bool 
     // secular equation phi(lambda) = sum g_k^2 / (a_k + lambda)^2 = 1 on
     // [-a_min + |g_0|, -a_min + |g|], Newton on 1/|x(lambda)| from the left
     // (monotone), clamped to the bracket
-    const T lo = -ev[0] + fabs(g[0]), hi = -ev[0] + gn;
+    // (a lower end strictly above -a_min keeps every 1/(a_k + lambda) finite)
+    const T lo = -ev[0] + fmax(fabs(g[0]), T(64) * Tol<T>::jac() * scale), hi = fmax(-ev[0] + gn, lo);
     T lam = lo;
     for (int it = 0; it < 60; ++it) {
         T phi = T(0), w2 = T(0);
@@ -328,7 +333,7 @@ __global__ void __launch_bounds__(256) k_p_sig(GraphDev<R> g, StateDev<R> S, Coe
         for (int r = 0; r < 4; ++r) b[r] += dsign<R>(r) * bo[r] - R(2) * dsign<R>(r) * bi[r];
         const R pkv[4] = {pk.w, pk.x, pk.y, pk.z};
         R x[4];
-        if (trs4<R>(A, b, pkv, x, sizeof(R) == sizeof(float))) {
+        if (trs4<R>(A, b, pkv, x, sizeof(R) == sizeof(float), R(64) * Tol<R>::jac())) {
             double Ad[4][4], bd[4], pd[4], xd[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
@@ -337,7 +342,7 @@ __global__ void __launch_bounds__(256) k_p_sig(GraphDev<R> g, StateDev<R> S, Coe
 #pragma unroll
                 for (int cc = 0; cc < 4; ++cc) Ad[r][cc] = double(A[r][cc]);
             }
-            trs4<double>(Ad, bd, pd, xd, false);
+            trs4<double>(Ad, bd, pd, xd, false, 1e-5);  // FP32 data
 #pragma unroll
             for (int r = 0; r < 4; ++r) x[r] = R(xd[r]);
             atomicAdd(&ctrl->fallbacks, 1ull);

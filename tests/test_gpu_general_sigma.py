@@ -127,3 +127,35 @@ def test_set_sigma_validation_and_reset(P):
     ref, _, _ = oracle.iterate(g, oracle.make_params(beta1=1.0, beta2=1.0, tau=1.5), st, 5)
     for key in KEYS:
         assert relerr(a[key], ref[key]) <= 1e-10, key
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-9), (1, 1e-5)])
+def test_hard_case_of_the_p_update(P, precision, tol):
+    # vertex 0's multiplier is chosen so that its b_1 has no component on the
+    # bottom eigenvector of A_1 and |-(A_1 - a_min I)^+ b_1| < 1: the p-update
+    # is the hard case of Lemma 1 on both sides (the FP32 handle re-solves it
+    # in FP64), and the sign rule (closer to p^k) picks the same minimiser
+    rng = np.random.default_rng(6)
+    g = synth.random_graph(10, 24, seed=3)
+    st = synth.random_state(rng, g.n)
+    S1, S2 = _spd(rng), _spd(rng)
+    st["lam"][0] = 0.0
+    A1, b0 = gs.p_system(g, PARAMS, S1, S2, st, 0)
+    a, V = np.linalg.eigh(A1)
+    b_des = 0.3 * (a[1] - a[0]) * V[:, 1] + 0.2 * (a[2] - a[0]) * V[:, 2]
+    st["lam"][0] = b0 - b_des
+    A1b, b1 = gs.p_system(g, PARAMS, S1, S2, st, 0)
+    _, _, hard = gs.trs_sphere(A1b, b1, st["p"][0])
+    assert hard
+    orc, _, nh = gs.iterate(g, PARAMS, S1, S2, st)
+    assert nh >= 1
+    with P.Solver(g, precision=precision) as S:
+        S.set_sigma(S1, S2)
+        S.set_state_full(st)
+        S.step(1)
+        gpu = S.state()
+        fallbacks = P.pradmm_counters(S.h)["fallbacks"]
+    assert np.linalg.norm(gpu["p"][0] - orc["p"][0]) <= tol
+    assert relerr(gpu["p"], orc["p"]) <= tol
+    if precision == 1:
+        assert fallbacks >= 1

@@ -163,3 +163,15 @@ def test_noise_free_truth_is_a_fixed_point_for_any_sigma():
     for key in ("t", "s"):
         np.testing.assert_allclose(x[key], g.t_gt, atol=1e-12)
     assert gs.objective(g, S1, S2, g.q_gt, g.t_gt) < 1e-24
+
+
+def test_p_system_matches_iterate():
+    rng = np.random.default_rng(9)
+    g = synth.random_graph(8, 20, seed=4)
+    st = synth.random_state(rng, g.n)
+    S1, S2 = _spd(rng, 4), _spd(rng, 4)
+    new, _, _ = gs.iterate(g, PARAMS, S1, S2, st)
+    for i in range(g.n):
+        A1, b1 = gs.p_system(g, PARAMS, S1, S2, st, i)
+        x, _, _ = gs.trs_sphere(A1, b1, st["p"][i])
+        np.testing.assert_allclose(x, new["p"][i], atol=1e-12)
