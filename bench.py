@@ -193,6 +193,31 @@ def run_batched(P, sample=32):
             "speedup_vs_plain": plain_total / t_batch, "objective_max_rel_diff_vs_plain": rel_F}
 
 
+def run_general_sigma(P, g, iters=300):
+    """General weight matrices (Lemma 1 p-update, 4x4/3x3 block solves) on the
+    same 1M-pose lattice, FP32, graph-launched, against the scalar path on the
+    same GPU: time per iteration and the FP64 re-solves of the p-update."""
+    rng = np.random.default_rng(0)
+    Q, _ = np.linalg.qr(rng.normal(size=(4, 4)))
+    S1 = Q @ np.diag([1.0, 2.0, 0.5, 4.0]) @ Q.T
+    S2 = np.diag([1.0, 0.5, 2.0, 1.0])
+    out = {}
+    for mode in ("scalar", "general"):
+        with P.Solver(g, precision=P.PRADMM_FP32) as S:
+            if mode == "general":
+                S.set_sigma(S1, S2)
+            S.init_odometry()
+            S.step(10)
+            t0 = time.perf_counter()
+            S.step(iters)
+            dt = (time.perf_counter() - t0) / iters
+            out[mode] = {"ms_per_iteration": 1e3 * dt, "edge_updates_per_s": g.m / dt,
+                         "fp64_resolves": P.pradmm_counters(S.h)["fallbacks"]}
+    return {"workload": "lattice1m with Sigma_1 = Q diag(1, 2, 0.5, 4) Q^T (random rotation Q), "
+                        "Sigma_2 = diag(1, 0.5, 2, 1)", "iterations": iters, **out,
+            "general_over_scalar_time": out["general"]["ms_per_iteration"] / out["scalar"]["ms_per_iteration"]}
+
+
 def run_adjoint(P, K=200, ckpt=20, reps=5):
     """Reverse mode vs the plain forward on the 10,000-pose walk (~30k edges):
     K unrolled iterations from the odometry start, checkpoint every `ckpt`.
@@ -420,6 +445,9 @@ def run_ours(args):
     adjoint = None
     if rank == 0 and ws == 1 and not args.no_adjoint:
         adjoint = run_adjoint(P)
+    general = None
+    if rank == 0 and ws == 1 and not args.no_general:
+        general = run_general_sigma(P, g)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = _cpu_baseline(g)
@@ -454,6 +482,8 @@ def run_ours(args):
         line["batched"] = batched
     if adjoint is not None:
         line["adjoint"] = adjoint
+    if general is not None:
+        line["general_sigma"] = general
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
@@ -472,6 +502,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-general", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
