@@ -179,3 +179,44 @@ def test_batch_autotune_keeps_state(P):
         after = B.state()
         for key in KEYS:
             np.testing.assert_array_equal(after[key], before[key])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_large_graphs_of_the_bench_distribution(P, precision):
+    # the largest graphs of the 4,096-walk batch recipe (n_g log-uniform in
+    # [50, 20000]) plus a spread of smaller ones, with clusters for the large
+    # graphs, against the FP64 oracle graph by graph: FP64 to 1e-10; FP32 no
+    # further from the oracle than the plain FP32 solver (both round
+    # differently, so they are compared through the oracle, not to each other)
+    rng = np.random.default_rng(4)
+    ns = np.exp(rng.uniform(np.log(50), np.log(20000), 4096)).round().astype(int)
+    dens = rng.uniform(0.5, 3.0, 4096)
+    seeds = rng.integers(0, 2 ** 62, 4096)
+    pick = list(np.argsort(-ns)[:4]) + list(rng.choice(4096, 8, replace=False))
+    graphs = [synth.random_walk_graph(int(ns[k]), n_closures=None, closure_density=float(dens[k]), sigma_r=0.02,
+                                      sigma_t=0.1, seed=int(seeds[k])) for k in pick]
+    assert max(g.n for g in graphs) > 19000
+    K = 30
+    with P.Batch(graphs, precision=precision) as B:
+        B.set_schedule(256, 64, 8, 2048)
+        B.init_odometry()
+        res = B.solve(rel_tol=0.0, max_iter=K)
+        st = B.state()
+    assert (res["iters"] == K).all()
+    prm = oracle.make_params(beta1=1.0, beta2=1.0, tau=1.5)
+    rel = lambda x, y: np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-300)
+    for k, g in enumerate(graphs):
+        q0, t0 = oracle.init_odometry(g)
+        orc, _, _ = oracle.iterate(g, prm, oracle.init_state(q0, t0), K)
+        sl = _slice(st, B.offsets[k], B.offsets[k + 1])
+        if precision == 0:
+            for key in KEYS:
+                assert rel(sl[key], orc[key]) <= 1e-10, (k, g.n, key, rel(sl[key], orc[key]))
+            continue
+        with P.Solver(g, precision=1) as S:
+            S.init_odometry()
+            S.step(K)
+            ref = S.state()
+        for key in ("p", "q", "t", "s"):
+            eb, ep = rel(sl[key], orc[key]), rel(ref[key], orc[key])
+            assert eb <= 3.0 * ep + 1e-6, (k, g.n, key, eb, ep)

@@ -95,3 +95,27 @@ def test_helix25k_2000_iterations_objective(P, precision, tol):
     print(f"helix25k precision={precision}: F={F:.12e} oracle={F_ref:.12e} relerr={err:.3e} "
           f"relerr(p)={relerr(st['p'], orc['p']):.3e} relerr(t)={relerr(st['t'], orc['t']):.3e}")
     assert err <= tol
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-9), (1, 1e-4)])
+def test_lattice1m_general_sigma_p_update_sampled(P, precision, tol):
+    # the general-Sigma p-update (Lemma 1) of 200 sampled vertices of the 1M-pose
+    # lattice, each recomputed by the oracle from the same x^0 one by one
+    from oracle import general_sigma as gs
+    g = synth.workload("lattice1m")
+    q0, t0 = oracle.init_odometry(g)
+    st = oracle.init_state(q0, t0)
+    rng = np.random.default_rng(7)
+    Q, _ = np.linalg.qr(rng.normal(size=(4, 4)))
+    S1 = Q @ np.diag([1.0, 2.0, 0.5, 4.0]) @ Q.T
+    S2 = np.diag([1.0, 0.5, 2.0, 1.0])
+    with P.Solver(g, precision=precision) as S:
+        S.set_sigma(S1, S2)
+        S.init_odometry()
+        S.step(1)
+        p1 = S.state()["p"]
+    params = (1.0, 1.0, 1.5, (1.0, 1e-3, 1e-3, 1e-3))
+    for i in rng.choice(g.n, 200, replace=False):
+        A1, b1 = gs.p_system(g, params, S1, S2, st, int(i))
+        x, _, _ = gs.trs_sphere(A1, b1, st["p"][i])
+        assert np.linalg.norm(p1[i] - x) <= tol, (int(i), np.linalg.norm(p1[i] - x))
