@@ -290,16 +290,65 @@ __device__ __forceinline__ void for_edges(int e0, int e1, LoadF load, UseF use) 
     }
 }
 
+// As for_edges with each edge's loads split in two: load_a(e, buffer) the
+// loads that need only e (the neighbour index and the edge records),
+// load_b(buffer) the gathers that need the index.  PIPE overlaps a group's
+// gathers with the next group's index and record loads (one dependent load
+// level per group instead of two) at the cost of registers: it pays where the
+// kernel has registers to spare (measured: the plain t sweep).  Uses run in
+// edge order either way; rounding can differ where the compiler contracts
+// multiply-adds differently.
+template <typename T, bool PIPE, typename LoadA, typename LoadB, typename UseF>
+__device__ __forceinline__ void for_edges2(int e0, int e1, LoadA load_a, LoadB load_b, UseF use) {
+    if (!PIPE) {
+        for_edges<T>(
+            e0, e1,
+            [&](int e, T& x) {
+                load_a(e, x);
+                load_b(x);
+            },
+            use);
+        return;
+    }
+    if (e0 >= e1) return;
+    T a[kUnroll];
+    int cnt = e1 - e0 < kUnroll ? e1 - e0 : kUnroll;
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+        if (u < cnt) load_a(e0 + u, a[u]);
+    int e = e0;
+    for (;;) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (u < cnt) load_b(a[u]);
+        const int en = e + cnt;
+        const int cn = e1 - en < kUnroll ? e1 - en : kUnroll;
+        T nx[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (u < cn) load_a(en + u, nx[u]);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (u < cnt) use(a[u]);
+        if (cn <= 0) break;
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) a[u] = nx[u];
+        e = en;
+        cnt = cn;
+    }
+}
+
 // ---- q-block (3b) / Appendix B.2 + lambda (3e) --------------------------------
 // q_i = [sum_{e=(i,j)} 2 (w_e r~ p_i t~_e^* + k_e p_j q_e^*) + beta1 p_i - lam_i + gamma2 q_i] / A_2,
 // r = t_j - s_i (t^k, s^k), p = p^{k+1};  lam_i -= tau beta1 (p_i - q_i^{new}).
 template <typename R>
 struct QEdge {
+    int j;
     R4<R> te, qk, tj, pj;
 };
 
 // One vertex of the q-block + lambda update; adds |dq_i|^2, |dlam_i|^2.
-template <typename R>
+template <typename R, bool PIPE = false>
 __device__ __forceinline__ void q_vertex(const GraphDev<R>& g, const StateDev<R>& S, const Coef<R>& c, const R* pn,
                                          int64_t i, Acc<R>& adq, Acc<R>& adl) {
     const Q<R> pi = asq<R>(IO<R>::ld(pn, i));
@@ -308,14 +357,16 @@ __device__ __forceinline__ void q_vertex(const GraphDev<R>& g, const StateDev<R>
     const R4<R> sr = IO<R>::ld(S.s, i);  // (s_i, 1/A_2)
     Q<R> b = {c.beta1 * pi.w - li.w + c.g2 * qi.w, c.beta1 * pi.x - li.x + c.g2 * qi.x,
               c.beta1 * pi.y - li.y + c.g2 * qi.y, c.beta1 * pi.z - li.z + c.g2 * qi.z};
-    for_edges<QEdge<R>>(
+    for_edges2<QEdge<R>, PIPE>(
         g.out_ptr[i], g.out_ptr[i + 1],
         [&](int e, QEdge<R>& x) {
-            const int j = __ldcs(g.out_idx + e);
+            x.j = __ldcs(g.out_idx + e);
             x.te = IO<R>::ldcs(g.out_te, e);
             x.qk = IO<R>::ldcs(g.out_qk, e);
-            x.tj = IO<R>::ld(S.t, j);
-            x.pj = IO<R>::ld(pn, j);
+        },
+        [&](QEdge<R>& x) {
+            x.tj = IO<R>::ld(S.t, x.j);
+            x.pj = IO<R>::ld(pn, x.j);
         },
         [&](const QEdge<R>& x) {
             const R rx = x.tj.a - sr.a, ry = x.tj.b - sr.b, rz = x.tj.c - sr.c;
@@ -341,11 +392,12 @@ __device__ __forceinline__ void q_vertex(const GraphDev<R>& g, const StateDev<R>
 // c_e is recomputed from the gathered tail state rather than stored.
 template <typename R>
 struct TEdge {
+    int l;
     R4<R> te, sl, ql, pl;
 };
 
-// One vertex of the t-block; adds |dt_i|^2.
-template <typename R>
+// One vertex of the t-block; adds |dt_i|^2.  PIPE: see for_edges2.
+template <typename R, bool PIPE = false>
 __device__ __forceinline__ void t_vertex(const GraphDev<R>& g, const StateDev<R>& S, const Coef<R>& c, const R* pn,
                                          int64_t i, Acc<R>& adt) {
     const R4<R> tr = IO<R>::ld(S.t, i);  // (t_i, 1/A_3)
@@ -354,14 +406,16 @@ __device__ __forceinline__ void t_vertex(const GraphDev<R>& g, const StateDev<R>
     R ax = c.beta2 * sr.a + zr.a + c.g3 * tr.a;
     R ay = c.beta2 * sr.b + zr.b + c.g3 * tr.b;
     R az = c.beta2 * sr.c + zr.c + c.g3 * tr.c;
-    for_edges<TEdge<R>>(
+    for_edges2<TEdge<R>, PIPE>(
         g.in_ptr[i], g.in_ptr[i + 1],
         [&](int e, TEdge<R>& x) {
-            const int l = __ldcs(g.in_idx + e);
+            x.l = __ldcs(g.in_idx + e);
             x.te = IO<R>::ldcs(g.in_te, e);
-            x.sl = IO<R>::ld(S.s, l);
-            x.ql = IO<R>::ld(S.q, l);
-            x.pl = IO<R>::ld(pn, l);
+        },
+        [&](TEdge<R>& x) {
+            x.sl = IO<R>::ld(S.s, x.l);
+            x.ql = IO<R>::ld(S.q, x.l);
+            x.pl = IO<R>::ld(pn, x.l);
         },
         [&](const TEdge<R>& x) {
             R cx, cy, cz;
@@ -392,16 +446,18 @@ __device__ __forceinline__ void t_vertex(const GraphDev<R>& g, const StateDev<R>
 // is the step of s, not a difference of absolute positions.
 template <typename R>
 struct SEdge {
+    int j;
     R4<R> te, tj;
 };
 template <typename R>
 struct PEdge {
+    int l;
     R4<R> qk, ql;
 };
 
 // One vertex of the s-block + z update (WITH_S; adds |dz_i|^2) followed by
 // the p-block of the next iteration, which reads p from pc and writes pn.
-template <typename R, bool WITH_S>
+template <typename R, bool WITH_S, bool PIPE = false>
 __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R>& S, const Coef<R>& c, const R* pc,
                                           R* pn, int64_t i, Acc<R>& adz, Ctrl* ctrl) {
     const R4<R> sr = IO<R>::ld(S.s, i);  // (s_i, 1/A_2)
@@ -413,13 +469,13 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
     R ax = R(0), ay = R(0), az = R(0);
     R wx = R(0), wy = R(0), wz = R(0);
     Q<R> u = {R(0), R(0), R(0), R(0)};
-    for_edges<SEdge<R>>(
+    for_edges2<SEdge<R>, PIPE>(
         g.out_ptr[i], g.out_ptr[i + 1],
         [&](int e, SEdge<R>& x) {
-            const int j = __ldcs(g.out_idx + e);
+            x.j = __ldcs(g.out_idx + e);
             x.te = IO<R>::ldcs(g.out_te, e);
-            x.tj = IO<R>::ld(S.t, j);
         },
+        [&](SEdge<R>& x) { x.tj = IO<R>::ld(S.t, x.j); },
         [&](const SEdge<R>& x) {
             const R w2 = R(2) * x.te.d;
             if (WITH_S) {
@@ -455,13 +511,13 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
     Q<R> v = {c.beta1 * qr.a + lr.a + c.g1 * pr.a, c.beta1 * qr.b + lr.b + c.g1 * pr.b,
               c.beta1 * qr.c + lr.c + c.g1 * pr.c, c.beta1 * qr.d + lr.d + c.g1 * pr.d};
     axpy(v, R(1), u);
-    for_edges<PEdge<R>>(
+    for_edges2<PEdge<R>, PIPE>(
         g.in_ptr[i], g.in_ptr[i + 1],
         [&](int e, PEdge<R>& x) {
-            const int l = __ldcs(g.in_idx + e);
+            x.l = __ldcs(g.in_idx + e);
             x.qk = IO<R>::ldcs(g.in_qk, e);
-            x.ql = IO<R>::ld(S.q, l);
         },
+        [&](PEdge<R>& x) { x.ql = IO<R>::ld(S.q, x.l); },
         [&](const PEdge<R>& x) { axpy(v, R(2), qmul(asq<R>(x.ql), asq<R>(x.qk))); });
     p_normalise<R>(g, S, i, v, qr, lr, pr, sx, sy, sz, c, pn, ctrl);
 }
