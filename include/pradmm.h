@@ -219,11 +219,19 @@ pradmm_status pradmm_set_sigma(pradmm_t h, const double* Sigma1, const double* S
  *
  * pradmm_adjoint_record runs `iters` iterations from the current state x^0
  * (like pradmm_step) and keeps a checkpoint of the full state every
- * `ckpt_every` iterations (>= 1; device memory for ceil(iters/ckpt_every)+1
- * checkpoints plus ckpt_every-1 recompute slots, 28 n reals each).  The
- * tape stays valid until the state changes (set_state, init_odometry, step,
- * solve, another record). */
+ * `ckpt_every` iterations (device memory for ceil(iters/ckpt_every)+1
+ * checkpoints plus ckpt_every-1 recompute slots, 28 n reals each).
+ * ckpt_every = 0 chooses the spacing from the device memory: the smallest
+ * one whose tape fits in half of the free memory (1 where it fits: every
+ * iterate is kept and the reverse pass recomputes nothing); negative values
+ * return PRADMM_ERR_ARG.  The tape stays valid until the state changes
+ * (set_state, init_odometry, step, solve, another record). */
 pradmm_status pradmm_adjoint_record(pradmm_t h, int32_t iters, int32_t ckpt_every);
+
+/* The checkpoint spacing and the tape's device bytes of the current
+ * recording (PRADMM_ERR_STATE if there is none).  Either pointer may be
+ * NULL. */
+pradmm_status pradmm_adjoint_tape_info(pradmm_t h, int32_t* ckpt_every, double* tape_bytes);
 
 /* Runs the reverse sweeps over the recorded iterations for the cotangent
  * (p_bar = dL/dp^K, n x 4; t_bar = dL/dt^K, n x 3; NULL means zero) and

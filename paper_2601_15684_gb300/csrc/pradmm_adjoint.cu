@@ -404,6 +404,26 @@ __global__ void k_tape_arm(Ctrl* ctrl, long long iter) {
     ctrl->ticket = 0u;
 }
 
+__global__ void k_tape_rec_arm(TapeRec* rec, const Ctrl* ctrl, void* base, long long K, long long C,
+                               long long slot_bytes) {
+    rec->base = static_cast<char*>(base);
+    rec->k0 = ctrl->iter;
+    rec->K = K;
+    rec->C = C;
+    rec->slot_bytes = slot_bytes;
+}
+
+__global__ void __launch_bounds__(256) k_tape_copy(const TapeRec* __restrict__ rec, const Ctrl* __restrict__ ctrl,
+                                                   const float4* __restrict__ src) {
+    const long long d = ctrl->iter - rec->k0;
+    if (d <= 0 || d > rec->K || (d % rec->C != 0 && d != rec->K)) return;
+    const long long slot = (d + rec->C - 1) / rec->C;
+    float4* dst = reinterpret_cast<float4*>(rec->base + slot * rec->slot_bytes);
+    const long long nv = rec->slot_bytes / 16;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
 int grid_for(int64_t n, int block) {
     const int64_t gmax = 152 * 16;
     int64_t gb = (n + block - 1) / block;
@@ -443,6 +463,17 @@ cudaError_t launch_adj_scatter(const double* g_qe, const double* g_te, const dou
                                cudaStream_t st) {
     if (m <= 0) return cudaSuccess;
     k_adj_scatter<<<grid_for(m, 256), 256, 0, st>>>(g_qe, g_te, g_ka, eidx, m, qe_bar, te_bar, ka_bar, om_bar);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tape_rec_arm(TapeRec* rec, const Ctrl* ctrl, void* base, long long K, long long C,
+                                long long slot_bytes, cudaStream_t st) {
+    k_tape_rec_arm<<<1, 1, 0, st>>>(rec, ctrl, base, K, C, slot_bytes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tape_copy(const TapeRec* rec, const Ctrl* ctrl, const void* src, int grid, cudaStream_t st) {
+    k_tape_copy<<<grid, 256, 0, st>>>(rec, ctrl, static_cast<const float4*>(src));
     return cudaGetLastError();
 }
 

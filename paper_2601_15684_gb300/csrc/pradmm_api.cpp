@@ -84,6 +84,12 @@ struct pradmm_s {
     cudaGraphExec_t graph_exec = nullptr;
     cudaGraphConditionalHandle cond = 0;
     bool graph_ready = false;
+    // the same loop with a checkpoint copy after every iteration (reverse-mode recording)
+    cudaGraph_t rec_graph = nullptr;
+    cudaGraphExec_t rec_exec = nullptr;
+    cudaGraphConditionalHandle rec_cond = 0;
+    bool rec_ready = false;
+    pradmm::TapeRec* tape_rec = nullptr;
 
     bool general = false;              // general Sigma_1, Sigma_2 (pradmm_set_sigma)
     double S1[16] = {}, S2[16] = {}, U[9] = {}, mu[3] = {};
@@ -457,6 +463,21 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
 
 void l2_window_off(pradmm_s* h);
 
+// Drops both captured loops (they hold the sweep form and the handle's
+// buffers by value).
+void drop_graphs(pradmm_s* h) {
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    if (h->rec_exec) cudaGraphExecDestroy(h->rec_exec);
+    if (h->rec_graph) cudaGraphDestroy(h->rec_graph);
+    h->graph_exec = nullptr;
+    h->graph = nullptr;
+    h->graph_ready = false;
+    h->rec_exec = nullptr;
+    h->rec_graph = nullptr;
+    h->rec_ready = false;
+}
+
 void free_all(pradmm_s* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->adj_exec) cudaGraphExecDestroy(h->adj_exec);
@@ -464,8 +485,7 @@ void free_all(pradmm_s* h) {
     l2_window_off(h);
     if (h->tape) cudaFree(h->tape);
     h->tape = nullptr;
-    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
-    if (h->graph) cudaGraphDestroy(h->graph);
+    drop_graphs(h);
     for (void* v : h->allocs) cudaFree(v);
     h->allocs.clear();
     if (h->ctrl_h) cudaFreeHost(h->ctrl_h);
@@ -667,39 +687,48 @@ pradmm_status launch_iters_plain(pradmm_s* h, long long iters) {
     return PRADMM_OK;
 }
 
+// One iteration per pass of a device-side while loop (the last CTA of the
+// s/z + p sweep sets the condition).  record: the reverse-mode recording
+// loop, whose body ends with the checkpoint copy (scalar Sigma only).
 template <typename R>
-pradmm_status ensure_graph(pradmm_s* h) {
-    if (h->graph_ready) return PRADMM_OK;
-    CU(cudaGraphCreate(&h->graph, 0));
-    CU(cudaGraphConditionalHandleCreate(&h->cond, h->graph, 1u, cudaGraphCondAssignDefault));
+pradmm_status ensure_graph(pradmm_s* h, bool record = false) {
+    if (record ? h->rec_ready : h->graph_ready) return PRADMM_OK;
+    cudaGraph_t& graph = record ? h->rec_graph : h->graph;
+    cudaGraphExec_t& exec = record ? h->rec_exec : h->graph_exec;
+    cudaGraphConditionalHandle& cond = record ? h->rec_cond : h->cond;
+    CU(cudaGraphCreate(&graph, 0));
+    CU(cudaGraphConditionalHandleCreate(&cond, graph, 1u, cudaGraphCondAssignDefault));
     cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
-    cp.conditional.handle = h->cond;
+    cp.conditional.handle = cond;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
     cudaGraphNode_t node;
-    CU(cudaGraphAddNode(&node, h->graph, nullptr, nullptr, 0, &cp));
+    CU(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     CU(cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     const auto g = h->gdev<R>();
     const auto S = h->sdev<R>();
     const auto c = h->coef<R>();
-    const auto L = h->launch(true);
-    cudaError_t e1 = cudaSuccess, e2 = cudaSuccess, e3 = cudaSuccess;
+    auto L = h->launch(true);
+    L.cond = cond;
+    cudaError_t e1 = cudaSuccess, e2 = cudaSuccess, e3 = cudaSuccess, e5 = cudaSuccess;
     if (h->general) {
         e1 = pradmm::launch_sigma_iteration<R>(g, S, c, h->sigma<R>(), L);
     } else {
         e1 = pradmm::launch_q<R>(g, S, c, L);
         e2 = pradmm::launch_t<R>(g, S, c, L);
         e3 = pradmm::launch_sp<R>(g, S, c, L);
+        if (record) e5 = pradmm::launch_tape_copy(h->tape_rec, h->ctrl, h->state_block, h->grids[3], h->stream);
     }
     cudaGraph_t captured = nullptr;
     cudaError_t e4 = cudaStreamEndCapture(h->stream, &captured);
     CU(e1);
     CU(e2);
     CU(e3);
+    CU(e5);
     CU(e4);
-    CU(cudaGraphInstantiate(&h->graph_exec, h->graph, 0));
-    h->graph_ready = true;
+    CU(cudaGraphInstantiate(&exec, graph, 0));
+    (record ? h->rec_ready : h->graph_ready) = true;
     return PRADMM_OK;
 }
 
@@ -913,20 +942,21 @@ pradmm_status profile_impl(pradmm_s* h, int32_t iters, double* ms_out) {
 }
 
 // ---- reverse mode ------------------------------------------------------------
-// Tape slot: p[0], p[1], q, lam, t, s, z, each 4 n reals, contiguous.  A slot
-// at iteration k holds p^k in p[k & 1] and p^{k+1} in p[(k+1) & 1], exactly
-// as the handle's own state does, so the forward sweep kernels run on a slot
+// Tape slot: t, s, q, p[0], p[1], lam, z, each 4 n reals, contiguous: the
+// layout of the handle's state block, so a checkpoint is one copy.  A slot at
+// iteration k holds p^k in p[k & 1] and p^{k+1} in p[(k+1) & 1], exactly as
+// the handle's own state does, so the forward sweep kernels run on a slot
 // unchanged.
 template <typename R>
 pradmm::StateDev<R> slot_state(void* base, int64_t n) {
     R* b = static_cast<R*>(base);
     pradmm::StateDev<R> S;
-    S.p[0] = b;
-    S.p[1] = b + 4 * n;
+    S.t = b;
+    S.s = b + 4 * n;
     S.q = b + 8 * n;
-    S.lam = b + 12 * n;
-    S.t = b + 16 * n;
-    S.s = b + 20 * n;
+    S.p[0] = b + 12 * n;
+    S.p[1] = b + 16 * n;
+    S.lam = b + 20 * n;
     S.z = b + 24 * n;
     return S;
 }
@@ -940,11 +970,33 @@ size_t slot_bytes(const pradmm_s* h) { return 28 * (size_t)h->n * h->rsize; }
 void* tape_slot(pradmm_s* h, int64_t idx) { return static_cast<char*>(h->tape) + (size_t)idx * slot_bytes(h); }
 
 pradmm_status snapshot(pradmm_s* h, void* dst) {
-    const size_t b = 4 * (size_t)h->n * h->rsize;
-    char* d = static_cast<char*>(dst);
-    const void* src[7] = {h->p[0], h->p[1], h->q, h->lam, h->t, h->s, h->z};
-    for (int k = 0; k < 7; ++k) CU(cudaMemcpyAsync(d + k * b, src[k], b, cudaMemcpyDeviceToDevice, h->stream));
+    CU(cudaMemcpyAsync(dst, h->state_block, slot_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
     return PRADMM_OK;
+}
+
+// Slots of a tape for K iterations with a checkpoint every C: ceil(K/C) + 1
+// checkpoints and C - 1 recompute slots.
+size_t tape_slots(int K, int C) { return K == 0 ? 1 : (size_t)((K + C - 1) / C + 1) + (size_t)(C - 1); }
+
+// Checkpoint spacing chosen from the device memory: the smallest C (least
+// recomputation; C = 1 stores every iterate and recomputes nothing) whose tape
+// fits in half of the free memory plus the tape already held; if none fits,
+// the C with the smallest tape.
+int auto_ckpt(const pradmm_s* h, int K) {
+    if (K <= 1) return 1;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        free_b = 0;
+    }
+    const size_t budget = free_b / 2 + h->tape_bytes;
+    const size_t sb = slot_bytes(h);
+    int best = 1;
+    for (int C = 1; C <= K; ++C) {
+        if (tape_slots(K, C) * sb <= budget) return C;
+        if (tape_slots(K, C) < tape_slots(K, best)) best = C;
+    }
+    return best;
 }
 
 template <typename R>
@@ -952,11 +1004,11 @@ pradmm_status adjoint_record(pradmm_s* h, int32_t iters, int32_t ckpt_every) {
     if (!h->state_set) return fail(PRADMM_ERR_STATE, "state is not set (pradmm_set_state or pradmm_init_odometry)");
     if (h->general) return fail(PRADMM_ERR_STATE, "the reverse mode supports scalar Sigma only");
     if (iters < 0) return fail(PRADMM_ERR_ARG, "iters must be >= 0");
-    if (ckpt_every < 1) return fail(PRADMM_ERR_ARG, "ckpt_every must be >= 1");
+    if (ckpt_every < 0) return fail(PRADMM_ERR_ARG, "ckpt_every must be >= 0 (0: chosen from free device memory)");
     h->tape_valid = false;
-    const int C = iters == 0 ? 1 : std::min(ckpt_every, iters);
+    const int C = iters == 0 ? 1 : (ckpt_every == 0 ? auto_ckpt(h, iters) : std::min(ckpt_every, iters));
     const int nck = iters == 0 ? 1 : (iters + C - 1) / C + 1;
-    const size_t need = (size_t)(nck + C - 1) * slot_bytes(h);
+    const size_t need = tape_slots(iters, C) * slot_bytes(h);
     if (need > h->tape_bytes) {
         if (h->tape) CU(cudaFree(h->tape));
         h->tape = nullptr;
@@ -975,13 +1027,34 @@ pradmm_status adjoint_record(pradmm_s* h, int32_t iters, int32_t ckpt_every) {
     }
     ST(read_ctrl(h));
     const long long k0 = h->ctrl_h->iter;
+    h->epoch++;
     ST(snapshot(h, tape_slot(h, 0)));
-    for (int c = 0; c + 1 < nck; ++c) {
-        const int L = std::min(C, iters - c * C);
-        ST(run<R>(h, L, false));
-        ST(snapshot(h, tape_slot(h, c + 1)));
+    if (iters > 0) {
+        // one pass over all iterations; the copy after each iteration writes
+        // the checkpoints (device-side test of the iteration count)
+        if (!h->tape_rec) ST(dalloc(h, &h->tape_rec, 1));
+        CU(pradmm::launch_arm(h->ctrl, iters, 0, h->prm.tol, h->stream));
+        CU(pradmm::launch_tape_rec_arm(h->tape_rec, h->ctrl, h->tape, iters, C, (long long)slot_bytes(h), h->stream));
+        if (h->prm.use_graph) {
+            ST(ensure_graph<R>(h, true));
+            CU(cudaGraphLaunch(h->rec_exec, h->stream));
+        } else {
+            const auto g = h->gdev<R>();
+            const auto S = h->sdev<R>();
+            const auto c = h->coef<R>();
+            const auto L = h->launch(false);
+            for (int k = 0; k < iters; ++k) {
+                CU(pradmm::launch_q<R>(g, S, c, L));
+                CU(pradmm::launch_t<R>(g, S, c, L));
+                CU(pradmm::launch_sp<R>(g, S, c, L));
+                CU(pradmm::launch_tape_copy(h->tape_rec, h->ctrl, h->state_block, h->grids[3], h->stream));
+            }
+        }
     }
-    CU(cudaStreamSynchronize(h->stream));
+    ST(read_ctrl(h));
+    if (h->ctrl_h->timeout) return fail(PRADMM_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (h->ctrl_h->nonfinite || h->ctrl_h->iter != k0 + iters)
+        return fail(PRADMM_ERR_NONFINITE, "the recorded iterations produced a non-finite residual");
     h->tape_k0 = k0;
     h->tape_K = iters;
     h->tape_C = C;
@@ -1267,12 +1340,8 @@ pradmm_status set_sigma_impl(pradmm_s* h, const double* S1, const double* S2) {
         CU(cudaMemcpy(h->sigma_d + 16, h->S2, sizeof(double) * 16, cudaMemcpyHostToDevice));
         h->general = true;
     }
-    // the captured loop and any precomputed p^{k+1} belong to the other form
-    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
-    if (h->graph) cudaGraphDestroy(h->graph);
-    h->graph_exec = nullptr;
-    h->graph = nullptr;
-    h->graph_ready = false;
+    // the captured loops and any precomputed p^{k+1} belong to the other form
+    drop_graphs(h);
     h->pending = false;
     h->epoch++;
     return PRADMM_OK;
@@ -1405,6 +1474,15 @@ pradmm_status pradmm_solve(pradmm_t h, int32_t* iters_done, double* e_final) {
 pradmm_status pradmm_adjoint_record(pradmm_t h, int32_t iters, int32_t ckpt_every) {
     if (!h) return fail(PRADMM_ERR_ARG, "handle is NULL");
     return h->fp64 ? adjoint_record<double>(h, iters, ckpt_every) : adjoint_record<float>(h, iters, ckpt_every);
+}
+
+pradmm_status pradmm_adjoint_tape_info(pradmm_t h, int32_t* ckpt_every, double* tape_bytes) {
+    if (!h) return fail(PRADMM_ERR_ARG, "handle is NULL");
+    if (!h->tape_valid || h->tape_epoch != h->epoch)
+        return fail(PRADMM_ERR_STATE, "no recorded iterations: call pradmm_adjoint_record after the last state change");
+    if (ckpt_every) *ckpt_every = h->tape_C;
+    if (tape_bytes) *tape_bytes = (double)h->tape_bytes;
+    return PRADMM_OK;
 }
 
 pradmm_status pradmm_adjoint(pradmm_t h, const double* p_bar, const double* t_bar, double* q_meas_bar,

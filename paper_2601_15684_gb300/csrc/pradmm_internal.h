@@ -99,6 +99,22 @@ cudaError_t launch_sp(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>&
 // bps[0] first p sweep, bps[1] q sweep, bps[2] t sweep, bps[3] s/z + p sweep.
 cudaError_t sweep_occupancy(int is_double, int block, int* bps);
 
+// Device-side parameters of a tape recording (reverse mode): after the
+// iteration that brings ctrl->iter to k0 + d, with d a multiple of C or
+// d = K, the whole state block (slot_bytes, a multiple of 16) is copied to
+// tape slot ceil(d / C) at base + slot * slot_bytes.
+struct TapeRec {
+    char* base;
+    long long k0, K, C, slot_bytes;
+};
+
+// Fills *rec with k0 = ctrl->iter (read on the device) and the arguments.
+cudaError_t launch_tape_rec_arm(TapeRec* rec, const Ctrl* ctrl, void* base, long long K, long long C,
+                                long long slot_bytes, cudaStream_t st);
+// The checkpoint copy that follows each recorded iteration (a no-op between
+// checkpoints); grid-stride 16-byte copies from the state block `src`.
+cudaError_t launch_tape_copy(const TapeRec* rec, const Ctrl* ctrl, const void* src, int grid, cudaStream_t st);
+
 // Sets target = iter + iters, halt = (iters <= 0), stop = 0, use_tol, tol.
 cudaError_t launch_arm(Ctrl* ctrl, long long iters, int use_tol, double tol, cudaStream_t st);
 

@@ -78,6 +78,7 @@ _SIGS = {
     "pradmm_l2_window_info": (ctypes.c_int, [_h, _d]),
     "pradmm_set_sigma": (ctypes.c_int, [_h, _d, _d]),
     "pradmm_adjoint_record": (ctypes.c_int, [_h, ctypes.c_int32, ctypes.c_int32]),
+    "pradmm_adjoint_tape_info": (ctypes.c_int, [_h, ctypes.POINTER(ctypes.c_int32), _d]),
     "pradmm_adjoint": (ctypes.c_int, [_h, _d, _d, _d, _d, _d, _d, _d]),
     "pradmm_adjoint_device": (ctypes.c_int, [_h] + [ctypes.c_void_p] * 7),
     "pradmm_objective_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 10),
@@ -267,8 +268,16 @@ def pradmm_set_sigma(h, Sigma1=None, Sigma2=None):
     _check(load().pradmm_set_sigma(h, _dp(S1), _dp(S2)), "pradmm_set_sigma")
 
 
-def pradmm_adjoint_record(h, iters: int, ckpt_every: int = 20):
+def pradmm_adjoint_record(h, iters: int, ckpt_every: int = 0):
     _check(load().pradmm_adjoint_record(h, int(iters), int(ckpt_every)), "pradmm_adjoint_record")
+
+
+def pradmm_adjoint_tape_info(h):
+    """(checkpoint spacing, tape bytes) of the current recording."""
+    c = ctypes.c_int32(0)
+    b = np.zeros(1)
+    _check(load().pradmm_adjoint_tape_info(h, ctypes.byref(c), _dp(b)), "pradmm_adjoint_tape_info")
+    return int(c.value), float(b[0])
 
 
 _X0 = (("p", 4), ("q", 4), ("t", 3), ("s", 3), ("lam", 4), ("z", 3))
@@ -384,8 +393,11 @@ class Solver:
     def set_sigma(self, Sigma1=None, Sigma2=None):
         pradmm_set_sigma(self.h, Sigma1, Sigma2)
 
-    def adjoint_record(self, iters, ckpt_every=20):
+    def adjoint_record(self, iters, ckpt_every=0):
         pradmm_adjoint_record(self.h, iters, ckpt_every)
+
+    def adjoint_tape_info(self):
+        return pradmm_adjoint_tape_info(self.h)
 
     def adjoint(self, p_bar=None, t_bar=None, x0=False):
         return pradmm_adjoint(self.h, self.n, self.m, p_bar, t_bar, x0)
@@ -520,13 +532,14 @@ class _Handle:
             pass
 
 
-def unrolled_poses(n, src, dst, q_meas, t_meas, kappa=None, omega=None, iters=200, ckpt_every=20, params=None,
+def unrolled_poses(n, src, dst, q_meas, t_meas, kappa=None, omega=None, iters=200, ckpt_every=0, params=None,
                    init=None):
     """(p^K, t^K) after `iters` iterations of Algorithm 1, differentiable with
     respect to q_meas (m x 4), t_meas (m x 3), kappa (m), omega (m): CUDA
     float64 tensors; src, dst CUDA int32 tensors.  The start is the odometry
     initialisation (init=None) or init=(q0, t0) host arrays, held fixed.
-    Forward and backward run in libpradmm's kernels on torch's current stream
+    ckpt_every: checkpoint spacing of the tape (0: chosen from the free device
+    memory, every iterate kept where it fits).  Forward and backward run in libpradmm's kernels on torch's current stream
     (pradmm_adjoint_record / pradmm_adjoint_device)."""
     import torch
 

@@ -24,7 +24,7 @@ def main(argv=None) -> int:
     ap.add_argument("--graph", type=int, default=0)
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--adjoint", type=int, default=0)
-    ap.add_argument("--ckpt", type=int, default=20)
+    ap.add_argument("--ckpt", type=int, default=20, help="checkpoint spacing (0: chosen from free memory)")
     a = ap.parse_args(argv)
     from paper_2601_15684_gb300 import build_lib, pradmm, synth
 

@@ -76,7 +76,7 @@ def test_checkpoint_spacing_is_bitwise_irrelevant(P):
     g = synth.random_graph(200, 600, seed=5)
     st = synth.random_state(np.random.default_rng(2), g.n)
     pb, tb = _cotangent(g.n, 3)
-    outs = [_gpu_adjoint(P, g, st, 23, pb, tb, 1, ckpt=c) for c in (1, 4, 7, 23, 100)]
+    outs = [_gpu_adjoint(P, g, st, 23, pb, tb, 1, ckpt=c) for c in (1, 4, 7, 23, 100, 0)]
     for o in outs[1:]:
         for key in GRADS:
             np.testing.assert_array_equal(o[key], outs[0][key])
@@ -138,8 +138,11 @@ def test_tape_is_invalidated_by_state_changes(P):
         with pytest.raises(P.PRADMMError):
             S.adjoint(pb, tb)
         with pytest.raises(P.PRADMMError) as ei:
-            S.adjoint_record(5, 0)
+            S.adjoint_record(5, -1)
         assert ei.value.status == P.PRADMM_ERR_ARG
+        with pytest.raises(P.PRADMMError) as ei:
+            S.adjoint_tape_info()
+        assert ei.value.status == P.PRADMM_ERR_STATE
 
 
 def test_adjoint_after_steps_uses_current_state(P):
@@ -230,3 +233,26 @@ def test_reverse_graph_is_reused_and_matches_plain_launches(P):
     for key in GRADS:
         np.testing.assert_array_equal(outs[1][0][key], outs[1][2][key])
         assert not np.array_equal(outs[1][0][key], outs[1][1][key])
+
+
+def test_automatic_checkpoint_spacing(P):
+    # ckpt_every = 0: a small graph's whole tape fits, so every iterate is kept
+    # (spacing 1, K + 1 slots of 28 n reals) and the gradients equal those of
+    # an explicit spacing bitwise; an explicit spacing is reported as given
+    g = synth.random_graph(150, 450, seed=17)
+    st = synth.random_state(np.random.default_rng(17), g.n)
+    pb, tb = _cotangent(g.n, 4)
+    K = 12
+    res = {}
+    for c in (0, 5):
+        with P.Solver(g, precision=1) as S:
+            S.set_state_full(st)
+            S.adjoint_record(K, c)
+            C, nbytes = S.adjoint_tape_info()
+            res[c] = S.adjoint(pb, tb, x0=True)
+        if c == 0:
+            assert C == 1 and nbytes >= (K + 1) * 28 * g.n * 4
+        else:
+            assert C == 5
+    for key in GRADS:
+        np.testing.assert_array_equal(res[0][key], res[5][key])
