@@ -138,11 +138,17 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_adj_t(GraphDev<R> g, AdjDev<R> A, AdjStep<R> X, Coef<R> c) {
     VERTEX_LOOP(g.n) {
         V3<R> TB = v3(IO<R>::ld(A.tb, i));
-        for (int e = g.in_ptr[i]; e < g.in_ptr[i + 1]; ++e) {
-            const int l = g.in_idx[e];
-            const R4<R> te = IO<R>::ld(g.in_te, e);
-            vaxpy(TB, R(2) * te.d, v3(IO<R>::ld(A.gs, l)));
-        }
+        struct E {
+            R w;
+            R4<R> gsl;
+        };
+        for_edges<E>(
+            g.in_ptr[i], g.in_ptr[i + 1],
+            [&](int e, E& x) {
+                x.w = IO<R>::ld(g.in_te, e).d;
+                x.gsl = IO<R>::ld(A.gs, g.in_idx[e]);
+            },
+            [&](const E& x) { vaxpy(TB, R(2) * x.w, v3(x.gsl)); });
         const R inv3 = IO<R>::ld(X.t, i).d;
         const V3<R> gt = {TB.x * inv3, TB.y * inv3, TB.z * inv3};
         const R a3b = -vdot(gt, v3(IO<R>::ld(X.tn, i)));
@@ -169,18 +175,25 @@ __global__ void __launch_bounds__(256) k_adj_q(GraphDev<R> g, AdjDev<R> A, AdjSt
         const V3<R> gs = v3(IO<R>::ld(A.gs, i));
         const Q<R> P = ldq(X.pn, i), Qn = ldq(X.qn, i);
         V3<R> os = v3(IO<R>::ld(A.os, i));
-        for (int e = g.out_ptr[i]; e < g.out_ptr[i + 1]; ++e) {
-            const int j = g.out_idx[e];
-            const R4<R> te = IO<R>::ld(g.out_te, e);
-            const V3<R> tv = {te.a, te.b, te.c};
-            const V3<R> gt = v3(IO<R>::ld(A.gt, j));
-            const R w2 = R(2) * te.d;
-            const V3<R> cb = {w2 * (gt.x - gs.x), w2 * (gt.y - gs.y), w2 * (gt.z - gs.z)};
-            // h p t~^* = -(h p) t~ and h^* q t~ = -(h q) t~ for pure h, t~
-            axpy(QB, R(-1), pr(pl(cb, P), tv));
-            axpy(PB, R(-1), pr(pl(cb, Qn), tv));
-            vaxpy(os, w2, gt);
-        }
+        struct E {
+            R4<R> te, gt;
+        };
+        for_edges<E>(
+            g.out_ptr[i], g.out_ptr[i + 1],
+            [&](int e, E& x) {
+                x.te = IO<R>::ld(g.out_te, e);
+                x.gt = IO<R>::ld(A.gt, g.out_idx[e]);
+            },
+            [&](const E& x) {
+                const V3<R> tv = {x.te.a, x.te.b, x.te.c};
+                const V3<R> gt = v3(x.gt);
+                const R w2 = R(2) * x.te.d;
+                const V3<R> cb = {w2 * (gt.x - gs.x), w2 * (gt.y - gs.y), w2 * (gt.z - gs.z)};
+                // h p t~^* = -(h p) t~ and h^* q t~ = -(h q) t~ for pure h, t~
+                axpy(QB, R(-1), pr(pl(cb, P), tv));
+                axpy(PB, R(-1), pr(pl(cb, Qn), tv));
+                vaxpy(os, w2, gt);
+            });
         const R inv2 = IO<R>::ld(X.s, i).d;
         const Q<R> gq = {QB.w * inv2, QB.x * inv2, QB.y * inv2, QB.z * inv2};
         const R a2b = -qdot(gq, Qn);
@@ -214,35 +227,52 @@ __global__ void __launch_bounds__(256) k_adj_p(GraphDev<R> g, AdjDev<R> A, AdjSt
         V3<R> os = v3(IO<R>::ld(A.os, i)), ot = v3(IO<R>::ld(A.ot, i));
         Q<R> u = {c.beta1 * qi.w + li.w + c.g1 * pk.w, c.beta1 * qi.x + li.x + c.g1 * pk.x,
                   c.beta1 * qi.y + li.y + c.g1 * pk.y, c.beta1 * qi.z + li.z + c.g1 * pk.z};
-        for (int e = g.out_ptr[i]; e < g.out_ptr[i + 1]; ++e) {
-            const int j = g.out_idx[e];
-            const R4<R> te = IO<R>::ld(g.out_te, e);
-            const V3<R> tv = {te.a, te.b, te.c};
-            const V3<R> tj = v3(IO<R>::ld(X.t, j));
-            const V3<R> r = {tj.x - si.x, tj.y - si.y, tj.z - si.z};
-            const R w2 = R(2) * te.d;
-            // r~^* = -r~ (pure)
-            axpy(u, -w2, pr(pl(r, qi), tv));
-            axpy(PB, -w2, pr(pl(r, gq), tv));
-            R cx, cy, cz;
-            im_rot(gq, te.a, te.b, te.c, P, cx, cy, cz);
-            os.x -= w2 * cx;
-            os.y -= w2 * cy;
-            os.z -= w2 * cz;
-        }
-        for (int e = g.in_ptr[i]; e < g.in_ptr[i + 1]; ++e) {
-            const int l = g.in_idx[e];
-            const Q<R> qk = ldq(g.in_qk, e);
-            const R4<R> te = IO<R>::ld(g.in_te, e);
-            axpy(u, R(2), qmul(ldq(X.q, l), qk));
-            axpy(PB, R(2), qmul(ldq(A.gq, l), qk));
-            R cx, cy, cz;
-            im_rot(ldq(A.gq, l), te.a, te.b, te.c, ldq(X.pn, l), cx, cy, cz);
-            const R w2 = R(2) * te.d;
-            ot.x += w2 * cx;
-            ot.y += w2 * cy;
-            ot.z += w2 * cz;
-        }
+        struct EO {
+            R4<R> te, tj;
+        };
+        for_edges<EO>(
+            g.out_ptr[i], g.out_ptr[i + 1],
+            [&](int e, EO& x) {
+                x.te = IO<R>::ld(g.out_te, e);
+                x.tj = IO<R>::ld(X.t, g.out_idx[e]);
+            },
+            [&](const EO& x) {
+                const V3<R> tv = {x.te.a, x.te.b, x.te.c};
+                const V3<R> r = {x.tj.a - si.x, x.tj.b - si.y, x.tj.c - si.z};
+                const R w2 = R(2) * x.te.d;
+                // r~^* = -r~ (pure)
+                axpy(u, -w2, pr(pl(r, qi), tv));
+                axpy(PB, -w2, pr(pl(r, gq), tv));
+                R cx, cy, cz;
+                im_rot(gq, x.te.a, x.te.b, x.te.c, P, cx, cy, cz);
+                os.x -= w2 * cx;
+                os.y -= w2 * cy;
+                os.z -= w2 * cz;
+            });
+        struct EI {
+            R4<R> qk, te, ql, gql, pl;
+        };
+        for_edges<EI>(
+            g.in_ptr[i], g.in_ptr[i + 1],
+            [&](int e, EI& x) {
+                const int l = g.in_idx[e];
+                x.qk = IO<R>::ld(g.in_qk, e);
+                x.te = IO<R>::ld(g.in_te, e);
+                x.ql = IO<R>::ld(X.q, l);
+                x.gql = IO<R>::ld(A.gq, l);
+                x.pl = IO<R>::ld(X.pn, l);
+            },
+            [&](const EI& x) {
+                const Q<R> qk = asq<R>(x.qk), gql = asq<R>(x.gql);
+                axpy(u, R(2), qmul(asq<R>(x.ql), qk));
+                axpy(PB, R(2), qmul(gql, qk));
+                R cx, cy, cz;
+                im_rot(gql, x.te.a, x.te.b, x.te.c, asq<R>(x.pl), cx, cy, cz);
+                const R w2 = R(2) * x.te.d;
+                ot.x += w2 * cx;
+                ot.y += w2 * cy;
+                ot.z += w2 * cz;
+            });
         const R nu = sqrt(qdot(u, u));
         Q<R> op = ldq(A.op, i), oq = ldq(A.oq, i), ol = ldq(A.ol, i);
         Q<R> ub = {R(0), R(0), R(0), R(0)};
@@ -338,23 +368,43 @@ __global__ void __launch_bounds__(256) k_adj_v(GraphDev<R> g, AdjDev<R> A, AdjSt
         const V3<R> si = v3(IO<R>::ld(X.s, i));
         Q<R> oq = ldq(A.oq, i);
         V3<R> os = v3(IO<R>::ld(A.os, i)), ot = v3(IO<R>::ld(A.ot, i));
-        for (int e = g.out_ptr[i]; e < g.out_ptr[i + 1]; ++e) {
-            const int j = g.out_idx[e];
-            const R4<R> te = IO<R>::ld(g.out_te, e);
-            const V3<R> tv = {te.a, te.b, te.c};
-            const R w2 = R(2) * te.d;
-            const V3<R> tj = v3(IO<R>::ld(X.t, j));
-            const V3<R> r = {tj.x - si.x, tj.y - si.y, tj.z - si.z};
-            axpy(oq, R(2) * A.ek[e], qmul_c(ldq(A.ub, j), ldq(A.eq, e)));
-            axpy(oq, -w2, pr(pl(r, ub), tv));  // r~ ub t~^* = -r~ ub t~
-            vaxpy(os, w2, im(qmul_c(ub, pr(qi, tv))));
-        }
-        for (int e = g.in_ptr[i]; e < g.in_ptr[i + 1]; ++e) {
-            const int l = g.in_idx[e];
-            const R4<R> te = IO<R>::ld(g.in_te, e);
-            const V3<R> tv = {te.a, te.b, te.c};
-            vaxpy(ot, R(-2) * te.d, im(qmul_c(ldq(A.ub, l), pr(ldq(X.q, l), tv))));
-        }
+        struct EO {
+            R ek;
+            R4<R> te, tj, ubj, eq;
+        };
+        for_edges<EO>(
+            g.out_ptr[i], g.out_ptr[i + 1],
+            [&](int e, EO& x) {
+                const int j = g.out_idx[e];
+                x.te = IO<R>::ld(g.out_te, e);
+                x.eq = IO<R>::ld(A.eq, e);
+                x.ek = A.ek[e];
+                x.tj = IO<R>::ld(X.t, j);
+                x.ubj = IO<R>::ld(A.ub, j);
+            },
+            [&](const EO& x) {
+                const V3<R> tv = {x.te.a, x.te.b, x.te.c};
+                const R w2 = R(2) * x.te.d;
+                const V3<R> r = {x.tj.a - si.x, x.tj.b - si.y, x.tj.c - si.z};
+                axpy(oq, R(2) * x.ek, qmul_c(asq<R>(x.ubj), asq<R>(x.eq)));
+                axpy(oq, -w2, pr(pl(r, ub), tv));  // r~ ub t~^* = -r~ ub t~
+                vaxpy(os, w2, im(qmul_c(ub, pr(qi, tv))));
+            });
+        struct EI {
+            R4<R> te, ubl, ql;
+        };
+        for_edges<EI>(
+            g.in_ptr[i], g.in_ptr[i + 1],
+            [&](int e, EI& x) {
+                const int l = g.in_idx[e];
+                x.te = IO<R>::ld(g.in_te, e);
+                x.ubl = IO<R>::ld(A.ub, l);
+                x.ql = IO<R>::ld(X.q, l);
+            },
+            [&](const EI& x) {
+                const V3<R> tv = {x.te.a, x.te.b, x.te.c};
+                vaxpy(ot, R(-2) * x.te.d, im(qmul_c(asq<R>(x.ubl), pr(asq<R>(x.ql), tv))));
+            });
         if (more) {
             // xbar^k is the xbar^{k+1} of iteration k-1, whose s^{k+1} is s^k here
             step_a<R>(A, c, i, ldq(A.op, i), oq, ot, os, ldq(A.ol, i), v3(IO<R>::ld(A.oz, i)), si,
