@@ -93,7 +93,11 @@ struct pradmm_s {
 
     bool general = false;              // general Sigma_1, Sigma_2 (pradmm_set_sigma)
     double S1[16] = {}, S2[16] = {}, U[9] = {}, mu[3] = {};
+    // sandwich maps (10 x 10) of the general-Sigma block matrices, see quad_map
+    double LM1D[100] = {}, LW2D[100] = {}, LW1[100] = {};
     double* sigma_d = nullptr;         // 32 doubles: S1, S2 (objective)
+    pradmm::FbRec* fb_q = nullptr;     // FP32 handles: queued FP64 p re-solves (n records)
+    unsigned int* fb_n = nullptr;      // their per-iteration counters (2)
     void* state_block = nullptr;       // t, s, q, p[0], p[1], lam, z: 28 n reals, contiguous
     bool l2_on = false;                // this handle holds an L2 set-aside
     cudaAccessPolicyWindow window{};   // persisting window over t, s, q, p[0], p[1]
@@ -153,6 +157,13 @@ struct pradmm_s {
         }
         for (int k = 0; k < 9; ++k) sg.U[k] = R(U[k]);
         for (int k = 0; k < 3; ++k) sg.mu[k] = R(mu[k]);
+        for (int k = 0; k < 100; ++k) {
+            sg.LM1D[k] = R(LM1D[k]);
+            sg.LW2D[k] = R(LW2D[k]);
+            sg.LW1[k] = R(LW1[k]);
+        }
+        sg.fb_q = fb_q;
+        sg.fb_n = fb_n;
         return sg;
     }
     template <typename R>
@@ -1259,6 +1270,41 @@ pradmm_status adjoint_impl(pradmm_s* h, const double* p_bar, const double* t_bar
 
 // ---- general Sigma ------------------------------------------------------------
 // Symmetric positive definite check by Cholesky.
+// X(a)^T S X(a) for the quaternion multiplication matrix X = M (M(a) b = a b)
+// or X = W (W(a) b = b a) is a quadratic form in a: entry (r, c), r <= c, is
+// sum_{m <= n} L[10 o + p] (a a^T)_{mn} over the 10 entries o = (r, c) and
+// p = (m, n) of the upper triangles.  With d, entry (r, c) is multiplied by
+// D_r D_c, D = diag(1, -1, -1, -1) (the conjugation D X^T S X D).  Summed
+// over edges with weights, the 4x4 block matrix is L applied to
+// sum_e w_e a_e a_e^T.
+void quad_map(const double S[16], bool m_type, bool d, double L[100]) {
+    double E[4][4][4];  // E[k][r][m]: coefficient of a_m in X(a)[k][r]
+    for (int m = 0; m < 4; ++m) {
+        const double a[4] = {m == 0 ? 1.0 : 0.0, m == 1 ? 1.0 : 0.0, m == 2 ? 1.0 : 0.0, m == 3 ? 1.0 : 0.0};
+        const double w = a[0], x = a[1], y = a[2], z = a[3];
+        const double Mm[4][4] = {{w, -x, -y, -z}, {x, w, -z, y}, {y, z, w, -x}, {z, -y, x, w}};
+        const double Wm[4][4] = {{w, -x, -y, -z}, {x, w, z, -y}, {y, -z, w, x}, {z, y, -x, w}};
+        for (int k = 0; k < 4; ++k)
+            for (int r = 0; r < 4; ++r) E[k][r][m] = m_type ? Mm[k][r] : Wm[k][r];
+    }
+    int o = 0;
+    for (int r = 0; r < 4; ++r)
+        for (int c = r; c < 4; ++c, ++o) {
+            const double dd = d ? (r == 0 ? 1.0 : -1.0) * (c == 0 ? 1.0 : -1.0) : 1.0;
+            int q = 0;
+            for (int m = 0; m < 4; ++m)
+                for (int n = m; n < 4; ++n, ++q) {
+                    double v = 0.0;
+                    for (int k = 0; k < 4; ++k)
+                        for (int l = 0; l < 4; ++l) {
+                            v += E[k][r][m] * S[4 * k + l] * E[l][c][n];
+                            if (n != m) v += E[k][r][n] * S[4 * k + l] * E[l][c][m];
+                        }
+                    L[10 * o + q] = dd * v;
+                }
+        }
+}
+
 bool spd4(const double* S) {
     double L[4][4] = {};
     for (int j = 0; j < 4; ++j) {
@@ -1335,7 +1381,15 @@ pradmm_status set_sigma_impl(pradmm_s* h, const double* S1, const double* S2) {
         for (int r = 0; r < 3; ++r)
             for (int c = 0; c < 3; ++c) hat[r][c] = S1[4 * (r + 1) + (c + 1)];
         eig3_host(hat, h->U, h->mu);
+        quad_map(S1, true, true, h->LM1D);
+        quad_map(S2, false, true, h->LW2D);
+        quad_map(S1, false, false, h->LW1);
         if (!h->sigma_d) ST(dalloc(h, &h->sigma_d, 32));
+        if (!h->fp64 && !h->fb_q) {
+            ST(dalloc(h, &h->fb_q, (size_t)h->n));
+            ST(dalloc(h, &h->fb_n, 2));
+            CU(cudaMemset(h->fb_n, 0, 2 * sizeof(unsigned int)));
+        }
         CU(cudaMemcpy(h->sigma_d, h->S1, sizeof(double) * 16, cudaMemcpyHostToDevice));
         CU(cudaMemcpy(h->sigma_d + 16, h->S2, sizeof(double) * 16, cudaMemcpyHostToDevice));
         h->general = true;

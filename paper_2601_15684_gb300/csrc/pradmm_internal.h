@@ -145,12 +145,35 @@ cudaError_t launch_unpack3(const R* src, const int32_t* perm, double* dst, int64
 // Passed by value as a kernel parameter.  S1, S2 row-major 4x4; U (row-major
 // 3x3, columns the eigenvectors) and mu the eigen-decomposition of the
 // translation block Sigma1_hat = S1[1..3][1..3].
+// One queued FP64 re-solve: vertex, FP32 A_1 (upper triangle, row by row),
+// b_1 and p^k.
+struct FbRec {
+    int32_t i;
+    float a[10];
+    float b[4];
+    float pk[4];
+    float pad;
+};
+
 template <typename R>
 struct SigmaDev {
     R S1[16];
     R S2[16];
     R U[9];
     R mu[3];
+    // sandwich maps: X(a)^T S X(a) (upper triangle, 10 entries) as a linear
+    // map of a a^T (10 entries), row-major 10 x 10.  LM1D: X = M, S = Sigma_1,
+    // D-conjugated (p-block out-edges); LW2D: X = W, S = Sigma_2,
+    // D-conjugated (p-block in-edges); LW1: X = W, S = Sigma_1 (q-block G3).
+    R LM1D[100];
+    R LW2D[100];
+    R LW1[100];
+    // FP32 handles: p-updates whose sphere-constrained quadratic needs the FP64
+    // re-solve are queued by the p sweep (their FP32 A_1, b_1, p^k) and solved
+    // together by the next kernel, full warps of FP64 work instead of one lane
+    // per warp.  fb_n[k & 1] counts iteration k's entries.
+    FbRec* fb_q = nullptr;   // n records
+    unsigned int* fb_n = nullptr;  // 2 counters
 };
 
 // One iteration with general Sigma: p, q, t sweeps and the s/z sweep with the

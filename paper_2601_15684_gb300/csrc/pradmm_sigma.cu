@@ -98,6 +98,40 @@ __device__ __forceinline__ void add_gts(T y[4], const T G[4][4], const R* S, con
     for (int c = 0; c < 4; ++c) y[c] += w * (G[0][c] * sv[0] + G[1][c] * sv[1] + G[2][c] * sv[2] + G[3][c] * sv[3]);
 }
 
+// P += w a a^T (upper triangle, row by row: 10 entries)
+template <typename T>
+__device__ __forceinline__ void add_outer(T P[10], const Q<T>& a, T w) {
+    const T v[4] = {a.w, a.x, a.y, a.z};
+    int t = 0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const T wm = w * v[m];
+#pragma unroll
+        for (int n = m; n < 4; ++n) P[t++] += wm * v[n];
+    }
+}
+
+// A += L(P): the 10 x 10 sandwich map (SigmaDev) applied to the accumulated
+// outer products, written to both triangles
+template <typename T, typename R>
+__device__ __forceinline__ void apply_map(T A[4][4], const R* L, const T P[10]) {
+    int o = 0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = r; c < 4; ++c, ++o) {
+            T v = T(0);
+#pragma unroll
+            for (int q = 0; q < 10; ++q) v += T(L[10 * o + q]) * P[q];
+            A[r][c] += v;
+            if (c != r) A[c][r] += v;
+        }
+}
+
+#ifndef PRADMM_SIG_MONO
+#define PRADMM_SIG_MONO 1
+#endif
+
 // D X D with D = diag(1, -1, -1, -1)
 template <typename T>
 __device__ __forceinline__ T dsign(int r) {
@@ -106,14 +140,32 @@ __device__ __forceinline__ T dsign(int r) {
 
 // ---- Lemma 1: min_{|x| = 1} 1/2 x^T A x + b^T x ------------------------------
 
+// One Jacobi rotation zeroing a[p][q].  A rotation only has to be orthogonal,
+// not the exact one, so the FP32 instance (PRADMM_FAST_ROT) takes its
+// parameters from the fast reciprocal square root and division intrinsics
+// (cs^2 + sn^2 = 1 to a few ulp; the sweeps still drive the off-diagonal part
+// to the FP32 tolerance).  The FP64 instance is exact.
+#ifndef PRADMM_FAST_ROT
+#define PRADMM_FAST_ROT 1
+#endif
 template <typename T>
 __device__ __forceinline__ void jacobi_rotate(T a[4][4], T v[4][4], int p, int q) {
     const T apq = a[p][q];
     if (apq == T(0)) return;
-    const T theta = (a[q][q] - a[p][p]) / (T(2) * apq);
-    const T at = fabs(theta);
-    T t = at > T(1e15) ? T(0.5) / theta : (theta >= T(0) ? T(1) : T(-1)) / (at + sqrt(theta * theta + T(1)));
-    const T cs = T(1) / sqrt(t * t + T(1)), sn = t * cs;
+    T t, cs;
+    if constexpr (sizeof(T) == sizeof(float) && PRADMM_FAST_ROT) {
+        const float theta = __fdividef(a[q][q] - a[p][p], 2.0f * apq);
+        const float at = fabsf(theta);
+        const float h = theta * theta + 1.0f;
+        t = at > 1e15f ? __fdividef(0.5f, theta) : __fdividef(theta >= 0.0f ? 1.0f : -1.0f, at + h * rsqrtf(h));
+        cs = rsqrtf(t * t + 1.0f);
+    } else {
+        const T theta = (a[q][q] - a[p][p]) / (T(2) * apq);
+        const T at = fabs(theta);
+        t = at > T(1e15) ? T(0.5) / theta : (theta >= T(0) ? T(1) : T(-1)) / (at + sqrt(theta * theta + T(1)));
+        cs = T(1) / sqrt(t * t + T(1));
+    }
+    const T sn = t * cs;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const T kp = a[k][p], kq = a[k][q];
@@ -186,14 +238,27 @@ __device__ void eig4(T a[4][4], T ev[4], T v[4][4]) {
 // the accuracy of the data A and b, not of the arithmetic (FP32 data re-solved
 // in FP64 keeps the FP32 threshold, so the hard case and its sign rule apply
 // as they would to exact data).
+// lam_init: a starting point for the secular Newton iteration (e.g. the root
+// found in lower precision), used when it lies inside the bracket; Newton on
+// the concave increasing 1/|x(lambda)| - 1 lands left of the root after one
+// step from either side and then rises monotonically.  lam_out, v_out
+// (optional): the root (NaN in the hard case) and the eigenvectors.
 template <typename T>
-__device__ int trs4(const T A0[4][4], const T b[4], const T pk[4], T x[4], bool want_fallback, T hard_eps) {
+__device__ int trs4(const T A0[4][4], const T b[4], const T pk[4], T x[4], bool want_fallback, T hard_eps,
+                    T lam_init = T(-1), T* lam_out = nullptr, T (*v_out)[4] = nullptr) {
     T a[4][4], v[4][4], ev[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) a[r][c] = A0[r][c];
     eig4(a, ev, v);
+    if (v_out) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v_out[r][c] = v[r][c];
+    }
+    if (lam_out) *lam_out = T(NAN);
     T g[4], gn2 = T(0);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -242,7 +307,7 @@ __device__ int trs4(const T A0[4][4], const T b[4], const T pk[4], T x[4], bool 
     // (monotone), clamped to the bracket
     // (a lower end strictly above -a_min keeps every 1/(a_k + lambda) finite)
     const T lo = -ev[0] + fmax(fabs(g[0]), T(64) * Tol<T>::jac() * scale), hi = fmax(-ev[0] + gn, lo);
-    T lam = lo;
+    T lam = (lam_init > lo && lam_init < hi) ? lam_init : lo;
     for (int it = 0; it < 60; ++it) {
         T phi = T(0), w2 = T(0);
 #pragma unroll
@@ -259,6 +324,7 @@ __device__ int trs4(const T A0[4][4], const T b[4], const T pk[4], T x[4], bool 
         if (nl == lam) break;
         lam = nl;
     }
+    if (lam_out) *lam_out = lam;
 #pragma unroll
     for (int k = 0; k < 4; ++k) y[k] = -g[k] / (ev[k] + lam);
     T nn = T(0);
@@ -291,18 +357,24 @@ __global__ void __launch_bounds__(256) k_p_sig(GraphDev<R> g, StateDev<R> S, Coe
 #pragma unroll
             for (int cc = 0; cc < 4; ++cc) A[r][cc] = r == cc ? c.beta1 + c.g1 : R(0);
         R G[4][4], bo[4] = {R(0), R(0), R(0), R(0)};
+        R P1[10] = {}, P2[10] = {};
         // out-edges: G1 = M(q_i t~_e) D (the D is applied once at the end)
         for (int e = g.out_ptr[i]; e < g.out_ptr[i + 1]; ++e) {
             const R4<R> te = IO<R>::ld(g.out_te, e);
             const R4<R> tj = IO<R>::ld(S.t, g.out_idx[e]);
-            mat_M(qmul_pr(qi, te.a, te.b, te.c), G);
+            const Q<R> a = qmul_pr(qi, te.a, te.b, te.c);
+            mat_M(a, G);
             const R r4[4] = {R(0), tj.a - sr.a, tj.b - sr.b, tj.c - sr.c};
-            R Ao[4][4] = {};
-            add_sandwich(Ao, G, sg.S1, R(2) * te.d);
+            if (PRADMM_SIG_MONO) {
+                add_outer(P1, a, R(2) * te.d);
+            } else {
+                R Ao[4][4] = {};
+                add_sandwich(Ao, G, sg.S1, R(2) * te.d);
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+                for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc) A[r][cc] += dsign<R>(r) * dsign<R>(cc) * Ao[r][cc];
+                    for (int cc = 0; cc < 4; ++cc) A[r][cc] += dsign<R>(r) * dsign<R>(cc) * Ao[r][cc];
+            }
             add_gts(bo, G, sg.S1, r4, R(-2) * te.d);
         }
         // in-edges: G2 = W(q_l q_e) D; the stored record is k_e q_e, so
@@ -313,17 +385,25 @@ __global__ void __launch_bounds__(256) k_p_sig(GraphDev<R> g, StateDev<R> S, Coe
             const Q<R> qk = asq<R>(IO<R>::ld(g.in_qk, e));
             const R kap = sqrt(qk.w * qk.w + qk.x * qk.x + qk.y * qk.y + qk.z * qk.z);
             const Q<R> h = qmul(asq<R>(IO<R>::ld(S.q, g.in_idx[e])), qk);
-            mat_W(h, G);
-            R Ai[4][4] = {};
-            add_sandwich(Ai, G, sg.S2, R(2) / kap);
+            if (PRADMM_SIG_MONO) {
+                add_outer(P2, h, R(2) / kap);
+            } else {
+                mat_W(h, G);
+                R Ai[4][4] = {};
+                add_sandwich(Ai, G, sg.S2, R(2) / kap);
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+                for (int r = 0; r < 4; ++r)
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc) A[r][cc] += dsign<R>(r) * dsign<R>(cc) * Ai[r][cc];
+                    for (int cc = 0; cc < 4; ++cc) A[r][cc] += dsign<R>(r) * dsign<R>(cc) * Ai[r][cc];
+            }
             hs.w += h.w;
             hs.x += h.x;
             hs.y += h.y;
             hs.z += h.z;
+        }
+        if (PRADMM_SIG_MONO) {
+            apply_map(A, sg.LM1D, P1);
+            apply_map(A, sg.LW2D, P2);
         }
         // b_1 = own - 2 D (sum G1-part) - 2 D (sigma2 (sum h)^*)
         const Q<R> s2 = {sg.S2[0], sg.S2[4], sg.S2[8], sg.S2[12]};
@@ -334,21 +414,124 @@ __global__ void __launch_bounds__(256) k_p_sig(GraphDev<R> g, StateDev<R> S, Coe
         const R pkv[4] = {pk.w, pk.x, pk.y, pk.z};
         R x[4];
         if (trs4<R>(A, b, pkv, x, sizeof(R) == sizeof(float), R(64) * Tol<R>::jac())) {
-            double Ad[4][4], bd[4], pd[4], xd[4];
+            // queued for k_p_sig_fb, which writes p_i
+            const unsigned slot = atomicAdd(&sg.fb_n[k & 1], 1u);
+            FbRec& q = sg.fb_q[slot];
+            q.i = (int32_t)i;
+            int t = 0;
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int cc = r; cc < 4; ++cc) q.a[t++] = float(A[r][cc]);
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                bd[r] = double(b[r]);
-                pd[r] = double(pkv[r]);
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) Ad[r][cc] = double(A[r][cc]);
+                q.b[r] = float(b[r]);
+                q.pk[r] = float(pkv[r]);
             }
-            trs4<double>(Ad, bd, pd, xd, false, 1e-5);  // FP32 data
-#pragma unroll
-            for (int r = 0; r < 4; ++r) x[r] = R(xd[r]);
             atomicAdd(&ctrl->fallbacks, 1ull);
+            continue;
         }
         IO<R>::st(pn, i, x[0], x[1], x[2], x[3]);
     }
+}
+
+// The FP64 re-solves queued by k_p_sig in iteration k (FP32 handles only):
+// entry kFbLanes w + l goes to lane l of global warp w, and consecutive warps
+// go to different CTAs, so the few warps of FP64 work spread over the SMs.
+// Warm start: the FP32 eigenvectors of A_1, orthonormalised in FP64, rotate
+// the problem (A' = V^T A V, b' = V^T b, p' = V^T p^k; the constraint |x| = 1
+// and the hard-case tests are invariant), so the FP64 Jacobi sweeps start
+// from a nearly diagonal matrix; x = V x'.  Clears iteration k+1's counter
+// (its last use was iteration k-1, finished).
+#ifndef PRADMM_FB_LANES
+#define PRADMM_FB_LANES 32
+#endif
+#ifndef PRADMM_FB_WARM
+#define PRADMM_FB_WARM 1
+#endif
+#ifndef PRADMM_FB_LAM
+#define PRADMM_FB_LAM 1
+#endif
+constexpr unsigned kFbLanes = PRADMM_FB_LANES;
+
+__global__ void __launch_bounds__(128) k_p_sig_fb(SigmaDev<float> sg, StateDev<float> S, const Ctrl* ctrl) {
+    if (ctrl->halt) return;
+    const long long k = ctrl->iter;
+    float* pn = S.p[(k + 1) & 1];
+    const unsigned cnt = sg.fb_n[k & 1];
+    const unsigned lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const unsigned nw = gridDim.x * wpb;
+    for (unsigned w = blockIdx.x + gridDim.x * wib; kFbLanes * w < cnt; w += nw) {
+        const unsigned e = kFbLanes * w + lane;
+        if (lane >= kFbLanes || e >= cnt) continue;
+        const FbRec& q = sg.fb_q[e];
+        double Ad[4][4], bd[4], pd[4], xd[4];
+        float Af[4][4];
+        int t = 0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int cc = r; cc < 4; ++cc) {
+                Ad[r][cc] = Ad[cc][r] = double(q.a[t]);
+                Af[r][cc] = Af[cc][r] = q.a[t];
+                ++t;
+            }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            bd[r] = double(q.b[r]);
+            pd[r] = double(q.pk[r]);
+        }
+        if (PRADMM_FB_WARM) {
+            // FP32 eigenvectors and secular root (no fallback test)
+            float vf[4][4], bf[4], pf[4], xf[4], lamf;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                bf[r] = q.b[r];
+                pf[r] = q.pk[r];
+            }
+            trs4<float>(Af, bf, pf, xf, false, 64.0f * Tol<float>::jac(), -1.0f, &lamf, vf);
+            double V[4][4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) V[r][cc] = double(vf[r][cc]);
+            // modified Gram-Schmidt on the columns
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+#pragma unroll
+                for (int i2 = 0; i2 < j; ++i2) {
+                    const double d = V[0][i2] * V[0][j] + V[1][i2] * V[1][j] + V[2][i2] * V[2][j] + V[3][i2] * V[3][j];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) V[r][j] -= d * V[r][i2];
+                }
+                const double nv = 1.0 / sqrt(V[0][j] * V[0][j] + V[1][j] * V[1][j] + V[2][j] * V[2][j] + V[3][j] * V[3][j]);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) V[r][j] *= nv;
+            }
+            double X[4][4], Ap[4][4], bp[4], pp[4], xp[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc)
+                    X[r][cc] = Ad[r][0] * V[0][cc] + Ad[r][1] * V[1][cc] + Ad[r][2] * V[2][cc] + Ad[r][3] * V[3][cc];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+#pragma unroll
+                for (int cc = r; cc < 4; ++cc)
+                    Ap[r][cc] = Ap[cc][r] = V[0][r] * X[0][cc] + V[1][r] * X[1][cc] + V[2][r] * X[2][cc] + V[3][r] * X[3][cc];
+                bp[r] = V[0][r] * bd[0] + V[1][r] * bd[1] + V[2][r] * bd[2] + V[3][r] * bd[3];
+                pp[r] = V[0][r] * pd[0] + V[1][r] * pd[1] + V[2][r] * pd[2] + V[3][r] * pd[3];
+            }
+            // lamf is NaN in the hard case: the bracket test then fails and Newton starts at lo
+            trs4<double>(Ap, bp, pp, xp, false, 1e-5, PRADMM_FB_LAM ? double(lamf) : -1.0);  // FP32 data
+#pragma unroll
+            for (int r = 0; r < 4; ++r) xd[r] = V[r][0] * xp[0] + V[r][1] * xp[1] + V[r][2] * xp[2] + V[r][3] * xp[3];
+        } else {
+            trs4<double>(Ad, bd, pd, xd, false, 1e-5);  // FP32 data
+        }
+        IO<float>::st(pn, q.i, float(xd[0]), float(xd[1]), float(xd[2]), float(xd[3]));
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) sg.fb_n[(k + 1) & 1] = 0u;
 }
 
 // 4x4 SPD solve by Cholesky (A = L L^T)
@@ -406,6 +589,7 @@ __global__ void __launch_bounds__(256) k_q_sig(GraphDev<R> g, StateDev<R> S, Coe
             for (int cc = 0; cc < 4; ++cc) A[r][cc] = r == cc ? c.beta1 + c.g2 : R(0);
         const Q<R> Pc = {P.w, -P.x, -P.y, -P.z};
         const Q<R> s2 = {sg.S2[0], sg.S2[4], sg.S2[8], sg.S2[12]};
+        R P3[10] = {};
         for (int e = g.out_ptr[i]; e < g.out_ptr[i + 1]; ++e) {
             const int j = g.out_idx[e];
             const R4<R> te = IO<R>::ld(g.out_te, e);
@@ -415,8 +599,10 @@ __global__ void __launch_bounds__(256) k_q_sig(GraphDev<R> g, StateDev<R> S, Coe
             const R kap = sqrt(qk.w * qk.w + qk.x * qk.x + qk.y * qk.y + qk.z * qk.z);
             // G3 = W(t~_e p_i^*)
             R G[4][4];
-            mat_W(qmul_pl(te.a, te.b, te.c, Pc), G);
-            add_sandwich(A, G, sg.S1, R(2) * te.d);
+            const Q<R> a3 = qmul_pl(te.a, te.b, te.c, Pc);
+            mat_W(a3, G);
+            if (PRADMM_SIG_MONO) add_outer(P3, a3, R(2) * te.d);
+            else add_sandwich(A, G, sg.S1, R(2) * te.d);
             const R r4[4] = {R(0), tj.a - sr.a, tj.b - sr.b, tj.c - sr.c};
             add_gts(b, G, sg.S1, r4, R(2) * te.d);
             // G4' = M(p_j^*) W(k_e q_e) = k_e G4: k_e G4^T S2 G4 = (1/k_e) G4'^T S2 G4',
@@ -436,6 +622,7 @@ __global__ void __launch_bounds__(256) k_q_sig(GraphDev<R> g, StateDev<R> S, Coe
             b[2] += R(2) * v.y;
             b[3] += R(2) * v.z;
         }
+        if (PRADMM_SIG_MONO) apply_map(A, sg.LW1, P3);
         R x[4];
         chol_solve4(A, b, x);
         const R lw = li.w - c.tb1 * (P.w - x[0]), lx = li.x - c.tb1 * (P.x - x[1]);
@@ -610,6 +797,7 @@ template <typename R>
 cudaError_t launch_sigma_iteration(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c,
                                    const SigmaDev<R>& sg, const Launch& L) {
     k_p_sig<R><<<L.grid_p, L.block, 0, L.stream>>>(g, s, c, sg, L.ctrl);
+    if constexpr (sizeof(R) == sizeof(float)) k_p_sig_fb<<<152, 128, 0, L.stream>>>(sg, s, L.ctrl);
     k_q_sig<R><<<L.grid_q, L.block, 0, L.stream>>>(g, s, c, sg, L.ctrl, L.part, L.pstride);
     k_t_sig<R><<<L.grid_t, L.block, 0, L.stream>>>(g, s, c, sg, L.ctrl, L.part, L.pstride);
     k_s_sig<R><<<L.grid_sp, L.block, 0, L.stream>>>(g, s, c, sg, L);

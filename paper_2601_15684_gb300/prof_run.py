@@ -7,7 +7,9 @@ so `ncu -k regex:... -s ... -c ...` can pick single sweeps), then exits.
     python -m paper_2601_15684_gb300.prof_run --workload lattice1m --iters 12
 
 With --adjoint K it records K iterations (checkpoint every --ckpt) and runs
-the reverse sweeps once for a seeded cotangent.
+the reverse sweeps once for a seeded cotangent.  With --sigma the iterations
+use general weight matrices: Sigma_1 = Q diag(1, 2, 0.5, 4) Q^T (Q a seeded
+random rotation) and Sigma_2 = diag(1, 0.5, 2, 1).
 """
 from __future__ import annotations
 
@@ -25,12 +27,18 @@ def main(argv=None) -> int:
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--adjoint", type=int, default=0)
     ap.add_argument("--ckpt", type=int, default=20, help="checkpoint spacing (0: chosen from free memory)")
+    ap.add_argument("--sigma", action="store_true", help="general Sigma_1, Sigma_2")
     a = ap.parse_args(argv)
     from paper_2601_15684_gb300 import build_lib, pradmm, synth
 
     build_lib.build()
     g = synth.workload(a.workload)
     with pradmm.Solver(g, precision=a.precision, use_graph=a.graph, block=a.block) as S:
+        if a.sigma:
+            import numpy as np
+            rng = np.random.default_rng(0)
+            Q, _ = np.linalg.qr(rng.normal(size=(4, 4)))
+            S.set_sigma(Q @ np.diag([1.0, 2.0, 0.5, 4.0]) @ Q.T, np.diag([1.0, 0.5, 2.0, 1.0]))
         S.init_odometry()
         t0 = time.perf_counter()
         e = S.step(a.iters)
