@@ -42,6 +42,11 @@ struct IO<float> {
     static __device__ __forceinline__ void st(float* p, int64_t i, float a, float b, float c, float d) {
         reinterpret_cast<float4*>(p)[i] = make_float4(a, b, c, d);
     }
+    // read-only (non-coherent) path: only for arrays no thread writes during the launch
+    static __device__ __forceinline__ R4<float> ldg(const float* __restrict__ p, int64_t i) {
+        float4 v = __ldg(reinterpret_cast<const float4*>(p) + i);
+        return {v.x, v.y, v.z, v.w};
+    }
 };
 
 template <>
@@ -61,7 +66,20 @@ struct IO<double> {
         v[0] = make_double2(a, b);
         v[1] = make_double2(c, d);
     }
+    static __device__ __forceinline__ R4<double> ldg(const double* __restrict__ p, int64_t i) {
+        const double2* v = reinterpret_cast<const double2*>(p) + 2 * i;
+        double2 u = __ldg(v), w = __ldg(v + 1);
+        return {u.x, u.y, w.x, w.y};
+    }
 };
+
+// Neighbour gather: the read-only path when NC (the launch writes none of the
+// gathered arrays), else a coherent load.
+template <typename R, bool NC>
+__device__ __forceinline__ R4<R> gat(const R* p, int64_t i) {
+    if constexpr (NC) return IO<R>::ldg(p, i);
+    else return IO<R>::ld(p, i);
+}
 
 template <typename A, typename R>
 __device__ __forceinline__ Q<A> asq(const R4<R>& v) {
@@ -348,7 +366,7 @@ struct QEdge {
 };
 
 // One vertex of the q-block + lambda update; adds |dq_i|^2, |dlam_i|^2.
-template <typename R, bool PIPE = false>
+template <typename R, bool PIPE = false, bool NC = false>
 __device__ __forceinline__ void q_vertex(const GraphDev<R>& g, const StateDev<R>& S, const Coef<R>& c, const R* pn,
                                          int64_t i, Acc<R>& adq, Acc<R>& adl) {
     const Q<R> pi = asq<R>(IO<R>::ld(pn, i));
@@ -365,8 +383,8 @@ __device__ __forceinline__ void q_vertex(const GraphDev<R>& g, const StateDev<R>
             x.qk = IO<R>::ldcs(g.out_qk, e);
         },
         [&](QEdge<R>& x) {
-            x.tj = IO<R>::ld(S.t, x.j);
-            x.pj = IO<R>::ld(pn, x.j);
+            x.tj = gat<R, NC>(S.t, x.j);
+            x.pj = gat<R, NC>(pn, x.j);
         },
         [&](const QEdge<R>& x) {
             const R rx = x.tj.a - sr.a, ry = x.tj.b - sr.b, rz = x.tj.c - sr.c;
@@ -397,7 +415,7 @@ struct TEdge {
 };
 
 // One vertex of the t-block; adds |dt_i|^2.  PIPE: see for_edges2.
-template <typename R, bool PIPE = false>
+template <typename R, bool PIPE = false, bool NC = false>
 __device__ __forceinline__ void t_vertex(const GraphDev<R>& g, const StateDev<R>& S, const Coef<R>& c, const R* pn,
                                          int64_t i, Acc<R>& adt) {
     const R4<R> tr = IO<R>::ld(S.t, i);  // (t_i, 1/A_3)
@@ -413,9 +431,9 @@ __device__ __forceinline__ void t_vertex(const GraphDev<R>& g, const StateDev<R>
             x.te = IO<R>::ldcs(g.in_te, e);
         },
         [&](TEdge<R>& x) {
-            x.sl = IO<R>::ld(S.s, x.l);
-            x.ql = IO<R>::ld(S.q, x.l);
-            x.pl = IO<R>::ld(pn, x.l);
+            x.sl = gat<R, NC>(S.s, x.l);
+            x.ql = gat<R, NC>(S.q, x.l);
+            x.pl = gat<R, NC>(pn, x.l);
         },
         [&](const TEdge<R>& x) {
             R cx, cy, cz;
@@ -457,7 +475,7 @@ struct PEdge {
 
 // One vertex of the s-block + z update (WITH_S; adds |dz_i|^2) followed by
 // the p-block of the next iteration, which reads p from pc and writes pn.
-template <typename R, bool WITH_S, bool PIPE = false>
+template <typename R, bool WITH_S, bool PIPE = false, bool NC = false>
 __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R>& S, const Coef<R>& c, const R* pc,
                                           R* pn, int64_t i, Acc<R>& adz, Ctrl* ctrl) {
     const R4<R> sr = IO<R>::ld(S.s, i);  // (s_i, 1/A_2)
@@ -475,7 +493,7 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
             x.j = __ldcs(g.out_idx + e);
             x.te = IO<R>::ldcs(g.out_te, e);
         },
-        [&](SEdge<R>& x) { x.tj = IO<R>::ld(S.t, x.j); },
+        [&](SEdge<R>& x) { x.tj = gat<R, NC>(S.t, x.j); },
         [&](const SEdge<R>& x) {
             const R w2 = R(2) * x.te.d;
             if (WITH_S) {
@@ -517,7 +535,7 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
             x.l = __ldcs(g.in_idx + e);
             x.qk = IO<R>::ldcs(g.in_qk, e);
         },
-        [&](PEdge<R>& x) { x.ql = IO<R>::ld(S.q, x.l); },
+        [&](PEdge<R>& x) { x.ql = gat<R, NC>(S.q, x.l); },
         [&](const PEdge<R>& x) { axpy(v, R(2), qmul(asq<R>(x.ql), asq<R>(x.qk))); });
     p_normalise<R>(g, S, i, v, qr, lr, pr, sx, sy, sz, c, pn, ctrl);
 }

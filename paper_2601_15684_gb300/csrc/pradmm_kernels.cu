@@ -51,6 +51,12 @@
 #ifndef PRADMM_PIPE_SP
 #define PRADMM_PIPE_SP 0
 #endif
+// 1: neighbour gathers on the read-only (non-coherent) path: each plain sweep
+// writes none of the arrays it gathers (the batched kernel, which runs all
+// sweeps in one launch, keeps coherent loads)
+#ifndef PRADMM_NC
+#define PRADMM_NC 1
+#endif
 #if PRADMM_MINB_T > 0
 #define PRADMM_BOUNDS_T __launch_bounds__(256, PRADMM_MINB_T)
 #else
@@ -71,7 +77,7 @@ __global__ void __launch_bounds__(256, PRADMM_MINB_Q) k_q(GraphDev<R> g, StateDe
     const R* pn = S.p[(k + 1) & 1];
     Acc<R> adq, adl;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x)
-        q_vertex<R, PRADMM_PIPE_Q != 0>(g, S, c, pn, i, adq, adl);
+        q_vertex<R, PRADMM_PIPE_Q != 0, PRADMM_NC != 0>(g, S, c, pn, i, adq, adl);
     const double sq = block_sum(adq.get(), sh);
     const double sl = block_sum(adl.get(), sh);
     if (threadIdx.x == 0) {
@@ -89,7 +95,7 @@ __global__ void PRADMM_BOUNDS_T k_t(GraphDev<R> g, StateDev<R> S, Coef<R> c, Ctr
     const R* pn = S.p[(k + 1) & 1];
     Acc<R> adt;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x)
-        t_vertex<R, true>(g, S, c, pn, i, adt);
+        t_vertex<R, true, PRADMM_NC != 0>(g, S, c, pn, i, adt);
     const double st = block_sum(adt.get(), sh);
     if (threadIdx.x == 0) part[SLOT_DT * pstride + blockIdx.x] = st;
 }
@@ -108,7 +114,7 @@ __global__ void __launch_bounds__(256, PRADMM_MINB_SP) k_sp(GraphDev<R> g, State
     R* pn = WITH_S ? S.p[k & 1] : S.p[(k + 1) & 1];        // p computed ahead
     Acc<R> adz;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x)
-        sp_vertex<R, WITH_S, PRADMM_PIPE_SP != 0>(g, S, c, pc, pn, i, adz, ctrl);
+        sp_vertex<R, WITH_S, PRADMM_PIPE_SP != 0, PRADMM_NC != 0>(g, S, c, pc, pn, i, adz, ctrl);
     if (WITH_S) {
         const double sd = block_sum(adz.get(), sh);
         if (threadIdx.x == 0) L.part[SLOT_DZ * L.pstride + blockIdx.x] = sd;
