@@ -20,7 +20,8 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libpradmm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["pradmm_kernels.cu", "pradmm_batch.cu", "pradmm_adjoint.cu", "pradmm_sigma.cu", "pradmm_noalloc.cu"]
+CU_SOURCES = ["pradmm_kernels.cu", "pradmm_batch.cu", "pradmm_adjoint.cu", "pradmm_sigma.cu", "pradmm_noalloc.cu",
+              "pradmm_setup.cu"]
 CPP_SOURCES = ["pradmm_api.cpp"]
 HEADERS = [os.path.join(CSRC, "pradmm_internal.h"), os.path.join(CSRC, "pradmm_device.cuh"),
            os.path.join(INCLUDE, "pradmm.h")]
@@ -62,8 +63,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         o = os.path.join(BUILD, src + ".o")
         objs.append(o)
         if force or _stale(o, [s] + HEADERS):
-            jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-I", INCLUDE, "-I", CSRC, "-I", cuda_inc,
-                         "-c", s, "-o", o])
+            # no contraction into fused multiply-adds: the host arithmetic that the
+            # device repeats (quaternion normalisation) rounds the same on both
+            jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-pthread", "-ffp-contract=off", "-I", INCLUDE,
+                         "-I", CSRC, "-I", cuda_inc, "-c", s, "-o", o])
     procs = [(j, subprocess.Popen(j, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)) for j in jobs]
     errors = []
     for j, p in procs:
@@ -76,7 +79,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         raise RuntimeError("libpradmm build failed:\n" + "\n".join(errors))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [_nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-cudart", "static"]
+        cmd = [_nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-cudart", "static", "-lpthread"]
         r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
         if r.returncode != 0:
             raise RuntimeError("libpradmm link failed:\n" + " ".join(cmd) + "\n" + r.stdout)

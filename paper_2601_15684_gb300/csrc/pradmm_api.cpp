@@ -13,6 +13,7 @@
 #include <new>
 #include <string>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "pradmm_internal.h"
@@ -260,15 +261,74 @@ pradmm_status check_params(const pradmm_params* p) {
     return PRADMM_OK;
 }
 
+// Runs f(begin, end) over [0, count) split into contiguous ranges, one per
+// host thread (up to 16; small counts run on the calling thread).
+template <typename F>
+void parallel_for(int64_t count, F f) {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int64_t T = std::min<int64_t>(std::min<unsigned>(hw, 16u), std::max<int64_t>(1, count / 32768));
+    if (T <= 1) {
+        f(int64_t(0), count);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(T);
+    for (int64_t t = 0; t < T; ++t) th.emplace_back(f, count * t / T, count * (t + 1) / T);
+    for (auto& x : th) x.join();
+}
+
 // Stable counting sort of edge ids by key; returns ptr[n+1] and perm (sorted
-// position -> input edge).
+// position -> input edge).  Each host thread owns a contiguous range of keys:
+// it scans every edge in input order and places those whose key it owns, so
+// every key's edges keep their input order.
 void counting_sort(int64_t n, int64_t m, const int32_t* key, std::vector<int32_t>& ptr, std::vector<int32_t>& perm) {
     ptr.assign(n + 1, 0);
-    for (int64_t e = 0; e < m; ++e) ptr[key[e] + 1]++;
-    for (int64_t i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
-    std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
     perm.assign(m, 0);
-    for (int64_t e = 0; e < m; ++e) perm[fill[key[e]]++] = (int32_t)e;
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int64_t T = std::min<int64_t>(std::min<unsigned>(hw, 16u), std::max<int64_t>(1, m / 65536));
+    std::vector<int64_t> k0(T + 1), base(T + 1, 0);
+    for (int64_t t = 0; t <= T; ++t) k0[t] = n * t / T;
+    auto count = [&](int64_t t) {
+        for (int64_t e = 0; e < m; ++e) {
+            const int64_t k = key[e];
+            if (k >= k0[t] && k < k0[t + 1]) ptr[k + 1]++;
+        }
+    };
+    auto place = [&](int64_t t) {
+        // prefix over the owned keys, offset by the edges of all lower keys;
+        // a thread touches only ptr[k + 1] of its own keys k
+        const int64_t a = k0[t], b = k0[t + 1];
+        std::vector<int32_t> fill(b - a);
+        int64_t run = base[t];
+        for (int64_t k = a; k < b; ++k) {
+            fill[k - a] = (int32_t)run;
+            run += ptr[k + 1];
+            ptr[k + 1] = (int32_t)run;
+        }
+        for (int64_t e = 0; e < m; ++e) {
+            const int64_t k = key[e];
+            if (k >= a && k < b) perm[fill[k - a]++] = (int32_t)e;
+        }
+    };
+    if (T <= 1) {
+        count(0);
+        place(0);
+        return;
+    }
+    {
+        std::vector<std::thread> th;
+        for (int64_t t = 0; t < T; ++t) th.emplace_back(count, t);
+        for (auto& x : th) x.join();
+    }
+    // edges owned by the threads before t (the counts of keys [k0[t], k0[t+1]) sit in ptr[k0[t]+1 .. k0[t+1]])
+    for (int64_t t = 0; t < T; ++t) {
+        int64_t c = 0;
+        for (int64_t k = k0[t]; k < k0[t + 1]; ++k) c += ptr[k + 1];
+        base[t + 1] = base[t] + c;
+    }
+    std::vector<std::thread> th;
+    for (int64_t t = 0; t < T; ++t) th.emplace_back(place, t);
+    for (auto& x : th) x.join();
 }
 
 // CSR of one edge order over internal vertex ids: the edges of internal
@@ -276,7 +336,7 @@ void counting_sort(int64_t n, int64_t m, const int32_t* key, std::vector<int32_t
 struct Csr {
     std::vector<int32_t> ptr;   // n + 1
     std::vector<int32_t> idx;   // other endpoint (internal id) per slot
-    std::vector<int64_t> edge;  // input edge per slot
+    std::vector<int32_t> edge;  // input edge per slot
 };
 
 Csr build_csr(int64_t n, const std::vector<int32_t>& perm, const std::vector<int32_t>& iperm,
@@ -287,67 +347,78 @@ Csr build_csr(int64_t n, const std::vector<int32_t>& perm, const std::vector<int
     const int64_t m = C.ptr[n];
     C.idx.assign(m, 0);
     C.edge.assign(m, -1);
-    for (int64_t i = 0; i < n; ++i) {
-        const int32_t u = perm[i];
-        for (int32_t k = 0; k < ptr[u + 1] - ptr[u]; ++k) {
-            const int64_t e = sorted_edges[ptr[u] + k];
-            C.idx[C.ptr[i] + k] = iperm[other[e]];
-            C.edge[C.ptr[i] + k] = e;
+    parallel_for(n, [&](int64_t i0, int64_t i1) {
+        for (int64_t i = i0; i < i1; ++i) {
+            const int32_t u = perm[i];
+            for (int32_t k = 0; k < ptr[u + 1] - ptr[u]; ++k) {
+                const int32_t e = sorted_edges[ptr[u] + k];
+                C.idx[C.ptr[i] + k] = iperm[other[e]];
+                C.edge[C.ptr[i] + k] = e;
+            }
         }
-    }
+    });
     return C;
 }
 
-// Packs (t_e, omega_e) and kappa_e q_e per slot; padding slots are zero.
-template <typename R>
-pradmm_status upload_slots(pradmm_s* h, const Csr& S, const std::vector<double>& ka, const std::vector<double>& om,
-                           void* te_d, void* qk_d) {
-    const int64_t slots = (int64_t)S.edge.size();
-    std::vector<R> te(4 * slots, R(0)), qk(4 * slots, R(0));
-    for (int64_t k = 0; k < slots; ++k) {
-        const int64_t e = S.edge[k];
-        if (e < 0) continue;
-        for (int c = 0; c < 3; ++c) te[4 * k + c] = R(h->te[3 * e + c]);
-        te[4 * k + 3] = R(om[e]);
-        for (int c = 0; c < 4; ++c) qk[4 * k + c] = R(ka[e] * h->qe[4 * e + c]);
+// Host-side check of one edge (the caller's graph is never trusted).
+pradmm_status check_edge(int64_t n, int64_t e, const int32_t* src, const int32_t* dst, const double* q_meas,
+                         const double* t_meas, const double* kappa, const double* omega) {
+    if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n)
+        return fail(PRADMM_ERR_INDEX, "edge %lld = (%d, %d) has an endpoint outside [0, %lld)", (long long)e, src[e],
+                    dst[e], (long long)n);
+    if (src[e] == dst[e]) return fail(PRADMM_ERR_SELFLOOP, "edge %lld is a self-loop (%d, %d)", (long long)e, src[e], dst[e]);
+    const double ka = kappa ? kappa[e] : 1.0, om = omega ? omega[e] : 1.0;
+    if (!std::isfinite(ka) || !std::isfinite(om) || !(ka > 0) || !(om > 0))
+        return fail(ka > 0 && om > 0 ? PRADMM_ERR_NONFINITE : PRADMM_ERR_ARG, "edge %lld: weights must be finite and > 0",
+                    (long long)e);
+    double nn = 0.0;
+    for (int c = 0; c < 4; ++c) {
+        if (!std::isfinite(q_meas[4 * e + c])) return fail(PRADMM_ERR_NONFINITE, "edge %lld: q_meas not finite", (long long)e);
+        nn += q_meas[4 * e + c] * q_meas[4 * e + c];
     }
-    if (slots > 0) {
-        CU(cudaMemcpy(te_d, te.data(), sizeof(R) * te.size(), cudaMemcpyHostToDevice));
-        CU(cudaMemcpy(qk_d, qk.data(), sizeof(R) * qk.size(), cudaMemcpyHostToDevice));
-    }
+    for (int c = 0; c < 3; ++c)
+        if (!std::isfinite(t_meas[3 * e + c])) return fail(PRADMM_ERR_NONFINITE, "edge %lld: t_meas not finite", (long long)e);
+    nn = std::sqrt(nn);
+    if (std::fabs(nn - 1.0) > 1e-6) return fail(PRADMM_ERR_QUATERNION, "edge %lld: |q_meas| = %.17g is not 1", (long long)e, nn);
     return PRADMM_OK;
 }
 
 pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const double* q_meas, const double* t_meas,
                     const double* kappa, const double* omega) {
     const int64_t n = h->n, m = h->m;
-    // ---- validation (never trust the caller's graph) ----
+    // ---- validation (never trust the caller's graph), in parallel; the first
+    // failing edge is re-checked on this thread for its message ----
     std::vector<double> ka(m, 1.0), om(m, 1.0);
     h->src.assign(src, src + m);
     h->dst.assign(dst, dst + m);
     h->qe.assign(q_meas, q_meas + 4 * m);
     h->te.assign(t_meas, t_meas + 3 * m);
-    for (int64_t e = 0; e < m; ++e) {
-        if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n)
-            return fail(PRADMM_ERR_INDEX, "edge %lld = (%d, %d) has an endpoint outside [0, %lld)", (long long)e,
-                        src[e], dst[e], (long long)n);
-        if (src[e] == dst[e]) return fail(PRADMM_ERR_SELFLOOP, "edge %lld is a self-loop (%d, %d)", (long long)e, src[e], dst[e]);
-        if (kappa) ka[e] = kappa[e];
-        if (omega) om[e] = omega[e];
-        if (!std::isfinite(ka[e]) || !std::isfinite(om[e]) || !(ka[e] > 0) || !(om[e] > 0))
-            return fail(ka[e] > 0 && om[e] > 0 ? PRADMM_ERR_NONFINITE : PRADMM_ERR_ARG,
-                        "edge %lld: weights must be finite and > 0", (long long)e);
-        double nn = 0.0;
-        for (int c = 0; c < 4; ++c) {
-            if (!std::isfinite(q_meas[4 * e + c])) return fail(PRADMM_ERR_NONFINITE, "edge %lld: q_meas not finite", (long long)e);
-            nn += q_meas[4 * e + c] * q_meas[4 * e + c];
+    std::mutex bad_mu;
+    int64_t bad = m;
+    parallel_for(m, [&](int64_t e0, int64_t e1) {
+        for (int64_t e = e0; e < e1; ++e) {
+            bool ok = src[e] >= 0 && src[e] < n && dst[e] >= 0 && dst[e] < n && src[e] != dst[e];
+            const double k_e = kappa ? kappa[e] : 1.0, w_e = omega ? omega[e] : 1.0;
+            ok = ok && std::isfinite(k_e) && std::isfinite(w_e) && k_e > 0 && w_e > 0;
+            double nn = 0.0;
+            for (int c = 0; c < 4; ++c) nn += q_meas[4 * e + c] * q_meas[4 * e + c];
+            ok = ok && std::isfinite(nn) && std::isfinite(t_meas[3 * e]) && std::isfinite(t_meas[3 * e + 1]) &&
+                 std::isfinite(t_meas[3 * e + 2]);
+            nn = std::sqrt(nn);
+            ok = ok && std::fabs(nn - 1.0) <= 1e-6;
+            if (!ok) {
+                std::lock_guard<std::mutex> lk(bad_mu);
+                bad = std::min(bad, e);
+                return;
+            }
+            ka[e] = k_e;
+            om[e] = w_e;
+            for (int c = 0; c < 4; ++c) h->qe[4 * e + c] /= nn;
         }
-        for (int c = 0; c < 3; ++c)
-            if (!std::isfinite(t_meas[3 * e + c])) return fail(PRADMM_ERR_NONFINITE, "edge %lld: t_meas not finite", (long long)e);
-        nn = std::sqrt(nn);
-        if (std::fabs(nn - 1.0) > 1e-6)
-            return fail(PRADMM_ERR_QUATERNION, "edge %lld: |q_meas| = %.17g is not 1", (long long)e, nn);
-        for (int c = 0; c < 4; ++c) h->qe[4 * e + c] /= nn;
+    });
+    if (bad < m) {
+        const pradmm_status st = check_edge(n, bad, src, dst, q_meas, t_meas, kappa, omega);
+        return st != PRADMM_OK ? st : fail(PRADMM_ERR_ARG, "edge %lld is invalid", (long long)bad);
     }
     // ---- CSR by tail (out) and by head (in), input order inside a vertex ----
     std::vector<int32_t> optr, operm, iptr, ipermv;
@@ -356,40 +427,47 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
     // ---- internal vertex order: by degree within windows of consecutive ids ----
     std::vector<int32_t> perm(n), iperm(n);
     for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
-    for (int64_t w0 = 0; w0 < n; w0 += kSortWindow) {
-        const int64_t w1 = std::min<int64_t>(n, w0 + kSortWindow);
-        std::stable_sort(perm.begin() + w0, perm.begin() + w1, [&](int32_t a, int32_t b) {
-            return (optr[a + 1] - optr[a]) + (iptr[a + 1] - iptr[a]) > (optr[b + 1] - optr[b]) + (iptr[b + 1] - iptr[b]);
-        });
+    if (kSortWindow > 1) {
+        for (int64_t w0 = 0; w0 < n; w0 += kSortWindow) {
+            const int64_t w1 = std::min<int64_t>(n, w0 + kSortWindow);
+            std::stable_sort(perm.begin() + w0, perm.begin() + w1, [&](int32_t a, int32_t b) {
+                return (optr[a + 1] - optr[a]) + (iptr[a + 1] - iptr[a]) > (optr[b + 1] - optr[b]) + (iptr[b + 1] - iptr[b]);
+            });
+        }
     }
     for (int64_t i = 0; i < n; ++i) iperm[perm[i]] = (int32_t)i;
     const Csr so = build_csr(n, perm, iperm, optr, operm, dst);
     const Csr si = build_csr(n, perm, iperm, iptr, ipermv, src);
     h->out_slots = (int64_t)so.idx.size();
     h->in_slots = (int64_t)si.idx.size();
-    h->out_edge.assign(so.edge.begin(), so.edge.end());
+    h->out_edge = so.edge;
     h->out_src.assign(h->out_slots, 0);
-    for (int64_t i = 0; i < n; ++i)
-        for (int32_t k = so.ptr[i]; k < so.ptr[i + 1]; ++k) h->out_src[k] = (int32_t)i;
-    // ---- iteration-invariant scalar block matrices (Appendix B, scalar Sigma) ----
-    std::vector<double> A2(n, h->prm.beta1 + h->prm.gamma[1]), A3(n, h->prm.beta2 + h->prm.gamma[2]),
-        A4(n, h->prm.beta2 + h->prm.gamma[3]);
-    for (int64_t e = 0; e < m; ++e) {
-        const double* tv = &h->te[3 * e];
-        const double tn2 = tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2];
-        A2[src[e]] += 2.0 * (om[e] * tn2 + ka[e]);  // |p_i| = |p_j| = |q_e| = 1
-        A3[dst[e]] += 2.0 * om[e];
-        A4[src[e]] += 2.0 * om[e];
-    }
+    parallel_for(n, [&](int64_t i0, int64_t i1) {
+        for (int64_t i = i0; i < i1; ++i)
+            for (int32_t k = so.ptr[i]; k < so.ptr[i + 1]; ++k) h->out_src[k] = (int32_t)i;
+    });
+    // ---- iteration-invariant scalar block matrices (Appendix B, scalar Sigma):
+    // per vertex over its CSR slots, which hold its edges in input order ----
     h->inv2.resize(n);
     h->inv3.resize(n);
     h->inv4.resize(n);
-    for (int64_t i = 0; i < n; ++i) {
-        const int32_t u = perm[i];
-        h->inv2[i] = 1.0 / A2[u];
-        h->inv3[i] = 1.0 / A3[u];
-        h->inv4[i] = 1.0 / A4[u];
-    }
+    parallel_for(n, [&](int64_t i0, int64_t i1) {
+        for (int64_t i = i0; i < i1; ++i) {
+            double A2 = h->prm.beta1 + h->prm.gamma[1], A3 = h->prm.beta2 + h->prm.gamma[2],
+                   A4 = h->prm.beta2 + h->prm.gamma[3];
+            for (int32_t k = so.ptr[i]; k < so.ptr[i + 1]; ++k) {
+                const int64_t e = so.edge[k];
+                const double* tv = &h->te[3 * e];
+                const double tn2 = tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2];
+                A2 += 2.0 * (om[e] * tn2 + ka[e]);  // |p_i| = |p_j| = |q_e| = 1
+                A4 += 2.0 * om[e];
+            }
+            for (int32_t k = si.ptr[i]; k < si.ptr[i + 1]; ++k) A3 += 2.0 * om[si.edge[k]];
+            h->inv2[i] = 1.0 / A2;
+            h->inv3[i] = 1.0 / A3;
+            h->inv4[i] = 1.0 / A4;
+        }
+    });
     // ---- device buffers ----
     ST(dalloc(h, &h->perm_d, n));
     ST(dalloc(h, &h->out_ptr, n + 1));
@@ -433,34 +511,59 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
         h->ctrl_h = static_cast<Ctrl*>(hp);
         std::memset(h->ctrl_h, 0, sizeof(Ctrl));
     }
-    // ---- uploads (synchronous with respect to the host buffers) ----
     CU(cudaMemcpy(h->perm_d, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
     CU(cudaMemcpy(h->out_ptr, so.ptr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(h->in_ptr, si.ptr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
     if (h->out_slots > 0) CU(cudaMemcpy(h->out_idx, so.idx.data(), sizeof(int32_t) * h->out_slots, cudaMemcpyHostToDevice));
     if (h->in_slots > 0) CU(cudaMemcpy(h->in_idx, si.idx.data(), sizeof(int32_t) * h->in_slots, cudaMemcpyHostToDevice));
-    if (h->fp64) {
-        ST(upload_slots<double>(h, so, ka, om, h->out_te, h->out_qk));
-        ST(upload_slots<double>(h, si, ka, om, h->in_te, h->in_qk));
-    } else {
-        ST(upload_slots<float>(h, so, ka, om, h->out_te, h->out_qk));
-        ST(upload_slots<float>(h, si, ka, om, h->in_te, h->in_qk));
-    }
-    if (h->out_slots > 0) {
-        const int64_t S = h->out_slots;
-        std::vector<double> b4(4 * S, 0.0), b3(3 * S, 0.0), b1k(S, 0.0), b1o(S, 0.0);
-        for (int64_t k = 0; k < S; ++k) {
-            const int64_t e = so.edge[k];
-            if (e < 0) continue;
-            for (int c = 0; c < 4; ++c) b4[4 * k + c] = h->qe[4 * e + c];
-            for (int c = 0; c < 3; ++c) b3[3 * k + c] = h->te[3 * e + c];
-            b1k[k] = ka[e];
-            b1o[k] = om[e];
+    // edge records: the caller's measurements go up once, the slots of both
+    // orders are packed on the device (pradmm_setup.cu)
+    if (m > 0) {
+        const size_t raw = (size_t)m * (4 + 3 + 2) * sizeof(double) + 2 * (size_t)m * sizeof(int32_t);
+        char* tmp = nullptr;
+        cudaError_t e = cudaMalloc(&tmp, raw);
+        if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? PRADMM_ERR_NOMEM : PRADMM_ERR_CUDA,
+                                          "set-up buffer of %zu bytes: %s", raw, cudaGetErrorString(e));
+        double* q_d = reinterpret_cast<double*>(tmp);
+        double* t_d = q_d + 4 * m;
+        double* k_d = t_d + 3 * m;
+        double* w_d = k_d + m;
+        int32_t* oe_d = reinterpret_cast<int32_t*>(w_d + m);
+        int32_t* ie_d = oe_d + m;
+        cudaStream_t st = h->stream;
+        pradmm_status ps = PRADMM_OK;
+        auto up = [&](void* d, const void* s, size_t bytes) {
+            if (ps == PRADMM_OK && (e = cudaMemcpyAsync(d, s, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                ps = fail(PRADMM_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
+        };
+        up(q_d, q_meas, sizeof(double) * 4 * m);
+        up(t_d, t_meas, sizeof(double) * 3 * m);
+        up(k_d, ka.data(), sizeof(double) * m);
+        up(w_d, om.data(), sizeof(double) * m);
+        up(oe_d, so.edge.data(), sizeof(int32_t) * m);
+        up(ie_d, si.edge.data(), sizeof(int32_t) * m);
+        if (ps == PRADMM_OK) {
+            e = h->fp64 ? pradmm::launch_pack_slots<double>(oe_d, m, q_d, t_d, k_d, w_d, static_cast<double*>(h->out_te),
+                                                            static_cast<double*>(h->out_qk), h->qe64, h->te64,
+                                                            h->ka64, h->om64, st)
+                        : pradmm::launch_pack_slots<float>(oe_d, m, q_d, t_d, k_d, w_d, static_cast<float*>(h->out_te),
+                                                           static_cast<float*>(h->out_qk), h->qe64, h->te64,
+                                                           h->ka64, h->om64, st);
+            if (e == cudaSuccess)
+                e = h->fp64 ? pradmm::launch_pack_slots<double>(ie_d, m, q_d, t_d, k_d, w_d,
+                                                                static_cast<double*>(h->in_te),
+                                                                static_cast<double*>(h->in_qk), nullptr, nullptr,
+                                                                nullptr, nullptr, st)
+                            : pradmm::launch_pack_slots<float>(ie_d, m, q_d, t_d, k_d, w_d,
+                                                               static_cast<float*>(h->in_te),
+                                                               static_cast<float*>(h->in_qk), nullptr, nullptr,
+                                                               nullptr, nullptr, st);
+            if (e != cudaSuccess) ps = fail(PRADMM_ERR_CUDA, "edge record packing: %s", cudaGetErrorString(e));
         }
-        CU(cudaMemcpy(h->qe64, b4.data(), sizeof(double) * 4 * S, cudaMemcpyHostToDevice));
-        CU(cudaMemcpy(h->te64, b3.data(), sizeof(double) * 3 * S, cudaMemcpyHostToDevice));
-        CU(cudaMemcpy(h->ka64, b1k.data(), sizeof(double) * S, cudaMemcpyHostToDevice));
-        CU(cudaMemcpy(h->om64, b1o.data(), sizeof(double) * S, cudaMemcpyHostToDevice));
+        e = cudaStreamSynchronize(st);
+        if (ps == PRADMM_OK && e != cudaSuccess) ps = fail(PRADMM_ERR_CUDA, "set-up: %s", cudaGetErrorString(e));
+        cudaFree(tmp);
+        if (ps != PRADMM_OK) return ps;
     }
     CU(cudaMemcpy(h->inv2_d, h->inv2.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
     CU(cudaMemcpy(h->inv3_d, h->inv3.data(), sizeof(double) * n, cudaMemcpyHostToDevice));

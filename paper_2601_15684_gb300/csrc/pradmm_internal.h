@@ -130,6 +130,16 @@ cudaError_t launch_objective(const GraphDev<R>& g, const StateDev<R>& s, const d
 // Layout conversion between caller arrays (double, user vertex order, n x 4 /
 // n x 3) and the padded internal arrays: internal vertex i is user vertex
 // perm[i]; `inv` (internal order) supplies the padding of a 3-vector.
+// Per-slot edge records of one CSR order (slot k holds input edge edge[k]),
+// packed from the caller's measurements in device memory: te_out (t_e,
+// omega_e) and qk_out kappa_e q_e/|q_e| in R; for the out order also the FP64
+// copies qe64 (normalised), te64, ka64, om64 (NULL for the in order).  ka, om
+// NULL mean all ones.  Asynchronous on st.
+template <typename R>
+cudaError_t launch_pack_slots(const int32_t* edge, int64_t slots, const double* q, const double* t, const double* ka,
+                              const double* om, R* te_out, R* qk_out, double* qe64, double* te64, double* ka64,
+                              double* om64, cudaStream_t st);
+
 template <typename R>
 cudaError_t launch_pack4(const double* src, const int32_t* perm, R* dst, int64_t n, cudaStream_t st);
 template <typename R>
