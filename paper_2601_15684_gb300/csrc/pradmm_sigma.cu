@@ -166,23 +166,26 @@ __device__ __forceinline__ void jacobi_rotate(T a[4][4], T v[4][4], int p, int q
         cs = T(1) / sqrt(t * t + T(1));
     }
     const T sn = t * cs;
+    // the rotation zeroes a[p][q]: the diagonal pair moves by t a[p][q], and
+    // only rows / columns p and q change elsewhere (tau = sn / (1 + cs))
+    T tau;
+    if constexpr (sizeof(T) == sizeof(float) && PRADMM_FAST_ROT) tau = __fdividef(sn, 1.0f + cs);
+    else tau = sn / (T(1) + cs);
+    a[p][p] -= t * apq;
+    a[q][q] += t * apq;
+    a[p][q] = a[q][p] = T(0);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const T kp = a[k][p], kq = a[k][q];
-        a[k][p] = cs * kp - sn * kq;
-        a[k][q] = sn * kp + cs * kq;
+    for (int r = 0; r < 4; ++r) {
+        if (r == p || r == q) continue;
+        const T arp = a[r][p], arq = a[r][q];
+        a[r][p] = a[p][r] = arp - sn * (arq + tau * arp);
+        a[r][q] = a[q][r] = arq + sn * (arp - tau * arq);
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const T pk = a[p][k], qk = a[q][k];
-        a[p][k] = cs * pk - sn * qk;
-        a[q][k] = sn * pk + cs * qk;
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const T kp = v[k][p], kq = v[k][q];
-        v[k][p] = cs * kp - sn * kq;
-        v[k][q] = sn * kp + cs * kq;
+    for (int r = 0; r < 4; ++r) {
+        const T vrp = v[r][p], vrq = v[r][q];
+        v[r][p] = vrp - sn * (vrq + tau * vrp);
+        v[r][q] = vrq + sn * (vrp - tau * vrq);
     }
 }
 
