@@ -20,8 +20,10 @@
 // The 32 vertices of a warp are consecutive, so their edge ranges form one
 // dense block of 16-byte records that L1 serves across the loop steps; each
 // step issues two edges' loads and neighbour gathers before using any of
-// them, and edge records are streamed with evict-first loads so the gathered
-// vertex arrays stay resident in L2.
+// them.  Edge records and neighbour gathers go through the read-only path
+// with normal caching (the records are invariant and no plain sweep writes
+// an array it gathers); the gathered vertex arrays stay in L2 through the
+// launches' access-policy window.
 // Residual partials are per-thread compensated FP32 sums (FP32 has the
 // throughput; FP64 on this part does not), then a fixed-order FP64 tree across
 // threads and CTAs.
