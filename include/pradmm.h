@@ -347,6 +347,14 @@ pradmm_status pradmm_batch_solve(pradmm_batch_t b, double rel_tol, int32_t max_i
 /* F of Eq. (1) of each graph at its (p, t), double precision: F has G entries. */
 pradmm_status pradmm_batch_objectives(pradmm_batch_t b, double* F);
 
+/* Tracing: for each graph g of the last pradmm_batch_solve (or autotune
+ * trial), the device time at which the work item that solves g started and
+ * finished, in nanoseconds of the GPU's global timer (the same clock for all
+ * graphs of one solve; differences are durations).  spans is 2 G uint64,
+ * (start, end) per graph, host memory.  The paper has no counterpart: it is
+ * for finding the graphs on a batch's critical path. */
+pradmm_status pradmm_batch_spans(pradmm_batch_t b, uint64_t* spans);
+
 /* State of all graphs (N rows each, graph order); any pointer may be NULL. */
 pradmm_status pradmm_batch_get_state(pradmm_batch_t b, double* p, double* q, double* t, double* s,
                                      double* lam, double* z);

@@ -2062,6 +2062,15 @@ pradmm_status pradmm_batch_objectives(pradmm_batch_t b, double* F) {
     return PRADMM_OK;
 }
 
+pradmm_status pradmm_batch_spans(pradmm_batch_t b, uint64_t* spans) {
+    if (!b || !spans) return fail(PRADMM_ERR_ARG, "NULL argument");
+    pradmm_s* h = b->h;
+    static_assert(sizeof(unsigned long long) == sizeof(uint64_t), "64-bit timer words");
+    CU(cudaMemcpyAsync(spans, b->t_span_d, sizeof(uint64_t) * 2 * (size_t)b->G, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return PRADMM_OK;
+}
+
 pradmm_status pradmm_batch_get_state(pradmm_batch_t b, double* p, double* q, double* t, double* s, double* lam,
                                      double* z) {
     if (!b) return fail(PRADMM_ERR_ARG, "NULL handle");

@@ -93,6 +93,7 @@ _SIGS = {
     "pradmm_batch_set_state": (ctypes.c_int, [_h, _d, _d]),
     "pradmm_batch_solve": (ctypes.c_int, [_h, ctypes.c_double, ctypes.c_int32, _i32, _d, _d, _i32]),
     "pradmm_batch_objectives": (ctypes.c_int, [_h, _d]),
+    "pradmm_batch_spans": (ctypes.c_int, [_h, ctypes.POINTER(ctypes.c_uint64)]),
     "pradmm_batch_get_state": (ctypes.c_int, [_h, _d, _d, _d, _d, _d, _d]),
     "pradmm_batch_destroy": (None, [_h]),
     "pradmm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -506,6 +507,13 @@ class Batch:
         F = np.zeros(self.G)
         _check(load().pradmm_batch_objectives(self.h, _dp(F)), "pradmm_batch_objectives")
         return F
+
+    def spans(self):
+        """(G, 2) uint64: device start / end time (ns) of each graph in the last solve."""
+        out = np.zeros((self.G, 2), dtype=np.uint64)
+        _check(load().pradmm_batch_spans(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))),
+               "pradmm_batch_spans")
+        return out
 
     def state(self):
         N = self.N

@@ -11,6 +11,8 @@
   convergence;
 - the autotuner keeps a valid schedule and leaves the state untouched.
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -179,6 +181,28 @@ def test_batch_autotune_keeps_state(P):
         after = B.state()
         for key in KEYS:
             np.testing.assert_array_equal(after[key], before[key])
+
+
+def test_batch_spans_trace_every_graph(P):
+    # per-graph device start / end times of the last solve: every graph was
+    # traced, ends after it starts, within the solve's wall time, and a graph
+    # run for more iterations of the same size takes longer
+    graphs = _graphs(16, seed=11, n_max=2500)
+    with P.Batch(graphs, precision=1) as B:
+        B.init_odometry()
+        B.set_schedule(256, 0, 1, 0)  # one CTA per graph: durations comparable
+        t0 = time.perf_counter()
+        res = B.solve(rel_tol=0.0, max_iter=40)
+        wall_ns = (time.perf_counter() - t0) * 1e9
+        sp = B.spans().astype(np.int64)
+    assert sp.shape == (len(graphs), 2)
+    assert (sp[:, 0] > 0).all() and (sp[:, 1] > sp[:, 0]).all()
+    assert sp[:, 1].max() - sp[:, 0].min() <= wall_ns
+    assert (res["iters"] == 40).all()
+    dur = sp[:, 1] - sp[:, 0]
+    big = int(np.argmax([g.m for g in graphs]))
+    small = int(np.argmin([g.m for g in graphs]))
+    assert dur[big] > dur[small]
 
 
 @pytest.mark.parametrize("precision", [0, 1])
