@@ -332,6 +332,21 @@ pradmm_status pradmm_batch_get_schedule(pradmm_batch_t b, int32_t* block, int32_
 pradmm_status pradmm_batch_autotune(pradmm_batch_t b, int32_t iters, int32_t* block_out,
                                     int32_t* warp_max_n_out, int32_t* cluster_out, int32_t* cluster_min_n_out);
 
+/* Schedule search with the iteration profile of the last pradmm_batch_solve
+ * (PRADMM_ERR_STATE if there is none): every candidate is timed on a probe in
+ * which graph g runs ceil(work_fraction x its iterations in that solve)
+ * iterations from the current state, so the probe has the solve's mix of work
+ * (a fixed-iteration probe weighs the small graphs far above their share) and
+ * its time is the score.  Candidates: block 128/256/512 x warp_max_n
+ * 0/64/256/1024 without clusters, then at 256 and 512 threads (with the best
+ * warp_max_n of that size) clusters of 2/4/8 above 2048/4096/8192 vertices.
+ * work_fraction in (0, 1].  Keeps the best schedule and restores the state;
+ * the per-graph outputs of the profiled solve are overwritten by the probes.
+ * Outputs are nullable.  The paper has no counterpart. */
+pradmm_status pradmm_batch_autotune_profiled(pradmm_batch_t b, double work_fraction, int32_t* block_out,
+                                             int32_t* warp_max_n_out, int32_t* cluster_out,
+                                             int32_t* cluster_min_n_out);
+
 /* Initial states, all graphs at once (q: N x 4, t: N x 3 with N = sum n_g, in
  * graph order): odometry composition per graph, or given poses. */
 pradmm_status pradmm_batch_init_odometry(pradmm_batch_t b);

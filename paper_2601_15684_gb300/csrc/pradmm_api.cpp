@@ -12,6 +12,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <limits>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -1801,6 +1802,9 @@ struct pradmm_batch_s {
     int n_big = 0;          // cluster items
     int* next_big_d = nullptr;
     int grid = 1;
+    bool solved = false;               // iters_d holds the per-graph iterations of a solve
+    int32_t* cap_d = nullptr;          // G per-graph iteration limits of a profiled autotune
+    bool use_cap = false;
 };
 
 namespace {
@@ -1882,6 +1886,7 @@ pradmm::BatchDev batch_dev(const pradmm_batch_s* b, double rel_tol, double abs_t
     d.rel_tol = rel_tol;
     d.abs_tol = abs_tol;
     d.max_iter = max_iter;
+    d.iter_cap = b->use_cap ? b->cap_d : nullptr;
     return d;
 }
 
@@ -2027,7 +2032,9 @@ pradmm_status pradmm_batch_solve(pradmm_batch_t b, double rel_tol, int32_t max_i
                                  double* e_last, int32_t* status) {
     if (!b) return fail(PRADMM_ERR_ARG, "NULL handle");
     if (!(rel_tol >= 0) || max_iter < 0) return fail(PRADMM_ERR_ARG, "need rel_tol >= 0 and max_iter >= 0");
+    b->solved = false;
     ST(batch_run_any(b, rel_tol, 0.0, max_iter));
+    b->solved = true;
     const size_t G = (size_t)b->G;
     std::vector<int32_t> st(G);
     cudaStream_t s = b->h->stream;
@@ -2075,6 +2082,96 @@ pradmm_status pradmm_batch_get_state(pradmm_batch_t b, double* p, double* q, dou
                                      double* z) {
     if (!b) return fail(PRADMM_ERR_ARG, "NULL handle");
     return pradmm_get_state(b->h, p, q, t, s, lam, z);
+}
+
+pradmm_status pradmm_batch_autotune_profiled(pradmm_batch_t b, double work_fraction, int32_t* block_out,
+                                             int32_t* warp_max_n_out, int32_t* cluster_out,
+                                             int32_t* cluster_min_n_out) {
+    if (!b) return fail(PRADMM_ERR_ARG, "NULL handle");
+    if (!(work_fraction > 0 && work_fraction <= 1)) return fail(PRADMM_ERR_ARG, "work_fraction must lie in (0, 1]");
+    if (!b->solved) return fail(PRADMM_ERR_STATE, "no solve to take the iteration profile from (pradmm_batch_solve)");
+    pradmm_s* h = b->h;
+    if (!h->state_set) return fail(PRADMM_ERR_STATE, "batch state is not set");
+    const int64_t n = h->n;
+    const size_t G = (size_t)b->G;
+    // each graph's probe length: its share of the profiled solve
+    std::vector<int32_t> cap(G);
+    CU(cudaMemcpy(cap.data(), b->iters_d, sizeof(int32_t) * G, cudaMemcpyDeviceToHost));
+    for (auto& c : cap) c = std::max<int32_t>(1, (int32_t)std::ceil(work_fraction * c));
+    if (!b->cap_d) ST(dalloc(h, &b->cap_d, G));
+    CU(cudaMemcpy(b->cap_d, cap.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice));
+    if (!b->save_d) ST(dalloc(h, &b->save_d, 24 * n));
+    double* sv = b->save_d;
+    ST(h->fp64 ? get_state_impl<double>(h, sv, sv + 4 * n, sv + 8 * n, sv + 11 * n, sv + 14 * n, sv + 18 * n, true)
+               : get_state_impl<float>(h, sv, sv + 4 * n, sv + 8 * n, sv + 11 * n, sv + 14 * n, sv + 18 * n, true));
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best = std::numeric_limits<float>::infinity();
+    int best_s[4] = {b->block, b->warp_max_n, b->cluster, b->cluster_min_n};
+    pradmm_status st = PRADMM_OK;
+    float last = best;
+    // Score = the probe's time.  Every graph runs the same fraction of its own
+    // iterations, so the probe has the solve's work mix and, scaled, its
+    // makespan: no separate critical-path term.
+    auto trial = [&](int blk, int wn, int cl, int cmin) {
+        last = std::numeric_limits<float>::infinity();
+        if (st != PRADMM_OK) return;
+        pradmm_status ts = batch_schedule(b, blk, wn, cl, cmin);
+        if (ts == PRADMM_ERR_ARG) return;  // a cluster shape that does not fit: skip it
+        st = ts;
+        if (st != PRADMM_OK) return;
+        st = set_state_any(h, sv, sv + 4 * n, sv + 8 * n, sv + 11 * n, sv + 14 * n, sv + 18 * n, true);
+        if (st != PRADMM_OK) return;
+        b->use_cap = true;
+        cudaEventRecord(e0, h->stream);
+        st = batch_run_any(b, 0.0, 0.0, 0);  // the per-graph limits stop every graph
+        cudaEventRecord(e1, h->stream);
+        cudaEventSynchronize(e1);
+        b->use_cap = false;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        last = ms;
+        if (st == PRADMM_OK && ms < best) {
+            best = ms;
+            best_s[0] = blk;
+            best_s[1] = wn;
+            best_s[2] = cl;
+            best_s[3] = cmin;
+        }
+    };
+    // stage 1: CTA size x warp-pack limit, no clusters (best limit per CTA size kept)
+    const int blocks[3] = {128, 256, 512};
+    const int warp_ns[4] = {0, 64, 256, 1024};
+    int best_w[3] = {256, 256, 256};
+    for (int bi = 0; bi < 3; ++bi) {
+        float here = std::numeric_limits<float>::infinity();
+        for (int wi = 0; wi < 4; ++wi) {
+            trial(blocks[bi], warp_ns[wi], 1, 0);
+            if (last < here) {
+                here = last;
+                best_w[bi] = warp_ns[wi];
+            }
+        }
+    }
+    // stage 2: clusters for the large graphs at 256 and 512 threads per CTA
+    const int cl_sizes[3] = {2, 4, 8};
+    const int cl_min[3] = {2048, 4096, 8192};
+    for (int bi = 1; bi < 3; ++bi)
+        for (int ci = 0; ci < 3; ++ci)
+            for (int mi = 0; mi < 3; ++mi) trial(blocks[bi], best_w[bi], cl_sizes[ci], cl_min[mi]);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->use_cap = false;
+    b->solved = false;  // the probes overwrote the per-graph outputs
+    if (st == PRADMM_OK) st = batch_schedule(b, best_s[0], best_s[1], best_s[2], best_s[3]);
+    if (st == PRADMM_OK) st = set_state_any(h, sv, sv + 4 * n, sv + 8 * n, sv + 11 * n, sv + 14 * n, sv + 18 * n, true);
+    if (st != PRADMM_OK) return st;
+    if (block_out) *block_out = best_s[0];
+    if (warp_max_n_out) *warp_max_n_out = best_s[1];
+    if (cluster_out) *cluster_out = best_s[2];
+    if (cluster_min_n_out) *cluster_min_n_out = best_s[3];
+    return PRADMM_OK;
 }
 
 pradmm_status pradmm_batch_autotune(pradmm_batch_t b, int32_t iters, int32_t* block_out, int32_t* warp_max_n_out,

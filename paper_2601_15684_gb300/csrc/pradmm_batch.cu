@@ -117,7 +117,8 @@ __device__ void solve_graph(const G& grp, const GraphDev<R>& g, const StateDev<R
     grp.sync();
     int k = 0, status = PRADMM_BATCH_MAXITER;
     double e1 = 0.0, e = 0.0;
-    while (k < b.max_iter) {
+    const int cap = b.iter_cap ? b.iter_cap[gid] : b.max_iter;
+    while (k < cap) {
         const R* pcur = S.p[(k + 1) & 1];  // p^{k+1}
         Acc<R> adq, adl, adt, adz;
         for (int64_t i = v0 + r; i < v1; i += nt) q_vertex<R>(g, S, c, pcur, i, adq, adl);

@@ -222,6 +222,7 @@ struct BatchDev {
     unsigned long long* t_span;  // 2 G: device clock (ns) at each graph's start and end
     double rel_tol, abs_tol;
     int max_iter;
+    const int32_t* iter_cap = nullptr;  // G per-graph iteration limits (NULL: max_iter for all)
 };
 
 // cluster > 1: the cluster kernel (grid a multiple of cluster); 1: k_batch.

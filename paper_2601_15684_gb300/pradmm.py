@@ -89,6 +89,7 @@ _SIGS = {
                                                  ctypes.c_int32]),
     "pradmm_batch_get_schedule": (ctypes.c_int, [_h, _i32, _i32, _i32, _i32]),
     "pradmm_batch_autotune": (ctypes.c_int, [_h, ctypes.c_int32, _i32, _i32, _i32, _i32]),
+    "pradmm_batch_autotune_profiled": (ctypes.c_int, [_h, ctypes.c_double, _i32, _i32, _i32, _i32]),
     "pradmm_batch_init_odometry": (ctypes.c_int, [_h]),
     "pradmm_batch_set_state": (ctypes.c_int, [_h, _d, _d]),
     "pradmm_batch_solve": (ctypes.c_int, [_h, ctypes.c_double, ctypes.c_int32, _i32, _d, _d, _i32]),
@@ -482,6 +483,14 @@ class Batch:
         v = [ctypes.c_int32(0) for _ in range(4)]
         _check(load().pradmm_batch_autotune(self.h, int(iters), *[ctypes.byref(x) for x in v]),
                "pradmm_batch_autotune")
+        return tuple(x.value for x in v)
+
+    def autotune_profiled(self, work_fraction=0.05):
+        """Schedule search on probes that run each graph for work_fraction of its
+        iterations in the last solve; returns (block, warp_max_n, cluster, cluster_min_n)."""
+        v = [ctypes.c_int32(0) for _ in range(4)]
+        _check(load().pradmm_batch_autotune_profiled(self.h, float(work_fraction), *[ctypes.byref(x) for x in v]),
+               "pradmm_batch_autotune_profiled")
         return tuple(x.value for x in v)
 
     def init_odometry(self):

@@ -183,6 +183,33 @@ def test_batch_autotune_keeps_state(P):
             np.testing.assert_array_equal(after[key], before[key])
 
 
+def test_batch_profiled_autotune(P):
+    # needs a solve for its profile; keeps the state; the chosen schedule is a
+    # candidate of the search and solves the batch as the oracle-pinned path does
+    graphs = _graphs(24, seed=13, n_max=3000)
+    with P.Batch(graphs, precision=1) as B:
+        B.init_odometry()
+        with pytest.raises(P.PRADMMError) as ei:
+            B.autotune_profiled(0.1)
+        assert ei.value.status == P.PRADMM_ERR_STATE
+        res0 = B.solve(rel_tol=1e-4, max_iter=200)
+        B.init_odometry()
+        before = B.state()
+        block, wmax, cl, cmin = B.autotune_profiled(0.2)
+        assert block in (128, 256, 512) and wmax in (0, 64, 256, 1024)
+        assert (cl, cmin) == (1, 0) or (cl in (2, 4, 8) and cmin in (2048, 4096, 8192) and block in (256, 512))
+        assert B.schedule() == (block, wmax, cl, cmin)
+        after = B.state()
+        for key in KEYS:
+            np.testing.assert_array_equal(after[key], before[key])
+        with pytest.raises(P.PRADMMError):
+            B.autotune_profiled(0.0)
+        res1 = B.solve(rel_tol=1e-4, max_iter=200)
+    # same stopping rule, another schedule: the same iteration counts up to
+    # rounding-order differences near the threshold
+    assert np.abs(res1["iters"] - res0["iters"]).max() <= 2
+
+
 def test_batch_spans_trace_every_graph(P):
     # per-graph device start / end times of the last solve: every graph was
     # traced, ends after it starts, within the solve's wall time, and a graph
