@@ -280,6 +280,30 @@ def test_input_errors(P):
         P.pradmm_destroy(h)
 
 
+def test_input_errors_in_a_large_edge_list_name_the_first_bad_edge(P):
+    # above ~32k edges validation runs on several host threads; the error must
+    # still be the first invalid edge in input order, with its own message
+    g = synth.random_graph(50000, 200000, seed=8)
+    cases = [
+        ("dst", {170000: 50000, 150001: -1}, P.PRADMM_ERR_INDEX, "edge 150001"),
+        ("dst", {199999: -3, 120000: "self"}, P.PRADMM_ERR_SELFLOOP, "edge 120000"),
+    ]
+    for field, bad, code, text in cases:
+        dst = g.dst.copy()
+        for e, v in bad.items():
+            dst[e] = g.src[e] if v == "self" else v
+        with pytest.raises(P.PRADMMError) as ei:
+            P.pradmm_create(g.n, g.src, dst, g.q_meas, g.t_meas)
+        assert ei.value.status == code
+        assert text in str(ei.value), str(ei.value)
+    qm = g.q_meas.copy()
+    qm[180000] *= 1.5
+    qm[160000, 2] = np.nan
+    with pytest.raises(P.PRADMMError) as ei:
+        P.pradmm_create(g.n, g.src, g.dst, qm, g.t_meas)
+    assert ei.value.status == P.PRADMM_ERR_NONFINITE and "edge 160000" in str(ei.value)
+
+
 def test_nonfinite_state_is_reported(P):
     g = synth.random_graph(50, 120, seed=6)
     st = synth.random_state(np.random.default_rng(6), g.n)
