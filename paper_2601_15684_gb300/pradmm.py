@@ -108,7 +108,8 @@ def load(path: str = LIB_PATH):
     with _lock:
         if _lib is None:
             if not os.path.exists(path):
-                raise RuntimeError(f"libpradmm.so not built at {path}; build it with paper_2601_15684_gb300.build_lib.build()")
+                raise RuntimeError(f"libpradmm.so not built at {path}; "
+                                   "build it with paper_2601_15684_gb300.build_lib.build()")
             lib = ctypes.CDLL(path)
             for name, (res, args) in _SIGS.items():
                 fn = getattr(lib, name)
