@@ -53,6 +53,9 @@ def lib():
             d, i32, i64 = P(ctypes.c_double), P(ctypes.c_int32), ctypes.c_int64
             L.orc_iterate.restype = ctypes.c_int64
             L.orc_iterate.argtypes = [i64, i64, i32, i32, d, d, d, d, P(Params), d, d, d, d, d, d, d]
+            L.orc_iterate_inertial.restype = ctypes.c_int64
+            L.orc_iterate_inertial.argtypes = [i64, i64, i32, i32, d, d, d, d, P(Params), ctypes.c_double,
+                                               d, d, d, d, d, d, d, d, d, d, d]
             L.orc_solve.restype = ctypes.c_int64
             L.orc_solve.argtypes = [i64, i64, i32, i32, d, d, d, d, P(Params), i64, ctypes.c_double,
                                     d, d, d, d, d, d, d, d]
@@ -143,6 +146,26 @@ def iterate(g, params: Params, state: dict, iters: int = 1):
             raise MemoryError("oracle iterate")
         nz += int(r)
     return st, res.copy(), nz
+
+
+def iterate_inertial(g, params: Params, state: dict, theta: float, iters: int = 1, prev: dict | None = None):
+    """Inertial PRADMM (reading R27): `iters` iterations whose proximal anchors
+    are x^k + theta (x^k - x^{k-1}) for x = p, q, t, s.  `prev` holds x^{k-1}
+    (p, q, t, s); None means x^{-1} = x^0.  Returns (new_state, new_prev,
+    residual parts of the last iteration, zero-|u| count)."""
+    st = copy_state(state)
+    pv = {k: st[k].copy() for k in ("p", "q", "t", "s")} if prev is None else copy_state(prev)
+    keep, a = _graph_args(g)
+    res = np.zeros(5)
+    nz = 0
+    for _ in range(iters):
+        r = lib().orc_iterate_inertial(*a, ctypes.byref(params), float(theta), _d(st["p"]), _d(st["q"]),
+                                       _d(st["t"]), _d(st["s"]), _d(st["lam"]), _d(st["z"]), _d(pv["p"]),
+                                       _d(pv["q"]), _d(pv["t"]), _d(pv["s"]), _d(res))
+        if r < 0:
+            raise MemoryError("oracle iterate_inertial")
+        nz += int(r)
+    return st, pv, res.copy(), nz
 
 
 def solve(g, params: Params, state: dict, max_iter: int, tol: float):

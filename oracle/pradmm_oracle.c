@@ -26,7 +26,9 @@
  *       form drops D); in product form its transpose times 1~ is q_l q_li.
  *   R2  x = A^{-1} b with b as printed for the q, t, s blocks; p = -b1/|b1|.
  *   R3  c_e = Im(q_tail t~_e p_tail^*) for e = (tail, head).
- *   R4  proximal anchors x^{k+1/2} are read as x^k.
+ *   R4  proximal anchors x^{k+1/2} are read as x^k (plain PRADMM).
+ *   R27 the inertial variant (named once, rule not given) extrapolates the
+ *       anchors: x^{k+1/2} = x^k + theta (x^k - x^{k-1}) for p, q, t, s.
  *   R5  z lives in R^{3n}.
  *   R6  e^{k+1} uses beta1 for the lambda / q terms and beta2 for z / t.
  *   R8  lambda^0 = z^0 = 0, p^0 = q^0, s^0 = t^0 (set by the caller).
@@ -266,10 +268,11 @@ double orc_lagrangian(int64_t n, int64_t m, const int32_t* src, const int32_t* d
  * then |dlam|^2, |dz|^2, |dq|^2, |dt|^2.
  * Returns the number of vertices whose p-block hit |u_i| == 0 (R11).
  */
-int64_t orc_iterate(int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
-                    const double* qe, const double* te, const double* kappa,
-                    const double* omega, const orc_params* prm, double* p, double* q,
-                    double* t, double* s, double* lam, double* z, double* res_out) {
+static int64_t iterate_anchored(int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                                const double* qe, const double* te, const double* kappa,
+                                const double* omega, const orc_params* prm, double* p, double* q,
+                                double* t, double* s, double* lam, double* z, const double* ap,
+                                const double* aq, const double* at, const double* as, double* res_out) {
     const double b1 = prm->beta1, b2 = prm->beta2, tau = prm->tau;
     const double g1 = prm->gamma[0], g2 = prm->gamma[1], g3 = prm->gamma[2], g4 = prm->gamma[3];
     double* u = (double*)calloc((size_t)(4 * n + 1), sizeof(double));
@@ -303,7 +306,7 @@ int64_t orc_iterate(int64_t n, int64_t m, const int32_t* src, const int32_t* dst
      * r_e = t~_j - s~_i.                                                    */
     for (int64_t i = 0; i < n; ++i)
         for (int k = 0; k < 4; ++k)
-            u[4 * i + k] = b1 * q[4 * i + k] + lam[4 * i + k] + g1 * p[4 * i + k];
+            u[4 * i + k] = b1 * q[4 * i + k] + lam[4 * i + k] + g1 * ap[4 * i + k];
     for (int64_t e = 0; e < m; ++e) { /* out-edge sums: e = (i, j) */
         int64_t i = src[e], j = dst[e];
         double r[4], rc[4], tp[4], a[4], v[4];
@@ -339,7 +342,7 @@ int64_t orc_iterate(int64_t n, int64_t m, const int32_t* src, const int32_t* dst
      * G4^T 1~ = p_j q_e^*     (G4 = W(q_e) M(p_j)^T).                        */
     for (int64_t i = 0; i < n; ++i) {
         a2[i] = b1 + g2;
-        for (int k = 0; k < 4; ++k) qn[4 * i + k] = b1 * p[4 * i + k] - lam[4 * i + k] + g2 * q[4 * i + k];
+        for (int k = 0; k < 4; ++k) qn[4 * i + k] = b1 * p[4 * i + k] - lam[4 * i + k] + g2 * aq[4 * i + k];
     }
     for (int64_t e = 0; e < m; ++e) {
         int64_t i = src[e], j = dst[e];
@@ -376,7 +379,7 @@ int64_t orc_iterate(int64_t n, int64_t m, const int32_t* src, const int32_t* dst
      *   t_i = [sum_{in} 2 w_e (s_l + c_e) + b2 s_i + z_i + g3 t_i] / [sum_{in} 2 w_e + b2 + g3] */
     for (int64_t i = 0; i < n; ++i) {
         a3[i] = b2 + g3;
-        for (int k = 0; k < 3; ++k) tn[3 * i + k] = b2 * s[3 * i + k] + z[3 * i + k] + g3 * t[3 * i + k];
+        for (int k = 0; k < 3; ++k) tn[3 * i + k] = b2 * s[3 * i + k] + z[3 * i + k] + g3 * at[3 * i + k];
     }
     for (int64_t e = 0; e < m; ++e) {
         int64_t l = src[e], i = dst[e];
@@ -391,7 +394,7 @@ int64_t orc_iterate(int64_t n, int64_t m, const int32_t* src, const int32_t* dst
      *   s_i = [sum_{out} 2 w_e (t_j - c_e) + b2 t_i - z_i + g4 s_i] / [sum_{out} 2 w_e + b2 + g4] */
     for (int64_t i = 0; i < n; ++i) {
         a4[i] = b2 + g4;
-        for (int k = 0; k < 3; ++k) sn[3 * i + k] = b2 * t[3 * i + k] - z[3 * i + k] + g4 * s[3 * i + k];
+        for (int k = 0; k < 3; ++k) sn[3 * i + k] = b2 * t[3 * i + k] - z[3 * i + k] + g4 * as[3 * i + k];
     }
     for (int64_t e = 0; e < m; ++e) {
         int64_t i = src[e], j = dst[e];
@@ -428,6 +431,52 @@ out:
     free(u); free(qn); free(a2); free(tn); free(a3); free(sn); free(a4); free(c);
     free(qold); free(told); free(lold); free(zold);
     return nzero;
+}
+
+/* The proximal anchors of the four primal blocks (the points the terms
+ * 1/2 |x - x^{k+1/2}|^2_{H} of Appendix B pull towards) are ap, aq, at, as;
+ * every term that reads them does so before its block overwrites the iterate,
+ * so passing the iterate itself gives the anchors x^{k+1/2} = x^k (reading
+ * R4) of plain PRADMM. */
+int64_t orc_iterate(int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                    const double* qe, const double* te, const double* kappa,
+                    const double* omega, const orc_params* prm, double* p, double* q,
+                    double* t, double* s, double* lam, double* z, double* res_out) {
+    return iterate_anchored(n, m, src, dst, qe, te, kappa, omega, prm, p, q, t, s, lam, z, p, q, t, s, res_out);
+}
+
+/* Inertial PRADMM (reading R27): the anchors are the extrapolated points
+ *   x^{k+1/2} = x^k + theta (x^k - x^{k-1})     for x = p, q, t, s,
+ * with x^{k-1} in pp, qp, tp, sp (equal to x^0 before the first iteration);
+ * theta = 0 is plain PRADMM.  On return pp .. sp hold x^k, the previous
+ * iterate of the next call.  Returns as orc_iterate, or -1 if out of memory. */
+int64_t orc_iterate_inertial(int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                             const double* qe, const double* te, const double* kappa,
+                             const double* omega, const orc_params* prm, double theta, double* p,
+                             double* q, double* t, double* s, double* lam, double* z, double* pp,
+                             double* qp, double* tp, double* sp, double* res_out) {
+    double* ap = (double*)malloc(sizeof(double) * (size_t)(4 * n + 1));
+    double* aq = (double*)malloc(sizeof(double) * (size_t)(4 * n + 1));
+    double* at = (double*)malloc(sizeof(double) * (size_t)(3 * n + 1));
+    double* as = (double*)malloc(sizeof(double) * (size_t)(3 * n + 1));
+    int64_t r = -1;
+    if (ap && aq && at && as) {
+        for (int64_t k = 0; k < 4 * n; ++k) {
+            ap[k] = p[k] + theta * (p[k] - pp[k]);
+            aq[k] = q[k] + theta * (q[k] - qp[k]);
+        }
+        for (int64_t k = 0; k < 3 * n; ++k) {
+            at[k] = t[k] + theta * (t[k] - tp[k]);
+            as[k] = s[k] + theta * (s[k] - sp[k]);
+        }
+        memcpy(pp, p, sizeof(double) * (size_t)(4 * n));
+        memcpy(qp, q, sizeof(double) * (size_t)(4 * n));
+        memcpy(tp, t, sizeof(double) * (size_t)(3 * n));
+        memcpy(sp, s, sizeof(double) * (size_t)(3 * n));
+        r = iterate_anchored(n, m, src, dst, qe, te, kappa, omega, prm, p, q, t, s, lam, z, ap, aq, at, as, res_out);
+    }
+    free(ap); free(aq); free(at); free(as);
+    return r;
 }
 
 /* Algorithm 1 with the stopping rule of Appendix E.1: iterate until

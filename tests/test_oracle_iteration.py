@@ -330,3 +330,69 @@ def test_odometry_init_forest_roots():
         rel = synth._qmul(synth._qconj(q[i]), q[j])
         assert min(np.abs(rel - qm[e]).max(), np.abs(rel + qm[e]).max()) < 1e-12
         np.testing.assert_allclose(synth._rotate(synth._qconj(q[i]), t[j] - t[i]), tm[e], atol=1e-12)
+
+
+# ---- inertial variant (reading R27: anchors x^k + theta (x^k - x^{k-1})) ------
+
+THETA = 0.45
+
+
+def _prev(g, seed):
+    pv = synth.random_state(np.random.default_rng(seed), g.n)
+    return {k: pv[k] for k in ("p", "q", "t", "s")}
+
+
+def test_inertial_with_zero_theta_is_plain():
+    g = synth.random_graph(20, 70, seed=3, isolated=1)
+    st = _state(g, 3)
+    a, res_a, _ = oracle.iterate(g, P(), st, 4)
+    b, _, res_b, _ = oracle.iterate_inertial(g, P(), st, 0.0, 4, _prev(g, 4))
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k])
+    np.testing.assert_array_equal(res_a, res_b)
+
+
+@pytest.mark.parametrize("gi", [0, 1, 2])
+def test_inertial_blocks_minimise_with_extrapolated_anchors(gi):
+    # every block of one inertial iteration minimises its subproblem of L_beta
+    # plus 1/2 gamma |x - a|^2 around the extrapolated anchor a, formed here
+    # from x^k and x^{k-1}; the returned previous iterate is x^k
+    g = list(_graphs())[gi]
+    st = _state(g, 40 + gi)
+    pv = _prev(g, 50 + gi)
+    new, pv_out, _, _ = oracle.iterate_inertial(g, P(), st, THETA, 1, pv)
+    for k in ("p", "q", "t", "s"):
+        np.testing.assert_array_equal(pv_out[k], st[k])
+    anchor = {k: st[k] + THETA * (st[k] - pv[k]) for k in ("p", "q", "t", "s")}
+    x_p, x_q, x_t, x_s = _blocks(g, st, new)
+    rng = np.random.default_rng(9)
+    cloud = rng.standard_normal((2000, 4))
+    cloud /= np.linalg.norm(cloud, axis=1, keepdims=True)
+    for i in range(g.n):
+        f = lambda v: _obj(g, x_p, "p", i, v, anchor["p"][i], GAMMA[0])
+        p_star = new["p"][i]
+        f_star = f(p_star)
+        assert f_star <= min(f(v) for v in cloud) + 1e-12
+        h = 1e-5
+        grad = np.array([(f(p_star + h * e) - f(p_star - h * e)) / (2 * h) for e in np.eye(4)])
+        rg = grad - p_star * (p_star @ grad)
+        assert np.linalg.norm(rg) < 1e-6 * max(1.0, np.linalg.norm(grad))
+    for key, base, gam, dim in (("q", x_q, GAMMA[1], 4), ("t", x_t, GAMMA[2], 3), ("s", x_s, GAMMA[3], 3)):
+        for i in range(g.n):
+            v = new[key][i]
+            f = lambda w: _obj(g, base, key, i, w, anchor[key][i], gam)
+            h = 1e-3
+            grad = np.array([(f(v + h * e) - f(v - h * e)) / (2 * h) for e in np.eye(dim)])
+            assert np.linalg.norm(grad) < 1e-7 * max(1.0, abs(f(v))), (key, i, grad)
+
+
+def test_inertial_noise_free_truth_is_fixed_point():
+    for g in _noise_free_graphs():
+        st = oracle.init_state(g.q_gt, g.t_gt)
+        pv = {"p": g.q_gt, "q": g.q_gt, "t": g.t_gt, "s": g.t_gt}
+        new, _, res, _ = oracle.iterate_inertial(g, P(), st, THETA, 3, pv)
+        assert res[0] < 1e-24
+        for k in ("p", "q"):
+            np.testing.assert_allclose(new[k], g.q_gt, atol=1e-12)
+        for k in ("t", "s"):
+            np.testing.assert_allclose(new[k], g.t_gt, atol=1e-12)
