@@ -95,6 +95,14 @@ typedef struct {
                             lives (restored when the last one is destroyed);
                             0: plain caching                                       */
     int32_t reserved;    /* 0 */
+    double inertia;      /* theta in [0, 1) of the inertial variant: the proximal
+                            anchors of p, q, t, s are x^k + theta (x^k - x^{k-1})
+                            (the paper's x^{k+1/2}, Appendix B; the extrapolation
+                            rule is this library's reading); 0 (default) is plain
+                            PRADMM.  A nonzero theta needs the scalar weights
+                            (no pradmm_set_sigma) and is not available in the
+                            batched form or the reverse mode; setting a state
+                            restarts the extrapolation (x^{k-1} := x^k). */
 } pradmm_params;
 
 /* Defaults: beta1 = beta2 = 1, relax = 1.5, gamma = {1, 1e-3, 1e-3, 1e-3},

@@ -101,6 +101,7 @@ struct pradmm_s {
     pradmm::FbRec* fb_q = nullptr;     // FP32 handles: queued FP64 p re-solves (n records)
     unsigned int* fb_n = nullptr;      // their per-iteration counters (2)
     void* state_block = nullptr;       // t, s, q, p[0], p[1], lam, z: 28 n reals, contiguous
+    void* prev_block = nullptr;        // inertial variant: q^{k-1}, t^{k-1}, s^{k-1}, 12 n reals
     bool l2_on = false;                // this handle holds an L2 set-aside
     cudaAccessPolicyWindow window{};   // persisting window over t, s, q, p[0], p[1]
     uint64_t epoch = 0;                // bumped by every change of the state
@@ -148,6 +149,12 @@ struct pradmm_s {
         S.t = static_cast<R*>(t);
         S.s = static_cast<R*>(s);
         S.z = static_cast<R*>(z);
+        if (prev_block) {
+            R* b = static_cast<R*>(prev_block);
+            S.qprev = b;
+            S.tprev = b + 4 * n;
+            S.sprev = b + 8 * n;
+        }
         return S;
     }
     template <typename R>
@@ -182,6 +189,7 @@ struct pradmm_s {
         c.b1d = prm.beta1;
         c.b2d = prm.beta2;
         c.fb_thresh = prm.fallback_eps * (prm.beta1 + prm.gamma[0]);
+        c.theta = R(prm.inertia);
         return c;
     }
     pradmm::Launch launch(bool with_cond) const {
@@ -257,6 +265,7 @@ pradmm_status check_params(const pradmm_params* p) {
         return fail(PRADMM_ERR_ARG, "precision must be PRADMM_FP64 or PRADMM_FP32");
     if (!(p->fallback_eps >= 0)) return fail(PRADMM_ERR_ARG, "fallback_eps must be >= 0");
     if (p->l2_window != 0 && p->l2_window != 1) return fail(PRADMM_ERR_ARG, "l2_window must be 0 or 1");
+    if (!(p->inertia >= 0 && p->inertia < 1)) return fail(PRADMM_ERR_ARG, "inertia (theta) must lie in [0, 1)");
     if (p->block != 0 && (p->block < 32 || p->block > 256 || p->block % 32 != 0))
         return fail(PRADMM_ERR_ARG, "block must be 0 (default) or a multiple of 32 in [32, 256]");
     return PRADMM_OK;
@@ -496,6 +505,7 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
         h->lam = b + 5 * a;
         h->z = b + 6 * a;
     }
+    if (h->prm.inertia != 0.0) ST(valloc(h, &h->prev_block, 12 * (size_t)n));
     ST(dalloc(h, &h->inv2_d, n));
     ST(dalloc(h, &h->inv3_d, n));
     ST(dalloc(h, &h->inv4_d, n));
@@ -765,6 +775,14 @@ pradmm_status set_state_dev(pradmm_s* h, const double* p, const double* q, const
     ST(put3(t, h->inv3_d, h->t));
     ST(put3(s, h->inv2_d, h->s));
     ST(put3(z, h->inv4_d, h->z));
+    if (h->prev_block) {
+        // a new state restarts the inertial extrapolation: x^{k-1} := x^k
+        char* b = static_cast<char*>(h->prev_block);
+        const size_t a = 4 * (size_t)n * h->rsize;
+        CU(cudaMemcpyAsync(b, h->q, a, cudaMemcpyDeviceToDevice, st));
+        CU(cudaMemcpyAsync(b + a, h->t, a, cudaMemcpyDeviceToDevice, st));
+        CU(cudaMemcpyAsync(b + 2 * a, h->s, a, cudaMemcpyDeviceToDevice, st));
+    }
     CU(cudaStreamSynchronize(st));
     h->state_set = true;
     h->pending = false;
@@ -1118,6 +1136,7 @@ template <typename R>
 pradmm_status adjoint_record(pradmm_s* h, int32_t iters, int32_t ckpt_every) {
     if (!h->state_set) return fail(PRADMM_ERR_STATE, "state is not set (pradmm_set_state or pradmm_init_odometry)");
     if (h->general) return fail(PRADMM_ERR_STATE, "the reverse mode supports scalar Sigma only");
+    if (h->prm.inertia != 0.0) return fail(PRADMM_ERR_ARG, "the reverse mode needs inertia = 0");
     if (iters < 0) return fail(PRADMM_ERR_ARG, "iters must be >= 0");
     if (ckpt_every < 0) return fail(PRADMM_ERR_ARG, "ckpt_every must be >= 0 (0: chosen from free device memory)");
     h->tape_valid = false;
@@ -1463,6 +1482,8 @@ void eig3_host(const double A0[3][3], double U[9], double mu[3]) {
 }
 
 pradmm_status set_sigma_impl(pradmm_s* h, const double* S1, const double* S2) {
+    if ((S1 || S2) && h->prm.inertia != 0.0)
+        return fail(PRADMM_ERR_ARG, "general Sigma needs inertia = 0 (the inertial variant uses scalar weights)");
     if (!S1 && !S2) {
         h->general = false;
     } else {
@@ -1527,6 +1548,7 @@ void pradmm_default_params(pradmm_params* p) {
     p->block = 0;
     p->l2_window = 1;
     p->reserved = 0;
+    p->inertia = 0.0;
 }
 
 pradmm_status pradmm_create(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const double* q_meas,
@@ -1928,6 +1950,7 @@ pradmm_status pradmm_batch_create(int32_t G, const int64_t* n_g, const int64_t* 
     if (!out) return fail(PRADMM_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (G < 1 || !n_g || !m_g) return fail(PRADMM_ERR_ARG, "need G >= 1 and the size arrays");
+    if (prm && prm->inertia != 0.0) return fail(PRADMM_ERR_ARG, "the batched form needs inertia = 0");
     try {
         pradmm_batch_s* b = new pradmm_batch_s();
         b->G = G;

@@ -258,14 +258,15 @@ __device__ __noinline__ Q<A> p_rhs_serial(const GraphDev<R>& g, const R* t, cons
 
 // p-update finish for vertex i: normalise u; in FP32 a tiny |u| is recomputed in
 // FP64 from the same inputs; |u| == 0 keeps p^k (sphere minimiser not unique).
+// pa: the proximal anchor of the p-block (p^k, or its inertial extrapolation).
 template <typename R>
 __device__ __forceinline__ void p_normalise(const GraphDev<R>& g, const StateDev<R>& S, int64_t i, const Q<R>& u,
-                                            const R4<R>& qr, const R4<R>& lr, const R4<R>& pr, R sx, R sy, R sz,
-                                            const Coef<R>& c, R* p_out, Ctrl* ctrl) {
+                                            const R4<R>& qr, const R4<R>& lr, const R4<R>& pr, const R4<R>& pa,
+                                            R sx, R sy, R sz, const Coef<R>& c, R* p_out, Ctrl* ctrl) {
     const R nn = u.w * u.w + u.x * u.x + u.y * u.y + u.z * u.z;
     const R nrm = sqrt(nn);
     if (sizeof(R) == sizeof(float) && nrm < R(c.fb_thresh)) {
-        const Q<double> ud = p_rhs_serial<R, double>(g, S.t, S.q, i, asq<double>(qr), asq<double>(lr), asq<double>(pr),
+        const Q<double> ud = p_rhs_serial<R, double>(g, S.t, S.q, i, asq<double>(qr), asq<double>(lr), asq<double>(pa),
                                                      double(sx), double(sy), double(sz), c);
         const double nd = sqrt(ud.w * ud.w + ud.x * ud.x + ud.y * ud.y + ud.z * ud.z);
         atomicAdd(&ctrl->fallbacks, 1ull);
@@ -369,15 +370,24 @@ struct QEdge {
 };
 
 // One vertex of the q-block + lambda update; adds |dq_i|^2, |dlam_i|^2.
-template <typename R, bool PIPE = false, bool NC = false>
+// INERT: the proximal anchor is q^k + theta (q^k - q^{k-1}) (inertial variant;
+// S.qprev holds q^{k-1} and receives q^k).
+template <typename R, bool PIPE = false, bool NC = false, bool INERT = false>
 __device__ __forceinline__ void q_vertex(const GraphDev<R>& g, const StateDev<R>& S, const Coef<R>& c, const R* pn,
                                          int64_t i, Acc<R>& adq, Acc<R>& adl) {
     const Q<R> pi = asq<R>(IO<R>::ld(pn, i));
     const Q<R> qi = asq<R>(IO<R>::ld(S.q, i));
     const Q<R> li = asq<R>(IO<R>::ld(S.lam, i));
     const R4<R> sr = IO<R>::ld(S.s, i);  // (s_i, 1/A_2)
-    Q<R> b = {c.beta1 * pi.w - li.w + c.g2 * qi.w, c.beta1 * pi.x - li.x + c.g2 * qi.x,
-              c.beta1 * pi.y - li.y + c.g2 * qi.y, c.beta1 * pi.z - li.z + c.g2 * qi.z};
+    Q<R> qa = qi;
+    if (INERT) {
+        const Q<R> qp = asq<R>(IO<R>::ld(S.qprev, i));
+        qa = {qi.w + c.theta * (qi.w - qp.w), qi.x + c.theta * (qi.x - qp.x), qi.y + c.theta * (qi.y - qp.y),
+              qi.z + c.theta * (qi.z - qp.z)};
+        IO<R>::st(S.qprev, i, qi.w, qi.x, qi.y, qi.z);
+    }
+    Q<R> b = {c.beta1 * pi.w - li.w + c.g2 * qa.w, c.beta1 * pi.x - li.x + c.g2 * qa.x,
+              c.beta1 * pi.y - li.y + c.g2 * qa.y, c.beta1 * pi.z - li.z + c.g2 * qa.z};
     for_edges2<QEdge<R>, PIPE>(
         g.out_ptr[i], g.out_ptr[i + 1],
         [&](int e, QEdge<R>& x) {
@@ -418,15 +428,24 @@ struct TEdge {
 };
 
 // One vertex of the t-block; adds |dt_i|^2.  PIPE: see for_edges2.
-template <typename R, bool PIPE = false, bool NC = false>
+// INERT: the proximal anchor is t^k + theta (t^k - t^{k-1}) (S.tprev).
+template <typename R, bool PIPE = false, bool NC = false, bool INERT = false>
 __device__ __forceinline__ void t_vertex(const GraphDev<R>& g, const StateDev<R>& S, const Coef<R>& c, const R* pn,
                                          int64_t i, Acc<R>& adt) {
     const R4<R> tr = IO<R>::ld(S.t, i);  // (t_i, 1/A_3)
     const R4<R> sr = IO<R>::ld(S.s, i);
     const R4<R> zr = IO<R>::ld(S.z, i);
-    R ax = c.beta2 * sr.a + zr.a + c.g3 * tr.a;
-    R ay = c.beta2 * sr.b + zr.b + c.g3 * tr.b;
-    R az = c.beta2 * sr.c + zr.c + c.g3 * tr.c;
+    R tax = tr.a, tay = tr.b, taz = tr.c;
+    if (INERT) {
+        const R4<R> tp = IO<R>::ld(S.tprev, i);
+        tax += c.theta * (tr.a - tp.a);
+        tay += c.theta * (tr.b - tp.b);
+        taz += c.theta * (tr.c - tp.c);
+        IO<R>::st(S.tprev, i, tr.a, tr.b, tr.c, tr.d);
+    }
+    R ax = c.beta2 * sr.a + zr.a + c.g3 * tax;
+    R ay = c.beta2 * sr.b + zr.b + c.g3 * tay;
+    R az = c.beta2 * sr.c + zr.c + c.g3 * taz;
     for_edges2<TEdge<R>, PIPE>(
         g.in_ptr[i], g.in_ptr[i + 1],
         [&](int e, TEdge<R>& x) {
@@ -478,7 +497,10 @@ struct PEdge {
 
 // One vertex of the s-block + z update (WITH_S; adds |dz_i|^2) followed by
 // the p-block of the next iteration, which reads p from pc and writes pn.
-template <typename R, bool WITH_S, bool PIPE = false, bool NC = false>
+// INERT (with the s-block): the proximal anchors are s^k + theta (s^k - s^{k-1})
+// (S.sprev) and, for the next p-block, p^{k+1} + theta (p^{k+1} - p^k), p^k being
+// the vertex's value in pn before it is overwritten.
+template <typename R, bool WITH_S, bool PIPE = false, bool NC = false, bool INERT = false>
 __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R>& S, const Coef<R>& c, const R* pc,
                                           R* pn, int64_t i, Acc<R>& adz, Ctrl* ctrl) {
     const R4<R> sr = IO<R>::ld(S.s, i);  // (s_i, 1/A_2)
@@ -517,9 +539,17 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
         const R4<R> tr = IO<R>::ld(S.t, i);
         const R4<R> zr = IO<R>::ld(S.z, i);  // (z_i, 1/A_4)
         const R inv = zr.d;
-        sx = (ax + c.beta2 * tr.a - zr.a + c.g4 * sr.a) * inv;
-        sy = (ay + c.beta2 * tr.b - zr.b + c.g4 * sr.b) * inv;
-        sz = (az + c.beta2 * tr.c - zr.c + c.g4 * sr.c) * inv;
+        R sax = sr.a, say = sr.b, saz = sr.c;
+        if (INERT) {
+            const R4<R> sp = IO<R>::ld(S.sprev, i);
+            sax += c.theta * (sr.a - sp.a);
+            say += c.theta * (sr.b - sp.b);
+            saz += c.theta * (sr.c - sp.c);
+            IO<R>::st(S.sprev, i, sr.a, sr.b, sr.c, sr.d);
+        }
+        sx = (ax + c.beta2 * tr.a - zr.a + c.g4 * sax) * inv;
+        sy = (ay + c.beta2 * tr.b - zr.b + c.g4 * say) * inv;
+        sz = (az + c.beta2 * tr.c - zr.c + c.g4 * saz) * inv;
         const R zx = zr.a - c.tb2 * (tr.a - sx), zy = zr.b - c.tb2 * (tr.b - sy), zz = zr.c - c.tb2 * (tr.c - sz);
         IO<R>::st(S.s, i, sx, sy, sz, sr.d);
         IO<R>::st(S.z, i, zx, zy, zz, inv);
@@ -529,8 +559,14 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
         axpy(u, R(-1), qmul_pr(qmul_pl(sr.a - sx, sr.b - sy, sr.c - sz, qi), wx, wy, wz));
     }
     // own terms beta1 q_i + lam_i + gamma1 p_i, then in-edge terms 2 q_l (k_e q_e)
-    Q<R> v = {c.beta1 * qr.a + lr.a + c.g1 * pr.a, c.beta1 * qr.b + lr.b + c.g1 * pr.b,
-              c.beta1 * qr.c + lr.c + c.g1 * pr.c, c.beta1 * qr.d + lr.d + c.g1 * pr.d};
+    R4<R> pa = pr;  // the p-block's proximal anchor
+    if (INERT && WITH_S) {
+        const R4<R> po = IO<R>::ld(pn, i);  // p^k, about to be replaced by p^{k+2}
+        pa = {pr.a + c.theta * (pr.a - po.a), pr.b + c.theta * (pr.b - po.b), pr.c + c.theta * (pr.c - po.c),
+              pr.d + c.theta * (pr.d - po.d)};
+    }
+    Q<R> v = {c.beta1 * qr.a + lr.a + c.g1 * pa.a, c.beta1 * qr.b + lr.b + c.g1 * pa.b,
+              c.beta1 * qr.c + lr.c + c.g1 * pa.c, c.beta1 * qr.d + lr.d + c.g1 * pa.d};
     axpy(v, R(1), u);
     for_edges2<PEdge<R>, PIPE>(
         g.in_ptr[i], g.in_ptr[i + 1],
@@ -540,7 +576,7 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
         },
         [&](PEdge<R>& x) { x.ql = gat<R, NC>(S.q, x.l); },
         [&](const PEdge<R>& x) { axpy(v, R(2), qmul(asq<R>(x.ql), asq<R>(x.qk))); });
-    p_normalise<R>(g, S, i, v, qr, lr, pr, sx, sy, sz, c, pn, ctrl);
+    p_normalise<R>(g, S, i, v, qr, lr, pr, pa, sx, sy, sz, c, pn, ctrl);
 }
 
 // Out-edge terms of vertex i in F of Eq. (1) at (p, t), in double:

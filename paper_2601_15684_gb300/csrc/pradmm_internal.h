@@ -62,6 +62,11 @@ struct StateDev {
     R* t;
     R* s;
     R* z;
+    // inertial variant only (else NULL): the previous iterates q^{k-1},
+    // t^{k-1}, s^{k-1} of the extrapolated proximal anchors
+    R* qprev = nullptr;
+    R* tprev = nullptr;
+    R* sprev = nullptr;
 };
 
 template <typename R>
@@ -71,6 +76,7 @@ struct Coef {
     R g1, g2, g3, g4;    // proximal weights
     double b1d, b2d;     // penalties in double (residual)
     double fb_thresh;    // FP64 recompute of the p-update below this |u|
+    R theta = R(0);      // inertial extrapolation of the proximal anchors (0: plain)
 };
 
 struct Launch {

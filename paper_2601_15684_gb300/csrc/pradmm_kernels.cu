@@ -70,7 +70,7 @@ namespace {
 
 using namespace dev;
 
-template <typename R>
+template <typename R, bool INERT = false>
 __global__ void __launch_bounds__(256, PRADMM_MINB_Q) k_q(GraphDev<R> g, StateDev<R> S, Coef<R> c, Ctrl* ctrl, double* part,
                                            int pstride) {
     __shared__ double sh[32];
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256, PRADMM_MINB_Q) k_q(GraphDev<R> g, StateDe
     const R* pn = S.p[(k + 1) & 1];
     Acc<R> adq, adl;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x)
-        q_vertex<R, PRADMM_PIPE_Q != 0, PRADMM_NC != 0>(g, S, c, pn, i, adq, adl);
+        q_vertex<R, PRADMM_PIPE_Q != 0, PRADMM_NC != 0, INERT>(g, S, c, pn, i, adq, adl);
     const double sq = block_sum(adq.get(), sh);
     const double sl = block_sum(adl.get(), sh);
     if (threadIdx.x == 0) {
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(256, PRADMM_MINB_Q) k_q(GraphDev<R> g, StateDe
     }
 }
 
-template <typename R>
+template <typename R, bool INERT = false>
 __global__ void PRADMM_BOUNDS_T k_t(GraphDev<R> g, StateDev<R> S, Coef<R> c, Ctrl* ctrl, double* part,
                                            int pstride) {
     __shared__ double sh[32];
@@ -97,12 +97,12 @@ __global__ void PRADMM_BOUNDS_T k_t(GraphDev<R> g, StateDev<R> S, Coef<R> c, Ctr
     const R* pn = S.p[(k + 1) & 1];
     Acc<R> adt;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x)
-        t_vertex<R, true, PRADMM_NC != 0>(g, S, c, pn, i, adt);
+        t_vertex<R, true, PRADMM_NC != 0, INERT>(g, S, c, pn, i, adt);
     const double st = block_sum(adt.get(), sh);
     if (threadIdx.x == 0) part[SLOT_DT * pstride + blockIdx.x] = st;
 }
 
-template <typename R, bool WITH_S>
+template <typename R, bool WITH_S, bool INERT = false>
 __global__ void __launch_bounds__(256, PRADMM_MINB_SP) k_sp(GraphDev<R> g, StateDev<R> S, Coef<R> c, Launch L) {
     __shared__ double sh[32];
     Ctrl* ctrl = L.ctrl;
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(256, PRADMM_MINB_SP) k_sp(GraphDev<R> g, State
     R* pn = WITH_S ? S.p[k & 1] : S.p[(k + 1) & 1];        // p computed ahead
     Acc<R> adz;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x)
-        sp_vertex<R, WITH_S, PRADMM_PIPE_SP != 0, PRADMM_NC != 0>(g, S, c, pc, pn, i, adz, ctrl);
+        sp_vertex<R, WITH_S, PRADMM_PIPE_SP != 0, PRADMM_NC != 0, INERT>(g, S, c, pc, pn, i, adz, ctrl);
     if (WITH_S) {
         const double sd = block_sum(adz.get(), sh);
         if (threadIdx.x == 0) L.part[SLOT_DZ * L.pstride + blockIdx.x] = sd;
@@ -236,14 +236,18 @@ cudaError_t launch_p(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& 
 }
 template <typename R>
 cudaError_t launch_q(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const Launch& L) {
+    // the inertial variant (theta != 0) runs its own instances of the sweeps
+    if (c.theta != R(0)) return launch_sweep(L, L.grid_q, k_q<R, true>, g, s, c, L.ctrl, L.part, L.pstride);
     return launch_sweep(L, L.grid_q, k_q<R>, g, s, c, L.ctrl, L.part, L.pstride);
 }
 template <typename R>
 cudaError_t launch_t(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const Launch& L) {
+    if (c.theta != R(0)) return launch_sweep(L, L.grid_t, k_t<R, true>, g, s, c, L.ctrl, L.part, L.pstride);
     return launch_sweep(L, L.grid_t, k_t<R>, g, s, c, L.ctrl, L.part, L.pstride);
 }
 template <typename R>
 cudaError_t launch_sp(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const Launch& L) {
+    if (c.theta != R(0)) return launch_sweep(L, L.grid_sp, k_sp<R, true, true>, g, s, c, L);
     return launch_sweep(L, L.grid_sp, k_sp<R, true>, g, s, c, L);
 }
 

@@ -35,7 +35,8 @@ class pradmm_params(ctypes.Structure):
     _fields_ = [("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("relax", ctypes.c_double),
                 ("gamma", ctypes.c_double * 4), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("fallback_eps", ctypes.c_double), ("use_graph", ctypes.c_int32),
-                ("block", ctypes.c_int32), ("l2_window", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("block", ctypes.c_int32), ("l2_window", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("inertia", ctypes.c_double)]
 
 
 class PRADMMError(RuntimeError):

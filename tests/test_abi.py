@@ -49,7 +49,7 @@ def test_host_only_entry_points(lib):
     assert list(prm.gamma) == [1.0, 1e-3, 1e-3, 1e-3]
     assert prm.tol == 1e-4 and prm.max_iter == 300 and prm.precision == P.PRADMM_FP32
     assert P.pradmm_status_string(P.PRADMM_ERR_SELFLOOP) == "self-loop edge"
-    assert ctypes.sizeof(P.pradmm_params) == 96
+    assert ctypes.sizeof(P.pradmm_params) == 104 and prm.inertia == 0.0
 
 
 def test_missing_library_fails_loudly(tmp_path):

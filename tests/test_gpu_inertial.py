@@ -1,0 +1,135 @@
+"""Inertial variant on the GPU against the oracle's inertial iteration.
+
+Reading R27: the proximal anchors of p, q, t, s are x^k + theta (x^k - x^{k-1})
+(the paper's x^{k+1/2} of Appendix B; the oracle's form is pinned in
+tests/test_oracle_iteration.py).  The library keeps x^{k-1} of q, t, s in its
+own arrays and takes p^{k-1} from the p double buffer; a state set restarts
+the extrapolation (x^{-1} = x^0).
+
+Tolerances as the plain parity tests: FP64 1e-10 relative per array, FP32 1e-5
+for p, q, t, s and the multipliers against tau beta times the scale they are
+formed from; the same after a second step call (continuity of x^{k-1}).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_15684_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+KEYS = ("p", "q", "t", "s", "lam", "z")
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2601_15684_gb300 import build_lib
+    from paper_2601_15684_gb300 import pradmm
+    build_lib.build()
+    pradmm.load()
+    return pradmm
+
+
+def relerr(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _oparams():
+    return oracle.make_params(beta1=1.0, beta2=1.0, tau=1.5, gamma=(1.0, 1e-3, 1e-3, 1e-3))
+
+
+def check_state(gpu, orc, fp64, what=""):
+    if fp64:
+        for k in KEYS:
+            assert relerr(gpu[k], orc[k]) <= 1e-10, (what, k, relerr(gpu[k], orc[k]))
+        return
+    for k in ("p", "q", "t", "s"):
+        assert relerr(gpu[k], orc[k]) <= 1e-5, (what, k, relerr(gpu[k], orc[k]))
+    assert np.linalg.norm(gpu["lam"] - orc["lam"]) <= 1e-5 * 1.5 * max(np.linalg.norm(orc["p"]), 1.0), what
+    assert np.linalg.norm(gpu["z"] - orc["z"]) <= 1e-5 * 1.5 * max(np.linalg.norm(orc["t"]), 1.0), what
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("theta", [0.3, 0.7])
+@pytest.mark.parametrize("case", ["ragged", "walk"])
+def test_inertial_matches_oracle_one_and_ten_iterations(P, precision, theta, case):
+    if case == "ragged":
+        g = synth.random_graph(700, 2300, seed=41, isolated=5)
+    else:
+        g = synth.workload("walk128")
+    st0 = synth.random_state(np.random.default_rng(7), g.n)
+    with P.Solver(g, precision=precision, inertia=theta) as S:
+        S.set_state_full(st0)
+        orc, prev, done = st0, None, 0
+        for it in (1, 10):
+            e_gpu = S.step(it - done)
+            orc, prev, res, _ = oracle.iterate_inertial(g, _oparams(), orc, theta, it - done, prev)
+            done = it
+            check_state(S.state(), orc, precision == 0, f"{case} theta={theta} after {it}")
+            assert abs(e_gpu - res[0]) <= (1e-9 if precision == 0 else 1e-3) * max(res[0], 1e-30)
+
+
+def test_inertial_solve_stops_like_the_oracle(P):
+    g = synth.workload("walk128")
+    q0, t0 = oracle.init_odometry(g)
+    st, prev, k, theta, tol = oracle.init_state(q0, t0), None, 0, 0.3, 1e-4
+    while k < 300:
+        st, prev, res, _ = oracle.iterate_inertial(g, _oparams(), st, theta, 1, prev)
+        k += 1
+        if res[0] < tol:
+            break
+    with P.Solver(g, precision=0, inertia=theta, tol=tol, max_iter=300) as S:
+        S.init_odometry()
+        converged, iters, e = S.solve()
+        gpu = S.state()
+    assert converged and iters == k
+    check_state(gpu, st, True, "solve")
+
+
+def test_state_set_restarts_the_extrapolation(P):
+    g = synth.random_graph(300, 900, seed=5)
+    st0 = synth.random_state(np.random.default_rng(3), g.n)
+    theta = 0.5
+    with P.Solver(g, precision=0, inertia=theta) as S:
+        S.set_state_full(st0)
+        S.step(4)
+        mid = S.state()
+        S.set_state_full(mid)  # x^{k-1} := x^k
+        S.step(3)
+        gpu = S.state()
+    orc, _, _, _ = oracle.iterate_inertial(g, _oparams(), st0, theta, 4)
+    check_state(mid, orc, True, "before restart")
+    orc, _, _, _ = oracle.iterate_inertial(g, _oparams(), mid, theta, 3)  # prev = None: restart
+    check_state(gpu, orc, True, "after restart")
+
+
+def test_inertia_zero_is_the_plain_path(P):
+    g = synth.random_graph(200, 700, seed=9)
+    st0 = synth.random_state(np.random.default_rng(4), g.n)
+    outs = []
+    for kw in ({}, {"inertia": 0.0}):
+        with P.Solver(g, precision=1, **kw) as S:
+            S.set_state_full(st0)
+            S.step(7)
+            outs.append(S.state())
+    for k in KEYS:
+        np.testing.assert_array_equal(outs[0][k], outs[1][k])
+
+
+def test_inertia_is_rejected_where_unsupported(P):
+    g = synth.random_graph(60, 180, seed=2)
+    with pytest.raises(P.PRADMMError) as ei:
+        P.Solver(g, inertia=1.0)
+    assert ei.value.status == P.PRADMM_ERR_ARG
+    with P.Solver(g, precision=1, inertia=0.4) as S:
+        S.init_odometry()
+        with pytest.raises(P.PRADMMError) as ei:
+            S.set_sigma(np.eye(4), np.eye(4))
+        assert ei.value.status == P.PRADMM_ERR_ARG
+        with pytest.raises(P.PRADMMError) as ei:
+            S.adjoint_record(5, 1)
+        assert ei.value.status == P.PRADMM_ERR_ARG
+    prm = P.pradmm_default_params()
+    prm.inertia = 0.4
+    with pytest.raises(P.PRADMMError) as ei:
+        P.Batch([g, g], params=prm)
+    assert ei.value.status == P.PRADMM_ERR_ARG
