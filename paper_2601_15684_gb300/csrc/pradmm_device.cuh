@@ -384,7 +384,6 @@ __device__ __forceinline__ void q_vertex(const GraphDev<R>& g, const StateDev<R>
         const Q<R> qp = asq<R>(IO<R>::ld(S.qprev, i));
         qa = {qi.w + c.theta * (qi.w - qp.w), qi.x + c.theta * (qi.x - qp.x), qi.y + c.theta * (qi.y - qp.y),
               qi.z + c.theta * (qi.z - qp.z)};
-        IO<R>::st(S.qprev, i, qi.w, qi.x, qi.y, qi.z);
     }
     Q<R> b = {c.beta1 * pi.w - li.w + c.g2 * qa.w, c.beta1 * pi.x - li.x + c.g2 * qa.x,
               c.beta1 * pi.y - li.y + c.g2 * qa.y, c.beta1 * pi.z - li.z + c.g2 * qa.z};
@@ -411,6 +410,7 @@ __device__ __forceinline__ void q_vertex(const GraphDev<R>& g, const StateDev<R>
     const R ly = li.y - c.tb1 * (pi.y - qy), lz = li.z - c.tb1 * (pi.z - qz);
     IO<R>::st(S.q, i, qw, qx, qy, qz);
     IO<R>::st(S.lam, i, lw, lx, ly, lz);
+    if (INERT) IO<R>::st(S.qprev, i, qi.w, qi.x, qi.y, qi.z);
     R d0 = qw - qi.w, d1 = qx - qi.x, d2 = qy - qi.y, d3 = qz - qi.z;
     adq.add(d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3);
     d0 = lw - li.w; d1 = lx - li.x; d2 = ly - li.y; d3 = lz - li.z;
@@ -441,7 +441,6 @@ __device__ __forceinline__ void t_vertex(const GraphDev<R>& g, const StateDev<R>
         tax += c.theta * (tr.a - tp.a);
         tay += c.theta * (tr.b - tp.b);
         taz += c.theta * (tr.c - tp.c);
-        IO<R>::st(S.tprev, i, tr.a, tr.b, tr.c, tr.d);
     }
     R ax = c.beta2 * sr.a + zr.a + c.g3 * tax;
     R ay = c.beta2 * sr.b + zr.b + c.g3 * tay;
@@ -468,6 +467,7 @@ __device__ __forceinline__ void t_vertex(const GraphDev<R>& g, const StateDev<R>
     const R inv = tr.d;
     const R nx = ax * inv, ny = ay * inv, nz = az * inv;
     IO<R>::st(S.t, i, nx, ny, nz, inv);
+    if (INERT) IO<R>::st(S.tprev, i, tr.a, tr.b, tr.c, tr.d);
     const R d0 = nx - tr.a, d1 = ny - tr.b, d2 = nz - tr.c;
     adt.add(d0 * d0 + d1 * d1 + d2 * d2);
 }
@@ -545,7 +545,6 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
             sax += c.theta * (sr.a - sp.a);
             say += c.theta * (sr.b - sp.b);
             saz += c.theta * (sr.c - sp.c);
-            IO<R>::st(S.sprev, i, sr.a, sr.b, sr.c, sr.d);
         }
         sx = (ax + c.beta2 * tr.a - zr.a + c.g4 * sax) * inv;
         sy = (ay + c.beta2 * tr.b - zr.b + c.g4 * say) * inv;
@@ -553,6 +552,7 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
         const R zx = zr.a - c.tb2 * (tr.a - sx), zy = zr.b - c.tb2 * (tr.b - sy), zz = zr.c - c.tb2 * (tr.c - sz);
         IO<R>::st(S.s, i, sx, sy, sz, sr.d);
         IO<R>::st(S.z, i, zx, zy, zz, inv);
+        if (INERT) IO<R>::st(S.sprev, i, sr.a, sr.b, sr.c, sr.d);
         const R d0 = zx - zr.a, d1 = zy - zr.b, d2 = zz - zr.c;
         adz.add(d0 * d0 + d1 * d1 + d2 * d2);
         // move the p-block's out-edge term from s^{old} to s^{new}

@@ -28,12 +28,13 @@ def main(argv=None) -> int:
     ap.add_argument("--adjoint", type=int, default=0)
     ap.add_argument("--ckpt", type=int, default=20, help="checkpoint spacing (0: chosen from free memory)")
     ap.add_argument("--sigma", action="store_true", help="general Sigma_1, Sigma_2")
+    ap.add_argument("--inertia", type=float, default=0.0, help="theta of the inertial variant")
     a = ap.parse_args(argv)
     from paper_2601_15684_gb300 import build_lib, pradmm, synth
 
     build_lib.build()
     g = synth.workload(a.workload)
-    with pradmm.Solver(g, precision=a.precision, use_graph=a.graph, block=a.block) as S:
+    with pradmm.Solver(g, precision=a.precision, use_graph=a.graph, block=a.block, inertia=a.inertia) as S:
         if a.sigma:
             import numpy as np
             rng = np.random.default_rng(0)
