@@ -227,6 +227,36 @@ def run_batched(P, rank=0, ws=1, sample=32):
     return out
 
 
+def run_inertial(P, g, thetas=(0.0, 0.3, 0.6), lattice_iters=200):
+    """Inertial variant (proximal anchors x^k + theta (x^k - x^{k-1})): solves
+    of the ring and cube workloads (tau = 1.4, tol = 1e-4, at most 3000
+    iterations) for each theta, FP32; and the time per
+    iteration on the 1M-pose lattice, graph-launched, against the plain path."""
+    from paper_2601_15684_gb300 import synth
+    solves = []
+    for wl in ("ring5000", "cube10"):
+        gw = synth.workload(wl)
+        for theta in thetas:
+            with P.Solver(gw, precision=P.PRADMM_FP32, inertia=theta, relax=1.4, tol=1e-4, max_iter=3000) as S:
+                S.init_odometry()
+                t0 = time.perf_counter()
+                conv, it, e = S.solve()
+                dt = time.perf_counter() - t0
+                F = S.objective()
+            solves.append({"workload": wl, "theta": theta, "converged": bool(conv), "iterations": int(it),
+                           "e_final": e, "objective": F, "ms": 1e3 * dt})
+    per_iter = {}
+    for theta in (0.0, 0.3):
+        with P.Solver(g, precision=P.PRADMM_FP32, inertia=theta) as S:
+            S.init_odometry()
+            S.step(10)
+            t0 = time.perf_counter()
+            S.step(lattice_iters)
+            per_iter[str(theta)] = 1e3 * (time.perf_counter() - t0) / lattice_iters
+    return {"solves": solves, "lattice_ms_per_iteration": per_iter,
+            "reading": "anchors x^k + theta (x^k - x^{k-1}) for p, q, t, s (the paper leaves the rule open)"}
+
+
 def run_general_sigma(P, g, iters=300):
     """General weight matrices (Lemma 1 p-update, 4x4/3x3 block solves) on the
     same 1M-pose lattice, FP32, graph-launched, against the scalar path on the
@@ -493,6 +523,9 @@ def run_ours(args):
     general = None
     if rank == 0 and ws == 1 and not args.no_general:
         general = run_general_sigma(P, g)
+    inertial = None
+    if rank == 0 and ws == 1 and not args.no_inertial:
+        inertial = run_inertial(P, g)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = _cpu_baseline(g)
@@ -529,6 +562,8 @@ def run_ours(args):
         line["adjoint"] = adjoint
     if general is not None:
         line["general_sigma"] = general
+    if inertial is not None:
+        line["inertial"] = inertial
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
@@ -548,6 +583,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-general", action="store_true")
+    ap.add_argument("--no-inertial", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
