@@ -26,6 +26,9 @@ Every block follows Appendix B with the literal 4x4 matrices of Appendix A.2:
   s-block (3d): s = A_4^{-1} b_4,  A_4 = 2 sum_out w E^T S1 E + (beta2 + gamma4) I,
                 b_4 = 2 sum_out w E^T S1 (t~_j - c~_e) - z + beta2 t + gamma4 s
   duals (3e, 3f) and the residual of Appendix E.1 as in the scalar case.
+The gamma terms above are the proximal terms around x^k; the inertial variant
+(reading R27) puts them around x^{k+1/2} = x^k + theta (x^k - x^{k-1}), the
+anchors Appendix B writes, for p, q, t and s.
 
 The p-block's sphere-constrained quadratic is solved by Algorithm 2: lambda*
 is the rightmost real eigenvalue of Q y = -lambda y with
@@ -104,10 +107,11 @@ def p_system(g, params, Sigma1, Sigma2, st, i):
     return A1, b1
 
 
-def iterate(g, params, Sigma1, Sigma2, st):
+def iterate(g, params, Sigma1, Sigma2, st, anchors=None):
     """One iteration of Eq. (3a)-(3f) with weights omega_e Sigma1, kappa_e Sigma2.
-    params: (beta1, beta2, tau, (gamma1..gamma4)).  Returns (new_state, e^{k+1},
-    number of hard-case p-updates)."""
+    params: (beta1, beta2, tau, (gamma1..gamma4)).  `anchors` (p, q, t, s) are
+    the proximal anchors x^{k+1/2} of Appendix B; None means x^k (plain
+    PRADMM).  Returns (new_state, e^{k+1}, number of hard-case p-updates)."""
     beta1, beta2, tau, gam = params
     g1, g2, g3, g4 = gam
     S1, S2 = np.asarray(Sigma1, dtype=np.float64), np.asarray(Sigma2, dtype=np.float64)
@@ -116,6 +120,10 @@ def iterate(g, params, Sigma1, Sigma2, st):
     qe, te, ka, om = g.q_meas, g.t_meas, g.kappa, g.omega
     p, q, t, s = (st[k].copy() for k in ("p", "q", "t", "s"))
     lam, z = st["lam"].copy(), st["z"].copy()
+    if anchors is None:
+        ap, aq, at, as_ = p, q, t, s
+    else:
+        ap, aq, at, as_ = (np.asarray(anchors[k], dtype=np.float64) for k in ("p", "q", "t", "s"))
     out_of = [[] for _ in range(n)]
     in_of = [[] for _ in range(n)]
     for e in range(m):
@@ -127,7 +135,7 @@ def iterate(g, params, Sigma1, Sigma2, st):
     pn = p.copy()
     for i in range(n):
         A1 = (beta1 + g1) * np.eye(4)
-        b1 = -beta1 * q[i] - lam[i] - g1 * p[i]
+        b1 = -beta1 * q[i] - lam[i] - g1 * ap[i]
         for e in out_of[i]:
             G1 = M(q[i]) @ M(pure(te[e])) @ D
             r = pure(t[dst[e]]) - pure(s[i])
@@ -145,7 +153,7 @@ def iterate(g, params, Sigma1, Sigma2, st):
     qn = q.copy()
     for i in range(n):
         A2 = (beta1 + g2) * np.eye(4)
-        b2 = beta1 * p[i] - lam[i] + g2 * q[i]
+        b2 = beta1 * p[i] - lam[i] + g2 * aq[i]
         for e in out_of[i]:
             j = dst[e]
             G3 = W(conj(p[i])) @ W(pure(te[e]))
@@ -164,7 +172,7 @@ def iterate(g, params, Sigma1, Sigma2, st):
     tn = t.copy()
     for i in range(n):
         A3 = (beta2 + g3) * np.eye(3)
-        b3 = beta2 * s[i] + z[i] + g3 * t[i]
+        b3 = beta2 * s[i] + z[i] + g3 * at[i]
         for e in in_of[i]:
             w = pure(s[src[e]]) + c_full(e)
             A3 += 2.0 * om[e] * E3.T @ S1 @ E3
@@ -176,7 +184,7 @@ def iterate(g, params, Sigma1, Sigma2, st):
     sn = s.copy()
     for i in range(n):
         A4 = (beta2 + g4) * np.eye(3)
-        b4 = beta2 * t[i] - z[i] + g4 * s[i]
+        b4 = beta2 * t[i] - z[i] + g4 * as_[i]
         for e in out_of[i]:
             w = pure(t[dst[e]]) - c_full(e)
             A4 += 2.0 * om[e] * E3.T @ S1 @ E3
@@ -191,6 +199,18 @@ def iterate(g, params, Sigma1, Sigma2, st):
     e_res = (np.sum((lam - lam_old) ** 2) / beta1 + np.sum((z - z_old) ** 2) / beta2
              + beta1 * np.sum((q - q_old) ** 2) + beta2 * np.sum((t - t_old) ** 2))
     return {"p": p, "q": q, "t": t, "s": s, "lam": lam, "z": z}, float(e_res), hard
+
+
+def iterate_inertial(g, params, Sigma1, Sigma2, st, theta, prev=None):
+    """One inertial iteration (reading R27): the anchors of Appendix B are
+    x^{k+1/2} = x^k + theta (x^k - x^{k-1}) for x = p, q, t, s; `prev` holds
+    x^{k-1} (None: x^{-1} = x^0).  The hard case's sign still follows p^k.
+    Returns (new_state, new_prev = x^k, e^{k+1}, hard-case count)."""
+    cur = {k: np.asarray(st[k], dtype=np.float64) for k in ("p", "q", "t", "s")}
+    old = cur if prev is None else {k: np.asarray(prev[k], dtype=np.float64) for k in ("p", "q", "t", "s")}
+    anchors = {k: cur[k] + theta * (cur[k] - old[k]) for k in cur}
+    new, e_res, hard = iterate(g, params, Sigma1, Sigma2, st, anchors)
+    return new, {k: cur[k].copy() for k in cur}, e_res, hard
 
 
 def lagrangian(g, params, Sigma1, Sigma2, st):

@@ -175,3 +175,98 @@ def test_p_system_matches_iterate():
         A1, b1 = gs.p_system(g, PARAMS, S1, S2, st, i)
         x, _, _ = gs.trs_sphere(A1, b1, st["p"][i])
         np.testing.assert_allclose(x, new["p"][i], atol=1e-12)
+
+
+# ---- inertial variant (reading R27) -------------------------------------------
+
+def test_inertial_zero_theta_is_plain():
+    rng = np.random.default_rng(21)
+    g = synth.random_graph(9, 24, seed=6)
+    st = synth.random_state(rng, g.n)
+    prev = synth.random_state(rng, g.n)
+    S1, S2 = _spd(rng, 4), _spd(rng, 4)
+    a, e_a, h_a = gs.iterate(g, PARAMS, S1, S2, st)
+    b, pv, e_b, h_b = gs.iterate_inertial(g, PARAMS, S1, S2, st, 0.0, prev)
+    for key in a:
+        np.testing.assert_array_equal(a[key], b[key])
+    assert e_a == e_b and h_a == h_b
+    for key in ("p", "q", "t", "s"):
+        np.testing.assert_array_equal(pv[key], st[key])
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.8])
+def test_inertial_identity_sigma_reduces_to_the_c_oracle(theta):
+    # Sigma = I is the scalar model: two inertial iterations of this module
+    # against the C oracle's inertial iteration (pinned on its own)
+    rng = np.random.default_rng(22)
+    g = synth.random_graph(14, 40, seed=7)
+    st = synth.random_state(rng, g.n)
+    prev = {k: v for k, v in synth.random_state(rng, g.n).items() if k in ("p", "q", "t", "s")}
+    x, pv = st, prev
+    for _ in range(2):
+        x, pv, e, hard = gs.iterate_inertial(g, PARAMS, np.eye(4), np.eye(4), x, theta, pv)
+    prm = oracle.make_params(beta1=PARAMS[0], beta2=PARAMS[1], tau=PARAMS[2], gamma=PARAMS[3])
+    ref, ref_pv, res, _ = oracle.iterate_inertial(g, prm, st, theta, 2, prev)
+    for key in ("p", "q", "t", "s", "lam", "z"):
+        np.testing.assert_allclose(x[key], ref[key], rtol=1e-11, atol=1e-11)
+    for key in ("p", "q", "t", "s"):
+        np.testing.assert_allclose(pv[key], ref_pv[key], rtol=1e-11, atol=1e-11)
+    assert abs(e - res[0]) <= 1e-11 * max(res[0], 1.0)
+    assert hard == 0
+
+
+def test_inertial_blocks_minimise_around_extrapolated_anchors():
+    # each block minimises its subproblem of L_beta plus 1/2 gamma |x - a|^2,
+    # the anchor a formed here from x^k and x^{k-1}
+    rng = np.random.default_rng(23)
+    g = synth.random_graph(6, 14, seed=12)
+    st = synth.random_state(rng, g.n)
+    prev = synth.random_state(rng, g.n)
+    S1, S2 = _spd(rng, 4), _spd(rng, 4)
+    theta = 0.6
+    prm = (1.0, 1.0, 1.5, (1.0, 0.7, 0.4, 0.9))  # proximal weights large enough to see the anchors
+    _, _, _, (g1, g2, g3, g4) = prm
+    new, _, _, _ = gs.iterate_inertial(g, prm, S1, S2, st, theta, prev)
+    a = {k: st[k] + theta * (st[k] - prev[k]) for k in ("p", "q", "t", "s")}
+    L = lambda s: gs.lagrangian(g, prm, S1, S2, s)
+
+    def with_(base, **kw):
+        d = {k: v.copy() for k, v in base.items()}
+        d.update(kw)
+        return d
+
+    for i in range(g.n):
+        def fp(x):
+            p = new["p"].copy()
+            p[i] = x
+            return L(with_(st, p=p)) + 0.5 * g1 * np.sum((x - a["p"][i]) ** 2)
+        x0 = new["p"][i]
+        f0 = fp(x0)
+        X = rng.normal(size=(2000, 4))
+        X /= np.linalg.norm(X, axis=1, keepdims=True)
+        assert min(fp(x) for x in X) >= f0 - 1e-9
+        gr = _num_grad(fp, x0)
+        gr -= (gr @ x0) * x0
+        assert np.linalg.norm(gr) < 1e-5
+    fq = lambda q: L(with_(st, p=new["p"], q=q)) + 0.5 * g2 * np.sum((q - a["q"]) ** 2)
+    assert np.abs(_num_grad(fq, new["q"])).max() < 1e-5
+    ft = lambda t: L(with_(st, p=new["p"], q=new["q"], t=t)) + 0.5 * g3 * np.sum((t - a["t"]) ** 2)
+    assert np.abs(_num_grad(ft, new["t"])).max() < 1e-5
+    fs = lambda s: (L(with_(st, p=new["p"], q=new["q"], t=new["t"], s=s))
+                    + 0.5 * g4 * np.sum((s - a["s"]) ** 2))
+    assert np.abs(_num_grad(fs, new["s"])).max() < 1e-5
+
+
+def test_inertial_noise_free_truth_is_a_fixed_point_for_any_sigma():
+    rng = np.random.default_rng(24)
+    g = synth.random_walk_graph(20, n_closures=15, sigma_r=0.0, sigma_t=0.0, seed=3)
+    S1, S2 = _spd(rng, 4), _spd(rng, 4)
+    st = oracle.init_state(g.q_gt, g.t_gt)
+    x, pv = st, None
+    for _ in range(3):
+        x, pv, e, _ = gs.iterate_inertial(g, PARAMS, S1, S2, x, 0.5, pv)
+    assert e < 1e-24
+    for key in ("p", "q"):
+        np.testing.assert_allclose(x[key], g.q_gt, atol=1e-12)
+    for key in ("t", "s"):
+        np.testing.assert_allclose(x[key], g.t_gt, atol=1e-12)
