@@ -230,8 +230,9 @@ def run_batched(P, rank=0, ws=1, sample=32):
 def run_inertial(P, g, thetas=(0.0, 0.3, 0.6), lattice_iters=200):
     """Inertial variant (proximal anchors x^k + theta (x^k - x^{k-1})): solves
     of the ring and cube workloads (tau = 1.4, tol = 1e-4, at most 3000
-    iterations) for each theta, FP32; and the time per
-    iteration on the 1M-pose lattice, graph-launched, against the plain path."""
+    iterations) for each theta, FP32; and the time per iteration on the
+    1M-pose lattice, graph-launched, at theta = 0.3 against theta = 0, with
+    scalar weights and with the general weights of the general-Sigma leg."""
     from paper_2601_15684_gb300 import synth
     solves = []
     for wl in ("ring5000", "cube10"):
@@ -245,15 +246,22 @@ def run_inertial(P, g, thetas=(0.0, 0.3, 0.6), lattice_iters=200):
                 F = S.objective()
             solves.append({"workload": wl, "theta": theta, "converged": bool(conv), "iterations": int(it),
                            "e_final": e, "objective": F, "ms": 1e3 * dt})
-    per_iter = {}
+    rng = np.random.default_rng(0)
+    Q, _ = np.linalg.qr(rng.normal(size=(4, 4)))
+    sigma = (Q @ np.diag([1.0, 2.0, 0.5, 4.0]) @ Q.T, np.diag([1.0, 0.5, 2.0, 1.0]))
+    per_iter, per_iter_sig = {}, {}
     for theta in (0.0, 0.3):
-        with P.Solver(g, precision=P.PRADMM_FP32, inertia=theta) as S:
-            S.init_odometry()
-            S.step(10)
-            t0 = time.perf_counter()
-            S.step(lattice_iters)
-            per_iter[str(theta)] = 1e3 * (time.perf_counter() - t0) / lattice_iters
+        for general, out in ((False, per_iter), (True, per_iter_sig)):
+            with P.Solver(g, precision=P.PRADMM_FP32, inertia=theta) as S:
+                if general:
+                    S.set_sigma(*sigma)
+                S.init_odometry()
+                S.step(10)
+                t0 = time.perf_counter()
+                S.step(lattice_iters)
+                out[str(theta)] = 1e3 * (time.perf_counter() - t0) / lattice_iters
     return {"solves": solves, "lattice_ms_per_iteration": per_iter,
+            "lattice_general_sigma_ms_per_iteration": per_iter_sig,
             "reading": "anchors x^k + theta (x^k - x^{k-1}) for p, q, t, s (the paper leaves the rule open)"}
 
 

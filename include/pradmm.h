@@ -99,10 +99,11 @@ typedef struct {
                             anchors of p, q, t, s are x^k + theta (x^k - x^{k-1})
                             (the paper's x^{k+1/2}, Appendix B; the extrapolation
                             rule is this library's reading); 0 (default) is plain
-                            PRADMM.  A nonzero theta needs the scalar weights
-                            (no pradmm_set_sigma) and is not available in the
-                            batched form or the reverse mode; setting a state
-                            restarts the extrapolation (x^{k-1} := x^k). */
+                            PRADMM.  A nonzero theta works with scalar and
+                            general weights (pradmm_set_sigma) and is not
+                            available in the batched form or the reverse
+                            mode; setting a state or the weights restarts the
+                            extrapolation (x^{k-1} := x^k). */
 } pradmm_params;
 
 /* Defaults: beta1 = beta2 = 1, relax = 1.5, gamma = {1, 1e-3, 1e-3, 1e-3},
@@ -209,8 +210,9 @@ pradmm_status pradmm_profile_sweeps(pradmm_t h, int32_t iters, double* ms_out);
  * The q, t and s blocks solve 4x4 / 3x3 systems.  Both NULL returns to the
  * scalar model (Sigma = I).  PRADMM_ERR_ARG if only one is given or one is
  * not symmetric positive definite, PRADMM_ERR_NONFINITE for non-finite
- * entries.  Keeps the state (the next iteration recomputes p^{k+1}); the
- * reverse mode and pradmm_profile_sweeps need the scalar model. */
+ * entries.  Keeps the state (the next iteration recomputes p^{k+1}) and,
+ * with a nonzero inertia, restarts the extrapolation; the reverse mode and
+ * pradmm_profile_sweeps need the scalar model. */
 pradmm_status pradmm_set_sigma(pradmm_t h, const double* Sigma1, const double* Sigma2);
 
 /* ---- reverse mode -------------------------------------------------------------

@@ -782,6 +782,7 @@ pradmm_status set_state_dev(pradmm_s* h, const double* p, const double* q, const
         CU(cudaMemcpyAsync(b, h->q, a, cudaMemcpyDeviceToDevice, st));
         CU(cudaMemcpyAsync(b + a, h->t, a, cudaMemcpyDeviceToDevice, st));
         CU(cudaMemcpyAsync(b + 2 * a, h->s, a, cudaMemcpyDeviceToDevice, st));
+        CU(cudaMemcpyAsync(h->p[1], h->p[0], a, cudaMemcpyDeviceToDevice, st));  // p^{-1} for the general-Sigma p sweep
     }
     CU(cudaStreamSynchronize(st));
     h->state_set = true;
@@ -1481,9 +1482,26 @@ void eig3_host(const double A0[3][3], double U[9], double mu[3]) {
     }
 }
 
+// The inertial variant restarts its extrapolation (x^{k-1} := x^k) where the
+// iteration changes form: q, t, s into the previous-iterate block, and p^k
+// into the p buffer that the next p-block overwrites (the general-Sigma p
+// sweep reads p^{k-1} there; the scalar form's first p sweep recomputes it).
+pradmm_status restart_inertia(pradmm_s* h) {
+    if (!h->prev_block || !h->state_set) return PRADMM_OK;
+    ST(read_ctrl(h));
+    const long long k = h->ctrl_h->iter;
+    const size_t a = 4 * (size_t)h->n * h->rsize;
+    char* b = static_cast<char*>(h->prev_block);
+    cudaStream_t st = h->stream;
+    CU(cudaMemcpyAsync(b, h->q, a, cudaMemcpyDeviceToDevice, st));
+    CU(cudaMemcpyAsync(b + a, h->t, a, cudaMemcpyDeviceToDevice, st));
+    CU(cudaMemcpyAsync(b + 2 * a, h->s, a, cudaMemcpyDeviceToDevice, st));
+    CU(cudaMemcpyAsync(h->p[(k + 1) & 1], h->p[k & 1], a, cudaMemcpyDeviceToDevice, st));
+    CU(cudaStreamSynchronize(st));
+    return PRADMM_OK;
+}
+
 pradmm_status set_sigma_impl(pradmm_s* h, const double* S1, const double* S2) {
-    if ((S1 || S2) && h->prm.inertia != 0.0)
-        return fail(PRADMM_ERR_ARG, "general Sigma needs inertia = 0 (the inertial variant uses scalar weights)");
     if (!S1 && !S2) {
         h->general = false;
     } else {
@@ -1522,6 +1540,7 @@ pradmm_status set_sigma_impl(pradmm_s* h, const double* S1, const double* S2) {
     // the captured loops and any precomputed p^{k+1} belong to the other form
     drop_graphs(h);
     h->pending = false;
+    ST(restart_inertia(h));
     h->epoch++;
     return PRADMM_OK;
 }

@@ -344,7 +344,11 @@ __device__ int trs4(const T A0[4][4], const T b[4], const T pk[4], T x[4], bool 
 
 // ---- kernels --------------------------------------------------------------------
 
-template <typename R>
+// INERT (inertial variant): the proximal anchors are x^k + theta (x^k - x^{k-1})
+// instead of x^k.  p^{k-1} is the vertex's value in the p buffer about to
+// receive p^{k+1}; q^{k-1}, t^{k-1}, s^{k-1} are in S.qprev, S.tprev, S.sprev,
+// which each sweep overwrites with x^k after its own stores.
+template <typename R, bool INERT>
 __global__ void __launch_bounds__(256) k_p_sig(GraphDev<R> g, StateDev<R> S, Coef<R> c, SigmaDev<R> sg, Ctrl* ctrl) {
     if (ctrl->halt) return;
     const long long k = ctrl->iter;
@@ -353,8 +357,14 @@ __global__ void __launch_bounds__(256) k_p_sig(GraphDev<R> g, StateDev<R> S, Coe
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
         const Q<R> qi = asq<R>(IO<R>::ld(S.q, i)), li = asq<R>(IO<R>::ld(S.lam, i)), pk = asq<R>(IO<R>::ld(pc, i));
         const R4<R> sr = IO<R>::ld(S.s, i);
-        R A[4][4], b[4] = {-c.beta1 * qi.w - li.w - c.g1 * pk.w, -c.beta1 * qi.x - li.x - c.g1 * pk.x,
-                           -c.beta1 * qi.y - li.y - c.g1 * pk.y, -c.beta1 * qi.z - li.z - c.g1 * pk.z};
+        Q<R> pa = pk;  // the proximal anchor
+        if (INERT) {
+            const Q<R> po = asq<R>(IO<R>::ld(pn, i));  // p^{k-1}
+            pa = {pk.w + c.theta * (pk.w - po.w), pk.x + c.theta * (pk.x - po.x), pk.y + c.theta * (pk.y - po.y),
+                  pk.z + c.theta * (pk.z - po.z)};
+        }
+        R A[4][4], b[4] = {-c.beta1 * qi.w - li.w - c.g1 * pa.w, -c.beta1 * qi.x - li.x - c.g1 * pa.x,
+                           -c.beta1 * qi.y - li.y - c.g1 * pa.y, -c.beta1 * qi.z - li.z - c.g1 * pa.z};
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -573,7 +583,7 @@ __device__ __forceinline__ void chol_solve4(T A[4][4], T b[4], T x[4]) {
     }
 }
 
-template <typename R>
+template <typename R, bool INERT>
 __global__ void __launch_bounds__(256) k_q_sig(GraphDev<R> g, StateDev<R> S, Coef<R> c, SigmaDev<R> sg, Ctrl* ctrl,
                                                double* part, int pstride) {
     __shared__ double sh[32];
@@ -584,8 +594,14 @@ __global__ void __launch_bounds__(256) k_q_sig(GraphDev<R> g, StateDev<R> S, Coe
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
         const Q<R> P = asq<R>(IO<R>::ld(pn, i)), qi = asq<R>(IO<R>::ld(S.q, i)), li = asq<R>(IO<R>::ld(S.lam, i));
         const R4<R> sr = IO<R>::ld(S.s, i);
-        R A[4][4], b[4] = {c.beta1 * P.w - li.w + c.g2 * qi.w, c.beta1 * P.x - li.x + c.g2 * qi.x,
-                           c.beta1 * P.y - li.y + c.g2 * qi.y, c.beta1 * P.z - li.z + c.g2 * qi.z};
+        Q<R> qa = qi;  // the proximal anchor
+        if (INERT) {
+            const Q<R> qp = asq<R>(IO<R>::ld(S.qprev, i));
+            qa = {qi.w + c.theta * (qi.w - qp.w), qi.x + c.theta * (qi.x - qp.x), qi.y + c.theta * (qi.y - qp.y),
+                  qi.z + c.theta * (qi.z - qp.z)};
+        }
+        R A[4][4], b[4] = {c.beta1 * P.w - li.w + c.g2 * qa.w, c.beta1 * P.x - li.x + c.g2 * qa.x,
+                           c.beta1 * P.y - li.y + c.g2 * qa.y, c.beta1 * P.z - li.z + c.g2 * qa.z};
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -632,6 +648,7 @@ __global__ void __launch_bounds__(256) k_q_sig(GraphDev<R> g, StateDev<R> S, Coe
         const R ly = li.y - c.tb1 * (P.y - x[2]), lz = li.z - c.tb1 * (P.z - x[3]);
         IO<R>::st(S.q, i, x[0], x[1], x[2], x[3]);
         IO<R>::st(S.lam, i, lw, lx, ly, lz);
+        if (INERT) IO<R>::st(S.qprev, i, qi.w, qi.x, qi.y, qi.z);
         R d0 = x[0] - qi.w, d1 = x[1] - qi.x, d2 = x[2] - qi.y, d3 = x[3] - qi.z;
         adq.add(d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3);
         d0 = lw - li.w; d1 = lx - li.x; d2 = ly - li.y; d3 = lz - li.z;
@@ -665,7 +682,7 @@ __device__ __forceinline__ void solve_hat(const SigmaDev<R>& sg, R a, R cI, cons
     for (int r = 0; r < 3; ++r) x[r] = sg.U[3 * r] * y[0] + sg.U[3 * r + 1] * y[1] + sg.U[3 * r + 2] * y[2];
 }
 
-template <typename R>
+template <typename R, bool INERT>
 __global__ void __launch_bounds__(256) k_t_sig(GraphDev<R> g, StateDev<R> S, Coef<R> c, SigmaDev<R> sg, Ctrl* ctrl,
                                                double* part, int pstride) {
     __shared__ double sh[32];
@@ -675,8 +692,13 @@ __global__ void __launch_bounds__(256) k_t_sig(GraphDev<R> g, StateDev<R> S, Coe
     Acc<R> adt;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
         const R4<R> tr = IO<R>::ld(S.t, i), sr = IO<R>::ld(S.s, i), zr = IO<R>::ld(S.z, i);
-        R bv[3] = {c.beta2 * sr.a + zr.a + c.g3 * tr.a, c.beta2 * sr.b + zr.b + c.g3 * tr.b,
-                   c.beta2 * sr.c + zr.c + c.g3 * tr.c};
+        R4<R> ta = tr;  // the proximal anchor
+        if (INERT) {
+            const R4<R> tp = IO<R>::ld(S.tprev, i);
+            ta = {tr.a + c.theta * (tr.a - tp.a), tr.b + c.theta * (tr.b - tp.b), tr.c + c.theta * (tr.c - tp.c), tr.d};
+        }
+        R bv[3] = {c.beta2 * sr.a + zr.a + c.g3 * ta.a, c.beta2 * sr.b + zr.b + c.g3 * ta.b,
+                   c.beta2 * sr.c + zr.c + c.g3 * ta.c};
         R a = R(0);
         for (int e = g.in_ptr[i]; e < g.in_ptr[i + 1]; ++e) {
             const int l = g.in_idx[e];
@@ -695,6 +717,7 @@ __global__ void __launch_bounds__(256) k_t_sig(GraphDev<R> g, StateDev<R> S, Coe
         R x[3];
         solve_hat(sg, a, c.beta2 + c.g3, bv, x);
         IO<R>::st(S.t, i, x[0], x[1], x[2], tr.d);
+        if (INERT) IO<R>::st(S.tprev, i, tr.a, tr.b, tr.c, tr.d);
         const R d0 = x[0] - tr.a, d1 = x[1] - tr.b, d2 = x[2] - tr.c;
         adt.add(d0 * d0 + d1 * d1 + d2 * d2);
     }
@@ -702,7 +725,7 @@ __global__ void __launch_bounds__(256) k_t_sig(GraphDev<R> g, StateDev<R> S, Coe
     if (threadIdx.x == 0) part[SLOT_DT * pstride + blockIdx.x] = st;
 }
 
-template <typename R>
+template <typename R, bool INERT>
 __global__ void __launch_bounds__(256) k_s_sig(GraphDev<R> g, StateDev<R> S, Coef<R> c, SigmaDev<R> sg, Launch L) {
     __shared__ double sh[32];
     Ctrl* ctrl = L.ctrl;
@@ -716,8 +739,13 @@ __global__ void __launch_bounds__(256) k_s_sig(GraphDev<R> g, StateDev<R> S, Coe
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
         const R4<R> tr = IO<R>::ld(S.t, i), sr = IO<R>::ld(S.s, i), zr = IO<R>::ld(S.z, i);
         const Q<R> qi = asq<R>(IO<R>::ld(S.q, i)), P = asq<R>(IO<R>::ld(pn, i));
-        R bv[3] = {c.beta2 * tr.a - zr.a + c.g4 * sr.a, c.beta2 * tr.b - zr.b + c.g4 * sr.b,
-                   c.beta2 * tr.c - zr.c + c.g4 * sr.c};
+        R4<R> sa = sr;  // the proximal anchor
+        if (INERT) {
+            const R4<R> sp = IO<R>::ld(S.sprev, i);
+            sa = {sr.a + c.theta * (sr.a - sp.a), sr.b + c.theta * (sr.b - sp.b), sr.c + c.theta * (sr.c - sp.c), sr.d};
+        }
+        R bv[3] = {c.beta2 * tr.a - zr.a + c.g4 * sa.a, c.beta2 * tr.b - zr.b + c.g4 * sa.b,
+                   c.beta2 * tr.c - zr.c + c.g4 * sa.c};
         R a = R(0);
         for (int e = g.out_ptr[i]; e < g.out_ptr[i + 1]; ++e) {
             const R4<R> te = IO<R>::ld(g.out_te, e);
@@ -737,6 +765,7 @@ __global__ void __launch_bounds__(256) k_s_sig(GraphDev<R> g, StateDev<R> S, Coe
         const R zx = zr.a - c.tb2 * (tr.a - x[0]), zy = zr.b - c.tb2 * (tr.b - x[1]), zz = zr.c - c.tb2 * (tr.c - x[2]);
         IO<R>::st(S.s, i, x[0], x[1], x[2], sr.d);
         IO<R>::st(S.z, i, zx, zy, zz, zr.d);
+        if (INERT) IO<R>::st(S.sprev, i, sr.a, sr.b, sr.c, sr.d);
         const R d0 = zx - zr.a, d1 = zy - zr.b, d2 = zz - zr.c;
         adz.add(d0 * d0 + d1 * d1 + d2 * d2);
     }
@@ -799,11 +828,19 @@ __global__ void __launch_bounds__(256) k_objective_sig(GraphDev<R> g, StateDev<R
 template <typename R>
 cudaError_t launch_sigma_iteration(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c,
                                    const SigmaDev<R>& sg, const Launch& L) {
-    k_p_sig<R><<<L.grid_p, L.block, 0, L.stream>>>(g, s, c, sg, L.ctrl);
-    if constexpr (sizeof(R) == sizeof(float)) k_p_sig_fb<<<152, 128, 0, L.stream>>>(sg, s, L.ctrl);
-    k_q_sig<R><<<L.grid_q, L.block, 0, L.stream>>>(g, s, c, sg, L.ctrl, L.part, L.pstride);
-    k_t_sig<R><<<L.grid_t, L.block, 0, L.stream>>>(g, s, c, sg, L.ctrl, L.part, L.pstride);
-    k_s_sig<R><<<L.grid_sp, L.block, 0, L.stream>>>(g, s, c, sg, L);
+    if (c.theta != R(0)) {
+        k_p_sig<R, true><<<L.grid_p, L.block, 0, L.stream>>>(g, s, c, sg, L.ctrl);
+        if constexpr (sizeof(R) == sizeof(float)) k_p_sig_fb<<<152, 128, 0, L.stream>>>(sg, s, L.ctrl);
+        k_q_sig<R, true><<<L.grid_q, L.block, 0, L.stream>>>(g, s, c, sg, L.ctrl, L.part, L.pstride);
+        k_t_sig<R, true><<<L.grid_t, L.block, 0, L.stream>>>(g, s, c, sg, L.ctrl, L.part, L.pstride);
+        k_s_sig<R, true><<<L.grid_sp, L.block, 0, L.stream>>>(g, s, c, sg, L);
+    } else {
+        k_p_sig<R, false><<<L.grid_p, L.block, 0, L.stream>>>(g, s, c, sg, L.ctrl);
+        if constexpr (sizeof(R) == sizeof(float)) k_p_sig_fb<<<152, 128, 0, L.stream>>>(sg, s, L.ctrl);
+        k_q_sig<R, false><<<L.grid_q, L.block, 0, L.stream>>>(g, s, c, sg, L.ctrl, L.part, L.pstride);
+        k_t_sig<R, false><<<L.grid_t, L.block, 0, L.stream>>>(g, s, c, sg, L.ctrl, L.part, L.pstride);
+        k_s_sig<R, false><<<L.grid_sp, L.block, 0, L.stream>>>(g, s, c, sg, L);
+    }
     return cudaGetLastError();
 }
 
