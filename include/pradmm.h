@@ -100,9 +100,10 @@ typedef struct {
                             (the paper's x^{k+1/2}, Appendix B; the extrapolation
                             rule is this library's reading); 0 (default) is plain
                             PRADMM.  A nonzero theta works with scalar and
-                            general weights (pradmm_set_sigma) and is not
-                            available in the batched form or the reverse
-                            mode; setting a state or the weights restarts the
+                            general weights (pradmm_set_sigma) and in the
+                            batched form (each pradmm_batch_solve starts the
+                            extrapolation afresh), not in the reverse mode;
+                            setting a state or the weights restarts the
                             extrapolation (x^{k-1} := x^k). */
 } pradmm_params;
 
@@ -312,7 +313,8 @@ typedef struct pradmm_batch_s* pradmm_batch_t;
 /* G graphs; graph g has n_g[g] >= 1 vertices and m_g[g] >= 0 edges.  Edge
  * arrays are concatenated in graph order with GRAPH-LOCAL endpoints in
  * [0, n_g[g]); layouts and validation as pradmm_create.  The schedule starts
- * at block 256, warp_max_n 256, no clusters. */
+ * at block 256, warp_max_n 256, no clusters.  prm->inertia applies to every
+ * graph (the inertial variant; each solve starts with x^{-1} = x^0). */
 pradmm_status pradmm_batch_create(int32_t G, const int64_t* n_g, const int64_t* m_g, const int32_t* src,
                                   const int32_t* dst, const double* q_meas, const double* t_meas,
                                   const double* kappa, const double* omega, const pradmm_params* prm,

@@ -20,11 +20,11 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libpradmm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["pradmm_kernels.cu", "pradmm_batch.cu", "pradmm_adjoint.cu", "pradmm_sigma.cu", "pradmm_noalloc.cu",
-              "pradmm_setup.cu"]
+CU_SOURCES = ["pradmm_kernels.cu", "pradmm_batch.cu", "pradmm_batch_inert.cu", "pradmm_adjoint.cu", "pradmm_sigma.cu",
+              "pradmm_noalloc.cu", "pradmm_setup.cu"]
 CPP_SOURCES = ["pradmm_api.cpp"]
 HEADERS = [os.path.join(CSRC, "pradmm_internal.h"), os.path.join(CSRC, "pradmm_device.cuh"),
-           os.path.join(INCLUDE, "pradmm.h")]
+           os.path.join(CSRC, "pradmm_batch.cuh"), os.path.join(INCLUDE, "pradmm.h")]
 
 
 def _cuda_home() -> str:

@@ -1899,12 +1899,19 @@ pradmm_status batch_schedule(pradmm_batch_s* b, int block, int warp_max_n, int c
     b->cluster_min_n = cluster_min_n;
     if (cluster > 1) {
         int clusters = 0;
-        CU(h->fp64 ? pradmm::batch_cluster_occupancy<double>(block, cluster, &clusters)
-                   : pradmm::batch_cluster_occupancy<float>(block, cluster, &clusters));
+        const bool in = h->prm.inertia != 0.0;
+        CU(h->fp64 ? (in ? pradmm::batch_cluster_occupancy<double, true>(block, cluster, &clusters)
+                         : pradmm::batch_cluster_occupancy<double, false>(block, cluster, &clusters))
+                   : (in ? pradmm::batch_cluster_occupancy<float, true>(block, cluster, &clusters)
+                         : pradmm::batch_cluster_occupancy<float, false>(block, cluster, &clusters)));
         if (clusters < 1) return fail(PRADMM_ERR_ARG, "no cluster of %d CTAs of %d threads fits the GPU", cluster, block);
         b->grid = clusters * cluster;
     } else {
-        CU(h->fp64 ? pradmm::batch_occupancy<double>(block, &bps) : pradmm::batch_occupancy<float>(block, &bps));
+        const bool in = h->prm.inertia != 0.0;
+        CU(h->fp64 ? (in ? pradmm::batch_occupancy<double, true>(block, &bps)
+                         : pradmm::batch_occupancy<double, false>(block, &bps))
+                   : (in ? pradmm::batch_occupancy<float, true>(block, &bps)
+                         : pradmm::batch_occupancy<float, false>(block, &bps)));
         b->grid = std::max(1, std::min(b->n_items, sms * std::max(bps, 1)));
     }
     return PRADMM_OK;
@@ -1940,8 +1947,9 @@ pradmm_status batch_run(pradmm_batch_s* b, double rel_tol, double abs_tol, int m
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e1 = pradmm::launch_batch<R>(h->gdev<R>(), h->sdev<R>(), h->coef<R>(), d, h->ctrl, b->grid, b->block,
-                                             b->cluster, h->stream);
+    const auto launch = h->prm.inertia != 0.0 ? pradmm::launch_batch<R, true> : pradmm::launch_batch<R, false>;
+    cudaError_t e1 = launch(h->gdev<R>(), h->sdev<R>(), h->coef<R>(), d, h->ctrl, b->grid, b->block, b->cluster,
+                            h->stream);
     cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
     CU(e1);
     CU(e2);
@@ -1969,7 +1977,6 @@ pradmm_status pradmm_batch_create(int32_t G, const int64_t* n_g, const int64_t* 
     if (!out) return fail(PRADMM_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (G < 1 || !n_g || !m_g) return fail(PRADMM_ERR_ARG, "need G >= 1 and the size arrays");
-    if (prm && prm->inertia != 0.0) return fail(PRADMM_ERR_ARG, "the batched form needs inertia = 0");
     try {
         pradmm_batch_s* b = new pradmm_batch_s();
         b->G = G;

@@ -232,12 +232,13 @@ struct BatchDev {
 };
 
 // cluster > 1: the cluster kernel (grid a multiple of cluster); 1: k_batch.
-template <typename R>
+// INERT: the inertial variant (S.qprev, S.tprev, S.sprev set; c.theta != 0).
+template <typename R, bool INERT>
 cudaError_t launch_batch(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const BatchDev& b,
                          Ctrl* ctrl, int grid, int block, int cluster, cudaStream_t st);
-template <typename R>
+template <typename R, bool INERT>
 cudaError_t batch_occupancy(int block, int* bps);
-template <typename R>
+template <typename R, bool INERT>
 cudaError_t batch_cluster_occupancy(int block, int cluster, int* clusters);
 template <typename R>
 cudaError_t launch_batch_objective(const GraphDev<R>& g, const StateDev<R>& s, const double* qe64,

@@ -130,11 +130,6 @@ def test_inertia_is_rejected_where_unsupported(P):
         with pytest.raises(P.PRADMMError) as ei:
             S.adjoint_record(5, 1)
         assert ei.value.status == P.PRADMM_ERR_ARG
-    prm = P.pradmm_default_params()
-    prm.inertia = 0.4
-    with pytest.raises(P.PRADMMError) as ei:
-        P.Batch([g, g], params=prm)
-    assert ei.value.status == P.PRADMM_ERR_ARG
 
 
 def _spd(rng, cond=8.0):
@@ -213,3 +208,60 @@ def test_setting_sigma_restarts_the_extrapolation(P):
         assert relerr(b[k], orc[k]) <= 1e-9, ("general", k, relerr(b[k], orc[k]))
     orc, _, _, _ = oracle.iterate_inertial(g, _oparams(), b, theta, 2)
     check_state(c, orc, True, "scalar again")
+
+
+def _walks(count, seed, n_max):
+    rng = np.random.default_rng(seed)
+    ns = np.exp(rng.uniform(np.log(20), np.log(n_max), count)).round().astype(int)
+    dens = rng.uniform(0.5, 3.0, count)
+    return [synth.random_walk_graph(int(ns[k]), n_closures=None, closure_density=float(dens[k]), sigma_r=0.02,
+                                    sigma_t=0.1, seed=2000 + k, name=f"w{k}") for k in range(count)]
+
+
+@pytest.mark.parametrize("schedule", [(256, 256, 1, 0), (128, 0, 8, 50)])
+def test_batch_inertial_matches_oracle_graph_by_graph(P, schedule):
+    # every graph of the batch runs its own inertial iteration (warp, CTA or
+    # cluster groups) and stops by the batch's relative rule; a second solve
+    # starts the extrapolation afresh from the first one's result
+    graphs = _walks(6, seed=11, n_max=400)
+    theta = 0.4
+    with P.Batch(graphs, precision=0, inertia=theta) as B:
+        B.set_schedule(*schedule)
+        B.init_odometry()
+        res = B.solve(rel_tol=1e-3, max_iter=60)
+        first = B.state()
+        B.solve(rel_tol=0.0, max_iter=5)
+        second = B.state()
+    for k, g in enumerate(graphs):
+        q0, t0 = oracle.init_odometry(g)
+        orc, _, _, _ = oracle.iterate_inertial(g, _oparams(), oracle.init_state(q0, t0), theta, int(res["iters"][k]))
+        sl = {key: v[B.offsets[k]:B.offsets[k + 1]] for key, v in first.items()}
+        check_state(sl, orc, True, f"graph {k}")
+        orc, _, _, _ = oracle.iterate_inertial(g, _oparams(), sl, theta, 5)
+        sl2 = {key: v[B.offsets[k]:B.offsets[k + 1]] for key, v in second.items()}
+        check_state(sl2, orc, True, f"graph {k}, second solve")
+    conv = res["status"] == P.PRADMM_OK
+    assert (res["e_last"][conv] <= 1e-3 * res["e_first"][conv]).all()
+
+
+def test_batch_inertial_fp32_matches_single_solver(P):
+    graphs = _walks(10, seed=12, n_max=2500)
+    theta = 0.3
+    with P.Batch(graphs, precision=1, inertia=theta) as B:
+        B.init_odometry()
+        B.solve(rel_tol=0.0, max_iter=20)
+        st = B.state()
+    for k, g in enumerate(graphs):
+        with P.Solver(g, precision=1, inertia=theta) as S:
+            S.init_odometry()
+            S.step(20)
+            ref = S.state()
+        sl = {key: v[B.offsets[k]:B.offsets[k + 1]] for key, v in st.items()}
+        # p, q, t, s at 1e-5; the multipliers are running sums of one rounded
+        # increment per iteration: 1e-5 sqrt(iterations) of the scale they are
+        # formed from (the batched form's tolerance)
+        for key in ("p", "q", "t", "s"):
+            assert relerr(sl[key], ref[key]) <= 1e-5, (k, key, relerr(sl[key], ref[key]))
+        grow = np.sqrt(20.0)
+        assert np.linalg.norm(sl["lam"] - ref["lam"]) <= 1e-5 * grow * 1.5 * max(np.linalg.norm(ref["p"]), 1.0), k
+        assert np.linalg.norm(sl["z"] - ref["z"]) <= 1e-5 * grow * 1.5 * max(np.linalg.norm(ref["t"]), 1.0), k
