@@ -143,6 +143,15 @@ pradmm_status pradmm_set_state(pradmm_t h, const double* q, const double* t);
 pradmm_status pradmm_set_state_full(pradmm_t h, const double* p, const double* q, const double* t,
                                     const double* s, const double* lam, const double* z);
 
+/* pradmm_set_state_full from device arrays (double, same shapes; lam and z
+ * may be NULL for zero multipliers).  The arrays are read on the handle's
+ * stream, so the caller's writes must be complete or ordered before the
+ * call; they are copied, not kept.  Finiteness is not checked on the host: a
+ * non-finite entry surfaces as PRADMM_ERR_NONFINITE from the next iteration.
+ * Like every state set, it restarts the inertial extrapolation. */
+pradmm_status pradmm_set_state_full_device(pradmm_t h, const double* p_d, const double* q_d, const double* t_d,
+                                           const double* s_d, const double* lam_d, const double* z_d);
+
 /* Initial poses by odometry composition along a spanning forest: edges are
  * taken in input order, an edge joins the forest when it links two
  * components, the lowest vertex of each component gets the identity, and the

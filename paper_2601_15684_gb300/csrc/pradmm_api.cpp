@@ -1638,6 +1638,12 @@ pradmm_status pradmm_set_state_full(pradmm_t h, const double* p, const double* q
     return set_state_any(h, p, q, t, s, lam, z, false);
 }
 
+pradmm_status pradmm_set_state_full_device(pradmm_t h, const double* p_d, const double* q_d, const double* t_d,
+                                           const double* s_d, const double* lam_d, const double* z_d) {
+    if (!h || !p_d || !q_d || !t_d || !s_d) return fail(PRADMM_ERR_ARG, "NULL argument (p, q, t, s are required)");
+    return set_state_any(h, p_d, q_d, t_d, s_d, lam_d, z_d, true);
+}
+
 pradmm_status pradmm_init_odometry(pradmm_t h) {
     if (!h) return fail(PRADMM_ERR_ARG, "NULL handle");
     try {

@@ -64,6 +64,8 @@ _SIGS = {
                                             _P(pradmm_params), ctypes.c_void_p, _P(ctypes.c_void_p)]),
     "pradmm_set_state": (ctypes.c_int, [_h, _d, _d]),
     "pradmm_set_state_full": (ctypes.c_int, [_h, _d, _d, _d, _d, _d, _d]),
+    "pradmm_set_state_full_device": (ctypes.c_int, [_h, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pradmm_init_odometry": (ctypes.c_int, [_h]),
     "pradmm_step": (ctypes.c_int, [_h, ctypes.c_int32, _d]),
     "pradmm_solve": (ctypes.c_int, [_h, _i32, _d]),
@@ -188,6 +190,14 @@ def pradmm_set_state_full(h, st: dict, n):
     a = {k: _f64(st[k], (n, 4) if k in ("p", "q", "lam") else (n, 3)) for k in ("p", "q", "t", "s", "lam", "z")}
     _check(load().pradmm_set_state_full(h, _dp(a["p"]), _dp(a["q"]), _dp(a["t"]), _dp(a["s"]), _dp(a["lam"]),
                                         _dp(a["z"])), "pradmm_set_state_full")
+
+
+def pradmm_set_state_full_device(h, p, q, t, s, lam=0, z=0):
+    """Device-pointer variant of pradmm_set_state_full (addresses of FP64
+    device arrays, e.g. torch tensors' data_ptr(); lam, z may be 0)."""
+    _check(load().pradmm_set_state_full_device(h, ctypes.c_void_p(p), ctypes.c_void_p(q), ctypes.c_void_p(t),
+                                               ctypes.c_void_p(s), ctypes.c_void_p(lam or 0),
+                                               ctypes.c_void_p(z or 0)), "pradmm_set_state_full_device")
 
 
 def pradmm_init_odometry(h):
@@ -375,6 +385,19 @@ class Solver:
 
     def set_state_full(self, st):
         pradmm_set_state_full(self.h, st, self.n)
+
+    def set_state_device(self, p, q, t, s, lam=None, z=None):
+        """Full state from CUDA float64 tensors (n x 4 for p, q, lam; n x 3 for
+        t, s, z; contiguous); the caller's stream must have finished writing them."""
+        def ptr(x, width, name, optional=False):
+            if x is None and optional:
+                return 0
+            if (x is None or not x.is_cuda or x.dtype.itemsize != 8 or not x.dtype.is_floating_point
+                    or not x.is_contiguous() or tuple(x.shape) != (self.n, width)):
+                raise ValueError(f"{name}: need a contiguous CUDA float64 tensor of shape ({self.n}, {width})")
+            return x.data_ptr()
+        pradmm_set_state_full_device(self.h, ptr(p, 4, "p"), ptr(q, 4, "q"), ptr(t, 3, "t"), ptr(s, 3, "s"),
+                                     ptr(lam, 4, "lam", True), ptr(z, 3, "z", True))
 
     def init_odometry(self):
         pradmm_init_odometry(self.h)
