@@ -70,6 +70,9 @@ def lib():
             L.orc_adjoint.restype = ctypes.c_int
             L.orc_adjoint.argtypes = [i64, i64, i32, i32, d, d, d, d, P(Params), i64, d, d, d, d, d, d, d, d,
                                       d, d, d, d, d, d, d]
+            L.orc_adjoint_inertial.restype = ctypes.c_int
+            L.orc_adjoint_inertial.argtypes = [i64, i64, i32, i32, d, d, d, d, P(Params), ctypes.c_double, i64,
+                                               d, d, d, d, d, d, d, d, d, d, d, d, d, d, d]
             L.orc_qmul.restype = None
             L.orc_qmul.argtypes = [d, d, d]
             L.orc_qrotate.restype = None
@@ -197,6 +200,32 @@ def adjoint(g, params: Params, state: dict, iters: int, p_bar, t_bar):
                            _d(out["q_meas"]), _d(out["t_meas"]), _d(out["kappa"]), _d(out["omega"]), _d(x0))
     if rc != 0:
         raise MemoryError("oracle adjoint")
+    sizes = (("p", 4), ("q", 4), ("t", 3), ("s", 3), ("lam", 4), ("z", 3))
+    o, x0d = 0, {}
+    for key, w in sizes:
+        x0d[key] = x0[o:o + w * n].reshape(n, w)
+        o += w * n
+    out["x0"] = x0d
+    return out
+
+
+def adjoint_inertial(g, params: Params, state: dict, iters: int, theta: float, p_bar, t_bar):
+    """adjoint() for the inertial iteration (reading R27) started with
+    x^{-1} = x^0: the gradients of L(p^K, t^K) through `iters` inertial
+    iterations with anchors x^k + theta (x^k - x^{k-1}).  Same outputs."""
+    n, m = g.n, g.m
+    st = copy_state(state)
+    keep, a = _graph_args(g)
+    pb, tb = _f64(p_bar), _f64(t_bar)
+    out = {"p": np.zeros((n, 4)), "t": np.zeros((n, 3)), "q_meas": np.zeros((m, 4)), "t_meas": np.zeros((m, 3)),
+           "kappa": np.zeros(m), "omega": np.zeros(m)}
+    x0 = np.zeros(21 * n)
+    rc = lib().orc_adjoint_inertial(*a, ctypes.byref(params), float(theta), int(iters), _d(st["p"]), _d(st["q"]),
+                                    _d(st["t"]), _d(st["s"]), _d(st["lam"]), _d(st["z"]), _d(pb), _d(tb),
+                                    _d(out["p"]), _d(out["t"]), _d(out["q_meas"]), _d(out["t_meas"]),
+                                    _d(out["kappa"]), _d(out["omega"]), _d(x0))
+    if rc != 0:
+        raise MemoryError("oracle adjoint_inertial")
     sizes = (("p", 4), ("q", 4), ("t", 3), ("s", 3), ("lam", 4), ("z", 3))
     o, x0d = 0, {}
     for key, w in sizes:

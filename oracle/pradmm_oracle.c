@@ -518,16 +518,24 @@ static void qadd(double* a, const double* b, double s) {
     for (int k = 0; k < 4; ++k) a[k] += s * b[k];
 }
 
-int orc_iterate_adjoint(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const double* qe,
-                        const double* te, const double* kappa, const double* omega, const orc_params* prm,
-                        const double* p, const double* q, const double* t, const double* s, const double* lam,
-                        const double* z, const double* pb1, const double* qb1, const double* tb1,
-                        const double* sb1, const double* lb1, const double* zb1, double* pb, double* qb,
-                        double* tb, double* sb, double* lb, double* zb, double* qeb, double* teb, double* kab,
-                        double* omb) {
+/* The reverse mode of one iteration as above, with proximal anchors ap, aq,
+ * at, as in place of x^k (the forward is iterate_anchored), formed as x^k + theta (x^k - x^{k-1}) (reading R27):
+ * each gamma term's adjoint goes (1 + theta) to x^k and -theta to x^{k-1},
+ * the latter written to ppb, qpb, tpb, spb (overwritten; NULL when theta is
+ * 0, where the anchors are x^k and this is orc_iterate_adjoint). */
+static int iterate_adjoint_anchored(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const double* qe,
+                                    const double* te, const double* kappa, const double* omega,
+                                    const orc_params* prm, const double* p, const double* q, const double* t,
+                                    const double* s, const double* lam, const double* z, const double* ap,
+                                    const double* aq, const double* at, const double* as, double theta,
+                                    const double* pb1, const double* qb1, const double* tb1, const double* sb1,
+                                    const double* lb1, const double* zb1, double* pb, double* qb, double* tb,
+                                    double* sb, double* lb, double* zb, double* ppb, double* qpb, double* tpb,
+                                    double* spb, double* qeb, double* teb, double* kab, double* omb) {
     const double b1 = prm->beta1, b2 = prm->beta2, tau = prm->tau;
     const double g1 = prm->gamma[0], g2 = prm->gamma[1], g3 = prm->gamma[2], g4 = prm->gamma[3];
-    /* forward intermediates, recomputed exactly as orc_iterate does */
+    const double cur = 1.0 + theta, prv = -theta; /* d anchor / d x^k, d anchor / d x^{k-1} */
+    /* forward intermediates, recomputed exactly as the forward does */
     double* P = (double*)malloc(sizeof(double) * (size_t)(4 * n + 1));
     double* Qn = (double*)malloc(sizeof(double) * (size_t)(4 * n + 1));
     double* Tn = (double*)malloc(sizeof(double) * (size_t)(3 * n + 1));
@@ -562,13 +570,13 @@ int orc_iterate_adjoint(int64_t n, int64_t m, const int32_t* src, const int32_t*
     memcpy(Sn, s, sizeof(double) * (size_t)(3 * n));
     memcpy(L, lam, sizeof(double) * (size_t)(4 * n));
     memcpy(Z, z, sizeof(double) * (size_t)(3 * n));
-    if (orc_iterate(n, m, src, dst, qe, te, kappa, omega, prm, P, Qn, Tn, Sn, L, Z, NULL) < 0) {
+    if (iterate_anchored(n, m, src, dst, qe, te, kappa, omega, prm, P, Qn, Tn, Sn, L, Z, ap, aq, at, as, NULL) < 0) {
         rc = -1;
         goto out;
     }
-    /* u and |u| of the p-block (same order of operations as orc_iterate) */
+    /* u and |u| of the p-block (same order of operations as the forward) */
     for (int64_t i = 0; i < n; ++i)
-        for (int k = 0; k < 4; ++k) u[4 * i + k] = b1 * q[4 * i + k] + lam[4 * i + k] + g1 * p[4 * i + k];
+        for (int k = 0; k < 4; ++k) u[4 * i + k] = b1 * q[4 * i + k] + lam[4 * i + k] + g1 * ap[4 * i + k];
     for (int64_t e = 0; e < m; ++e) {
         int64_t i = src[e], j = dst[e];
         double r[4], rc_[4], tp[4], a[4], v[4];
@@ -631,7 +639,8 @@ int orc_iterate_adjoint(int64_t n, int64_t m, const int32_t* src, const int32_t*
             a4b -= gs[3 * i + k] * Sn[3 * i + k];
             tba[3 * i + k] += b2 * gs[3 * i + k];
             zb[3 * i + k] -= gs[3 * i + k];
-            sb[3 * i + k] += g4 * gs[3 * i + k];
+            sb[3 * i + k] += cur * g4 * gs[3 * i + k];
+            if (spb) spb[3 * i + k] = prv * g4 * gs[3 * i + k];
         }
         a4[i] = a4b; /* reuse: adjoint of A_4 */
     }
@@ -653,7 +662,8 @@ int orc_iterate_adjoint(int64_t n, int64_t m, const int32_t* src, const int32_t*
             a3b -= gt[3 * i + k] * Tn[3 * i + k];
             sb[3 * i + k] += b2 * gt[3 * i + k];
             zb[3 * i + k] += gt[3 * i + k];
-            tb[3 * i + k] += g3 * gt[3 * i + k];
+            tb[3 * i + k] += cur * g3 * gt[3 * i + k];
+            if (tpb) tpb[3 * i + k] = prv * g3 * gt[3 * i + k];
         }
         a3[i] = a3b;
     }
@@ -697,7 +707,8 @@ int orc_iterate_adjoint(int64_t n, int64_t m, const int32_t* src, const int32_t*
             a2b -= gq[4 * i + k] * Qn[4 * i + k];
             pba[4 * i + k] += b1 * gq[4 * i + k];
             lb[4 * i + k] -= gq[4 * i + k];
-            qb[4 * i + k] += g2 * gq[4 * i + k];
+            qb[4 * i + k] += cur * g2 * gq[4 * i + k];
+            if (qpb) qpb[4 * i + k] = prv * g2 * gq[4 * i + k];
         }
         a2[i] = a2b;
     }
@@ -762,7 +773,8 @@ int orc_iterate_adjoint(int64_t n, int64_t m, const int32_t* src, const int32_t*
         for (int k = 0; k < 4; ++k) {
             qb[4 * i + k] += b1 * ub[4 * i + k];
             lb[4 * i + k] += ub[4 * i + k];
-            pb[4 * i + k] += g1 * ub[4 * i + k];
+            pb[4 * i + k] += cur * g1 * ub[4 * i + k];
+            if (ppb) ppb[4 * i + k] = prv * g1 * ub[4 * i + k];
         }
     }
     for (int64_t e = 0; e < m; ++e) {
@@ -814,6 +826,18 @@ out:
     free(P); free(Qn); free(Tn); free(Sn); free(L); free(Z); free(u); free(nu); free(a2); free(a3); free(a4);
     free(c); free(pba); free(qba); free(tba); free(sba); free(cb); free(gs); free(gt); free(gq); free(ub);
     return rc;
+}
+
+int orc_iterate_adjoint(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const double* qe,
+                        const double* te, const double* kappa, const double* omega, const orc_params* prm,
+                        const double* p, const double* q, const double* t, const double* s, const double* lam,
+                        const double* z, const double* pb1, const double* qb1, const double* tb1,
+                        const double* sb1, const double* lb1, const double* zb1, double* pb, double* qb,
+                        double* tb, double* sb, double* lb, double* zb, double* qeb, double* teb, double* kab,
+                        double* omb) {
+    return iterate_adjoint_anchored(n, m, src, dst, qe, te, kappa, omega, prm, p, q, t, s, lam, z, p, q, t, s, 0.0,
+                                    pb1, qb1, tb1, sb1, lb1, zb1, pb, qb, tb, sb, lb, zb, NULL, NULL, NULL, NULL,
+                                    qeb, teb, kab, omb);
 }
 
 /* Gradient of a terminal loss through `iters` iterations of Algorithm 1 from
@@ -878,5 +902,93 @@ int orc_adjoint(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, co
 out:
     free(tape);
     free(bar);
+    return rc;
+}
+
+/* orc_adjoint for the inertial iteration (orc_iterate_inertial, reading R27)
+ * started with x^{-1} = x^0.  Iteration k reads x^k and x^{k-1} (through
+ * its anchors), so the reverse pass carries, besides the adjoint of x^{k+1},
+ * the share of x^k's adjoint that iteration k+1 produced through its anchors
+ * (p, q, t, s); x^{-1} is x^0, so the last such share joins x0b.  Arguments
+ * and outputs as orc_adjoint, plus theta. */
+int orc_adjoint_inertial(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const double* qe,
+                         const double* te, const double* kappa, const double* omega, const orc_params* prm,
+                         double theta, int64_t iters, const double* p0, const double* q0, const double* t0,
+                         const double* s0, const double* lam0, const double* z0, const double* pbK,
+                         const double* tbK, double* pK, double* tK, double* qeb, double* teb, double* kab,
+                         double* omb, double* x0b) {
+    const int64_t W = 21 * n;
+    const int64_t off[6] = {0, 4 * n, 8 * n, 11 * n, 14 * n, 18 * n};
+    double* tape = (double*)malloc(sizeof(double) * (size_t)(W * (iters + 1) + 1));
+    double* bar = (double*)calloc((size_t)(2 * W + 1), sizeof(double));
+    double* pend = (double*)calloc((size_t)(W + 1), sizeof(double)); /* p, q, t, s parts used */
+    double* prev = (double*)calloc((size_t)(W + 1), sizeof(double));
+    double* anc = (double*)malloc(sizeof(double) * (size_t)(W + 1));
+    int rc = 0;
+    if (!tape || !bar || !pend || !prev || !anc) {
+        rc = -1;
+        goto out;
+    }
+    memcpy(tape + off[0], p0, sizeof(double) * (size_t)(4 * n));
+    memcpy(tape + off[1], q0, sizeof(double) * (size_t)(4 * n));
+    memcpy(tape + off[2], t0, sizeof(double) * (size_t)(3 * n));
+    memcpy(tape + off[3], s0, sizeof(double) * (size_t)(3 * n));
+    memcpy(tape + off[4], lam0, sizeof(double) * (size_t)(4 * n));
+    memcpy(tape + off[5], z0, sizeof(double) * (size_t)(3 * n));
+    memcpy(prev, tape, sizeof(double) * (size_t)W); /* x^{-1} = x^0 */
+    for (int64_t k = 0; k < iters; ++k) {
+        double* x = tape + W * (k + 1);
+        memcpy(x, tape + W * k, sizeof(double) * (size_t)W);
+        if (orc_iterate_inertial(n, m, src, dst, qe, te, kappa, omega, prm, theta, x + off[0], x + off[1],
+                                 x + off[2], x + off[3], x + off[4], x + off[5], prev + off[0], prev + off[1],
+                                 prev + off[2], prev + off[3], NULL) < 0) {
+            rc = -1;
+            goto out;
+        }
+    }
+    if (pK) memcpy(pK, tape + W * iters + off[0], sizeof(double) * (size_t)(4 * n));
+    if (tK) memcpy(tK, tape + W * iters + off[2], sizeof(double) * (size_t)(3 * n));
+    memset(qeb, 0, sizeof(double) * (size_t)(4 * m));
+    memset(teb, 0, sizeof(double) * (size_t)(3 * m));
+    memset(kab, 0, sizeof(double) * (size_t)m);
+    memset(omb, 0, sizeof(double) * (size_t)m);
+    memcpy(bar + off[0], pbK, sizeof(double) * (size_t)(4 * n));
+    memcpy(bar + off[2], tbK, sizeof(double) * (size_t)(3 * n));
+    for (int64_t k = iters - 1; k >= 0; --k) {
+        const double* x = tape + W * k;
+        const double* xp = tape + W * (k > 0 ? k - 1 : 0);
+        /* the anchors of iteration k, formed as the forward forms them */
+        for (int64_t j = 0; j < 4 * n; ++j) {
+            anc[off[0] + j] = x[off[0] + j] + theta * (x[off[0] + j] - xp[off[0] + j]);
+            anc[off[1] + j] = x[off[1] + j] + theta * (x[off[1] + j] - xp[off[1] + j]);
+        }
+        for (int64_t j = 0; j < 3 * n; ++j) {
+            anc[off[2] + j] = x[off[2] + j] + theta * (x[off[2] + j] - xp[off[2] + j]);
+            anc[off[3] + j] = x[off[3] + j] + theta * (x[off[3] + j] - xp[off[3] + j]);
+        }
+        double *a1 = bar, *a0 = bar + W;
+        if (iterate_adjoint_anchored(n, m, src, dst, qe, te, kappa, omega, prm, x + off[0], x + off[1], x + off[2],
+                                     x + off[3], x + off[4], x + off[5], anc + off[0], anc + off[1], anc + off[2],
+                                     anc + off[3], theta, a1 + off[0], a1 + off[1], a1 + off[2], a1 + off[3],
+                                     a1 + off[4], a1 + off[5], a0 + off[0], a0 + off[1], a0 + off[2], a0 + off[3],
+                                     a0 + off[4], a0 + off[5], prev + off[0], prev + off[1], prev + off[2],
+                                     prev + off[3], qeb, teb, kab, omb) < 0) {
+            rc = -1;
+            goto out;
+        }
+        /* adjoint of x^k: this iteration's share plus iteration k+1's anchor share */
+        for (int64_t j = 0; j < 14 * n; ++j) a0[j] += pend[j];
+        memcpy(pend, prev, sizeof(double) * (size_t)(14 * n));
+        memcpy(a1, a0, sizeof(double) * (size_t)W);
+    }
+    /* x^{-1} is x^0 */
+    for (int64_t j = 0; j < 14 * n; ++j) bar[j] += pend[j];
+    if (x0b) memcpy(x0b, bar, sizeof(double) * (size_t)W);
+out:
+    free(tape);
+    free(bar);
+    free(pend);
+    free(prev);
+    free(anc);
     return rc;
 }

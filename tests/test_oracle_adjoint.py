@@ -141,3 +141,71 @@ def test_adjoint_of_zero_iterations_is_the_cotangent(case):
     np.testing.assert_array_equal(res["x0"]["t"], b)
     for key in ("q", "s", "lam", "z"):
         assert not res["x0"][key].any()
+
+
+# ---- the inertial iteration (reading R27) ----------------------------------------
+
+def _linear_inertial(g, prm, st, K, theta, a, b):
+    x, _, _, _ = oracle.iterate_inertial(g, prm, st, theta, K)
+    return float((a * x["p"]).sum() + (b * x["t"]).sum())
+
+
+@pytest.fixture(scope="module")
+def icase():
+    # proximal weights large enough that the anchors carry weight
+    g = synth.random_graph(14, 36, seed=12)
+    st = synth.random_state(np.random.default_rng(6), g.n)
+    prm = oracle.make_params(beta1=1.0, beta2=1.0, tau=1.5, gamma=(1.0, 0.6, 0.5, 0.7))
+    rng = np.random.default_rng(22)
+    a, b = rng.normal(size=(g.n, 4)), rng.normal(size=(g.n, 3))
+    return g, st, prm, a, b
+
+
+def test_inertial_adjoint_with_zero_theta_is_the_plain_adjoint(icase):
+    g, st, prm, a, b = icase
+    r0 = oracle.adjoint(g, prm, st, 6, a, b)
+    r1 = oracle.adjoint_inertial(g, prm, st, 6, 0.0, a, b)
+    for key in ("p", "t", "q_meas", "t_meas", "kappa", "omega"):
+        np.testing.assert_array_equal(r0[key], r1[key])
+    for key in KEYS:
+        np.testing.assert_array_equal(r0["x0"][key], r1["x0"][key])
+
+
+@pytest.mark.parametrize("theta", [0.4, 0.8])
+def test_inertial_adjoint_matches_central_differences_on_measurements(icase, theta):
+    g, st, prm, a, b = icase
+    K = 7
+    res = oracle.adjoint_inertial(g, prm, st, K, theta, a, b)
+    rng = np.random.default_rng(15)
+    fd, ad = [], []
+    for key in ("q_meas", "t_meas", "kappa", "omega"):
+        shape = getattr(g, key).shape
+        for _ in range(12):
+            idx = tuple(int(rng.integers(0, s)) for s in shape)
+            fd.append(_fd_measurement(g, key, idx, lambda gg: _linear_inertial(gg, prm, st, K, theta, a, b)))
+            ad.append(res[key][idx])
+    fd, ad = np.array(fd), np.array(ad)
+    assert np.linalg.norm(fd - ad) <= 1e-6 * np.linalg.norm(ad)
+    assert np.abs(fd - ad).max() <= 1e-6 * np.abs(ad).max()
+    x, _, _, _ = oracle.iterate_inertial(g, prm, st, theta, K)
+    np.testing.assert_array_equal(res["p"], x["p"])
+    np.testing.assert_array_equal(res["t"], x["t"])
+
+
+def test_inertial_adjoint_matches_central_differences_on_initial_state(icase):
+    # x^0 enters twice (as x^0 and as x^{-1}); the adjoint holds both shares
+    g, st, prm, a, b = icase
+    K, theta = 5, 0.6
+    res = oracle.adjoint_inertial(g, prm, st, K, theta, a, b)
+    rng = np.random.default_rng(18)
+    for key in KEYS:
+        for _ in range(4):
+            idx = (int(rng.integers(0, g.n)), int(rng.integers(0, st[key].shape[1])))
+            vals = []
+            for sgn in (1.0, -1.0):
+                s2 = oracle.copy_state(st)
+                s2[key][idx] += sgn * H
+                vals.append(_linear_inertial(g, prm, s2, K, theta, a, b))
+            fd = (vals[0] - vals[1]) / (2 * H)
+            ad = res["x0"][key][idx]
+            assert abs(fd - ad) <= 1e-6 * max(1.0, abs(ad)), (key, idx, fd, ad)
