@@ -100,11 +100,13 @@ typedef struct {
                             (the paper's x^{k+1/2}, Appendix B; the extrapolation
                             rule is this library's reading); 0 (default) is plain
                             PRADMM.  A nonzero theta works with scalar and
-                            general weights (pradmm_set_sigma) and in the
-                            batched form (each pradmm_batch_solve starts the
-                            extrapolation afresh), not in the reverse mode;
-                            setting a state or the weights restarts the
-                            extrapolation (x^{k-1} := x^k). */
+                            general weights (pradmm_set_sigma), in the batched
+                            form (each pradmm_batch_solve starts the
+                            extrapolation afresh) and in the reverse mode
+                            (scalar weights; the recording starts afresh and
+                            keeps every iterate); setting a state or the
+                            weights restarts the extrapolation
+                            (x^{k-1} := x^k). */
 } pradmm_params;
 
 /* Defaults: beta1 = beta2 = 1, relax = 1.5, gamma = {1, 1e-3, 1e-3, 1e-3},
@@ -244,7 +246,10 @@ pradmm_status pradmm_set_sigma(pradmm_t h, const double* Sigma1, const double* S
  * ckpt_every = 0 chooses the spacing from the device memory: the smallest
  * one whose tape fits in half of the free memory (1 where it fits: every
  * iterate is kept and the reverse pass recomputes nothing); negative values
- * return PRADMM_ERR_ARG.  The tape stays valid until the state changes
+ * return PRADMM_ERR_ARG.  With a nonzero inertia the recording restarts the
+ * extrapolation (x^{-1} := x^0, whose adjoint then holds both shares) and
+ * keeps every iterate: ckpt_every must be 0 or 1 (PRADMM_ERR_ARG otherwise),
+ * PRADMM_ERR_NOMEM when that tape does not fit.  The tape stays valid until the state changes
  * (set_state, init_odometry, step, solve, another record). */
 pradmm_status pradmm_adjoint_record(pradmm_t h, int32_t iters, int32_t ckpt_every);
 

@@ -15,6 +15,13 @@
 //   k_adj_v   the p-block's edge terms of the state adjoints, and step A of
 //             the next (earlier) iteration
 //
+// Inertial variant (Coef::theta != 0): the proximal terms of iteration k are
+// gamma (x^k + theta (x^k - x^{k-1})), so each gamma term's adjoint goes
+// (1 + theta) to x^k and -theta to x^{k-1}.  The latter is held in A.vp ..
+// A.vs until step A of iteration k-2 starts xbar^{k-1} with it; after the
+// first iteration it joins xbar^0 (x^{-1} = x^0).  The p-block's recomputed
+// u takes p^{k-1} from the step (X.pp).
+//
 // For a quaternion product V = a x b the adjoint of x is a^* Vbar b^*
 // (Lemma MW: M(a)^T = M(a^*), W(b)^T = W(b^*)), and a conjugated operand
 // takes the conjugate of its adjoint.  Every sum a vertex needs is a gather
@@ -94,10 +101,13 @@ __device__ __forceinline__ Q<R> pr(const Q<R>& a, const V3<R>& v) {
 // updates (3e, 3f) and of the s-block (3d), s^{k+1} = sn / A_4.  Starts the
 // accumulators of iteration k: pbar, qbar, tbar of the block outputs
 // p^{k+1}, q^{k+1}, t^{k+1}, and the six parts of xbar^k.
+// Inertial variant: xbar^k starts from the shares that iteration k+1's anchors
+// left in A.vp .. A.vs (none for the last iteration, `first`), and A.vs
+// receives iteration k's own s share of xbar^{k-1}.
 template <typename R>
 __device__ __forceinline__ void step_a(const AdjDev<R>& A, const Coef<R>& c, int64_t i, const Q<R>& pb1,
                                        const Q<R>& qb1, const V3<R>& tb1, const V3<R>& sb1, const Q<R>& lb1,
-                                       const V3<R>& zb1, const V3<R>& s_next, R inv4) {
+                                       const V3<R>& zb1, const V3<R>& s_next, R inv4, bool first) {
     const Q<R> PB = {pb1.w - c.tb1 * lb1.w, pb1.x - c.tb1 * lb1.x, pb1.y - c.tb1 * lb1.y, pb1.z - c.tb1 * lb1.z};
     const Q<R> QB = {qb1.w + c.tb1 * lb1.w, qb1.x + c.tb1 * lb1.x, qb1.y + c.tb1 * lb1.y, qb1.z + c.tb1 * lb1.z};
     const V3<R> gs = {(sb1.x + c.tb2 * zb1.x) * inv4, (sb1.y + c.tb2 * zb1.y) * inv4, (sb1.z + c.tb2 * zb1.z) * inv4};
@@ -105,13 +115,30 @@ __device__ __forceinline__ void step_a(const AdjDev<R>& A, const Coef<R>& c, int
     const V3<R> TB = {tb1.x - c.tb2 * zb1.x + c.beta2 * gs.x, tb1.y - c.tb2 * zb1.y + c.beta2 * gs.y,
                       tb1.z - c.tb2 * zb1.z + c.beta2 * gs.z};
     const V3<R> oz = {zb1.x - gs.x, zb1.y - gs.y, zb1.z - gs.z};
-    const V3<R> os = {c.g4 * gs.x, c.g4 * gs.y, c.g4 * gs.z};
     stv(A.gs, i, gs, a4b);
     stq(A.pb, i, PB);
     stq(A.qb, i, QB);
     stv(A.tb, i, TB, R(0));
     stq(A.ol, i, lb1);
     stv(A.oz, i, oz, R(0));
+    if (c.theta != R(0)) {
+        const R g4c = c.g4 * (R(1) + c.theta), g4p = -c.g4 * c.theta;
+        R4<R> hp = {R(0), R(0), R(0), R(0)}, hq = hp, ht = hp, hs = hp;
+        if (!first) {
+            hp = IO<R>::ld(A.vp, i);
+            hq = IO<R>::ld(A.vq, i);
+            ht = IO<R>::ld(A.vt, i);
+            hs = IO<R>::ld(A.vs, i);
+        }
+        const V3<R> os = {g4c * gs.x + hs.a, g4c * gs.y + hs.b, g4c * gs.z + hs.c};
+        stv(A.os, i, os, R(0));
+        IO<R>::st(A.vs, i, g4p * gs.x, g4p * gs.y, g4p * gs.z, R(0));
+        IO<R>::st(A.op, i, hp.a, hp.b, hp.c, hp.d);
+        IO<R>::st(A.oq, i, hq.a, hq.b, hq.c, hq.d);
+        IO<R>::st(A.ot, i, ht.a, ht.b, ht.c, R(0));
+        return;
+    }
+    const V3<R> os = {c.g4 * gs.x, c.g4 * gs.y, c.g4 * gs.z};
     stv(A.os, i, os, R(0));
     IO<R>::st(A.op, i, R(0), R(0), R(0), R(0));
     IO<R>::st(A.oq, i, R(0), R(0), R(0), R(0));
@@ -129,7 +156,7 @@ __global__ void __launch_bounds__(256) k_adj_seed(GraphDev<R> g, AdjDev<R> A, Co
         const V3<R> tb1 = v3(IO<R>::ld(A.ot, i));
         const Q<R> zq = {R(0), R(0), R(0), R(0)};
         const V3<R> zv = {R(0), R(0), R(0)};
-        step_a<R>(A, c, i, pb1, zq, tb1, zv, zq, zv, v3(IO<R>::ld(s_K, i)), IO<R>::ld(z_K, i).d);
+        step_a<R>(A, c, i, pb1, zq, tb1, zv, zq, zv, v3(IO<R>::ld(s_K, i)), IO<R>::ld(z_K, i).d, true);
     }
 }
 
@@ -156,7 +183,13 @@ __global__ void __launch_bounds__(256) k_adj_t(GraphDev<R> g, AdjDev<R> A, AdjSt
         V3<R> os = v3(IO<R>::ld(A.os, i)), oz = v3(IO<R>::ld(A.oz, i)), ot = v3(IO<R>::ld(A.ot, i));
         vaxpy(os, c.beta2, gt);
         vaxpy(oz, R(1), gt);
-        vaxpy(ot, c.g3, gt);
+        if (c.theta != R(0)) {
+            vaxpy(ot, c.g3 * (R(1) + c.theta), gt);
+            const R g3p = -c.g3 * c.theta;
+            IO<R>::st(A.vt, i, g3p * gt.x, g3p * gt.y, g3p * gt.z, R(0));
+        } else {
+            vaxpy(ot, c.g3, gt);
+        }
         stv(A.os, i, os, R(0));
         stv(A.oz, i, oz, R(0));
         stv(A.ot, i, ot, R(0));
@@ -200,7 +233,13 @@ __global__ void __launch_bounds__(256) k_adj_q(GraphDev<R> g, AdjDev<R> A, AdjSt
         axpy(PB, c.beta1, gq);
         Q<R> ol = ldq(A.ol, i), oq = ldq(A.oq, i);
         axpy(ol, R(-1), gq);
-        axpy(oq, c.g2, gq);
+        if (c.theta != R(0)) {
+            axpy(oq, c.g2 * (R(1) + c.theta), gq);
+            const R g2p = -c.g2 * c.theta;
+            IO<R>::st(A.vq, i, g2p * gq.w, g2p * gq.x, g2p * gq.y, g2p * gq.z);
+        } else {
+            axpy(oq, c.g2, gq);
+        }
         stq(A.gq, i, gq);
         A.a2b[i] = a2b;
         stq(A.pb, i, PB);
@@ -225,8 +264,14 @@ __global__ void __launch_bounds__(256) k_adj_p(GraphDev<R> g, AdjDev<R> A, AdjSt
         const Q<R> P = ldq(X.pn, i), gq = ldq(A.gq, i);
         Q<R> PB = ldq(A.pb, i);
         V3<R> os = v3(IO<R>::ld(A.os, i)), ot = v3(IO<R>::ld(A.ot, i));
-        Q<R> u = {c.beta1 * qi.w + li.w + c.g1 * pk.w, c.beta1 * qi.x + li.x + c.g1 * pk.x,
-                  c.beta1 * qi.y + li.y + c.g1 * pk.y, c.beta1 * qi.z + li.z + c.g1 * pk.z};
+        Q<R> pa = pk;  // the proximal anchor, formed as the forward forms it
+        if (c.theta != R(0)) {
+            const Q<R> po = ldq(X.pp, i);
+            pa = {pk.w + c.theta * (pk.w - po.w), pk.x + c.theta * (pk.x - po.x), pk.y + c.theta * (pk.y - po.y),
+                  pk.z + c.theta * (pk.z - po.z)};
+        }
+        Q<R> u = {c.beta1 * qi.w + li.w + c.g1 * pa.w, c.beta1 * qi.x + li.x + c.g1 * pa.x,
+                  c.beta1 * qi.y + li.y + c.g1 * pa.y, c.beta1 * qi.z + li.z + c.g1 * pa.z};
         struct EO {
             R4<R> te, tj;
         };
@@ -286,7 +331,13 @@ __global__ void __launch_bounds__(256) k_adj_p(GraphDev<R> g, AdjDev<R> A, AdjSt
         }
         axpy(oq, c.beta1, ub);
         axpy(ol, R(1), ub);
-        axpy(op, c.g1, ub);
+        if (c.theta != R(0)) {
+            axpy(op, c.g1 * (R(1) + c.theta), ub);
+            const R g1p = -c.g1 * c.theta;
+            IO<R>::st(A.vp, i, g1p * ub.w, g1p * ub.x, g1p * ub.y, g1p * ub.z);
+        } else {
+            axpy(op, c.g1, ub);
+        }
         stq(A.ub, i, ub);
         stq(A.op, i, op);
         stq(A.oq, i, oq);
@@ -408,8 +459,17 @@ __global__ void __launch_bounds__(256) k_adj_v(GraphDev<R> g, AdjDev<R> A, AdjSt
         if (more) {
             // xbar^k is the xbar^{k+1} of iteration k-1, whose s^{k+1} is s^k here
             step_a<R>(A, c, i, ldq(A.op, i), oq, ot, os, ldq(A.ol, i), v3(IO<R>::ld(A.oz, i)), si,
-                      IO<R>::ld(X.z, i).d);
+                      IO<R>::ld(X.z, i).d, false);
         } else {
+            if (c.theta != R(0)) {
+                // the first iteration's anchor shares belong to x^{-1} = x^0
+                Q<R> op = ldq(A.op, i);
+                axpy(op, R(1), ldq(A.vp, i));
+                axpy(oq, R(1), ldq(A.vq, i));
+                vaxpy(ot, R(1), v3(IO<R>::ld(A.vt, i)));
+                vaxpy(os, R(1), v3(IO<R>::ld(A.vs, i)));
+                stq(A.op, i, op);
+            }
             stq(A.oq, i, oq);
             stv(A.os, i, os, R(0));
             stv(A.ot, i, ot, R(0));

@@ -116,6 +116,7 @@ struct pradmm_s {
     long long tape_k0 = 0;             // iteration counter at x^0
     int tape_K = 0, tape_C = 1, tape_nck = 0;
     void* adj = nullptr;               // per-vertex adjoint arrays + per-slot q_e, kappa_e
+    void* adj_v = nullptr;             // inertial variant: anchor shares of xbar^{k-1}, 16 n reals
     double* adj_g = nullptr;           // 9 m: per-slot gradients
     int32_t* out_edge_d = nullptr;
     int32_t* out_src_d = nullptr;
@@ -1133,15 +1134,19 @@ int auto_ckpt(const pradmm_s* h, int K) {
     return best;
 }
 
+pradmm_status restart_inertia(pradmm_s* h);
+
 template <typename R>
 pradmm_status adjoint_record(pradmm_s* h, int32_t iters, int32_t ckpt_every) {
     if (!h->state_set) return fail(PRADMM_ERR_STATE, "state is not set (pradmm_set_state or pradmm_init_odometry)");
     if (h->general) return fail(PRADMM_ERR_STATE, "the reverse mode supports scalar Sigma only");
-    if (h->prm.inertia != 0.0) return fail(PRADMM_ERR_ARG, "the reverse mode needs inertia = 0");
     if (iters < 0) return fail(PRADMM_ERR_ARG, "iters must be >= 0");
     if (ckpt_every < 0) return fail(PRADMM_ERR_ARG, "ckpt_every must be >= 0 (0: chosen from free device memory)");
+    const bool inert = h->prm.inertia != 0.0;
+    if (inert && ckpt_every > 1)
+        return fail(PRADMM_ERR_ARG, "the inertial reverse mode keeps every iterate: ckpt_every must be 0 or 1");
     h->tape_valid = false;
-    const int C = iters == 0 ? 1 : (ckpt_every == 0 ? auto_ckpt(h, iters) : std::min(ckpt_every, iters));
+    const int C = iters == 0 || inert ? 1 : (ckpt_every == 0 ? auto_ckpt(h, iters) : std::min(ckpt_every, iters));
     const int nck = iters == 0 ? 1 : (iters + C - 1) / C + 1;
     const size_t need = tape_slots(iters, C) * slot_bytes(h);
     if (need > h->tape_bytes) {
@@ -1155,6 +1160,11 @@ pradmm_status adjoint_record(pradmm_s* h, int32_t iters, int32_t ckpt_every) {
                         "tape of %zu bytes: %s", need, cudaGetErrorString(e));
         }
         h->tape_bytes = need;
+    }
+    if (inert) {
+        // the recorded iterations start with x^{-1} = x^0, as the reverse pass assumes
+        ST(restart_inertia(h));
+        h->pending = false;
     }
     if (!h->pending) {
         CU(pradmm::launch_p<R>(h->gdev<R>(), h->sdev<R>(), h->coef<R>(), h->launch(false)));
@@ -1218,6 +1228,7 @@ pradmm_status ensure_adjoint(pradmm_s* h) {
         CU(pradmm::launch_adj_edges<R>(h->qe64, h->ka64, m, eq, eq + 4 * m, h->stream));
         CU(cudaMemsetAsync(h->tape_ctrl, 0, sizeof(Ctrl), h->stream));
     }
+    if (h->prm.inertia != 0.0 && !h->adj_v) ST(valloc(h, &h->adj_v, 16 * (size_t)n));
     return PRADMM_OK;
 }
 
@@ -1234,6 +1245,13 @@ pradmm::AdjDev<R> adj_dev(pradmm_s* h) {
     A.g_te = h->adj_g;
     A.g_qe = h->adj_g + 4 * m;
     A.g_ka = h->adj_g + 8 * m;
+    if (h->adj_v) {
+        R* v = static_cast<R*>(h->adj_v);
+        A.vp = v;
+        A.vq = v + 4 * n;
+        A.vt = v + 8 * n;
+        A.vs = v + 12 * n;
+    }
     return A;
 }
 
@@ -1287,6 +1305,10 @@ cudaError_t enqueue_reverse(pradmm_s* h, const pradmm::AdjDev<R>& A) {
             X.z = S0.z;
             X.qn = S1.q;
             X.tn = S1.t;
+            if (c.theta != R(0)) {
+                // p^{k-1}: the previous slot (the inertial tape keeps every iterate), p^{-1} = p^0
+                X.pp = ci > 0 ? slot_state<R>(tape_slot(h, ci - 1), n).p[(k - 1) & 1] : X.pc;
+            }
             RQ(pradmm::launch_adj_iteration<R>(g, A, X, c, h->out_src_d, (ci == 0 && j == 0) ? 0 : 1, h->block, st));
         }
     }

@@ -260,6 +260,9 @@ struct AdjDev {
     R* tb;   // adjoint of t^{k+1}
     R* ub;   // adjoint of u (sphere projection)
     R *op, *oq, *ot, *os, *ol, *oz;  // adjoint of x^k (p, q, t, s, lam, z)
+    // inertial variant (else NULL): the share of x^{k-1}'s adjoint that
+    // iteration k's anchors x^k + theta (x^k - x^{k-1}) produce (p, q, t, s)
+    R *vp = nullptr, *vq = nullptr, *vt = nullptr, *vs = nullptr;
     const R* eq;     // 4m: q_e per out-slot (unscaled)
     const R* ek;     // m: kappa_e per out-slot
     double* g_te;    // 4m: (dL/dt_e, dL/domega_e) per out-slot
@@ -274,6 +277,7 @@ struct AdjStep {
     const R* pn;   // p^{k+1}
     const R *q, *lam, *t, *s, *z;  // x^k
     const R *qn, *tn;              // q^{k+1}, t^{k+1}
+    const R* pp = nullptr;         // p^{k-1} (inertial variant)
 };
 
 template <typename R>

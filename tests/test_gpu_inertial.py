@@ -128,7 +128,7 @@ def test_inertia_is_rejected_where_unsupported(P):
     with P.Solver(g, precision=1, inertia=0.4) as S:
         S.init_odometry()
         with pytest.raises(P.PRADMMError) as ei:
-            S.adjoint_record(5, 1)
+            S.adjoint_record(5, 2)  # the inertial reverse mode keeps every iterate
         assert ei.value.status == P.PRADMM_ERR_ARG
 
 
@@ -265,3 +265,45 @@ def test_batch_inertial_fp32_matches_single_solver(P):
         grow = np.sqrt(20.0)
         assert np.linalg.norm(sl["lam"] - ref["lam"]) <= 1e-5 * grow * 1.5 * max(np.linalg.norm(ref["p"]), 1.0), k
         assert np.linalg.norm(sl["z"] - ref["z"]) <= 1e-5 * grow * 1.5 * max(np.linalg.norm(ref["t"]), 1.0), k
+
+
+# ---- reverse mode of the inertial iteration ------------------------------------
+# Against the oracle's inertial reverse mode (pinned by central differences),
+# per gradient array: FP64 1e-8, FP32 1e-3, as the plain reverse-mode tests.
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-8), (1, 1e-3)])
+@pytest.mark.parametrize("theta", [0.4, 0.8])
+def test_inertial_reverse_mode_matches_oracle(P, precision, tol, theta):
+    g = synth.random_graph(240, 700, seed=44, isolated=3)
+    st = synth.random_state(np.random.default_rng(12), g.n)
+    rng = np.random.default_rng(13)
+    pb, tb = rng.normal(size=(g.n, 4)), rng.normal(size=(g.n, 3))
+    K = 17
+    prm = oracle.make_params(beta1=1.0, beta2=1.0, tau=1.5, gamma=(1.0, 0.6, 0.5, 0.7))
+    ref = oracle.adjoint_inertial(g, prm, st, K, theta, pb, tb)
+    with P.Solver(g, precision=precision, inertia=theta, gamma=(1.0, 0.6, 0.5, 0.7)) as S:
+        S.set_state_full(st)
+        S.adjoint_record(K, 0)
+        assert S.adjoint_tape_info()[0] == 1
+        fin = S.state()
+        got = S.adjoint(pb, tb, x0=True)
+    for key in ("q_meas", "t_meas", "kappa", "omega"):
+        assert relerr(got[key], ref[key]) <= tol, (key, relerr(got[key], ref[key]))
+    for key in KEYS:
+        assert relerr(got["x0"][key], ref["x0"][key]) <= tol, ("x0", key, relerr(got["x0"][key], ref["x0"][key]))
+    assert relerr(fin["p"], ref["p"]) <= (1e-10 if precision == 0 else 1e-4)
+
+
+def test_inertial_record_restarts_the_extrapolation(P):
+    # a record after steps starts from the current state with x^{-1} = x^0
+    g = synth.random_graph(150, 420, seed=45)
+    st = synth.random_state(np.random.default_rng(14), g.n)
+    theta = 0.5
+    with P.Solver(g, precision=0, inertia=theta) as S:
+        S.set_state_full(st)
+        S.step(4)
+        mid = S.state()
+        S.adjoint_record(6, 1)
+        fin = S.state()
+    orc, _, _, _ = oracle.iterate_inertial(g, _oparams(), mid, theta, 6)
+    check_state(fin, orc, True, "recorded")
