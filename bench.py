@@ -232,7 +232,9 @@ def run_inertial(P, g, thetas=(0.0, 0.3, 0.6), lattice_iters=200):
     of the ring and cube workloads (tau = 1.4, tol = 1e-4, at most 3000
     iterations) for each theta, FP32; and the time per iteration on the
     1M-pose lattice, graph-launched, at theta = 0.3 against theta = 0, with
-    scalar weights and with the general weights of the general-Sigma leg."""
+    scalar weights and with the general weights of the general-Sigma leg; and
+    the reverse mode on the 10,000-pose walk at theta = 0.3 (as the adjoint
+    leg, the spacing chosen by the library: every iterate kept)."""
     from paper_2601_15684_gb300 import synth
     solves = []
     for wl in ("ring5000", "cube10"):
@@ -260,8 +262,12 @@ def run_inertial(P, g, thetas=(0.0, 0.3, 0.6), lattice_iters=200):
                 t0 = time.perf_counter()
                 S.step(lattice_iters)
                 out[str(theta)] = 1e3 * (time.perf_counter() - t0) / lattice_iters
+    rev = run_adjoint(P, spacings=(0,), reps=3, inertia=0.3)
+    reverse = {"workload": "walk10k", "theta": 0.3, "iterations": rev["iterations"], "forward_ms": rev["forward_ms"],
+               "record_ms": rev["by_spacing"][0]["record_ms"], "backward_ms": rev["by_spacing"][0]["backward_ms"],
+               "forward_plus_backward_over_forward": rev["forward_plus_backward_over_forward"]}
     return {"solves": solves, "lattice_ms_per_iteration": per_iter,
-            "lattice_general_sigma_ms_per_iteration": per_iter_sig,
+            "lattice_general_sigma_ms_per_iteration": per_iter_sig, "reverse_mode": reverse,
             "reading": "anchors x^k + theta (x^k - x^{k-1}) for p, q, t, s (the paper leaves the rule open)"}
 
 
@@ -290,7 +296,7 @@ def run_general_sigma(P, g, iters=300):
             "general_over_scalar_time": out["general"]["ms_per_iteration"] / out["scalar"]["ms_per_iteration"]}
 
 
-def run_adjoint(P, K=200, spacings=(20, 0), reps=5):
+def run_adjoint(P, K=200, spacings=(20, 0), reps=5, inertia=0.0):
     """Reverse mode vs the plain forward on the 10,000-pose walk (~30k edges):
     K unrolled iterations from the odometry start.  forward = K iterations
     (pradmm_step); record = the same iterations with checkpoints
@@ -299,7 +305,8 @@ def run_adjoint(P, K=200, spacings=(20, 0), reps=5):
     segments between checkpoints and runs the reverse sweeps).  Each spacing
     in `spacings` is timed: 20 (a checkpoint every 20 iterations) and 0 (the
     spacing chosen from the free device memory).  Medians of `reps`
-    wall-clock runs, each call synchronised."""
+    wall-clock runs, each call synchronised.  `inertia`: theta of the
+    inertial variant (its recording keeps every iterate)."""
     import torch
     from paper_2601_15684_gb300 import synth
     from paper_2601_15684_gb300.anchor import anchor_loss
@@ -308,7 +315,7 @@ def run_adjoint(P, K=200, spacings=(20, 0), reps=5):
     dev = torch.device("cuda:0")
     fwd = []
     legs = []
-    with P.Solver(g, precision=P.PRADMM_FP32) as S:
+    with P.Solver(g, precision=P.PRADMM_FP32, inertia=inertia) as S:
         for ckpt in spacings:
             rec, bwd = [], []
             for r in range(reps + 1):
