@@ -307,3 +307,57 @@ def test_inertial_record_restarts_the_extrapolation(P):
         fin = S.state()
     orc, _, _, _ = oracle.iterate_inertial(g, _oparams(), mid, theta, 6)
     check_state(fin, orc, True, "recorded")
+
+
+def test_inertial_degenerate_graphs(P):
+    # no edges (n = 1 and 5), and a vertex whose u is 0 in the first
+    # iteration (its p is kept, as in the plain iteration)
+    theta = 0.5
+    for n in (1, 5):
+        g = synth.PoseGraph(n=n, src=np.zeros(0, np.int32), dst=np.zeros(0, np.int32), q_meas=np.zeros((0, 4)),
+                            t_meas=np.zeros((0, 3)), kappa=np.zeros(0), omega=np.zeros(0))
+        st0 = synth.random_state(np.random.default_rng(n), n)
+        for precision in (0, 1):
+            with P.Solver(g, precision=precision, inertia=theta) as S:
+                S.set_state_full(st0)
+                S.step(1)
+                S.step(3)
+                gpu = S.state()
+            orc, _, _, _ = oracle.iterate_inertial(g, _oparams(), st0, theta, 4)
+            check_state(gpu, orc, precision == 0, f"n={n}")
+    g = synth.random_graph(6, 10, seed=31, isolated=1)
+    st = synth.random_state(np.random.default_rng(32), g.n)
+    st["p"][5] = st["q"][5] = [1.0, 0, 0, 0]
+    st["lam"][5] = [-2.0, 0, 0, 0]
+    with P.Solver(g, precision=0, inertia=theta) as S:
+        S.set_state_full(st)
+        S.step(1)
+        assert S.counters()["zero_u"] == 1
+        gpu = S.state()
+    np.testing.assert_array_equal(gpu["p"][5], [1.0, 0, 0, 0])
+    orc, _, _, _ = oracle.iterate_inertial(g, _oparams(), st, theta, 1)
+    check_state(gpu, orc, True, "zero u")
+
+
+@pytest.mark.parametrize("K", [0, 1, 2])
+def test_inertial_reverse_mode_short_tapes(P, K):
+    g = synth.random_graph(60, 170, seed=46, isolated=2)
+    st = synth.random_state(np.random.default_rng(15), g.n)
+    rng = np.random.default_rng(16)
+    pb, tb = rng.normal(size=(g.n, 4)), rng.normal(size=(g.n, 3))
+    prm = oracle.make_params(beta1=1.0, beta2=1.0, tau=1.5, gamma=(1.0, 0.6, 0.5, 0.7))
+    ref = oracle.adjoint_inertial(g, prm, st, K, 0.6, pb, tb)
+    with P.Solver(g, precision=0, inertia=0.6, gamma=(1.0, 0.6, 0.5, 0.7)) as S:
+        S.set_state_full(st)
+        S.adjoint_record(K, 1)
+        got = S.adjoint(pb, tb, x0=True)
+    for key in ("q_meas", "t_meas", "kappa", "omega"):
+        if K == 0:
+            assert not np.any(got[key])
+        else:
+            assert relerr(got[key], ref[key]) <= 1e-8, (key, relerr(got[key], ref[key]))
+    for key in KEYS:
+        if np.linalg.norm(ref["x0"][key]) == 0.0:
+            assert not np.any(got["x0"][key]), key
+        else:
+            assert relerr(got["x0"][key], ref["x0"][key]) <= 1e-8, ("x0", key)
