@@ -162,6 +162,16 @@ pradmm_status pradmm_set_state_full_device(pradmm_t h, const double* p_d, const 
  * not define.) */
 pradmm_status pradmm_init_odometry(pradmm_t h);
 
+/* Schedule search: times `iters` >= 1 iterations from the current state at
+ * each CTA size of the sweeps (32, 64, 128 and 256 threads; a thread per
+ * vertex), keeps the fastest and restores the state as
+ * pradmm_set_state_full would (the iteration count and the inertial
+ * extrapolation restart).  The iterates do not depend on the CTA size (each
+ * vertex sums its edges in the same order); the residual's reduction tree
+ * does, in its last bits.  block_out (nullable) receives the choice.
+ * PRADMM_ERR_STATE before a state is set. */
+pradmm_status pradmm_autotune(pradmm_t h, int32_t iters, int32_t* block_out);
+
 /* Runs `iters` >= 0 iterations of Algorithm 1 (no stopping test).
  * e_last (nullable) receives e^k of the last iteration. */
 pradmm_status pradmm_step(pradmm_t h, int32_t iters, double* e_last);

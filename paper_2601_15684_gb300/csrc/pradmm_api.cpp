@@ -55,7 +55,7 @@ struct pradmm_s {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int grids[4] = {1, 1, 1, 1};  // p, q, t, s/z+p sweeps
-    int pstride = 1, block = 256, obj_grid = 1;
+    int pstride = 1, block = 256, obj_grid = 1, sms = 1;
     int64_t out_slots = 0, in_slots = 0;  // edges per order (= m)
 
     // host copies (input order) for the odometry initialisation
@@ -117,6 +117,7 @@ struct pradmm_s {
     int tape_K = 0, tape_C = 1, tape_nck = 0;
     void* adj = nullptr;               // per-vertex adjoint arrays + per-slot q_e, kappa_e
     void* adj_v = nullptr;             // inertial variant: anchor shares of xbar^{k-1}, 16 n reals
+    double* tune_save = nullptr;       // pradmm_autotune: the state it restores (21 n doubles)
     double* adj_g = nullptr;           // 9 m: per-slot gradients
     int32_t* out_edge_d = nullptr;
     int32_t* out_src_d = nullptr;
@@ -512,8 +513,9 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
     ST(dalloc(h, &h->inv4_d, n));
     ST(dalloc(h, &h->stage, 4 * n));
     ST(dalloc(h, &h->zeros, 4 * n));
-    ST(dalloc(h, &h->part, 4 * (size_t)h->pstride));
-    ST(dalloc(h, &h->obj_part, (size_t)h->obj_grid));
+    // room for the partials of any CTA size the sweeps may be given (pradmm_autotune)
+    ST(dalloc(h, &h->part, 4 * (size_t)std::max(h->pstride, h->sms * 32)));
+    ST(dalloc(h, &h->obj_part, (size_t)std::max(h->obj_grid, h->sms * 4)));
     ST(dalloc(h, &h->obj_ticket, 1));
     ST(dalloc(h, &h->F_dev, 1));
     ST(dalloc(h, &h->ctrl, 1));
@@ -664,6 +666,24 @@ void l2_window_off(pradmm_s* h) {
     }
 }
 
+// Grids of the sweeps for `block` threads per CTA: a thread per vertex, at most
+// a full wave of resident CTAs (the sweeps loop over vertices).
+pradmm_status set_grids(pradmm_s* h, int block) {
+    int bps[4] = {0, 0, 0, 0};
+    cudaError_t e = pradmm::sweep_occupancy(h->fp64 ? 1 : 0, block, bps);
+    if (e != cudaSuccess) return fail(PRADMM_ERR_CUDA, "device query: %s", cudaGetErrorString(e));
+    const int64_t tiles = (h->n + block - 1) / block;
+    h->block = block;
+    h->pstride = 1;
+    for (int k = 0; k < 4; ++k) {
+        const int64_t cap = (int64_t)h->sms * std::max(bps[k], 1);
+        h->grids[k] = (int)std::max<int64_t>(1, std::min(tiles, cap));
+        h->pstride = std::max(h->pstride, h->grids[k]);
+    }
+    h->obj_grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)h->sms * 4));
+    return PRADMM_OK;
+}
+
 pradmm_status create_common(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const double* q_meas,
                             const double* t_meas, const double* kappa, const double* omega, const pradmm_params* prm,
                             void* stream, pradmm_t* out) {
@@ -713,20 +733,9 @@ pradmm_status create_common(int64_t n, int64_t m, const int32_t* src, const int3
             // 256, 64 and 32 for both the forward and the reverse sweeps)
             while (h->block > 32 && 2 * ((n + h->block - 1) / h->block) < sms) h->block /= 2;
         }
-        if ((e = pradmm::sweep_occupancy(h->fp64 ? 1 : 0, h->block, bps)) != cudaSuccess) {
-            st = fail(PRADMM_ERR_CUDA, "device query: %s", cudaGetErrorString(e));
-            break;
-        }
-        // a thread per vertex, at most a full wave of resident CTAs (the
-        // sweeps loop over vertices)
-        const int64_t tiles = (n + h->block - 1) / h->block;
-        h->pstride = 1;
-        for (int k = 0; k < 4; ++k) {
-            const int64_t cap = (int64_t)sms * std::max(bps[k], 1);
-            h->grids[k] = (int)std::max<int64_t>(1, std::min(tiles, cap));
-            h->pstride = std::max(h->pstride, h->grids[k]);
-        }
-        h->obj_grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sms * 4));
+        (void)bps;
+        h->sms = sms;
+        if ((st = set_grids(h, h->block)) != PRADMM_OK) break;
         st = build(h, src, dst, q_meas, t_meas, kappa, omega);
         if (st == PRADMM_OK && p.l2_window) l2_window_on(h, dev);
     } while (0);
@@ -1664,6 +1673,54 @@ pradmm_status pradmm_set_state_full_device(pradmm_t h, const double* p_d, const 
                                            const double* s_d, const double* lam_d, const double* z_d) {
     if (!h || !p_d || !q_d || !t_d || !s_d) return fail(PRADMM_ERR_ARG, "NULL argument (p, q, t, s are required)");
     return set_state_any(h, p_d, q_d, t_d, s_d, lam_d, z_d, true);
+}
+
+pradmm_status pradmm_autotune(pradmm_t h, int32_t iters, int32_t* block_out) {
+    if (!h) return fail(PRADMM_ERR_ARG, "NULL handle");
+    if (iters < 1) return fail(PRADMM_ERR_ARG, "iters must be >= 1");
+    if (!h->state_set) return fail(PRADMM_ERR_STATE, "state is not set");
+    const int64_t n = h->n;
+    if (!h->tune_save) ST(dalloc(h, &h->tune_save, 21 * (size_t)n));
+    double* sv = h->tune_save;
+    ST(h->fp64 ? get_state_impl<double>(h, sv, sv + 4 * n, sv + 8 * n, sv + 11 * n, sv + 14 * n, sv + 18 * n, true)
+               : get_state_impl<float>(h, sv, sv + 4 * n, sv + 8 * n, sv + 11 * n, sv + 14 * n, sv + 18 * n, true));
+    // a new CTA size changes every captured launch
+    auto regrid = [&](int blk) -> pradmm_status {
+        ST(set_grids(h, blk));
+        drop_graphs(h);
+        if (h->adj_exec) cudaGraphExecDestroy(h->adj_exec);
+        h->adj_exec = nullptr;
+        return PRADMM_OK;
+    };
+    auto restore = [&]() { return set_state_any(h, sv, sv + 4 * n, sv + 8 * n, sv + 11 * n, sv + 14 * n, sv + 18 * n, true); };
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    int best = h->block;
+    float best_ms = 3.4e38f;
+    pradmm_status st = PRADMM_OK;
+    for (int blk : {32, 64, 128, 256}) {
+        if ((st = regrid(blk)) != PRADMM_OK || (st = restore()) != PRADMM_OK) break;
+        if ((st = run_any(h, 1, false)) != PRADMM_OK) break;  // captures the loop, first p sweep
+        cudaEventRecord(e0, h->stream);
+        st = run_any(h, iters, false);
+        cudaEventRecord(e1, h->stream);
+        cudaEventSynchronize(e1);
+        if (st != PRADMM_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = blk;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == PRADMM_OK) st = regrid(best);
+    if (st == PRADMM_OK) st = restore();
+    if (st != PRADMM_OK) return st;
+    if (block_out) *block_out = best;
+    return PRADMM_OK;
 }
 
 pradmm_status pradmm_init_odometry(pradmm_t h) {

@@ -67,6 +67,7 @@ _SIGS = {
     "pradmm_set_state_full_device": (ctypes.c_int, [_h, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pradmm_init_odometry": (ctypes.c_int, [_h]),
+    "pradmm_autotune": (ctypes.c_int, [_h, ctypes.c_int32, _i32]),
     "pradmm_step": (ctypes.c_int, [_h, ctypes.c_int32, _d]),
     "pradmm_solve": (ctypes.c_int, [_h, _i32, _d]),
     "pradmm_objective": (ctypes.c_int, [_h, _d]),
@@ -198,6 +199,13 @@ def pradmm_set_state_full_device(h, p, q, t, s, lam=0, z=0):
     _check(load().pradmm_set_state_full_device(h, ctypes.c_void_p(p), ctypes.c_void_p(q), ctypes.c_void_p(t),
                                                ctypes.c_void_p(s), ctypes.c_void_p(lam or 0),
                                                ctypes.c_void_p(z or 0)), "pradmm_set_state_full_device")
+
+
+def pradmm_autotune(h, iters: int) -> int:
+    """CTA size of the sweeps chosen by timing `iters` iterations (state restored)."""
+    b = ctypes.c_int32(0)
+    _check(load().pradmm_autotune(h, int(iters), ctypes.byref(b)), "pradmm_autotune")
+    return int(b.value)
 
 
 def pradmm_init_odometry(h):
@@ -401,6 +409,9 @@ class Solver:
 
     def init_odometry(self):
         pradmm_init_odometry(self.h)
+
+    def autotune(self, iters=20):
+        return pradmm_autotune(self.h, iters)
 
     def step(self, iters=1):
         return pradmm_step(self.h, iters)

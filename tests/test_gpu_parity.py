@@ -314,3 +314,28 @@ def test_nonfinite_state_is_reported(P):
         with pytest.raises(P.PRADMMError) as ei:
             S.step(3)
         assert ei.value.status == P.PRADMM_ERR_NONFINITE
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotune_picks_a_cta_size_and_restores_the_state(P, precision):
+    g = synth.random_graph(5000, 15000, seed=51, isolated=4)
+    st0 = synth.random_state(np.random.default_rng(52), g.n)
+    with P.Solver(g, _params(P, precision)) as S:
+        S.set_state_full(st0)
+        before = S.state()
+        blk = S.autotune(8)
+        assert blk in (32, 64, 128, 256)
+        after = S.state()
+        assert S.iterations() == 0
+        for k in KEYS:
+            np.testing.assert_array_equal(after[k], before[k])
+        S.step(5)
+        tuned = S.state()
+    with P.Solver(g, _params(P, precision, block=blk)) as S:
+        S.set_state_full(st0)
+        S.step(5)
+        ref = S.state()
+    for k in KEYS:
+        assert relerr(tuned[k], ref[k]) <= (1e-13 if precision == 0 else 1e-6), k
+    orc, _, _ = oracle.iterate(g, _oparams(), st0, 5)
+    check_state(tuned, orc, precision == 0, _params(P, precision))
