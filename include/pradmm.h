@@ -40,7 +40,9 @@
  *    fixed point);
  *  - c_e = Im(q_tail t~_e p_tail^*) for an edge e = (tail, head)
  *    (Appendix B.3 prints garbled indices);
- *  - proximal anchors x^{k+1/2} of Appendix B are x^k;
+ *  - proximal anchors x^{k+1/2} of Appendix B are x^k, or with a nonzero
+ *    pradmm_params.inertia theta the extrapolated x^k + theta (x^k - x^{k-1})
+ *    (the inertial variant; the paper gives no rule for x^{k+1/2});
  *  - e^{k+1} = |dlambda|^2/beta1 + |dz|^2/beta2 + beta1 |dq|^2 + beta2 |dt|^2
  *    (Appendix E.1 uses a single beta);
  *  - lambda^0 = z^0 = 0, p^0 = q^0, s^0 = t^0;
