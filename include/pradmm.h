@@ -387,6 +387,15 @@ pradmm_status pradmm_batch_autotune_profiled(pradmm_batch_t b, double work_fract
 
 /* Initial states, all graphs at once (q: N x 4, t: N x 3 with N = sum n_g, in
  * graph order): odometry composition per graph, or given poses. */
+/* General weight matrices for every graph of the batch (as pradmm_set_sigma;
+ * both NULL returns to scalar weights).  Each graph's iteration then runs the
+ * four general-weight sweeps; an FP32 p-update that needs the FP64 re-solve
+ * does it in the same thread (counted in the handle's FP64 re-solves), and
+ * pradmm_batch_objectives uses the Sigma-weighted norms.  The schedule's grid
+ * is re-sized for the other kernel; a cluster shape that no longer fits
+ * falls back to the start schedule. */
+pradmm_status pradmm_batch_set_sigma(pradmm_batch_t b, const double* Sigma1, const double* Sigma2);
+
 pradmm_status pradmm_batch_init_odometry(pradmm_batch_t b);
 pradmm_status pradmm_batch_set_state(pradmm_batch_t b, const double* q, const double* t);
 

@@ -22,9 +22,15 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["pradmm_kernels.cu", "pradmm_batch.cu", "pradmm_batch_inert.cu", "pradmm_adjoint.cu", "pradmm_sigma.cu",
               "pradmm_noalloc.cu", "pradmm_setup.cu"]
+# sources compiled once per set of defines (object name suffix, defines): the
+# batched general-Sigma kernels, one object per precision and inertial flag
+CU_SPLIT = {"pradmm_batch_sigma.cu": [(f"{r}{'_inert' if i else ''}",
+                                       [f"-DPRADMM_BATCH_SIGMA_R={r}", f"-DPRADMM_BATCH_SIGMA_INERT={str(i).lower()}"])
+                                      for r in ("float", "double") for i in (False, True)]}
 CPP_SOURCES = ["pradmm_api.cpp"]
 HEADERS = [os.path.join(CSRC, "pradmm_internal.h"), os.path.join(CSRC, "pradmm_device.cuh"),
-           os.path.join(CSRC, "pradmm_batch.cuh"), os.path.join(INCLUDE, "pradmm.h")]
+           os.path.join(CSRC, "pradmm_batch.cuh"), os.path.join(CSRC, "pradmm_sigma.cuh"),
+           os.path.join(INCLUDE, "pradmm.h")]
 
 
 def _cuda_home() -> str:
@@ -58,6 +64,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if force or _stale(o, [s] + HEADERS):
             jobs.append([_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                          "-I", INCLUDE, "-I", CSRC, "-c", s, "-o", o])
+    for src, variants in CU_SPLIT.items():
+        s = os.path.join(CSRC, src)
+        for tag, defs in variants:
+            o = os.path.join(BUILD, f"{src}.{tag}.o")
+            objs.append(o)
+            if force or _stale(o, [s] + HEADERS):
+                jobs.append([_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", *defs,
+                             "-I", INCLUDE, "-I", CSRC, "-c", s, "-o", o])
     for src in CPP_SOURCES:
         s = os.path.join(CSRC, src)
         o = os.path.join(BUILD, src + ".o")

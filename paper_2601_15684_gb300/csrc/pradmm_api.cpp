@@ -1944,6 +1944,32 @@ void batch_free(pradmm_batch_s* b) {
     delete b;
 }
 
+// Occupancy of the persistent kernel the batch will launch: the plain or the
+// general-Sigma iteration, plain or inertial, in the handle's precision.
+template <typename R>
+cudaError_t batch_occupancy_r(const pradmm_s* h, int block, int* bps) {
+    const bool in = h->prm.inertia != 0.0;
+    if (h->general)
+        return in ? pradmm::batch_sigma_occupancy<R, true>(block, bps) : pradmm::batch_sigma_occupancy<R, false>(block, bps);
+    return in ? pradmm::batch_occupancy<R, true>(block, bps) : pradmm::batch_occupancy<R, false>(block, bps);
+}
+cudaError_t batch_occupancy_any(const pradmm_s* h, int block, int* bps) {
+    return h->fp64 ? batch_occupancy_r<double>(h, block, bps) : batch_occupancy_r<float>(h, block, bps);
+}
+template <typename R>
+cudaError_t batch_cluster_occupancy_r(const pradmm_s* h, int block, int cluster, int* clusters) {
+    const bool in = h->prm.inertia != 0.0;
+    if (h->general)
+        return in ? pradmm::batch_sigma_cluster_occupancy<R, true>(block, cluster, clusters)
+                  : pradmm::batch_sigma_cluster_occupancy<R, false>(block, cluster, clusters);
+    return in ? pradmm::batch_cluster_occupancy<R, true>(block, cluster, clusters)
+              : pradmm::batch_cluster_occupancy<R, false>(block, cluster, clusters);
+}
+cudaError_t batch_cluster_occupancy_any(const pradmm_s* h, int block, int cluster, int* clusters) {
+    return h->fp64 ? batch_cluster_occupancy_r<double>(h, block, cluster, clusters)
+                   : batch_cluster_occupancy_r<float>(h, block, cluster, clusters);
+}
+
 // Work items: graphs larger than warp_max_n get a whole CTA each (largest
 // first); the others are packed, in decreasing size, block/32 per CTA.
 pradmm_status batch_schedule(pradmm_batch_s* b, int block, int warp_max_n, int cluster, int cluster_min_n) {
@@ -1984,19 +2010,11 @@ pradmm_status batch_schedule(pradmm_batch_s* b, int block, int warp_max_n, int c
     b->cluster_min_n = cluster_min_n;
     if (cluster > 1) {
         int clusters = 0;
-        const bool in = h->prm.inertia != 0.0;
-        CU(h->fp64 ? (in ? pradmm::batch_cluster_occupancy<double, true>(block, cluster, &clusters)
-                         : pradmm::batch_cluster_occupancy<double, false>(block, cluster, &clusters))
-                   : (in ? pradmm::batch_cluster_occupancy<float, true>(block, cluster, &clusters)
-                         : pradmm::batch_cluster_occupancy<float, false>(block, cluster, &clusters)));
+        CU(batch_cluster_occupancy_any(h, block, cluster, &clusters));
         if (clusters < 1) return fail(PRADMM_ERR_ARG, "no cluster of %d CTAs of %d threads fits the GPU", cluster, block);
         b->grid = clusters * cluster;
     } else {
-        const bool in = h->prm.inertia != 0.0;
-        CU(h->fp64 ? (in ? pradmm::batch_occupancy<double, true>(block, &bps)
-                         : pradmm::batch_occupancy<double, false>(block, &bps))
-                   : (in ? pradmm::batch_occupancy<float, true>(block, &bps)
-                         : pradmm::batch_occupancy<float, false>(block, &bps)));
+        CU(batch_occupancy_any(h, block, &bps));
         b->grid = std::max(1, std::min(b->n_items, sms * std::max(bps, 1)));
     }
     return PRADMM_OK;
@@ -2032,9 +2050,16 @@ pradmm_status batch_run(pradmm_batch_s* b, double rel_tol, double abs_tol, int m
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    const auto launch = h->prm.inertia != 0.0 ? pradmm::launch_batch<R, true> : pradmm::launch_batch<R, false>;
-    cudaError_t e1 = launch(h->gdev<R>(), h->sdev<R>(), h->coef<R>(), d, h->ctrl, b->grid, b->block, b->cluster,
-                            h->stream);
+    const bool in = h->prm.inertia != 0.0;
+    cudaError_t e1;
+    if (h->general) {
+        const auto launch = in ? pradmm::launch_batch_sigma<R, true> : pradmm::launch_batch_sigma<R, false>;
+        e1 = launch(h->gdev<R>(), h->sdev<R>(), h->coef<R>(), h->sigma<R>(), d, h->ctrl, b->grid, b->block,
+                    b->cluster, h->stream);
+    } else {
+        const auto launch = in ? pradmm::launch_batch<R, true> : pradmm::launch_batch<R, false>;
+        e1 = launch(h->gdev<R>(), h->sdev<R>(), h->coef<R>(), d, h->ctrl, b->grid, b->block, b->cluster, h->stream);
+    }
     cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
     CU(e1);
     CU(e2);
@@ -2152,6 +2177,15 @@ pradmm_status pradmm_batch_get_schedule(pradmm_batch_t b, int32_t* block, int32_
     return PRADMM_OK;
 }
 
+pradmm_status pradmm_batch_set_sigma(pradmm_batch_t b, const double* Sigma1, const double* Sigma2) {
+    if (!b) return fail(PRADMM_ERR_ARG, "NULL handle");
+    ST(set_sigma_impl(b->h, Sigma1, Sigma2));
+    // the other iteration has its own register count: re-size the schedule's grid
+    pradmm_status st = batch_schedule(b, b->block, b->warp_max_n, b->cluster, b->cluster_min_n);
+    if (st == PRADMM_ERR_ARG) st = batch_schedule(b, 256, 256, 1, 0);  // the cluster shape no longer fits
+    return st;
+}
+
 pradmm_status pradmm_batch_init_odometry(pradmm_batch_t b) {
     if (!b) return fail(PRADMM_ERR_ARG, "NULL handle");
     return pradmm_init_odometry(b->h);
@@ -2193,10 +2227,14 @@ pradmm_status pradmm_batch_objectives(pradmm_batch_t b, double* F) {
     pradmm_s* h = b->h;
     if (!h->state_set) return fail(PRADMM_ERR_STATE, "batch state is not set");
     const pradmm::BatchDev d = batch_dev(b, 0.0, 0.0, 0);
+    const double* S1 = h->general ? h->sigma_d : nullptr;
+    const double* S2 = h->general ? h->sigma_d + 16 : nullptr;
     cudaError_t e = h->fp64 ? pradmm::launch_batch_objective<double>(h->gdev<double>(), h->sdev<double>(), h->qe64,
-                                                                    h->te64, h->ka64, h->om64, d, b->F_d, b->G, h->stream)
+                                                                    h->te64, h->ka64, h->om64, S1, S2, d, b->F_d, b->G,
+                                                                    h->stream)
                             : pradmm::launch_batch_objective<float>(h->gdev<float>(), h->sdev<float>(), h->qe64,
-                                                                   h->te64, h->ka64, h->om64, d, b->F_d, b->G, h->stream);
+                                                                   h->te64, h->ka64, h->om64, S1, S2, d, b->F_d, b->G,
+                                                                   h->stream);
     CU(e);
     CU(cudaMemcpyAsync(F, b->F_d, sizeof(double) * b->G, cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));

@@ -15,11 +15,13 @@
 // e^k < abs_tol, the residual is not finite, or max_iter is reached.  Apart
 // from the barriers of its own cluster, no CTA ever waits for another CTA.
 //
-// This header holds the persistent kernels and their launchers as templates on
+// This header holds the persistent kernels, templated on a policy that solves
+// one graph with a group (the plain iteration here, general weights in
+// pradmm_batch_sigma.cu), and the plain iteration's launchers as templates on
 // INERT (the inertial variant: proximal anchors x^k + theta (x^k - x^{k-1}),
 // the previous iterates in S.qprev, S.tprev, S.sprev, each solve starting
 // afresh with x^{-1} = x^0).  pradmm_batch.cu instantiates the plain form and
-// pradmm_batch_inert.cu the inertial one, so the two compile in parallel.
+// pradmm_batch_inert.cu the inertial one, so they compile in parallel.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -175,9 +177,23 @@ __device__ void solve_graph(const G& grp, const GraphDev<R>& g, const StateDev<R
     }
 }
 
-// Persistent solver: every CTA takes items until the queue is empty.
-template <typename R, int WPB, bool INERT>
-__global__ void __launch_bounds__(WPB * 32) k_batch(GraphDev<R> g, StateDev<R> S, Coef<R> c, BatchDev b, Ctrl* ctrl) {
+// The plain iteration as a batch policy: solves graph gid with group grp.
+template <typename R, bool INERT>
+struct PlainSolve {
+    GraphDev<R> g;
+    StateDev<R> S;
+    Coef<R> c;
+    template <typename G>
+    __device__ __forceinline__ void operator()(const G& grp, const BatchDev& b, int gid, Ctrl* ctrl) const {
+        solve_graph<R, INERT>(grp, g, S, c, b, gid, ctrl);
+    }
+};
+
+// Persistent solver: every CTA takes items until the queue is empty.  Policy
+// P solves one graph with a group (PlainSolve here; general weights in
+// pradmm_batch_sigma.cu).
+template <typename P, int WPB>
+__global__ void __launch_bounds__(WPB * 32) k_batch(P solve, BatchDev b, Ctrl* ctrl) {
     __shared__ double sh[32];
     __shared__ int s_item;
     const CtaGroup cta{sh};
@@ -190,10 +206,10 @@ __global__ void __launch_bounds__(WPB * 32) k_batch(GraphDev<R> g, StateDev<R> S
         if (it >= b.n_items) break;
         const int2 item = b.items[it];  // (first position in order, graphs; < 0: one graph for the CTA)
         if (item.y < 0) {
-            solve_graph<R, INERT>(cta, g, S, c, b, b.order[item.x], ctrl);
+            solve(cta, b, b.order[item.x], ctrl);
         } else {
             const int w = threadIdx.x >> 5;
-            if (w < item.y) solve_graph<R, INERT>(warp, g, S, c, b, b.order[item.x + w], ctrl);
+            if (w < item.y) solve(warp, b, b.order[item.x + w], ctrl);
             __syncthreads();
         }
     }
@@ -202,8 +218,8 @@ __global__ void __launch_bounds__(WPB * 32) k_batch(GraphDev<R> g, StateDev<R> S
 // Persistent solver with clusters: each cluster first takes cluster items
 // (graphs too large for one CTA) from their queue, largest first; once that
 // queue is empty every CTA takes the CTA and warp-pack items as k_batch does.
-template <typename R, int WPB, bool INERT>
-__global__ void __launch_bounds__(WPB * 32) k_batch_cl(GraphDev<R> g, StateDev<R> S, Coef<R> c, BatchDev b, Ctrl* ctrl) {
+template <typename P, int WPB>
+__global__ void __launch_bounds__(WPB * 32) k_batch_cl(P solve, BatchDev b, Ctrl* ctrl) {
     __shared__ double sh[32];
     __shared__ double slots[2 * kMaxCluster * 4];
     __shared__ int s_item, s_bank;
@@ -216,7 +232,7 @@ __global__ void __launch_bounds__(WPB * 32) k_batch_cl(GraphDev<R> g, StateDev<R
         const int it = *cl.map_shared_rank(&s_item, 0);
         cl.sync();  // every CTA has read the item before rank 0 fetches the next
         if (it >= b.n_big) break;
-        solve_graph<R, INERT>(cgp, g, S, c, b, b.order[it], ctrl);
+        solve(cgp, b, b.order[it], ctrl);
     }
     const CtaGroup cta{sh};
     const WarpGroup warp;
@@ -228,19 +244,18 @@ __global__ void __launch_bounds__(WPB * 32) k_batch_cl(GraphDev<R> g, StateDev<R
         if (it >= b.n_items) break;
         const int2 item = b.items[it];
         if (item.y < 0) {
-            solve_graph<R, INERT>(cta, g, S, c, b, b.order[item.x], ctrl);
+            solve(cta, b, b.order[item.x], ctrl);
         } else {
             const int w = threadIdx.x >> 5;
-            if (w < item.y) solve_graph<R, INERT>(warp, g, S, c, b, b.order[item.x + w], ctrl);
+            if (w < item.y) solve(warp, b, b.order[item.x + w], ctrl);
             __syncthreads();
         }
     }
     cl.sync();  // no CTA leaves while a peer could still address its shared memory
 }
 
-template <typename R, int WPB, bool INERT>
-cudaError_t launch_cl(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const BatchDev& b, Ctrl* ctrl,
-                      int grid, int cluster, cudaStream_t st) {
+template <typename P, int WPB>
+cudaError_t launch_cl(const P& solve, const BatchDev& b, Ctrl* ctrl, int grid, int cluster, cudaStream_t st) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(WPB * 32);
@@ -252,10 +267,10 @@ cudaError_t launch_cl(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>&
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_batch_cl<R, WPB, INERT>, g, s, c, b, ctrl);
+    return cudaLaunchKernelEx(&cfg, k_batch_cl<P, WPB>, solve, b, ctrl);
 }
 
-template <typename R, int WPB, bool INERT>
+template <typename P, int WPB>
 cudaError_t occupancy_cl(int cluster, int* clusters) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)cluster);
@@ -267,7 +282,52 @@ cudaError_t occupancy_cl(int cluster, int* clusters) {
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaOccupancyMaxActiveClusters(clusters, k_batch_cl<R, WPB, INERT>, &cfg);
+    return cudaOccupancyMaxActiveClusters(clusters, k_batch_cl<P, WPB>, &cfg);
+}
+
+// One persistent launch of policy P: cluster > 1 the cluster kernel (grid a
+// multiple of cluster), else k_batch; block 64, 128, 256 or 512.
+template <typename P>
+cudaError_t launch_persistent(const P& solve, const BatchDev& b, Ctrl* ctrl, int grid, int block, int cluster,
+                              cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(b.next, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    if (cluster > 1) {
+        if ((e = cudaMemsetAsync(b.next_big, 0, sizeof(int), st)) != cudaSuccess) return e;
+        switch (block) {
+            case 64: return launch_cl<P, 2>(solve, b, ctrl, grid, cluster, st);
+            case 128: return launch_cl<P, 4>(solve, b, ctrl, grid, cluster, st);
+            case 512: return launch_cl<P, 16>(solve, b, ctrl, grid, cluster, st);
+            default: return launch_cl<P, 8>(solve, b, ctrl, grid, cluster, st);
+        }
+    }
+    switch (block) {
+        case 64: k_batch<P, 2><<<grid, 64, 0, st>>>(solve, b, ctrl); break;
+        case 128: k_batch<P, 4><<<grid, 128, 0, st>>>(solve, b, ctrl); break;
+        case 512: k_batch<P, 16><<<grid, 512, 0, st>>>(solve, b, ctrl); break;
+        default: k_batch<P, 8><<<grid, 256, 0, st>>>(solve, b, ctrl); break;
+    }
+    return cudaGetLastError();
+}
+
+template <typename P>
+cudaError_t persistent_occupancy(int block, int* bps) {
+    switch (block) {
+        case 64: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_batch<P, 2>, 64, 0);
+        case 128: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_batch<P, 4>, 128, 0);
+        case 512: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_batch<P, 16>, 512, 0);
+        default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_batch<P, 8>, 256, 0);
+    }
+}
+
+template <typename P>
+cudaError_t persistent_cluster_occupancy(int block, int cluster, int* clusters) {
+    switch (block) {
+        case 64: return occupancy_cl<P, 2>(cluster, clusters);
+        case 128: return occupancy_cl<P, 4>(cluster, clusters);
+        case 512: return occupancy_cl<P, 16>(cluster, clusters);
+        default: return occupancy_cl<P, 8>(cluster, clusters);
+    }
 }
 
 }  // namespace
@@ -275,44 +335,17 @@ cudaError_t occupancy_cl(int cluster, int* clusters) {
 template <typename R, bool INERT>
 cudaError_t launch_batch(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const BatchDev& b, Ctrl* ctrl,
                          int grid, int block, int cluster, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(b.next, 0, sizeof(int), st);
-    if (e != cudaSuccess) return e;
-    if (cluster > 1) {
-        if ((e = cudaMemsetAsync(b.next_big, 0, sizeof(int), st)) != cudaSuccess) return e;
-        switch (block) {
-            case 64: return launch_cl<R, 2, INERT>(g, s, c, b, ctrl, grid, cluster, st);
-            case 128: return launch_cl<R, 4, INERT>(g, s, c, b, ctrl, grid, cluster, st);
-            case 512: return launch_cl<R, 16, INERT>(g, s, c, b, ctrl, grid, cluster, st);
-            default: return launch_cl<R, 8, INERT>(g, s, c, b, ctrl, grid, cluster, st);
-        }
-    }
-    switch (block) {
-        case 64: k_batch<R, 2, INERT><<<grid, 64, 0, st>>>(g, s, c, b, ctrl); break;
-        case 128: k_batch<R, 4, INERT><<<grid, 128, 0, st>>>(g, s, c, b, ctrl); break;
-        case 512: k_batch<R, 16, INERT><<<grid, 512, 0, st>>>(g, s, c, b, ctrl); break;
-        default: k_batch<R, 8, INERT><<<grid, 256, 0, st>>>(g, s, c, b, ctrl); break;
-    }
-    return cudaGetLastError();
+    return launch_persistent(PlainSolve<R, INERT>{g, s, c}, b, ctrl, grid, block, cluster, st);
 }
 
 template <typename R, bool INERT>
 cudaError_t batch_occupancy(int block, int* bps) {
-    switch (block) {
-        case 64: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_batch<R, 2, INERT>, 64, 0);
-        case 128: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_batch<R, 4, INERT>, 128, 0);
-        case 512: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_batch<R, 16, INERT>, 512, 0);
-        default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_batch<R, 8, INERT>, 256, 0);
-    }
+    return persistent_occupancy<PlainSolve<R, INERT>>(block, bps);
 }
 
 template <typename R, bool INERT>
 cudaError_t batch_cluster_occupancy(int block, int cluster, int* clusters) {
-    switch (block) {
-        case 64: return occupancy_cl<R, 2, INERT>(cluster, clusters);
-        case 128: return occupancy_cl<R, 4, INERT>(cluster, clusters);
-        case 512: return occupancy_cl<R, 16, INERT>(cluster, clusters);
-        default: return occupancy_cl<R, 8, INERT>(cluster, clusters);
-    }
+    return persistent_cluster_occupancy<PlainSolve<R, INERT>>(block, cluster, clusters);
 }
 
 }  // namespace pradmm

@@ -240,10 +240,19 @@ template <typename R, bool INERT>
 cudaError_t batch_occupancy(int block, int* bps);
 template <typename R, bool INERT>
 cudaError_t batch_cluster_occupancy(int block, int cluster, int* clusters);
+// The batched form with general weights (pradmm_batch_sigma.cu).
+template <typename R, bool INERT>
+cudaError_t launch_batch_sigma(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const SigmaDev<R>& sg,
+                               const BatchDev& b, Ctrl* ctrl, int grid, int block, int cluster, cudaStream_t st);
+template <typename R, bool INERT>
+cudaError_t batch_sigma_occupancy(int block, int* bps);
+template <typename R, bool INERT>
+cudaError_t batch_sigma_cluster_occupancy(int block, int cluster, int* clusters);
+// S1, S2: Sigma_1, Sigma_2 on the device (16 doubles each), or NULL for scalar weights.
 template <typename R>
 cudaError_t launch_batch_objective(const GraphDev<R>& g, const StateDev<R>& s, const double* qe64,
-                                   const double* te64, const double* ka64, const double* om64,
-                                   const BatchDev& b, double* F, int G, cudaStream_t st);
+                                   const double* te64, const double* ka64, const double* om64, const double* S1,
+                                   const double* S2, const BatchDev& b, double* F, int G, cudaStream_t st);
 
 // ---- reverse mode (adjoint) ------------------------------------------------------
 

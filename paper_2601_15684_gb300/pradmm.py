@@ -95,6 +95,7 @@ _SIGS = {
     "pradmm_batch_autotune": (ctypes.c_int, [_h, ctypes.c_int32, _i32, _i32, _i32, _i32]),
     "pradmm_batch_autotune_profiled": (ctypes.c_int, [_h, ctypes.c_double, _i32, _i32, _i32, _i32]),
     "pradmm_batch_init_odometry": (ctypes.c_int, [_h]),
+    "pradmm_batch_set_sigma": (ctypes.c_int, [_h, _d, _d]),
     "pradmm_batch_set_state": (ctypes.c_int, [_h, _d, _d]),
     "pradmm_batch_solve": (ctypes.c_int, [_h, ctypes.c_double, ctypes.c_int32, _i32, _d, _d, _i32]),
     "pradmm_batch_objectives": (ctypes.c_int, [_h, _d]),
@@ -531,6 +532,12 @@ class Batch:
 
     def init_odometry(self):
         _check(load().pradmm_batch_init_odometry(self.h), "pradmm_batch_init_odometry")
+
+    def set_sigma(self, Sigma1=None, Sigma2=None):
+        """General 4x4 weight matrices for every graph; both None: Sigma = I."""
+        S1 = None if Sigma1 is None else _f64(Sigma1, (4, 4))
+        S2 = None if Sigma2 is None else _f64(Sigma2, (4, 4))
+        _check(load().pradmm_batch_set_sigma(self.h, _dp(S1), _dp(S2)), "pradmm_batch_set_sigma")
 
     def set_state(self, q, t):
         q, t = _f64(q, (self.N, 4)), _f64(t, (self.N, 3))

@@ -13,7 +13,7 @@ random rotation) and Sigma_2 = diag(1, 0.5, 2, 1).  With --batch G it
 instead solves G random-walk graphs of the batched workload's distribution
 (log-uniform sizes in [50, 20000]) for exactly --iters iterations in one
 persistent launch, with the schedule --schedule block,warp_max_n,cluster,
-cluster_min_n.
+cluster_min_n (and the general weights above with --sigma).
 """
 from __future__ import annotations
 
@@ -43,6 +43,11 @@ def main(argv=None) -> int:
         graphs = synth.batch_graphs(count=a.batch)
         sch = [int(x) for x in a.schedule.split(",")]
         with pradmm.Batch(graphs, precision=a.precision, inertia=a.inertia) as B:
+            if a.sigma:
+                import numpy as np
+                rng = np.random.default_rng(0)
+                Q, _ = np.linalg.qr(rng.normal(size=(4, 4)))
+                B.set_sigma(Q @ np.diag([1.0, 2.0, 0.5, 4.0]) @ Q.T, np.diag([1.0, 0.5, 2.0, 1.0]))
             B.set_schedule(*sch)
             B.init_odometry()
             t0 = time.perf_counter()

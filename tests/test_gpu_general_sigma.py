@@ -159,3 +159,94 @@ def test_hard_case_of_the_p_update(P, precision, tol):
     assert relerr(gpu["p"], orc["p"]) <= tol
     if precision == 1:
         assert fallbacks >= 1
+
+
+# ---- the batched form with general weights ---------------------------------------
+
+def _walks(count, seed, n_max):
+    rng = np.random.default_rng(seed)
+    ns = np.exp(rng.uniform(np.log(20), np.log(n_max), count)).round().astype(int)
+    dens = rng.uniform(0.5, 3.0, count)
+    return [synth.random_walk_graph(int(ns[k]), n_closures=None, closure_density=float(dens[k]), sigma_r=0.02,
+                                    sigma_t=0.1, seed=3000 + k, name=f"s{k}") for k in range(count)]
+
+
+@pytest.mark.parametrize("schedule", [(256, 256, 1, 0), (128, 0, 8, 50)])
+def test_batch_general_sigma_matches_oracle(P, schedule):
+    # FP64: every graph against the general-Sigma oracle for the iterations it
+    # ran (warp/CTA items, or 8-CTA clusters above 50 poses), and the per-graph
+    # objectives with the Sigma-weighted norms
+    graphs = _walks(5, seed=21, n_max=300)
+    rng = np.random.default_rng(22)
+    S1, S2 = _spd(rng), _spd(rng)
+    with P.Batch(graphs, precision=0) as B:
+        B.set_sigma(S1, S2)
+        B.set_schedule(*schedule)
+        B.init_odometry()
+        res = B.solve(rel_tol=1e-3, max_iter=40)
+        st = B.state()
+        F = B.objectives()
+    for k, g in enumerate(graphs):
+        q0, t0 = oracle.init_odometry(g)
+        orc = oracle.init_state(q0, t0)
+        for _ in range(int(res["iters"][k])):
+            orc, _, _ = gs.iterate(g, PARAMS, S1, S2, orc)
+        sl = {key: v[B.offsets[k]:B.offsets[k + 1]] for key, v in st.items()}
+        for key in KEYS:
+            assert relerr(sl[key], orc[key]) <= 1e-9, (k, key, relerr(sl[key], orc[key]))
+        Fo = gs.objective(g, S1, S2, orc["p"], orc["t"])
+        assert abs(F[k] - Fo) <= 1e-10 * max(Fo, 1.0), (k, F[k], Fo)
+    conv = res["status"] == P.PRADMM_OK
+    assert (res["e_last"][conv] <= 1e-3 * res["e_first"][conv]).all()
+
+
+def test_batch_general_sigma_fp32_matches_single_solver(P):
+    # FP32, the FP64 re-solves included: the batched form does them in the
+    # sweep's own thread, the single solver in a separate kernel, from the same
+    # FP32 data
+    graphs = _walks(8, seed=23, n_max=3000)
+    rng = np.random.default_rng(24)
+    S1, S2 = _spd(rng), _spd(rng)
+    with P.Batch(graphs, precision=1) as B:
+        B.set_sigma(S1, S2)
+        B.init_odometry()
+        B.solve(rel_tol=0.0, max_iter=15)
+        st = B.state()
+    for k, g in enumerate(graphs):
+        with P.Solver(g, precision=1) as S:
+            S.set_sigma(S1, S2)
+            S.init_odometry()
+            S.step(15)
+            ref = S.state()
+        sl = {key: v[B.offsets[k]:B.offsets[k + 1]] for key, v in st.items()}
+        for key in ("p", "q", "t", "s"):
+            assert relerr(sl[key], ref[key]) <= 1e-5, (k, key, relerr(sl[key], ref[key]))
+
+
+def test_batch_general_sigma_inertial_and_back_to_scalar(P):
+    graphs = _walks(4, seed=25, n_max=200)
+    rng = np.random.default_rng(26)
+    S1, S2 = _spd(rng), _spd(rng)
+    theta = 0.5
+    with P.Batch(graphs, precision=0, inertia=theta) as B:
+        B.set_sigma(S1, S2)
+        B.init_odometry()
+        B.solve(rel_tol=0.0, max_iter=12)
+        st = B.state()
+        B.set_sigma(None, None)  # scalar weights again
+        B.init_odometry()
+        B.solve(rel_tol=0.0, max_iter=6)
+        st2 = B.state()
+    for k, g in enumerate(graphs):
+        q0, t0 = oracle.init_odometry(g)
+        orc, prev = oracle.init_state(q0, t0), None
+        for _ in range(12):
+            orc, prev, _, _ = gs.iterate_inertial(g, PARAMS, S1, S2, orc, theta, prev)
+        sl = {key: v[B.offsets[k]:B.offsets[k + 1]] for key, v in st.items()}
+        for key in KEYS:
+            assert relerr(sl[key], orc[key]) <= 1e-9, (k, key, relerr(sl[key], orc[key]))
+        o2, _, _, _ = oracle.iterate_inertial(g, oracle.make_params(beta1=1.0, beta2=1.0, tau=1.5),
+                                              oracle.init_state(q0, t0), theta, 6)
+        sl2 = {key: v[B.offsets[k]:B.offsets[k + 1]] for key, v in st2.items()}
+        for key in KEYS:
+            assert relerr(sl2[key], o2[key]) <= 1e-10, (k, key)
