@@ -7,6 +7,11 @@ with the device-side while loop, default block and grids).
   one iteration of this graph in well under a second), with the FP32 rules of
   the parity tests: p, q, t, s within 1e-5 relative; multipliers within 1e-5
   of the scale they are formed from.  The odometry start is compared first.
+- the 4,096-walk batch (14.0M poses, 37.4M edges), solved as the benchmark
+  solves it (a first solve, the profiled schedule search, then the solve to a
+  relative residual of 1e-6, at most 3,000 iterations): the stopping rule on every graph, and sampled graphs (the
+  largest and four seeded picks) against the FP64 oracle run for the
+  iterations each took, no further from it than the single FP32 solver.
 - helix25k (25,000 poses, 74,799 edges): 2,000 iterations.  FP64 path:
   final objective within 1e-6 relative of the oracle's.  FP32 path: the final
   objective's relative error is stated, not guaranteed (FP32 cancellation in
@@ -119,3 +124,37 @@ def test_lattice1m_general_sigma_p_update_sampled(P, precision, tol):
         A1, b1 = gs.p_system(g, params, S1, S2, st, int(i))
         x, _, _ = gs.trs_sphere(A1, b1, st["p"][i])
         assert np.linalg.norm(p1[i] - x) <= tol, (int(i), np.linalg.norm(p1[i] - x))
+
+
+def test_batch_4096_walks_at_the_benchmark_configuration(P):
+    import bench  # the benchmark's batch recipe and its parallel graph builder
+    graphs = bench._batch_workload(bench._batch_args())
+    assert len(graphs) == 4096
+    with P.Batch(graphs, precision=1) as B:
+        B.init_odometry()
+        B.solve(rel_tol=1e-6, max_iter=3000)  # the first solve, whose iteration profile the search takes
+        B.init_odometry()
+        B.autotune_profiled()
+        B.init_odometry()
+        res = B.solve(rel_tol=1e-6, max_iter=3000)
+        st = B.state()
+        offs = B.offsets
+    conv = res["status"] == P.PRADMM_OK
+    assert conv.mean() > 0.9
+    assert (res["e_last"][conv] <= 1e-6 * res["e_first"][conv]).all()
+    assert (res["iters"][~conv] == 3000).all()
+    rng = np.random.default_rng(11)
+    pick = [int(np.argmax([g.n for g in graphs]))] + [int(k) for k in rng.choice(4096, 4, replace=False)]
+    prm = _oparams()
+    for k in pick:
+        g, K = graphs[k], int(res["iters"][k])
+        q0, t0 = oracle.init_odometry(g)
+        orc, _, _ = oracle.iterate(g, prm, oracle.init_state(q0, t0), K)
+        with P.Solver(g, precision=1) as S:
+            S.init_odometry()
+            S.step(K)
+            ref = S.state()
+        sl = {key: v[offs[k]:offs[k + 1]] for key, v in st.items()}
+        for key in ("p", "q", "t", "s"):
+            eb, ep = relerr(sl[key], orc[key]), relerr(ref[key], orc[key])
+            assert eb <= 3.0 * ep + 1e-6, (k, g.n, K, key, eb, ep)
