@@ -105,10 +105,9 @@ typedef struct {
                             general weights (pradmm_set_sigma), in the batched
                             form (each pradmm_batch_solve starts the
                             extrapolation afresh) and in the reverse mode
-                            (scalar weights; the recording starts afresh and
-                            keeps every iterate); setting a state or the
-                            weights restarts the extrapolation
-                            (x^{k-1} := x^k). */
+                            (scalar weights; the recording starts afresh);
+                            setting a state or the weights restarts the
+                            extrapolation (x^{k-1} := x^k). */
 } pradmm_params;
 
 /* Defaults: beta1 = beta2 = 1, relax = 1.5, gamma = {1, 1e-3, 1e-3, 1e-3},
@@ -260,8 +259,7 @@ pradmm_status pradmm_set_sigma(pradmm_t h, const double* Sigma1, const double* S
  * iterate is kept and the reverse pass recomputes nothing); negative values
  * return PRADMM_ERR_ARG.  With a nonzero inertia the recording restarts the
  * extrapolation (x^{-1} := x^0, whose adjoint then holds both shares) and
- * keeps every iterate: ckpt_every must be 0 or 1 (PRADMM_ERR_ARG otherwise),
- * PRADMM_ERR_NOMEM when that tape does not fit.  The tape stays valid until the state changes
+ * each slot also keeps x^{k-1} (q, t, s and p: 44 n reals a slot).  The tape stays valid until the state changes
  * (set_state, init_odometry, step, solve, another record). */
 pradmm_status pradmm_adjoint_record(pradmm_t h, int32_t iters, int32_t ckpt_every);
 

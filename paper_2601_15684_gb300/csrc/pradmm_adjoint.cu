@@ -534,6 +534,20 @@ __global__ void __launch_bounds__(256) k_tape_copy(const TapeRec* __restrict__ r
         dst[i] = src[i];
 }
 
+// Inertial recording: before the s/z + next-p sweep of iteration k overwrites
+// p^k, keep it in the state block's p^{k-1} area, so the checkpoint copied
+// after the iteration (x^{k+1}) carries its p^{(k+1)-1}.
+template <typename R>
+__global__ void __launch_bounds__(256) k_keep_pk(const Ctrl* __restrict__ ctrl, const R* p0, const R* p1, R* dst,
+                                                 int64_t n) {
+    if (ctrl->halt) return;
+    const R* src = (ctrl->iter & 1) ? p1 : p0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const R4<R> v = IO<R>::ld(src, i);
+        IO<R>::st(dst, i, v.a, v.b, v.c, v.d);
+    }
+}
+
 int grid_for(int64_t n, int block) {
     const int64_t gmax = 152 * 16;
     int64_t gb = (n + block - 1) / block;
@@ -558,6 +572,12 @@ cudaError_t launch_adj_iteration(const GraphDev<R>& g, const AdjDev<R>& A, const
     k_adj_p<R><<<grid, block, 0, st>>>(g, A, X, c);
     if (g.m > 0) k_adj_grad<R><<<grid_for(g.m, 256), 256, 0, st>>>(g, A, X, out_src);
     k_adj_v<R><<<grid, block, 0, st>>>(g, A, X, c, more);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_keep_pk(const Ctrl* ctrl, const R* p0, const R* p1, R* dst, int64_t n, int grid, cudaStream_t st) {
+    k_keep_pk<R><<<grid, 256, 0, st>>>(ctrl, p0, p1, dst, n);
     return cudaGetLastError();
 }
 
@@ -597,7 +617,8 @@ cudaError_t launch_tape_arm(Ctrl* ctrl, long long iter, cudaStream_t st) {
                                             int, cudaStream_t);                                                    \
     template cudaError_t launch_adj_iteration<R>(const GraphDev<R>&, const AdjDev<R>&, const AdjStep<R>&,             \
                                                  const Coef<R>&, const int32_t*, int, int, cudaStream_t);          \
-    template cudaError_t launch_adj_edges<R>(const double*, const double*, int64_t, R*, R*, cudaStream_t);
+    template cudaError_t launch_adj_edges<R>(const double*, const double*, int64_t, R*, R*, cudaStream_t);        \
+    template cudaError_t launch_keep_pk<R>(const Ctrl*, const R*, const R*, R*, int64_t, int, cudaStream_t);
 
 PRADMM_ADJ_INST(float)
 PRADMM_ADJ_INST(double)

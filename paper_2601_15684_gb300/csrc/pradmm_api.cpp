@@ -100,8 +100,10 @@ struct pradmm_s {
     double* sigma_d = nullptr;         // 32 doubles: S1, S2 (objective)
     pradmm::FbRec* fb_q = nullptr;     // FP32 handles: queued FP64 p re-solves (n records)
     unsigned int* fb_n = nullptr;      // their per-iteration counters (2)
-    void* state_block = nullptr;       // t, s, q, p[0], p[1], lam, z: 28 n reals, contiguous
+    void* state_block = nullptr;       // t, s, q, p[0], p[1], lam, z: 28 n reals, contiguous; the
+                                       // inertial variant appends q, t, s ^{k-1} and p^{k-1} (44 n)
     void* prev_block = nullptr;        // inertial variant: q^{k-1}, t^{k-1}, s^{k-1}, 12 n reals
+    void* pm1 = nullptr;               // inertial variant: p^{k-1} for the tape, 4 n reals
     bool l2_on = false;                // this handle holds an L2 set-aside
     cudaAccessPolicyWindow window{};   // persisting window over t, s, q, p[0], p[1]
     uint64_t epoch = 0;                // bumped by every change of the state
@@ -495,7 +497,8 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
     ST(dalloc(h, &h->ka64, h->out_slots));
     ST(dalloc(h, &h->om64, h->out_slots));
     // one block, gathered arrays first (the L2 persistence window covers them)
-    ST(valloc(h, &h->state_block, 28 * (size_t)n));
+    const bool inert = h->prm.inertia != 0.0;
+    ST(valloc(h, &h->state_block, (inert ? 44 : 28) * (size_t)n));
     {
         char* b = static_cast<char*>(h->state_block);
         const size_t a = 4 * (size_t)n * h->rsize;
@@ -506,8 +509,11 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
         h->p[1] = b + 4 * a;
         h->lam = b + 5 * a;
         h->z = b + 6 * a;
+        if (inert) {
+            h->prev_block = b + 7 * a;  // q, t, s of x^{k-1}
+            h->pm1 = b + 10 * a;        // p^{k-1} at the last recorded iteration's start
+        }
     }
-    if (h->prm.inertia != 0.0) ST(valloc(h, &h->prev_block, 12 * (size_t)n));
     ST(dalloc(h, &h->inv2_d, n));
     ST(dalloc(h, &h->inv3_d, n));
     ST(dalloc(h, &h->inv4_d, n));
@@ -861,6 +867,9 @@ pradmm_status ensure_graph(pradmm_s* h, bool record = false) {
     } else {
         e1 = pradmm::launch_q<R>(g, S, c, L);
         e2 = pradmm::launch_t<R>(g, S, c, L);
+        if (record && h->pm1)
+            e2 = pradmm::launch_keep_pk<R>(h->ctrl, S.p[0], S.p[1], static_cast<R*>(h->pm1), h->n, h->grids[3],
+                                           h->stream);
         e3 = pradmm::launch_sp<R>(g, S, c, L);
         if (record) e5 = pradmm::launch_tape_copy(h->tape_rec, h->ctrl, h->state_block, h->grids[3], h->stream);
     }
@@ -1091,8 +1100,10 @@ pradmm_status profile_impl(pradmm_s* h, int32_t iters, double* ms_out) {
 // iteration k holds p^k in p[k & 1] and p^{k+1} in p[(k+1) & 1], exactly as
 // the handle's own state does, so the forward sweep kernels run on a slot
 // unchanged.
+// A tape slot in the state block's layout; with `inert` its previous iterates
+// (q, t, s) follow at 28 n, and p^{k-1} of a checkpoint at 40 n.
 template <typename R>
-pradmm::StateDev<R> slot_state(void* base, int64_t n) {
+pradmm::StateDev<R> slot_state(void* base, int64_t n, bool inert) {
     R* b = static_cast<R*>(base);
     pradmm::StateDev<R> S;
     S.t = b;
@@ -1102,6 +1113,11 @@ pradmm::StateDev<R> slot_state(void* base, int64_t n) {
     S.p[1] = b + 16 * n;
     S.lam = b + 20 * n;
     S.z = b + 24 * n;
+    if (inert) {
+        S.qprev = b + 28 * n;
+        S.tprev = b + 32 * n;
+        S.sprev = b + 36 * n;
+    }
     return S;
 }
 
@@ -1109,7 +1125,7 @@ pradmm::StateDev<R> slot_state(void* base, int64_t n) {
 // still starts on a 16-byte boundary for float4 / double2 accesses.
 int64_t pad4(int64_t n) { return (n + 3) & ~int64_t(3); }
 
-size_t slot_bytes(const pradmm_s* h) { return 28 * (size_t)h->n * h->rsize; }
+size_t slot_bytes(const pradmm_s* h) { return (h->prm.inertia != 0.0 ? 44 : 28) * (size_t)h->n * h->rsize; }
 
 void* tape_slot(pradmm_s* h, int64_t idx) { return static_cast<char*>(h->tape) + (size_t)idx * slot_bytes(h); }
 
@@ -1152,10 +1168,8 @@ pradmm_status adjoint_record(pradmm_s* h, int32_t iters, int32_t ckpt_every) {
     if (iters < 0) return fail(PRADMM_ERR_ARG, "iters must be >= 0");
     if (ckpt_every < 0) return fail(PRADMM_ERR_ARG, "ckpt_every must be >= 0 (0: chosen from free device memory)");
     const bool inert = h->prm.inertia != 0.0;
-    if (inert && ckpt_every > 1)
-        return fail(PRADMM_ERR_ARG, "the inertial reverse mode keeps every iterate: ckpt_every must be 0 or 1");
     h->tape_valid = false;
-    const int C = iters == 0 || inert ? 1 : (ckpt_every == 0 ? auto_ckpt(h, iters) : std::min(ckpt_every, iters));
+    const int C = iters == 0 ? 1 : (ckpt_every == 0 ? auto_ckpt(h, iters) : std::min(ckpt_every, iters));
     const int nck = iters == 0 ? 1 : (iters + C - 1) / C + 1;
     const size_t need = tape_slots(iters, C) * slot_bytes(h);
     if (need > h->tape_bytes) {
@@ -1200,6 +1214,9 @@ pradmm_status adjoint_record(pradmm_s* h, int32_t iters, int32_t ckpt_every) {
             for (int k = 0; k < iters; ++k) {
                 CU(pradmm::launch_q<R>(g, S, c, L));
                 CU(pradmm::launch_t<R>(g, S, c, L));
+                if (h->pm1)
+                    CU(pradmm::launch_keep_pk<R>(h->ctrl, S.p[0], S.p[1], static_cast<R*>(h->pm1), h->n, h->grids[3],
+                                                 h->stream));
                 CU(pradmm::launch_sp<R>(g, S, c, L));
                 CU(pradmm::launch_tape_copy(h->tape_rec, h->ctrl, h->state_block, h->grids[3], h->stream));
             }
@@ -1278,7 +1295,8 @@ cudaError_t enqueue_reverse(pradmm_s* h, const pradmm::AdjDev<R>& A) {
     do {                                    \
         if ((e = (call)) != cudaSuccess) return e; \
     } while (0)
-    const auto SK = slot_state<R>(tape_slot(h, nck - 1), n);
+    const bool inert = h->prm.inertia != 0.0;
+    const auto SK = slot_state<R>(tape_slot(h, nck - 1), n, inert);
     RQ(pradmm::launch_adj_seed<R>(g, A, c, SK.s, SK.z, h->block, st));
     const int64_t seg0 = nck;  // first recompute slot
     pradmm::Launch L = h->launch(false);
@@ -1294,7 +1312,7 @@ cudaError_t enqueue_reverse(pradmm_s* h, const pradmm::AdjDev<R>& A) {
             RQ(pradmm::launch_tape_arm(h->tape_ctrl, kc, st));
             for (int j = 0; j + 1 < len; ++j) {
                 RQ(cudaMemcpyAsync(slot[j + 1], slot[j], slot_bytes(h), cudaMemcpyDeviceToDevice, st));
-                const auto S = slot_state<R>(slot[j + 1], n);
+                const auto S = slot_state<R>(slot[j + 1], n, inert);
                 RQ(pradmm::launch_q<R>(g, S, c, L));
                 RQ(pradmm::launch_t<R>(g, S, c, L));
                 RQ(pradmm::launch_sp<R>(g, S, c, L));
@@ -1302,8 +1320,8 @@ cudaError_t enqueue_reverse(pradmm_s* h, const pradmm::AdjDev<R>& A) {
         }
         for (int j = len - 1; j >= 0; --j) {
             const long long k = kc + j;
-            const auto S0 = slot_state<R>(slot[j], n);
-            const auto S1 = slot_state<R>(slot[j + 1], n);
+            const auto S0 = slot_state<R>(slot[j], n, inert);
+            const auto S1 = slot_state<R>(slot[j + 1], n, inert);
             pradmm::AdjStep<R> X;
             X.pc = S0.p[k & 1];
             X.pn = S0.p[(k + 1) & 1];
@@ -1314,9 +1332,10 @@ cudaError_t enqueue_reverse(pradmm_s* h, const pradmm::AdjDev<R>& A) {
             X.z = S0.z;
             X.qn = S1.q;
             X.tn = S1.t;
-            if (c.theta != R(0)) {
-                // p^{k-1}: the previous slot (the inertial tape keeps every iterate), p^{-1} = p^0
-                X.pp = ci > 0 ? slot_state<R>(tape_slot(h, ci - 1), n).p[(k - 1) & 1] : X.pc;
+            if (inert) {
+                // p^{k-1}: the previous slot of the segment, or the checkpoint's own copy
+                X.pp = j > 0 ? static_cast<const R*>(slot_state<R>(slot[j - 1], n, inert).p[(k - 1) & 1])
+                             : static_cast<const R*>(slot[0]) + 40 * n;
             }
             RQ(pradmm::launch_adj_iteration<R>(g, A, X, c, h->out_src_d, (ci == 0 && j == 0) ? 0 : 1, h->block, st));
         }
@@ -1528,6 +1547,7 @@ pradmm_status restart_inertia(pradmm_s* h) {
     CU(cudaMemcpyAsync(b + a, h->t, a, cudaMemcpyDeviceToDevice, st));
     CU(cudaMemcpyAsync(b + 2 * a, h->s, a, cudaMemcpyDeviceToDevice, st));
     CU(cudaMemcpyAsync(h->p[(k + 1) & 1], h->p[k & 1], a, cudaMemcpyDeviceToDevice, st));
+    if (h->pm1) CU(cudaMemcpyAsync(h->pm1, h->p[k & 1], a, cudaMemcpyDeviceToDevice, st));  // the tape's p^{k-1}
     CU(cudaStreamSynchronize(st));
     return PRADMM_OK;
 }

@@ -114,6 +114,10 @@ struct TapeRec {
     long long k0, K, C, slot_bytes;
 };
 
+// Inertial recording: copies p[ctrl->iter & 1] (p^k, before the s/z + next-p
+// sweep overwrites it) to dst (n 4-real rows).
+template <typename R>
+cudaError_t launch_keep_pk(const Ctrl* ctrl, const R* p0, const R* p1, R* dst, int64_t n, int grid, cudaStream_t st);
 // Fills *rec with k0 = ctrl->iter (read on the device) and the arguments.
 cudaError_t launch_tape_rec_arm(TapeRec* rec, const Ctrl* ctrl, void* base, long long K, long long C,
                                 long long slot_bytes, cudaStream_t st);
