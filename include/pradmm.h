@@ -258,8 +258,9 @@ pradmm_status pradmm_set_sigma(pradmm_t h, const double* Sigma1, const double* S
  * one whose tape fits in half of the free memory (1 where it fits: every
  * iterate is kept and the reverse pass recomputes nothing); negative values
  * return PRADMM_ERR_ARG.  With a nonzero inertia the recording restarts the
- * extrapolation (x^{-1} := x^0, whose adjoint then holds both shares) and
- * each slot also keeps x^{k-1} (q, t, s and p: 44 n reals a slot).  The tape stays valid until the state changes
+ * extrapolation (x^{-1} := x^0, whose adjoint then holds both shares); with
+ * a spacing above 1 each slot also keeps x^{k-1} (q, t, s and p: 44 n reals
+ * a slot), with spacing 1 the previous slot holds it.  The tape stays valid until the state changes
  * (set_state, init_odometry, step, solve, another record). */
 pradmm_status pradmm_adjoint_record(pradmm_t h, int32_t iters, int32_t ckpt_every);
 

@@ -1125,12 +1125,18 @@ pradmm::StateDev<R> slot_state(void* base, int64_t n, bool inert) {
 // still starts on a 16-byte boundary for float4 / double2 accesses.
 int64_t pad4(int64_t n) { return (n + 3) & ~int64_t(3); }
 
-size_t slot_bytes(const pradmm_s* h) { return (h->prm.inertia != 0.0 ? 44 : 28) * (size_t)h->n * h->rsize; }
+// A tape slot for checkpoint spacing C: the state block, and for the inertial
+// variant with C > 1 also its x^{k-1} part (segments are recomputed from a
+// checkpoint; with C = 1 the previous slot holds x^{k-1}).
+size_t slot_bytes(const pradmm_s* h, int C) {
+    return (h->prm.inertia != 0.0 && C > 1 ? 44 : 28) * (size_t)h->n * h->rsize;
+}
+bool slot_inert(const pradmm_s* h) { return h->prm.inertia != 0.0 && h->tape_C > 1; }
 
-void* tape_slot(pradmm_s* h, int64_t idx) { return static_cast<char*>(h->tape) + (size_t)idx * slot_bytes(h); }
+void* tape_slot(pradmm_s* h, int64_t idx) { return static_cast<char*>(h->tape) + (size_t)idx * slot_bytes(h, h->tape_C); }
 
 pradmm_status snapshot(pradmm_s* h, void* dst) {
-    CU(cudaMemcpyAsync(dst, h->state_block, slot_bytes(h), cudaMemcpyDeviceToDevice, h->stream));
+    CU(cudaMemcpyAsync(dst, h->state_block, slot_bytes(h, h->tape_C), cudaMemcpyDeviceToDevice, h->stream));
     return PRADMM_OK;
 }
 
@@ -1150,11 +1156,10 @@ int auto_ckpt(const pradmm_s* h, int K) {
         free_b = 0;
     }
     const size_t budget = free_b / 2 + h->tape_bytes;
-    const size_t sb = slot_bytes(h);
     int best = 1;
     for (int C = 1; C <= K; ++C) {
-        if (tape_slots(K, C) * sb <= budget) return C;
-        if (tape_slots(K, C) < tape_slots(K, best)) best = C;
+        if (tape_slots(K, C) * slot_bytes(h, C) <= budget) return C;
+        if (tape_slots(K, C) * slot_bytes(h, C) < tape_slots(K, best) * slot_bytes(h, best)) best = C;
     }
     return best;
 }
@@ -1171,7 +1176,8 @@ pradmm_status adjoint_record(pradmm_s* h, int32_t iters, int32_t ckpt_every) {
     h->tape_valid = false;
     const int C = iters == 0 ? 1 : (ckpt_every == 0 ? auto_ckpt(h, iters) : std::min(ckpt_every, iters));
     const int nck = iters == 0 ? 1 : (iters + C - 1) / C + 1;
-    const size_t need = tape_slots(iters, C) * slot_bytes(h);
+    h->tape_C = C;  // the slot geometry the copies below use
+    const size_t need = tape_slots(iters, C) * slot_bytes(h, C);
     if (need > h->tape_bytes) {
         if (h->tape) CU(cudaFree(h->tape));
         h->tape = nullptr;
@@ -1202,7 +1208,7 @@ pradmm_status adjoint_record(pradmm_s* h, int32_t iters, int32_t ckpt_every) {
         // the checkpoints (device-side test of the iteration count)
         if (!h->tape_rec) ST(dalloc(h, &h->tape_rec, 1));
         CU(pradmm::launch_arm(h->ctrl, iters, 0, h->prm.tol, h->stream));
-        CU(pradmm::launch_tape_rec_arm(h->tape_rec, h->ctrl, h->tape, iters, C, (long long)slot_bytes(h), h->stream));
+        CU(pradmm::launch_tape_rec_arm(h->tape_rec, h->ctrl, h->tape, iters, C, (long long)slot_bytes(h, C), h->stream));
         if (h->prm.use_graph) {
             ST(ensure_graph<R>(h, true));
             CU(cudaGraphLaunch(h->rec_exec, h->stream));
@@ -1295,7 +1301,7 @@ cudaError_t enqueue_reverse(pradmm_s* h, const pradmm::AdjDev<R>& A) {
     do {                                    \
         if ((e = (call)) != cudaSuccess) return e; \
     } while (0)
-    const bool inert = h->prm.inertia != 0.0;
+    const bool inert = slot_inert(h);  // slots carry x^{k-1}
     const auto SK = slot_state<R>(tape_slot(h, nck - 1), n, inert);
     RQ(pradmm::launch_adj_seed<R>(g, A, c, SK.s, SK.z, h->block, st));
     const int64_t seg0 = nck;  // first recompute slot
@@ -1311,7 +1317,7 @@ cudaError_t enqueue_reverse(pradmm_s* h, const pradmm::AdjDev<R>& A) {
         if (len > 1) {
             RQ(pradmm::launch_tape_arm(h->tape_ctrl, kc, st));
             for (int j = 0; j + 1 < len; ++j) {
-                RQ(cudaMemcpyAsync(slot[j + 1], slot[j], slot_bytes(h), cudaMemcpyDeviceToDevice, st));
+                RQ(cudaMemcpyAsync(slot[j + 1], slot[j], slot_bytes(h, C), cudaMemcpyDeviceToDevice, st));
                 const auto S = slot_state<R>(slot[j + 1], n, inert);
                 RQ(pradmm::launch_q<R>(g, S, c, L));
                 RQ(pradmm::launch_t<R>(g, S, c, L));
@@ -1336,6 +1342,10 @@ cudaError_t enqueue_reverse(pradmm_s* h, const pradmm::AdjDev<R>& A) {
                 // p^{k-1}: the previous slot of the segment, or the checkpoint's own copy
                 X.pp = j > 0 ? static_cast<const R*>(slot_state<R>(slot[j - 1], n, inert).p[(k - 1) & 1])
                              : static_cast<const R*>(slot[0]) + 40 * n;
+            } else if (c.theta != R(0)) {
+                // every iterate kept: p^{k-1} in the previous checkpoint, p^{-1} = p^0
+                X.pp = ci > 0 ? static_cast<const R*>(slot_state<R>(tape_slot(h, ci - 1), n, false).p[(k - 1) & 1])
+                              : X.pc;
             }
             RQ(pradmm::launch_adj_iteration<R>(g, A, X, c, h->out_src_d, (ci == 0 && j == 0) ? 0 : 1, h->block, st));
         }
