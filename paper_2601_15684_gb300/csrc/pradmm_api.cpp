@@ -104,6 +104,7 @@ struct pradmm_s {
                                        // inertial variant appends q, t, s ^{k-1} and p^{k-1} (44 n)
     void* prev_block = nullptr;        // inertial variant: q^{k-1}, t^{k-1}, s^{k-1}, 12 n reals
     void* pm1 = nullptr;               // inertial variant: p^{k-1} for the tape, 4 n reals
+    bool rec_keep = false;             // the recording keeps p^{k-1} (inertial tape, spacing > 1)
     bool l2_on = false;                // this handle holds an L2 set-aside
     cudaAccessPolicyWindow window{};   // persisting window over t, s, q, p[0], p[1]
     uint64_t epoch = 0;                // bumped by every change of the state
@@ -867,7 +868,7 @@ pradmm_status ensure_graph(pradmm_s* h, bool record = false) {
     } else {
         e1 = pradmm::launch_q<R>(g, S, c, L);
         e2 = pradmm::launch_t<R>(g, S, c, L);
-        if (record && h->pm1)
+        if (record && h->rec_keep)
             e2 = pradmm::launch_keep_pk<R>(h->ctrl, S.p[0], S.p[1], static_cast<R*>(h->pm1), h->n, h->grids[3],
                                            h->stream);
         e3 = pradmm::launch_sp<R>(g, S, c, L);
@@ -1177,6 +1178,15 @@ pradmm_status adjoint_record(pradmm_s* h, int32_t iters, int32_t ckpt_every) {
     const int C = iters == 0 ? 1 : (ckpt_every == 0 ? auto_ckpt(h, iters) : std::min(ckpt_every, iters));
     const int nck = iters == 0 ? 1 : (iters + C - 1) / C + 1;
     h->tape_C = C;  // the slot geometry the copies below use
+    if (h->rec_keep != (inert && C > 1)) {
+        // the recording loop keeps p^{k-1} only for slots that carry it
+        h->rec_keep = inert && C > 1;
+        if (h->rec_exec) cudaGraphExecDestroy(h->rec_exec);
+        if (h->rec_graph) cudaGraphDestroy(h->rec_graph);
+        h->rec_exec = nullptr;
+        h->rec_graph = nullptr;
+        h->rec_ready = false;
+    }
     const size_t need = tape_slots(iters, C) * slot_bytes(h, C);
     if (need > h->tape_bytes) {
         if (h->tape) CU(cudaFree(h->tape));
@@ -1220,7 +1230,7 @@ pradmm_status adjoint_record(pradmm_s* h, int32_t iters, int32_t ckpt_every) {
             for (int k = 0; k < iters; ++k) {
                 CU(pradmm::launch_q<R>(g, S, c, L));
                 CU(pradmm::launch_t<R>(g, S, c, L));
-                if (h->pm1)
+                if (h->rec_keep)
                     CU(pradmm::launch_keep_pk<R>(h->ctrl, S.p[0], S.p[1], static_cast<R*>(h->pm1), h->n, h->grids[3],
                                                  h->stream));
                 CU(pradmm::launch_sp<R>(g, S, c, L));
