@@ -1572,7 +1572,9 @@ pradmm_status restart_inertia(pradmm_s* h) {
     return PRADMM_OK;
 }
 
-pradmm_status set_sigma_impl(pradmm_s* h, const double* S1, const double* S2) {
+// queue: allocate the FP64 re-solve queue of the stand-alone Sigma sweeps (n
+// records); the batched form re-solves in the sweep's own thread and needs none.
+pradmm_status set_sigma_impl(pradmm_s* h, const double* S1, const double* S2, bool queue = true) {
     if (!S1 && !S2) {
         h->general = false;
     } else {
@@ -1599,7 +1601,7 @@ pradmm_status set_sigma_impl(pradmm_s* h, const double* S1, const double* S2) {
         quad_map(S2, false, true, h->LW2D);
         quad_map(S1, false, false, h->LW1);
         if (!h->sigma_d) ST(dalloc(h, &h->sigma_d, 32));
-        if (!h->fp64 && !h->fb_q) {
+        if (queue && !h->fp64 && !h->fb_q) {
             ST(dalloc(h, &h->fb_q, (size_t)h->n));
             ST(dalloc(h, &h->fb_n, 2));
             CU(cudaMemset(h->fb_n, 0, 2 * sizeof(unsigned int)));
@@ -2219,7 +2221,7 @@ pradmm_status pradmm_batch_get_schedule(pradmm_batch_t b, int32_t* block, int32_
 
 pradmm_status pradmm_batch_set_sigma(pradmm_batch_t b, const double* Sigma1, const double* Sigma2) {
     if (!b) return fail(PRADMM_ERR_ARG, "NULL handle");
-    ST(set_sigma_impl(b->h, Sigma1, Sigma2));
+    ST(set_sigma_impl(b->h, Sigma1, Sigma2, false));
     // the other iteration has its own register count: re-size the schedule's grid
     pradmm_status st = batch_schedule(b, b->block, b->warp_max_n, b->cluster, b->cluster_min_n);
     if (st == PRADMM_ERR_ARG) st = batch_schedule(b, 256, 256, 1, 0);  // the cluster shape no longer fits
