@@ -68,7 +68,8 @@ typedef enum {
     PRADMM_ERR_NONFINITE = 4,      /* NaN/Inf in an input or in the iteration  */
     PRADMM_ERR_NOMEM = 5,          /* host or device allocation failed          */
     PRADMM_ERR_CUDA = 6,           /* a CUDA runtime call failed                */
-    PRADMM_ERR_TIMEOUT = 7,        /* a bounded device wait ran out             */
+    PRADMM_ERR_TIMEOUT = 7,        /* reserved: no call returns it (the library
+                                      has no device-side waits)                */
     PRADMM_ERR_NOT_CONVERGED = 8,  /* solve hit max_iter with e >= tol (state valid) */
     PRADMM_ERR_QUATERNION = 9,     /* |q_meas| differs from 1 by more than 1e-6 */
     PRADMM_ERR_STATE = 10          /* operation needs a state that was never set */
@@ -293,7 +294,8 @@ pradmm_status pradmm_adjoint_device(pradmm_t h, const double* p_bar_d, const dou
  * memory at start-up and forbids allocation afterwards, since an allocation
  * can synchronise the device and stall the loop), and that therefore cannot
  * create a handle.
- *   src_d, dst_d     m int32 edge endpoints in [0, n) (not validated)
+ *   src_d, dst_d     m int32 edge endpoints in [0, n); an edge with an
+ *                    endpoint outside [0, n) reads no pose and makes *F_d NaN
  *   q_meas_d         m x 4 relative rotations (used as given, not renormalised)
  *   t_meas_d         m x 3 relative translations
  *   kappa_d, omega_d m weights, or NULL for all ones
@@ -301,10 +303,14 @@ pradmm_status pradmm_adjoint_device(pradmm_t h, const double* p_bar_d, const dou
  *   F_d              one double, written on `cuda_stream`
  * All pointers are device memory; the call is asynchronous on cuda_stream.
  * Scratch: one FP64 partial per chunk of 1024 edges and a counter live in a
- * 32 KiB static device array that every GPU loading the library keeps until
- * process exit; m above 4,194,304 is rejected with PRADMM_ERR_ARG.  The first
- * call on a device looks up that array's device address (with the device
- * current); make that first call before any stream capture.  Every call on
+ * 32 KiB static device array, part of the library's device code; m above
+ * 4,194,304 is rejected with PRADMM_ERR_ARG.  A GPU receives that array when
+ * the library's device code is loaded onto it and keeps it until process
+ * exit.  Under CUDA's lazy module loading (the default) that load happens at
+ * the first call on the GPU, and loading allocates device memory and may
+ * synchronise: make the first call on each GPU at start-up, before any
+ * stream capture (it also looks up the array's device address with the
+ * device current).  Later calls allocate nothing.  Every call on
  * a device shares that device's array and leaves its contents behind, so
  * calls that may overlap on the same GPU (for example on different streams)
  * race: serialise them.  Each call clears the counter before its kernel

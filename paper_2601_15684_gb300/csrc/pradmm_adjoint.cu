@@ -510,7 +510,6 @@ __global__ void k_tape_arm(Ctrl* ctrl, long long iter) {
     ctrl->use_tol = 0;
     ctrl->tol = 0.0;
     ctrl->nonfinite = 0;
-    ctrl->timeout = 0;
     ctrl->ticket = 0u;
 }
 

@@ -862,14 +862,14 @@ pradmm_status ensure_graph(pradmm_s* h, bool record = false) {
     const auto c = h->coef<R>();
     auto L = h->launch(true);
     L.cond = cond;
-    cudaError_t e1 = cudaSuccess, e2 = cudaSuccess, e3 = cudaSuccess, e5 = cudaSuccess;
+    cudaError_t e1 = cudaSuccess, e2 = cudaSuccess, e3 = cudaSuccess, e5 = cudaSuccess, e6 = cudaSuccess;
     if (h->general) {
         e1 = pradmm::launch_sigma_iteration<R>(g, S, c, h->sigma<R>(), L);
     } else {
         e1 = pradmm::launch_q<R>(g, S, c, L);
         e2 = pradmm::launch_t<R>(g, S, c, L);
         if (record && h->rec_keep)
-            e2 = pradmm::launch_keep_pk<R>(h->ctrl, S.p[0], S.p[1], static_cast<R*>(h->pm1), h->n, h->grids[3],
+            e6 = pradmm::launch_keep_pk<R>(h->ctrl, S.p[0], S.p[1], static_cast<R*>(h->pm1), h->n, h->grids[3],
                                            h->stream);
         e3 = pradmm::launch_sp<R>(g, S, c, L);
         if (record) e5 = pradmm::launch_tape_copy(h->tape_rec, h->ctrl, h->state_block, h->grids[3], h->stream);
@@ -880,6 +880,7 @@ pradmm_status ensure_graph(pradmm_s* h, bool record = false) {
     CU(e2);
     CU(e3);
     CU(e5);
+    CU(e6);
     CU(e4);
     CU(cudaGraphInstantiate(&exec, graph, 0));
     (record ? h->rec_ready : h->graph_ready) = true;
@@ -903,7 +904,6 @@ pradmm_status run(pradmm_s* h, long long iters, bool use_tol) {
         ST(launch_iters_plain<R>(h, iters));
     }
     ST(read_ctrl(h));
-    if (h->ctrl_h->timeout) return fail(PRADMM_ERR_TIMEOUT, "a bounded device wait ran out (staged copy never landed)");
     if (h->ctrl_h->nonfinite) return fail(PRADMM_ERR_NONFINITE, "the iteration produced a non-finite residual");
     return PRADMM_OK;
 }
@@ -1239,7 +1239,6 @@ pradmm_status adjoint_record(pradmm_s* h, int32_t iters, int32_t ckpt_every) {
         }
     }
     ST(read_ctrl(h));
-    if (h->ctrl_h->timeout) return fail(PRADMM_ERR_TIMEOUT, "a bounded device wait ran out");
     if (h->ctrl_h->nonfinite || h->ctrl_h->iter != k0 + iters)
         return fail(PRADMM_ERR_NONFINITE, "the recorded iterations produced a non-finite residual");
     h->tape_k0 = k0;

@@ -23,7 +23,6 @@ struct Ctrl {
     int stop;              // 1: e^k < tol was met
     int use_tol;           // 1: solve (stopping test on), 0: step
     int nonfinite;         // 1: e^k was NaN or Inf
-    int timeout;           // 1: a bounded device wait ran out
     unsigned long long fallbacks;  // p-updates recomputed in FP64
     unsigned long long zero_u;     // p-updates with |u| == 0 (kept p^k)
 };

@@ -131,7 +131,6 @@ __global__ void k_arm(Ctrl* ctrl, long long iters, int use_tol, double tol) {
     ctrl->use_tol = use_tol;
     ctrl->tol = tol;
     ctrl->nonfinite = 0;
-    ctrl->timeout = 0;
     ctrl->ticket = 0u;
 }
 

@@ -11,8 +11,12 @@
 // point takes the caller's device arrays and writes F to a caller-provided
 // device double; the only scratch it needs -- one FP64 partial sum per chunk
 // of kChunkEdges edges and an arrival counter -- lives in the file-scope array
-// g_objective_scratch below, which every GPU that loads the library keeps
-// for the life of the process.
+// g_objective_scratch below.  The array belongs to the library's device code:
+// a GPU receives it when that code is loaded onto it (under CUDA's lazy
+// module loading, at the first launch or symbol lookup on that GPU, which
+// itself allocates and may synchronise) and keeps it until process exit.
+// The first call on each GPU therefore belongs to the caller's start-up;
+// later calls allocate nothing.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -97,7 +101,9 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // partial[c]; the last CTA to finish adds the partials in chunk order, so
 // the result does not depend on scheduling.
 //   F += w_e |t~_j - t~_i - q_i t~_e q_i^*|^2 + k_e |q_j^* q_i q_e - 1|^2
-__global__ void __launch_bounds__(kThreads) k_objective_noalloc(int64_t m, const int32_t* __restrict__ src,
+// An edge whose endpoint lies outside [0, n) is skipped (no pose is read for
+// it) and its chunk's partial becomes NaN, so F comes back NaN.
+__global__ void __launch_bounds__(kThreads) k_objective_noalloc(int64_t n, int64_t m, const int32_t* __restrict__ src,
                                                                 const int32_t* __restrict__ dst,
                                                                 const double* __restrict__ qe,
                                                                 const double* __restrict__ te,
@@ -113,8 +119,13 @@ __global__ void __launch_bounds__(kThreads) k_objective_noalloc(int64_t m, const
     const int64_t e0 = (int64_t)blockIdx.x * kChunkEdges;
     const int64_t e1 = e0 + kChunkEdges < m ? e0 + kChunkEdges : m;
     double acc = 0.0;
+    bool bad = false;
     for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         const int64_t i = src[e], j = dst[e];
+        if (i < 0 || i >= n || j < 0 || j >= n) {
+            bad = true;
+            continue;
+        }
         const Qd qi = {q[4 * i], q[4 * i + 1], q[4 * i + 2], q[4 * i + 3]};
         const Qd qj = {q[4 * j], q[4 * j + 1], q[4 * j + 2], q[4 * j + 3]};
         const Qd tp = {0.0, te[3 * e], te[3 * e + 1], te[3 * e + 2]};
@@ -131,6 +142,7 @@ __global__ void __launch_bounds__(kThreads) k_objective_noalloc(int64_t m, const
         h.w -= 1.0;
         acc += (ka ? ka[e] : 1.0) * (h.w * h.w + h.x * h.x + h.y * h.y + h.z * h.z);
     }
+    if (bad) acc = __longlong_as_double(0x7ff8000000000000ll);  // quiet NaN
     const double bs = block_sum(acc, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = bs;
     __threadfence();
@@ -176,7 +188,7 @@ extern "C" pradmm_status pradmm_objective_noalloc(int64_t n, int64_t m, const in
     cudaError_t e = cudaMemsetAsync(scratch + kTicketOffset, 0, sizeof(unsigned int), stream);
     if (e == cudaSuccess) {
         const int chunks = m > 0 ? (int)((m + kChunkEdges - 1) / kChunkEdges) : 1;
-        k_objective_noalloc<<<chunks, kThreads, 0, stream>>>(m, src_d, dst_d, q_meas_d, t_meas_d, kappa_d, omega_d,
+        k_objective_noalloc<<<chunks, kThreads, 0, stream>>>(n, m, src_d, dst_d, q_meas_d, t_meas_d, kappa_d, omega_d,
                                                               q_d, t_d, F_d, scratch);
         e = cudaGetLastError();
     }

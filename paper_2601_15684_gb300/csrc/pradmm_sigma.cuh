@@ -148,7 +148,12 @@ __device__ __forceinline__ T dsign(int r) {
 
 // ---- Lemma 1: min_{|x| = 1} 1/2 x^T A x + b^T x ------------------------------
 
-// One Jacobi rotation zeroing a[p][q].  A rotation only has to be orthogonal,
+// One Jacobi rotation zeroing a[p][q], in Rutishauser's formulation of the
+// cyclic Jacobi eigenvalue method (H. Rutishauser, "The Jacobi method for
+// real symmetric matrices", Numer. Math. 9, 1966; the form textbooks give:
+// theta = (a_qq - a_pp) / (2 a_pq), t = sgn(theta) / (|theta| + sqrt(theta^2 + 1)),
+// c = 1 / sqrt(t^2 + 1), s = t c, and updates through tau = s / (1 + c)).
+// A rotation only has to be orthogonal,
 // not the exact one, so the FP32 instance (PRADMM_FAST_ROT) takes its
 // parameters from the fast reciprocal square root and division intrinsics
 // (cs^2 + sn^2 = 1 to a few ulp; the sweeps still drive the off-diagonal part

@@ -1,0 +1,88 @@
+"""Element-wise comparison of a state against the FP64 oracle.
+
+For every vertex i and state array X the per-element error is
+
+    err_i(X) = |X_gpu,i - X_orc,i| / max(|X_orc,i|, scale_X,i)
+
+(|.| the Euclidean norm of the vertex's row), and a check asserts the
+maximum over vertices.  The floor scale_X,i keeps an entry whose own value
+is near zero from demanding more than its inputs can give:
+
+- p, q (unit quaternions, and q near unit length): 1;
+- t, s (positions): the translation magnitude of the graph, the root mean
+  square of the oracle's |t_i|; a position near the origin is formed from
+  neighbours that far apart, so its FP32 rounding is of that size;
+- lam: tau*beta1 (|p_i| + |q_i|), the size of the terms tau*beta1 (p - q)
+  it accumulates;
+- z: tau*beta2 (|t_i| + |s_i|), floored by tau*beta2 times the
+  translation magnitude for the same reason as t.
+
+The per-array relative error |X_gpu - X_orc|_2 / |X_orc|_2 is reported
+beside it; a localized mistake (one vertex's wrong CSR slot, a race on a
+few vertices) shows in the per-element maximum where the per-array norm
+over a million vertices hides it.
+"""
+import numpy as np
+
+STATE_KEYS = ("p", "q", "t", "s", "lam", "z")
+
+
+def relerr(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def translation_scale(orc):
+    t = np.asarray(orc["t"])
+    if t.size == 0:
+        return 1.0
+    return max(float(np.sqrt(np.mean(np.sum(t * t, axis=1)))), 1e-300)
+
+
+def element_errors(gpu, orc, tau=1.5, beta1=1.0, beta2=1.0, keys=STATE_KEYS):
+    """{key: per-vertex error array} with the floors above."""
+    rn = lambda a: np.linalg.norm(np.asarray(a, dtype=np.float64), axis=1)
+    ts = translation_scale(orc)
+    floors = {
+        "p": np.ones(len(orc["p"])),
+        "q": np.ones(len(orc["q"])),
+        "t": np.full(len(orc["t"]), ts),
+        "s": np.full(len(orc["s"]), ts),
+    }
+    if "lam" in orc:
+        floors["lam"] = tau * beta1 * (rn(orc["p"]) + rn(orc["q"]))
+    if "z" in orc:
+        floors["z"] = tau * beta2 * np.maximum(rn(orc["t"]) + rn(orc["s"]), ts)
+    out = {}
+    for k in keys:
+        if k not in orc:
+            continue
+        d = rn(np.asarray(gpu[k]) - np.asarray(orc[k]))
+        out[k] = d / np.maximum(rn(orc[k]), floors[k])
+    return out
+
+
+def max_element_errors(gpu, orc, **kw):
+    return {k: (float(v.max()) if v.size else 0.0) for k, v in element_errors(gpu, orc, **kw).items()}
+
+
+def check_elements(gpu, orc, tol, what="", tau=1.5, beta1=1.0, beta2=1.0, keys=STATE_KEYS, verbose=True):
+    """Assert max_i err_i(X) <= tol for every array; returns the maxima."""
+    errs = element_errors(gpu, orc, tau=tau, beta1=beta1, beta2=beta2, keys=keys)
+    mx = {}
+    for k, v in errs.items():
+        m = float(v.max()) if v.size else 0.0
+        mx[k] = m
+        if verbose:
+            arg = int(np.argmax(v)) if v.size else -1
+            print(f"{what}: {k}: max element error {m:.3e} (vertex {arg}), array relerr {relerr(gpu[k], orc[k]):.3e}")
+    for k, m in mx.items():
+        assert m <= tol, (what, k, m, tol)
+    return mx
+
+
+# Per-element bounds against the FP64 oracle after 1 and 10 iterations.
+# FP64: rounding-order differences only.  FP32: unit roundoff 6e-8 times the
+# terms of one update (a vertex's degree plus its own terms) and the
+# cancellation in r = t_j - s_i, carried over ten iterations.
+ELEM_TOL_FP64 = 1e-10
+ELEM_TOL_FP32 = 1e-4

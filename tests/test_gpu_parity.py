@@ -1,5 +1,9 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
+Every state comparison is made twice: per array and element by element
+(tests/parity.py: per vertex |X_gpu,i - X_orc,i| / max(|X_orc,i|, floor),
+the maximum over vertices within ELEM_TOL_FP64 / ELEM_TOL_FP32).
+
 Tolerances (relerr(X) = |X_gpu - X_oracle|_2 / |X_oracle|_2 per state array):
   FP64 path: 1e-10 after 1 and 10 iterations (rounding-order differences only;
              measured ~1e-15), final objective within 1e-6 relative.
@@ -16,6 +20,7 @@ import pytest
 
 import oracle
 from paper_2601_15684_gb300 import synth
+from parity import ELEM_TOL_FP32, ELEM_TOL_FP64, check_elements
 
 pytestmark = pytest.mark.gpu
 
@@ -53,7 +58,9 @@ def _oparams(beta1=1.0, beta2=1.0, tau=1.5, gamma=(1.0, 1e-3, 1e-3, 1e-3)):
     return oracle.make_params(beta1=beta1, beta2=beta2, tau=tau, gamma=gamma)
 
 
-def check_state(gpu, orc, fp64, prm):
+def check_state(gpu, orc, fp64, prm, what=""):
+    check_elements(gpu, orc, ELEM_TOL_FP64 if fp64 else ELEM_TOL_FP32, what=what, tau=prm.relax, beta1=prm.beta1,
+                   beta2=prm.beta2)
     if fp64:
         for k in KEYS:
             assert relerr(gpu[k], orc[k]) <= 1e-10, (k, relerr(gpu[k], orc[k]))
@@ -75,7 +82,7 @@ def _run_pair(P, g, st0, prm, iters_list=(1, 10)):
             orc, res, _ = oracle.iterate(g, op, orc, it - done)
             done = it
             gpu = S.state()
-            check_state(gpu, orc, prm.precision == P.PRADMM_FP64, prm)
+            check_state(gpu, orc, prm.precision == P.PRADMM_FP64, prm, what=f"{g.name or g.n} after {it}")
             assert abs(e_gpu - res[0]) <= (1e-9 if prm.precision == P.PRADMM_FP64 else 1e-3) * max(res[0], 1e-30)
             assert S.iterations() == it
 
@@ -127,6 +134,7 @@ def test_walk128_fp64_solve_500_objective(P):
     assert abs(oracle.objective(g, gpu["p"], gpu["t"]) - F_gpu) <= 1e-12 * F_orc
     for k in KEYS:
         assert relerr(gpu[k], orc[k]) <= 1e-8, k
+    check_elements(gpu, orc, 1e-8, what="walk128 FP64 after 500")
 
 
 def test_solve_stops_like_the_oracle(P):
@@ -145,6 +153,7 @@ def test_solve_stops_like_the_oracle(P):
             gpu = S.state()
             for key in KEYS:
                 assert relerr(gpu[key], orc[key]) <= 1e-10, key
+            check_elements(gpu, orc, ELEM_TOL_FP64, what=f"solve stopped at {k}")
 
 
 def test_solve_not_converged_keeps_state(P):

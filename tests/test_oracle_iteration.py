@@ -91,6 +91,49 @@ def test_oracle_lagrangian_matches_definition():
         assert abs(oracle.lagrangian(g, P(), st) - lagrangian(g, st, BETA1, BETA2)) < 1e-11
 
 
+def _edge_terms(g, q, t):
+    """Per-edge squared residuals of Eq. (1), written out here from the
+    problem statement: translation |t~_j - t~_i - q_i t~_ij q_i^*|^2 and
+    rotation |q_j^* q_i q_ij - 1|^2."""
+    i, j = g.src, g.dst
+    r1 = _pure(t[j]) - _pure(t[i]) - _qm(_qm(q[i], _pure(g.t_meas)), _cj(q[i]))
+    r2 = _qm(_qm(_cj(q[j]), q[i]), g.q_meas) - np.array([1.0, 0, 0, 0])
+    return np.sum(r1 * r1, -1), np.sum(r2 * r2, -1)
+
+
+def test_oracle_objective_matches_definition_with_edge_weights():
+    # Eq. (1) with per-edge weights omega_e (translation) and kappa_e
+    # (rotation), drawn independently so that swapping them, dropping one,
+    # or using the head's weight instead of the edge's changes F
+    rng = np.random.default_rng(21)
+    for g in _graphs():
+        g = synth.PoseGraph(n=g.n, src=g.src, dst=g.dst, q_meas=g.q_meas, t_meas=g.t_meas,
+                            kappa=rng.uniform(0.1, 3.0, g.m), omega=rng.uniform(0.1, 3.0, g.m))
+        st = _state(g, 6)
+        q, t = st["q"], st["t"]
+        ft, fr = _edge_terms(g, q, t)
+        F = oracle.objective(g, q, t)
+        F_def = float(np.sum(g.omega * ft) + np.sum(g.kappa * fr))
+        assert abs(F - F_def) <= 1e-12 * F_def, (F, F_def)
+        # F is the split model's L_beta at p = q, s = t with zero multipliers
+        x = dict(st, p=q, s=t, lam=np.zeros_like(st["lam"]), z=np.zeros_like(st["z"]))
+        assert abs(F - lagrangian(g, x, BETA1, BETA2)) <= 1e-12 * F_def
+        # each weight reaches its own term only
+        only_t = synth.PoseGraph(n=g.n, src=g.src, dst=g.dst, q_meas=g.q_meas, t_meas=g.t_meas,
+                                 kappa=np.zeros(g.m), omega=g.omega)
+        only_r = synth.PoseGraph(n=g.n, src=g.src, dst=g.dst, q_meas=g.q_meas, t_meas=g.t_meas,
+                                 kappa=g.kappa, omega=np.zeros(g.m))
+        assert abs(oracle.objective(only_t, q, t) - np.sum(g.omega * ft)) <= 1e-12 * F_def
+        assert abs(oracle.objective(only_r, q, t) - np.sum(g.kappa * fr)) <= 1e-12 * F_def
+        # one edge's weight moves F by that edge's own term
+        e = g.m // 2
+        w2 = g.omega.copy()
+        w2[e] += 1.0
+        bumped = synth.PoseGraph(n=g.n, src=g.src, dst=g.dst, q_meas=g.q_meas, t_meas=g.t_meas,
+                                 kappa=g.kappa, omega=w2)
+        assert abs(oracle.objective(bumped, q, t) - F - ft[e]) <= 1e-12 * F_def
+
+
 # ---- T4 brute force ---------------------------------------------------------
 
 def _blocks(g, st, new):
