@@ -363,25 +363,74 @@ def _workload():
     return synth.workload(WORKLOAD)
 
 
-def _cpu_baseline(g, budget_s: float = 12.0):
-    """The FP64 oracle as it stands, single threaded, on a bounded sample:
-    whole iterations of the same 1M-pose graph until ~budget_s of CPU time."""
-    import oracle
+def _time_iterations(step, max_iters, budget_s):
+    """Runs step(k) (k iterations) in growing chunks until max_iters or about
+    budget_s; returns (iterations, seconds)."""
+    done, el, chunk = 0, 0.0, 1
+    while done < max_iters and el < budget_s:
+        k = min(chunk, max_iters - done)
+        t0 = time.perf_counter()
+        step(k)
+        el += time.perf_counter() - t0
+        done += k
+        chunk = min(2 * chunk, 64)
+    return done, el
 
-    q0, t0 = oracle.init_odometry(g)
-    st = oracle.init_state(q0, t0)
+
+def _cpu_baseline(g, budget_s: float = 8.0):
+    """The FP64 oracle on the host cores, as a reported baseline: the
+    single-threaded checker as it stands, and its OpenMP timing build (the
+    same source compiled with -DORC_OPENMP -fopenmp: every block's loop over
+    vertices, the state bitwise the checker's) on all host cores.  For the
+    bench workload (the 1M-pose lattice) whole iterations for about budget_s
+    each; for the other stated workloads (the 128-pose walk, FP64, 500
+    iterations; the 25,000-pose helix, 2,000 iterations; the 10,000-pose
+    walk, 200 unrolled iterations with its reverse mode) bounded samples of
+    their iterations, the full run's time extrapolated per iteration."""
+    import oracle
+    from paper_2601_15684_gb300 import synth
+
+    threads = oracle.omp_threads()
     prm = oracle.make_params(beta1=1.0, beta2=1.0, tau=1.5)
-    iters = 0
-    t_start = time.perf_counter()
-    while True:
-        st, _, _ = oracle.iterate(g, prm, st, 1)
-        iters += 1
-        el = time.perf_counter() - t_start
-        if el >= budget_s or iters >= 50:
-            break
-    return {"value": g.m * iters / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{iters} full iterations of the {WORKLOAD} graph (n={g.n}, m={g.m}), FP64, "
-                      f"single-threaded C, {el:.2f} s"}
+
+    def leg(gw, name, iters, budget):
+        q0, t0 = oracle.init_odometry(gw)
+        st0 = oracle.init_state(q0, t0)
+        edges = oracle.vertex_edges(gw)
+        out = {"workload": name, "n": gw.n, "m": gw.m, "iterations_stated": iters}
+        for kind, fn in (("single", lambda k: oracle.iterate(gw, prm, st0, k)),
+                         ("openmp", lambda k: oracle.iterate_omp(gw, prm, st0, k, edges))):
+            k, el = _time_iterations(fn, iters, budget)
+            out[kind] = {"cores": 1 if kind == "single" else threads, "iterations_timed": k, "seconds": el,
+                         "edge_updates_per_s": gw.m * k / el, "stated_run_s": el / k * iters}
+        return out
+
+    by_config = [leg(synth.workload("walk128"), "walk128 (128-pose walk, FP64, 500 iterations)", 500, 2.0),
+                 leg(synth.workload("helix25k"), "helix25k (25,000-pose helix, 2,000 iterations)", 2000, 2.5),
+                 leg(g, f"{WORKLOAD} (1,000,000-pose lattice walk, 1,000 iterations)", 1000, budget_s)]
+    g10 = synth.workload("walk10k")
+    rev = leg(g10, "walk10k (10,000-pose walk, 200 unrolled iterations)", 200, 2.0)
+    q0, t0 = oracle.init_odometry(g10)
+    st0 = oracle.init_state(q0, t0)
+    rng = np.random.default_rng(0)
+    pb, tb = rng.normal(size=(g10.n, 4)), rng.normal(size=(g10.n, 3))
+    k_adj = 20
+    t_a = time.perf_counter()
+    oracle.adjoint(g10, prm, st0, k_adj, pb, tb)
+    el = time.perf_counter() - t_a
+    rev["reverse_mode_single"] = {"cores": 1, "iterations_timed": k_adj, "seconds": el,
+                                  "stated_run_s": el / k_adj * 200,
+                                  "note": "forward recording + reverse sweeps of the oracle's reverse mode"}
+    by_config.append(rev)
+    lat = by_config[2]
+    return {"value": lat["single"]["edge_updates_per_s"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{lat['single']['iterations_timed']} full iterations of the {WORKLOAD} graph (n={g.n}, "
+                      f"m={g.m}), FP64, single-threaded C, {lat['single']['seconds']:.2f} s",
+            "openmp": {"value": lat["openmp"]["edge_updates_per_s"], "unit": UNIT, "cores": threads,
+                       "kind": "oracle, OpenMP timing build (same source, -DORC_OPENMP)",
+                       "sample": f"{lat['openmp']['iterations_timed']} full iterations of the same graph, "
+                                 f"{lat['openmp']['seconds']:.2f} s"},
+            "by_config": by_config}
 
 
 def run_reference(args):

@@ -43,6 +43,78 @@ def build(force: bool = False) -> str:
     return _SO
 
 
+_SO_OMP = os.path.join(_BUILD, "liboracle_omp.so")
+_lib_omp = None
+
+
+def build_omp(force: bool = False) -> str:
+    """The OpenMP timing build: the same source with -DORC_OPENMP -fopenmp.
+    A CPU baseline for the benchmark, never the checker."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO_OMP) or os.path.getmtime(_SO_OMP) < os.path.getmtime(_SRC):
+        tmp = _SO_OMP + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
+                               "-fopenmp", "-DORC_OPENMP", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO_OMP)
+    return _SO_OMP
+
+
+def lib_omp():
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            build_omp()
+            L = ctypes.CDLL(_SO_OMP)
+            P = ctypes.POINTER
+            d, i32, i64 = P(ctypes.c_double), P(ctypes.c_int32), ctypes.c_int64
+            L.orc_iterate_omp.restype = ctypes.c_int64
+            L.orc_iterate_omp.argtypes = [i64, i64, i32, i32, d, d, d, d, P(Params), P(ctypes.c_int64), i32,
+                                          P(ctypes.c_int64), i32, d, d, d, d, d, d, d]
+            L.orc_omp_threads.restype = ctypes.c_int
+            L.orc_omp_threads.argtypes = []
+            _lib_omp = L
+    return _lib_omp
+
+
+def omp_threads() -> int:
+    """Threads the OpenMP timing build runs on (OMP_NUM_THREADS, else all cores)."""
+    return int(lib_omp().orc_omp_threads())
+
+
+def vertex_edges(g):
+    """Each vertex's out-edges (tail i) and in-edges (head i) in input order:
+    (out_ptr, out_eid, in_ptr, in_eid) for iterate_omp."""
+    src = np.asarray(g.src, dtype=np.int64)
+    dst = np.asarray(g.dst, dtype=np.int64)
+    out_eid = np.argsort(src, kind="stable").astype(np.int32)
+    in_eid = np.argsort(dst, kind="stable").astype(np.int32)
+    out_ptr = np.zeros(g.n + 1, np.int64)
+    in_ptr = np.zeros(g.n + 1, np.int64)
+    np.cumsum(np.bincount(src, minlength=g.n), out=out_ptr[1:])
+    np.cumsum(np.bincount(dst, minlength=g.n), out=in_ptr[1:])
+    return out_ptr, out_eid, in_ptr, in_eid
+
+
+def iterate_omp(g, params: Params, state: dict, iters: int = 1, edges=None):
+    """`iters` iterations of the OpenMP timing build (state bitwise equal to
+    iterate's; the residuals are summed in another order)."""
+    keep, a = _graph_args(g)
+    out_ptr, out_eid, in_ptr, in_eid = edges if edges is not None else vertex_edges(g)
+    st = copy_state(state)
+    res = np.zeros(5)
+    trace = np.zeros(iters)
+    pi = lambda x: x.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    L = lib_omp()
+    for k in range(iters):
+        r = L.orc_iterate_omp(*a, ctypes.byref(params), pi(out_ptr), _i(out_eid), pi(in_ptr), _i(in_eid),
+                              _d(st["p"]), _d(st["q"]), _d(st["t"]), _d(st["s"]), _d(st["lam"]), _d(st["z"]),
+                              _d(res))
+        if r < 0:
+            raise MemoryError("oracle OpenMP iteration: allocation failed")
+        trace[k] = res[0]
+    return st, trace
+
+
 def lib():
     global _lib
     with _lock:

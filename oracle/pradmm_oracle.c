@@ -992,3 +992,158 @@ out:
     free(anc);
     return rc;
 }
+
+#ifdef ORC_OPENMP
+/* ---- OpenMP timing build (compiled only with -DORC_OPENMP -fopenmp) ---------
+ * A CPU baseline, not the checker: the same iteration as orc_iterate with
+ * every block's loop running over vertices in parallel.  The sweeps of
+ * Eq. (3a)-(3d) are Jacobi over vertices (every vertex of a block reads only
+ * values from before the block), so a vertex can sum its own edges.  The
+ * caller passes each vertex's out-edges (tail i) and in-edges (head i) in
+ * input order -- out_eid[out_ptr[i] .. out_ptr[i+1]) and likewise for in --
+ * so every per-vertex sum adds the same terms in the same order as the
+ * sequential edge loops above, and the state comes out bitwise equal to
+ * orc_iterate's.  Only the residual's four sums are reduced in another
+ * order.  Plain PRADMM (anchors x^k), scalar weights. */
+#include <omp.h>
+
+int orc_omp_threads(void) { return omp_get_max_threads(); }
+
+int64_t orc_iterate_omp(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const double* qe,
+                        const double* te, const double* kappa, const double* omega, const orc_params* prm,
+                        const int64_t* out_ptr, const int32_t* out_eid, const int64_t* in_ptr,
+                        const int32_t* in_eid, double* p, double* q, double* t, double* s, double* lam, double* z,
+                        double* res_out) {
+    const double b1 = prm->beta1, b2 = prm->beta2, tau = prm->tau;
+    const double g1 = prm->gamma[0], g2 = prm->gamma[1], g3 = prm->gamma[2], g4 = prm->gamma[3];
+    double* c = (double*)malloc(sizeof(double) * (size_t)(3 * m + 1));
+    double* lold = (double*)malloc(sizeof(double) * (size_t)(4 * n + 1));
+    if (!c || !lold) {
+        free(c);
+        free(lold);
+        return -1;
+    }
+    int64_t nzero = 0;
+    double dl = 0.0, dz = 0.0, dq = 0.0, dt = 0.0;
+    (void)dst;
+    /* (3a) p-block */
+#pragma omp parallel for schedule(static) reduction(+ : nzero)
+    for (int64_t i = 0; i < n; ++i) {
+        double u[4];
+        for (int k = 0; k < 4; ++k) u[k] = b1 * q[4 * i + k] + lam[4 * i + k] + g1 * p[4 * i + k];
+        for (int64_t x = out_ptr[i]; x < out_ptr[i + 1]; ++x) {
+            const int64_t e = out_eid[x], j = dst[e];
+            double r[4], rc[4], tp[4], a[4], v[4];
+            r[0] = 0.0;
+            for (int k = 0; k < 3; ++k) r[k + 1] = t[3 * j + k] - s[3 * i + k];
+            qconj(r, rc);
+            qpure(&te[3 * e], tp);
+            qmul(rc, &q[4 * i], a);
+            qmul(a, tp, v);
+            double w = 2.0 * (omega ? omega[e] : 1.0);
+            for (int k = 0; k < 4; ++k) u[k] += w * v[k];
+        }
+        for (int64_t x = in_ptr[i]; x < in_ptr[i + 1]; ++x) {
+            const int64_t e = in_eid[x], l = src[e];
+            double v[4];
+            qmul(&q[4 * l], &qe[4 * e], v);
+            double w = 2.0 * (kappa ? kappa[e] : 1.0);
+            for (int k = 0; k < 4; ++k) u[k] += w * v[k];
+        }
+        double nu = sqrt(dot4(u, u));
+        if (nu > 0.0) {
+            for (int k = 0; k < 4; ++k) p[4 * i + k] = u[k] / nu;
+        } else {
+            nzero++;
+        }
+    }
+    /* (3b) q-block; the old lambda is kept for the residual */
+#pragma omp parallel for schedule(static) reduction(+ : dq)
+    for (int64_t i = 0; i < n; ++i) {
+        double a2 = b1 + g2, qn[4];
+        for (int k = 0; k < 4; ++k) qn[k] = b1 * p[4 * i + k] - lam[4 * i + k] + g2 * q[4 * i + k];
+        for (int64_t x = out_ptr[i]; x < out_ptr[i + 1]; ++x) {
+            const int64_t e = out_eid[x], j = dst[e];
+            double w = omega ? omega[e] : 1.0, kk = kappa ? kappa[e] : 1.0;
+            double r[4], tp[4], tc[4], a[4], v[4], qc[4], h[4];
+            r[0] = 0.0;
+            for (int k = 0; k < 3; ++k) r[k + 1] = t[3 * j + k] - s[3 * i + k];
+            qpure(&te[3 * e], tp);
+            qconj(tp, tc);
+            qmul(r, &p[4 * i], a);
+            qmul(a, tc, v);
+            qconj(&qe[4 * e], qc);
+            qmul(&p[4 * j], qc, h);
+            double tn2 = dot4(tp, tp);
+            a2 += 2.0 * (w * dot4(&p[4 * i], &p[4 * i]) * tn2 +
+                         kk * dot4(&p[4 * j], &p[4 * j]) * dot4(&qe[4 * e], &qe[4 * e]));
+            for (int k = 0; k < 4; ++k) qn[k] += 2.0 * (w * v[k] + kk * h[k]);
+        }
+        for (int k = 0; k < 4; ++k) {
+            const double qk = qn[k] / a2, d = qk - q[4 * i + k];
+            dq += d * d;
+            q[4 * i + k] = qk;
+            lold[4 * i + k] = lam[4 * i + k];
+        }
+    }
+    /* c_e = Im(q_i^{k+1} t~_e (p_i^{k+1})^*) */
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < m; ++e) {
+        int64_t i = src[e];
+        double tp[4], a[4], pc[4], v[4];
+        qpure(&te[3 * e], tp);
+        qmul(&q[4 * i], tp, a);
+        qconj(&p[4 * i], pc);
+        qmul(a, pc, v);
+        c[3 * e] = v[1]; c[3 * e + 1] = v[2]; c[3 * e + 2] = v[3];
+    }
+    /* (3c) t-block: a vertex reads only its own t here, so t is written in place */
+#pragma omp parallel for schedule(static) reduction(+ : dt)
+    for (int64_t i = 0; i < n; ++i) {
+        double a3 = b2 + g3, tn[3];
+        for (int k = 0; k < 3; ++k) tn[k] = b2 * s[3 * i + k] + z[3 * i + k] + g3 * t[3 * i + k];
+        for (int64_t x = in_ptr[i]; x < in_ptr[i + 1]; ++x) {
+            const int64_t e = in_eid[x], l = src[e];
+            double w = omega ? omega[e] : 1.0;
+            a3 += 2.0 * w;
+            for (int k = 0; k < 3; ++k) tn[k] += 2.0 * w * (s[3 * l + k] + c[3 * e + k]);
+        }
+        for (int k = 0; k < 3; ++k) {
+            const double tk = tn[k] / a3, d = tk - t[3 * i + k];
+            dt += d * d;
+            t[3 * i + k] = tk;
+        }
+    }
+    /* (3d) s-block, then the relaxed duals (3e), (3f) of the same vertex */
+#pragma omp parallel for schedule(static) reduction(+ : dl, dz)
+    for (int64_t i = 0; i < n; ++i) {
+        double a4 = b2 + g4, sn[3];
+        for (int k = 0; k < 3; ++k) sn[k] = b2 * t[3 * i + k] - z[3 * i + k] + g4 * s[3 * i + k];
+        for (int64_t x = out_ptr[i]; x < out_ptr[i + 1]; ++x) {
+            const int64_t e = out_eid[x], j = dst[e];
+            double w = omega ? omega[e] : 1.0;
+            a4 += 2.0 * w;
+            for (int k = 0; k < 3; ++k) sn[k] += 2.0 * w * (t[3 * j + k] - c[3 * e + k]);
+        }
+        for (int k = 0; k < 3; ++k) s[3 * i + k] = sn[k] / a4;
+        for (int k = 0; k < 4; ++k) {
+            lam[4 * i + k] -= tau * b1 * (p[4 * i + k] - q[4 * i + k]);
+            const double d = lam[4 * i + k] - lold[4 * i + k];
+            dl += d * d;
+        }
+        for (int k = 0; k < 3; ++k) {
+            const double zo = z[3 * i + k];
+            z[3 * i + k] -= tau * b2 * (t[3 * i + k] - s[3 * i + k]);
+            const double d = z[3 * i + k] - zo;
+            dz += d * d;
+        }
+    }
+    if (res_out) {
+        res_out[0] = dl / b1 + dz / b2 + b1 * dq + b2 * dt;
+        res_out[1] = dl; res_out[2] = dz; res_out[3] = dq; res_out[4] = dt;
+    }
+    free(c);
+    free(lold);
+    return nzero;
+}
+#endif /* ORC_OPENMP */

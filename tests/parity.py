@@ -80,9 +80,53 @@ def check_elements(gpu, orc, tol, what="", tau=1.5, beta1=1.0, beta2=1.0, keys=S
     return mx
 
 
-# Per-element bounds against the FP64 oracle after 1 and 10 iterations.
-# FP64: rounding-order differences only.  FP32: unit roundoff 6e-8 times the
-# terms of one update (a vertex's degree plus its own terms) and the
-# cancellation in r = t_j - s_i, carried over ten iterations.
+# Per-element bounds against the FP64 oracle.
+# FP64: rounding-order differences only.
+# FP32: every element within ELEM_FLOOR_FP32 of its scale, or within
+# ELEM_FACTOR_FP32 times the FP64 oracle's own deviation when its state is
+# stored in FP32 (fp32_storage_run), whichever is larger.  A vertex whose
+# update is ill conditioned (|u_i| small against its terms, long drifted
+# closures) amplifies the rounding of stored FP32 values by itself; no FP32
+# implementation can be closer to the FP64 oracle there than FP32 storage
+# alone allows.  The floor covers FP32 arithmetic (a hub's sums over hundreds
+# of edges) where storage rounding alone moves the state less.
 ELEM_TOL_FP64 = 1e-10
-ELEM_TOL_FP32 = 1e-4
+ELEM_FLOOR_FP32 = 1e-4
+ELEM_FACTOR_FP32 = 8.0
+
+
+def to_fp32(st):
+    """A state rounded to FP32 (and held in double)."""
+    return {k: np.asarray(v, dtype=np.float32).astype(np.float64) for k, v in st.items()}
+
+
+def fp32_storage_run(step, st0, iters):
+    """The oracle's iterates with the state stored in FP32: starting from
+    to_fp32(st0), each iteration runs the FP64 oracle step and rounds its
+    result to FP32.  step(state) -> state after one iteration."""
+    st = to_fp32(st0)
+    for _ in range(iters):
+        st = to_fp32(step(st))
+    return st
+
+
+def check_elements_fp32(gpu, orc, orc32, what="", tau=1.5, beta1=1.0, beta2=1.0, keys=STATE_KEYS,
+                        floor=ELEM_FLOOR_FP32, factor=ELEM_FACTOR_FP32):
+    """FP32 per-element rule: err_i(gpu) <= max(floor, factor * err_i(orc32))
+    for every vertex and array, errors against the FP64 oracle orc."""
+    eg = element_errors(gpu, orc, tau=tau, beta1=beta1, beta2=beta2, keys=keys)
+    e3 = element_errors(orc32, orc, tau=tau, beta1=beta1, beta2=beta2, keys=keys)
+    worst = {}
+    for k in eg:
+        if eg[k].size == 0:
+            continue
+        bound = np.maximum(floor, factor * e3[k])
+        r = eg[k] / bound
+        i = int(np.argmax(r))
+        worst[k] = float(r[i])
+        print(f"{what}: {k}: max element error {eg[k].max():.3e} (FP32-storage oracle {e3[k].max():.3e}); "
+              f"worst error / bound {r[i]:.3f} at vertex {i} ({eg[k][i]:.3e} vs {bound[i]:.3e}); "
+              f"array relerr {relerr(gpu[k], orc[k]):.3e}")
+    for k, r in worst.items():
+        assert r <= 1.0, (what, k, r)
+    return worst

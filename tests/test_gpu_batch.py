@@ -18,6 +18,7 @@ import pytest
 
 import oracle
 from paper_2601_15684_gb300 import synth
+from parity import ELEM_TOL_FP64, check_elements, check_elements_fp32, fp32_storage_run
 
 pytestmark = pytest.mark.gpu
 KEYS = ("p", "q", "t", "s", "lam", "z")
@@ -98,6 +99,7 @@ def test_batch_fp64_matches_oracle(P):
         for key in KEYS:
             err = np.linalg.norm(sl[key] - orc[key]) / max(np.linalg.norm(orc[key]), 1e-300)
             assert err <= 1e-10, (k, key, err)
+        check_elements(sl, orc, ELEM_TOL_FP64, what=f"batched graph {k}", verbose=False)
 
 
 def test_batch_schedules_agree_and_stop_rule(P):
@@ -142,6 +144,7 @@ def test_batch_cluster_schedule_matches_oracle_fp64_and_stops(P):
         for key in KEYS:
             err = np.linalg.norm(sl[key] - orc[key]) / max(np.linalg.norm(orc[key]), 1e-300)
             assert err <= 1e-10, (k, key, err)
+        check_elements(sl, orc, ELEM_TOL_FP64, what=f"batched graph {k}", verbose=False)
     conv = res["status"] == P.PRADMM_OK
     assert (res["e_last"][conv] <= 1e-3 * res["e_first"][conv]).all()
 
@@ -236,9 +239,8 @@ def test_batch_spans_trace_every_graph(P):
 def test_batch_large_graphs_of_the_bench_distribution(P, precision):
     # the largest graphs of the 4,096-walk batch recipe (n_g log-uniform in
     # [50, 20000]) plus a spread of smaller ones, with clusters for the large
-    # graphs, against the FP64 oracle graph by graph: FP64 to 1e-10; FP32 no
-    # further from the oracle than the plain FP32 solver (both round
-    # differently, so they are compared through the oracle, not to each other)
+    # graphs, against the FP64 oracle graph by graph: FP64 to 1e-10; FP32 to
+    # the plain parity bounds against the oracle (per array and per element)
     rng = np.random.default_rng(4)
     ns = np.exp(rng.uniform(np.log(50), np.log(20000), 4096)).round().astype(int)
     dens = rng.uniform(0.5, 3.0, 4096)
@@ -263,11 +265,11 @@ def test_batch_large_graphs_of_the_bench_distribution(P, precision):
         if precision == 0:
             for key in KEYS:
                 assert rel(sl[key], orc[key]) <= 1e-10, (k, g.n, key, rel(sl[key], orc[key]))
+            check_elements(sl, orc, ELEM_TOL_FP64, what=f"graph {k}", verbose=False)
             continue
-        with P.Solver(g, precision=1) as S:
-            S.init_odometry()
-            S.step(K)
-            ref = S.state()
+        # FP32: against the oracle, as the plain parity tests (1e-5 per array
+        # for p, q, t, s; per element the FP32-storage rule)
+        orc32 = fp32_storage_run(lambda x: oracle.iterate(g, prm, x, 1)[0], oracle.init_state(q0, t0), K)
         for key in ("p", "q", "t", "s"):
-            eb, ep = rel(sl[key], orc[key]), rel(ref[key], orc[key])
-            assert eb <= 3.0 * ep + 1e-6, (k, g.n, key, eb, ep)
+            assert rel(sl[key], orc[key]) <= 1e-5, (k, g.n, key, rel(sl[key], orc[key]))
+        check_elements_fp32(sl, orc, orc32, what=f"graph {k} (n={g.n})", keys=("p", "q", "t", "s"))

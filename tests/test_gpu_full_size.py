@@ -11,13 +11,14 @@ printed.
   10 iterations against the FP64 oracle (the oracle runs one iteration of
   this graph in well under a second): p, q, t, s within 1e-5 per array;
   multipliers within 1e-5 of the scale they are formed from; every element
-  within ELEM_TOL_FP32.  The odometry start is compared first.
+  within max(1e-4, 8 x the deviation of the FP64 oracle run with its state
+  stored in FP32).  The odometry start is compared first.
 - the 4,096-walk batch (14.0M poses, 37.4M edges), solved as the benchmark
   solves it (a first solve, the profiled schedule search, then the solve to a
   relative residual of 1e-6): the stopping rule on every graph, and sampled
   graphs (the largest and four seeded picks) against the FP64 oracle run for
-  the iterations each took, within BATCH_TOL per array and BATCH_ELEM_TOL
-  per element.
+  the iterations each took, within BATCH_TOL per array and, per element,
+  within the FP32 rule above.
 - helix25k (25,000 poses, 74,799 edges): 2,000 iterations.  FP64 path:
   final objective within 1e-6 relative of the oracle's.  FP32 path: the final
   objective's relative error is stated, not guaranteed (FP32 cancellation in
@@ -28,7 +29,7 @@ import pytest
 
 import oracle
 from paper_2601_15684_gb300 import synth
-from parity import ELEM_TOL_FP32, check_elements, max_element_errors
+from parity import check_elements_fp32, fp32_storage_run, relerr as relerr_, to_fp32
 
 pytestmark = pytest.mark.gpu
 
@@ -50,7 +51,7 @@ def _oparams():
     return oracle.make_params(beta1=1.0, beta2=1.0, tau=1.5, gamma=(1.0, 1e-3, 1e-3, 1e-3))
 
 
-def _check_fp32(gpu, orc, what, tau=1.5, beta1=1.0, beta2=1.0):
+def _check_fp32(gpu, orc, what, orc32, tau=1.5, beta1=1.0, beta2=1.0):
     """p, q, t, s within 1e-5 relative.  A multiplier is a running sum of
     tau*beta*(p - q) (resp. (t - s)); on the lattice q is far from unit length
     in the first iterations (long drifted closures), so its error is measured
@@ -67,7 +68,7 @@ def _check_fp32(gpu, orc, what, tau=1.5, beta1=1.0, beta2=1.0):
     ez = nl(gpu["z"] - orc["z"]) / scale_z
     print(f"{what}: lam error / scale = {el:.3e}, z error / scale = {ez:.3e}")
     assert el <= 1e-5 and ez <= 1e-5, (what, el, ez)
-    check_elements(gpu, orc, ELEM_TOL_FP32, what=what, tau=tau, beta1=beta1, beta2=beta2)
+    check_elements_fp32(gpu, orc, orc32, what=what, tau=tau, beta1=beta1, beta2=beta2)
 
 
 def test_lattice1m_one_and_ten_iterations(P):
@@ -80,12 +81,15 @@ def test_lattice1m_one_and_ten_iterations(P):
         # odometry composition in FP64 on both sides, stored as FP32 on the GPU
         assert relerr(st0["p"], q0) <= 1e-7 and relerr(st0["t"], t0) <= 1e-7
         orc = oracle.init_state(q0, t0)
+        orc32 = orc
+        step = lambda st: oracle.iterate(g, _oparams(), st, 1)[0]
         done = 0
         for it in (1, 10):
             e_gpu = S.step(it - done)
             orc, res, _ = oracle.iterate(g, _oparams(), orc, it - done)
+            orc32 = fp32_storage_run(step, orc32, it - done)
             done = it
-            _check_fp32(S.state(), orc, f"lattice1m after {it}")
+            _check_fp32(S.state(), orc, f"lattice1m after {it}", orc32)
             assert abs(e_gpu - res[0]) <= 1e-3 * res[0]
         F = S.objective()
     F_ref = oracle.objective(g, orc["p"], orc["t"])
@@ -134,6 +138,12 @@ def test_lattice1m_general_sigma_p_update_sampled(P, precision, tol):
         assert np.linalg.norm(p1[i] - x) <= tol, (int(i), np.linalg.norm(p1[i] - x))
 
 
+# sampled graphs of the full-size batch after their own iteration counts (up
+# to thousands of FP32 iterations): p, q, t, s within BATCH_TOL per array of
+# the FP64 oracle run for the same iterations
+BATCH_TOL = 5e-4
+
+
 def test_batch_4096_walks_at_the_benchmark_configuration(P):
     import bench  # the benchmark's batch recipe and its parallel graph builder
     graphs = bench._batch_workload(bench._batch_args())
@@ -148,6 +158,7 @@ def test_batch_4096_walks_at_the_benchmark_configuration(P):
         st = B.state()
         offs = B.offsets
     conv = res["status"] == P.PRADMM_OK
+    print(f"batch: {conv.sum()} of {len(graphs)} graphs met e^k <= 1e-6 e^1; iterations max {res['iters'].max()}")
     assert conv.mean() > 0.9
     assert (res["e_last"][conv] <= 1e-6 * res["e_first"][conv]).all()
     assert (res["iters"][~conv] == 3000).all()
@@ -157,12 +168,13 @@ def test_batch_4096_walks_at_the_benchmark_configuration(P):
     for k in pick:
         g, K = graphs[k], int(res["iters"][k])
         q0, t0 = oracle.init_odometry(g)
-        orc, _, _ = oracle.iterate(g, prm, oracle.init_state(q0, t0), K)
-        with P.Solver(g, precision=1) as S:
-            S.init_odometry()
-            S.step(K)
-            ref = S.state()
+        st0 = oracle.init_state(q0, t0)
+        orc, _, _ = oracle.iterate(g, prm, st0, K)
+        orc32 = fp32_storage_run(lambda x: oracle.iterate(g, prm, x, 1)[0], st0, K)
         sl = {key: v[offs[k]:offs[k + 1]] for key, v in st.items()}
+        what = f"batch graph {k} (n={g.n}, {K} iterations)"
         for key in ("p", "q", "t", "s"):
-            eb, ep = relerr(sl[key], orc[key]), relerr(ref[key], orc[key])
-            assert eb <= 3.0 * ep + 1e-6, (k, g.n, K, key, eb, ep)
+            eb = relerr(sl[key], orc[key])
+            print(f"{what}: relerr({key}) {eb:.3e}, FP32-storage oracle {relerr_(orc32[key], orc[key]):.3e}")
+            assert eb <= BATCH_TOL, (what, key, eb)
+        check_elements_fp32(sl, orc, orc32, what=what, keys=("p", "q", "t", "s"))

@@ -13,6 +13,7 @@ import pytest
 import oracle
 from oracle import general_sigma as gs
 from paper_2601_15684_gb300 import synth
+from parity import check_elements, check_elements_fp32, fp32_storage_run
 
 pytestmark = pytest.mark.gpu
 KEYS = ("p", "q", "t", "s", "lam", "z")
@@ -44,6 +45,8 @@ def test_general_sigma_matches_oracle(P, precision, tol):
     st = synth.random_state(rng, g.n)
     S1, S2 = _spd(rng), _spd(rng)
     orc = st
+    orc32 = st
+    step = lambda x: gs.iterate(g, PARAMS, S1, S2, x)[0]
     with P.Solver(g, precision=precision) as S:
         S.set_sigma(S1, S2)
         S.set_state_full(st)
@@ -52,6 +55,7 @@ def test_general_sigma_matches_oracle(P, precision, tol):
             S.step(it - done)
             for _ in range(it - done):
                 orc, _, _ = gs.iterate(g, PARAMS, S1, S2, orc)
+            orc32 = fp32_storage_run(step, orc32, it - done)
             done = it
             gpu = S.state()
             for key in ("p", "q", "t", "s"):
@@ -59,6 +63,11 @@ def test_general_sigma_matches_oracle(P, precision, tol):
             if precision == 0:
                 for key in ("lam", "z"):
                     assert relerr(gpu[key], orc[key]) <= tol, (it, key)
+                check_elements(gpu, orc, tol, what=f"general Sigma after {it}")
+            else:
+                # the general path's FP32 rule: ten times the scalar path's floor,
+                # as its per-array bound is ten times the scalar path's
+                check_elements_fp32(gpu, orc, orc32, what=f"general Sigma after {it}", floor=1e-3)
         F = S.objective()
     assert abs(F - gs.objective(g, S1, S2, orc["p"], orc["t"])) <= (1e-10 if precision == 0 else 1e-4) * max(F, 1.0)
 
@@ -98,6 +107,7 @@ def test_walk_with_anisotropic_weights_converges_like_oracle(P):
     assert es[-1] < 1e-2 * es[0]  # the residual falls (3e-3 of the first after 60 iterations)
     for key in KEYS:
         assert relerr(gpu[key], orc[key]) <= 1e-8, key
+    check_elements(gpu, orc, 1e-8, what="anisotropic walk after 60")
 
 
 def test_set_sigma_validation_and_reset(P):

@@ -6,9 +6,12 @@ tests/test_oracle_iteration.py).  The library keeps x^{k-1} of q, t, s in its
 own arrays and takes p^{k-1} from the p double buffer; a state set restarts
 the extrapolation (x^{-1} = x^0).
 
-Tolerances as the plain parity tests: FP64 1e-10 relative per array, FP32 1e-5
-for p, q, t, s and the multipliers against tau beta times the scale they are
-formed from; the same after a second step call (continuity of x^{k-1}).  With
+Tolerances as the plain parity tests: FP64 1e-10 relative per array and per
+element, FP32 1e-5 for p, q, t, s and the multipliers against tau beta times
+the scale they are formed from, and per element max(1e-4, 8 x the deviation
+of the oracle's inertial iteration with its state and previous iterate
+stored in FP32); the same after a second step call (continuity of x^{k-1}).
+With
 general weights (pradmm_set_sigma) the general-Sigma oracle's inertial
 iteration is the reference, at the general parity tolerances (FP64 1e-9, FP32
 1e-4: the sphere-constrained p-update is solved by different algorithms on
@@ -20,6 +23,7 @@ import pytest
 import oracle
 from oracle import general_sigma as gs
 from paper_2601_15684_gb300 import synth
+from parity import ELEM_TOL_FP64, check_elements, check_elements_fp32, fp32_storage_run, to_fp32
 
 pytestmark = pytest.mark.gpu
 KEYS = ("p", "q", "t", "s", "lam", "z")
@@ -42,7 +46,21 @@ def _oparams():
     return oracle.make_params(beta1=1.0, beta2=1.0, tau=1.5, gamma=(1.0, 1e-3, 1e-3, 1e-3))
 
 
-def check_state(gpu, orc, fp64, what=""):
+def _inertial_fp32(g, theta, st, prev, iters):
+    """The oracle's inertial iteration with the state and x^{k-1} stored in FP32."""
+    st = to_fp32(st)
+    prev = None if prev is None else to_fp32(prev)
+    for _ in range(iters):
+        st, prev, _, _ = oracle.iterate_inertial(g, _oparams(), st, theta, 1, prev)
+        st, prev = to_fp32(st), to_fp32(prev)
+    return st, prev
+
+
+def check_state(gpu, orc, fp64, what="", orc32=None):
+    if fp64:
+        check_elements(gpu, orc, ELEM_TOL_FP64, what=what)
+    elif orc32 is not None:
+        check_elements_fp32(gpu, orc, orc32, what=what)
     if fp64:
         for k in KEYS:
             assert relerr(gpu[k], orc[k]) <= 1e-10, (what, k, relerr(gpu[k], orc[k]))
@@ -65,11 +83,13 @@ def test_inertial_matches_oracle_one_and_ten_iterations(P, precision, theta, cas
     with P.Solver(g, precision=precision, inertia=theta) as S:
         S.set_state_full(st0)
         orc, prev, done = st0, None, 0
+        orc32, prev32 = st0, None
         for it in (1, 10):
             e_gpu = S.step(it - done)
             orc, prev, res, _ = oracle.iterate_inertial(g, _oparams(), orc, theta, it - done, prev)
+            orc32, prev32 = _inertial_fp32(g, theta, orc32, prev32, it - done)
             done = it
-            check_state(S.state(), orc, precision == 0, f"{case} theta={theta} after {it}")
+            check_state(S.state(), orc, precision == 0, f"{case} theta={theta} after {it}", orc32=orc32)
             assert abs(e_gpu - res[0]) <= (1e-9 if precision == 0 else 1e-3) * max(res[0], 1e-30)
 
 
@@ -160,6 +180,7 @@ def test_inertial_general_sigma_matches_oracle(P, precision, tol, theta):
             if precision == 0:
                 for key in ("lam", "z"):
                     assert relerr(gpu[key], orc[key]) <= tol, (it, key)
+                check_elements(gpu, orc, tol, what=f"general theta={theta} after {it}")
 
 
 def test_inertial_identity_sigma_equals_scalar_inertial_path(P):
