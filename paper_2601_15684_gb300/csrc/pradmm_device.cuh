@@ -28,11 +28,29 @@ struct R4 {
 template <typename R>
 struct IO;
 
+#ifndef PRADMM_OWN_NA
+#define PRADMM_OWN_NA 0
+#endif
+
 template <>
 struct IO<float> {
     static __device__ __forceinline__ R4<float> ld(const float* p, int64_t i) {
         float4 v = reinterpret_cast<const float4*>(p)[i];
         return {v.x, v.y, v.z, v.w};
+    }
+    // a vertex's own record, read once per sweep by its own thread: with
+    // PRADMM_OWN_NA it does not take L1 lines from the edge records and
+    // gathers, which neighbouring lanes reuse
+    static __device__ __forceinline__ R4<float> ldo(const float* p, int64_t i) {
+#if PRADMM_OWN_NA
+        float4 v;
+        asm volatile("ld.global.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                     : "l"(reinterpret_cast<const float4*>(p) + i));
+        return {v.x, v.y, v.z, v.w};
+#else
+        return ld(p, i);
+#endif
     }
     // edge records (invariant while any sweep runs) on the read-only path with
     // normal caching: the 32 lanes of a warp walk one dense block of records,
@@ -59,6 +77,7 @@ struct IO<double> {
         double2 u = v[0], w = v[1];
         return {u.x, u.y, w.x, w.y};
     }
+    static __device__ __forceinline__ R4<double> ldo(const double* p, int64_t i) { return ld(p, i); }
     static __device__ __forceinline__ R4<double> ldr(const double* __restrict__ p, int64_t i) {
         const double2* v = reinterpret_cast<const double2*>(p) + 2 * i;
         double2 u = __ldg(v), w = __ldg(v + 1);
@@ -500,13 +519,81 @@ struct PEdge {
 // INERT (with the s-block): the proximal anchors are s^k + theta (s^k - s^{k-1})
 // (S.sprev) and, for the next p-block, p^{k+1} + theta (p^{k+1} - p^k), p^k being
 // the vertex's value in pn before it is overwritten.
+// p-update finish with the FP64 recompute's inputs re-read from memory
+// (PRADMM_SP_RELOAD): q_i, lam_i, p_i and s_i (s^{new} once the s-block has
+// stored it) are not held in registers through the in-edge pass for the rare
+// vertex whose |u| is tiny.
+template <typename R, bool ANCHOR_PN>
+__device__ __noinline__ void p_fallback_reload(const GraphDev<R>& g, const StateDev<R>& S, int64_t i, const R* pc,
+                                               R* pn, const Coef<R>& c, Ctrl* ctrl) {
+    const R4<R> qr = IO<R>::ld(S.q, i), lr = IO<R>::ld(S.lam, i), pr = IO<R>::ld(pc, i), sr = IO<R>::ld(S.s, i);
+    R4<R> pa = pr;
+    if (ANCHOR_PN) {
+        const R4<R> po = IO<R>::ld(pn, i);
+        pa = {pr.a + c.theta * (pr.a - po.a), pr.b + c.theta * (pr.b - po.b), pr.c + c.theta * (pr.c - po.c),
+              pr.d + c.theta * (pr.d - po.d)};
+    }
+    const Q<double> ud = p_rhs_serial<R, double>(g, S.t, S.q, i, asq<double>(qr), asq<double>(lr), asq<double>(pa),
+                                                 double(sr.a), double(sr.b), double(sr.c), c);
+    const double nd = sqrt(ud.w * ud.w + ud.x * ud.x + ud.y * ud.y + ud.z * ud.z);
+    atomicAdd(&ctrl->fallbacks, 1ull);
+    if (nd > 0.0) {
+        IO<R>::st(pn, i, R(ud.w / nd), R(ud.x / nd), R(ud.y / nd), R(ud.z / nd));
+    } else {
+        atomicAdd(&ctrl->zero_u, 1ull);
+        IO<R>::st(pn, i, pr.a, pr.b, pr.c, pr.d);
+    }
+}
+
+template <typename R, bool ANCHOR_PN>
+__device__ __forceinline__ void p_normalise_reload(const GraphDev<R>& g, const StateDev<R>& S, int64_t i,
+                                                   const Q<R>& u, const R* pc, R* pn, const Coef<R>& c, Ctrl* ctrl) {
+    const R nn = u.w * u.w + u.x * u.x + u.y * u.y + u.z * u.z;
+    const R nrm = sqrt(nn);
+    if (sizeof(R) == sizeof(float) && nrm < R(c.fb_thresh)) {
+        p_fallback_reload<R, ANCHOR_PN>(g, S, i, pc, pn, c, ctrl);
+        return;
+    }
+    if (nn > R(0)) {
+        const R inv = R(1) / nrm;
+        IO<R>::st(pn, i, u.w * inv, u.x * inv, u.y * inv, u.z * inv);
+    } else {
+        atomicAdd(&ctrl->zero_u, 1ull);
+        const R4<R> pr = IO<R>::ld(pc, i);
+        IO<R>::st(pn, i, pr.a, pr.b, pr.c, pr.d);
+    }
+}
+
+// Variants of the s/z + p sweep (compile-time switches, all 0 = the form above
+// them in the history of this file):
+//  PRADMM_SP_LIN    sum_e 2 w_e c_e formed once as Im(q (sum_e 2 w_e t~_e) p^*)
+//                   (c_e is linear in t_e), not per edge
+//  PRADMM_SP_HOIST  the in-edge CSR range read with the vertex's first loads,
+//                   lam_i after the out-edge pass
+//  PRADMM_SP_RELOAD the FP64 recompute re-reads its inputs (p_normalise_reload)
+#ifndef PRADMM_SP_LIN
+#define PRADMM_SP_LIN 0
+#endif
+#ifndef PRADMM_SP_HOIST
+#define PRADMM_SP_HOIST 0
+#endif
+#ifndef PRADMM_SP_RELOAD
+#define PRADMM_SP_RELOAD 0
+#endif
+
 template <typename R, bool WITH_S, bool PIPE = false, bool NC = false, bool INERT = false>
 __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R>& S, const Coef<R>& c, const R* pc,
                                           R* pn, int64_t i, Acc<R>& adz, Ctrl* ctrl) {
-    const R4<R> sr = IO<R>::ld(S.s, i);  // (s_i, 1/A_2)
-    const R4<R> qr = IO<R>::ld(S.q, i);
-    const R4<R> pr = IO<R>::ld(pc, i);
-    const R4<R> lr = IO<R>::ld(S.lam, i);
+    int in0 = 0, in1 = 0;
+    if (PRADMM_SP_HOIST) {
+        in0 = __ldg(g.in_ptr + i);
+        in1 = __ldg(g.in_ptr + i + 1);
+    }
+    const R4<R> sr = IO<R>::ldo(S.s, i);  // (s_i, 1/A_2)
+    const R4<R> qr = IO<R>::ldo(S.q, i);
+    const R4<R> pr = IO<R>::ldo(pc, i);
+    R4<R> lr;
+    if (!PRADMM_SP_HOIST) lr = IO<R>::ldo(S.lam, i);
     const Q<R> qi = asq<R>(qr), pi = asq<R>(pr);
     // out-edge pass: s-block sum (WITH_S), p-block term at s^{old}, sum 2 w t_e
     R ax = R(0), ay = R(0), az = R(0);
@@ -522,11 +609,17 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
         [&](const SEdge<R>& x) {
             const R w2 = R(2) * x.te.d;
             if (WITH_S) {
-                R cx, cy, cz;
-                im_rot(qi, x.te.a, x.te.b, x.te.c, pi, cx, cy, cz);
-                ax += w2 * (x.tj.a - cx);
-                ay += w2 * (x.tj.b - cy);
-                az += w2 * (x.tj.c - cz);
+                if (PRADMM_SP_LIN) {
+                    ax += w2 * x.tj.a;
+                    ay += w2 * x.tj.b;
+                    az += w2 * x.tj.c;
+                } else {
+                    R cx, cy, cz;
+                    im_rot(qi, x.te.a, x.te.b, x.te.c, pi, cx, cy, cz);
+                    ax += w2 * (x.tj.a - cx);
+                    ay += w2 * (x.tj.b - cy);
+                    az += w2 * (x.tj.c - cz);
+                }
                 wx += w2 * x.te.a;
                 wy += w2 * x.te.b;
                 wz += w2 * x.te.c;
@@ -536,8 +629,16 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
         });
     R sx = sr.a, sy = sr.b, sz = sr.c;
     if (WITH_S) {
-        const R4<R> tr = IO<R>::ld(S.t, i);
-        const R4<R> zr = IO<R>::ld(S.z, i);  // (z_i, 1/A_4)
+        if (PRADMM_SP_LIN) {
+            // sum_e 2 w_e c_e = Im(q_i (sum_e 2 w_e t~_e) p_i^*)
+            R cx, cy, cz;
+            im_rot(qi, wx, wy, wz, pi, cx, cy, cz);
+            ax -= cx;
+            ay -= cy;
+            az -= cz;
+        }
+        const R4<R> tr = IO<R>::ldo(S.t, i);
+        const R4<R> zr = IO<R>::ldo(S.z, i);  // (z_i, 1/A_4)
         const R inv = zr.d;
         R sax = sr.a, say = sr.b, saz = sr.c;
         if (INERT) {
@@ -558,6 +659,7 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
         // move the p-block's out-edge term from s^{old} to s^{new}
         axpy(u, R(-1), qmul_pr(qmul_pl(sr.a - sx, sr.b - sy, sr.c - sz, qi), wx, wy, wz));
     }
+    if (PRADMM_SP_HOIST) lr = IO<R>::ldo(S.lam, i);
     // own terms beta1 q_i + lam_i + gamma1 p_i, then in-edge terms 2 q_l (k_e q_e)
     R4<R> pa = pr;  // the p-block's proximal anchor
     if (INERT && WITH_S) {
@@ -569,14 +671,15 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
               c.beta1 * qr.c + lr.c + c.g1 * pa.c, c.beta1 * qr.d + lr.d + c.g1 * pa.d};
     axpy(v, R(1), u);
     for_edges2<PEdge<R>, PIPE>(
-        g.in_ptr[i], g.in_ptr[i + 1],
+        PRADMM_SP_HOIST ? in0 : g.in_ptr[i], PRADMM_SP_HOIST ? in1 : g.in_ptr[i + 1],
         [&](int e, PEdge<R>& x) {
             x.l = __ldg(g.in_idx + e);
             x.qk = IO<R>::ldr(g.in_qk, e);
         },
         [&](PEdge<R>& x) { x.ql = gat<R, NC>(S.q, x.l); },
         [&](const PEdge<R>& x) { axpy(v, R(2), qmul(asq<R>(x.ql), asq<R>(x.qk))); });
-    p_normalise<R>(g, S, i, v, qr, lr, pr, pa, sx, sy, sz, c, pn, ctrl);
+    if (PRADMM_SP_RELOAD) p_normalise_reload<R, INERT && WITH_S>(g, S, i, v, pc, pn, c, ctrl);
+    else p_normalise<R>(g, S, i, v, qr, lr, pr, pa, sx, sy, sz, c, pn, ctrl);
 }
 
 // Out-edge terms of vertex i in F of Eq. (1) at (p, t), in double:
