@@ -145,6 +145,8 @@ def lib():
             L.orc_adjoint_inertial.restype = ctypes.c_int
             L.orc_adjoint_inertial.argtypes = [i64, i64, i32, i32, d, d, d, d, P(Params), ctypes.c_double, i64,
                                                d, d, d, d, d, d, d, d, d, d, d, d, d, d, d]
+            L.orc_block.restype = ctypes.c_int64
+            L.orc_block.argtypes = [ctypes.c_int, i64, i64, i32, i32, d, d, d, d, P(Params), d, d, d, d, d, d, d]
             L.orc_qmul.restype = None
             L.orc_qmul.argtypes = [d, d, d]
             L.orc_qrotate.restype = None
@@ -241,6 +243,21 @@ def iterate_inertial(g, params: Params, state: dict, theta: float, iters: int = 
             raise MemoryError("oracle iterate_inertial")
         nz += int(r)
     return st, pv, res.copy(), nz
+
+
+BLOCKS = {"p": 0, "q": 1, "c": 2, "t": 3, "s": 4, "duals": 5}
+
+
+def block(g, params: Params, state: dict, which: str, c):
+    """One block of Algorithm 1 in place on `state` (arrays of float64,
+    modified): "p", "q", "c" (c_e into c, m x 3), "t", "s", "duals".  Run in
+    that order the blocks are one iteration of `iterate`, bitwise."""
+    keep, a = _graph_args(g)
+    r = lib().orc_block(BLOCKS[which], *a, ctypes.byref(params), _d(state["p"]), _d(state["q"]), _d(state["t"]),
+                        _d(state["s"]), _d(state["lam"]), _d(state["z"]), _d(c))
+    if r < 0:
+        raise MemoryError("oracle block")
+    return int(r)
 
 
 def solve(g, params: Params, state: dict, max_iter: int, tol: float):

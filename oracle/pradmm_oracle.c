@@ -263,47 +263,25 @@ double orc_lagrangian(int64_t n, int64_t m, const int32_t* src, const int32_t* d
 }
 
 /* ---- one PRADMM iteration, Eq. (3a)-(3f) / Algorithm 1 --------------------
- * Updates (p, q, t, s, lam, z) in place from x^k to x^{k+1}.
- * res_out (nullable) receives 5 numbers: e^{k+1} (Appendix E.1, reading R6),
- * then |dlam|^2, |dz|^2, |dq|^2, |dt|^2.
- * Returns the number of vertices whose p-block hit |u_i| == 0 (R11).
- */
-static int64_t iterate_anchored(int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
-                                const double* qe, const double* te, const double* kappa,
-                                const double* omega, const orc_params* prm, double* p, double* q,
-                                double* t, double* s, double* lam, double* z, const double* ap,
-                                const double* aq, const double* at, const double* as, double* res_out) {
-    const double b1 = prm->beta1, b2 = prm->beta2, tau = prm->tau;
-    const double g1 = prm->gamma[0], g2 = prm->gamma[1], g3 = prm->gamma[2], g4 = prm->gamma[3];
-    double* u = (double*)calloc((size_t)(4 * n + 1), sizeof(double));
-    double* qn = (double*)calloc((size_t)(4 * n + 1), sizeof(double));
-    double* a2 = (double*)calloc((size_t)(n + 1), sizeof(double));
-    double* tn = (double*)calloc((size_t)(3 * n + 1), sizeof(double));
-    double* a3 = (double*)calloc((size_t)(n + 1), sizeof(double));
-    double* sn = (double*)calloc((size_t)(3 * n + 1), sizeof(double));
-    double* a4 = (double*)calloc((size_t)(n + 1), sizeof(double));
-    double* c = (double*)calloc((size_t)(3 * m + 1), sizeof(double));
-    double* qold = (double*)malloc(sizeof(double) * (size_t)(4 * n + 1));
-    double* told = (double*)malloc(sizeof(double) * (size_t)(3 * n + 1));
-    double* lold = (double*)malloc(sizeof(double) * (size_t)(4 * n + 1));
-    double* zold = (double*)malloc(sizeof(double) * (size_t)(3 * n + 1));
-    int64_t nzero = 0;
-    if (!u || !qn || !a2 || !tn || !a3 || !sn || !a4 || !c || !qold || !told || !lold || !zold) {
-        nzero = -1;
-        goto out;
-    }
-    memcpy(qold, q, sizeof(double) * (size_t)(4 * n));
-    memcpy(told, t, sizeof(double) * (size_t)(3 * n));
-    memcpy(lold, lam, sizeof(double) * (size_t)(4 * n));
-    memcpy(zold, z, sizeof(double) * (size_t)(3 * n));
+ * The blocks below update (p, q, t, s, lam, z) in place from x^k to x^{k+1}
+ * when called in the order of Algorithm 1: p, q, c, t, s, duals.  Each
+ * block reads only what Eq. (3) gives it; ap .. as are the proximal anchors.
+ * u, qn, tn, sn (4n, 4n, 3n, 3n) and a (n) are scratch; c (3m) carries c_e
+ * from block_c to the t- and s-blocks. */
 
-    /* (3a) p-block, Appendix B.1.  With scalar Sigma the quadratic form A_1 is
-     * a multiple of I_4 (Lemma MW(c)) and the minimiser of the linear term on
-     * the unit sphere is p = -b_1/|b_1| = u/|u|, where
-     *   u_i = sum_{out} 2 w_e G1^T r_e + sum_{in} 2 k_e G2^T 1~ + b1 q_i + lam_i + g1 p_i,
-     * G1^T r = r^* q_i t~_e  (G1 = M(q_i) M(t~_e) D),
-     * G2^T 1~ = q_l q_e      (G2 = W(q_e) W(q_l) D, reading R1),
-     * r_e = t~_j - s~_i.                                                    */
+/* (3a) p-block, Appendix B.1.  With scalar Sigma the quadratic form A_1 is
+ * a multiple of I_4 (Lemma MW(c)) and the minimiser of the linear term on
+ * the unit sphere is p = -b_1/|b_1| = u/|u|, where
+ *   u_i = sum_{out} 2 w_e G1^T r_e + sum_{in} 2 k_e G2^T 1~ + b1 q_i + lam_i + g1 p_i,
+ * G1^T r = r^* q_i t~_e  (G1 = M(q_i) M(t~_e) D),
+ * G2^T 1~ = q_l q_e      (G2 = W(q_e) W(q_l) D, reading R1),
+ * r_e = t~_j - s~_i.  Returns the vertices whose |u_i| == 0 (R11). */
+static int64_t block_p(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const double* qe,
+                       const double* te, const double* kappa, const double* omega, const orc_params* prm,
+                       double* p, const double* q, const double* t, const double* s, const double* lam,
+                       const double* ap, double* u) {
+    const double b1 = prm->beta1, g1 = prm->gamma[0];
+    int64_t nzero = 0;
     for (int64_t i = 0; i < n; ++i)
         for (int k = 0; k < 4; ++k)
             u[4 * i + k] = b1 * q[4 * i + k] + lam[4 * i + k] + g1 * ap[4 * i + k];
@@ -334,12 +312,19 @@ static int64_t iterate_anchored(int64_t n, int64_t m, const int32_t* src, const 
             nzero++; /* R11: keep p_i^k */
         }
     }
+    return nzero;
+}
 
-    /* (3b) q-block, Appendix B.2: q_i = b_2 / A_2 with
-     *   A_2 = sum_{out} 2 (w_e |p_i|^2 |t_e|^2 + k_e |p_j|^2 |q_e|^2) + b1 + g2,
-     *   b_2 = sum_{out} 2 (w_e G3^T r_e + k_e G4^T 1~) + b1 p_i - lam_i + g2 q_i,
-     * G3^T r = r p_i t~_e^*   (G3 = W(p_i)^T W(t~_e)),
-     * G4^T 1~ = p_j q_e^*     (G4 = W(q_e) M(p_j)^T).                        */
+/* (3b) q-block, Appendix B.2: q_i = b_2 / A_2 with
+ *   A_2 = sum_{out} 2 (w_e |p_i|^2 |t_e|^2 + k_e |p_j|^2 |q_e|^2) + b1 + g2,
+ *   b_2 = sum_{out} 2 (w_e G3^T r_e + k_e G4^T 1~) + b1 p_i - lam_i + g2 q_i,
+ * G3^T r = r p_i t~_e^*   (G3 = W(p_i)^T W(t~_e)),
+ * G4^T 1~ = p_j q_e^*     (G4 = W(q_e) M(p_j)^T).                        */
+static void block_q(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const double* qe,
+                    const double* te, const double* kappa, const double* omega, const orc_params* prm,
+                    const double* p, double* q, const double* t, const double* s, const double* lam,
+                    const double* aq, double* qn, double* a2) {
+    const double b1 = prm->beta1, g2 = prm->gamma[1];
     for (int64_t i = 0; i < n; ++i) {
         a2[i] = b1 + g2;
         for (int k = 0; k < 4; ++k) qn[4 * i + k] = b1 * p[4 * i + k] - lam[4 * i + k] + g2 * aq[4 * i + k];
@@ -363,8 +348,10 @@ static int64_t iterate_anchored(int64_t n, int64_t m, const int32_t* src, const 
     }
     for (int64_t i = 0; i < n; ++i)
         for (int k = 0; k < 4; ++k) q[4 * i + k] = qn[4 * i + k] / a2[i];
+}
 
-    /* c_e = Im(q_i^{k+1} t~_e (p_i^{k+1})^*) for e = (i, j) (reading R3) */
+/* c_e = Im(q_i^{k+1} t~_e (p_i^{k+1})^*) for e = (i, j) (reading R3) */
+static void block_c(int64_t m, const int32_t* src, const double* te, const double* p, const double* q, double* c) {
     for (int64_t e = 0; e < m; ++e) {
         int64_t i = src[e];
         double tp[4], a[4], pc[4], v[4];
@@ -374,9 +361,14 @@ static int64_t iterate_anchored(int64_t n, int64_t m, const int32_t* src, const 
         qmul(a, pc, v);
         c[3 * e] = v[1]; c[3 * e + 1] = v[2]; c[3 * e + 2] = v[3];
     }
+}
 
-    /* (3c) t-block, Appendix B.3 with hat-Sigma_1 = w_e I_3:
-     *   t_i = [sum_{in} 2 w_e (s_l + c_e) + b2 s_i + z_i + g3 t_i] / [sum_{in} 2 w_e + b2 + g3] */
+/* (3c) t-block, Appendix B.3 with hat-Sigma_1 = w_e I_3:
+ *   t_i = [sum_{in} 2 w_e (s_l + c_e) + b2 s_i + z_i + g3 t_i] / [sum_{in} 2 w_e + b2 + g3] */
+static void block_t(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const double* omega,
+                    const orc_params* prm, double* t, const double* s, const double* z, const double* at,
+                    const double* c, double* tn, double* a3) {
+    const double b2 = prm->beta2, g3 = prm->gamma[2];
     for (int64_t i = 0; i < n; ++i) {
         a3[i] = b2 + g3;
         for (int k = 0; k < 3; ++k) tn[3 * i + k] = b2 * s[3 * i + k] + z[3 * i + k] + g3 * at[3 * i + k];
@@ -389,9 +381,14 @@ static int64_t iterate_anchored(int64_t n, int64_t m, const int32_t* src, const 
     }
     for (int64_t i = 0; i < n; ++i)
         for (int k = 0; k < 3; ++k) t[3 * i + k] = tn[3 * i + k] / a3[i];
+}
 
-    /* (3d) s-block, Appendix B.4 (the section's variable is s_i):
-     *   s_i = [sum_{out} 2 w_e (t_j - c_e) + b2 t_i - z_i + g4 s_i] / [sum_{out} 2 w_e + b2 + g4] */
+/* (3d) s-block, Appendix B.4 (the section's variable is s_i):
+ *   s_i = [sum_{out} 2 w_e (t_j - c_e) + b2 t_i - z_i + g4 s_i] / [sum_{out} 2 w_e + b2 + g4] */
+static void block_s(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const double* omega,
+                    const orc_params* prm, const double* t, double* s, const double* z, const double* as,
+                    const double* c, double* sn, double* a4) {
+    const double b2 = prm->beta2, g4 = prm->gamma[3];
     for (int64_t i = 0; i < n; ++i) {
         a4[i] = b2 + g4;
         for (int k = 0; k < 3; ++k) sn[3 * i + k] = b2 * t[3 * i + k] - z[3 * i + k] + g4 * as[3 * i + k];
@@ -404,12 +401,56 @@ static int64_t iterate_anchored(int64_t n, int64_t m, const int32_t* src, const 
     }
     for (int64_t i = 0; i < n; ++i)
         for (int k = 0; k < 3; ++k) s[3 * i + k] = sn[3 * i + k] / a4[i];
+}
 
-    /* (3e), (3f) relaxed dual updates */
+/* (3e), (3f) relaxed dual updates */
+static void block_duals(int64_t n, const orc_params* prm, const double* p, const double* q, const double* t,
+                        const double* s, double* lam, double* z) {
+    const double b1 = prm->beta1, b2 = prm->beta2, tau = prm->tau;
     for (int64_t i = 0; i < n; ++i) {
         for (int k = 0; k < 4; ++k) lam[4 * i + k] -= tau * b1 * (p[4 * i + k] - q[4 * i + k]);
         for (int k = 0; k < 3; ++k) z[3 * i + k] -= tau * b2 * (t[3 * i + k] - s[3 * i + k]);
     }
+}
+
+/* One iteration x^k -> x^{k+1} (in place).  res_out (nullable) receives 5
+ * numbers: e^{k+1} (Appendix E.1, reading R6), then |dlam|^2, |dz|^2, |dq|^2,
+ * |dt|^2.  Returns the number of vertices whose p-block hit |u_i| == 0 (R11),
+ * or -1 if out of memory. */
+static int64_t iterate_anchored(int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                                const double* qe, const double* te, const double* kappa,
+                                const double* omega, const orc_params* prm, double* p, double* q,
+                                double* t, double* s, double* lam, double* z, const double* ap,
+                                const double* aq, const double* at, const double* as, double* res_out) {
+    const double b1 = prm->beta1, b2 = prm->beta2;
+    double* u = (double*)calloc((size_t)(4 * n + 1), sizeof(double));
+    double* qn = (double*)calloc((size_t)(4 * n + 1), sizeof(double));
+    double* a2 = (double*)calloc((size_t)(n + 1), sizeof(double));
+    double* tn = (double*)calloc((size_t)(3 * n + 1), sizeof(double));
+    double* a3 = (double*)calloc((size_t)(n + 1), sizeof(double));
+    double* sn = (double*)calloc((size_t)(3 * n + 1), sizeof(double));
+    double* a4 = (double*)calloc((size_t)(n + 1), sizeof(double));
+    double* c = (double*)calloc((size_t)(3 * m + 1), sizeof(double));
+    double* qold = (double*)malloc(sizeof(double) * (size_t)(4 * n + 1));
+    double* told = (double*)malloc(sizeof(double) * (size_t)(3 * n + 1));
+    double* lold = (double*)malloc(sizeof(double) * (size_t)(4 * n + 1));
+    double* zold = (double*)malloc(sizeof(double) * (size_t)(3 * n + 1));
+    int64_t nzero = 0;
+    if (!u || !qn || !a2 || !tn || !a3 || !sn || !a4 || !c || !qold || !told || !lold || !zold) {
+        nzero = -1;
+        goto out;
+    }
+    memcpy(qold, q, sizeof(double) * (size_t)(4 * n));
+    memcpy(told, t, sizeof(double) * (size_t)(3 * n));
+    memcpy(lold, lam, sizeof(double) * (size_t)(4 * n));
+    memcpy(zold, z, sizeof(double) * (size_t)(3 * n));
+
+    nzero = block_p(n, m, src, dst, qe, te, kappa, omega, prm, p, q, t, s, lam, ap, u);
+    block_q(n, m, src, dst, qe, te, kappa, omega, prm, p, q, t, s, lam, aq, qn, a2);
+    block_c(m, src, te, p, q, c);
+    block_t(n, m, src, dst, omega, prm, t, s, z, at, c, tn, a3);
+    block_s(n, m, src, dst, omega, prm, t, s, z, as, c, sn, a4);
+    block_duals(n, prm, p, q, t, s, lam, z);
 
     /* residual of Appendix E.1 (reading R6) */
     if (res_out) {
@@ -431,6 +472,51 @@ out:
     free(u); free(qn); free(a2); free(tn); free(a3); free(sn); free(a4); free(c);
     free(qold); free(told); free(lold); free(zold);
     return nzero;
+}
+
+/* One block of plain PRADMM (anchors x^k), for callers that run the blocks
+ * of Algorithm 1 one at a time (the vertex-partitioned iteration exchanges
+ * halo values between them): which = 0 p, 1 q, 2 c_e, 3 t, 4 s, 5 duals.
+ * c (3m) carries c_e from block 2 to blocks 3 and 4.  Returns the p-block's
+ * |u| == 0 count (block 0), 0 for the others, -1 if out of memory or
+ * `which` is unknown. */
+int64_t orc_block(int which, int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const double* qe,
+                  const double* te, const double* kappa, const double* omega, const orc_params* prm, double* p,
+                  double* q, double* t, double* s, double* lam, double* z, double* c) {
+    int64_t r = 0;
+    double* w4 = (double*)malloc(sizeof(double) * (size_t)(4 * n + 1));
+    double* w1 = (double*)malloc(sizeof(double) * (size_t)(n + 1));
+    double* anc = (double*)malloc(sizeof(double) * (size_t)(4 * n + 1));
+    if (!w4 || !w1 || !anc) {
+        r = -1;
+        goto out;
+    }
+    switch (which) {
+        case 0:
+            memcpy(anc, p, sizeof(double) * (size_t)(4 * n));
+            r = block_p(n, m, src, dst, qe, te, kappa, omega, prm, p, q, t, s, lam, anc, w4);
+            break;
+        case 1:
+            memcpy(anc, q, sizeof(double) * (size_t)(4 * n));
+            block_q(n, m, src, dst, qe, te, kappa, omega, prm, p, q, t, s, lam, anc, w4, w1);
+            break;
+        case 2: block_c(m, src, te, p, q, c); break;
+        case 3:
+            memcpy(anc, t, sizeof(double) * (size_t)(3 * n));
+            block_t(n, m, src, dst, omega, prm, t, s, z, anc, c, w4, w1);
+            break;
+        case 4:
+            memcpy(anc, s, sizeof(double) * (size_t)(3 * n));
+            block_s(n, m, src, dst, omega, prm, t, s, z, anc, c, w4, w1);
+            break;
+        case 5: block_duals(n, prm, p, q, t, s, lam, z); break;
+        default: r = -1;
+    }
+out:
+    free(w4);
+    free(w1);
+    free(anc);
+    return r;
 }
 
 /* The proximal anchors of the four primal blocks (the points the terms
