@@ -126,6 +126,10 @@ struct pradmm_s {
     int32_t* out_src_d = nullptr;
     double* adj_stage = nullptr;       // max(9 m, 21 n) doubles
     Ctrl* tape_ctrl = nullptr;
+    // the reverse pass recomputes the next segment on a second stream while
+    // the reverse sweeps of the current one run (fork / join by events)
+    cudaStream_t adj_stream = nullptr;
+    cudaEvent_t adj_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaGraphExec_t adj_exec = nullptr;  // reverse pass of the current tape geometry
     long long adj_key[5] = {0, 0, 0, 0, 0};
 
@@ -624,6 +628,9 @@ void free_all(pradmm_s* h) {
     for (void* v : h->allocs) cudaFree(v);
     h->allocs.clear();
     if (h->ctrl_h) cudaFreeHost(h->ctrl_h);
+    for (cudaEvent_t& ev : h->adj_ev)
+        if (ev) cudaEventDestroy(ev);
+    if (h->adj_stream) cudaStreamDestroy(h->adj_stream);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -1142,8 +1149,14 @@ pradmm_status snapshot(pradmm_s* h, void* dst) {
 }
 
 // Slots of a tape for K iterations with a checkpoint every C: ceil(K/C) + 1
-// checkpoints and C - 1 recompute slots.
-size_t tape_slots(int K, int C) { return K == 0 ? 1 : (size_t)((K + C - 1) / C + 1) + (size_t)(C - 1); }
+// checkpoints and C - 1 recompute slots, twice when there are several
+// segments (the reverse pass recomputes one segment while it runs the
+// reverse sweeps of the next, each in its own set of slots).
+size_t tape_slots(int K, int C) {
+    if (K == 0) return 1;
+    const size_t segs = (size_t)((K + C - 1) / C);
+    return segs + 1 + (size_t)(C - 1) * (segs > 1 ? 2 : 1);
+}
 
 // Checkpoint spacing chosen from the device memory: the smallest C (least
 // recomputation; C = 1 stores every iterate and recomputes nothing) whose tape
@@ -1260,6 +1273,8 @@ pradmm_status ensure_adjoint(pradmm_s* h) {
         ST(dalloc(h, &h->out_src_d, (size_t)m));
         ST(dalloc(h, &h->adj_stage, std::max<size_t>(9 * (size_t)m, 21 * (size_t)n)));
         ST(dalloc(h, &h->tape_ctrl, 1));
+        CU(cudaStreamCreateWithFlags(&h->adj_stream, cudaStreamNonBlocking));
+        for (cudaEvent_t& ev : h->adj_ev) CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
         if (m > 0) {
             CU(cudaMemcpy(h->out_edge_d, h->out_edge.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
             CU(cudaMemcpy(h->out_src_d, h->out_src.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
@@ -1296,8 +1311,14 @@ pradmm::AdjDev<R> adj_dev(pradmm_s* h) {
     return A;
 }
 
-// Seed + every segment (recompute from its checkpoint, then the reverse
-// sweeps from its last iteration back to its first), in stream order.
+// Seed + every segment from the last: the segment's states recomputed from
+// its checkpoint, then its reverse sweeps from its last iteration back to its
+// first.  With several segments the recomputation runs on a second stream,
+// one segment ahead of the reverse sweeps and into the other of two sets of
+// recompute slots: segment ci - 1 is recomputed while the reverse sweeps of
+// segment ci run (a segment's set is rewritten only after the reverse sweeps
+// of the segment two later have read it).  The recomputation uses its own
+// control block and the residual partials; the reverse sweeps use neither.
 template <typename R>
 cudaError_t enqueue_reverse(pradmm_s* h, const pradmm::AdjDev<R>& A) {
     const int64_t n = h->n;
@@ -1314,25 +1335,59 @@ cudaError_t enqueue_reverse(pradmm_s* h, const pradmm::AdjDev<R>& A) {
     const auto SK = slot_state<R>(tape_slot(h, nck - 1), n, inert);
     RQ(pradmm::launch_adj_seed<R>(g, A, c, SK.s, SK.z, h->block, st));
     const int64_t seg0 = nck;  // first recompute slot
+    const bool two = nck - 1 > 1 && C > 1;
+    cudaStream_t st2 = two ? h->adj_stream : st;
+    cudaEvent_t* ev_rc = h->adj_ev;       // recomputation of a segment done (by parity)
+    cudaEvent_t* ev_rev = h->adj_ev + 2;  // reverse sweeps of a segment done (by parity)
     pradmm::Launch L = h->launch(false);
     L.ctrl = h->tape_ctrl;
-    for (int ci = nck - 2; ci >= 0; --ci) {
-        const long long kc = h->tape_k0 + (long long)ci * C;
+    L.stream = st2;
+    // the slots of segment ci: checkpoint, recomputed states, next checkpoint
+    auto slots_of = [&](int ci) {
         const int len = std::min(C, K - ci * C);
         std::vector<void*> slot(len + 1);
         slot[0] = tape_slot(h, ci);
         slot[len] = tape_slot(h, ci + 1);
-        for (int j = 1; j < len; ++j) slot[j] = tape_slot(h, seg0 + j - 1);
+        const int64_t base = seg0 + (two ? (int64_t)(ci & 1) * (C - 1) : 0);
+        for (int j = 1; j < len; ++j) slot[j] = tape_slot(h, base + j - 1);
+        return slot;
+    };
+    auto recompute = [&](int ci) -> cudaError_t {
+        const long long kc = h->tape_k0 + (long long)ci * C;
+        const std::vector<void*> slot = slots_of(ci);
+        const int len = (int)slot.size() - 1;
         if (len > 1) {
-            RQ(pradmm::launch_tape_arm(h->tape_ctrl, kc, st));
+            RQ(pradmm::launch_tape_arm(h->tape_ctrl, kc, st2));
             for (int j = 0; j + 1 < len; ++j) {
-                RQ(cudaMemcpyAsync(slot[j + 1], slot[j], slot_bytes(h, C), cudaMemcpyDeviceToDevice, st));
+                RQ(cudaMemcpyAsync(slot[j + 1], slot[j], slot_bytes(h, C), cudaMemcpyDeviceToDevice, st2));
                 const auto S = slot_state<R>(slot[j + 1], n, inert);
                 RQ(pradmm::launch_q<R>(g, S, c, L));
                 RQ(pradmm::launch_t<R>(g, S, c, L));
                 RQ(pradmm::launch_sp<R>(g, S, c, L));
             }
         }
+        return cudaSuccess;
+    };
+    if (two) {
+        RQ(cudaEventRecord(h->adj_ev[4], st));  // fork
+        RQ(cudaStreamWaitEvent(st2, h->adj_ev[4], 0));
+    }
+    RQ(recompute(nck - 2));
+    if (two) RQ(cudaEventRecord(ev_rc[(nck - 2) & 1], st2));
+    for (int ci = nck - 2; ci >= 0; --ci) {
+        if (two && ci >= 1) {
+            if (ci + 1 <= nck - 2) RQ(cudaStreamWaitEvent(st2, ev_rev[(ci + 1) & 1], 0));
+            RQ(recompute(ci - 1));
+            RQ(cudaEventRecord(ev_rc[(ci - 1) & 1], st2));
+        }
+        if (two) {
+            RQ(cudaStreamWaitEvent(st, ev_rc[ci & 1], 0));
+        } else if (ci != nck - 2) {
+            RQ(recompute(ci));
+        }
+        const long long kc = h->tape_k0 + (long long)ci * C;
+        const std::vector<void*> slot = slots_of(ci);
+        const int len = (int)slot.size() - 1;
         for (int j = len - 1; j >= 0; --j) {
             const long long k = kc + j;
             const auto S0 = slot_state<R>(slot[j], n, inert);
@@ -1358,6 +1413,11 @@ cudaError_t enqueue_reverse(pradmm_s* h, const pradmm::AdjDev<R>& A) {
             }
             RQ(pradmm::launch_adj_iteration<R>(g, A, X, c, h->out_src_d, (ci == 0 && j == 0) ? 0 : 1, h->block, st));
         }
+        if (two) RQ(cudaEventRecord(ev_rev[ci & 1], st));
+    }
+    if (two) {
+        RQ(cudaEventRecord(h->adj_ev[4], st2));  // join
+        RQ(cudaStreamWaitEvent(st, h->adj_ev[4], 0));
     }
 #undef RQ
     return cudaSuccess;

@@ -581,9 +581,21 @@ __device__ __forceinline__ void p_normalise_reload(const GraphDev<R>& g, const S
 #define PRADMM_SP_RELOAD 0
 #endif
 
-template <typename R, bool WITH_S, bool PIPE = false, bool NC = false, bool INERT = false>
+// A warp's edge records staged in shared memory (FP32 sweeps): out-slots
+// [ob, ob + on) and in-slots [ib, ib + inn) of the warp's 32 consecutive
+// vertices; slots past the staged count are read from global memory.
+struct Stage {
+    int ob, on, ib, inn;
+    const int32_t* oidx;
+    const float4* ote;
+    const int32_t* iidx;
+    const float4* iqk;
+};
+
+template <typename R, bool WITH_S, bool PIPE = false, bool NC = false, bool INERT = false, bool STAGED = false>
 __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R>& S, const Coef<R>& c, const R* pc,
-                                          R* pn, int64_t i, Acc<R>& adz, Ctrl* ctrl) {
+                                          R* pn, int64_t i, Acc<R>& adz, Ctrl* ctrl, const Stage* stg = nullptr) {
+    static_assert(!STAGED || sizeof(R) == sizeof(float), "staged records are FP32");
     int in0 = 0, in1 = 0;
     if (PRADMM_SP_HOIST) {
         in0 = __ldg(g.in_ptr + i);
@@ -602,6 +614,15 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
     for_edges2<SEdge<R>, PIPE>(
         g.out_ptr[i], g.out_ptr[i + 1],
         [&](int e, SEdge<R>& x) {
+            if constexpr (STAGED) {
+                const int r = e - stg->ob;
+                if (r < stg->on) {
+                    x.j = stg->oidx[r];
+                    const float4 v = stg->ote[r];
+                    x.te = {v.x, v.y, v.z, v.w};
+                    return;
+                }
+            }
             x.j = __ldg(g.out_idx + e);
             x.te = IO<R>::ldr(g.out_te, e);
         },
@@ -673,6 +694,15 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
     for_edges2<PEdge<R>, PIPE>(
         PRADMM_SP_HOIST ? in0 : g.in_ptr[i], PRADMM_SP_HOIST ? in1 : g.in_ptr[i + 1],
         [&](int e, PEdge<R>& x) {
+            if constexpr (STAGED) {
+                const int r = e - stg->ib;
+                if (r < stg->inn) {
+                    x.l = stg->iidx[r];
+                    const float4 v = stg->iqk[r];
+                    x.qk = {v.x, v.y, v.z, v.w};
+                    return;
+                }
+            }
             x.l = __ldg(g.in_idx + e);
             x.qk = IO<R>::ldr(g.in_qk, e);
         },
