@@ -155,14 +155,18 @@ def _batch_workload(args):
         return pool.map(_batch_graph, args, chunksize=16)
 
 
-def run_batched(P, rank=0, ws=1, sample=32):
+def run_batched(P, rank=0, ws=1, sample=512, long_cap=20000):
     """Batched form vs the plain form on the same GPU: all graphs solved to
-    e^k/e^1 <= 1e-6 in one persistent launch; a seeded sample of graphs is
-    re-solved one by one by the plain solver for the same iteration counts,
-    which gives the plain time (scaled to the whole batch by edge-iterations)
-    and the objective agreement.  With several ranks the graphs are split by
-    size (no exchange on the data path), the time is the slowest rank's and
-    the counts are summed; the plain comparison is then left out."""
+    e^k/e^1 <= 1e-6 in one persistent launch (at most 3,000 iterations); a
+    seeded sample of 512 graphs is re-solved one by one by the plain solver
+    for the same iteration counts, which gives the measured plain time of the
+    sample (and, scaled by edge-iterations, of the whole batch) and the
+    objective agreement.  A second solve from the same start with a cap of
+    long_cap iterations gives the time until all but the slowest graphs meet
+    the rule (the graphs past 3,000 iterations need as many in FP64: ADMM's
+    slow tail on them, not the FP32 state).  With several ranks the graphs are
+    split by size (no exchange on the data path), the time is the slowest
+    rank's and the counts are summed; the plain comparison is then left out."""
     from paper_2601_15684_gb300.shard import max_over_ranks, shard_graphs, sum_over_ranks
 
     args = _batch_args()
@@ -186,6 +190,10 @@ def run_batched(P, rank=0, ws=1, sample=32):
         t_batch = time.perf_counter() - t0
         F = B.objectives()
         m_g = B.m_g
+        B.init_odometry()
+        t0 = time.perf_counter()
+        res_long = B.solve(rel_tol=rel_tol, max_iter=long_cap)
+        t_long = time.perf_counter() - t0
     work = m_g * res["iters"]
     t_all = max_over_ranks(t_batch)
     total = {"graphs": sum_over_ranks(len(graphs)), "poses": sum_over_ranks(sum(g.n for g in graphs)),
@@ -198,6 +206,11 @@ def run_batched(P, rank=0, ws=1, sample=32):
            "graphs_per_s": total["graphs"] / t_all, "edge_updates_per_s": total["work"] / t_all,
            "iters_mean": total["iters"] / total["graphs"], "iters_max": int(iters_max),
            "converged_fraction": total["converged"] / total["graphs"],
+           "graphs_at_cap": int(total["graphs"] - total["converged"]),
+           "long_solve": {"max_iter": long_cap, "time_s": max_over_ranks(t_long),
+                          "converged_fraction": sum_over_ranks(float((res_long["status"] == 0).sum())) / total["graphs"],
+                          "iters_max": max_over_ranks(int(res_long["iters"].max())),
+                          "iters_of_graphs_past_the_cap": sorted(int(x) for x in res_long["iters"][res["status"] != 0])},
            "schedule": {"block": schedule_p[0], "warp_max_n": schedule_p[1], "cluster": schedule_p[2],
                         "cluster_min_n": schedule_p[3],
                         "autotuned": "profiled: probes at 5 % of each graph's iterations in a first solve"},
@@ -219,10 +232,13 @@ def run_batched(P, rank=0, ws=1, sample=32):
             t_plain += time.perf_counter() - t0
             Fp = S.objective()
         rel_F = max(rel_F, abs(F[k] - Fp) / max(abs(Fp), 1e-300))
-    scale = float(work.sum()) / max(float(work[pick].sum()), 1.0)
-    plain_total = t_plain * scale
-    out.update({"plain": {"sample_graphs": int(len(pick)), "sample_time_s": t_plain, "estimated_total_s": plain_total,
-                          "method": "plain solver, graph by graph, same iteration counts, scaled by edge-iterations"},
+    frac = float(work[pick].sum()) / max(float(work.sum()), 1.0)
+    plain_total = t_plain / max(frac, 1e-300)
+    out.update({"plain": {"sample_graphs": int(len(pick)), "sample_time_s": t_plain,
+                          "sample_share_of_edge_iterations": frac, "estimated_total_s": plain_total,
+                          "method": "plain solver, graph by graph, the batch's iteration counts (same stopping "
+                                    "point, objectives compared); the sample's measured time, and scaled by "
+                                    "edge-iterations to the whole batch"},
                 "speedup_vs_plain": plain_total / t_batch, "objective_max_rel_diff_vs_plain": rel_F})
     return out
 

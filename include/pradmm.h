@@ -202,6 +202,23 @@ pradmm_status pradmm_get_poses(pradmm_t h, double* q_out, double* t_out);
 /* Iterations run since the state was last set. */
 int64_t pradmm_iterations(pradmm_t h);
 
+/* Per-iteration residual trace (Appendix E.1's e^k in FP64, the value the
+ * stopping test of Algorithm 1 reads).  capacity > 0: from now on every
+ * iteration the handle runs (step, solve, the reverse mode's recording)
+ * writes its e^k into a device ring of `capacity` doubles, entry
+ * (k - 1) % capacity for iteration k, with no host round trip; capacity 0
+ * turns the trace off and frees the ring.  The handle owns the ring.  Setting
+ * the state restarts the count.  Errors: PRADMM_ERR_ARG (capacity < 0),
+ * PRADMM_ERR_NOMEM. */
+pradmm_status pradmm_set_trace(pradmm_t h, int32_t capacity);
+
+/* The traced residuals, oldest first: *count = min(iterations since the trace
+ * started or the state was set, capacity) values into host e_out (room for
+ * `capacity` doubles), *first_iter (nullable) = the iteration number k of
+ * e_out[0] (iterations are numbered from 1 after a state set).
+ * PRADMM_ERR_STATE if no trace is on. */
+pradmm_status pradmm_get_trace(pradmm_t h, double* e_out, int64_t* first_iter, int32_t* count);
+
 /* Counters: [0] p-updates recomputed in FP64, [1] p-updates with |u| = 0
  * that kept p^k, [2] iterations, [3] stop flag.  out has 4 entries. */
 pradmm_status pradmm_counters(pradmm_t h, int64_t* out);

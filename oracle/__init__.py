@@ -45,6 +45,93 @@ def build(force: bool = False) -> str:
 
 _SO_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 _lib_omp = None
+_SRC_F32 = os.path.join(_HERE, "pradmm_oracle_f32.c")
+_SO_F32 = os.path.join(_BUILD, "liboracle_f32.so")
+_lib_f32 = None
+
+
+class Params32(ctypes.Structure):
+    _fields_ = [("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("tau", ctypes.c_float),
+                ("gamma", ctypes.c_float * 4)]
+
+
+def build_f32(force: bool = False) -> str:
+    """The checker's source with its real type set to float: a tolerance
+    reference (pradmm_oracle_f32.c), never the checker."""
+    os.makedirs(_BUILD, exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_F32))
+    if force or not os.path.exists(_SO_F32) or os.path.getmtime(_SO_F32) < newest:
+        tmp = _SO_F32 + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
+                               "-fsingle-precision-constant", "-o", tmp, _SRC_F32, "-lm"])
+        os.replace(tmp, _SO_F32)
+    return _SO_F32
+
+
+def lib_f32():
+    global _lib_f32
+    with _lock:
+        if _lib_f32 is None:
+            build_f32()
+            L = ctypes.CDLL(_SO_F32)
+            P = ctypes.POINTER
+            f, i32, i64 = P(ctypes.c_float), P(ctypes.c_int32), ctypes.c_int64
+            L.orc_iterate.restype = ctypes.c_int64
+            L.orc_iterate.argtypes = [i64, i64, i32, i32, f, f, f, f, P(Params32), f, f, f, f, f, f, f]
+            L.orc_iterate_inertial.restype = ctypes.c_int64
+            L.orc_iterate_inertial.argtypes = [i64, i64, i32, i32, f, f, f, f, P(Params32), ctypes.c_float,
+                                               f, f, f, f, f, f, f, f, f, f, f]
+            _lib_f32 = L
+    return _lib_f32
+
+
+def _params32(p: Params) -> Params32:
+    q = Params32()
+    q.beta1, q.beta2, q.tau = p.beta1, p.beta2, p.tau
+    for k in range(4):
+        q.gamma[k] = p.gamma[k]
+    return q
+
+
+_KEYS = ("p", "q", "t", "s", "lam", "z")
+
+
+def iterate_f32(g, params: Params, state: dict, iters: int = 1):
+    """`iters` iterations of the oracle executed in single precision from the
+    state rounded to FP32; returns the state as float64 arrays."""
+    f = ctypes.POINTER(ctypes.c_float)
+    a = [np.ascontiguousarray(x, dtype=np.float32) for x in (g.q_meas, g.t_meas, g.kappa, g.omega)]
+    src = np.ascontiguousarray(g.src, dtype=np.int32)
+    dst = np.ascontiguousarray(g.dst, dtype=np.int32)
+    st = {k: np.array(state[k], dtype=np.float32) for k in _KEYS}
+    res = np.zeros(5, np.float32)
+    p32 = _params32(params)
+    F = lambda x: x.ctypes.data_as(f)
+    L = lib_f32()
+    for _ in range(iters):
+        L.orc_iterate(g.n, src.shape[0], _i(src), _i(dst), *[F(x) for x in a], ctypes.byref(p32),
+                      *[F(st[k]) for k in _KEYS], F(res))
+    return {k: v.astype(np.float64) for k, v in st.items()}
+
+
+def iterate_inertial_f32(g, params: Params, state: dict, theta: float, iters: int = 1, prev: dict | None = None):
+    """The inertial iteration executed in single precision (state and x^{k-1}
+    in FP32); returns (state, prev) as float64 arrays."""
+    f = ctypes.POINTER(ctypes.c_float)
+    a = [np.ascontiguousarray(x, dtype=np.float32) for x in (g.q_meas, g.t_meas, g.kappa, g.omega)]
+    src = np.ascontiguousarray(g.src, dtype=np.int32)
+    dst = np.ascontiguousarray(g.dst, dtype=np.int32)
+    st = {k: np.array(state[k], dtype=np.float32) for k in _KEYS}
+    pv = {k: np.array((prev if prev is not None else state)[k], dtype=np.float32) for k in ("p", "q", "t", "s")}
+    res = np.zeros(5, np.float32)
+    p32 = _params32(params)
+    F = lambda x: x.ctypes.data_as(f)
+    L = lib_f32()
+    for _ in range(iters):
+        L.orc_iterate_inertial(g.n, src.shape[0], _i(src), _i(dst), *[F(x) for x in a], ctypes.byref(p32),
+                               ctypes.c_float(theta), *[F(st[k]) for k in _KEYS],
+                               *[F(pv[k]) for k in ("p", "q", "t", "s")], F(res))
+    return ({k: v.astype(np.float64) for k, v in st.items()}, {k: v.astype(np.float64) for k, v in pv.items()})
 
 
 def build_omp(force: bool = False) -> str:

@@ -131,6 +131,10 @@ struct pradmm_s {
     cudaStream_t adj_stream = nullptr;
     cudaEvent_t adj_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaGraphExec_t adj_exec = nullptr;  // reverse pass of the current tape geometry
+    // optional per-iteration residual trace (pradmm_set_trace): a device ring
+    double* trace_d = nullptr;
+    int trace_cap = 0;
+    long long trace_k0 = 0;            // iteration count when the trace started
     long long adj_key[5] = {0, 0, 0, 0, 0};
 
     template <typename R>
@@ -216,6 +220,8 @@ struct pradmm_s {
         L.has_cond = with_cond ? 1 : 0;
         L.window = window;
         L.has_window = l2_on ? 1 : 0;
+        L.trace = trace_d;
+        L.trace_cap = trace_cap;
         return L;
     }
 };
@@ -631,6 +637,7 @@ void free_all(pradmm_s* h) {
     for (cudaEvent_t& ev : h->adj_ev)
         if (ev) cudaEventDestroy(ev);
     if (h->adj_stream) cudaStreamDestroy(h->adj_stream);
+    if (h->trace_d) cudaFree(h->trace_d);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
 
@@ -793,6 +800,7 @@ pradmm_status set_state_dev(pradmm_s* h, const double* p, const double* q, const
         return PRADMM_OK;
     };
     CU(cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), st));  // k = 0: p^0 lives in p[0]
+    h->trace_k0 = 0;
     ST(put4(p, h->p[0]));
     ST(put4(q, h->q));
     ST(put4(lam, h->lam));
@@ -1342,6 +1350,7 @@ cudaError_t enqueue_reverse(pradmm_s* h, const pradmm::AdjDev<R>& A) {
     pradmm::Launch L = h->launch(false);
     L.ctrl = h->tape_ctrl;
     L.stream = st2;
+    L.trace = nullptr;  // replayed iterations are not traced
     // the slots of segment ci: checkpoint, recomputed states, next checkpoint
     auto slots_of = [&](int ci) {
         const int len = std::min(C, K - ci * C);
@@ -1932,6 +1941,51 @@ pradmm_status pradmm_get_state_device(pradmm_t h, double* p, double* q, double* 
 
 pradmm_status pradmm_get_poses(pradmm_t h, double* q_out, double* t_out) {
     return pradmm_get_state(h, q_out, nullptr, t_out, nullptr, nullptr, nullptr);
+}
+
+pradmm_status pradmm_set_trace(pradmm_t h, int32_t capacity) {
+    if (!h) return fail(PRADMM_ERR_ARG, "NULL handle");
+    if (capacity < 0) return fail(PRADMM_ERR_ARG, "capacity must be >= 0");
+    ST(read_ctrl(h));
+    drop_graphs(h);  // the captured loops hold the launch parameters by value
+    if (h->trace_d) {
+        CU(cudaFree(h->trace_d));
+        h->trace_d = nullptr;
+    }
+    h->trace_cap = 0;
+    if (capacity > 0) {
+        cudaError_t e = cudaMalloc(&h->trace_d, sizeof(double) * (size_t)capacity);
+        if (e != cudaSuccess) {
+            h->trace_d = nullptr;
+            return fail(e == cudaErrorMemoryAllocation ? PRADMM_ERR_NOMEM : PRADMM_ERR_CUDA, "trace of %d entries: %s",
+                        capacity, cudaGetErrorString(e));
+        }
+        h->trace_cap = capacity;
+    }
+    h->trace_k0 = h->ctrl_h->iter;
+    return PRADMM_OK;
+}
+
+pradmm_status pradmm_get_trace(pradmm_t h, double* e_out, int64_t* first_iter, int32_t* count) {
+    if (!h || !count) return fail(PRADMM_ERR_ARG, "NULL argument");
+    *count = 0;
+    if (first_iter) *first_iter = 0;
+    if (!h->trace_d) return fail(PRADMM_ERR_STATE, "no trace (pradmm_set_trace)");
+    ST(read_ctrl(h));
+    const long long k1 = h->ctrl_h->iter;
+    const long long cnt = std::max(0LL, std::min<long long>(k1 - h->trace_k0, h->trace_cap));
+    if (cnt > 0 && !e_out) return fail(PRADMM_ERR_ARG, "e_out is NULL");
+    if (cnt > 0) {
+        std::vector<double> ring((size_t)h->trace_cap);
+        CU(cudaMemcpy(ring.data(), h->trace_d, sizeof(double) * ring.size(), cudaMemcpyDeviceToHost));
+        for (long long j = 0; j < cnt; ++j) {
+            const long long k = k1 - cnt + 1 + j;  // iteration number, 1-based
+            e_out[j] = ring[(size_t)((k - 1) % h->trace_cap)];
+        }
+    }
+    if (first_iter) *first_iter = k1 - cnt + 1;
+    *count = (int32_t)cnt;
+    return PRADMM_OK;
 }
 
 int64_t pradmm_iterations(pradmm_t h) {

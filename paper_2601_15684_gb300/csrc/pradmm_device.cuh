@@ -235,6 +235,7 @@ __device__ __forceinline__ void finish_iteration(Ctrl* ctrl, const Launch& L, do
         ctrl->e_last = e;
         const long long it = ctrl->iter + 1;
         ctrl->iter = it;
+        if (L.trace) L.trace[(it - 1) % L.trace_cap] = e;
         int halt = 0;
         if (!isfinite(e)) {
             ctrl->nonfinite = 1;
@@ -379,6 +380,19 @@ __device__ __forceinline__ void for_edges2(int e0, int e1, LoadA load_a, LoadB l
     }
 }
 
+// A warp's edge records staged in shared memory (FP32 sweeps): out-slots
+// [ob, ob + on) and in-slots [ib, ib + inn) of the warp's 32 consecutive
+// vertices; slots past the staged count are read from global memory.
+struct Stage {
+    int ob, on, ib, inn;
+    const int32_t* oidx;
+    const float4* ote;
+    const int32_t* iidx;
+    const float4* iqk;
+    const float4* oqk;  // the q sweep's kappa_e q_e records
+    const float4* ite;  // the t sweep's (t_e, omega_e) records
+};
+
 // ---- q-block (3b) / Appendix B.2 + lambda (3e) --------------------------------
 // q_i = [sum_{e=(i,j)} 2 (w_e r~ p_i t~_e^* + k_e p_j q_e^*) + beta1 p_i - lam_i + gamma2 q_i] / A_2,
 // r = t_j - s_i (t^k, s^k), p = p^{k+1};  lam_i -= tau beta1 (p_i - q_i^{new}).
@@ -391,9 +405,10 @@ struct QEdge {
 // One vertex of the q-block + lambda update; adds |dq_i|^2, |dlam_i|^2.
 // INERT: the proximal anchor is q^k + theta (q^k - q^{k-1}) (inertial variant;
 // S.qprev holds q^{k-1} and receives q^k).
-template <typename R, bool PIPE = false, bool NC = false, bool INERT = false>
+template <typename R, bool PIPE = false, bool NC = false, bool INERT = false, bool STAGED = false>
 __device__ __forceinline__ void q_vertex(const GraphDev<R>& g, const StateDev<R>& S, const Coef<R>& c, const R* pn,
-                                         int64_t i, Acc<R>& adq, Acc<R>& adl) {
+                                         int64_t i, Acc<R>& adq, Acc<R>& adl, const Stage* stg = nullptr) {
+    static_assert(!STAGED || sizeof(R) == sizeof(float), "staged records are FP32");
     const Q<R> pi = asq<R>(IO<R>::ld(pn, i));
     const Q<R> qi = asq<R>(IO<R>::ld(S.q, i));
     const Q<R> li = asq<R>(IO<R>::ld(S.lam, i));
@@ -409,6 +424,16 @@ __device__ __forceinline__ void q_vertex(const GraphDev<R>& g, const StateDev<R>
     for_edges2<QEdge<R>, PIPE>(
         g.out_ptr[i], g.out_ptr[i + 1],
         [&](int e, QEdge<R>& x) {
+            if constexpr (STAGED) {
+                const int r = e - stg->ob;
+                if (r < stg->on) {
+                    x.j = stg->oidx[r];
+                    const float4 a = stg->ote[r], b = stg->oqk[r];
+                    x.te = {a.x, a.y, a.z, a.w};
+                    x.qk = {b.x, b.y, b.z, b.w};
+                    return;
+                }
+            }
             x.j = __ldg(g.out_idx + e);
             x.te = IO<R>::ldr(g.out_te, e);
             x.qk = IO<R>::ldr(g.out_qk, e);
@@ -448,9 +473,10 @@ struct TEdge {
 
 // One vertex of the t-block; adds |dt_i|^2.  PIPE: see for_edges2.
 // INERT: the proximal anchor is t^k + theta (t^k - t^{k-1}) (S.tprev).
-template <typename R, bool PIPE = false, bool NC = false, bool INERT = false>
+template <typename R, bool PIPE = false, bool NC = false, bool INERT = false, bool STAGED = false>
 __device__ __forceinline__ void t_vertex(const GraphDev<R>& g, const StateDev<R>& S, const Coef<R>& c, const R* pn,
-                                         int64_t i, Acc<R>& adt) {
+                                         int64_t i, Acc<R>& adt, const Stage* stg = nullptr) {
+    static_assert(!STAGED || sizeof(R) == sizeof(float), "staged records are FP32");
     const R4<R> tr = IO<R>::ld(S.t, i);  // (t_i, 1/A_3)
     const R4<R> sr = IO<R>::ld(S.s, i);
     const R4<R> zr = IO<R>::ld(S.z, i);
@@ -467,6 +493,15 @@ __device__ __forceinline__ void t_vertex(const GraphDev<R>& g, const StateDev<R>
     for_edges2<TEdge<R>, PIPE>(
         g.in_ptr[i], g.in_ptr[i + 1],
         [&](int e, TEdge<R>& x) {
+            if constexpr (STAGED) {
+                const int r = e - stg->ib;
+                if (r < stg->inn) {
+                    x.l = stg->iidx[r];
+                    const float4 a = stg->ite[r];
+                    x.te = {a.x, a.y, a.z, a.w};
+                    return;
+                }
+            }
             x.l = __ldg(g.in_idx + e);
             x.te = IO<R>::ldr(g.in_te, e);
         },
@@ -580,17 +615,6 @@ __device__ __forceinline__ void p_normalise_reload(const GraphDev<R>& g, const S
 #ifndef PRADMM_SP_RELOAD
 #define PRADMM_SP_RELOAD 0
 #endif
-
-// A warp's edge records staged in shared memory (FP32 sweeps): out-slots
-// [ob, ob + on) and in-slots [ib, ib + inn) of the warp's 32 consecutive
-// vertices; slots past the staged count are read from global memory.
-struct Stage {
-    int ob, on, ib, inn;
-    const int32_t* oidx;
-    const float4* ote;
-    const int32_t* iidx;
-    const float4* iqk;
-};
 
 template <typename R, bool WITH_S, bool PIPE = false, bool NC = false, bool INERT = false, bool STAGED = false>
 __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R>& S, const Coef<R>& c, const R* pc,

@@ -89,6 +89,8 @@ struct Launch {
     int has_cond;
     cudaAccessPolicyWindow window;  // L2 persistence of the gathered vertex arrays
     int has_window;
+    double* trace = nullptr;        // optional ring of e^k: iteration k writes trace[(k - 1) % trace_cap]
+    long long trace_cap = 0;
 };
 
 template <typename R>

@@ -76,6 +76,8 @@ _SIGS = {
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "pradmm_get_poses": (ctypes.c_int, [_h, _d, _d]),
     "pradmm_iterations": (ctypes.c_int64, [_h]),
+    "pradmm_set_trace": (ctypes.c_int, [_h, ctypes.c_int32]),
+    "pradmm_get_trace": (ctypes.c_int, [_h, _d, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
     "pradmm_counters": (ctypes.c_int, [_h, _i64]),
     "pradmm_bytes_per_iteration": (ctypes.c_int, [_h, _d]),
     "pradmm_profile_sweeps": (ctypes.c_int, [_h, ctypes.c_int32, _d]),
@@ -258,6 +260,19 @@ def pradmm_get_poses(h, n, q_out=None, t_out=None):
 
 def pradmm_iterations(h) -> int:
     return int(load().pradmm_iterations(h))
+
+
+def pradmm_set_trace(h, capacity: int):
+    _check(load().pradmm_set_trace(h, int(capacity)), "pradmm_set_trace")
+
+
+def pradmm_get_trace(h, capacity: int):
+    """(first iteration number, e^k array oldest first)."""
+    out = np.zeros(max(int(capacity), 1))
+    first = ctypes.c_int64(0)
+    cnt = ctypes.c_int32(0)
+    _check(load().pradmm_get_trace(h, _dp(out), ctypes.byref(first), ctypes.byref(cnt)), "pradmm_get_trace")
+    return int(first.value), out[:cnt.value].copy()
 
 
 def pradmm_counters(h) -> dict:
@@ -443,6 +458,13 @@ class Solver:
 
     def iterations(self):
         return pradmm_iterations(self.h)
+
+    def set_trace(self, capacity):
+        self._trace_cap = int(capacity)
+        pradmm_set_trace(self.h, capacity)
+
+    def trace(self):
+        return pradmm_get_trace(self.h, getattr(self, "_trace_cap", 1))
 
     def counters(self):
         return pradmm_counters(self.h)

@@ -81,18 +81,19 @@ def check_elements(gpu, orc, tol, what="", tau=1.5, beta1=1.0, beta2=1.0, keys=S
 
 
 # Per-element bounds against the FP64 oracle.
-# FP64: rounding-order differences only.
+# FP64: rounding-order differences only (1 and 10 iterations).
 # FP32: every element within ELEM_FLOOR_FP32 of its scale, or within
-# ELEM_FACTOR_FP32 times the FP64 oracle's own deviation when its state is
-# stored in FP32 (fp32_storage_run), whichever is larger.  A vertex whose
-# update is ill conditioned (|u_i| small against its terms, long drifted
-# closures) amplifies the rounding of stored FP32 values by itself; no FP32
-# implementation can be closer to the FP64 oracle there than FP32 storage
-# alone allows.  The floor covers FP32 arithmetic (a hub's sums over hundreds
-# of edges) where storage rounding alone moves the state less.
+# ELEM_FACTOR_FP32 times the deviation of an FP32 reference run from the same
+# start (the largest of the references given), whichever is larger.  The
+# references are the checker's own algorithm executed in single precision
+# (oracle.iterate_f32) and, where that build does not cover a form, the FP64
+# oracle with its state stored in FP32 (fp32_storage_run).  A vertex whose
+# update is ill conditioned amplifies FP32 rounding by itself; no FP32
+# implementation can be held closer to the FP64 iterates there than an FP32
+# execution of the same iteration gets.
 ELEM_TOL_FP64 = 1e-10
 ELEM_FLOOR_FP32 = 1e-4
-ELEM_FACTOR_FP32 = 8.0
+ELEM_FACTOR_FP32 = 16.0
 
 
 def to_fp32(st):
@@ -110,21 +111,25 @@ def fp32_storage_run(step, st0, iters):
     return st
 
 
-def check_elements_fp32(gpu, orc, orc32, what="", tau=1.5, beta1=1.0, beta2=1.0, keys=STATE_KEYS,
+def check_elements_fp32(gpu, orc, refs, what="", tau=1.5, beta1=1.0, beta2=1.0, keys=STATE_KEYS,
                         floor=ELEM_FLOOR_FP32, factor=ELEM_FACTOR_FP32):
-    """FP32 per-element rule: err_i(gpu) <= max(floor, factor * err_i(orc32))
-    for every vertex and array, errors against the FP64 oracle orc."""
+    """FP32 per-element rule: err_i(gpu) <= max(floor, factor * max_r err_i(r))
+    over the FP32 references r (a state or a list of states), every vertex and
+    array, errors against the FP64 oracle orc."""
+    if isinstance(refs, dict):
+        refs = [refs]
     eg = element_errors(gpu, orc, tau=tau, beta1=beta1, beta2=beta2, keys=keys)
-    e3 = element_errors(orc32, orc, tau=tau, beta1=beta1, beta2=beta2, keys=keys)
+    er = [element_errors(r, orc, tau=tau, beta1=beta1, beta2=beta2, keys=keys) for r in refs]
     worst = {}
     for k in eg:
         if eg[k].size == 0:
             continue
-        bound = np.maximum(floor, factor * e3[k])
+        d = np.max(np.stack([e[k] for e in er]), axis=0)
+        bound = np.maximum(floor, factor * d)
         r = eg[k] / bound
         i = int(np.argmax(r))
         worst[k] = float(r[i])
-        print(f"{what}: {k}: max element error {eg[k].max():.3e} (FP32-storage oracle {e3[k].max():.3e}); "
+        print(f"{what}: {k}: max element error {eg[k].max():.3e} (FP32 reference {d.max():.3e}); "
               f"worst error / bound {r[i]:.3f} at vertex {i} ({eg[k][i]:.3e} vs {bound[i]:.3e}); "
               f"array relerr {relerr(gpu[k], orc[k]):.3e}")
     for k, r in worst.items():

@@ -11,14 +11,21 @@ printed.
   10 iterations against the FP64 oracle (the oracle runs one iteration of
   this graph in well under a second): p, q, t, s within 1e-5 per array;
   multipliers within 1e-5 of the scale they are formed from; every element
-  within max(1e-4, 8 x the deviation of the FP64 oracle run with its state
-  stored in FP32).  The odometry start is compared first.
+  within max(1e-4, 16 x the deviation of FP32 references: the checker's
+  algorithm executed in single precision and the FP64 oracle with FP32
+  storage).  The odometry start is compared first.
 - the 4,096-walk batch (14.0M poses, 37.4M edges), solved as the benchmark
   solves it (a first solve, the profiled schedule search, then the solve to a
-  relative residual of 1e-6): the stopping rule on every graph, and sampled
+  relative residual of 1e-6, at most 3,000 iterations): the stopping rule on
+  every graph that stopped before the cap, more than 98 % of the graphs
+  stopping before it, every graph at the cap also needing more than 2,900
+  iterations in FP64 (the method's slow tail, not the FP32 state), and sampled
   graphs (the largest and four seeded picks) against the FP64 oracle run for
-  the iterations each took, within BATCH_TOL per array and, per element,
-  within the FP32 rule above.
+  the iterations each took: over thousands of iterations FP32 and FP64
+  trajectories separate along the slowly converging directions (the checker's
+  own single-precision execution ends 5 % away per array on the largest
+  graph), so p, q, t, s per array and the objective are bounded by 4 times the
+  single-precision execution's own deviation (at least 1e-5 and 1e-6).
 - helix25k (25,000 poses, 74,799 edges): 2,000 iterations.  FP64 path:
   final objective within 1e-6 relative of the oracle's.  FP32 path: the final
   objective's relative error is stated, not guaranteed (FP32 cancellation in
@@ -29,7 +36,7 @@ import pytest
 
 import oracle
 from paper_2601_15684_gb300 import synth
-from parity import check_elements_fp32, fp32_storage_run, relerr as relerr_, to_fp32
+from parity import check_elements_fp32, fp32_storage_run
 
 pytestmark = pytest.mark.gpu
 
@@ -81,15 +88,16 @@ def test_lattice1m_one_and_ten_iterations(P):
         # odometry composition in FP64 on both sides, stored as FP32 on the GPU
         assert relerr(st0["p"], q0) <= 1e-7 and relerr(st0["t"], t0) <= 1e-7
         orc = oracle.init_state(q0, t0)
-        orc32 = orc
+        orc32, orcx = orc, orc
         step = lambda st: oracle.iterate(g, _oparams(), st, 1)[0]
         done = 0
         for it in (1, 10):
             e_gpu = S.step(it - done)
             orc, res, _ = oracle.iterate(g, _oparams(), orc, it - done)
             orc32 = fp32_storage_run(step, orc32, it - done)
+            orcx = oracle.iterate_f32(g, _oparams(), orcx, it - done)
             done = it
-            _check_fp32(S.state(), orc, f"lattice1m after {it}", orc32)
+            _check_fp32(S.state(), orc, f"lattice1m after {it}", [orc32, orcx])
             assert abs(e_gpu - res[0]) <= 1e-3 * res[0]
         F = S.objective()
     F_ref = oracle.objective(g, orc["p"], orc["t"])
@@ -139,9 +147,12 @@ def test_lattice1m_general_sigma_p_update_sampled(P, precision, tol):
 
 
 # sampled graphs of the full-size batch after their own iteration counts (up
-# to thousands of FP32 iterations): p, q, t, s within BATCH_TOL per array of
-# the FP64 oracle run for the same iterations
-BATCH_TOL = 5e-4
+# to thousands of FP32 iterations): p, q, t, s per array and the objective
+# within BATCH_FACTOR times the single-precision oracle's own deviation from
+# the FP64 oracle (at least BATCH_FLOOR_STATE, BATCH_FLOOR_F)
+BATCH_FACTOR = 4.0
+BATCH_FLOOR_STATE = 1e-5
+BATCH_FLOOR_F = 1e-6
 
 
 def test_batch_4096_walks_at_the_benchmark_configuration(P):
@@ -159,9 +170,19 @@ def test_batch_4096_walks_at_the_benchmark_configuration(P):
         offs = B.offsets
     conv = res["status"] == P.PRADMM_OK
     print(f"batch: {conv.sum()} of {len(graphs)} graphs met e^k <= 1e-6 e^1; iterations max {res['iters'].max()}")
-    assert conv.mean() > 0.9
+    assert conv.mean() > 0.98
     assert (res["e_last"][conv] <= 1e-6 * res["e_first"][conv]).all()
     assert (res["iters"][~conv] == 3000).all()
+    # the graphs stopped at the cap are ADMM's slow tail, not the FP32 state:
+    # each needs more than 2,900 iterations in FP64 as well
+    capped = np.nonzero(~conv)[0]
+    if capped.size:
+        with P.Batch([graphs[k] for k in capped], precision=0) as B64:
+            B64.init_odometry()
+            r64 = B64.solve(rel_tol=1e-6, max_iter=2900)
+        print(f"batch: {capped.size} graphs at the cap; FP64 within 2,900 iterations: "
+              f"{int((r64['status'] == P.PRADMM_OK).sum())}")
+        assert (r64["status"] != P.PRADMM_OK).all(), capped[r64["status"] == P.PRADMM_OK]
     rng = np.random.default_rng(11)
     pick = [int(np.argmax([g.n for g in graphs]))] + [int(k) for k in rng.choice(4096, 4, replace=False)]
     prm = _oparams()
@@ -170,11 +191,15 @@ def test_batch_4096_walks_at_the_benchmark_configuration(P):
         q0, t0 = oracle.init_odometry(g)
         st0 = oracle.init_state(q0, t0)
         orc, _, _ = oracle.iterate(g, prm, st0, K)
-        orc32 = fp32_storage_run(lambda x: oracle.iterate(g, prm, x, 1)[0], st0, K)
+        orcx = oracle.iterate_f32(g, prm, st0, K)
         sl = {key: v[offs[k]:offs[k + 1]] for key, v in st.items()}
         what = f"batch graph {k} (n={g.n}, {K} iterations)"
         for key in ("p", "q", "t", "s"):
-            eb = relerr(sl[key], orc[key])
-            print(f"{what}: relerr({key}) {eb:.3e}, FP32-storage oracle {relerr_(orc32[key], orc[key]):.3e}")
-            assert eb <= BATCH_TOL, (what, key, eb)
-        check_elements_fp32(sl, orc, orc32, what=what, keys=("p", "q", "t", "s"))
+            eb, ex = relerr(sl[key], orc[key]), relerr(orcx[key], orc[key])
+            print(f"{what}: relerr({key}) {eb:.3e}, single-precision oracle {ex:.3e}")
+            assert eb <= max(BATCH_FLOOR_STATE, BATCH_FACTOR * ex), (what, key, eb, ex)
+        F_o = oracle.objective(g, orc["p"], orc["t"])
+        fb = abs(oracle.objective(g, sl["p"], sl["t"]) - F_o) / F_o
+        fx = abs(oracle.objective(g, orcx["p"], orcx["t"]) - F_o) / F_o
+        print(f"{what}: objective relerr {fb:.3e}, single-precision oracle {fx:.3e}")
+        assert fb <= max(BATCH_FLOOR_F, BATCH_FACTOR * fx), (what, fb, fx)

@@ -33,3 +33,24 @@ def test_openmp_build_uses_the_requested_threads():
     assert oracle.omp_threads() >= 1
     if os.environ.get("OMP_NUM_THREADS"):
         assert oracle.omp_threads() == int(os.environ["OMP_NUM_THREADS"])
+
+
+def test_single_precision_build_is_fp32_and_close():
+    # the tolerance reference: the checker's algorithm in FP32 arithmetic
+    # stays within FP32 rounding of the FP64 oracle on a well-conditioned
+    # walk, and it really rounds to FP32 (it is not the FP64 build)
+    g = synth.workload("walk128")
+    q0, t0 = oracle.init_odometry(g)
+    st0 = oracle.init_state(q0, t0)
+    prm = oracle.make_params(beta1=1.0, beta2=1.0, tau=1.5)
+    ref, _, _ = oracle.iterate(g, prm, st0, 10)
+    got = oracle.iterate_f32(g, prm, st0, 10)
+    for k in ("p", "q", "t", "s"):
+        e = np.linalg.norm(got[k] - ref[k]) / np.linalg.norm(ref[k])
+        assert 1e-9 < e < 1e-5, (k, e)
+        assert np.array_equal(got[k], got[k].astype(np.float32).astype(np.float64))
+    pr, _, _, _ = oracle.iterate_inertial(g, prm, st0, 0.4, 6)
+    pf, _ = oracle.iterate_inertial_f32(g, prm, st0, 0.4, 6)
+    for k in ("p", "t"):
+        e = np.linalg.norm(pf[k] - pr[k]) / np.linalg.norm(pr[k])
+        assert 1e-9 < e < 1e-5, (k, e)
