@@ -223,7 +223,7 @@ def run_batched(P, rank=0, ws=1, sample=512, long_cap=20000):
         return out
     rng = np.random.default_rng(0)
     pick = rng.choice(len(graphs), size=min(sample, len(graphs)), replace=False)
-    t_plain, rel_F = 0.0, 0.0
+    t_plain, rel_F = 0.0, []
     for k in pick:
         with P.Solver(graphs[k], precision=P.PRADMM_FP32) as S:
             S.init_odometry()
@@ -231,7 +231,9 @@ def run_batched(P, rank=0, ws=1, sample=512, long_cap=20000):
             S.step(int(res["iters"][k]))
             t_plain += time.perf_counter() - t0
             Fp = S.objective()
-        rel_F = max(rel_F, abs(F[k] - Fp) / max(abs(Fp), 1e-300))
+        rel_F.append(abs(F[k] - Fp) / max(abs(Fp), 1e-300))
+    rel_F = np.array(rel_F)
+    conv_pick = res["status"][pick] == 0
     frac = float(work[pick].sum()) / max(float(work.sum()), 1.0)
     plain_total = t_plain / max(frac, 1e-300)
     out.update({"plain": {"sample_graphs": int(len(pick)), "sample_time_s": t_plain,
@@ -239,7 +241,14 @@ def run_batched(P, rank=0, ws=1, sample=512, long_cap=20000):
                           "method": "plain solver, graph by graph, the batch's iteration counts (same stopping "
                                     "point, objectives compared); the sample's measured time, and scaled by "
                                     "edge-iterations to the whole batch"},
-                "speedup_vs_plain": plain_total / t_batch, "objective_max_rel_diff_vs_plain": rel_F})
+                "speedup_vs_plain": plain_total / t_batch,
+                "objective_rel_diff_vs_plain": {
+                    "median": float(np.median(rel_F)), "p99": float(np.quantile(rel_F, 0.99)),
+                    "max": float(rel_F.max()),
+                    "max_converged": float(rel_F[conv_pick].max()) if conv_pick.any() else None,
+                    "note": "two FP32 executions (batched and plain kernels contract multiply-adds differently) "
+                            "of the same iterations: over hundreds of iterations they drift apart along slowly "
+                            "converging directions"}})
     return out
 
 

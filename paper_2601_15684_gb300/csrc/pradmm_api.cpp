@@ -58,10 +58,8 @@ struct pradmm_s {
     int pstride = 1, block = 256, obj_grid = 1, sms = 1;
     int64_t out_slots = 0, in_slots = 0;  // edges per order (= m)
 
-    // host copies (input order) for the odometry initialisation
+    // the caller's edge endpoints (input order), for the odometry start's spanning forest
     std::vector<int32_t> src, dst;
-    std::vector<double> qe, te;
-    std::vector<double> inv2, inv3, inv4;  // 1/A_2, 1/A_3, 1/A_4 per internal vertex
 
     std::vector<void*> allocs;
     int32_t *out_ptr = nullptr, *in_ptr = nullptr, *out_idx = nullptr, *in_idx = nullptr;
@@ -108,8 +106,6 @@ struct pradmm_s {
     bool l2_on = false;                // this handle holds an L2 set-aside
     cudaAccessPolicyWindow window{};   // persisting window over t, s, q, p[0], p[1]
     uint64_t epoch = 0;                // bumped by every change of the state
-    std::vector<int32_t> out_edge;     // out-slot -> input edge
-    std::vector<int32_t> out_src;      // out-slot -> tail (internal id)
 
     // reverse mode: checkpoints + recompute slots, 28 n reals per slot
     void* tape = nullptr;
@@ -122,8 +118,9 @@ struct pradmm_s {
     void* adj_v = nullptr;             // inertial variant: anchor shares of xbar^{k-1}, 16 n reals
     double* tune_save = nullptr;       // pradmm_autotune: the state it restores (21 n doubles)
     double* adj_g = nullptr;           // 9 m: per-slot gradients
-    int32_t* out_edge_d = nullptr;
-    int32_t* out_src_d = nullptr;
+    int32_t* out_edge_d = nullptr;     // out-slot -> input edge
+    int32_t* edge_slot_d = nullptr;    // input edge -> out-slot
+    int32_t* out_src_d = nullptr;      // out-slot -> tail (reverse mode, on first use)
     double* adj_stage = nullptr;       // max(9 m, 21 n) doubles
     Ctrl* tape_ctrl = nullptr;
     // the reverse pass recomputes the next segment on a second stream while
@@ -228,12 +225,7 @@ struct pradmm_s {
 
 namespace {
 
-// Vertices are ordered by degree within windows of this many consecutive ids
-// (1 keeps the caller's order, which keeps chain neighbours adjacent).
-#ifndef PRADMM_SORT_WINDOW
-#define PRADMM_SORT_WINDOW 1
-#endif
-constexpr int64_t kSortWindow = PRADMM_SORT_WINDOW;
+
 
 template <typename T>
 pradmm_status dalloc(pradmm_s* h, T** ptr, size_t count) {
@@ -302,89 +294,6 @@ void parallel_for(int64_t count, F f) {
     for (auto& x : th) x.join();
 }
 
-// Stable counting sort of edge ids by key; returns ptr[n+1] and perm (sorted
-// position -> input edge).  Each host thread owns a contiguous range of keys:
-// it scans every edge in input order and places those whose key it owns, so
-// every key's edges keep their input order.
-void counting_sort(int64_t n, int64_t m, const int32_t* key, std::vector<int32_t>& ptr, std::vector<int32_t>& perm) {
-    ptr.assign(n + 1, 0);
-    perm.assign(m, 0);
-    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    const int64_t T = std::min<int64_t>(std::min<unsigned>(hw, 16u), std::max<int64_t>(1, m / 65536));
-    std::vector<int64_t> k0(T + 1), base(T + 1, 0);
-    for (int64_t t = 0; t <= T; ++t) k0[t] = n * t / T;
-    auto count = [&](int64_t t) {
-        for (int64_t e = 0; e < m; ++e) {
-            const int64_t k = key[e];
-            if (k >= k0[t] && k < k0[t + 1]) ptr[k + 1]++;
-        }
-    };
-    auto place = [&](int64_t t) {
-        // prefix over the owned keys, offset by the edges of all lower keys;
-        // a thread touches only ptr[k + 1] of its own keys k
-        const int64_t a = k0[t], b = k0[t + 1];
-        std::vector<int32_t> fill(b - a);
-        int64_t run = base[t];
-        for (int64_t k = a; k < b; ++k) {
-            fill[k - a] = (int32_t)run;
-            run += ptr[k + 1];
-            ptr[k + 1] = (int32_t)run;
-        }
-        for (int64_t e = 0; e < m; ++e) {
-            const int64_t k = key[e];
-            if (k >= a && k < b) perm[fill[k - a]++] = (int32_t)e;
-        }
-    };
-    if (T <= 1) {
-        count(0);
-        place(0);
-        return;
-    }
-    {
-        std::vector<std::thread> th;
-        for (int64_t t = 0; t < T; ++t) th.emplace_back(count, t);
-        for (auto& x : th) x.join();
-    }
-    // edges owned by the threads before t (the counts of keys [k0[t], k0[t+1]) sit in ptr[k0[t]+1 .. k0[t+1]])
-    for (int64_t t = 0; t < T; ++t) {
-        int64_t c = 0;
-        for (int64_t k = k0[t]; k < k0[t + 1]; ++k) c += ptr[k + 1];
-        base[t + 1] = base[t] + c;
-    }
-    std::vector<std::thread> th;
-    for (int64_t t = 0; t < T; ++t) th.emplace_back(place, t);
-    for (auto& x : th) x.join();
-}
-
-// CSR of one edge order over internal vertex ids: the edges of internal
-// vertex i (user vertex perm[i]) keep their input order.
-struct Csr {
-    std::vector<int32_t> ptr;   // n + 1
-    std::vector<int32_t> idx;   // other endpoint (internal id) per slot
-    std::vector<int32_t> edge;  // input edge per slot
-};
-
-Csr build_csr(int64_t n, const std::vector<int32_t>& perm, const std::vector<int32_t>& iperm,
-              const std::vector<int32_t>& ptr, const std::vector<int32_t>& sorted_edges, const int32_t* other) {
-    Csr C;
-    C.ptr.assign(n + 1, 0);
-    for (int64_t i = 0; i < n; ++i) C.ptr[i + 1] = C.ptr[i] + (ptr[perm[i] + 1] - ptr[perm[i]]);
-    const int64_t m = C.ptr[n];
-    C.idx.assign(m, 0);
-    C.edge.assign(m, -1);
-    parallel_for(n, [&](int64_t i0, int64_t i1) {
-        for (int64_t i = i0; i < i1; ++i) {
-            const int32_t u = perm[i];
-            for (int32_t k = 0; k < ptr[u + 1] - ptr[u]; ++k) {
-                const int32_t e = sorted_edges[ptr[u] + k];
-                C.idx[C.ptr[i] + k] = iperm[other[e]];
-                C.edge[C.ptr[i] + k] = e;
-            }
-        }
-    });
-    return C;
-}
-
 // Host-side check of one edge (the caller's graph is never trusted).
 pradmm_status check_edge(int64_t n, int64_t e, const int32_t* src, const int32_t* dst, const double* q_meas,
                          const double* t_meas, const double* kappa, const double* omega) {
@@ -411,16 +320,18 @@ pradmm_status check_edge(int64_t n, int64_t e, const int32_t* src, const int32_t
 pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const double* q_meas, const double* t_meas,
                     const double* kappa, const double* omega) {
     const int64_t n = h->n, m = h->m;
-    // ---- validation (never trust the caller's graph), in parallel; the first
-    // failing edge is re-checked on this thread for its message ----
-    std::vector<double> ka(m, 1.0), om(m, 1.0);
-    h->src.assign(src, src + m);
-    h->dst.assign(dst, dst + m);
-    h->qe.assign(q_meas, q_meas + 4 * m);
-    h->te.assign(t_meas, t_meas + 3 * m);
+    // ---- validation (never trust the caller's graph), in parallel host threads;
+    // the endpoints are kept for the odometry start.  The first failing edge is
+    // re-checked on this thread for its message ----
+    h->src.resize(m);
+    h->dst.resize(m);
     std::mutex bad_mu;
     int64_t bad = m;
     parallel_for(m, [&](int64_t e0, int64_t e1) {
+        if (e1 > e0) {
+            std::memcpy(h->src.data() + e0, src + e0, sizeof(int32_t) * (e1 - e0));
+            std::memcpy(h->dst.data() + e0, dst + e0, sizeof(int32_t) * (e1 - e0));
+        }
         for (int64_t e = e0; e < e1; ++e) {
             bool ok = src[e] >= 0 && src[e] < n && dst[e] >= 0 && dst[e] < n && src[e] != dst[e];
             const double k_e = kappa ? kappa[e] : 1.0, w_e = omega ? omega[e] : 1.0;
@@ -429,76 +340,28 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
             for (int c = 0; c < 4; ++c) nn += q_meas[4 * e + c] * q_meas[4 * e + c];
             ok = ok && std::isfinite(nn) && std::isfinite(t_meas[3 * e]) && std::isfinite(t_meas[3 * e + 1]) &&
                  std::isfinite(t_meas[3 * e + 2]);
-            nn = std::sqrt(nn);
-            ok = ok && std::fabs(nn - 1.0) <= 1e-6;
+            ok = ok && std::fabs(std::sqrt(nn) - 1.0) <= 1e-6;
             if (!ok) {
                 std::lock_guard<std::mutex> lk(bad_mu);
                 bad = std::min(bad, e);
                 return;
             }
-            ka[e] = k_e;
-            om[e] = w_e;
-            for (int c = 0; c < 4; ++c) h->qe[4 * e + c] /= nn;
         }
     });
     if (bad < m) {
         const pradmm_status st = check_edge(n, bad, src, dst, q_meas, t_meas, kappa, omega);
         return st != PRADMM_OK ? st : fail(PRADMM_ERR_ARG, "edge %lld is invalid", (long long)bad);
     }
-    // ---- CSR by tail (out) and by head (in), input order inside a vertex ----
-    std::vector<int32_t> optr, operm, iptr, ipermv;
-    counting_sort(n, m, src, optr, operm);
-    counting_sort(n, m, dst, iptr, ipermv);
-    // ---- internal vertex order: by degree within windows of consecutive ids ----
-    std::vector<int32_t> perm(n), iperm(n);
-    for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
-    if (kSortWindow > 1) {
-        for (int64_t w0 = 0; w0 < n; w0 += kSortWindow) {
-            const int64_t w1 = std::min<int64_t>(n, w0 + kSortWindow);
-            std::stable_sort(perm.begin() + w0, perm.begin() + w1, [&](int32_t a, int32_t b) {
-                return (optr[a + 1] - optr[a]) + (iptr[a + 1] - iptr[a]) > (optr[b + 1] - optr[b]) + (iptr[b + 1] - iptr[b]);
-            });
-        }
-    }
-    for (int64_t i = 0; i < n; ++i) iperm[perm[i]] = (int32_t)i;
-    const Csr so = build_csr(n, perm, iperm, optr, operm, dst);
-    const Csr si = build_csr(n, perm, iperm, iptr, ipermv, src);
-    h->out_slots = (int64_t)so.idx.size();
-    h->in_slots = (int64_t)si.idx.size();
-    h->out_edge = so.edge;
-    h->out_src.assign(h->out_slots, 0);
-    parallel_for(n, [&](int64_t i0, int64_t i1) {
-        for (int64_t i = i0; i < i1; ++i)
-            for (int32_t k = so.ptr[i]; k < so.ptr[i + 1]; ++k) h->out_src[k] = (int32_t)i;
-    });
-    // ---- iteration-invariant scalar block matrices (Appendix B, scalar Sigma):
-    // per vertex over its CSR slots, which hold its edges in input order ----
-    h->inv2.resize(n);
-    h->inv3.resize(n);
-    h->inv4.resize(n);
-    parallel_for(n, [&](int64_t i0, int64_t i1) {
-        for (int64_t i = i0; i < i1; ++i) {
-            double A2 = h->prm.beta1 + h->prm.gamma[1], A3 = h->prm.beta2 + h->prm.gamma[2],
-                   A4 = h->prm.beta2 + h->prm.gamma[3];
-            for (int32_t k = so.ptr[i]; k < so.ptr[i + 1]; ++k) {
-                const int64_t e = so.edge[k];
-                const double* tv = &h->te[3 * e];
-                const double tn2 = tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2];
-                A2 += 2.0 * (om[e] * tn2 + ka[e]);  // |p_i| = |p_j| = |q_e| = 1
-                A4 += 2.0 * om[e];
-            }
-            for (int32_t k = si.ptr[i]; k < si.ptr[i + 1]; ++k) A3 += 2.0 * om[si.edge[k]];
-            h->inv2[i] = 1.0 / A2;
-            h->inv3[i] = 1.0 / A3;
-            h->inv4[i] = 1.0 / A4;
-        }
-    });
+    h->out_slots = m;
+    h->in_slots = m;
     // ---- device buffers ----
     ST(dalloc(h, &h->perm_d, n));
     ST(dalloc(h, &h->out_ptr, n + 1));
     ST(dalloc(h, &h->in_ptr, n + 1));
-    ST(dalloc(h, &h->out_idx, h->out_slots));
-    ST(dalloc(h, &h->in_idx, h->in_slots));
+    ST(dalloc(h, &h->out_idx, std::max<int64_t>(m, 1)));
+    ST(dalloc(h, &h->in_idx, std::max<int64_t>(m, 1)));
+    ST(dalloc(h, &h->out_edge_d, std::max<int64_t>(m, 1)));
+    ST(dalloc(h, &h->edge_slot_d, std::max<int64_t>(m, 1)));
     ST(valloc(h, &h->out_te, 4 * h->out_slots));
     ST(valloc(h, &h->out_qk, 4 * h->out_slots));
     ST(valloc(h, &h->in_te, 4 * h->in_slots));
@@ -542,68 +405,75 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
         h->ctrl_h = static_cast<Ctrl*>(hp);
         std::memset(h->ctrl_h, 0, sizeof(Ctrl));
     }
-    CU(cudaMemcpy(h->perm_d, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
-    CU(cudaMemcpy(h->out_ptr, so.ptr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
-    CU(cudaMemcpy(h->in_ptr, si.ptr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
-    if (h->out_slots > 0) CU(cudaMemcpy(h->out_idx, so.idx.data(), sizeof(int32_t) * h->out_slots, cudaMemcpyHostToDevice));
-    if (h->in_slots > 0) CU(cudaMemcpy(h->in_idx, si.idx.data(), sizeof(int32_t) * h->in_slots, cudaMemcpyHostToDevice));
-    // edge records: the caller's measurements go up once, the slots of both
-    // orders are packed on the device (pradmm_setup.cu)
-    if (m > 0) {
-        const size_t raw = (size_t)m * (4 + 3 + 2) * sizeof(double) + 2 * (size_t)m * sizeof(int32_t);
-        char* tmp = nullptr;
-        cudaError_t e = cudaMalloc(&tmp, raw);
-        if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? PRADMM_ERR_NOMEM : PRADMM_ERR_CUDA,
-                                          "set-up buffer of %zu bytes: %s", raw, cudaGetErrorString(e));
-        double* q_d = reinterpret_cast<double*>(tmp);
-        double* t_d = q_d + 4 * m;
-        double* k_d = t_d + 3 * m;
-        double* w_d = k_d + m;
-        int32_t* oe_d = reinterpret_cast<int32_t*>(w_d + m);
-        int32_t* ie_d = oe_d + m;
-        cudaStream_t st = h->stream;
-        pradmm_status ps = PRADMM_OK;
-        auto up = [&](void* d, const void* s, size_t bytes) {
-            if (ps == PRADMM_OK && (e = cudaMemcpyAsync(d, s, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-                ps = fail(PRADMM_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
-        };
-        up(q_d, q_meas, sizeof(double) * 4 * m);
-        up(t_d, t_meas, sizeof(double) * 3 * m);
-        up(k_d, ka.data(), sizeof(double) * m);
-        up(w_d, om.data(), sizeof(double) * m);
-        up(oe_d, so.edge.data(), sizeof(int32_t) * m);
-        up(ie_d, si.edge.data(), sizeof(int32_t) * m);
-        if (ps == PRADMM_OK) {
-            e = h->fp64 ? pradmm::launch_pack_slots<double>(oe_d, m, q_d, t_d, k_d, w_d, static_cast<double*>(h->out_te),
-                                                            static_cast<double*>(h->out_qk), h->qe64, h->te64,
-                                                            h->ka64, h->om64, st)
-                        : pradmm::launch_pack_slots<float>(oe_d, m, q_d, t_d, k_d, w_d, static_cast<float*>(h->out_te),
-                                                           static_cast<float*>(h->out_qk), h->qe64, h->te64,
-                                                           h->ka64, h->om64, st);
-            if (e == cudaSuccess)
-                e = h->fp64 ? pradmm::launch_pack_slots<double>(ie_d, m, q_d, t_d, k_d, w_d,
-                                                                static_cast<double*>(h->in_te),
-                                                                static_cast<double*>(h->in_qk), nullptr, nullptr,
-                                                                nullptr, nullptr, st)
-                            : pradmm::launch_pack_slots<float>(ie_d, m, q_d, t_d, k_d, w_d,
-                                                               static_cast<float*>(h->in_te),
-                                                               static_cast<float*>(h->in_qk), nullptr, nullptr,
-                                                               nullptr, nullptr, st);
-            if (e != cudaSuccess) ps = fail(PRADMM_ERR_CUDA, "edge record packing: %s", cudaGetErrorString(e));
-        }
-        e = cudaStreamSynchronize(st);
-        if (ps == PRADMM_OK && e != cudaSuccess) ps = fail(PRADMM_ERR_CUDA, "set-up: %s", cudaGetErrorString(e));
-        cudaFree(tmp);
-        if (ps != PRADMM_OK) return ps;
+    // ---- the graph on the device: the caller's arrays go up once; both CSR
+    // orders (input order inside a vertex), the iteration-invariant scalar
+    // block matrices (Appendix B) and the per-slot edge records are built there ----
+    const int64_t nb = (n + 1023) / 1024;
+    const size_t raw = (size_t)m * (4 + 3) * sizeof(double) + (kappa ? (size_t)m * sizeof(double) : 0) +
+                       (omega ? (size_t)m * sizeof(double) : 0) + 3 * (size_t)m * sizeof(int32_t) +
+                       (size_t)(n + nb + 4) * sizeof(int32_t);
+    char* tmp = nullptr;
+    cudaError_t e = cudaMalloc(&tmp, raw);
+    if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? PRADMM_ERR_NOMEM : PRADMM_ERR_CUDA,
+                                      "set-up buffer of %zu bytes: %s", raw, cudaGetErrorString(e));
+    double* q_d = reinterpret_cast<double*>(tmp);
+    double* t_d = q_d + 4 * m;
+    double* k_d = kappa ? t_d + 3 * m : nullptr;
+    double* w_d = omega ? t_d + 3 * m + (kappa ? m : 0) : nullptr;
+    int32_t* src_d = reinterpret_cast<int32_t*>(t_d + 3 * m + (kappa ? m : 0) + (omega ? m : 0));
+    int32_t* dst_d = src_d + m;
+    int32_t* ie_d = dst_d + m;  // in-slot -> input edge
+    int32_t* fill = ie_d + m;
+    int32_t* sums = fill + n;
+    cudaStream_t st = h->stream;
+    pradmm_status ps = PRADMM_OK;
+    auto up = [&](void* d, const void* s, size_t bytes) {
+        if (ps == PRADMM_OK && bytes > 0 && (e = cudaMemcpyAsync(d, s, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            ps = fail(PRADMM_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
+    };
+    auto dev = [&](cudaError_t r, const char* what) {
+        if (ps == PRADMM_OK && r != cudaSuccess) ps = fail(PRADMM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(r));
+    };
+    up(q_d, q_meas, sizeof(double) * 4 * m);
+    up(t_d, t_meas, sizeof(double) * 3 * m);
+    if (kappa) up(k_d, kappa, sizeof(double) * m);
+    if (omega) up(w_d, omega, sizeof(double) * m);
+    up(src_d, src, sizeof(int32_t) * m);
+    up(dst_d, dst, sizeof(int32_t) * m);
+    if (ps == PRADMM_OK) {
+        dev(pradmm::build_csr_device(src_d, dst_d, n, m, h->out_ptr, h->out_edge_d, h->out_idx, h->edge_slot_d, fill,
+                                     sums, st), "out-edge CSR");
+        dev(pradmm::build_csr_device(dst_d, src_d, n, m, h->in_ptr, ie_d, h->in_idx, nullptr, fill, sums, st),
+            "in-edge CSR");
+        dev(pradmm::launch_block_inv(h->out_ptr, h->out_edge_d, h->in_ptr, ie_d, n, t_d, k_d, w_d,
+                                     h->prm.beta1 + h->prm.gamma[1], h->prm.beta2 + h->prm.gamma[2],
+                                     h->prm.beta2 + h->prm.gamma[3], h->inv2_d, h->inv3_d, h->inv4_d, st),
+            "block matrices");
+        dev(pradmm::launch_iota(h->perm_d, n, st), "vertex order");
     }
-    CU(cudaMemcpy(h->inv2_d, h->inv2.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
-    CU(cudaMemcpy(h->inv3_d, h->inv3.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
-    CU(cudaMemcpy(h->inv4_d, h->inv4.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
-    CU(cudaMemsetAsync(h->zeros, 0, sizeof(double) * 4 * n, h->stream));
-    CU(cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream));
-    CU(cudaMemsetAsync(h->obj_ticket, 0, sizeof(unsigned int), h->stream));
-    CU(cudaStreamSynchronize(h->stream));
-    return PRADMM_OK;
+    if (ps == PRADMM_OK && m > 0) {
+        e = h->fp64 ? pradmm::launch_pack_slots<double>(h->out_edge_d, m, q_d, t_d, k_d, w_d,
+                                                        static_cast<double*>(h->out_te), static_cast<double*>(h->out_qk),
+                                                        h->qe64, h->te64, h->ka64, h->om64, st)
+                    : pradmm::launch_pack_slots<float>(h->out_edge_d, m, q_d, t_d, k_d, w_d,
+                                                       static_cast<float*>(h->out_te), static_cast<float*>(h->out_qk),
+                                                       h->qe64, h->te64, h->ka64, h->om64, st);
+        if (e == cudaSuccess)
+            e = h->fp64 ? pradmm::launch_pack_slots<double>(ie_d, m, q_d, t_d, k_d, w_d, static_cast<double*>(h->in_te),
+                                                            static_cast<double*>(h->in_qk), nullptr, nullptr, nullptr,
+                                                            nullptr, st)
+                        : pradmm::launch_pack_slots<float>(ie_d, m, q_d, t_d, k_d, w_d, static_cast<float*>(h->in_te),
+                                                           static_cast<float*>(h->in_qk), nullptr, nullptr, nullptr,
+                                                           nullptr, st);
+        dev(e, "edge record packing");
+    }
+    dev(cudaMemsetAsync(h->zeros, 0, sizeof(double) * 4 * n, st), "memset");
+    dev(cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), st), "memset");
+    dev(cudaMemsetAsync(h->obj_ticket, 0, sizeof(unsigned int), st), "memset");
+    e = cudaStreamSynchronize(st);
+    if (ps == PRADMM_OK && e != cudaSuccess) ps = fail(PRADMM_ERR_CUDA, "set-up: %s", cudaGetErrorString(e));
+    cudaFree(tmp);
+    return ps;
 }
 
 void l2_window_off(pradmm_s* h);
@@ -942,34 +812,19 @@ struct UF {
     }
 };
 
-inline void hmul(const double* a, const double* b, double* o) {
-    const double w = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
-    const double x = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
-    const double y = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
-    const double z = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
-    o[0] = w;
-    o[1] = x;
-    o[2] = y;
-    o[3] = z;
-}
-
-// R(q) v via the rotation matrix of a unit quaternion
-inline void hrot(const double* q, const double* v, double* o) {
-    const double w = q[0], x = q[1], y = q[2], z = q[3];
-    const double r00 = 1 - 2 * (y * y + z * z), r01 = 2 * (x * y - w * z), r02 = 2 * (x * z + w * y);
-    const double r10 = 2 * (x * y + w * z), r11 = 1 - 2 * (x * x + z * z), r12 = 2 * (y * z - w * x);
-    const double r20 = 2 * (x * z - w * y), r21 = 2 * (y * z + w * x), r22 = 1 - 2 * (x * x + y * y);
-    o[0] = r00 * v[0] + r01 * v[1] + r02 * v[2];
-    o[1] = r10 * v[0] + r11 * v[1] + r12 * v[2];
-    o[2] = r20 * v[0] + r21 * v[1] + r22 * v[2];
-}
-
-void odometry(const pradmm_s* h, std::vector<double>& q, std::vector<double>& t) {
+// Spanning forest by edge order (Kruskal: an edge joins the forest when it
+// links two components; the scan stops once one tree spans every vertex),
+// rooted at the lowest vertex of each component by a breadth-first walk.
+// Per vertex: its parent (-1 for a root) and the tree edge e to it, coded e
+// when the vertex is the edge's head and -(e + 2) when it is its tail (-1 for
+// a root); `rounds` = the pointer-jumping
+// rounds the deepest vertex needs, ceil(log2(depth + 1)).
+void odometry_forest(const pradmm_s* h, std::vector<int32_t>& par, std::vector<int32_t>& pedge, int& rounds) {
     const int64_t n = h->n, m = h->m;
     UF uf(n);
     std::vector<int32_t> tree;
     tree.reserve(n);
-    for (int64_t e = 0; e < m; ++e) {
+    for (int64_t e = 0; e < m && (int64_t)tree.size() < n - 1; ++e) {
         const int64_t a = uf.find(h->src[e]), b = uf.find(h->dst[e]);
         if (a == b) continue;
         if (a < b) uf.par[b] = a; else uf.par[a] = b;
@@ -987,15 +842,16 @@ void odometry(const pradmm_s* h, std::vector<double>& q, std::vector<double>& t)
         adj[fill[h->src[e]]++] = e;
         adj[fill[h->dst[e]]++] = e;
     }
-    q.assign(4 * n, 0.0);
-    t.assign(3 * n, 0.0);
+    par.assign(n, -1);
+    pedge.assign(n, -1);
+    std::vector<int32_t> depth(n, 0);
     std::vector<char> seen(n, 0);
     std::vector<int64_t> queue;
     queue.reserve(n);
+    int32_t dmax = 0;
     for (int64_t r = 0; r < n; ++r) {
         if (seen[r]) continue;
         seen[r] = 1;
-        q[4 * r] = 1.0;
         queue.clear();
         queue.push_back(r);
         for (size_t head = 0; head < queue.size(); ++head) {
@@ -1003,24 +859,19 @@ void odometry(const pradmm_s* h, std::vector<double>& q, std::vector<double>& t)
             for (int64_t k = ptr[v]; k < ptr[v + 1]; ++k) {
                 const int32_t e = adj[k];
                 const int64_t a = h->src[e], b = h->dst[e];
-                double rt[3];
-                if (a == v && !seen[b]) {
-                    hmul(&q[4 * a], &h->qe[4 * e], &q[4 * b]);
-                    hrot(&q[4 * a], &h->te[3 * e], rt);
-                    for (int c = 0; c < 3; ++c) t[3 * b + c] = t[3 * a + c] + rt[c];
-                    seen[b] = 1;
-                    queue.push_back(b);
-                } else if (b == v && !seen[a]) {
-                    const double qc[4] = {h->qe[4 * e], -h->qe[4 * e + 1], -h->qe[4 * e + 2], -h->qe[4 * e + 3]};
-                    hmul(&q[4 * b], qc, &q[4 * a]);
-                    hrot(&q[4 * a], &h->te[3 * e], rt);
-                    for (int c = 0; c < 3; ++c) t[3 * a + c] = t[3 * b + c] - rt[c];
-                    seen[a] = 1;
-                    queue.push_back(a);
-                }
+                const int64_t w = a == v ? b : a;
+                if (seen[w]) continue;
+                seen[w] = 1;
+                par[w] = (int32_t)v;
+                pedge[w] = w == a ? -(e + 2) : e;
+                depth[w] = depth[v] + 1;
+                dmax = std::max(dmax, depth[w]);
+                queue.push_back(w);
             }
         }
     }
+    rounds = 0;
+    while (((int64_t)1 << rounds) <= dmax) ++rounds;
 }
 
 template <typename R>
@@ -1277,16 +1128,12 @@ pradmm_status ensure_adjoint(pradmm_s* h) {
     if (!h->adj) {
         ST(valloc(h, &h->adj, 13 * 4 * (size_t)n + (size_t)pad4(n) + 4 * (size_t)m + (size_t)m));
         ST(dalloc(h, &h->adj_g, 9 * (size_t)m));
-        ST(dalloc(h, &h->out_edge_d, (size_t)m));
-        ST(dalloc(h, &h->out_src_d, (size_t)m));
+        ST(dalloc(h, &h->out_src_d, std::max<size_t>((size_t)m, 1)));
         ST(dalloc(h, &h->adj_stage, std::max<size_t>(9 * (size_t)m, 21 * (size_t)n)));
         ST(dalloc(h, &h->tape_ctrl, 1));
         CU(cudaStreamCreateWithFlags(&h->adj_stream, cudaStreamNonBlocking));
         for (cudaEvent_t& ev : h->adj_ev) CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-        if (m > 0) {
-            CU(cudaMemcpy(h->out_edge_d, h->out_edge.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
-            CU(cudaMemcpy(h->out_src_d, h->out_src.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
-        }
+        CU(pradmm::launch_slot_owner(h->out_ptr, n, h->out_src_d, h->stream));
         R* b = static_cast<R*>(h->adj);
         R* eq = b + 13 * 4 * n + pad4(n);
         CU(pradmm::launch_adj_edges<R>(h->qe64, h->ka64, m, eq, eq + 4 * m, h->stream));
@@ -1835,13 +1682,39 @@ pradmm_status pradmm_autotune(pradmm_t h, int32_t iters, int32_t* block_out) {
 
 pradmm_status pradmm_init_odometry(pradmm_t h) {
     if (!h) return fail(PRADMM_ERR_ARG, "NULL handle");
+    std::vector<int32_t> par, pedge;
+    int rounds = 0;
     try {
-        std::vector<double> q, t;
-        odometry(h, q, t);
-        return set_state_any(h, q.data(), q.data(), t.data(), t.data(), nullptr, nullptr, false);
+        odometry_forest(h, par, pedge, rounds);
     } catch (const std::bad_alloc&) {
         return fail(PRADMM_ERR_NOMEM, "host allocation failed");
     }
+    // the compositions along the tree paths on the device (pointer jumping)
+    const int64_t n = h->n;
+    char* tmp = nullptr;
+    const size_t bytes = (size_t)n * (3 * sizeof(int32_t) + 14 * sizeof(double)) + 64;
+    cudaError_t e = cudaMalloc(&tmp, bytes);
+    if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? PRADMM_ERR_NOMEM : PRADMM_ERR_CUDA,
+                                      "odometry buffer of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    double* q = reinterpret_cast<double*>(tmp);
+    double* t = q + 4 * n;
+    double* q2 = t + 3 * n;
+    double* t2 = q2 + 4 * n;
+    int32_t* pe_d = reinterpret_cast<int32_t*>(t2 + 3 * n);
+    int32_t* par_d = pe_d + n;
+    int32_t* par2 = par_d + n;
+    cudaStream_t st = h->stream;
+    pradmm_status ps = PRADMM_OK;
+    if ((e = cudaMemcpyAsync(pe_d, pedge.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(par_d, par.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = pradmm::launch_odometry(pe_d, par_d, rounds, h->edge_slot_d, h->qe64, h->te64, n, par2, q, t, q2, t2,
+                                     st)) != cudaSuccess)
+        ps = fail(PRADMM_ERR_CUDA, "odometry: %s", cudaGetErrorString(e));
+    if (ps == PRADMM_OK) ps = set_state_any(h, q, q, t, t, nullptr, nullptr, true);
+    e = cudaStreamSynchronize(st);
+    if (ps == PRADMM_OK && e != cudaSuccess) ps = fail(PRADMM_ERR_CUDA, "odometry: %s", cudaGetErrorString(e));
+    cudaFree(tmp);
+    return ps;
 }
 
 pradmm_status pradmm_step(pradmm_t h, int32_t iters, double* e_last) {

@@ -28,29 +28,11 @@ struct R4 {
 template <typename R>
 struct IO;
 
-#ifndef PRADMM_OWN_NA
-#define PRADMM_OWN_NA 0
-#endif
-
 template <>
 struct IO<float> {
     static __device__ __forceinline__ R4<float> ld(const float* p, int64_t i) {
         float4 v = reinterpret_cast<const float4*>(p)[i];
         return {v.x, v.y, v.z, v.w};
-    }
-    // a vertex's own record, read once per sweep by its own thread: with
-    // PRADMM_OWN_NA it does not take L1 lines from the edge records and
-    // gathers, which neighbouring lanes reuse
-    static __device__ __forceinline__ R4<float> ldo(const float* p, int64_t i) {
-#if PRADMM_OWN_NA
-        float4 v;
-        asm volatile("ld.global.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
-                     : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                     : "l"(reinterpret_cast<const float4*>(p) + i));
-        return {v.x, v.y, v.z, v.w};
-#else
-        return ld(p, i);
-#endif
     }
     // edge records (invariant while any sweep runs) on the read-only path with
     // normal caching: the 32 lanes of a warp walk one dense block of records,
@@ -77,7 +59,6 @@ struct IO<double> {
         double2 u = v[0], w = v[1];
         return {u.x, u.y, w.x, w.y};
     }
-    static __device__ __forceinline__ R4<double> ldo(const double* p, int64_t i) { return ld(p, i); }
     static __device__ __forceinline__ R4<double> ldr(const double* __restrict__ p, int64_t i) {
         const double2* v = reinterpret_cast<const double2*>(p) + 2 * i;
         double2 u = __ldg(v), w = __ldg(v + 1);
@@ -380,19 +361,6 @@ __device__ __forceinline__ void for_edges2(int e0, int e1, LoadA load_a, LoadB l
     }
 }
 
-// A warp's edge records staged in shared memory (FP32 sweeps): out-slots
-// [ob, ob + on) and in-slots [ib, ib + inn) of the warp's 32 consecutive
-// vertices; slots past the staged count are read from global memory.
-struct Stage {
-    int ob, on, ib, inn;
-    const int32_t* oidx;
-    const float4* ote;
-    const int32_t* iidx;
-    const float4* iqk;
-    const float4* oqk;  // the q sweep's kappa_e q_e records
-    const float4* ite;  // the t sweep's (t_e, omega_e) records
-};
-
 // ---- q-block (3b) / Appendix B.2 + lambda (3e) --------------------------------
 // q_i = [sum_{e=(i,j)} 2 (w_e r~ p_i t~_e^* + k_e p_j q_e^*) + beta1 p_i - lam_i + gamma2 q_i] / A_2,
 // r = t_j - s_i (t^k, s^k), p = p^{k+1};  lam_i -= tau beta1 (p_i - q_i^{new}).
@@ -405,10 +373,9 @@ struct QEdge {
 // One vertex of the q-block + lambda update; adds |dq_i|^2, |dlam_i|^2.
 // INERT: the proximal anchor is q^k + theta (q^k - q^{k-1}) (inertial variant;
 // S.qprev holds q^{k-1} and receives q^k).
-template <typename R, bool PIPE = false, bool NC = false, bool INERT = false, bool STAGED = false>
+template <typename R, bool PIPE = false, bool NC = false, bool INERT = false>
 __device__ __forceinline__ void q_vertex(const GraphDev<R>& g, const StateDev<R>& S, const Coef<R>& c, const R* pn,
-                                         int64_t i, Acc<R>& adq, Acc<R>& adl, const Stage* stg = nullptr) {
-    static_assert(!STAGED || sizeof(R) == sizeof(float), "staged records are FP32");
+                                         int64_t i, Acc<R>& adq, Acc<R>& adl) {
     const Q<R> pi = asq<R>(IO<R>::ld(pn, i));
     const Q<R> qi = asq<R>(IO<R>::ld(S.q, i));
     const Q<R> li = asq<R>(IO<R>::ld(S.lam, i));
@@ -424,16 +391,6 @@ __device__ __forceinline__ void q_vertex(const GraphDev<R>& g, const StateDev<R>
     for_edges2<QEdge<R>, PIPE>(
         g.out_ptr[i], g.out_ptr[i + 1],
         [&](int e, QEdge<R>& x) {
-            if constexpr (STAGED) {
-                const int r = e - stg->ob;
-                if (r < stg->on) {
-                    x.j = stg->oidx[r];
-                    const float4 a = stg->ote[r], b = stg->oqk[r];
-                    x.te = {a.x, a.y, a.z, a.w};
-                    x.qk = {b.x, b.y, b.z, b.w};
-                    return;
-                }
-            }
             x.j = __ldg(g.out_idx + e);
             x.te = IO<R>::ldr(g.out_te, e);
             x.qk = IO<R>::ldr(g.out_qk, e);
@@ -473,10 +430,9 @@ struct TEdge {
 
 // One vertex of the t-block; adds |dt_i|^2.  PIPE: see for_edges2.
 // INERT: the proximal anchor is t^k + theta (t^k - t^{k-1}) (S.tprev).
-template <typename R, bool PIPE = false, bool NC = false, bool INERT = false, bool STAGED = false>
+template <typename R, bool PIPE = false, bool NC = false, bool INERT = false>
 __device__ __forceinline__ void t_vertex(const GraphDev<R>& g, const StateDev<R>& S, const Coef<R>& c, const R* pn,
-                                         int64_t i, Acc<R>& adt, const Stage* stg = nullptr) {
-    static_assert(!STAGED || sizeof(R) == sizeof(float), "staged records are FP32");
+                                         int64_t i, Acc<R>& adt) {
     const R4<R> tr = IO<R>::ld(S.t, i);  // (t_i, 1/A_3)
     const R4<R> sr = IO<R>::ld(S.s, i);
     const R4<R> zr = IO<R>::ld(S.z, i);
@@ -493,15 +449,6 @@ __device__ __forceinline__ void t_vertex(const GraphDev<R>& g, const StateDev<R>
     for_edges2<TEdge<R>, PIPE>(
         g.in_ptr[i], g.in_ptr[i + 1],
         [&](int e, TEdge<R>& x) {
-            if constexpr (STAGED) {
-                const int r = e - stg->ib;
-                if (r < stg->inn) {
-                    x.l = stg->iidx[r];
-                    const float4 a = stg->ite[r];
-                    x.te = {a.x, a.y, a.z, a.w};
-                    return;
-                }
-            }
             x.l = __ldg(g.in_idx + e);
             x.te = IO<R>::ldr(g.in_te, e);
         },
@@ -554,82 +501,13 @@ struct PEdge {
 // INERT (with the s-block): the proximal anchors are s^k + theta (s^k - s^{k-1})
 // (S.sprev) and, for the next p-block, p^{k+1} + theta (p^{k+1} - p^k), p^k being
 // the vertex's value in pn before it is overwritten.
-// p-update finish with the FP64 recompute's inputs re-read from memory
-// (PRADMM_SP_RELOAD): q_i, lam_i, p_i and s_i (s^{new} once the s-block has
-// stored it) are not held in registers through the in-edge pass for the rare
-// vertex whose |u| is tiny.
-template <typename R, bool ANCHOR_PN>
-__device__ __noinline__ void p_fallback_reload(const GraphDev<R>& g, const StateDev<R>& S, int64_t i, const R* pc,
-                                               R* pn, const Coef<R>& c, Ctrl* ctrl) {
-    const R4<R> qr = IO<R>::ld(S.q, i), lr = IO<R>::ld(S.lam, i), pr = IO<R>::ld(pc, i), sr = IO<R>::ld(S.s, i);
-    R4<R> pa = pr;
-    if (ANCHOR_PN) {
-        const R4<R> po = IO<R>::ld(pn, i);
-        pa = {pr.a + c.theta * (pr.a - po.a), pr.b + c.theta * (pr.b - po.b), pr.c + c.theta * (pr.c - po.c),
-              pr.d + c.theta * (pr.d - po.d)};
-    }
-    const Q<double> ud = p_rhs_serial<R, double>(g, S.t, S.q, i, asq<double>(qr), asq<double>(lr), asq<double>(pa),
-                                                 double(sr.a), double(sr.b), double(sr.c), c);
-    const double nd = sqrt(ud.w * ud.w + ud.x * ud.x + ud.y * ud.y + ud.z * ud.z);
-    atomicAdd(&ctrl->fallbacks, 1ull);
-    if (nd > 0.0) {
-        IO<R>::st(pn, i, R(ud.w / nd), R(ud.x / nd), R(ud.y / nd), R(ud.z / nd));
-    } else {
-        atomicAdd(&ctrl->zero_u, 1ull);
-        IO<R>::st(pn, i, pr.a, pr.b, pr.c, pr.d);
-    }
-}
-
-template <typename R, bool ANCHOR_PN>
-__device__ __forceinline__ void p_normalise_reload(const GraphDev<R>& g, const StateDev<R>& S, int64_t i,
-                                                   const Q<R>& u, const R* pc, R* pn, const Coef<R>& c, Ctrl* ctrl) {
-    const R nn = u.w * u.w + u.x * u.x + u.y * u.y + u.z * u.z;
-    const R nrm = sqrt(nn);
-    if (sizeof(R) == sizeof(float) && nrm < R(c.fb_thresh)) {
-        p_fallback_reload<R, ANCHOR_PN>(g, S, i, pc, pn, c, ctrl);
-        return;
-    }
-    if (nn > R(0)) {
-        const R inv = R(1) / nrm;
-        IO<R>::st(pn, i, u.w * inv, u.x * inv, u.y * inv, u.z * inv);
-    } else {
-        atomicAdd(&ctrl->zero_u, 1ull);
-        const R4<R> pr = IO<R>::ld(pc, i);
-        IO<R>::st(pn, i, pr.a, pr.b, pr.c, pr.d);
-    }
-}
-
-// Variants of the s/z + p sweep (compile-time switches, all 0 = the form above
-// them in the history of this file):
-//  PRADMM_SP_LIN    sum_e 2 w_e c_e formed once as Im(q (sum_e 2 w_e t~_e) p^*)
-//                   (c_e is linear in t_e), not per edge
-//  PRADMM_SP_HOIST  the in-edge CSR range read with the vertex's first loads,
-//                   lam_i after the out-edge pass
-//  PRADMM_SP_RELOAD the FP64 recompute re-reads its inputs (p_normalise_reload)
-#ifndef PRADMM_SP_LIN
-#define PRADMM_SP_LIN 0
-#endif
-#ifndef PRADMM_SP_HOIST
-#define PRADMM_SP_HOIST 0
-#endif
-#ifndef PRADMM_SP_RELOAD
-#define PRADMM_SP_RELOAD 0
-#endif
-
-template <typename R, bool WITH_S, bool PIPE = false, bool NC = false, bool INERT = false, bool STAGED = false>
+template <typename R, bool WITH_S, bool PIPE = false, bool NC = false, bool INERT = false>
 __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R>& S, const Coef<R>& c, const R* pc,
-                                          R* pn, int64_t i, Acc<R>& adz, Ctrl* ctrl, const Stage* stg = nullptr) {
-    static_assert(!STAGED || sizeof(R) == sizeof(float), "staged records are FP32");
-    int in0 = 0, in1 = 0;
-    if (PRADMM_SP_HOIST) {
-        in0 = __ldg(g.in_ptr + i);
-        in1 = __ldg(g.in_ptr + i + 1);
-    }
-    const R4<R> sr = IO<R>::ldo(S.s, i);  // (s_i, 1/A_2)
-    const R4<R> qr = IO<R>::ldo(S.q, i);
-    const R4<R> pr = IO<R>::ldo(pc, i);
-    R4<R> lr;
-    if (!PRADMM_SP_HOIST) lr = IO<R>::ldo(S.lam, i);
+                                          R* pn, int64_t i, Acc<R>& adz, Ctrl* ctrl) {
+    const R4<R> sr = IO<R>::ld(S.s, i);  // (s_i, 1/A_2)
+    const R4<R> qr = IO<R>::ld(S.q, i);
+    const R4<R> pr = IO<R>::ld(pc, i);
+    const R4<R> lr = IO<R>::ld(S.lam, i);
     const Q<R> qi = asq<R>(qr), pi = asq<R>(pr);
     // out-edge pass: s-block sum (WITH_S), p-block term at s^{old}, sum 2 w t_e
     R ax = R(0), ay = R(0), az = R(0);
@@ -638,15 +516,6 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
     for_edges2<SEdge<R>, PIPE>(
         g.out_ptr[i], g.out_ptr[i + 1],
         [&](int e, SEdge<R>& x) {
-            if constexpr (STAGED) {
-                const int r = e - stg->ob;
-                if (r < stg->on) {
-                    x.j = stg->oidx[r];
-                    const float4 v = stg->ote[r];
-                    x.te = {v.x, v.y, v.z, v.w};
-                    return;
-                }
-            }
             x.j = __ldg(g.out_idx + e);
             x.te = IO<R>::ldr(g.out_te, e);
         },
@@ -654,17 +523,9 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
         [&](const SEdge<R>& x) {
             const R w2 = R(2) * x.te.d;
             if (WITH_S) {
-                if (PRADMM_SP_LIN) {
-                    ax += w2 * x.tj.a;
-                    ay += w2 * x.tj.b;
-                    az += w2 * x.tj.c;
-                } else {
-                    R cx, cy, cz;
-                    im_rot(qi, x.te.a, x.te.b, x.te.c, pi, cx, cy, cz);
-                    ax += w2 * (x.tj.a - cx);
-                    ay += w2 * (x.tj.b - cy);
-                    az += w2 * (x.tj.c - cz);
-                }
+                ax += w2 * x.tj.a;
+                ay += w2 * x.tj.b;
+                az += w2 * x.tj.c;
                 wx += w2 * x.te.a;
                 wy += w2 * x.te.b;
                 wz += w2 * x.te.c;
@@ -674,16 +535,15 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
         });
     R sx = sr.a, sy = sr.b, sz = sr.c;
     if (WITH_S) {
-        if (PRADMM_SP_LIN) {
-            // sum_e 2 w_e c_e = Im(q_i (sum_e 2 w_e t~_e) p_i^*)
-            R cx, cy, cz;
-            im_rot(qi, wx, wy, wz, pi, cx, cy, cz);
-            ax -= cx;
-            ay -= cy;
-            az -= cz;
-        }
-        const R4<R> tr = IO<R>::ldo(S.t, i);
-        const R4<R> zr = IO<R>::ldo(S.z, i);  // (z_i, 1/A_4)
+        // sum_e 2 w_e c_e = Im(q_i (sum_e 2 w_e t~_e) p_i^*): c_e is linear in t_e,
+        // so the s-block's c_e terms are formed once, not edge by edge
+        R cx, cy, cz;
+        im_rot(qi, wx, wy, wz, pi, cx, cy, cz);
+        ax -= cx;
+        ay -= cy;
+        az -= cz;
+        const R4<R> tr = IO<R>::ld(S.t, i);
+        const R4<R> zr = IO<R>::ld(S.z, i);  // (z_i, 1/A_4)
         const R inv = zr.d;
         R sax = sr.a, say = sr.b, saz = sr.c;
         if (INERT) {
@@ -704,7 +564,6 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
         // move the p-block's out-edge term from s^{old} to s^{new}
         axpy(u, R(-1), qmul_pr(qmul_pl(sr.a - sx, sr.b - sy, sr.c - sz, qi), wx, wy, wz));
     }
-    if (PRADMM_SP_HOIST) lr = IO<R>::ldo(S.lam, i);
     // own terms beta1 q_i + lam_i + gamma1 p_i, then in-edge terms 2 q_l (k_e q_e)
     R4<R> pa = pr;  // the p-block's proximal anchor
     if (INERT && WITH_S) {
@@ -716,24 +575,14 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
               c.beta1 * qr.c + lr.c + c.g1 * pa.c, c.beta1 * qr.d + lr.d + c.g1 * pa.d};
     axpy(v, R(1), u);
     for_edges2<PEdge<R>, PIPE>(
-        PRADMM_SP_HOIST ? in0 : g.in_ptr[i], PRADMM_SP_HOIST ? in1 : g.in_ptr[i + 1],
+        g.in_ptr[i], g.in_ptr[i + 1],
         [&](int e, PEdge<R>& x) {
-            if constexpr (STAGED) {
-                const int r = e - stg->ib;
-                if (r < stg->inn) {
-                    x.l = stg->iidx[r];
-                    const float4 v = stg->iqk[r];
-                    x.qk = {v.x, v.y, v.z, v.w};
-                    return;
-                }
-            }
             x.l = __ldg(g.in_idx + e);
             x.qk = IO<R>::ldr(g.in_qk, e);
         },
         [&](PEdge<R>& x) { x.ql = gat<R, NC>(S.q, x.l); },
         [&](const PEdge<R>& x) { axpy(v, R(2), qmul(asq<R>(x.ql), asq<R>(x.qk))); });
-    if (PRADMM_SP_RELOAD) p_normalise_reload<R, INERT && WITH_S>(g, S, i, v, pc, pn, c, ctrl);
-    else p_normalise<R>(g, S, i, v, qr, lr, pr, pa, sx, sy, sz, c, pn, ctrl);
+    p_normalise<R>(g, S, i, v, qr, lr, pr, pa, sx, sy, sz, c, pn, ctrl);
 }
 
 // Out-edge terms of vertex i in F of Eq. (1) at (p, t), in double:

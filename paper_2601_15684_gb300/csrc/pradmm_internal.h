@@ -106,6 +106,27 @@ cudaError_t launch_sp(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>&
 // bps[0] first p sweep, bps[1] q sweep, bps[2] t sweep, bps[3] s/z + p sweep.
 cudaError_t sweep_occupancy(int is_double, int block, int* bps);
 
+// Set-up on the device (pradmm_setup.cu).  build_csr_device: CSR of the edges
+// by `key` (input order inside a row): ptr (n+1), slot_edge (slot -> edge),
+// idx (slot -> other endpoint), edge_slot (edge -> slot, nullable); fill (n)
+// and sums ((n + 1023) / 1024) are scratch.
+cudaError_t build_csr_device(const int32_t* key, const int32_t* other, int64_t n, int64_t m, int32_t* ptr,
+                             int32_t* slot_edge, int32_t* idx, int32_t* edge_slot, int32_t* fill, int32_t* sums,
+                             cudaStream_t st);
+cudaError_t launch_block_inv(const int32_t* out_ptr, const int32_t* out_edge, const int32_t* in_ptr,
+                             const int32_t* in_edge, int64_t n, const double* t, const double* ka, const double* om,
+                             double a2_0, double a3_0, double a4_0, double* inv2, double* inv3, double* inv4,
+                             cudaStream_t st);
+cudaError_t launch_iota(int32_t* a, int64_t n, cudaStream_t st);
+cudaError_t launch_slot_owner(const int32_t* ptr, int64_t n, int32_t* owner, cudaStream_t st);
+// Odometry poses from the spanning forest: pedge[v] = e when v is the head of
+// its tree edge e, -(e + 2) when v is its tail, -1 for a root; par[v] the
+// parent (-1 for a root), overwritten; the
+// poses end in q (4n), t (3n); par_tmp, q_tmp, t_tmp are scratch.
+cudaError_t launch_odometry(const int32_t* pedge, const int32_t* par, int rounds, const int32_t* edge_slot,
+                            const double* qe64, const double* te64, int64_t n, int32_t* par_tmp, double* q,
+                            double* t, double* q_tmp, double* t_tmp, cudaStream_t st);
+
 // Device-side parameters of a tape recording (reverse mode): after the
 // iteration that brings ctrl->iter to k0 + d, with d a multiple of C or
 // d = K, the whole state block (slot_bytes, a multiple of 16) is copied to

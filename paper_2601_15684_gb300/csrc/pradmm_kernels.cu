@@ -124,183 +124,6 @@ __global__ void __launch_bounds__(256, PRADMM_MINB_SP) k_sp(GraphDev<R> g, State
     }
 }
 
-// ---- the s/z + p sweep with each warp's edge records staged in shared memory ----
-// A warp owns 32 consecutive vertices, whose out-edge slots (and in-edge
-// slots) form one contiguous block.  Before the vertices are processed, the
-// warp copies up to kStageE records of each block into its own shared-memory
-// buffer with cp.async (no registers held while the copies are in flight, all
-// of them issued at once), so the per-edge loop reads its neighbour index
-// and record from shared memory and only the neighbour gather stays a
-// dependent global load: one level of memory latency per edge group instead
-// of two.  Slots beyond kStageE come from global memory as before.
-#ifndef PRADMM_SP_STAGE
-#define PRADMM_SP_STAGE 0
-#endif
-#ifndef PRADMM_STAGE_E
-#define PRADMM_STAGE_E 96
-#endif
-constexpr int kStageE = PRADMM_STAGE_E;
-constexpr int kStageWarpBytes = kStageE * (4 + 4 + 16 + 16);  // out idx, in idx, out (t_e, w), in k q_e
-
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
-                 "l"(gmem)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
-                 "l"(gmem)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-__global__ void __launch_bounds__(256, PRADMM_MINB_SP) k_sp_st(GraphDev<float> g, StateDev<float> S, Coef<float> c,
-                                                               Launch L) {
-    extern __shared__ __align__(16) unsigned char stage_mem[];
-    __shared__ double sh[32];
-    Ctrl* ctrl = L.ctrl;
-    if (ctrl->halt) {
-        if (L.has_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(L.cond, 0u);
-        return;
-    }
-    const long long k = ctrl->iter;
-    const float* pc = S.p[(k + 1) & 1];
-    float* pn = S.p[k & 1];
-    const int lane = threadIdx.x & 31;
-    unsigned char* wb = stage_mem + (threadIdx.x >> 5) * kStageWarpBytes;
-    int32_t* s_oidx = reinterpret_cast<int32_t*>(wb);
-    int32_t* s_iidx = s_oidx + kStageE;
-    float4* s_ote = reinterpret_cast<float4*>(wb + 8 * kStageE);
-    float4* s_iqk = s_ote + kStageE;
-    const float4* ote = reinterpret_cast<const float4*>(g.out_te);
-    const float4* iqk = reinterpret_cast<const float4*>(g.in_qk);
-    Acc<float> adz;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // warp-uniform loop over blocks of 32 consecutive vertices
-    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < g.n; base += stride) {
-        const int64_t vend = base + 32 < g.n ? base + 32 : g.n;
-        Stage st;
-        st.ob = g.out_ptr[base];
-        st.ib = g.in_ptr[base];
-        const int oe = g.out_ptr[vend], ie = g.in_ptr[vend];
-        st.on = oe - st.ob < kStageE ? oe - st.ob : kStageE;
-        st.inn = ie - st.ib < kStageE ? ie - st.ib : kStageE;
-        for (int x = lane; x < st.on; x += 32) {
-            cp_async4(s_oidx + x, g.out_idx + st.ob + x);
-            cp_async16(s_ote + x, ote + st.ob + x);
-        }
-        for (int x = lane; x < st.inn; x += 32) {
-            cp_async4(s_iidx + x, g.in_idx + st.ib + x);
-            cp_async16(s_iqk + x, iqk + st.ib + x);
-        }
-        cp_async_wait_all();
-        __syncwarp();
-        st.oidx = s_oidx;
-        st.ote = s_ote;
-        st.iidx = s_iidx;
-        st.iqk = s_iqk;
-        const int64_t i = base + lane;
-        if (i < g.n)
-            sp_vertex<float, true, PRADMM_PIPE_SP != 0, PRADMM_NC != 0, false, true>(g, S, c, pc, pn, i, adz, ctrl, &st);
-        __syncwarp();  // the buffer is refilled for the next block
-    }
-    const double sd = block_sum(adz.get(), sh);
-    if (threadIdx.x == 0) L.part[SLOT_DZ * L.pstride + blockIdx.x] = sd;
-    finish_iteration(ctrl, L, c.b1d, c.b2d, sh);
-}
-
-// The q and t sweeps with staged records (same scheme as k_sp_st): the q
-// sweep stages its out-edge indices, (t_e, w_e) and kappa_e q_e records, the
-// t sweep its in-edge indices and (t_e, w_e) records.
-#ifndef PRADMM_Q_STAGE
-#define PRADMM_Q_STAGE 0
-#endif
-#ifndef PRADMM_T_STAGE
-#define PRADMM_T_STAGE 0
-#endif
-constexpr int kStageQBytes = kStageE * (4 + 16 + 16);
-constexpr int kStageTBytes = kStageE * (4 + 16);
-
-__global__ void __launch_bounds__(256, PRADMM_MINB_Q) k_q_st(GraphDev<float> g, StateDev<float> S, Coef<float> c,
-                                                             Ctrl* ctrl, double* part, int pstride) {
-    extern __shared__ __align__(16) unsigned char stage_mem[];
-    __shared__ double sh[32];
-    if (ctrl->halt) return;
-    const long long k = ctrl->iter;
-    const float* pn = S.p[(k + 1) & 1];
-    const int lane = threadIdx.x & 31;
-    unsigned char* wb = stage_mem + (threadIdx.x >> 5) * kStageQBytes;
-    float4* s_ote = reinterpret_cast<float4*>(wb);
-    float4* s_oqk = s_ote + kStageE;
-    int32_t* s_oidx = reinterpret_cast<int32_t*>(s_oqk + kStageE);
-    const float4* ote = reinterpret_cast<const float4*>(g.out_te);
-    const float4* oqk = reinterpret_cast<const float4*>(g.out_qk);
-    Acc<float> adq, adl;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < g.n; base += stride) {
-        const int64_t vend = base + 32 < g.n ? base + 32 : g.n;
-        Stage st = {};
-        st.ob = g.out_ptr[base];
-        const int oe = g.out_ptr[vend];
-        st.on = oe - st.ob < kStageE ? oe - st.ob : kStageE;
-        for (int x = lane; x < st.on; x += 32) {
-            cp_async4(s_oidx + x, g.out_idx + st.ob + x);
-            cp_async16(s_ote + x, ote + st.ob + x);
-            cp_async16(s_oqk + x, oqk + st.ob + x);
-        }
-        cp_async_wait_all();
-        __syncwarp();
-        st.oidx = s_oidx;
-        st.ote = s_ote;
-        st.oqk = s_oqk;
-        const int64_t i = base + lane;
-        if (i < g.n) q_vertex<float, PRADMM_PIPE_Q != 0, PRADMM_NC != 0, false, true>(g, S, c, pn, i, adq, adl, &st);
-        __syncwarp();
-    }
-    const double sq = block_sum(adq.get(), sh);
-    const double sl = block_sum(adl.get(), sh);
-    if (threadIdx.x == 0) {
-        part[SLOT_DQ * pstride + blockIdx.x] = sq;
-        part[SLOT_DLAM * pstride + blockIdx.x] = sl;
-    }
-}
-
-__global__ void PRADMM_BOUNDS_T k_t_st(GraphDev<float> g, StateDev<float> S, Coef<float> c, Ctrl* ctrl, double* part,
-                                       int pstride) {
-    extern __shared__ __align__(16) unsigned char stage_mem[];
-    __shared__ double sh[32];
-    if (ctrl->halt) return;
-    const long long k = ctrl->iter;
-    const float* pn = S.p[(k + 1) & 1];
-    const int lane = threadIdx.x & 31;
-    unsigned char* wb = stage_mem + (threadIdx.x >> 5) * kStageTBytes;
-    float4* s_ite = reinterpret_cast<float4*>(wb);
-    int32_t* s_iidx = reinterpret_cast<int32_t*>(s_ite + kStageE);
-    const float4* ite = reinterpret_cast<const float4*>(g.in_te);
-    Acc<float> adt;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < g.n; base += stride) {
-        const int64_t vend = base + 32 < g.n ? base + 32 : g.n;
-        Stage st = {};
-        st.ib = g.in_ptr[base];
-        const int ie = g.in_ptr[vend];
-        st.inn = ie - st.ib < kStageE ? ie - st.ib : kStageE;
-        for (int x = lane; x < st.inn; x += 32) {
-            cp_async4(s_iidx + x, g.in_idx + st.ib + x);
-            cp_async16(s_ite + x, ite + st.ib + x);
-        }
-        cp_async_wait_all();
-        __syncwarp();
-        st.iidx = s_iidx;
-        st.ite = s_ite;
-        const int64_t i = base + lane;
-        if (i < g.n) t_vertex<float, true, PRADMM_NC != 0, false, true>(g, S, c, pn, i, adt, &st);
-        __syncwarp();
-    }
-    const double st_ = block_sum(adt.get(), sh);
-    if (threadIdx.x == 0) part[SLOT_DT * pstride + blockIdx.x] = st_;
-}
-
 __global__ void k_arm(Ctrl* ctrl, long long iters, int use_tol, double tol) {
     ctrl->target = ctrl->iter + iters;
     ctrl->halt = iters <= 0 ? 1 : 0;
@@ -390,11 +213,11 @@ inline int conv_grid(int64_t n) {
 // Sweep launch with the handle's L2 access-policy window as a launch
 // attribute (captured into the CUDA graph with the kernel node).
 template <typename... P, typename... A>
-cudaError_t launch_sweep_smem(const Launch& L, int grid, size_t smem, void (*kern)(P...), A&&... args) {
+cudaError_t launch_sweep(const Launch& L, int grid, void (*kern)(P...), A&&... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3((unsigned)L.block);
-    cfg.dynamicSmemBytes = smem;
+    cfg.dynamicSmemBytes = 0;
     cfg.stream = L.stream;
     cudaLaunchAttribute at[1];
     if (L.has_window) {
@@ -406,14 +229,6 @@ cudaError_t launch_sweep_smem(const Launch& L, int grid, size_t smem, void (*ker
     return cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
 }
 
-template <typename... P, typename... A>
-cudaError_t launch_sweep(const Launch& L, int grid, void (*kern)(P...), A&&... args) {
-    return launch_sweep_smem(L, grid, 0, kern, std::forward<A>(args)...);
-}
-
-inline size_t stage_smem(int block) { return (size_t)(block / 32) * kStageWarpBytes; }
-inline size_t stage_smem_q(int block) { return (size_t)(block / 32) * kStageQBytes; }
-inline size_t stage_smem_t(int block) { return (size_t)(block / 32) * kStageTBytes; }
 
 template <typename R>
 cudaError_t launch_p(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const Launch& L) {
@@ -423,22 +238,16 @@ template <typename R>
 cudaError_t launch_q(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const Launch& L) {
     // the inertial variant (theta != 0) runs its own instances of the sweeps
     if (c.theta != R(0)) return launch_sweep(L, L.grid_q, k_q<R, true>, g, s, c, L.ctrl, L.part, L.pstride);
-    if constexpr (sizeof(R) == sizeof(float) && PRADMM_Q_STAGE)
-        return launch_sweep_smem(L, L.grid_q, stage_smem_q(L.block), k_q_st, g, s, c, L.ctrl, L.part, L.pstride);
     return launch_sweep(L, L.grid_q, k_q<R>, g, s, c, L.ctrl, L.part, L.pstride);
 }
 template <typename R>
 cudaError_t launch_t(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const Launch& L) {
     if (c.theta != R(0)) return launch_sweep(L, L.grid_t, k_t<R, true>, g, s, c, L.ctrl, L.part, L.pstride);
-    if constexpr (sizeof(R) == sizeof(float) && PRADMM_T_STAGE)
-        return launch_sweep_smem(L, L.grid_t, stage_smem_t(L.block), k_t_st, g, s, c, L.ctrl, L.part, L.pstride);
     return launch_sweep(L, L.grid_t, k_t<R>, g, s, c, L.ctrl, L.part, L.pstride);
 }
 template <typename R>
 cudaError_t launch_sp(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const Launch& L) {
     if (c.theta != R(0)) return launch_sweep(L, L.grid_sp, k_sp<R, true, true>, g, s, c, L);
-    if constexpr (sizeof(R) == sizeof(float) && PRADMM_SP_STAGE)
-        return launch_sweep_smem(L, L.grid_sp, stage_smem(L.block), k_sp_st, g, s, c, L);
     return launch_sweep(L, L.grid_sp, k_sp<R, true>, g, s, c, L);
 }
 
@@ -446,18 +255,8 @@ template <typename R>
 cudaError_t occupancy_r(int block, int* bps) {
     cudaError_t e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps[0], k_sp<R, false>, block, 0))) return e;
-    if constexpr (sizeof(R) == sizeof(float) && PRADMM_Q_STAGE) {
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps[1], k_q_st, block, stage_smem_q(block)))) return e;
-    } else {
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps[1], k_q<R>, block, 0))) return e;
-    }
-    if constexpr (sizeof(R) == sizeof(float) && PRADMM_T_STAGE) {
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps[2], k_t_st, block, stage_smem_t(block)))) return e;
-    } else {
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps[2], k_t<R>, block, 0))) return e;
-    }
-    if constexpr (sizeof(R) == sizeof(float) && PRADMM_SP_STAGE)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps[3], k_sp_st, block, stage_smem(block));
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps[1], k_q<R>, block, 0))) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps[2], k_t<R>, block, 0))) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps[3], k_sp<R, true>, block, 0);
 }
 

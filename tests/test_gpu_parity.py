@@ -3,9 +3,10 @@
 Every comparison with the oracle is made per array and element by element
 (tests/parity.py: per vertex |X_gpu,i - X_orc,i| / max(|X_orc,i|, floor)):
 FP64 every element within ELEM_TOL_FP64 = 1e-10; FP32 every element within
-max(1e-4, 16 x the deviation of FP32 references from the same start: the
-checker's algorithm executed in single precision and the FP64 oracle with its
-state stored in FP32), vertex by vertex.
+max(1e-4, 16 x the deviation at the vertex of FP32 references from the same
+start -- the checker's algorithm executed in single precision and the FP64
+oracle with its state stored in FP32 --, 32 x their root mean square
+deviation).
 
 Tolerances (relerr(X) = |X_gpu - X_oracle|_2 / |X_oracle|_2 per state array):
   FP64 path: 1e-10 after 1 and 10 iterations (rounding-order differences only;
