@@ -514,19 +514,24 @@ __global__ void k_tape_arm(Ctrl* ctrl, long long iter) {
 }
 
 __global__ void k_tape_rec_arm(TapeRec* rec, const Ctrl* ctrl, void* base, long long K, long long C,
-                               long long slot_bytes) {
+                               long long slot_bytes, long long d_last, long long slot_last) {
     rec->base = static_cast<char*>(base);
     rec->k0 = ctrl->iter;
     rec->K = K;
     rec->C = C;
     rec->slot_bytes = slot_bytes;
+    rec->d_last = d_last;
+    rec->slot_last = slot_last;
 }
 
 __global__ void __launch_bounds__(256) k_tape_copy(const TapeRec* __restrict__ rec, const Ctrl* __restrict__ ctrl,
                                                    const float4* __restrict__ src) {
     const long long d = ctrl->iter - rec->k0;
-    if (d <= 0 || d > rec->K || (d % rec->C != 0 && d != rec->K)) return;
-    const long long slot = (d + rec->C - 1) / rec->C;
+    if (d <= 0 || d > rec->K) return;
+    long long slot;
+    if (d % rec->C == 0 || d == rec->K) slot = (d + rec->C - 1) / rec->C;  // a checkpoint
+    else if (d > rec->d_last) slot = rec->slot_last + (d - rec->d_last) - 1;  // inside the last segment
+    else return;
     float4* dst = reinterpret_cast<float4*>(rec->base + slot * rec->slot_bytes);
     const long long nv = rec->slot_bytes / 16;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x)
@@ -596,8 +601,8 @@ cudaError_t launch_adj_scatter(const double* g_qe, const double* g_te, const dou
 }
 
 cudaError_t launch_tape_rec_arm(TapeRec* rec, const Ctrl* ctrl, void* base, long long K, long long C,
-                                long long slot_bytes, cudaStream_t st) {
-    k_tape_rec_arm<<<1, 1, 0, st>>>(rec, ctrl, base, K, C, slot_bytes);
+                                long long slot_bytes, long long d_last, long long slot_last, cudaStream_t st) {
+    k_tape_rec_arm<<<1, 1, 0, st>>>(rec, ctrl, base, K, C, slot_bytes, d_last, slot_last);
     return cudaGetLastError();
 }
 

@@ -1017,6 +1017,14 @@ size_t tape_slots(int K, int C) {
     return segs + 1 + (size_t)(C - 1) * (segs > 1 ? 2 : 1);
 }
 
+// First tape slot of segment ci's recomputed states (nck checkpoints): the
+// recompute slots follow the checkpoints, in two sets used by alternate
+// segments when there are several segments.
+int64_t recompute_base(int nck, int C, int ci) {
+    const bool two = nck - 1 > 1 && C > 1;
+    return (int64_t)nck + (two ? (int64_t)(ci & 1) * (C - 1) : 0);
+}
+
 // Checkpoint spacing chosen from the device memory: the smallest C (least
 // recomputation; C = 1 stores every iterate and recomputes nothing) whose tape
 // fits in half of the free memory plus the tape already held; if none fits,
@@ -1090,7 +1098,10 @@ pradmm_status adjoint_record(pradmm_s* h, int32_t iters, int32_t ckpt_every) {
         // the checkpoints (device-side test of the iteration count)
         if (!h->tape_rec) ST(dalloc(h, &h->tape_rec, 1));
         CU(pradmm::launch_arm(h->ctrl, iters, 0, h->prm.tol, h->stream));
-        CU(pradmm::launch_tape_rec_arm(h->tape_rec, h->ctrl, h->tape, iters, C, (long long)slot_bytes(h, C), h->stream));
+        // the last segment's states are kept as the recording passes them
+        const long long d_last = (long long)(nck - 2) * C;
+        CU(pradmm::launch_tape_rec_arm(h->tape_rec, h->ctrl, h->tape, iters, C, (long long)slot_bytes(h, C), d_last,
+                                       recompute_base(nck, C, nck - 2), h->stream));
         if (h->prm.use_graph) {
             ST(ensure_graph<R>(h, true));
             CU(cudaGraphLaunch(h->rec_exec, h->stream));
@@ -1167,8 +1178,9 @@ pradmm::AdjDev<R> adj_dev(pradmm_s* h) {
 }
 
 // Seed + every segment from the last: the segment's states recomputed from
-// its checkpoint, then its reverse sweeps from its last iteration back to its
-// first.  With several segments the recomputation runs on a second stream,
+// its checkpoint (the last segment's were kept by the recording), then its
+// reverse sweeps from its last iteration back to its first.  With several
+// segments the recomputation runs on a second stream,
 // one segment ahead of the reverse sweeps and into the other of two sets of
 // recompute slots: segment ci - 1 is recomputed while the reverse sweeps of
 // segment ci run (a segment's set is rewritten only after the reverse sweeps
@@ -1189,7 +1201,6 @@ cudaError_t enqueue_reverse(pradmm_s* h, const pradmm::AdjDev<R>& A) {
     const bool inert = slot_inert(h);  // slots carry x^{k-1}
     const auto SK = slot_state<R>(tape_slot(h, nck - 1), n, inert);
     RQ(pradmm::launch_adj_seed<R>(g, A, c, SK.s, SK.z, h->block, st));
-    const int64_t seg0 = nck;  // first recompute slot
     const bool two = nck - 1 > 1 && C > 1;
     cudaStream_t st2 = two ? h->adj_stream : st;
     cudaEvent_t* ev_rc = h->adj_ev;       // recomputation of a segment done (by parity)
@@ -1204,7 +1215,7 @@ cudaError_t enqueue_reverse(pradmm_s* h, const pradmm::AdjDev<R>& A) {
         std::vector<void*> slot(len + 1);
         slot[0] = tape_slot(h, ci);
         slot[len] = tape_slot(h, ci + 1);
-        const int64_t base = seg0 + (two ? (int64_t)(ci & 1) * (C - 1) : 0);
+        const int64_t base = recompute_base(nck, C, ci);
         for (int j = 1; j < len; ++j) slot[j] = tape_slot(h, base + j - 1);
         return slot;
     };
@@ -1228,7 +1239,7 @@ cudaError_t enqueue_reverse(pradmm_s* h, const pradmm::AdjDev<R>& A) {
         RQ(cudaEventRecord(h->adj_ev[4], st));  // fork
         RQ(cudaStreamWaitEvent(st2, h->adj_ev[4], 0));
     }
-    RQ(recompute(nck - 2));
+    // the last segment's states were kept by the recording
     if (two) RQ(cudaEventRecord(ev_rc[(nck - 2) & 1], st2));
     for (int ci = nck - 2; ci >= 0; --ci) {
         if (two && ci >= 1) {

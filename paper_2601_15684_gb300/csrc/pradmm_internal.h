@@ -134,6 +134,10 @@ cudaError_t launch_odometry(const int32_t* pedge, const int32_t* par, int rounds
 struct TapeRec {
     char* base;
     long long k0, K, C, slot_bytes;
+    // the states inside the last segment (iterations d_last + j, 0 < j,
+    // below K) also go to slots slot_last + j - 1: the recompute slots the
+    // reverse pass reads for that segment, which it then need not recompute
+    long long d_last, slot_last;
 };
 
 // Inertial recording: copies p[ctrl->iter & 1] (p^k, before the s/z + next-p
@@ -142,7 +146,7 @@ template <typename R>
 cudaError_t launch_keep_pk(const Ctrl* ctrl, const R* p0, const R* p1, R* dst, int64_t n, int grid, cudaStream_t st);
 // Fills *rec with k0 = ctrl->iter (read on the device) and the arguments.
 cudaError_t launch_tape_rec_arm(TapeRec* rec, const Ctrl* ctrl, void* base, long long K, long long C,
-                                long long slot_bytes, cudaStream_t st);
+                                long long slot_bytes, long long d_last, long long slot_last, cudaStream_t st);
 // The checkpoint copy that follows each recorded iteration (a no-op between
 // checkpoints); grid-stride 16-byte copies from the state block `src`.
 cudaError_t launch_tape_copy(const TapeRec* rec, const Ctrl* ctrl, const void* src, int grid, cudaStream_t st);

@@ -35,7 +35,11 @@
 #include "pradmm_device.cuh"
 #include "pradmm_internal.h"
 
-// Resident 256-thread CTAs per SM requested from the register allocator.
+// Resident CTAs per SM requested from the register allocator (for CTAs of
+// PRADMM_SP_THREADS threads in the s/z + p sweep, 256 in the others).
+#ifndef PRADMM_SP_THREADS
+#define PRADMM_SP_THREADS 256
+#endif
 #ifndef PRADMM_MINB_SP
 #define PRADMM_MINB_SP 3
 #endif
@@ -103,7 +107,7 @@ __global__ void PRADMM_BOUNDS_T k_t(GraphDev<R> g, StateDev<R> S, Coef<R> c, Ctr
 }
 
 template <typename R, bool WITH_S, bool INERT = false>
-__global__ void __launch_bounds__(256, PRADMM_MINB_SP) k_sp(GraphDev<R> g, StateDev<R> S, Coef<R> c, Launch L) {
+__global__ void __launch_bounds__(PRADMM_SP_THREADS, PRADMM_MINB_SP) k_sp(GraphDev<R> g, StateDev<R> S, Coef<R> c, Launch L) {
     __shared__ double sh[32];
     Ctrl* ctrl = L.ctrl;
     if (WITH_S && ctrl->halt) {

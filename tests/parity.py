@@ -98,7 +98,7 @@ def check_elements(gpu, orc, tol, what="", tau=1.5, beta1=1.0, beta2=1.0, keys=S
 # execution of the same iteration gets.
 ELEM_TOL_FP64 = 1e-10
 ELEM_FLOOR_FP32 = 1e-4
-ELEM_FACTOR_FP32 = 16.0
+ELEM_FACTOR_FP32 = 32.0
 ELEM_SPREAD_FP32 = 32.0
 
 

@@ -8,7 +8,7 @@ the extrapolation (x^{-1} = x^0).
 
 Tolerances as the plain parity tests: FP64 1e-10 relative per array and per
 element, FP32 1e-5 for p, q, t, s and the multipliers against tau beta times
-the scale they are formed from, and per element max(1e-4, 16 x the deviation
+the scale they are formed from, and per element max(1e-4, 32 x the deviation
 of FP32 references of the oracle's inertial iteration: executed in single
 precision, and with its state and previous iterate stored in FP32); the same after a second step call (continuity of x^{k-1}).
 With

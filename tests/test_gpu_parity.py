@@ -3,7 +3,7 @@
 Every comparison with the oracle is made per array and element by element
 (tests/parity.py: per vertex |X_gpu,i - X_orc,i| / max(|X_orc,i|, floor)):
 FP64 every element within ELEM_TOL_FP64 = 1e-10; FP32 every element within
-max(1e-4, 16 x the deviation at the vertex of FP32 references from the same
+max(1e-4, 32 x the deviation at the vertex of FP32 references from the same
 start -- the checker's algorithm executed in single precision and the FP64
 oracle with its state stored in FP32 --, 32 x their root mean square
 deviation).
