@@ -1008,21 +1008,26 @@ pradmm_status snapshot(pradmm_s* h, void* dst) {
 }
 
 // Slots of a tape for K iterations with a checkpoint every C: ceil(K/C) + 1
-// checkpoints and C - 1 recompute slots, twice when there are several
-// segments (the reverse pass recomputes one segment while it runs the
-// reverse sweeps of the next, each in its own set of slots).
+// checkpoints and C - 1 recompute slots; with several segments three sets of
+// them: the last segment's states, kept by the recording and read by every
+// reverse pass of the tape, and two sets the reverse pass recomputes the
+// other segments into, alternately (one segment is recomputed while the
+// reverse sweeps of the next run).
 size_t tape_slots(int K, int C) {
     if (K == 0) return 1;
     const size_t segs = (size_t)((K + C - 1) / C);
-    return segs + 1 + (size_t)(C - 1) * (segs > 1 ? 2 : 1);
+    return segs + 1 + (size_t)(C - 1) * (segs > 1 ? 3 : 1);
 }
 
-// First tape slot of segment ci's recomputed states (nck checkpoints): the
-// recompute slots follow the checkpoints, in two sets used by alternate
-// segments when there are several segments.
+// First tape slot of segment ci's states between its checkpoints (nck
+// checkpoints): the recompute slots follow the checkpoints; with several
+// segments the last segment has a set of its own (the recording fills it,
+// nothing overwrites it) and the others use two sets alternately.
 int64_t recompute_base(int nck, int C, int ci) {
     const bool two = nck - 1 > 1 && C > 1;
-    return (int64_t)nck + (two ? (int64_t)(ci & 1) * (C - 1) : 0);
+    if (!two) return (int64_t)nck;
+    if (ci == nck - 2) return (int64_t)nck + 2 * (int64_t)(C - 1);
+    return (int64_t)nck + (int64_t)(ci & 1) * (C - 1);
 }
 
 // Checkpoint spacing chosen from the device memory: the smallest C (least
@@ -1183,8 +1188,9 @@ pradmm::AdjDev<R> adj_dev(pradmm_s* h) {
 // segments the recomputation runs on a second stream,
 // one segment ahead of the reverse sweeps and into the other of two sets of
 // recompute slots: segment ci - 1 is recomputed while the reverse sweeps of
-// segment ci run (a segment's set is rewritten only after the reverse sweeps
-// of the segment two later have read it).  The recomputation uses its own
+// segment ci run (a set is rewritten only after the reverse sweeps of the
+// segment two later have read it; the last segment's own set is never
+// rewritten, so every reverse pass of a tape finds it).  The recomputation uses its own
 // control block and the residual partials; the reverse sweeps use neither.
 template <typename R>
 cudaError_t enqueue_reverse(pradmm_s* h, const pradmm::AdjDev<R>& A) {
@@ -1243,7 +1249,9 @@ cudaError_t enqueue_reverse(pradmm_s* h, const pradmm::AdjDev<R>& A) {
     if (two) RQ(cudaEventRecord(ev_rc[(nck - 2) & 1], st2));
     for (int ci = nck - 2; ci >= 0; --ci) {
         if (two && ci >= 1) {
-            if (ci + 1 <= nck - 2) RQ(cudaStreamWaitEvent(st2, ev_rev[(ci + 1) & 1], 0));
+            // segment ci + 1 read the set segment ci - 1 is about to fill (the
+            // last segment reads its own set)
+            if (ci + 1 <= nck - 3) RQ(cudaStreamWaitEvent(st2, ev_rev[(ci + 1) & 1], 0));
             RQ(recompute(ci - 1));
             RQ(cudaEventRecord(ev_rc[(ci - 1) & 1], st2));
         }
