@@ -373,11 +373,9 @@ struct QEdge {
 // One vertex of the q-block + lambda update; adds |dq_i|^2, |dlam_i|^2.
 // INERT: the proximal anchor is q^k + theta (q^k - q^{k-1}) (inertial variant;
 // S.qprev holds q^{k-1} and receives q^k).
-// r0, r1: the vertex's out-edge slot range when the caller loaded it ahead
-// (r0 < 0: read here).
 template <typename R, bool PIPE = false, bool NC = false, bool INERT = false>
 __device__ __forceinline__ void q_vertex(const GraphDev<R>& g, const StateDev<R>& S, const Coef<R>& c, const R* pn,
-                                         int64_t i, Acc<R>& adq, Acc<R>& adl, int r0 = -1, int r1 = -1) {
+                                         int64_t i, Acc<R>& adq, Acc<R>& adl) {
     const Q<R> pi = asq<R>(IO<R>::ld(pn, i));
     const Q<R> qi = asq<R>(IO<R>::ld(S.q, i));
     const Q<R> li = asq<R>(IO<R>::ld(S.lam, i));
@@ -391,7 +389,7 @@ __device__ __forceinline__ void q_vertex(const GraphDev<R>& g, const StateDev<R>
     Q<R> b = {c.beta1 * pi.w - li.w + c.g2 * qa.w, c.beta1 * pi.x - li.x + c.g2 * qa.x,
               c.beta1 * pi.y - li.y + c.g2 * qa.y, c.beta1 * pi.z - li.z + c.g2 * qa.z};
     for_edges2<QEdge<R>, PIPE>(
-        r0 >= 0 ? r0 : g.out_ptr[i], r0 >= 0 ? r1 : g.out_ptr[i + 1],
+        g.out_ptr[i], g.out_ptr[i + 1],
         [&](int e, QEdge<R>& x) {
             x.j = __ldg(g.out_idx + e);
             x.te = IO<R>::ldr(g.out_te, e);
@@ -432,10 +430,9 @@ struct TEdge {
 
 // One vertex of the t-block; adds |dt_i|^2.  PIPE: see for_edges2.
 // INERT: the proximal anchor is t^k + theta (t^k - t^{k-1}) (S.tprev).
-// r0, r1: the vertex's in-edge slot range when the caller loaded it ahead.
 template <typename R, bool PIPE = false, bool NC = false, bool INERT = false>
 __device__ __forceinline__ void t_vertex(const GraphDev<R>& g, const StateDev<R>& S, const Coef<R>& c, const R* pn,
-                                         int64_t i, Acc<R>& adt, int r0 = -1, int r1 = -1) {
+                                         int64_t i, Acc<R>& adt) {
     const R4<R> tr = IO<R>::ld(S.t, i);  // (t_i, 1/A_3)
     const R4<R> sr = IO<R>::ld(S.s, i);
     const R4<R> zr = IO<R>::ld(S.z, i);
@@ -450,7 +447,7 @@ __device__ __forceinline__ void t_vertex(const GraphDev<R>& g, const StateDev<R>
     R ay = c.beta2 * sr.b + zr.b + c.g3 * tay;
     R az = c.beta2 * sr.c + zr.c + c.g3 * taz;
     for_edges2<TEdge<R>, PIPE>(
-        r0 >= 0 ? r0 : g.in_ptr[i], r0 >= 0 ? r1 : g.in_ptr[i + 1],
+        g.in_ptr[i], g.in_ptr[i + 1],
         [&](int e, TEdge<R>& x) {
             x.l = __ldg(g.in_idx + e);
             x.te = IO<R>::ldr(g.in_te, e);
@@ -504,11 +501,9 @@ struct PEdge {
 // INERT (with the s-block): the proximal anchors are s^k + theta (s^k - s^{k-1})
 // (S.sprev) and, for the next p-block, p^{k+1} + theta (p^{k+1} - p^k), p^k being
 // the vertex's value in pn before it is overwritten.
-// rg: the vertex's out- and in-edge slot ranges {o0, o1, i0, i1} when the
-// caller loaded them ahead (nullptr: read here).
 template <typename R, bool WITH_S, bool PIPE = false, bool NC = false, bool INERT = false>
 __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R>& S, const Coef<R>& c, const R* pc,
-                                          R* pn, int64_t i, Acc<R>& adz, Ctrl* ctrl, const int* rg = nullptr) {
+                                          R* pn, int64_t i, Acc<R>& adz, Ctrl* ctrl) {
     const R4<R> sr = IO<R>::ld(S.s, i);  // (s_i, 1/A_2)
     const R4<R> qr = IO<R>::ld(S.q, i);
     const R4<R> pr = IO<R>::ld(pc, i);
@@ -519,7 +514,7 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
     R wx = R(0), wy = R(0), wz = R(0);
     Q<R> u = {R(0), R(0), R(0), R(0)};
     for_edges2<SEdge<R>, PIPE>(
-        rg ? rg[0] : g.out_ptr[i], rg ? rg[1] : g.out_ptr[i + 1],
+        g.out_ptr[i], g.out_ptr[i + 1],
         [&](int e, SEdge<R>& x) {
             x.j = __ldg(g.out_idx + e);
             x.te = IO<R>::ldr(g.out_te, e);
@@ -580,7 +575,7 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
               c.beta1 * qr.c + lr.c + c.g1 * pa.c, c.beta1 * qr.d + lr.d + c.g1 * pa.d};
     axpy(v, R(1), u);
     for_edges2<PEdge<R>, PIPE>(
-        rg ? rg[2] : g.in_ptr[i], rg ? rg[3] : g.in_ptr[i + 1],
+        g.in_ptr[i], g.in_ptr[i + 1],
         [&](int e, PEdge<R>& x) {
             x.l = __ldg(g.in_idx + e);
             x.qk = IO<R>::ldr(g.in_qk, e);

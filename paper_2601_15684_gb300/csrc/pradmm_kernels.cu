@@ -35,11 +35,7 @@
 #include "pradmm_device.cuh"
 #include "pradmm_internal.h"
 
-// Resident CTAs per SM requested from the register allocator (for CTAs of
-// PRADMM_SP_THREADS threads in the s/z + p sweep, 256 in the others).
-#ifndef PRADMM_SP_THREADS
-#define PRADMM_SP_THREADS 256
-#endif
+// Resident 256-thread CTAs per SM requested from the register allocator.
 #ifndef PRADMM_MINB_SP
 #define PRADMM_MINB_SP 3
 #endif
@@ -63,11 +59,6 @@
 #ifndef PRADMM_NC
 #define PRADMM_NC 1
 #endif
-// 1: the next grid-stride vertex's CSR slot range is loaded while the current
-// vertex is processed (one dependent load level less per vertex)
-#ifndef PRADMM_NEXT_PTR
-#define PRADMM_NEXT_PTR 0
-#endif
 #if PRADMM_MINB_T > 0
 #define PRADMM_BOUNDS_T __launch_bounds__(256, PRADMM_MINB_T)
 #else
@@ -87,29 +78,8 @@ __global__ void __launch_bounds__(256, PRADMM_MINB_Q) k_q(GraphDev<R> g, StateDe
     const long long k = ctrl->iter;
     const R* pn = S.p[(k + 1) & 1];
     Acc<R> adq, adl;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    if (PRADMM_NEXT_PTR) {
-        int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-        int r0 = 0, r1 = 0;
-        if (i < g.n) {
-            r0 = __ldg(g.out_ptr + i);
-            r1 = __ldg(g.out_ptr + i + 1);
-        }
-        for (; i < g.n; i += stride) {
-            const int64_t nx = i + stride;
-            int n0 = 0, n1 = 0;
-            if (nx < g.n) {
-                n0 = __ldg(g.out_ptr + nx);
-                n1 = __ldg(g.out_ptr + nx + 1);
-            }
-            q_vertex<R, PRADMM_PIPE_Q != 0, PRADMM_NC != 0, INERT>(g, S, c, pn, i, adq, adl, r0, r1);
-            r0 = n0;
-            r1 = n1;
-        }
-    } else {
-        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += stride)
-            q_vertex<R, PRADMM_PIPE_Q != 0, PRADMM_NC != 0, INERT>(g, S, c, pn, i, adq, adl);
-    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x)
+        q_vertex<R, PRADMM_PIPE_Q != 0, PRADMM_NC != 0, INERT>(g, S, c, pn, i, adq, adl);
     const double sq = block_sum(adq.get(), sh);
     const double sl = block_sum(adl.get(), sh);
     if (threadIdx.x == 0) {
@@ -126,35 +96,14 @@ __global__ void PRADMM_BOUNDS_T k_t(GraphDev<R> g, StateDev<R> S, Coef<R> c, Ctr
     const long long k = ctrl->iter;
     const R* pn = S.p[(k + 1) & 1];
     Acc<R> adt;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    if (PRADMM_NEXT_PTR) {
-        int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-        int r0 = 0, r1 = 0;
-        if (i < g.n) {
-            r0 = __ldg(g.in_ptr + i);
-            r1 = __ldg(g.in_ptr + i + 1);
-        }
-        for (; i < g.n; i += stride) {
-            const int64_t nx = i + stride;
-            int n0 = 0, n1 = 0;
-            if (nx < g.n) {
-                n0 = __ldg(g.in_ptr + nx);
-                n1 = __ldg(g.in_ptr + nx + 1);
-            }
-            t_vertex<R, true, PRADMM_NC != 0, INERT>(g, S, c, pn, i, adt, r0, r1);
-            r0 = n0;
-            r1 = n1;
-        }
-    } else {
-        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += stride)
-            t_vertex<R, true, PRADMM_NC != 0, INERT>(g, S, c, pn, i, adt);
-    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x)
+        t_vertex<R, true, PRADMM_NC != 0, INERT>(g, S, c, pn, i, adt);
     const double st = block_sum(adt.get(), sh);
     if (threadIdx.x == 0) part[SLOT_DT * pstride + blockIdx.x] = st;
 }
 
 template <typename R, bool WITH_S, bool INERT = false>
-__global__ void __launch_bounds__(PRADMM_SP_THREADS, PRADMM_MINB_SP) k_sp(GraphDev<R> g, StateDev<R> S, Coef<R> c, Launch L) {
+__global__ void __launch_bounds__(256, PRADMM_MINB_SP) k_sp(GraphDev<R> g, StateDev<R> S, Coef<R> c, Launch L) {
     __shared__ double sh[32];
     Ctrl* ctrl = L.ctrl;
     if (WITH_S && ctrl->halt) {
@@ -166,33 +115,8 @@ __global__ void __launch_bounds__(PRADMM_SP_THREADS, PRADMM_MINB_SP) k_sp(GraphD
     const R* pc = WITH_S ? S.p[(k + 1) & 1] : S.p[k & 1];  // p used by this sweep
     R* pn = WITH_S ? S.p[k & 1] : S.p[(k + 1) & 1];        // p computed ahead
     Acc<R> adz;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    if (PRADMM_NEXT_PTR) {
-        int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-        int rg[4] = {0, 0, 0, 0};
-        if (i < g.n) {
-            rg[0] = __ldg(g.out_ptr + i);
-            rg[1] = __ldg(g.out_ptr + i + 1);
-            rg[2] = __ldg(g.in_ptr + i);
-            rg[3] = __ldg(g.in_ptr + i + 1);
-        }
-        for (; i < g.n; i += stride) {
-            const int64_t nx = i + stride;
-            int nr[4] = {0, 0, 0, 0};
-            if (nx < g.n) {
-                nr[0] = __ldg(g.out_ptr + nx);
-                nr[1] = __ldg(g.out_ptr + nx + 1);
-                nr[2] = __ldg(g.in_ptr + nx);
-                nr[3] = __ldg(g.in_ptr + nx + 1);
-            }
-            sp_vertex<R, WITH_S, PRADMM_PIPE_SP != 0, PRADMM_NC != 0, INERT>(g, S, c, pc, pn, i, adz, ctrl, rg);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) rg[k] = nr[k];
-        }
-    } else {
-        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += stride)
-            sp_vertex<R, WITH_S, PRADMM_PIPE_SP != 0, PRADMM_NC != 0, INERT>(g, S, c, pc, pn, i, adz, ctrl);
-    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x)
+        sp_vertex<R, WITH_S, PRADMM_PIPE_SP != 0, PRADMM_NC != 0, INERT>(g, S, c, pc, pn, i, adz, ctrl);
     if (WITH_S) {
         const double sd = block_sum(adz.get(), sh);
         if (threadIdx.x == 0) L.part[SLOT_DZ * L.pstride + blockIdx.x] = sd;
