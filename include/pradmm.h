@@ -202,6 +202,17 @@ pradmm_status pradmm_get_poses(pradmm_t h, double* q_out, double* t_out);
 /* Iterations run since the state was last set. */
 int64_t pradmm_iterations(pradmm_t h);
 
+/* Index-checked builds (libpradmm_debug.so, compiled with
+ * PRADMM_DEBUG_CHECKS): every neighbour index and CSR row bound the plain
+ * sweeps read is range-checked on the device; an out-of-range value is
+ * counted, replaced by 0 so the access stays in bounds, and the run returns
+ * PRADMM_ERR_INDEX.  No counterpart in the paper: a test hook that writes
+ * `value` (in [0, n], where n itself is out of range) into out-edge slot
+ * `slot` of the device CSR, to check that the checks fire.  The release
+ * library returns PRADMM_ERR_STATE.  PRADMM_ERR_ARG for a slot outside [0, m)
+ * or a value outside [0, n]. */
+pradmm_status pradmm_debug_set_neighbour(pradmm_t h, int64_t slot, int32_t value);
+
 /* Per-iteration residual trace (Appendix E.1's e^k in FP64, the value the
  * stopping test of Algorithm 1 reads).  capacity > 0: from now on every
  * iteration the handle runs (step, solve, the reverse mode's recording)

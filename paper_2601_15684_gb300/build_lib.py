@@ -1,8 +1,14 @@
 """In-tree build of libpradmm.so for sm_103a (nvcc + g++, no cmake).
 
-The CUDA translation unit and the host C++ translation unit compile in
+The CUDA translation units and the host C++ translation unit compile in
 parallel; nvcc links them into `paper_2601_15684_gb300/_lib/libpradmm.so`
 with the CUDA runtime linked statically.
+
+build(debug=True) also links `_lib/libpradmm_debug.so`: the plain sweeps and
+the host code recompiled with -DPRADMM_DEBUG_CHECKS=1 (every neighbour index
+and CSR row bound a sweep reads is range-checked on the device and the run
+fails with PRADMM_ERR_INDEX if one is out of range), the other objects
+shared with the release build.
 """
 from __future__ import annotations
 
@@ -18,6 +24,10 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libpradmm.so")
+LIB_DEBUG = os.path.join(LIBDIR, "libpradmm_debug.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+# translation units that carry the index checks of the debug build
+DEBUG_UNITS = ["pradmm_kernels.cu", "pradmm_api.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["pradmm_kernels.cu", "pradmm_batch.cu", "pradmm_batch_inert.cu", "pradmm_adjoint.cu", "pradmm_sigma.cu",
@@ -51,7 +61,7 @@ def _stale(out: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     cuda_inc = os.path.join(_cuda_home(), "include")
@@ -92,13 +102,47 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if errors:
         raise RuntimeError("libpradmm build failed:\n" + "\n".join(errors))
     if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [_nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-cudart", "static", "-lpthread"]
-        r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
-        if r.returncode != 0:
-            raise RuntimeError("libpradmm link failed:\n" + " ".join(cmd) + "\n" + r.stdout)
-        os.replace(tmp, LIB)
+        _link(LIB, objs)
+    if debug:
+        _build_debug(objs, force, cuda_inc)
     return LIB
+
+
+def _link(out: str, objs: list[str]) -> None:
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = [_nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-cudart", "static", "-lpthread"]
+    r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("libpradmm link failed:\n" + " ".join(cmd) + "\n" + r.stdout)
+    os.replace(tmp, out)
+
+
+def _build_debug(release_objs: list[str], force: bool, cuda_inc: str) -> None:
+    os.makedirs(BUILD_DEBUG, exist_ok=True)
+    objs, procs = [], []
+    for o in release_objs:
+        src = os.path.basename(o)[:-2]
+        if src not in DEBUG_UNITS:
+            objs.append(o)
+            continue
+        s = os.path.join(CSRC, src)
+        od = os.path.join(BUILD_DEBUG, os.path.basename(o))
+        objs.append(od)
+        if not (force or _stale(od, [s] + HEADERS)):
+            continue
+        if src.endswith(".cu"):
+            cmd = [_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-DPRADMM_DEBUG_CHECKS=1",
+                   "-I", INCLUDE, "-I", CSRC, "-c", s, "-o", od]
+        else:
+            cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-pthread", "-ffp-contract=off", "-DPRADMM_DEBUG_CHECKS=1",
+                   "-I", INCLUDE, "-I", CSRC, "-I", cuda_inc, "-c", s, "-o", od]
+        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
+    for cmd, p in procs:
+        out, _ = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError("libpradmm debug build failed:\n" + " ".join(cmd) + "\n" + (out or ""))
+    if force or procs or _stale(LIB_DEBUG, objs):
+        _link(LIB_DEBUG, objs)
 
 
 if __name__ == "__main__":

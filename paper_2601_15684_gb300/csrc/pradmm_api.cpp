@@ -74,6 +74,7 @@ struct pradmm_s {
     double* obj_part = nullptr;
     unsigned int* obj_ticket = nullptr;
     double* F_dev = nullptr;
+    unsigned int* dbg_d = nullptr;  // index-checked builds: out-of-range count, last value
     Ctrl* ctrl = nullptr;
     Ctrl* ctrl_h = nullptr;   // pinned mirror
 
@@ -147,6 +148,7 @@ struct pradmm_s {
         g.in_idx = in_idx;
         g.in_te = static_cast<const R*>(in_te);
         g.in_qk = static_cast<const R*>(in_qk);
+        g.dbg = dbg_d;
         return g;
     }
     template <typename R>
@@ -398,6 +400,7 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
     ST(dalloc(h, &h->obj_part, (size_t)std::max(h->obj_grid, h->sms * 4)));
     ST(dalloc(h, &h->obj_ticket, 1));
     ST(dalloc(h, &h->F_dev, 1));
+    ST(dalloc(h, &h->dbg_d, 2));
     ST(dalloc(h, &h->ctrl, 1));
     {
         void* hp = nullptr;
@@ -470,6 +473,7 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
     dev(cudaMemsetAsync(h->zeros, 0, sizeof(double) * 4 * n, st), "memset");
     dev(cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), st), "memset");
     dev(cudaMemsetAsync(h->obj_ticket, 0, sizeof(unsigned int), st), "memset");
+    dev(cudaMemsetAsync(h->dbg_d, 0, 2 * sizeof(unsigned int), st), "memset");
     e = cudaStreamSynchronize(st);
     if (ps == PRADMM_OK && e != cudaSuccess) ps = fail(PRADMM_ERR_CUDA, "set-up: %s", cudaGetErrorString(e));
     cudaFree(tmp);
@@ -772,6 +776,21 @@ pradmm_status ensure_graph(pradmm_s* h, bool record = false) {
     return PRADMM_OK;
 }
 
+#ifndef PRADMM_DEBUG_CHECKS
+#define PRADMM_DEBUG_CHECKS 0
+#endif
+// Index-checked builds: the sweeps count the neighbour indices and row bounds
+// they found out of range (and replaced); a nonzero count is an error.
+pradmm_status check_indices(pradmm_s* h) {
+    if (!PRADMM_DEBUG_CHECKS) return PRADMM_OK;
+    unsigned int d[2] = {0, 0};
+    CU(cudaMemcpy(d, h->dbg_d, sizeof(d), cudaMemcpyDeviceToHost));
+    if (d[0] == 0) return PRADMM_OK;
+    CU(cudaMemset(h->dbg_d, 0, sizeof(d)));
+    return fail(PRADMM_ERR_INDEX, "device index check: %u indices or row bounds out of range (last value %u)", d[0],
+                d[1]);
+}
+
 template <typename R>
 pradmm_status run(pradmm_s* h, long long iters, bool use_tol) {
     if (!h->state_set) return fail(PRADMM_ERR_STATE, "state is not set (pradmm_set_state or pradmm_init_odometry)");
@@ -789,6 +808,7 @@ pradmm_status run(pradmm_s* h, long long iters, bool use_tol) {
         ST(launch_iters_plain<R>(h, iters));
     }
     ST(read_ctrl(h));
+    ST(check_indices(h));
     if (h->ctrl_h->nonfinite) return fail(PRADMM_ERR_NONFINITE, "the iteration produced a non-finite residual");
     return PRADMM_OK;
 }
@@ -1833,6 +1853,15 @@ pradmm_status pradmm_get_state_device(pradmm_t h, double* p, double* q, double* 
 
 pradmm_status pradmm_get_poses(pradmm_t h, double* q_out, double* t_out) {
     return pradmm_get_state(h, q_out, nullptr, t_out, nullptr, nullptr, nullptr);
+}
+
+pradmm_status pradmm_debug_set_neighbour(pradmm_t h, int64_t slot, int32_t value) {
+    if (!h) return fail(PRADMM_ERR_ARG, "NULL handle");
+    if (!PRADMM_DEBUG_CHECKS) return fail(PRADMM_ERR_STATE, "only the index-checked build plants indices");
+    if (slot < 0 || slot >= h->out_slots) return fail(PRADMM_ERR_ARG, "slot outside [0, m)");
+    if (value < 0 || value > h->n) return fail(PRADMM_ERR_ARG, "value outside [0, n]");
+    CU(cudaMemcpy(h->out_idx + slot, &value, sizeof(int32_t), cudaMemcpyHostToDevice));
+    return PRADMM_OK;
 }
 
 pradmm_status pradmm_set_trace(pradmm_t h, int32_t capacity) {

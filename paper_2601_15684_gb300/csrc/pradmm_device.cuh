@@ -84,6 +84,28 @@ __device__ __forceinline__ R4<R> gat(const R* p, int64_t i) {
     else return IO<R>::ld(p, i);
 }
 
+// Index-checked builds (-DPRADMM_DEBUG_CHECKS=1): a neighbour index outside
+// [0, n) or a CSR row bound outside [0, m] read by a sweep is recorded in
+// g.dbg (count and value) and replaced by 0, so the access that follows stays
+// in bounds and the host reports the count as an error after the run.  No
+// trap: the kernel completes.  Release builds compile the check away.
+#ifndef PRADMM_DEBUG_CHECKS
+#define PRADMM_DEBUG_CHECKS 0
+#endif
+template <typename G>
+__device__ __forceinline__ int32_t chk(const G& g, int32_t v, int64_t bound) {
+#if PRADMM_DEBUG_CHECKS
+    if (v < 0 || (int64_t)v >= bound) {
+        atomicAdd(g.dbg, 1u);
+        atomicExch(g.dbg + 1, (unsigned int)v);
+        return 0;
+    }
+#endif
+    (void)g;
+    (void)bound;
+    return v;
+}
+
 template <typename A, typename R>
 __device__ __forceinline__ Q<A> asq(const R4<R>& v) {
     return {A(v.a), A(v.b), A(v.c), A(v.d)};
@@ -246,14 +268,14 @@ __device__ __noinline__ Q<A> p_rhs_serial(const GraphDev<R>& g, const R* t, cons
     const A b1 = A(c.beta1), g1 = A(c.g1);
     Q<A> u = {b1 * qi.w + li.w + g1 * pi.w, b1 * qi.x + li.x + g1 * pi.x, b1 * qi.y + li.y + g1 * pi.y,
               b1 * qi.z + li.z + g1 * pi.z};
-    for (int e = g.out_ptr[i]; e < g.out_ptr[i + 1]; ++e) {
+    for (int e = chk(g, g.out_ptr[i], g.m + 1), e1 = chk(g, g.out_ptr[i + 1], g.m + 1); e < e1; ++e) {
         const R4<R> te = IO<R>::ld(g.out_te, e);
-        const R4<R> tj = IO<R>::ld(t, g.out_idx[e]);
+        const R4<R> tj = IO<R>::ld(t, chk(g, g.out_idx[e], g.n));
         const A rx = A(tj.a) - sx, ry = A(tj.b) - sy, rz = A(tj.c) - sz;
         axpy(u, A(-2) * A(te.d), qmul_pr(qmul_pl(rx, ry, rz, qi), A(te.a), A(te.b), A(te.c)));
     }
-    for (int e = g.in_ptr[i]; e < g.in_ptr[i + 1]; ++e)
-        axpy(u, A(2), qmul(asq<A>(IO<R>::ld(q, g.in_idx[e])), asq<A>(IO<R>::ld(g.in_qk, e))));
+    for (int e = chk(g, g.in_ptr[i], g.m + 1), e1 = chk(g, g.in_ptr[i + 1], g.m + 1); e < e1; ++e)
+        axpy(u, A(2), qmul(asq<A>(IO<R>::ld(q, chk(g, g.in_idx[e], g.n))), asq<A>(IO<R>::ld(g.in_qk, e))));
     return u;
 }
 
@@ -389,9 +411,9 @@ __device__ __forceinline__ void q_vertex(const GraphDev<R>& g, const StateDev<R>
     Q<R> b = {c.beta1 * pi.w - li.w + c.g2 * qa.w, c.beta1 * pi.x - li.x + c.g2 * qa.x,
               c.beta1 * pi.y - li.y + c.g2 * qa.y, c.beta1 * pi.z - li.z + c.g2 * qa.z};
     for_edges2<QEdge<R>, PIPE>(
-        g.out_ptr[i], g.out_ptr[i + 1],
+        chk(g, g.out_ptr[i], g.m + 1), chk(g, g.out_ptr[i + 1], g.m + 1),
         [&](int e, QEdge<R>& x) {
-            x.j = __ldg(g.out_idx + e);
+            x.j = chk(g, __ldg(g.out_idx + e), g.n);
             x.te = IO<R>::ldr(g.out_te, e);
             x.qk = IO<R>::ldr(g.out_qk, e);
         },
@@ -447,9 +469,9 @@ __device__ __forceinline__ void t_vertex(const GraphDev<R>& g, const StateDev<R>
     R ay = c.beta2 * sr.b + zr.b + c.g3 * tay;
     R az = c.beta2 * sr.c + zr.c + c.g3 * taz;
     for_edges2<TEdge<R>, PIPE>(
-        g.in_ptr[i], g.in_ptr[i + 1],
+        chk(g, g.in_ptr[i], g.m + 1), chk(g, g.in_ptr[i + 1], g.m + 1),
         [&](int e, TEdge<R>& x) {
-            x.l = __ldg(g.in_idx + e);
+            x.l = chk(g, __ldg(g.in_idx + e), g.n);
             x.te = IO<R>::ldr(g.in_te, e);
         },
         [&](TEdge<R>& x) {
@@ -514,9 +536,9 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
     R wx = R(0), wy = R(0), wz = R(0);
     Q<R> u = {R(0), R(0), R(0), R(0)};
     for_edges2<SEdge<R>, PIPE>(
-        g.out_ptr[i], g.out_ptr[i + 1],
+        chk(g, g.out_ptr[i], g.m + 1), chk(g, g.out_ptr[i + 1], g.m + 1),
         [&](int e, SEdge<R>& x) {
-            x.j = __ldg(g.out_idx + e);
+            x.j = chk(g, __ldg(g.out_idx + e), g.n);
             x.te = IO<R>::ldr(g.out_te, e);
         },
         [&](SEdge<R>& x) { x.tj = gat<R, NC>(S.t, x.j); },
@@ -575,9 +597,9 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
               c.beta1 * qr.c + lr.c + c.g1 * pa.c, c.beta1 * qr.d + lr.d + c.g1 * pa.d};
     axpy(v, R(1), u);
     for_edges2<PEdge<R>, PIPE>(
-        g.in_ptr[i], g.in_ptr[i + 1],
+        chk(g, g.in_ptr[i], g.m + 1), chk(g, g.in_ptr[i + 1], g.m + 1),
         [&](int e, PEdge<R>& x) {
-            x.l = __ldg(g.in_idx + e);
+            x.l = chk(g, __ldg(g.in_idx + e), g.n);
             x.qk = IO<R>::ldr(g.in_qk, e);
         },
         [&](PEdge<R>& x) { x.ql = gat<R, NC>(S.q, x.l); },

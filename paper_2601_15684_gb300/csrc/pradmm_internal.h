@@ -46,6 +46,9 @@ struct GraphDev {
     const int32_t* in_idx;   // m: tail l (internal id) of each in-edge
     const R* in_te;          // 4m: (t_e x, y, z, omega_e)
     const R* in_qk;          // 4m: kappa_e q_e
+    // index-checked builds (PRADMM_DEBUG_CHECKS): [0] indices found out of
+    // range, [1] the last such value (device memory; unused otherwise)
+    unsigned int* dbg = nullptr;
 };
 
 // Pose / multiplier state in internal vertex order.  p is double buffered:

@@ -77,6 +77,7 @@ _SIGS = {
     "pradmm_get_poses": (ctypes.c_int, [_h, _d, _d]),
     "pradmm_iterations": (ctypes.c_int64, [_h]),
     "pradmm_set_trace": (ctypes.c_int, [_h, ctypes.c_int32]),
+    "pradmm_debug_set_neighbour": (ctypes.c_int, [_h, ctypes.c_int64, ctypes.c_int32]),
     "pradmm_get_trace": (ctypes.c_int, [_h, _d, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
     "pradmm_counters": (ctypes.c_int, [_h, _i64]),
     "pradmm_bytes_per_iteration": (ctypes.c_int, [_h, _d]),
@@ -260,6 +261,10 @@ def pradmm_get_poses(h, n, q_out=None, t_out=None):
 
 def pradmm_iterations(h) -> int:
     return int(load().pradmm_iterations(h))
+
+
+def pradmm_debug_set_neighbour(h, slot: int, value: int):
+    _check(load().pradmm_debug_set_neighbour(h, int(slot), int(value)), "pradmm_debug_set_neighbour")
 
 
 def pradmm_set_trace(h, capacity: int):
