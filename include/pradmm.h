@@ -250,6 +250,12 @@ pradmm_status pradmm_l2_window_info(pradmm_t h, double* out);
  * iteration time.  The state advances by `iters` iterations. */
 pradmm_status pradmm_profile_sweeps(pradmm_t h, int32_t iters, double* ms_out);
 
+/* The same launches, every iteration's durations kept: per_iter_ms (host,
+ * 4 x iters, row k for the k-th profiled iteration) receives the q/lambda,
+ * t and s/z+p kernel times and the iteration time (ms).  The state advances
+ * by `iters` iterations. */
+pradmm_status pradmm_profile_iterations(pradmm_t h, int32_t iters, double* per_iter_ms);
+
 /* General weight matrices (Lemma 1, Algorithm 1's branch for non-scalar
  * Sigma): edge e weighs its translation residual with omega_e Sigma1 and its
  * rotation residual with kappa_e Sigma2, Sigma1 and Sigma2 symmetric positive

@@ -928,7 +928,7 @@ pradmm_status get_state_impl(pradmm_s* h, double* p, double* q, double* t, doubl
 }
 
 template <typename R>
-pradmm_status profile_impl(pradmm_s* h, int32_t iters, double* ms_out) {
+pradmm_status profile_impl(pradmm_s* h, int32_t iters, double* ms_out, double* per_iter = nullptr) {
     if (!h->state_set) return fail(PRADMM_ERR_STATE, "state is not set");
     if (h->general) return fail(PRADMM_ERR_STATE, "the per-sweep profile covers the scalar-Sigma sweeps");
     if (iters < 1) return fail(PRADMM_ERR_ARG, "iters must be >= 1");
@@ -973,8 +973,15 @@ pradmm_status profile_impl(pradmm_s* h, int32_t iters, double* ms_out) {
             acc[1] += b;
             acc[2] += cc;
             acc[3] += d;
+            if (per_iter) {
+                per_iter[4 * (size_t)k] = a;
+                per_iter[4 * (size_t)k + 1] = b;
+                per_iter[4 * (size_t)k + 2] = cc;
+                per_iter[4 * (size_t)k + 3] = d;
+            }
         }
-        for (int j = 0; j < 4; ++j) ms_out[j] = acc[j] / iters;
+        if (ms_out)
+            for (int j = 0; j < 4; ++j) ms_out[j] = acc[j] / iters;
     }
     for (auto& e : ev) cudaEventDestroy(e);
     if (st == PRADMM_OK) st = read_ctrl(h);
@@ -1948,6 +1955,12 @@ pradmm_status pradmm_l2_window_info(pradmm_t h, double* out) {
 pradmm_status pradmm_profile_sweeps(pradmm_t h, int32_t iters, double* ms_out) {
     if (!h || !ms_out) return fail(PRADMM_ERR_ARG, "NULL argument");
     return h->fp64 ? profile_impl<double>(h, iters, ms_out) : profile_impl<float>(h, iters, ms_out);
+}
+
+pradmm_status pradmm_profile_iterations(pradmm_t h, int32_t iters, double* per_iter_ms) {
+    if (!h || !per_iter_ms) return fail(PRADMM_ERR_ARG, "NULL argument");
+    return h->fp64 ? profile_impl<double>(h, iters, nullptr, per_iter_ms)
+                   : profile_impl<float>(h, iters, nullptr, per_iter_ms);
 }
 
 void pradmm_destroy(pradmm_t h) {

@@ -77,6 +77,7 @@ _SIGS = {
     "pradmm_get_poses": (ctypes.c_int, [_h, _d, _d]),
     "pradmm_iterations": (ctypes.c_int64, [_h]),
     "pradmm_set_trace": (ctypes.c_int, [_h, ctypes.c_int32]),
+    "pradmm_profile_iterations": (ctypes.c_int, [_h, ctypes.c_int32, _d]),
     "pradmm_debug_set_neighbour": (ctypes.c_int, [_h, ctypes.c_int64, ctypes.c_int32]),
     "pradmm_get_trace": (ctypes.c_int, [_h, _d, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
     "pradmm_counters": (ctypes.c_int, [_h, _i64]),
@@ -265,6 +266,13 @@ def pradmm_iterations(h) -> int:
 
 def pradmm_debug_set_neighbour(h, slot: int, value: int):
     _check(load().pradmm_debug_set_neighbour(h, int(slot), int(value)), "pradmm_debug_set_neighbour")
+
+
+def pradmm_profile_iterations(h, iters: int):
+    """(iters x 4) ms: q/lambda, t, s/z+p kernel and iteration time of each iteration."""
+    out = np.zeros((int(iters), 4))
+    _check(load().pradmm_profile_iterations(h, int(iters), _dp(out)), "pradmm_profile_iterations")
+    return out
 
 
 def pradmm_set_trace(h, capacity: int):
