@@ -818,19 +818,6 @@ pradmm_status run_any(pradmm_s* h, long long iters, bool use_tol) {
 }
 
 // ---- odometry initialisation (host): spanning forest by edge order --------
-struct UF {
-    std::vector<int64_t> par;
-    explicit UF(int64_t n) : par(n) {
-        for (int64_t i = 0; i < n; ++i) par[i] = i;
-    }
-    int64_t find(int64_t x) {
-        while (par[x] != x) {
-            par[x] = par[par[x]];
-            x = par[x];
-        }
-        return x;
-    }
-};
 
 // Spanning forest by edge order (Kruskal: an edge joins the forest when it
 // links two components; the scan stops once one tree spans every vertex),
@@ -841,54 +828,67 @@ struct UF {
 // rounds the deepest vertex needs, ceil(log2(depth + 1)).
 void odometry_forest(const pradmm_s* h, std::vector<int32_t>& par, std::vector<int32_t>& pedge, int& rounds) {
     const int64_t n = h->n, m = h->m;
-    UF uf(n);
-    std::vector<int32_t> tree;
-    tree.reserve(n);
+    // Kruskal by edge order (union-find with path halving; the lower root wins)
+    std::vector<int32_t> uf(n), tree;
+    for (int64_t i = 0; i < n; ++i) uf[i] = (int32_t)i;
+    auto find = [&](int32_t x) {
+        while (uf[x] != x) {
+            uf[x] = uf[uf[x]];
+            x = uf[x];
+        }
+        return x;
+    };
+    tree.reserve(n > 0 ? n - 1 : 0);
     for (int64_t e = 0; e < m && (int64_t)tree.size() < n - 1; ++e) {
-        const int64_t a = uf.find(h->src[e]), b = uf.find(h->dst[e]);
+        const int32_t a = find(h->src[e]), b = find(h->dst[e]);
         if (a == b) continue;
-        if (a < b) uf.par[b] = a; else uf.par[a] = b;
+        if (a < b) uf[b] = a; else uf[a] = b;
         tree.push_back((int32_t)e);
     }
-    std::vector<int64_t> ptr(n + 1, 0);
+    // tree adjacency (each tree edge listed at both endpoints), int32 CSR;
+    // uf's storage is reused for the row offsets' fill cursor
+    std::vector<int32_t> ptr(n + 1, 0), adj(2 * tree.size());
     for (int32_t e : tree) {
         ptr[h->src[e] + 1]++;
         ptr[h->dst[e] + 1]++;
     }
     for (int64_t i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
-    std::vector<int32_t> adj(2 * tree.size());
-    std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+    std::vector<int32_t>& cur = uf;
+    std::copy(ptr.begin(), ptr.end() - 1, cur.begin());
     for (int32_t e : tree) {
-        adj[fill[h->src[e]]++] = e;
-        adj[fill[h->dst[e]]++] = e;
+        adj[cur[h->src[e]]++] = e;
+        adj[cur[h->dst[e]]++] = e;
     }
+    // breadth-first from the lowest vertex of each component, level by level
+    // (the deepest level gives the pointer-jumping rounds)
     par.assign(n, -1);
     pedge.assign(n, -1);
-    std::vector<int32_t> depth(n, 0);
     std::vector<char> seen(n, 0);
-    std::vector<int64_t> queue;
-    queue.reserve(n);
-    int32_t dmax = 0;
+    std::vector<int32_t>& queue = cur;  // the fill cursor is no longer needed
+    int64_t dmax = 0;
     for (int64_t r = 0; r < n; ++r) {
         if (seen[r]) continue;
         seen[r] = 1;
-        queue.clear();
-        queue.push_back(r);
-        for (size_t head = 0; head < queue.size(); ++head) {
-            const int64_t v = queue[head];
-            for (int64_t k = ptr[v]; k < ptr[v + 1]; ++k) {
+        int64_t head = 0, tail = 0, level_end = 1, depth = 0;
+        queue[tail++] = (int32_t)r;
+        while (head < tail) {
+            const int32_t v = queue[head++];
+            for (int32_t k = ptr[v]; k < ptr[v + 1]; ++k) {
                 const int32_t e = adj[k];
-                const int64_t a = h->src[e], b = h->dst[e];
-                const int64_t w = a == v ? b : a;
+                const int32_t a = h->src[e], b = h->dst[e];
+                const int32_t w = a == v ? b : a;
                 if (seen[w]) continue;
                 seen[w] = 1;
-                par[w] = (int32_t)v;
+                par[w] = v;
                 pedge[w] = w == a ? -(e + 2) : e;
-                depth[w] = depth[v] + 1;
-                dmax = std::max(dmax, depth[w]);
-                queue.push_back(w);
+                queue[tail++] = w;
+            }
+            if (head == level_end && head < tail) {
+                ++depth;
+                level_end = tail;
             }
         }
+        dmax = std::max(dmax, depth);
     }
     rounds = 0;
     while (((int64_t)1 << rounds) <= dmax) ++rounds;
