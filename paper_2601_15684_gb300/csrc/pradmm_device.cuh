@@ -317,40 +317,16 @@ __device__ __forceinline__ void p_normalise(const GraphDev<R>& g, const StateDev
 #define PRADMM_UNROLL 2
 #endif
 constexpr int kUnroll = PRADMM_UNROLL;
-// edges per group in the s/z + p sweep's out- and in-edge passes
-#ifndef PRADMM_UNROLL_SP_OUT
-#define PRADMM_UNROLL_SP_OUT PRADMM_UNROLL
-#endif
-#ifndef PRADMM_UNROLL_SP_IN
-#define PRADMM_UNROLL_SP_IN PRADMM_UNROLL
-#endif
-constexpr int kUnrollSpOut = PRADMM_UNROLL_SP_OUT;
-constexpr int kUnrollSpIn = PRADMM_UNROLL_SP_IN;
 
-template <typename T, int U = kUnroll, typename LoadF, typename UseF>
+template <typename T, typename LoadF, typename UseF>
 __device__ __forceinline__ void for_edges(int e0, int e1, LoadF load, UseF use) {
-    if constexpr (U > 2) {
-        // groups of up to U edges, the last one partial (its loads predicated),
-        // so a vertex of degree d <= U waits for one load level per pass
-        for (int e = e0; e < e1; e += U) {
-            const int cnt = e1 - e < U ? e1 - e : U;
-            T b[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (u < cnt) load(e + u, b[u]);
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (u < cnt) use(b[u]);
-        }
-        return;
-    }
     int e = e0;
-    for (; e + U <= e1; e += U) {
-        T b[U];
+    for (; e + kUnroll <= e1; e += kUnroll) {
+        T b[kUnroll];
 #pragma unroll
-        for (int u = 0; u < U; ++u) load(e + u, b[u]);
+        for (int u = 0; u < kUnroll; ++u) load(e + u, b[u]);
 #pragma unroll
-        for (int u = 0; u < U; ++u) use(b[u]);
+        for (int u = 0; u < kUnroll; ++u) use(b[u]);
     }
     for (; e < e1; ++e) {
         T b0;
@@ -367,10 +343,10 @@ __device__ __forceinline__ void for_edges(int e0, int e1, LoadF load, UseF use) 
 // kernel has registers to spare (measured: the plain t sweep).  Uses run in
 // edge order either way; rounding can differ where the compiler contracts
 // multiply-adds differently.
-template <typename T, bool PIPE, int U = kUnroll, typename LoadA, typename LoadB, typename UseF>
+template <typename T, bool PIPE, typename LoadA, typename LoadB, typename UseF>
 __device__ __forceinline__ void for_edges2(int e0, int e1, LoadA load_a, LoadB load_b, UseF use) {
     if (!PIPE) {
-        for_edges<T, U>(
+        for_edges<T>(
             e0, e1,
             [&](int e, T& x) {
                 load_a(e, x);
@@ -380,28 +356,28 @@ __device__ __forceinline__ void for_edges2(int e0, int e1, LoadA load_a, LoadB l
         return;
     }
     if (e0 >= e1) return;
-    T a[U];
-    int cnt = e1 - e0 < U ? e1 - e0 : U;
+    T a[kUnroll];
+    int cnt = e1 - e0 < kUnroll ? e1 - e0 : kUnroll;
 #pragma unroll
-    for (int u = 0; u < U; ++u)
+    for (int u = 0; u < kUnroll; ++u)
         if (u < cnt) load_a(e0 + u, a[u]);
     int e = e0;
     for (;;) {
 #pragma unroll
-        for (int u = 0; u < U; ++u)
+        for (int u = 0; u < kUnroll; ++u)
             if (u < cnt) load_b(a[u]);
         const int en = e + cnt;
-        const int cn = e1 - en < U ? e1 - en : U;
-        T nx[U];
+        const int cn = e1 - en < kUnroll ? e1 - en : kUnroll;
+        T nx[kUnroll];
 #pragma unroll
-        for (int u = 0; u < U; ++u)
+        for (int u = 0; u < kUnroll; ++u)
             if (u < cn) load_a(en + u, nx[u]);
 #pragma unroll
-        for (int u = 0; u < U; ++u)
+        for (int u = 0; u < kUnroll; ++u)
             if (u < cnt) use(a[u]);
         if (cn <= 0) break;
 #pragma unroll
-        for (int u = 0; u < U; ++u) a[u] = nx[u];
+        for (int u = 0; u < kUnroll; ++u) a[u] = nx[u];
         e = en;
         cnt = cn;
     }
@@ -559,7 +535,7 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
     R ax = R(0), ay = R(0), az = R(0);
     R wx = R(0), wy = R(0), wz = R(0);
     Q<R> u = {R(0), R(0), R(0), R(0)};
-    for_edges2<SEdge<R>, PIPE, kUnrollSpOut>(
+    for_edges2<SEdge<R>, PIPE>(
         chk(g, g.out_ptr[i], g.m + 1), chk(g, g.out_ptr[i + 1], g.m + 1),
         [&](int e, SEdge<R>& x) {
             x.j = chk(g, __ldg(g.out_idx + e), g.n);
@@ -620,7 +596,7 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
     Q<R> v = {c.beta1 * qr.a + lr.a + c.g1 * pa.a, c.beta1 * qr.b + lr.b + c.g1 * pa.b,
               c.beta1 * qr.c + lr.c + c.g1 * pa.c, c.beta1 * qr.d + lr.d + c.g1 * pa.d};
     axpy(v, R(1), u);
-    for_edges2<PEdge<R>, PIPE, kUnrollSpIn>(
+    for_edges2<PEdge<R>, PIPE>(
         chk(g, g.in_ptr[i], g.m + 1), chk(g, g.in_ptr[i + 1], g.m + 1),
         [&](int e, PEdge<R>& x) {
             x.l = chk(g, __ldg(g.in_idx + e), g.n);
