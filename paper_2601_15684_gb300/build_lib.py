@@ -31,7 +31,7 @@ DEBUG_UNITS = ["pradmm_kernels.cu", "pradmm_api.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["pradmm_kernels.cu", "pradmm_batch.cu", "pradmm_batch_inert.cu", "pradmm_adjoint.cu", "pradmm_sigma.cu",
-              "pradmm_noalloc.cu", "pradmm_setup.cu"]
+              "pradmm_noalloc.cu", "pradmm_setup.cu", "pradmm_forest.cu"]
 # sources compiled once per set of defines (object name suffix, defines): the
 # batched general-Sigma kernels, one object per precision and inertial flag
 CU_SPLIT = {"pradmm_batch_sigma.cu": [(f"{r}{'_inert' if i else ''}",

@@ -58,9 +58,6 @@ struct pradmm_s {
     int pstride = 1, block = 256, obj_grid = 1, sms = 1;
     int64_t out_slots = 0, in_slots = 0;  // edges per order (= m)
 
-    // the caller's edge endpoints (input order), for the odometry start's spanning forest
-    std::vector<int32_t> src, dst;
-
     std::vector<void*> allocs;
     int32_t *out_ptr = nullptr, *in_ptr = nullptr, *out_idx = nullptr, *in_idx = nullptr;
     int32_t* perm_d = nullptr;  // internal vertex -> user vertex
@@ -322,18 +319,12 @@ pradmm_status check_edge(int64_t n, int64_t e, const int32_t* src, const int32_t
 pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const double* q_meas, const double* t_meas,
                     const double* kappa, const double* omega) {
     const int64_t n = h->n, m = h->m;
-    // ---- validation (never trust the caller's graph), in parallel host threads;
-    // the endpoints are kept for the odometry start.  The first failing edge is
-    // re-checked on this thread for its message ----
-    h->src.resize(m);
-    h->dst.resize(m);
+    // ---- validation (never trust the caller's graph), in parallel host
+    // threads.  The first failing edge is re-checked on this thread for its
+    // message ----
     std::mutex bad_mu;
     int64_t bad = m;
     parallel_for(m, [&](int64_t e0, int64_t e1) {
-        if (e1 > e0) {
-            std::memcpy(h->src.data() + e0, src + e0, sizeof(int32_t) * (e1 - e0));
-            std::memcpy(h->dst.data() + e0, dst + e0, sizeof(int32_t) * (e1 - e0));
-        }
         for (int64_t e = e0; e < e1; ++e) {
             bool ok = src[e] >= 0 && src[e] < n && dst[e] >= 0 && dst[e] < n && src[e] != dst[e];
             const double k_e = kappa ? kappa[e] : 1.0, w_e = omega ? omega[e] : 1.0;
@@ -815,83 +806,6 @@ pradmm_status run(pradmm_s* h, long long iters, bool use_tol) {
 
 pradmm_status run_any(pradmm_s* h, long long iters, bool use_tol) {
     return h->fp64 ? run<double>(h, iters, use_tol) : run<float>(h, iters, use_tol);
-}
-
-// ---- odometry initialisation (host): spanning forest by edge order --------
-
-// Spanning forest by edge order (Kruskal: an edge joins the forest when it
-// links two components; the scan stops once one tree spans every vertex),
-// rooted at the lowest vertex of each component by a breadth-first walk.
-// Per vertex: its parent (-1 for a root) and the tree edge e to it, coded e
-// when the vertex is the edge's head and -(e + 2) when it is its tail (-1 for
-// a root); `rounds` = the pointer-jumping
-// rounds the deepest vertex needs, ceil(log2(depth + 1)).
-void odometry_forest(const pradmm_s* h, std::vector<int32_t>& par, std::vector<int32_t>& pedge, int& rounds) {
-    const int64_t n = h->n, m = h->m;
-    // Kruskal by edge order (union-find with path halving; the lower root wins)
-    std::vector<int32_t> uf(n), tree;
-    for (int64_t i = 0; i < n; ++i) uf[i] = (int32_t)i;
-    auto find = [&](int32_t x) {
-        while (uf[x] != x) {
-            uf[x] = uf[uf[x]];
-            x = uf[x];
-        }
-        return x;
-    };
-    tree.reserve(n > 0 ? n - 1 : 0);
-    for (int64_t e = 0; e < m && (int64_t)tree.size() < n - 1; ++e) {
-        const int32_t a = find(h->src[e]), b = find(h->dst[e]);
-        if (a == b) continue;
-        if (a < b) uf[b] = a; else uf[a] = b;
-        tree.push_back((int32_t)e);
-    }
-    // tree adjacency (each tree edge listed at both endpoints), int32 CSR;
-    // uf's storage is reused for the row offsets' fill cursor
-    std::vector<int32_t> ptr(n + 1, 0), adj(2 * tree.size());
-    for (int32_t e : tree) {
-        ptr[h->src[e] + 1]++;
-        ptr[h->dst[e] + 1]++;
-    }
-    for (int64_t i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
-    std::vector<int32_t>& cur = uf;
-    std::copy(ptr.begin(), ptr.end() - 1, cur.begin());
-    for (int32_t e : tree) {
-        adj[cur[h->src[e]]++] = e;
-        adj[cur[h->dst[e]]++] = e;
-    }
-    // breadth-first from the lowest vertex of each component, level by level
-    // (the deepest level gives the pointer-jumping rounds)
-    par.assign(n, -1);
-    pedge.assign(n, -1);
-    std::vector<char> seen(n, 0);
-    std::vector<int32_t>& queue = cur;  // the fill cursor is no longer needed
-    int64_t dmax = 0;
-    for (int64_t r = 0; r < n; ++r) {
-        if (seen[r]) continue;
-        seen[r] = 1;
-        int64_t head = 0, tail = 0, level_end = 1, depth = 0;
-        queue[tail++] = (int32_t)r;
-        while (head < tail) {
-            const int32_t v = queue[head++];
-            for (int32_t k = ptr[v]; k < ptr[v + 1]; ++k) {
-                const int32_t e = adj[k];
-                const int32_t a = h->src[e], b = h->dst[e];
-                const int32_t w = a == v ? b : a;
-                if (seen[w]) continue;
-                seen[w] = 1;
-                par[w] = v;
-                pedge[w] = w == a ? -(e + 2) : e;
-                queue[tail++] = w;
-            }
-            if (head == level_end && head < tail) {
-                ++depth;
-                level_end = tail;
-            }
-        }
-        dmax = std::max(dmax, depth);
-    }
-    rounds = 0;
-    while (((int64_t)1 << rounds) <= dmax) ++rounds;
 }
 
 template <typename R>
@@ -1726,19 +1640,17 @@ pradmm_status pradmm_autotune(pradmm_t h, int32_t iters, int32_t* block_out) {
     return PRADMM_OK;
 }
 
+// ---- odometry initialisation --------------------------------------------
+// The spanning forest by edge order (an edge joins when it links two
+// components), rooted at each component's lowest vertex, and the poses
+// composed along its paths: all on the device (pradmm_forest.cu, the
+// composition in pradmm_setup.cu), from the out-edge CSR.
 pradmm_status pradmm_init_odometry(pradmm_t h) {
     if (!h) return fail(PRADMM_ERR_ARG, "NULL handle");
-    std::vector<int32_t> par, pedge;
-    int rounds = 0;
-    try {
-        odometry_forest(h, par, pedge, rounds);
-    } catch (const std::bad_alloc&) {
-        return fail(PRADMM_ERR_NOMEM, "host allocation failed");
-    }
-    // the compositions along the tree paths on the device (pointer jumping)
-    const int64_t n = h->n;
+    const int64_t n = h->n, m = h->m;
+    const size_t fs = pradmm::forest_scratch_ints(n, m);
+    const size_t bytes = (size_t)n * 14 * sizeof(double) + ((size_t)3 * n + 1 + fs) * sizeof(int32_t) + 64;
     char* tmp = nullptr;
-    const size_t bytes = (size_t)n * (3 * sizeof(int32_t) + 14 * sizeof(double)) + 64;
     cudaError_t e = cudaMalloc(&tmp, bytes);
     if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? PRADMM_ERR_NOMEM : PRADMM_ERR_CUDA,
                                       "odometry buffer of %zu bytes: %s", bytes, cudaGetErrorString(e));
@@ -1749,12 +1661,16 @@ pradmm_status pradmm_init_odometry(pradmm_t h) {
     int32_t* pe_d = reinterpret_cast<int32_t*>(t2 + 3 * n);
     int32_t* par_d = pe_d + n;
     int32_t* par2 = par_d + n;
+    int32_t* flag = par2 + n;
+    int32_t* scratch = flag + 1;
+    int max_rounds = 1;
+    while (((int64_t)1 << max_rounds) <= n) ++max_rounds;
     cudaStream_t st = h->stream;
     pradmm_status ps = PRADMM_OK;
-    if ((e = cudaMemcpyAsync(pe_d, pedge.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(par_d, par.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = pradmm::launch_odometry(pe_d, par_d, rounds, h->edge_slot_d, h->qe64, h->te64, n, par2, q, t, q2, t2,
-                                     st)) != cudaSuccess)
+    if ((e = pradmm::launch_forest(h->out_ptr, h->out_idx, h->out_edge_d, n, m, scratch, par_d, pe_d, st)) !=
+            cudaSuccess ||
+        (e = pradmm::launch_odometry(pe_d, par_d, max_rounds, flag, h->edge_slot_d, h->qe64, h->te64, n, par2, q, t,
+                                     q2, t2, st)) != cudaSuccess)
         ps = fail(PRADMM_ERR_CUDA, "odometry: %s", cudaGetErrorString(e));
     if (ps == PRADMM_OK) ps = set_state_any(h, q, q, t, t, nullptr, nullptr, true);
     e = cudaStreamSynchronize(st);

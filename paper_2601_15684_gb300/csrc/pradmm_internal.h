@@ -116,6 +116,18 @@ cudaError_t sweep_occupancy(int is_double, int block, int* bps);
 cudaError_t build_csr_device(const int32_t* key, const int32_t* other, int64_t n, int64_t m, int32_t* ptr,
                              int32_t* slot_edge, int32_t* idx, int32_t* edge_slot, int32_t* fill, int32_t* sums,
                              cudaStream_t st);
+// Inclusive scan of a[0, len) in place; sums holds (len + 1023) / 1024 ints.
+cudaError_t inclusive_scan_i32(int32_t* a, int64_t len, int32_t* sums, cudaStream_t st);
+// The odometry start's spanning forest (Kruskal by edge order, found by
+// Boruvka's rounds) rooted at each component's lowest vertex
+// (pradmm_forest.cu), from the out-edge CSR (out_ptr, out_idx: heads,
+// out_edge: input edge per slot): par[v] the parent (-1 for a root), pedge[v]
+// the tree edge e to it coded as for launch_odometry.  scratch:
+// forest_scratch_ints(n, m) ints.  Synchronises the stream (host reads of
+// the round counts).
+size_t forest_scratch_ints(int64_t n, int64_t m);
+cudaError_t launch_forest(const int32_t* out_ptr, const int32_t* out_idx, const int32_t* out_edge, int64_t n,
+                          int64_t m, int32_t* scratch, int32_t* par, int32_t* pedge, cudaStream_t st);
 cudaError_t launch_block_inv(const int32_t* out_ptr, const int32_t* out_edge, const int32_t* in_ptr,
                              const int32_t* in_edge, int64_t n, const double* t, const double* ka, const double* om,
                              double a2_0, double a3_0, double a4_0, double* inv2, double* inv3, double* inv4,
@@ -125,10 +137,13 @@ cudaError_t launch_slot_owner(const int32_t* ptr, int64_t n, int32_t* owner, cud
 // Odometry poses from the spanning forest: pedge[v] = e when v is the head of
 // its tree edge e, -(e + 2) when v is its tail, -1 for a root; par[v] the
 // parent (-1 for a root), overwritten; the
-// poses end in q (4n), t (3n); par_tmp, q_tmp, t_tmp are scratch.
-cudaError_t launch_odometry(const int32_t* pedge, const int32_t* par, int rounds, const int32_t* edge_slot,
-                            const double* qe64, const double* te64, int64_t n, int32_t* par_tmp, double* q,
-                            double* t, double* q_tmp, double* t_tmp, cudaStream_t st);
+// poses end in q (4n), t (3n); par_tmp, q_tmp, t_tmp are scratch.  The
+// pointer-jumping rounds run in pairs until no vertex has a parent left
+// (*flag, one device int, read back after each pair: synchronises the
+// stream), at most max_rounds (rounded up to even).
+cudaError_t launch_odometry(const int32_t* pedge, const int32_t* par, int max_rounds, int32_t* flag,
+                            const int32_t* edge_slot, const double* qe64, const double* te64, int64_t n,
+                            int32_t* par_tmp, double* q, double* t, double* q_tmp, double* t_tmp, cudaStream_t st);
 
 // Device-side parameters of a tape recording (reverse mode): after the
 // iteration that brings ctrl->iter to k0 + d, with d a multiple of C or

@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(256) k_slot_owner(const int32_t* __restrict__ 
 }
 
 // ---- odometry composition on the device -----------------------------------
-// The spanning forest (host) gives every vertex its parent and the tree edge
+// The spanning forest (pradmm_forest.cu) gives every vertex its parent and the tree edge
 // to it; the pose of a vertex is the composition of the SE(3) steps along the
 // tree path from its component's root, T_v = T_parent o T_step with
 // (q_a, t_a) o (q_b, t_b) = (q_a q_b, t_a + R(q_a) t_b).  Pointer jumping
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(256) k_odo_steps(const int32_t* __restrict__ p
 
 __global__ void __launch_bounds__(256) k_odo_jump(const int32_t* __restrict__ par_in, const double* __restrict__ q_in,
                                                   const double* __restrict__ t_in, int64_t n, int32_t* par_out,
-                                                  double* q_out, double* t_out) {
+                                                  double* q_out, double* t_out, int32_t* more) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const int32_t p = par_in[v];
         double qv[4], tv[3];
@@ -293,7 +293,9 @@ __global__ void __launch_bounds__(256) k_odo_jump(const int32_t* __restrict__ pa
             hq_rot(qp, tv, r);
             for (int c = 0; c < 4; ++c) qv[c] = qn[c];
             for (int c = 0; c < 3; ++c) tv[c] = tp[c] + r[c];
-            par_out[v] = par_in[p];
+            const int32_t pp = par_in[p];
+            par_out[v] = pp;
+            if (more && pp >= 0) *more = 1;
         } else {
             par_out[v] = p;
         }
@@ -309,6 +311,15 @@ inline int grid_of(int64_t work) {
 
 }  // namespace
 
+cudaError_t inclusive_scan_i32(int32_t* a, int64_t len, int32_t* sums, cudaStream_t st) {
+    if (len <= 0) return cudaSuccess;
+    const int64_t nb = (len + kScanBlock - 1) / kScanBlock;
+    k_scan_blocks<<<(unsigned)nb, 256, 0, st>>>(a, len, sums);
+    k_scan_sums<<<1, 256, 0, st>>>(sums, nb);
+    k_scan_add<<<(unsigned)nb, 256, 0, st>>>(a, len, sums);
+    return cudaGetLastError();
+}
+
 cudaError_t build_csr_device(const int32_t* key, const int32_t* other, int64_t n, int64_t m, int32_t* ptr,
                              int32_t* slot_edge, int32_t* idx, int32_t* edge_slot, int32_t* fill, int32_t* sums,
                              cudaStream_t st) {
@@ -316,10 +327,7 @@ cudaError_t build_csr_device(const int32_t* key, const int32_t* other, int64_t n
     if ((e = cudaMemsetAsync(ptr, 0, sizeof(int32_t) * (n + 1), st))) return e;
     if ((e = cudaMemsetAsync(fill, 0, sizeof(int32_t) * n, st))) return e;
     if (m > 0) k_degree<<<grid_of(m), 256, 0, st>>>(key, m, ptr + 1);
-    const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
-    k_scan_blocks<<<(unsigned)nb, 256, 0, st>>>(ptr + 1, n, sums);
-    k_scan_sums<<<1, 256, 0, st>>>(sums, nb);
-    k_scan_add<<<(unsigned)nb, 256, 0, st>>>(ptr + 1, n, sums);
+    if ((e = inclusive_scan_i32(ptr + 1, n, sums, st))) return e;
     if (m > 0) {
         k_place<<<grid_of(m), 256, 0, st>>>(key, m, ptr, fill, slot_edge);
         k_sort_rows<<<grid_of(n), 256, 0, st>>>(ptr, n, slot_edge);
@@ -347,23 +355,22 @@ cudaError_t launch_slot_owner(const int32_t* ptr, int64_t n, int32_t* owner, cud
     return cudaGetLastError();
 }
 
-cudaError_t launch_odometry(const int32_t* pedge, const int32_t* par, int rounds, const int32_t* edge_slot,
-                            const double* qe64, const double* te64, int64_t n, int32_t* par_tmp, double* q,
-                            double* t, double* q_tmp, double* t_tmp, cudaStream_t st) {
+cudaError_t launch_odometry(const int32_t* pedge, const int32_t* par, int max_rounds, int32_t* flag,
+                            const int32_t* edge_slot, const double* qe64, const double* te64, int64_t n,
+                            int32_t* par_tmp, double* q, double* t, double* q_tmp, double* t_tmp, cudaStream_t st) {
+    cudaError_t e;
     k_odo_steps<<<grid_of(n), 256, 0, st>>>(pedge, edge_slot, qe64, te64, n, q, t);
-    const int32_t* pi = par;
-    int32_t* bufs_p[2] = {par_tmp, const_cast<int32_t*>(par)};
-    double* bufs_q[2] = {q_tmp, q};
-    double* bufs_t[2] = {t_tmp, t};
-    const double* qi = q;
-    const double* ti = t;
-    // rounds alternate between the two buffers; an even count ends in q, t
-    const int r_all = rounds + (rounds & 1);
-    for (int r = 0; r < r_all; ++r) {
-        k_odo_jump<<<grid_of(n), 256, 0, st>>>(pi, qi, ti, n, bufs_p[r & 1], bufs_q[r & 1], bufs_t[r & 1]);
-        pi = bufs_p[r & 1];
-        qi = bufs_q[r & 1];
-        ti = bufs_t[r & 1];
+    // rounds in pairs (par_tmp, q_tmp, t_tmp then back into par, q, t);
+    // the second of a pair raises *flag while a parent is left
+    int32_t* par_w = const_cast<int32_t*>(par);
+    for (int r = 0; r < max_rounds; r += 2) {
+        if ((e = cudaMemsetAsync(flag, 0, sizeof(int32_t), st))) return e;
+        k_odo_jump<<<grid_of(n), 256, 0, st>>>(par_w, q, t, n, par_tmp, q_tmp, t_tmp, nullptr);
+        k_odo_jump<<<grid_of(n), 256, 0, st>>>(par_tmp, q_tmp, t_tmp, n, par_w, q, t, flag);
+        int32_t more = 0;
+        if ((e = cudaMemcpyAsync(&more, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st))) return e;
+        if ((e = cudaStreamSynchronize(st))) return e;
+        if (!more) break;
     }
     return cudaGetLastError();
 }
