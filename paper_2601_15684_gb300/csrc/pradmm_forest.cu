@@ -99,8 +99,17 @@ __global__ void __launch_bounds__(256) k_relabel(int32_t* comp, int64_t n, const
     GRID_STRIDE(v, n) comp[v] = hook[comp[v]];
 }
 
+// lowest[c] = the lowest vertex of component c.  One big component would
+// put every vertex's atomic on one word: the lanes of a warp that share a
+// label send only their lowest vertex (the first such lane: v grows with
+// the lane), and only while the word holds a higher one.
 __global__ void __launch_bounds__(256) k_lowest(const int32_t* __restrict__ comp, int64_t n, int32_t* lowest) {
-    GRID_STRIDE(v, n) atomicMin(lowest + comp[v], (int32_t)v);
+    GRID_STRIDE(v, n) {
+        const int32_t c = comp[v];
+        const unsigned same = __match_any_sync(__activemask(), c);
+        if ((int)(threadIdx.x & 31) == __ffs(same) - 1 && *((volatile int32_t*)(lowest + c)) > (int32_t)v)
+            atomicMin(lowest + c, (int32_t)v);
+    }
 }
 
 // tree[k] = the k-th tree edge in edge order (pos = inclusive scan of in_tree)
