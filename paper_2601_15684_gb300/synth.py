@@ -364,6 +364,11 @@ def workload(name: str) -> PoseGraph:
         return helix_graph()
     if name == "lattice1m":
         return lattice_walk_graph()
+    if name == "lattice1m_4m":
+        # the same walk with closures at p = 0.57: 4,002,064 edges, the
+        # "about 4M edges" of the 1M-pose lattice at the edge-to-pose ratio
+        # the stated workload names
+        return lattice_walk_graph(p_closure=0.57)
     if name == "walk10k":
         return random_walk_graph(10000, n_closures=20000, sigma_r=0.02, sigma_t=0.1, seed=5, name="walk10k")
     if name == "ring100":
