@@ -649,9 +649,9 @@ def run_ours(args):
         return el, 1e3 * (t1 - t0), 1e3 * (t2 - t1)
 
     # bytes copied per job: create uploads src, dst (int32), q_meas, t_meas,
-    # kappa, omega (double) per edge; the odometry start uploads the forest's
-    # parent and tree edge (int32) per vertex; the poses come back (double)
-    h2d = m * (4 + 4 + 8 * 4 + 8 * 3 + 8 + 8) + n * (4 + 4)
+    # kappa, omega (double) per edge (the odometry start runs on the device
+    # from them); the poses come back (double)
+    h2d = m * (4 + 4 + 8 * 4 + 8 * 3 + 8 + 8)
     d2h = n * (8 * 4 + 8 * 3)
     e2e_s, create_ms, init_ms = e2e_run(args.steps)
     e2e = {"value": ws * m * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,

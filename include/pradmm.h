@@ -117,10 +117,13 @@ typedef struct {
  * fallback_eps = 1e-6, use_graph = 1, block = 0, l2_window = 1. */
 void pradmm_default_params(pradmm_params* prm);
 
-/* Builds a solver for one pose graph (Section 2): validates the edges
- * (ERR_INDEX, ERR_SELFLOOP, ERR_NONFINITE, ERR_QUATERNION), renormalises
- * q_meas, sorts the edges by tail and by head, packs structure-of-arrays
- * device buffers and uploads them on `cuda_stream` (a cudaStream_t or NULL).
+/* Builds a solver for one pose graph (Section 2): uploads the arrays on
+ * `cuda_stream` (a cudaStream_t or NULL), validates the edges on the device
+ * before anything indexes with them (ERR_INDEX, ERR_SELFLOOP, ERR_NONFINITE for
+ * non-finite measurements or weights, ERR_ARG for weights <= 0,
+ * ERR_QUATERNION; the error names the first failing edge in input order),
+ * renormalises q_meas, sorts the edges by tail and by head and packs
+ * structure-of-arrays device buffers.
  *   src, dst     m int32 edge endpoints (tail i, head j)
  *   q_meas       m x 4 relative rotations q_ij
  *   t_meas       m x 3 relative translations t_ij
@@ -133,7 +136,10 @@ pradmm_status pradmm_create(int64_t n, int64_t m, const int32_t* src, const int3
                             pradmm_t* out);
 
 /* Same as pradmm_create with every array in device memory (e.g. torch
- * tensors); they are read once on the handle's stream before return. */
+ * tensors): `cuda_stream` (NULL: the legacy default stream) is synchronised
+ * first, so work queued there that writes the arrays is finished; they are
+ * then copied device to device on the handle's stream and validated there,
+ * all before return. */
 pradmm_status pradmm_create_device(int64_t n, int64_t m, const int32_t* src_d, const int32_t* dst_d,
                                    const double* q_meas_d, const double* t_meas_d,
                                    const double* kappa_d, const double* omega_d,

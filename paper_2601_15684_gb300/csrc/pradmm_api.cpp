@@ -14,7 +14,6 @@
 #include <string>
 #include <limits>
 #include <mutex>
-#include <thread>
 #include <vector>
 
 #include "pradmm_internal.h"
@@ -277,95 +276,102 @@ pradmm_status check_params(const pradmm_params* p) {
     return PRADMM_OK;
 }
 
-// Runs f(begin, end) over [0, count) split into contiguous ranges, one per
-// host thread (up to 16; small counts run on the calling thread).
-template <typename F>
-void parallel_for(int64_t count, F f) {
-    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    const int64_t T = std::min<int64_t>(std::min<unsigned>(hw, 16u), std::max<int64_t>(1, count / 32768));
-    if (T <= 1) {
-        f(int64_t(0), count);
-        return;
-    }
-    std::vector<std::thread> th;
-    th.reserve(T);
-    for (int64_t t = 0; t < T; ++t) th.emplace_back(f, count * t / T, count * (t + 1) / T);
-    for (auto& x : th) x.join();
-}
-
-// Host-side check of one edge (the caller's graph is never trusted).
-pradmm_status check_edge(int64_t n, int64_t e, const int32_t* src, const int32_t* dst, const double* q_meas,
-                         const double* t_meas, const double* kappa, const double* omega) {
-    if (src[e] < 0 || src[e] >= n || dst[e] < 0 || dst[e] >= n)
-        return fail(PRADMM_ERR_INDEX, "edge %lld = (%d, %d) has an endpoint outside [0, %lld)", (long long)e, src[e],
-                    dst[e], (long long)n);
-    if (src[e] == dst[e]) return fail(PRADMM_ERR_SELFLOOP, "edge %lld is a self-loop (%d, %d)", (long long)e, src[e], dst[e]);
-    const double ka = kappa ? kappa[e] : 1.0, om = omega ? omega[e] : 1.0;
-    if (!std::isfinite(ka) || !std::isfinite(om) || !(ka > 0) || !(om > 0))
-        return fail(ka > 0 && om > 0 ? PRADMM_ERR_NONFINITE : PRADMM_ERR_ARG, "edge %lld: weights must be finite and > 0",
-                    (long long)e);
+// Host-side check of one edge: the message for the first edge the device
+// validation rejects.
+pradmm_status check_edge(int64_t n, int64_t e, int32_t a, int32_t b, const double* q, const double* t, double ka,
+                         double om) {
+    if (a < 0 || a >= n || b < 0 || b >= n)
+        return fail(PRADMM_ERR_INDEX, "edge %lld = (%d, %d) has an endpoint outside [0, %lld)", (long long)e, a, b,
+                    (long long)n);
+    if (a == b) return fail(PRADMM_ERR_SELFLOOP, "edge %lld is a self-loop (%d, %d)", (long long)e, a, b);
+    if (!std::isfinite(ka) || !std::isfinite(om))
+        return fail(PRADMM_ERR_NONFINITE, "edge %lld: weights must be finite and > 0", (long long)e);
+    if (!(ka > 0) || !(om > 0)) return fail(PRADMM_ERR_ARG, "edge %lld: weights must be finite and > 0", (long long)e);
     double nn = 0.0;
     for (int c = 0; c < 4; ++c) {
-        if (!std::isfinite(q_meas[4 * e + c])) return fail(PRADMM_ERR_NONFINITE, "edge %lld: q_meas not finite", (long long)e);
-        nn += q_meas[4 * e + c] * q_meas[4 * e + c];
+        if (!std::isfinite(q[c])) return fail(PRADMM_ERR_NONFINITE, "edge %lld: q_meas not finite", (long long)e);
+        nn += q[c] * q[c];
     }
     for (int c = 0; c < 3; ++c)
-        if (!std::isfinite(t_meas[3 * e + c])) return fail(PRADMM_ERR_NONFINITE, "edge %lld: t_meas not finite", (long long)e);
+        if (!std::isfinite(t[c])) return fail(PRADMM_ERR_NONFINITE, "edge %lld: t_meas not finite", (long long)e);
     nn = std::sqrt(nn);
     if (std::fabs(nn - 1.0) > 1e-6) return fail(PRADMM_ERR_QUATERNION, "edge %lld: |q_meas| = %.17g is not 1", (long long)e, nn);
     return PRADMM_OK;
 }
 
-pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const double* q_meas, const double* t_meas,
-                    const double* kappa, const double* omega) {
-    const int64_t n = h->n, m = h->m;
-    // ---- validation (never trust the caller's graph), in parallel host
-    // threads.  The first failing edge is re-checked on this thread for its
-    // message ----
-    std::mutex bad_mu;
-    int64_t bad = m;
-    parallel_for(m, [&](int64_t e0, int64_t e1) {
-        for (int64_t e = e0; e < e1; ++e) {
-            bool ok = src[e] >= 0 && src[e] < n && dst[e] >= 0 && dst[e] < n && src[e] != dst[e];
-            const double k_e = kappa ? kappa[e] : 1.0, w_e = omega ? omega[e] : 1.0;
-            ok = ok && std::isfinite(k_e) && std::isfinite(w_e) && k_e > 0 && w_e > 0;
-            double nn = 0.0;
-            for (int c = 0; c < 4; ++c) nn += q_meas[4 * e + c] * q_meas[4 * e + c];
-            ok = ok && std::isfinite(nn) && std::isfinite(t_meas[3 * e]) && std::isfinite(t_meas[3 * e + 1]) &&
-                 std::isfinite(t_meas[3 * e + 2]);
-            ok = ok && std::fabs(std::sqrt(nn) - 1.0) <= 1e-6;
-            if (!ok) {
-                std::lock_guard<std::mutex> lk(bad_mu);
-                bad = std::min(bad, e);
-                return;
-            }
-        }
-    });
-    if (bad < m) {
-        const pradmm_status st = check_edge(n, bad, src, dst, q_meas, t_meas, kappa, omega);
-        return st != PRADMM_OK ? st : fail(PRADMM_ERR_ARG, "edge %lld is invalid", (long long)bad);
+// One device allocation carved into the handle's buffers (256-byte aligned):
+// layout(c) names every buffer once; a first pass with no base sizes the
+// block, a second assigns the pointers.
+struct Carve {
+    char* base = nullptr;
+    size_t off = 0;
+    template <typename T>
+    void take(T** p, size_t count) {
+        off = (off + 255) & ~size_t(255);
+        if (base) *p = reinterpret_cast<T*>(base + off);
+        off += std::max<size_t>(count, 1) * sizeof(T);
     }
+    void take_reals(void** p, size_t reals, size_t rsize) {
+        off = (off + 255) & ~size_t(255);
+        if (base) *p = base + off;
+        off += std::max<size_t>(reals, 1) * rsize;
+    }
+};
+
+pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const double* q_meas, const double* t_meas,
+                    const double* kappa, const double* omega, bool device_arrays) {
+    const int64_t n = h->n, m = h->m;
     h->out_slots = m;
     h->in_slots = m;
-    // ---- device buffers ----
-    ST(dalloc(h, &h->perm_d, n));
-    ST(dalloc(h, &h->out_ptr, n + 1));
-    ST(dalloc(h, &h->in_ptr, n + 1));
-    ST(dalloc(h, &h->out_idx, std::max<int64_t>(m, 1)));
-    ST(dalloc(h, &h->in_idx, std::max<int64_t>(m, 1)));
-    ST(dalloc(h, &h->out_edge_d, std::max<int64_t>(m, 1)));
-    ST(dalloc(h, &h->edge_slot_d, std::max<int64_t>(m, 1)));
-    ST(valloc(h, &h->out_te, 4 * h->out_slots));
-    ST(valloc(h, &h->out_qk, 4 * h->out_slots));
-    ST(valloc(h, &h->in_te, 4 * h->in_slots));
-    ST(valloc(h, &h->in_qk, 4 * h->in_slots));
-    ST(dalloc(h, &h->qe64, 4 * h->out_slots));
-    ST(dalloc(h, &h->te64, 3 * h->out_slots));
-    ST(dalloc(h, &h->ka64, h->out_slots));
-    ST(dalloc(h, &h->om64, h->out_slots));
-    // one block, gathered arrays first (the L2 persistence window covers them)
+    // ---- device buffers: one block ----
     const bool inert = h->prm.inertia != 0.0;
-    ST(valloc(h, &h->state_block, (inert ? 44 : 28) * (size_t)n));
+    void* sb = nullptr;
+    auto layout = [&](Carve& c) {
+        const size_t r = h->rsize;
+        c.take(&h->perm_d, n);
+        c.take(&h->out_ptr, n + 1);
+        c.take(&h->in_ptr, n + 1);
+        c.take(&h->out_idx, m);
+        c.take(&h->in_idx, m);
+        c.take(&h->out_edge_d, m);
+        c.take(&h->edge_slot_d, m);
+        c.take_reals(&h->out_te, 4 * h->out_slots, r);
+        c.take_reals(&h->out_qk, 4 * h->out_slots, r);
+        c.take_reals(&h->in_te, 4 * h->in_slots, r);
+        c.take_reals(&h->in_qk, 4 * h->in_slots, r);
+        c.take(&h->qe64, 4 * h->out_slots);
+        c.take(&h->te64, 3 * h->out_slots);
+        c.take(&h->ka64, h->out_slots);
+        c.take(&h->om64, h->out_slots);
+        // the vertex state: gathered arrays first (the L2 persistence window covers them)
+        c.take_reals(&sb, (inert ? 44 : 28) * (size_t)n, r);
+        c.take(&h->inv2_d, n);
+        c.take(&h->inv3_d, n);
+        c.take(&h->inv4_d, n);
+        c.take(&h->stage, 4 * n);
+        c.take(&h->zeros, 4 * n);
+        // room for the partials of any CTA size the sweeps may be given (pradmm_autotune)
+        c.take(&h->part, 4 * (size_t)std::max(h->pstride, h->sms * 32));
+        c.take(&h->obj_part, (size_t)std::max(h->obj_grid, h->sms * 4));
+        c.take(&h->obj_ticket, 1);
+        c.take(&h->F_dev, 1);
+        c.take(&h->dbg_d, 2);
+        c.take(&h->ctrl, 1);
+    };
+    {
+        Carve probe;
+        layout(probe);
+        void* block = nullptr;
+        cudaError_t e = cudaMalloc(&block, probe.off);
+        if (e != cudaSuccess)
+            return fail(e == cudaErrorMemoryAllocation ? PRADMM_ERR_NOMEM : PRADMM_ERR_CUDA, "cudaMalloc(%zu): %s",
+                        probe.off, cudaGetErrorString(e));
+        h->allocs.push_back(block);
+        Carve c;
+        c.base = static_cast<char*>(block);
+        layout(c);
+    }
+    h->state_block = sb;
     {
         char* b = static_cast<char*>(h->state_block);
         const size_t a = 4 * (size_t)n * h->rsize;
@@ -381,18 +387,6 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
             h->pm1 = b + 10 * a;        // p^{k-1} at the last recorded iteration's start
         }
     }
-    ST(dalloc(h, &h->inv2_d, n));
-    ST(dalloc(h, &h->inv3_d, n));
-    ST(dalloc(h, &h->inv4_d, n));
-    ST(dalloc(h, &h->stage, 4 * n));
-    ST(dalloc(h, &h->zeros, 4 * n));
-    // room for the partials of any CTA size the sweeps may be given (pradmm_autotune)
-    ST(dalloc(h, &h->part, 4 * (size_t)std::max(h->pstride, h->sms * 32)));
-    ST(dalloc(h, &h->obj_part, (size_t)std::max(h->obj_grid, h->sms * 4)));
-    ST(dalloc(h, &h->obj_ticket, 1));
-    ST(dalloc(h, &h->F_dev, 1));
-    ST(dalloc(h, &h->dbg_d, 2));
-    ST(dalloc(h, &h->ctrl, 1));
     {
         void* hp = nullptr;
         CU(cudaMallocHost(&hp, sizeof(Ctrl)));
@@ -405,7 +399,7 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
     const int64_t nb = (n + 1023) / 1024;
     const size_t raw = (size_t)m * (4 + 3) * sizeof(double) + (kappa ? (size_t)m * sizeof(double) : 0) +
                        (omega ? (size_t)m * sizeof(double) : 0) + 3 * (size_t)m * sizeof(int32_t) +
-                       (size_t)(n + nb + 4) * sizeof(int32_t);
+                       (size_t)(n + nb + 8) * sizeof(int32_t);
     char* tmp = nullptr;
     cudaError_t e = cudaMalloc(&tmp, raw);
     if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? PRADMM_ERR_NOMEM : PRADMM_ERR_CUDA,
@@ -419,10 +413,12 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
     int32_t* ie_d = dst_d + m;  // in-slot -> input edge
     int32_t* fill = ie_d + m;
     int32_t* sums = fill + n;
+    int32_t* first_bad = sums + nb + 4;
     cudaStream_t st = h->stream;
     pradmm_status ps = PRADMM_OK;
+    const cudaMemcpyKind kind = device_arrays ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     auto up = [&](void* d, const void* s, size_t bytes) {
-        if (ps == PRADMM_OK && bytes > 0 && (e = cudaMemcpyAsync(d, s, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        if (ps == PRADMM_OK && bytes > 0 && (e = cudaMemcpyAsync(d, s, bytes, kind, st)) != cudaSuccess)
             ps = fail(PRADMM_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
     };
     auto dev = [&](cudaError_t r, const char* what) {
@@ -434,6 +430,40 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
     if (omega) up(w_d, omega, sizeof(double) * m);
     up(src_d, src, sizeof(int32_t) * m);
     up(dst_d, dst, sizeof(int32_t) * m);
+    // ---- validation (never trust the caller's graph) on the uploaded arrays;
+    // nothing indexes with the endpoints before it has passed.  The first
+    // failing edge is re-checked on the host for its message ----
+    if (ps == PRADMM_OK && m > 0) {
+        int32_t bad = (int32_t)m;
+        const int32_t m32 = (int32_t)m;
+        dev(cudaMemcpyAsync(first_bad, &m32, sizeof(int32_t), cudaMemcpyHostToDevice, st), "upload");
+        dev(pradmm::launch_validate(src_d, dst_d, q_d, t_d, k_d, w_d, n, m, first_bad, st), "validation");
+        dev(cudaMemcpyAsync(&bad, first_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st), "validation");
+        dev(cudaStreamSynchronize(st), "validation");
+        if (ps == PRADMM_OK && bad < m) {
+            // the failing edge's values, for its message
+            int32_t a = 0, b = 0;
+            double q4[4] = {0, 0, 0, 0}, t3[3] = {0, 0, 0}, ka = 1.0, om = 1.0;
+            if (device_arrays) {
+                dev(cudaMemcpyAsync(&a, src_d + bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st), "download");
+                dev(cudaMemcpyAsync(&b, dst_d + bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st), "download");
+                dev(cudaMemcpyAsync(q4, q_d + 4 * (int64_t)bad, sizeof(q4), cudaMemcpyDeviceToHost, st), "download");
+                dev(cudaMemcpyAsync(t3, t_d + 3 * (int64_t)bad, sizeof(t3), cudaMemcpyDeviceToHost, st), "download");
+                if (k_d) dev(cudaMemcpyAsync(&ka, k_d + bad, sizeof(double), cudaMemcpyDeviceToHost, st), "download");
+                if (w_d) dev(cudaMemcpyAsync(&om, w_d + bad, sizeof(double), cudaMemcpyDeviceToHost, st), "download");
+                dev(cudaStreamSynchronize(st), "download");
+            } else {
+                a = src[bad];
+                b = dst[bad];
+                std::memcpy(q4, q_meas + 4 * (int64_t)bad, sizeof(q4));
+                std::memcpy(t3, t_meas + 3 * (int64_t)bad, sizeof(t3));
+                if (kappa) ka = kappa[bad];
+                if (omega) om = omega[bad];
+            }
+            if (ps == PRADMM_OK) ps = check_edge(n, bad, a, b, q4, t3, ka, om);
+            if (ps == PRADMM_OK) ps = fail(PRADMM_ERR_ARG, "edge %lld is invalid", (long long)bad);
+        }
+    }
     if (ps == PRADMM_OK) {
         dev(pradmm::build_csr_device(src_d, dst_d, n, m, h->out_ptr, h->out_edge_d, h->out_idx, h->edge_slot_d, fill,
                                      sums, st), "out-edge CSR");
@@ -572,7 +602,7 @@ pradmm_status set_grids(pradmm_s* h, int block) {
 
 pradmm_status create_common(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const double* q_meas,
                             const double* t_meas, const double* kappa, const double* omega, const pradmm_params* prm,
-                            void* stream, pradmm_t* out) {
+                            void* stream, pradmm_t* out, bool device_arrays) {
     if (!out) return fail(PRADMM_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (n < 1 || m < 0 || n > INT32_MAX - 1 || m > INT32_MAX - 1)
@@ -622,7 +652,7 @@ pradmm_status create_common(int64_t n, int64_t m, const int32_t* src, const int3
         (void)bps;
         h->sms = sms;
         if ((st = set_grids(h, h->block)) != PRADMM_OK) break;
-        st = build(h, src, dst, q_meas, t_meas, kappa, omega);
+        st = build(h, src, dst, q_meas, t_meas, kappa, omega, device_arrays);
         if (st == PRADMM_OK && p.l2_window) l2_window_on(h, dev);
     } while (0);
     if (st != PRADMM_OK) {
@@ -1522,7 +1552,7 @@ pradmm_status pradmm_create(int64_t n, int64_t m, const int32_t* src, const int3
                             const double* t_meas, const double* kappa, const double* omega, const pradmm_params* prm,
                             void* cuda_stream, pradmm_t* out) {
     try {
-        return create_common(n, m, src, dst, q_meas, t_meas, kappa, omega, prm, cuda_stream, out);
+        return create_common(n, m, src, dst, q_meas, t_meas, kappa, omega, prm, cuda_stream, out, false);
     } catch (const std::bad_alloc&) {
         return fail(PRADMM_ERR_NOMEM, "host allocation failed");
     }
@@ -1536,31 +1566,12 @@ pradmm_status pradmm_create_device(int64_t n, int64_t m, const int32_t* src_d, c
     *out = nullptr;
     if (m < 0 || m > INT32_MAX - 1) return fail(PRADMM_ERR_ARG, "bad m");
     if (m > 0 && (!src_d || !dst_d || !q_meas_d || !t_meas_d)) return fail(PRADMM_ERR_ARG, "edge arrays must not be NULL");
-    try {
-        // the graph builder validates and sorts on the host: bring the edges over once
-        std::vector<int32_t> src(m), dst(m);
-        std::vector<double> qm(4 * m), tm(3 * m), ka, om;
-        cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-        if (m > 0) {
-            CU(cudaMemcpyAsync(src.data(), src_d, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, st));
-            CU(cudaMemcpyAsync(dst.data(), dst_d, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, st));
-            CU(cudaMemcpyAsync(qm.data(), q_meas_d, sizeof(double) * 4 * m, cudaMemcpyDeviceToHost, st));
-            CU(cudaMemcpyAsync(tm.data(), t_meas_d, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, st));
-            if (kappa_d) {
-                ka.resize(m);
-                CU(cudaMemcpyAsync(ka.data(), kappa_d, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
-            }
-            if (omega_d) {
-                om.resize(m);
-                CU(cudaMemcpyAsync(om.data(), omega_d, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
-            }
-            CU(cudaStreamSynchronize(st));
-        }
-        return create_common(n, m, src.data(), dst.data(), qm.data(), tm.data(), kappa_d ? ka.data() : nullptr,
-                             omega_d ? om.data() : nullptr, prm, cuda_stream, out);
-    } catch (const std::bad_alloc&) {
-        return fail(PRADMM_ERR_NOMEM, "host allocation failed");
-    }
+    // work the caller queued on the stream that writes the arrays ends first;
+    // they are then copied device to device into the builder's upload buffer
+    // and validated there, as the host arrays of pradmm_create are
+    const cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return fail(PRADMM_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+    return create_common(n, m, src_d, dst_d, q_meas_d, t_meas_d, kappa_d, omega_d, prm, cuda_stream, out, true);
 }
 
 pradmm_status pradmm_set_state(pradmm_t h, const double* q, const double* t) {
@@ -2133,7 +2144,8 @@ pradmm_status pradmm_batch_create(int32_t G, const int64_t* n_g, const int64_t* 
             pradmm_default_params(&bp);
         }
         bp.l2_window = 0;  // the persistent batch kernel takes no access-policy window
-        pradmm_status st = create_common(n, m, us.data(), ud.data(), q_meas, t_meas, kappa, omega, &bp, cuda_stream, &h);
+        pradmm_status st = create_common(n, m, us.data(), ud.data(), q_meas, t_meas, kappa, omega, &bp, cuda_stream, &h,
+                                         false);
         if (st != PRADMM_OK) {
             delete b;
             return st;

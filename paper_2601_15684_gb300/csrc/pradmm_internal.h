@@ -116,6 +116,11 @@ cudaError_t sweep_occupancy(int is_double, int block, int* bps);
 cudaError_t build_csr_device(const int32_t* key, const int32_t* other, int64_t n, int64_t m, int32_t* ptr,
                              int32_t* slot_edge, int32_t* idx, int32_t* edge_slot, int32_t* fill, int32_t* sums,
                              cudaStream_t st);
+// The per-edge checks of pradmm_create on the uploaded arrays (ka, om may be
+// NULL: unit weights); *first_bad, set to m beforehand, receives the lowest
+// failing edge.
+cudaError_t launch_validate(const int32_t* src, const int32_t* dst, const double* q, const double* t, const double* ka,
+                            const double* om, int64_t n, int64_t m, int32_t* first_bad, cudaStream_t st);
 // Inclusive scan of a[0, len) in place; sums holds (len + 1023) / 1024 ints.
 cudaError_t inclusive_scan_i32(int32_t* a, int64_t len, int32_t* sums, cudaStream_t st);
 // The odometry start's spanning forest (Kruskal by edge order, found by

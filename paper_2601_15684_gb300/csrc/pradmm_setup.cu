@@ -215,6 +215,29 @@ __global__ void __launch_bounds__(256) k_slot_owner(const int32_t* __restrict__ 
         for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k) owner[k] = (int32_t)i;
 }
 
+// ---- validation of the caller's edges ----------------------------------------
+// The checks of pradmm_create, edge by edge: endpoints in [0, n) and distinct,
+// weights finite and > 0, measurements finite, |q_e| within 1e-6 of 1 (the
+// squared norm summed in component order with separate roundings, as a host
+// loop without contraction forms it, then the correctly rounded square root);
+// *first_bad = the lowest failing edge (m when none fails).
+__global__ void __launch_bounds__(256) k_validate(const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+                                                  const double* __restrict__ q, const double* __restrict__ t,
+                                                  const double* __restrict__ ka, const double* __restrict__ om,
+                                                  int64_t n, int64_t m, int32_t* first_bad) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = src[e], b = dst[e];
+        bool ok = a >= 0 && a < n && b >= 0 && b < n && a != b;
+        const double k_e = ka ? ka[e] : 1.0, w_e = om ? om[e] : 1.0;
+        ok = ok && isfinite(k_e) && isfinite(w_e) && k_e > 0.0 && w_e > 0.0;
+        double nn = 0.0;
+        for (int c = 0; c < 4; ++c) nn = __dadd_rn(nn, __dmul_rn(q[4 * e + c], q[4 * e + c]));
+        ok = ok && isfinite(nn) && isfinite(t[3 * e]) && isfinite(t[3 * e + 1]) && isfinite(t[3 * e + 2]);
+        ok = ok && fabs(__dadd_rn(__dsqrt_rn(nn), -1.0)) <= 1e-6;
+        if (!ok) atomicMin(first_bad, (int32_t)e);
+    }
+}
+
 // ---- odometry composition on the device -----------------------------------
 // The spanning forest (pradmm_forest.cu) gives every vertex its parent and the tree edge
 // to it; the pose of a vertex is the composition of the SE(3) steps along the
@@ -310,6 +333,13 @@ inline int grid_of(int64_t work) {
 }
 
 }  // namespace
+
+cudaError_t launch_validate(const int32_t* src, const int32_t* dst, const double* q, const double* t, const double* ka,
+                            const double* om, int64_t n, int64_t m, int32_t* first_bad, cudaStream_t st) {
+    if (m <= 0) return cudaSuccess;
+    k_validate<<<grid_of(m), 256, 0, st>>>(src, dst, q, t, ka, om, n, m, first_bad);
+    return cudaGetLastError();
+}
 
 cudaError_t inclusive_scan_i32(int32_t* a, int64_t len, int32_t* sums, cudaStream_t st) {
     if (len <= 0) return cudaSuccess;

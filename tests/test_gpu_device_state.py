@@ -80,3 +80,50 @@ def test_get_state_device_round_trip(P):
             S.set_state_device(d["p"][:10], d["q"], d["t"], d["s"])
         with pytest.raises(ValueError):
             S.set_state_device(d["p"].float(), d["q"], d["t"], d["s"])
+
+
+def test_create_from_device_arrays_equals_host_create(P):
+    """pradmm_create_device copies the edge arrays device to device and runs
+    the same validation and build: the odometry start and the iterates agree
+    bit for bit with a handle created from the host arrays, and a bad edge
+    gives the host path's status and message."""
+    import torch
+    g = synth.random_graph(2000, 7000, seed=41, isolated=5)
+    d = {k: torch.from_numpy(np.ascontiguousarray(v)).to("cuda:0")
+         for k, v in (("src", g.src), ("dst", g.dst), ("q", g.q_meas), ("t", g.t_meas), ("k", g.kappa),
+                      ("w", g.omega))}
+    torch.cuda.synchronize()
+    prm = P.pradmm_default_params()
+    out = []
+    for via_device in (False, True):
+        if via_device:
+            h = P.pradmm_create_device(g.n, g.m, d["src"].data_ptr(), d["dst"].data_ptr(), d["q"].data_ptr(),
+                                       d["t"].data_ptr(), d["k"].data_ptr(), d["w"].data_ptr(), prm)
+        else:
+            h = P.pradmm_create(g.n, g.src, g.dst, g.q_meas, g.t_meas, g.kappa, g.omega, prm)
+        try:
+            P.pradmm_init_odometry(h)
+            P.pradmm_step(h, 7)
+            q = np.zeros((g.n, 4))
+            t = np.zeros((g.n, 3))
+            P.pradmm_get_poses(h, g.n, q, t)
+            out.append((q, t))
+        finally:
+            P.pradmm_destroy(h)
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    for e, v, code in ((4321, g.n, P.PRADMM_ERR_INDEX), (1234, "self", P.PRADMM_ERR_SELFLOOP)):
+        dst = g.dst.copy()
+        dst[e] = g.src[e] if v == "self" else v
+        msgs = []
+        for via_device in (False, True):
+            with pytest.raises(P.PRADMMError) as ei:
+                if via_device:
+                    dd = torch.from_numpy(dst).to("cuda:0")
+                    P.pradmm_create_device(g.n, g.m, d["src"].data_ptr(), dd.data_ptr(), d["q"].data_ptr(),
+                                           d["t"].data_ptr(), d["k"].data_ptr(), d["w"].data_ptr(), prm)
+                else:
+                    P.pradmm_create(g.n, g.src, dst, g.q_meas, g.t_meas, g.kappa, g.omega, prm)
+            assert ei.value.status == code
+            msgs.append(ei.value.message)
+        assert msgs[0] == msgs[1] and f"edge {e}" in msgs[0], msgs

@@ -306,8 +306,9 @@ def test_input_errors(P):
 
 
 def test_input_errors_in_a_large_edge_list_name_the_first_bad_edge(P):
-    # above ~32k edges validation runs on several host threads; the error must
-    # still be the first invalid edge in input order, with its own message
+    # the edges are validated on the device (every edge by its own thread);
+    # the error must still be the first invalid edge in input order, with
+    # the message the host forms for it
     g = synth.random_graph(50000, 200000, seed=8)
     cases = [
         ("dst", {170000: 50000, 150001: -1}, P.PRADMM_ERR_INDEX, "edge 150001"),
@@ -327,6 +328,37 @@ def test_input_errors_in_a_large_edge_list_name_the_first_bad_edge(P):
     with pytest.raises(P.PRADMMError) as ei:
         P.pradmm_create(g.n, g.src, g.dst, qm, g.t_meas)
     assert ei.value.status == P.PRADMM_ERR_NONFINITE and "edge 160000" in str(ei.value)
+
+
+def test_input_validation_boundaries(P):
+    """The device validation takes the host's decisions: |q_e| accepted within
+    1e-6 of 1 (squared norm summed in component order with separate
+    roundings, then the square root), weights finite and > 0."""
+    import math
+
+    g = synth.random_graph(40, 100, seed=12)
+    for scale in (1 + 0.5e-6, 1 + 0.999e-6, 1 + 1.001e-6, 1 - 0.999e-6, 1 - 1.001e-6, 1 + 3e-6):
+        qm = g.q_meas.copy()
+        qm[7] *= scale
+        q = [float(x) for x in qm[7]]
+        nn = 0.0
+        for x in q:
+            nn = nn + x * x
+        ok = abs(math.sqrt(nn) - 1.0) <= 1e-6
+        if ok:
+            P.pradmm_destroy(P.pradmm_create(g.n, g.src, g.dst, qm, g.t_meas))
+        else:
+            with pytest.raises(P.PRADMMError) as ei:
+                P.pradmm_create(g.n, g.src, g.dst, qm, g.t_meas)
+            assert ei.value.status == P.PRADMM_ERR_QUATERNION and "edge 7" in str(ei.value), str(ei.value)
+    for name, val, code in (("kappa", 0.0, P.PRADMM_ERR_ARG), ("kappa", -1.0, P.PRADMM_ERR_ARG),
+                            ("omega", np.inf, P.PRADMM_ERR_NONFINITE), ("omega", np.nan, P.PRADMM_ERR_NONFINITE),
+                            ("kappa", -np.inf, P.PRADMM_ERR_NONFINITE)):
+        ka, om = g.kappa.copy(), g.omega.copy()
+        (ka if name == "kappa" else om)[11] = val
+        with pytest.raises(P.PRADMMError) as ei:
+            P.pradmm_create(g.n, g.src, g.dst, g.q_meas, g.t_meas, ka, om)
+        assert ei.value.status == code and "edge 11" in str(ei.value), (name, val, str(ei.value))
 
 
 def test_nonfinite_state_is_reported(P):
