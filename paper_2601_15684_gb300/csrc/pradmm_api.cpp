@@ -1659,8 +1659,9 @@ pradmm_status pradmm_autotune(pradmm_t h, int32_t iters, int32_t* block_out) {
 pradmm_status pradmm_init_odometry(pradmm_t h) {
     if (!h) return fail(PRADMM_ERR_ARG, "NULL handle");
     const int64_t n = h->n, m = h->m;
-    const size_t fs = pradmm::forest_scratch_ints(n, m);
-    const size_t bytes = (size_t)n * 14 * sizeof(double) + ((size_t)3 * n + 1 + fs) * sizeof(int32_t) + 64;
+    // the forest's work space, then the composition's, in one region
+    const size_t work = std::max(pradmm::forest_scratch_ints(n, m) * sizeof(int32_t), pradmm::odometry_scratch_bytes(n));
+    const size_t bytes = (size_t)n * 14 * sizeof(double) + work + (size_t)2 * n * sizeof(int32_t) + 64;
     char* tmp = nullptr;
     cudaError_t e = cudaMalloc(&tmp, bytes);
     if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? PRADMM_ERR_NOMEM : PRADMM_ERR_CUDA,
@@ -1669,19 +1670,15 @@ pradmm_status pradmm_init_odometry(pradmm_t h) {
     double* t = q + 4 * n;
     double* q2 = t + 3 * n;
     double* t2 = q2 + 4 * n;
-    int32_t* pe_d = reinterpret_cast<int32_t*>(t2 + 3 * n);
+    char* ws = reinterpret_cast<char*>(t2 + 3 * n);
+    int32_t* pe_d = reinterpret_cast<int32_t*>(ws + work);
     int32_t* par_d = pe_d + n;
-    int32_t* par2 = par_d + n;
-    int32_t* flag = par2 + n;
-    int32_t* scratch = flag + 1;
-    int max_rounds = 1;
-    while (((int64_t)1 << max_rounds) <= n) ++max_rounds;
     cudaStream_t st = h->stream;
     pradmm_status ps = PRADMM_OK;
-    if ((e = pradmm::launch_forest(h->out_ptr, h->out_idx, h->out_edge_d, n, m, scratch, par_d, pe_d, st)) !=
-            cudaSuccess ||
-        (e = pradmm::launch_odometry(pe_d, par_d, max_rounds, flag, h->edge_slot_d, h->qe64, h->te64, n, par2, q, t,
-                                     q2, t2, st)) != cudaSuccess)
+    if ((e = pradmm::launch_forest(h->out_ptr, h->out_idx, h->out_edge_d, n, m, reinterpret_cast<int32_t*>(ws), par_d,
+                                   pe_d, st)) != cudaSuccess ||
+        (e = pradmm::launch_odometry(pe_d, par_d, h->edge_slot_d, h->qe64, h->te64, n, ws, q, t, q2, t2, st)) !=
+            cudaSuccess)
         ps = fail(PRADMM_ERR_CUDA, "odometry: %s", cudaGetErrorString(e));
     if (ps == PRADMM_OK) ps = set_state_any(h, q, q, t, t, nullptr, nullptr, true);
     e = cudaStreamSynchronize(st);

@@ -141,14 +141,14 @@ cudaError_t launch_iota(int32_t* a, int64_t n, cudaStream_t st);
 cudaError_t launch_slot_owner(const int32_t* ptr, int64_t n, int32_t* owner, cudaStream_t st);
 // Odometry poses from the spanning forest: pedge[v] = e when v is the head of
 // its tree edge e, -(e + 2) when v is its tail, -1 for a root; par[v] the
-// parent (-1 for a root), overwritten; the
-// poses end in q (4n), t (3n); par_tmp, q_tmp, t_tmp are scratch.  The
-// pointer-jumping rounds run in pairs until no vertex has a parent left
-// (*flag, one device int, read back after each pair: synchronises the
-// stream), at most max_rounds (rounded up to even).
-cudaError_t launch_odometry(const int32_t* pedge, const int32_t* par, int max_rounds, int32_t* flag,
-                            const int32_t* edge_slot, const double* qe64, const double* te64, int64_t n,
-                            int32_t* par_tmp, double* q, double* t, double* q_tmp, double* t_tmp, cudaStream_t st);
+// parent (-1 for a root).  The poses end in q (4n), t (3n); q_tmp, t_tmp and
+// `scratch` (odometry_scratch_bytes(n), 8-byte aligned) are work space.  No
+// host synchronisation: every pointer-jumping loop runs enough rounds for
+// any tree of n vertices.
+size_t odometry_scratch_bytes(int64_t n);
+cudaError_t launch_odometry(const int32_t* pedge, const int32_t* par, const int32_t* edge_slot, const double* qe64,
+                            const double* te64, int64_t n, void* scratch, double* q, double* t, double* q_tmp,
+                            double* t_tmp, cudaStream_t st);
 
 // Device-side parameters of a tape recording (reverse mode): after the
 // iteration that brings ctrl->iter to k0 + d, with d a multiple of C or

@@ -242,8 +242,8 @@ __global__ void __launch_bounds__(256) k_validate(const int32_t* __restrict__ sr
 // The spanning forest (pradmm_forest.cu) gives every vertex its parent and the tree edge
 // to it; the pose of a vertex is the composition of the SE(3) steps along the
 // tree path from its component's root, T_v = T_parent o T_step with
-// (q_a, t_a) o (q_b, t_b) = (q_a q_b, t_a + R(q_a) t_b).  Pointer jumping
-// composes the paths in ceil(log2(depth + 1)) rounds.
+// (q_a, t_a) o (q_b, t_b) = (q_a q_b, t_a + R(q_a) t_b), composed by pointer
+// jumping in segments of tree levels (below).
 __device__ __forceinline__ void hq_mul(const double* a, const double* b, double* o) {
     const double w = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
     const double x = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
@@ -300,30 +300,160 @@ __global__ void __launch_bounds__(256) k_odo_steps(const int32_t* __restrict__ p
     }
 }
 
-__global__ void __launch_bounds__(256) k_odo_jump(const int32_t* __restrict__ par_in, const double* __restrict__ q_in,
-                                                  const double* __restrict__ t_in, int64_t n, int32_t* par_out,
-                                                  double* q_out, double* t_out, int32_t* more) {
+// (q_a, t_a) o (q_b, t_b) into (qo, to)
+__device__ __forceinline__ void se3_compose(const double* qa, const double* ta, const double* qb, const double* tb,
+                                            double* qo, double* to) {
+    double r[3];
+    hq_mul(qa, qb, qo);
+    hq_rot(qa, tb, r);
+    for (int c = 0; c < 3; ++c) to[c] = ta[c] + r[c];
+}
+
+__device__ __forceinline__ void ld_pose(const double* q, const double* t, int64_t v, double* qv, double* tv) {
+    for (int c = 0; c < 4; ++c) qv[c] = q[4 * v + c];
+    for (int c = 0; c < 3; ++c) tv[c] = t[3 * v + c];
+}
+
+__device__ __forceinline__ void st_pose(double* q, double* t, int64_t v, const double* qv, const double* tv) {
+    for (int c = 0; c < 4; ++c) q[4 * v + c] = qv[c];
+    for (int c = 0; c < 3; ++c) t[3 * v + c] = tv[c];
+}
+
+// The poses are composed in segments of kSeg tree levels.  A vertex whose
+// depth is a multiple of kSeg (every root) heads a segment; every other
+// vertex v composes the steps below its segment head sigma(v) by pointer
+// jumping that stops at heads (log2 kSeg rounds), the heads, packed into a
+// dense list (one vertex in kSeg on a deep tree, so that their FP64 work
+// fills whole warps), compose their head-to-head chains by pointer jumping
+// among themselves, and each vertex then takes pose(sigma(v)) o C(v).
+// About log2(kSeg) + 1 compositions per vertex instead of log2(depth).
+constexpr int kSeg = 16;
+
+// depth by pointer jumping: d = number of steps to the current pointer
+__global__ void __launch_bounds__(256) k_depth_init(const int32_t* __restrict__ par, int64_t n, int32_t* p_out,
+                                                    int32_t* d_out) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t p = par_in[v];
-        double qv[4], tv[3];
-        for (int c = 0; c < 4; ++c) qv[c] = q_in[4 * v + c];
-        for (int c = 0; c < 3; ++c) tv[c] = t_in[3 * v + c];
+        const int32_t p = par[v];
+        p_out[v] = p;
+        d_out[v] = p >= 0 ? 1 : 0;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_depth_jump(const int32_t* __restrict__ p_in, const int32_t* __restrict__ d_in,
+                                                    int64_t n, int32_t* p_out, int32_t* d_out) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = p_in[v];
         if (p >= 0) {
-            double qp[4], tp[3], r[3], qn[4];
-            for (int c = 0; c < 4; ++c) qp[c] = q_in[4 * (int64_t)p + c];
-            for (int c = 0; c < 3; ++c) tp[c] = t_in[3 * (int64_t)p + c];
-            hq_mul(qp, qv, qn);
-            hq_rot(qp, tv, r);
-            for (int c = 0; c < 4; ++c) qv[c] = qn[c];
-            for (int c = 0; c < 3; ++c) tv[c] = tp[c] + r[c];
-            const int32_t pp = par_in[p];
-            par_out[v] = pp;
-            if (more && pp >= 0) *more = 1;
+            d_out[v] = d_in[v] + d_in[p];
+            p_out[v] = p_in[p];
         } else {
-            par_out[v] = p;
+            d_out[v] = d_in[v];
+            p_out[v] = p;
         }
-        for (int c = 0; c < 4; ++c) q_out[4 * v + c] = qv[c];
-        for (int c = 0; c < 3; ++c) t_out[3 * v + c] = tv[c];
+    }
+}
+
+__device__ __forceinline__ bool seg_head(const int32_t* depth, int64_t v) { return depth[v] % kSeg == 0; }
+
+// segment pointers (a head's is -1: it does not jump; every other vertex's
+// its parent) and the head flags
+__global__ void __launch_bounds__(256) k_seg_init(const int32_t* __restrict__ par, const int32_t* __restrict__ depth,
+                                                  int64_t n, int32_t* p_out, int32_t* head_flag) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const bool h = seg_head(depth, v);
+        p_out[v] = h ? -1 : par[v];
+        head_flag[v] = h ? 1 : 0;
+    }
+}
+
+// one round inside the segments: (P(v), v] grows to (P(P(v)), v] unless P(v) is a head
+__global__ void __launch_bounds__(256) k_seg_jump(const int32_t* __restrict__ p_in, const double* __restrict__ q_in,
+                                                  const double* __restrict__ t_in, const int32_t* __restrict__ depth,
+                                                  int64_t n, int32_t* p_out, double* q_out, double* t_out) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = p_in[v];
+        double qv[4], tv[3];
+        ld_pose(q_in, t_in, v, qv, tv);
+        if (p >= 0 && !seg_head(depth, p)) {
+            double qp[4], tp[3], qn[4], tn[3];
+            ld_pose(q_in, t_in, p, qp, tp);
+            se3_compose(qp, tp, qv, tv, qn, tn);
+            st_pose(q_out, t_out, v, qn, tn);
+            p_out[v] = p_in[p];
+        } else {
+            st_pose(q_out, t_out, v, qv, tv);
+            p_out[v] = p;
+        }
+    }
+}
+
+// Head k (ordinal: hpos[v] - 1, hpos the inclusive scan of the head flags):
+// the vertex it is, the ordinal of the head above (-1 for a root) and the
+// pose step from it, C(par(s)) o step(s) (just step(s) when the parent is a
+// head itself; the identity for a root).
+__global__ void __launch_bounds__(256) k_head_init(const int32_t* __restrict__ par, const int32_t* __restrict__ seg_p,
+                                                   const int32_t* __restrict__ depth, const int32_t* __restrict__ hpos,
+                                                   const double* __restrict__ q, const double* __restrict__ t, int64_t n,
+                                                   int32_t* hp, double* hq, double* ht) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        if (!seg_head(depth, v)) continue;
+        const int64_t k = hpos[v] - 1;
+        const int32_t p = par[v];
+        double qv[4], tv[3];
+        ld_pose(q, t, v, qv, tv);
+        if (p < 0) {
+            hp[k] = -1;
+        } else if (seg_head(depth, p)) {
+            hp[k] = hpos[p] - 1;
+        } else {
+            double qp[4], tp[3], qn[4], tn[3];
+            ld_pose(q, t, p, qp, tp);
+            se3_compose(qp, tp, qv, tv, qn, tn);
+            for (int c = 0; c < 4; ++c) qv[c] = qn[c];
+            for (int c = 0; c < 3; ++c) tv[c] = tn[c];
+            hp[k] = hpos[seg_p[p]] - 1;
+        }
+        st_pose(hq, ht, k, qv, tv);
+    }
+}
+
+// pointer jumping over the dense head list (its length read on the device)
+__global__ void __launch_bounds__(256) k_head_jump(const int32_t* __restrict__ p_in, const double* __restrict__ q_in,
+                                                   const double* __restrict__ t_in, const int32_t* __restrict__ count,
+                                                   int32_t* p_out, double* q_out, double* t_out) {
+    const int64_t H = *count;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < H; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = p_in[k];
+        double qv[4], tv[3];
+        ld_pose(q_in, t_in, k, qv, tv);
+        if (p >= 0) {
+            double qp[4], tp[3], qn[4], tn[3];
+            ld_pose(q_in, t_in, p, qp, tp);
+            se3_compose(qp, tp, qv, tv, qn, tn);
+            st_pose(q_out, t_out, k, qn, tn);
+            p_out[k] = p_in[p];
+        } else {
+            st_pose(q_out, t_out, k, qv, tv);
+            p_out[k] = p;
+        }
+    }
+}
+
+// pose(v) = pose(sigma(v)) o C(v); a head's pose is its chain's; in place in q, t
+__global__ void __launch_bounds__(256) k_seg_apply(const int32_t* __restrict__ seg_p, const int32_t* __restrict__ depth,
+                                                   const int32_t* __restrict__ hpos, const double* __restrict__ hq,
+                                                   const double* __restrict__ ht, int64_t n, double* q, double* t) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        double qn[4], tn[3];
+        if (seg_head(depth, v)) {
+            ld_pose(hq, ht, hpos[v] - 1, qn, tn);
+        } else {
+            double qs[4], ts[3], qv[4], tv[3];
+            ld_pose(hq, ht, hpos[seg_p[v]] - 1, qs, ts);
+            ld_pose(q, t, v, qv, tv);
+            se3_compose(qs, ts, qv, tv, qn, tn);
+        }
+        st_pose(q, t, v, qn, tn);
     }
 }
 
@@ -385,23 +515,56 @@ cudaError_t launch_slot_owner(const int32_t* ptr, int64_t n, int32_t* owner, cud
     return cudaGetLastError();
 }
 
-cudaError_t launch_odometry(const int32_t* pedge, const int32_t* par, int max_rounds, int32_t* flag,
-                            const int32_t* edge_slot, const double* qe64, const double* te64, int64_t n,
-                            int32_t* par_tmp, double* q, double* t, double* q_tmp, double* t_tmp, cudaStream_t st) {
+size_t odometry_scratch_bytes(int64_t n) {
+    return (size_t)n * (8 * sizeof(int32_t) + 14 * sizeof(double)) + (size_t)((n + 1023) / 1024 + 8) * sizeof(int32_t) +
+           256;
+}
+
+cudaError_t launch_odometry(const int32_t* pedge, const int32_t* par, const int32_t* edge_slot, const double* qe64,
+                            const double* te64, int64_t n, void* scratch, double* q, double* t, double* q_tmp,
+                            double* t_tmp, cudaStream_t st) {
     cudaError_t e;
-    k_odo_steps<<<grid_of(n), 256, 0, st>>>(pedge, edge_slot, qe64, te64, n, q, t);
-    // rounds in pairs (par_tmp, q_tmp, t_tmp then back into par, q, t);
-    // the second of a pair raises *flag while a parent is left
-    int32_t* par_w = const_cast<int32_t*>(par);
-    for (int r = 0; r < max_rounds; r += 2) {
-        if ((e = cudaMemsetAsync(flag, 0, sizeof(int32_t), st))) return e;
-        k_odo_jump<<<grid_of(n), 256, 0, st>>>(par_w, q, t, n, par_tmp, q_tmp, t_tmp, nullptr);
-        k_odo_jump<<<grid_of(n), 256, 0, st>>>(par_tmp, q_tmp, t_tmp, n, par_w, q, t, flag);
-        int32_t more = 0;
-        if ((e = cudaMemcpyAsync(&more, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st))) return e;
-        if ((e = cudaStreamSynchronize(st))) return e;
-        if (!more) break;
-    }
+    double* hq[2] = {static_cast<double*>(scratch), static_cast<double*>(scratch) + 7 * n};
+    double* ht[2] = {hq[0] + 4 * n, hq[1] + 4 * n};
+    int32_t* ib = reinterpret_cast<int32_t*>(hq[1] + 7 * n);
+    int32_t* pp[2] = {ib, ib + n};  // depth pointers, then segment pointers
+    int32_t* dd[2] = {ib + 2 * n, ib + 3 * n};
+    int32_t* hp[2] = {ib + 4 * n, ib + 5 * n};
+    int32_t* hpos = ib + 6 * n;      // head flags, then their inclusive scan
+    int32_t* sums = ib + 7 * n;
+    const int g = grid_of(n);
+    // smallest even r with 2^r >= x
+    auto even_rounds = [](int64_t x) {
+        int r = 0;
+        while (((int64_t)1 << r) < x) ++r;
+        return r + (r & 1);
+    };
+    // depth of every vertex (integer pointer jumping, enough rounds for any depth < n)
+    k_depth_init<<<g, 256, 0, st>>>(par, n, pp[0], dd[0]);
+    const int rd = even_rounds(n);
+    for (int r = 0; r < rd; ++r)
+        k_depth_jump<<<g, 256, 0, st>>>(pp[r & 1], dd[r & 1], n, pp[(r + 1) & 1], dd[(r + 1) & 1]);
+    const int32_t* depth = dd[0];
+    // the steps, then the compositions inside the segments: a vertex is at
+    // most kSeg - 1 steps below its head (ends in q, t)
+    k_odo_steps<<<g, 256, 0, st>>>(pedge, edge_slot, qe64, te64, n, q, t);
+    k_seg_init<<<g, 256, 0, st>>>(par, depth, n, pp[0], hpos);
+    double* qb[2] = {q, q_tmp};
+    double* tb[2] = {t, t_tmp};
+    const int rs = even_rounds(kSeg - 1);
+    for (int r = 0; r < rs; ++r)
+        k_seg_jump<<<g, 256, 0, st>>>(pp[r & 1], qb[r & 1], tb[r & 1], depth, n, pp[(r + 1) & 1], qb[(r + 1) & 1],
+                                      tb[(r + 1) & 1]);
+    const int32_t* seg_p = pp[0];
+    // the heads, packed: their chains by pointer jumping, then every vertex's pose
+    if ((e = inclusive_scan_i32(hpos, n, sums, st))) return e;
+    k_head_init<<<g, 256, 0, st>>>(par, seg_p, depth, hpos, q, t, n, hp[0], hq[0], ht[0]);
+    const int32_t* count = hpos + n - 1;
+    const int rh = even_rounds(n / kSeg + 2);
+    for (int r = 0; r < rh; ++r)
+        k_head_jump<<<grid_of(n / kSeg + 1), 256, 0, st>>>(hp[r & 1], hq[r & 1], ht[r & 1], count, hp[(r + 1) & 1],
+                                                            hq[(r + 1) & 1], ht[(r + 1) & 1]);
+    k_seg_apply<<<g, 256, 0, st>>>(seg_p, depth, hpos, hq[0], ht[0], n, q, t);
     return cudaGetLastError();
 }
 
