@@ -115,7 +115,7 @@ __device__ __forceinline__ void step_a(const AdjDev<R>& A, const Coef<R>& c, int
     const V3<R> TB = {tb1.x - c.tb2 * zb1.x + c.beta2 * gs.x, tb1.y - c.tb2 * zb1.y + c.beta2 * gs.y,
                       tb1.z - c.tb2 * zb1.z + c.beta2 * gs.z};
     const V3<R> oz = {zb1.x - gs.x, zb1.y - gs.y, zb1.z - gs.z};
-    stv(A.gs, i, gs, a4b);
+    stv(A.gs_w, i, gs, a4b);
     stq(A.pb, i, PB);
     stq(A.qb, i, QB);
     stv(A.tb, i, TB, R(0));
@@ -569,13 +569,22 @@ cudaError_t launch_adj_seed(const GraphDev<R>& g, const AdjDev<R>& A, const Coef
 
 template <typename R>
 cudaError_t launch_adj_iteration(const GraphDev<R>& g, const AdjDev<R>& A, const AdjStep<R>& X, const Coef<R>& c,
-                                 const int32_t* out_src, int more, int block, cudaStream_t st) {
+                                 const int32_t* out_src, int more, int block, cudaStream_t st, cudaStream_t side,
+                                 cudaEvent_t fork, cudaEvent_t join) {
+    cudaError_t e;
     const int grid = grid_for(g.n, block);
     k_adj_t<R><<<grid, block, 0, st>>>(g, A, X, c);
     k_adj_q<R><<<grid, block, 0, st>>>(g, A, X, c);
     k_adj_p<R><<<grid, block, 0, st>>>(g, A, X, c);
-    if (g.m > 0) k_adj_grad<R><<<grid_for(g.m, 256), 256, 0, st>>>(g, A, X, out_src);
+    const bool split = side && g.m > 0 && A.gs_w != A.gs;
+    if (split) {
+        if ((e = cudaEventRecord(fork, st))) return e;
+        if ((e = cudaStreamWaitEvent(side, fork, 0))) return e;
+    }
+    if (g.m > 0) k_adj_grad<R><<<grid_for(g.m, 256), 256, 0, split ? side : st>>>(g, A, X, out_src);
+    if (split && (e = cudaEventRecord(join, side))) return e;
     k_adj_v<R><<<grid, block, 0, st>>>(g, A, X, c, more);
+    if (split && (e = cudaStreamWaitEvent(st, join, 0))) return e;
     return cudaGetLastError();
 }
 
@@ -620,7 +629,8 @@ cudaError_t launch_tape_arm(Ctrl* ctrl, long long iter, cudaStream_t st) {
     template cudaError_t launch_adj_seed<R>(const GraphDev<R>&, const AdjDev<R>&, const Coef<R>&, const R*, const R*, \
                                             int, cudaStream_t);                                                    \
     template cudaError_t launch_adj_iteration<R>(const GraphDev<R>&, const AdjDev<R>&, const AdjStep<R>&,             \
-                                                 const Coef<R>&, const int32_t*, int, int, cudaStream_t);          \
+                                                 const Coef<R>&, const int32_t*, int, int, cudaStream_t,           \
+                                                 cudaStream_t, cudaEvent_t, cudaEvent_t);                          \
     template cudaError_t launch_adj_edges<R>(const double*, const double*, int64_t, R*, R*, cudaStream_t);        \
     template cudaError_t launch_keep_pk<R>(const Ctrl*, const R*, const R*, R*, int64_t, int, cudaStream_t);
 

@@ -124,6 +124,11 @@ struct pradmm_s {
     // the reverse sweeps of the current one run (fork / join by events)
     cudaStream_t adj_stream = nullptr;
     cudaEvent_t adj_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    // the per-edge gradient sweep of a reverse iteration runs on a side
+    // stream beside the sweep that starts the next (fork / join events)
+    cudaStream_t adj_side = nullptr;
+    cudaEvent_t adj_fj[2] = {nullptr, nullptr};
+    void* adj_gs2 = nullptr;           // the second gs buffer (4 n reals)
     cudaGraphExec_t adj_exec = nullptr;  // reverse pass of the current tape geometry
     // optional per-iteration residual trace (pradmm_set_trace): a device ring
     double* trace_d = nullptr;
@@ -532,6 +537,9 @@ void free_all(pradmm_s* h) {
     for (cudaEvent_t& ev : h->adj_ev)
         if (ev) cudaEventDestroy(ev);
     if (h->adj_stream) cudaStreamDestroy(h->adj_stream);
+    for (cudaEvent_t& ev : h->adj_fj)
+        if (ev) cudaEventDestroy(ev);
+    if (h->adj_side) cudaStreamDestroy(h->adj_side);
     if (h->trace_d) cudaFree(h->trace_d);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
 }
@@ -750,7 +758,8 @@ pradmm_status launch_iters_plain(pradmm_s* h, long long iters) {
 
 // One iteration per pass of a device-side while loop (the last CTA of the
 // s/z + p sweep sets the condition).  record: the reverse-mode recording
-// loop, whose body ends with the checkpoint copy (scalar Sigma only).
+// loop (scalar Sigma only), whose s/z + p sweep also writes the tape slots;
+// with inertia a copy kernel after it takes the block with p^{k-1}.
 template <typename R>
 pradmm_status ensure_graph(pradmm_s* h, bool record = false) {
     if (record ? h->rec_ready : h->graph_ready) return PRADMM_OK;
@@ -781,8 +790,13 @@ pradmm_status ensure_graph(pradmm_s* h, bool record = false) {
         if (record && h->rec_keep)
             e6 = pradmm::launch_keep_pk<R>(h->ctrl, S.p[0], S.p[1], static_cast<R*>(h->pm1), h->n, h->grids[3],
                                            h->stream);
+        // scalar recording: the s/z + p sweep writes the tape slots itself;
+        // the inertial one copies the block (with p^{k-1}) after it
+        const bool fused = record && h->prm.inertia == 0.0;
+        if (fused) L.tape = h->tape_rec;
         e3 = pradmm::launch_sp<R>(g, S, c, L);
-        if (record) e5 = pradmm::launch_tape_copy(h->tape_rec, h->ctrl, h->state_block, h->grids[3], h->stream);
+        if (record && !fused)
+            e5 = pradmm::launch_tape_copy(h->tape_rec, h->ctrl, h->state_block, h->grids[3], h->stream);
     }
     cudaGraph_t captured = nullptr;
     cudaError_t e4 = cudaStreamEndCapture(h->stream, &captured);
@@ -1085,7 +1099,9 @@ pradmm_status adjoint_record(pradmm_s* h, int32_t iters, int32_t ckpt_every) {
             const auto g = h->gdev<R>();
             const auto S = h->sdev<R>();
             const auto c = h->coef<R>();
-            const auto L = h->launch(false);
+            auto L = h->launch(false);
+            const bool fused = h->prm.inertia == 0.0;
+            if (fused) L.tape = h->tape_rec;
             for (int k = 0; k < iters; ++k) {
                 CU(pradmm::launch_q<R>(g, S, c, L));
                 CU(pradmm::launch_t<R>(g, S, c, L));
@@ -1093,7 +1109,7 @@ pradmm_status adjoint_record(pradmm_s* h, int32_t iters, int32_t ckpt_every) {
                     CU(pradmm::launch_keep_pk<R>(h->ctrl, S.p[0], S.p[1], static_cast<R*>(h->pm1), h->n, h->grids[3],
                                                  h->stream));
                 CU(pradmm::launch_sp<R>(g, S, c, L));
-                CU(pradmm::launch_tape_copy(h->tape_rec, h->ctrl, h->state_block, h->grids[3], h->stream));
+                if (!fused) CU(pradmm::launch_tape_copy(h->tape_rec, h->ctrl, h->state_block, h->grids[3], h->stream));
             }
         }
     }
@@ -1118,8 +1134,11 @@ pradmm_status ensure_adjoint(pradmm_s* h) {
         ST(dalloc(h, &h->out_src_d, std::max<size_t>((size_t)m, 1)));
         ST(dalloc(h, &h->adj_stage, std::max<size_t>(9 * (size_t)m, 21 * (size_t)n)));
         ST(dalloc(h, &h->tape_ctrl, 1));
+        ST(valloc(h, &h->adj_gs2, 4 * (size_t)n));
         CU(cudaStreamCreateWithFlags(&h->adj_stream, cudaStreamNonBlocking));
+        CU(cudaStreamCreateWithFlags(&h->adj_side, cudaStreamNonBlocking));
         for (cudaEvent_t& ev : h->adj_ev) CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        for (cudaEvent_t& ev : h->adj_fj) CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
         CU(pradmm::launch_slot_owner(h->out_ptr, n, h->out_src_d, h->stream));
         R* b = static_cast<R*>(h->adj);
         R* eq = b + 13 * 4 * n + pad4(n);
@@ -1137,6 +1156,7 @@ pradmm::AdjDev<R> adj_dev(pradmm_s* h) {
     pradmm::AdjDev<R> A;
     R** v[13] = {&A.gs, &A.gt, &A.gq, &A.pb, &A.qb, &A.tb, &A.ub, &A.op, &A.oq, &A.ot, &A.os, &A.ol, &A.oz};
     for (int k = 0; k < 13; ++k) *v[k] = b + 4 * n * k;
+    A.gs_w = A.gs;  // enqueue_reverse alternates it with adj_gs2
     A.a2b = b + 4 * n * 13;
     A.eq = A.a2b + pad4(n);  // 4-real records need 16-byte alignment
     A.ek = A.eq + 4 * m;
@@ -1177,7 +1197,20 @@ cudaError_t enqueue_reverse(pradmm_s* h, const pradmm::AdjDev<R>& A) {
     } while (0)
     const bool inert = slot_inert(h);  // slots carry x^{k-1}
     const auto SK = slot_state<R>(tape_slot(h, nck - 1), n, inert);
-    RQ(pradmm::launch_adj_seed<R>(g, A, c, SK.s, SK.z, h->block, st));
+    // gs of iteration k lives in gsb[k & 1]: step A of iteration k - 1 (in the
+    // sweep that ends iteration k) writes the other buffer
+    R* gsb[2] = {A.gs, static_cast<R*>(h->adj_gs2)};
+    auto adj_at = [&](long long k) {
+        pradmm::AdjDev<R> a = A;
+        a.gs = gsb[k & 1];
+        a.gs_w = gsb[(k - 1) & 1];
+        return a;
+    };
+    {
+        pradmm::AdjDev<R> a = A;
+        a.gs_w = gsb[(h->tape_k0 + K - 1) & 1];
+        RQ(pradmm::launch_adj_seed<R>(g, a, c, SK.s, SK.z, h->block, st));
+    }
     const bool two = nck - 1 > 1 && C > 1;
     cudaStream_t st2 = two ? h->adj_stream : st;
     cudaEvent_t* ev_rc = h->adj_ev;       // recomputation of a segment done (by parity)
@@ -1257,7 +1290,8 @@ cudaError_t enqueue_reverse(pradmm_s* h, const pradmm::AdjDev<R>& A) {
                 X.pp = ci > 0 ? static_cast<const R*>(slot_state<R>(tape_slot(h, ci - 1), n, false).p[(k - 1) & 1])
                               : X.pc;
             }
-            RQ(pradmm::launch_adj_iteration<R>(g, A, X, c, h->out_src_d, (ci == 0 && j == 0) ? 0 : 1, h->block, st));
+            RQ(pradmm::launch_adj_iteration<R>(g, adj_at(k), X, c, h->out_src_d, (ci == 0 && j == 0) ? 0 : 1, h->block,
+                                               st, h->adj_side, h->adj_fj[0], h->adj_fj[1]));
         }
         if (two) RQ(cudaEventRecord(ev_rev[ci & 1], st));
     }

@@ -523,9 +523,12 @@ struct PEdge {
 // INERT (with the s-block): the proximal anchors are s^k + theta (s^k - s^{k-1})
 // (S.sprev) and, for the next p-block, p^{k+1} + theta (p^{k+1} - p^k), p^k being
 // the vertex's value in pn before it is overwritten.
-template <typename R, bool WITH_S, bool PIPE = false, bool NC = false, bool INERT = false>
+// REC with tape != nullptr: vertex i's rows of the state after this
+// iteration (t, s, q, both p buffers, lam, z) also go to `tape`, a copy of
+// the state block's layout.
+template <typename R, bool WITH_S, bool PIPE = false, bool NC = false, bool INERT = false, bool REC = false>
 __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R>& S, const Coef<R>& c, const R* pc,
-                                          R* pn, int64_t i, Acc<R>& adz, Ctrl* ctrl) {
+                                          R* pn, int64_t i, Acc<R>& adz, Ctrl* ctrl, R* tape = nullptr) {
     const R4<R> sr = IO<R>::ld(S.s, i);  // (s_i, 1/A_2)
     const R4<R> qr = IO<R>::ld(S.q, i);
     const R4<R> pr = IO<R>::ld(pc, i);
@@ -581,6 +584,11 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
         IO<R>::st(S.s, i, sx, sy, sz, sr.d);
         IO<R>::st(S.z, i, zx, zy, zz, inv);
         if (INERT) IO<R>::st(S.sprev, i, sr.a, sr.b, sr.c, sr.d);
+        if (REC && tape) {
+            IO<R>::st(tape, i, tr.a, tr.b, tr.c, tr.d);  // t: the block's first array
+            IO<R>::st(tape + (S.s - S.t), i, sx, sy, sz, sr.d);
+            IO<R>::st(tape + (S.z - S.t), i, zx, zy, zz, inv);
+        }
         const R d0 = zx - zr.a, d1 = zy - zr.b, d2 = zz - zr.c;
         adz.add(d0 * d0 + d1 * d1 + d2 * d2);
         // move the p-block's out-edge term from s^{old} to s^{new}
@@ -605,6 +613,13 @@ __device__ __forceinline__ void sp_vertex(const GraphDev<R>& g, const StateDev<R
         [&](PEdge<R>& x) { x.ql = gat<R, NC>(S.q, x.l); },
         [&](const PEdge<R>& x) { axpy(v, R(2), qmul(asq<R>(x.ql), asq<R>(x.qk))); });
     p_normalise<R>(g, S, i, v, qr, lr, pr, pa, sx, sy, sz, c, pn, ctrl);
+    if (REC && tape) {
+        const R4<R> pv = IO<R>::ld(pn, i);  // this thread's own store
+        IO<R>::st(tape + (S.q - S.t), i, qr.a, qr.b, qr.c, qr.d);
+        IO<R>::st(tape + (S.lam - S.t), i, lr.a, lr.b, lr.c, lr.d);
+        IO<R>::st(tape + (pc - S.t), i, pr.a, pr.b, pr.c, pr.d);
+        IO<R>::st(tape + (pn - S.t), i, pv.a, pv.b, pv.c, pv.d);
+    }
 }
 
 // Out-edge terms of vertex i in F of Eq. (1) at (p, t), in double:

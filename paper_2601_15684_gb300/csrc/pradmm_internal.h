@@ -81,6 +81,8 @@ struct Coef {
     R theta = R(0);      // inertial extrapolation of the proximal anchors (0: plain)
 };
 
+struct TapeRec;
+
 struct Launch {
     int grid_p, grid_q, grid_t, grid_sp;  // CTAs of each sweep (fixed per handle)
     int pstride;              // partial slot stride (>= every grid)
@@ -94,6 +96,9 @@ struct Launch {
     int has_window;
     double* trace = nullptr;        // optional ring of e^k: iteration k writes trace[(k - 1) % trace_cap]
     long long trace_cap = 0;
+    // reverse-mode recording with scalar weights: the s/z + p sweep also
+    // writes each vertex's state into the tape slot of its iteration
+    const TapeRec* tape = nullptr;
 };
 
 template <typename R>
@@ -314,6 +319,9 @@ cudaError_t launch_batch_objective(const GraphDev<R>& g, const StateDev<R>& s, c
 template <typename R>
 struct AdjDev {
     R* gs;   // (gs, A_4bar): adjoint of the s-block numerator / A_4, and of A_4
+    R* gs_w; // where step A writes the next (earlier) iteration's gs: the other
+             // of two buffers by iteration parity, so that the gradient sweep of
+             // iteration k can still read its gs while step A of k - 1 runs
     R* gt;   // (gt, A_3bar)
     R* gq;   // gq = qbar / A_2
     R* a2b;  // n: A_2bar
@@ -346,10 +354,14 @@ template <typename R>
 cudaError_t launch_adj_seed(const GraphDev<R>& g, const AdjDev<R>& A, const Coef<R>& c, const R* s_K, const R* z_K,
                             int block, cudaStream_t st);
 // The reverse sweeps of iteration k (out_src: tail of each out-slot); `more`
-// = 1 starts iteration k-1.
+// = 1 starts iteration k-1.  With `side` (and the events fork, join) the
+// per-edge gradient sweep runs on that stream beside the sweep that starts
+// iteration k-1 (they share no written array: A.gs_w != A.gs), joined
+// before return; else everything runs on st in order.
 template <typename R>
 cudaError_t launch_adj_iteration(const GraphDev<R>& g, const AdjDev<R>& A, const AdjStep<R>& X, const Coef<R>& c,
-                                 const int32_t* out_src, int more, int block, cudaStream_t st);
+                                 const int32_t* out_src, int more, int block, cudaStream_t st,
+                                 cudaStream_t side = nullptr, cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
 template <typename R>
 cudaError_t launch_adj_edges(const double* qe64, const double* ka64, int64_t m, R* eq, R* ek, cudaStream_t st);
 cudaError_t launch_adj_scatter(const double* g_qe, const double* g_te, const double* g_ka, const int32_t* eidx,

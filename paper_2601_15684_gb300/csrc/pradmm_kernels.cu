@@ -102,7 +102,10 @@ __global__ void PRADMM_BOUNDS_T k_t(GraphDev<R> g, StateDev<R> S, Coef<R> c, Ctr
     if (threadIdx.x == 0) part[SLOT_DT * pstride + blockIdx.x] = st;
 }
 
-template <typename R, bool WITH_S, bool INERT = false>
+// REC (scalar-weight recording, WITH_S): the state after this iteration
+// goes to the tape slot of its iteration, if it has one (checkpoints and the
+// last segment's iterates), each thread writing its own vertex's rows.
+template <typename R, bool WITH_S, bool INERT = false, bool REC = false>
 __global__ void __launch_bounds__(256, PRADMM_MINB_SP) k_sp(GraphDev<R> g, StateDev<R> S, Coef<R> c, Launch L) {
     __shared__ double sh[32];
     Ctrl* ctrl = L.ctrl;
@@ -114,9 +117,20 @@ __global__ void __launch_bounds__(256, PRADMM_MINB_SP) k_sp(GraphDev<R> g, State
     const long long k = ctrl->iter;
     const R* pc = WITH_S ? S.p[(k + 1) & 1] : S.p[k & 1];  // p used by this sweep
     R* pn = WITH_S ? S.p[k & 1] : S.p[(k + 1) & 1];        // p computed ahead
+    R* tape = nullptr;
+    if (REC) {
+        const TapeRec* T = L.tape;
+        const long long d = k + 1 - T->k0;
+        long long slot = -1;
+        if (d > 0 && d <= T->K) {
+            if (d % T->C == 0 || d == T->K) slot = (d + T->C - 1) / T->C;  // a checkpoint
+            else if (d > T->d_last) slot = T->slot_last + (d - T->d_last) - 1;  // inside the last segment
+        }
+        if (slot >= 0) tape = reinterpret_cast<R*>(T->base + slot * T->slot_bytes);
+    }
     Acc<R> adz;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x)
-        sp_vertex<R, WITH_S, PRADMM_PIPE_SP != 0, PRADMM_NC != 0, INERT>(g, S, c, pc, pn, i, adz, ctrl);
+        sp_vertex<R, WITH_S, PRADMM_PIPE_SP != 0, PRADMM_NC != 0, INERT, REC>(g, S, c, pc, pn, i, adz, ctrl, tape);
     if (WITH_S) {
         const double sd = block_sum(adz.get(), sh);
         if (threadIdx.x == 0) L.part[SLOT_DZ * L.pstride + blockIdx.x] = sd;
@@ -248,6 +262,7 @@ cudaError_t launch_t(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& 
 template <typename R>
 cudaError_t launch_sp(const GraphDev<R>& g, const StateDev<R>& s, const Coef<R>& c, const Launch& L) {
     if (c.theta != R(0)) return launch_sweep(L, L.grid_sp, k_sp<R, true, true>, g, s, c, L);
+    if (L.tape) return launch_sweep(L, L.grid_sp, k_sp<R, true, false, true>, g, s, c, L);
     return launch_sweep(L, L.grid_sp, k_sp<R, true>, g, s, c, L);
 }
 
