@@ -488,12 +488,12 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
                                                        static_cast<float*>(h->out_te), static_cast<float*>(h->out_qk),
                                                        h->qe64, h->te64, h->ka64, h->om64, st);
         if (e == cudaSuccess)
-            e = h->fp64 ? pradmm::launch_pack_slots<double>(ie_d, m, q_d, t_d, k_d, w_d, static_cast<double*>(h->in_te),
-                                                            static_cast<double*>(h->in_qk), nullptr, nullptr, nullptr,
-                                                            nullptr, st)
-                        : pradmm::launch_pack_slots<float>(ie_d, m, q_d, t_d, k_d, w_d, static_cast<float*>(h->in_te),
-                                                           static_cast<float*>(h->in_qk), nullptr, nullptr, nullptr,
-                                                           nullptr, st);
+            e = h->fp64 ? pradmm::launch_pack_in<double>(ie_d, h->edge_slot_d, m, h->qe64, h->te64, h->ka64, h->om64,
+                                                         static_cast<double*>(h->in_te), static_cast<double*>(h->in_qk),
+                                                         st)
+                        : pradmm::launch_pack_in<float>(ie_d, h->edge_slot_d, m, h->qe64, h->te64, h->ka64, h->om64,
+                                                        static_cast<float*>(h->in_te), static_cast<float*>(h->in_qk),
+                                                        st);
         dev(e, "edge record packing");
     }
     dev(cudaMemsetAsync(h->zeros, 0, sizeof(double) * 4 * n, st), "memset");

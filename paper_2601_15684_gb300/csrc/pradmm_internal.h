@@ -203,6 +203,12 @@ template <typename R>
 cudaError_t launch_pack_slots(const int32_t* edge, int64_t slots, const double* q, const double* t, const double* ka,
                               const double* om, R* te_out, R* qk_out, double* qe64, double* te64, double* ka64,
                               double* om64, cudaStream_t st);
+// In-order records (te_out, qk_out per in-slot; ie: in-slot -> input edge)
+// gathered from the out-order FP64 copies that launch_pack_slots wrote.
+template <typename R>
+cudaError_t launch_pack_in(const int32_t* ie, const int32_t* edge_slot, int64_t slots, const double* qe64,
+                           const double* te64, const double* ka64, const double* om64, R* te_out, R* qk_out,
+                           cudaStream_t st);
 
 template <typename R>
 cudaError_t launch_pack4(const double* src, const int32_t* perm, R* dst, int64_t n, cudaStream_t st);

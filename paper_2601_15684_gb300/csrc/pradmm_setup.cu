@@ -56,6 +56,28 @@ __global__ void __launch_bounds__(256) k_pack_slots(const int32_t* __restrict__ 
     }
 }
 
+// In-order records from the out-order FP64 copies: in-slot k holds input edge
+// ie[k], whose out-slot is edge_slot[ie[k]]; the values are those k_pack_slots
+// formed there (the normalised q_e among them), so both orders hold the same
+// bits without a second normalisation.
+template <typename R>
+__global__ void __launch_bounds__(256) k_pack_in(const int32_t* __restrict__ ie, const int32_t* __restrict__ edge_slot,
+                                                 int64_t slots, const double* __restrict__ qe64,
+                                                 const double* __restrict__ te64, const double* __restrict__ ka64,
+                                                 const double* __restrict__ om64, R* __restrict__ te_out,
+                                                 R* __restrict__ qk_out) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < slots; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = edge_slot[ie[k]];
+        const double k_e = ka64[o];
+        te_out[4 * k] = R(te64[3 * o]);
+        te_out[4 * k + 1] = R(te64[3 * o + 1]);
+        te_out[4 * k + 2] = R(te64[3 * o + 2]);
+        te_out[4 * k + 3] = R(om64[o]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) qk_out[4 * k + c] = R(k_e * qe64[4 * o + c]);
+    }
+}
+
 // ---- CSR of one edge order on the device ------------------------------------
 // ptr[k + 1] counts the edges with key k; an inclusive scan of ptr[1 .. n]
 // turns the counts into row offsets; each edge takes a slot of its row by an
@@ -579,7 +601,18 @@ cudaError_t launch_pack_slots(const int32_t* edge, int64_t slots, const double* 
     return cudaGetLastError();
 }
 
+template <typename R>
+cudaError_t launch_pack_in(const int32_t* ie, const int32_t* edge_slot, int64_t slots, const double* qe64,
+                           const double* te64, const double* ka64, const double* om64, R* te_out, R* qk_out,
+                           cudaStream_t st) {
+    if (slots <= 0) return cudaSuccess;
+    k_pack_in<R><<<grid_of(slots), 256, 0, st>>>(ie, edge_slot, slots, qe64, te64, ka64, om64, te_out, qk_out);
+    return cudaGetLastError();
+}
+
 #define PRADMM_SETUP_INST(R)                                                                                     \
+    template cudaError_t launch_pack_in<R>(const int32_t*, const int32_t*, int64_t, const double*, const double*, \
+                                           const double*, const double*, R*, R*, cudaStream_t);                  \
     template cudaError_t launch_pack_slots<R>(const int32_t*, int64_t, const double*, const double*,             \
                                               const double*, const double*, R*, R*, double*, double*, double*,  \
                                               double*, cudaStream_t);
