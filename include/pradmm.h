@@ -122,8 +122,10 @@ void pradmm_default_params(pradmm_params* prm);
  * before anything indexes with them (ERR_INDEX, ERR_SELFLOOP, ERR_NONFINITE for
  * non-finite measurements or weights, ERR_ARG for weights <= 0,
  * ERR_QUATERNION; the error names the first failing edge in input order),
- * renormalises q_meas, sorts the edges by tail and by head and packs
- * structure-of-arrays device buffers.
+ * renormalises q_meas, sorts the edges by tail and by head, finds the
+ * spanning forest of pradmm_init_odometry (from the endpoints, while the
+ * measurements upload on a second stream) and packs structure-of-arrays
+ * device buffers.
  *   src, dst     m int32 edge endpoints (tail i, head j)
  *   q_meas       m x 4 relative rotations q_ij
  *   t_meas       m x 3 relative translations t_ij
@@ -167,7 +169,8 @@ pradmm_status pradmm_set_state_full_device(pradmm_t h, const double* p_d, const 
  * components, the lowest vertex of each component gets the identity, and the
  * others follow q_j = q_i q_ij, t_j = t_i + R(q_i) t_ij (Section 2).  Then as
  * pradmm_set_state.  (The paper starts from a chordal initialisation it does
- * not define.) */
+ * not define.)  The forest is found by pradmm_create; this call composes the
+ * poses along it on the device, in FP64. */
 pradmm_status pradmm_init_odometry(pradmm_t h);
 
 /* Schedule search: times `iters` >= 1 iterations from the current state at

@@ -71,6 +71,11 @@ struct pradmm_s {
     unsigned int* obj_ticket = nullptr;
     double* F_dev = nullptr;
     unsigned int* dbg_d = nullptr;  // index-checked builds: out-of-range count, last value
+    // the odometry start's spanning forest, found by create while the
+    // measurements upload: parent and tree-edge code per vertex
+    int32_t *forest_par = nullptr, *forest_pedge = nullptr;
+    cudaStream_t aux_stream = nullptr;  // create: the measurements' upload
+    cudaEvent_t aux_ev = nullptr;
     Ctrl* ctrl = nullptr;
     Ctrl* ctrl_h = nullptr;   // pinned mirror
 
@@ -362,6 +367,8 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
         c.take(&h->F_dev, 1);
         c.take(&h->dbg_d, 2);
         c.take(&h->ctrl, 1);
+        c.take(&h->forest_par, n);
+        c.take(&h->forest_pedge, n);
     };
     {
         Carve probe;
@@ -399,12 +406,20 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
         std::memset(h->ctrl_h, 0, sizeof(Ctrl));
     }
     // ---- the graph on the device: the caller's arrays go up once; both CSR
-    // orders (input order inside a vertex), the iteration-invariant scalar
-    // block matrices (Appendix B) and the per-slot edge records are built there ----
-    const int64_t nb = (n + 1023) / 1024;
+    // orders (input order inside a vertex), the odometry start's spanning
+    // forest, the iteration-invariant scalar block matrices (Appendix B) and
+    // the per-slot edge records are built there.  The endpoints go first; the
+    // structure (CSR, forest) is built from them while the measurements
+    // upload on a second stream ----
+    if (!h->aux_stream) {
+        CU(cudaStreamCreateWithFlags(&h->aux_stream, cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&h->aux_ev, cudaEventDisableTiming));
+    }
+    const int64_t nb = (std::max(n, m) + 1023) / 1024;
+    const size_t fs = pradmm::forest_scratch_ints(n, m) * sizeof(int32_t);
     const size_t raw = (size_t)m * (4 + 3) * sizeof(double) + (kappa ? (size_t)m * sizeof(double) : 0) +
                        (omega ? (size_t)m * sizeof(double) : 0) + 3 * (size_t)m * sizeof(int32_t) +
-                       (size_t)(n + nb + 8) * sizeof(int32_t);
+                       (size_t)(n + nb + 8) * sizeof(int32_t) + fs + 16;
     char* tmp = nullptr;
     cudaError_t e = cudaMalloc(&tmp, raw);
     if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? PRADMM_ERR_NOMEM : PRADMM_ERR_CUDA,
@@ -419,29 +434,49 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
     int32_t* fill = ie_d + m;
     int32_t* sums = fill + n;
     int32_t* first_bad = sums + nb + 4;
+    int32_t* fscratch = first_bad + 4;
     cudaStream_t st = h->stream;
     pradmm_status ps = PRADMM_OK;
     const cudaMemcpyKind kind = device_arrays ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    auto up = [&](void* d, const void* s, size_t bytes) {
-        if (ps == PRADMM_OK && bytes > 0 && (e = cudaMemcpyAsync(d, s, bytes, kind, st)) != cudaSuccess)
+    auto up = [&](void* d, const void* s, size_t bytes, cudaStream_t on) {
+        if (ps == PRADMM_OK && bytes > 0 && (e = cudaMemcpyAsync(d, s, bytes, kind, on)) != cudaSuccess)
             ps = fail(PRADMM_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
     };
     auto dev = [&](cudaError_t r, const char* what) {
         if (ps == PRADMM_OK && r != cudaSuccess) ps = fail(PRADMM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(r));
     };
-    up(q_d, q_meas, sizeof(double) * 4 * m);
-    up(t_d, t_meas, sizeof(double) * 3 * m);
-    if (kappa) up(k_d, kappa, sizeof(double) * m);
-    if (omega) up(w_d, omega, sizeof(double) * m);
-    up(src_d, src, sizeof(int32_t) * m);
-    up(dst_d, dst, sizeof(int32_t) * m);
-    // ---- validation (never trust the caller's graph) on the uploaded arrays;
-    // nothing indexes with the endpoints before it has passed.  The first
-    // failing edge is re-checked on the host for its message ----
+    // the endpoints, checked (out-of-range ones zeroed, so nothing below
+    // indexes out of bounds; the error is reported after the full checks)
+    const int32_t m32 = (int32_t)m;
+    up(src_d, src, sizeof(int32_t) * m, st);
+    up(dst_d, dst, sizeof(int32_t) * m, st);
+    if (m > 0) {
+        dev(cudaMemcpyAsync(first_bad, &m32, sizeof(int32_t), cudaMemcpyHostToDevice, st), "upload");
+        dev(pradmm::launch_check_ends(src_d, dst_d, n, m, first_bad, st), "validation");
+    }
+    // the measurements on the second stream
+    dev(cudaEventRecord(h->aux_ev, st), "upload");
+    dev(cudaStreamWaitEvent(h->aux_stream, h->aux_ev, 0), "upload");
+    up(q_d, q_meas, sizeof(double) * 4 * m, h->aux_stream);
+    up(t_d, t_meas, sizeof(double) * 3 * m, h->aux_stream);
+    if (kappa) up(k_d, kappa, sizeof(double) * m, h->aux_stream);
+    if (omega) up(w_d, omega, sizeof(double) * m, h->aux_stream);
+    dev(cudaEventRecord(h->aux_ev, h->aux_stream), "upload");
+    // meanwhile the structure: both CSR orders and the spanning forest
+    if (ps == PRADMM_OK) {
+        dev(pradmm::build_csr_device(src_d, dst_d, n, m, h->out_ptr, h->out_edge_d, h->out_idx, h->edge_slot_d, fill,
+                                     sums, st), "out-edge CSR");
+        dev(pradmm::build_csr_device(dst_d, src_d, n, m, h->in_ptr, ie_d, h->in_idx, nullptr, fill, sums, st),
+            "in-edge CSR");
+        dev(pradmm::launch_iota(h->perm_d, n, st), "vertex order");
+        dev(pradmm::launch_forest(h->out_ptr, h->out_idx, h->out_edge_d, n, m, fscratch, h->forest_par,
+                                  h->forest_pedge, st), "spanning forest");
+    }
+    dev(cudaStreamWaitEvent(st, h->aux_ev, 0), "upload");
+    // ---- the full checks (never trust the caller's graph); the first failing
+    // edge is re-checked on the host, from the caller's arrays, for its message ----
     if (ps == PRADMM_OK && m > 0) {
         int32_t bad = (int32_t)m;
-        const int32_t m32 = (int32_t)m;
-        dev(cudaMemcpyAsync(first_bad, &m32, sizeof(int32_t), cudaMemcpyHostToDevice, st), "upload");
         dev(pradmm::launch_validate(src_d, dst_d, q_d, t_d, k_d, w_d, n, m, first_bad, st), "validation");
         dev(cudaMemcpyAsync(&bad, first_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st), "validation");
         dev(cudaStreamSynchronize(st), "validation");
@@ -450,8 +485,8 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
             int32_t a = 0, b = 0;
             double q4[4] = {0, 0, 0, 0}, t3[3] = {0, 0, 0}, ka = 1.0, om = 1.0;
             if (device_arrays) {
-                dev(cudaMemcpyAsync(&a, src_d + bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st), "download");
-                dev(cudaMemcpyAsync(&b, dst_d + bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st), "download");
+                dev(cudaMemcpyAsync(&a, src + bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st), "download");
+                dev(cudaMemcpyAsync(&b, dst + bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st), "download");
                 dev(cudaMemcpyAsync(q4, q_d + 4 * (int64_t)bad, sizeof(q4), cudaMemcpyDeviceToHost, st), "download");
                 dev(cudaMemcpyAsync(t3, t_d + 3 * (int64_t)bad, sizeof(t3), cudaMemcpyDeviceToHost, st), "download");
                 if (k_d) dev(cudaMemcpyAsync(&ka, k_d + bad, sizeof(double), cudaMemcpyDeviceToHost, st), "download");
@@ -469,17 +504,11 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
             if (ps == PRADMM_OK) ps = fail(PRADMM_ERR_ARG, "edge %lld is invalid", (long long)bad);
         }
     }
-    if (ps == PRADMM_OK) {
-        dev(pradmm::build_csr_device(src_d, dst_d, n, m, h->out_ptr, h->out_edge_d, h->out_idx, h->edge_slot_d, fill,
-                                     sums, st), "out-edge CSR");
-        dev(pradmm::build_csr_device(dst_d, src_d, n, m, h->in_ptr, ie_d, h->in_idx, nullptr, fill, sums, st),
-            "in-edge CSR");
+    if (ps == PRADMM_OK)
         dev(pradmm::launch_block_inv(h->out_ptr, h->out_edge_d, h->in_ptr, ie_d, n, t_d, k_d, w_d,
                                      h->prm.beta1 + h->prm.gamma[1], h->prm.beta2 + h->prm.gamma[2],
                                      h->prm.beta2 + h->prm.gamma[3], h->inv2_d, h->inv3_d, h->inv4_d, st),
             "block matrices");
-        dev(pradmm::launch_iota(h->perm_d, n, st), "vertex order");
-    }
     if (ps == PRADMM_OK && m > 0) {
         e = h->fp64 ? pradmm::launch_pack_slots<double>(h->out_edge_d, m, q_d, t_d, k_d, w_d,
                                                         static_cast<double*>(h->out_te), static_cast<double*>(h->out_qk),
@@ -502,6 +531,7 @@ pradmm_status build(pradmm_s* h, const int32_t* src, const int32_t* dst, const d
     dev(cudaMemsetAsync(h->dbg_d, 0, 2 * sizeof(unsigned int), st), "memset");
     e = cudaStreamSynchronize(st);
     if (ps == PRADMM_OK && e != cudaSuccess) ps = fail(PRADMM_ERR_CUDA, "set-up: %s", cudaGetErrorString(e));
+    cudaStreamSynchronize(h->aux_stream);  // the upload buffer is free of copies on every path
     cudaFree(tmp);
     return ps;
 }
@@ -539,6 +569,8 @@ void free_all(pradmm_s* h) {
     if (h->adj_stream) cudaStreamDestroy(h->adj_stream);
     for (cudaEvent_t& ev : h->adj_fj)
         if (ev) cudaEventDestroy(ev);
+    if (h->aux_ev) cudaEventDestroy(h->aux_ev);
+    if (h->aux_stream) cudaStreamDestroy(h->aux_stream);
     if (h->adj_side) cudaStreamDestroy(h->adj_side);
     if (h->trace_d) cudaFree(h->trace_d);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -1687,15 +1719,16 @@ pradmm_status pradmm_autotune(pradmm_t h, int32_t iters, int32_t* block_out) {
 
 // ---- odometry initialisation --------------------------------------------
 // The spanning forest by edge order (an edge joins when it links two
-// components), rooted at each component's lowest vertex, and the poses
-// composed along its paths: all on the device (pradmm_forest.cu, the
-// composition in pradmm_setup.cu), from the out-edge CSR.
+// components), rooted at each component's lowest vertex, is found by
+// pradmm_create on the device while the measurements upload
+// (pradmm_forest.cu); here the poses are composed along its paths
+// (pradmm_setup.cu).
 pradmm_status pradmm_init_odometry(pradmm_t h) {
     if (!h) return fail(PRADMM_ERR_ARG, "NULL handle");
-    const int64_t n = h->n, m = h->m;
-    // the forest's work space, then the composition's, in one region
-    const size_t work = std::max(pradmm::forest_scratch_ints(n, m) * sizeof(int32_t), pradmm::odometry_scratch_bytes(n));
-    const size_t bytes = (size_t)n * 14 * sizeof(double) + work + (size_t)2 * n * sizeof(int32_t) + 64;
+    const int64_t n = h->n;
+    // the spanning forest was found by create; the compositions along its paths
+    const size_t work = pradmm::odometry_scratch_bytes(n);
+    const size_t bytes = (size_t)n * 14 * sizeof(double) + work + 64;
     char* tmp = nullptr;
     cudaError_t e = cudaMalloc(&tmp, bytes);
     if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? PRADMM_ERR_NOMEM : PRADMM_ERR_CUDA,
@@ -1705,14 +1738,10 @@ pradmm_status pradmm_init_odometry(pradmm_t h) {
     double* q2 = t + 3 * n;
     double* t2 = q2 + 4 * n;
     char* ws = reinterpret_cast<char*>(t2 + 3 * n);
-    int32_t* pe_d = reinterpret_cast<int32_t*>(ws + work);
-    int32_t* par_d = pe_d + n;
     cudaStream_t st = h->stream;
     pradmm_status ps = PRADMM_OK;
-    if ((e = pradmm::launch_forest(h->out_ptr, h->out_idx, h->out_edge_d, n, m, reinterpret_cast<int32_t*>(ws), par_d,
-                                   pe_d, st)) != cudaSuccess ||
-        (e = pradmm::launch_odometry(pe_d, par_d, h->edge_slot_d, h->qe64, h->te64, n, ws, q, t, q2, t2, st)) !=
-            cudaSuccess)
+    if ((e = pradmm::launch_odometry(h->forest_pedge, h->forest_par, h->edge_slot_d, h->qe64, h->te64, n, ws, q, t,
+                                     q2, t2, st)) != cudaSuccess)
         ps = fail(PRADMM_ERR_CUDA, "odometry: %s", cudaGetErrorString(e));
     if (ps == PRADMM_OK) ps = set_state_any(h, q, q, t, t, nullptr, nullptr, true);
     e = cudaStreamSynchronize(st);

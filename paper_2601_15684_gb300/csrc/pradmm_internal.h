@@ -126,6 +126,10 @@ cudaError_t build_csr_device(const int32_t* key, const int32_t* other, int64_t n
 // failing edge.
 cudaError_t launch_validate(const int32_t* src, const int32_t* dst, const double* q, const double* t, const double* ka,
                             const double* om, int64_t n, int64_t m, int32_t* first_bad, cudaStream_t st);
+// The endpoint checks of launch_validate on their own (endpoints in [0, n),
+// no self-loop), lowering *first_bad; endpoints outside [0, n) are replaced
+// by 0 in place so that kernels indexing with them stay in bounds.
+cudaError_t launch_check_ends(int32_t* src, int32_t* dst, int64_t n, int64_t m, int32_t* first_bad, cudaStream_t st);
 // Inclusive scan of a[0, len) in place; sums holds (len + 1023) / 1024 ints.
 cudaError_t inclusive_scan_i32(int32_t* a, int64_t len, int32_t* sums, cudaStream_t st);
 // The odometry start's spanning forest (Kruskal by edge order, found by
@@ -134,7 +138,7 @@ cudaError_t inclusive_scan_i32(int32_t* a, int64_t len, int32_t* sums, cudaStrea
 // out_edge: input edge per slot): par[v] the parent (-1 for a root), pedge[v]
 // the tree edge e to it coded as for launch_odometry.  scratch:
 // forest_scratch_ints(n, m) ints.  Synchronises the stream (host reads of
-// the round counts).
+// the round counts).  pradmm_create runs it once per handle.
 size_t forest_scratch_ints(int64_t n, int64_t m);
 cudaError_t launch_forest(const int32_t* out_ptr, const int32_t* out_idx, const int32_t* out_edge, int64_t n,
                           int64_t m, int32_t* scratch, int32_t* par, int32_t* pedge, cudaStream_t st);

@@ -260,6 +260,24 @@ __global__ void __launch_bounds__(256) k_validate(const int32_t* __restrict__ sr
     }
 }
 
+// The endpoint checks alone, before the measurements have arrived: an edge
+// with an endpoint outside [0, n) or a self-loop lowers *first_bad, and an
+// endpoint outside [0, n) is replaced by 0, so the structure kernels that
+// follow (CSR, spanning forest) stay in bounds whatever the caller passed;
+// the handle is discarded when *first_bad < m after the full checks.
+__global__ void __launch_bounds__(256) k_check_ends(int32_t* src, int32_t* dst, int64_t n, int64_t m,
+                                                    int32_t* first_bad) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = src[e], b = dst[e];
+        const bool ia = a >= 0 && a < n, ib = b >= 0 && b < n;
+        if (!(ia && ib && a != b)) {
+            atomicMin(first_bad, (int32_t)e);
+            if (!ia) src[e] = 0;
+            if (!ib) dst[e] = 0;
+        }
+    }
+}
+
 // ---- odometry composition on the device -----------------------------------
 // The spanning forest (pradmm_forest.cu) gives every vertex its parent and the tree edge
 // to it; the pose of a vertex is the composition of the SE(3) steps along the
@@ -490,6 +508,12 @@ cudaError_t launch_validate(const int32_t* src, const int32_t* dst, const double
                             const double* om, int64_t n, int64_t m, int32_t* first_bad, cudaStream_t st) {
     if (m <= 0) return cudaSuccess;
     k_validate<<<grid_of(m), 256, 0, st>>>(src, dst, q, t, ka, om, n, m, first_bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_ends(int32_t* src, int32_t* dst, int64_t n, int64_t m, int32_t* first_bad, cudaStream_t st) {
+    if (m <= 0) return cudaSuccess;
+    k_check_ends<<<grid_of(m), 256, 0, st>>>(src, dst, n, m, first_bad);
     return cudaGetLastError();
 }
 
