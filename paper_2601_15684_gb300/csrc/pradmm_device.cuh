@@ -209,24 +209,52 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return r;
 }
 
+// N CTA totals at once (thread 0 gets them), each with block_sum's tree, so
+// each equals a block_sum of its own: sh holds N x 32 doubles.
+template <int N>
+__device__ __forceinline__ void block_sum_n(double* v, double* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = warp_sum(v[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < N; ++k) sh[32 * k + wid] = v[k];
+    __syncthreads();
+    if (wid == 0)
+#pragma unroll
+        for (int k = 0; k < N; ++k) v[k] = warp_sum(lane < nw ? sh[32 * k + lane] : 0.0);
+    __syncthreads();
+}
+
 // ---- residual e^{k+1} and stop decision (last CTA of the s/z + p sweep) ---------
 // Called by every CTA of the last sweep of an iteration after writing its
 // partials; the last CTA to arrive forms e^{k+1}, advances the iteration and
 // sets the stop state and the while-node condition.
-__device__ __forceinline__ void finish_iteration(Ctrl* ctrl, const Launch& L, double b1, double b2, double* sh) {
+__device__ __forceinline__ void finish_iteration(Ctrl* ctrl, const Launch& L, double b1, double b2) {
     __shared__ bool last;
-    __threadfence();
-    if (threadIdx.x == 0) last = (atomicAdd(&ctrl->ticket, 1u) == gridDim.x - 1);
+    // thread 0 wrote the CTA's partial: it publishes it before taking a ticket
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = (atomicAdd(&ctrl->ticket, 1u) == gridDim.x - 1);
+    }
     __syncthreads();
     if (!last) return;
     __threadfence();
     const int cnt[4] = {L.grid_q, L.grid_sp, L.grid_q, L.grid_t};  // slots DLAM, DZ, DQ, DT
     double tot[4];
+    // the four slots in one pass (each slot's terms in the same order and
+    // tree as a pass of its own)
+    {
+        __shared__ double sh4[4 * 32];
+        const int most = max(max(cnt[0], cnt[1]), max(cnt[2], cnt[3]));
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int b = threadIdx.x; b < most; b += blockDim.x)
 #pragma unroll
-    for (int sl = 0; sl < 4; ++sl) {
-        double v = 0.0;
-        for (int b = threadIdx.x; b < cnt[sl]; b += blockDim.x) v += __ldcg(L.part + sl * L.pstride + b);
-        tot[sl] = block_sum(v, sh);
+            for (int sl = 0; sl < 4; ++sl)
+                if (b < cnt[sl]) v[sl] += __ldcg(L.part + sl * L.pstride + b);
+        block_sum_n<4>(v, sh4);
+#pragma unroll
+        for (int sl = 0; sl < 4; ++sl) tot[sl] = v[sl];
     }
     if (threadIdx.x == 0) {
         const double dl = tot[SLOT_DLAM], dz = tot[SLOT_DZ], dq = tot[SLOT_DQ], dt = tot[SLOT_DT];

@@ -80,8 +80,10 @@ __global__ void __launch_bounds__(256, PRADMM_MINB_Q) k_q(GraphDev<R> g, StateDe
     Acc<R> adq, adl;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x)
         q_vertex<R, PRADMM_PIPE_Q != 0, PRADMM_NC != 0, INERT>(g, S, c, pn, i, adq, adl);
-    const double sq = block_sum(adq.get(), sh);
-    const double sl = block_sum(adl.get(), sh);
+    __shared__ double sh2[2 * 32];
+    double v[2] = {adq.get(), adl.get()};
+    block_sum_n<2>(v, sh2);  // both CTA totals in one reduction
+    const double sq = v[0], sl = v[1];
     if (threadIdx.x == 0) {
         part[SLOT_DQ * pstride + blockIdx.x] = sq;
         part[SLOT_DLAM * pstride + blockIdx.x] = sl;
@@ -134,7 +136,7 @@ __global__ void __launch_bounds__(256, PRADMM_MINB_SP) k_sp(GraphDev<R> g, State
     if (WITH_S) {
         const double sd = block_sum(adz.get(), sh);
         if (threadIdx.x == 0) L.part[SLOT_DZ * L.pstride + blockIdx.x] = sd;
-        finish_iteration(ctrl, L, c.b1d, c.b2d, sh);
+        finish_iteration(ctrl, L, c.b1d, c.b2d);
     }
 }
 

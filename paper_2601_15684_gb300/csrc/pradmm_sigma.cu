@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(256) k_s_sig(GraphDev<R> g, StateDev<R> S, Coe
         s_sig_vertex<R, INERT>(g, S, c, sg, pn, i, adz);
     const double sd = block_sum(adz.get(), sh);
     if (threadIdx.x == 0) L.part[SLOT_DZ * L.pstride + blockIdx.x] = sd;
-    finish_iteration(ctrl, L, c.b1d, c.b2d, sh);
+    finish_iteration(ctrl, L, c.b1d, c.b2d);
 }
 
 // F of Eq. (1) with Sigma-weighted norms at (p^k, t^k), in double.
