@@ -39,7 +39,7 @@ using namespace dev;
 
 // Thread group that owns one graph: the whole CTA or one warp.
 struct CtaGroup {
-    double* sh;  // 32 doubles of shared scratch for the reductions
+    double* sh;  // 4 x 32 doubles of shared scratch for the reductions
     __device__ int rank() const { return threadIdx.x; }
     __device__ int size() const { return blockDim.x; }
     __device__ void sync() const { __syncthreads(); }
@@ -52,8 +52,15 @@ struct CtaGroup {
         __syncthreads();
         return out;
     }
+    // the four residual parts in one CTA reduction (each with sum()'s tree),
+    // then broadcast: 4 barriers instead of 16
     __device__ void sum4(double* v) const {
-        for (int k = 0; k < 4; ++k) v[k] = sum(v[k]);
+        block_sum_n<4>(v, sh);
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 4; ++k) sh[k] = v[k];
+        __syncthreads();
+        for (int k = 0; k < 4; ++k) v[k] = sh[k];
+        __syncthreads();
     }
 };
 
@@ -77,7 +84,7 @@ struct WarpGroup {
 // only after the barrier of the next sum has passed.
 constexpr int kMaxCluster = 16;
 struct ClusterGroup {
-    double* sh;       // 32 doubles of shared scratch (CTA reductions)
+    double* sh;       // 4 x 32 doubles of shared scratch (CTA reductions)
     double* slots;    // 2 * kMaxCluster * 4 doubles in this CTA's shared memory
     int* bank;        // this CTA's bank toggle (shared)
     __device__ int rank() const {
@@ -88,8 +95,8 @@ struct ClusterGroup {
     // four sums with one exchange
     __device__ void sum4(double* v) const {
         auto cl = cooperative_groups::this_cluster();
-        double cta[4];
-        for (int k = 0; k < 4; ++k) cta[k] = block_sum(v[k], sh);  // thread 0 holds the CTA totals
+        double cta[4] = {v[0], v[1], v[2], v[3]};
+        block_sum_n<4>(cta, sh);  // thread 0 holds the CTA totals
         const int b = *bank;
         const unsigned me = cl.block_rank(), nb = cl.num_blocks();
         if (threadIdx.x == 0)
@@ -194,7 +201,7 @@ struct PlainSolve {
 // pradmm_batch_sigma.cu).
 template <typename P, int WPB>
 __global__ void __launch_bounds__(WPB * 32) k_batch(P solve, BatchDev b, Ctrl* ctrl) {
-    __shared__ double sh[32];
+    __shared__ double sh[4 * 32];
     __shared__ int s_item;
     const CtaGroup cta{sh};
     const WarpGroup warp;
@@ -220,7 +227,7 @@ __global__ void __launch_bounds__(WPB * 32) k_batch(P solve, BatchDev b, Ctrl* c
 // queue is empty every CTA takes the CTA and warp-pack items as k_batch does.
 template <typename P, int WPB>
 __global__ void __launch_bounds__(WPB * 32) k_batch_cl(P solve, BatchDev b, Ctrl* ctrl) {
-    __shared__ double sh[32];
+    __shared__ double sh[4 * 32];
     __shared__ double slots[2 * kMaxCluster * 4];
     __shared__ int s_item, s_bank;
     auto cl = cooperative_groups::this_cluster();
