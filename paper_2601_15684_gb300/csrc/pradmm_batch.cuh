@@ -62,6 +62,8 @@ struct CtaGroup {
         for (int k = 0; k < 4; ++k) v[k] = sh[k];
         __syncthreads();
     }
+    // after sum4: its barriers already follow every write of the iteration
+    __device__ void sync_after_sum() const {}
 };
 
 struct WarpGroup {
@@ -75,6 +77,8 @@ struct WarpGroup {
     __device__ void sum4(double* v) const {
         for (int k = 0; k < 4; ++k) v[k] = sum(v[k]);
     }
+    // shuffles do not order memory: a warp barrier after the sums
+    __device__ void sync_after_sum() const { __syncwarp(); }
 };
 
 // The CTAs of one thread-block cluster.  A sum is each CTA's fixed-tree total
@@ -114,6 +118,8 @@ struct ClusterGroup {
         if (threadIdx.x == 0) *bank = b ^ 1;
         __syncthreads();
     }
+    // after sum4: its cluster barrier already follows every write of the iteration
+    __device__ void sync_after_sum() const {}
 };
 
 __device__ __forceinline__ unsigned long long clock_ns() {
@@ -157,7 +163,7 @@ __device__ void solve_graph(const G& grp, const GraphDev<R>& g, const StateDev<R
         e = dl / c.b1d + dz / c.b2d + c.b1d * dq + c.b2d * dt;
         ++k;
         if (k == 1) e1 = e;
-        grp.sync();
+        grp.sync_after_sum();
         if (!isfinite(e)) {
             status = PRADMM_BATCH_NONFINITE;
             break;

@@ -63,7 +63,7 @@ __device__ void solve_graph_sigma(const G& grp, const GraphDev<R>& g, const Stat
         e = d4[0] / c.b1d + d4[1] / c.b2d + c.b1d * d4[2] + c.b2d * d4[3];
         ++k;
         if (k == 1) e1 = e;
-        grp.sync();
+        grp.sync_after_sum();
         if (!isfinite(e)) {
             status = PRADMM_BATCH_NONFINITE;
             break;
