@@ -173,6 +173,14 @@ pradmm_status pradmm_set_state_full_device(pradmm_t h, const double* p_d, const 
  * poses along it on the device, in FP64. */
 pradmm_status pradmm_init_odometry(pradmm_t h);
 
+/* The spanning forest of pradmm_init_odometry, copied to host arrays of n
+ * int32 each: parent[v] is v's forest parent (-1 for the root of a
+ * component, its lowest vertex); pedge[v] the forest edge e joining v to it,
+ * coded e when v is the edge's head (dst[e] == v) and -(e + 2) when v is its
+ * tail (src[e] == v), -1 for a root.  Edge indices are input order.  NULL
+ * arguments are ERR_ARG.  Synchronises the handle's stream. */
+pradmm_status pradmm_odometry_forest(pradmm_t h, int32_t* parent, int32_t* pedge);
+
 /* Schedule search: times `iters` >= 1 iterations from the current state at
  * each CTA size of the sweeps (32, 64, 128 and 256 threads; a thread per
  * vertex), keeps the fastest and restores the state as

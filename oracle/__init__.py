@@ -226,6 +226,8 @@ def lib():
             L.orc_lagrangian.argtypes = [i64, i64, i32, i32, d, d, d, d, P(Params), d, d, d, d, d, d]
             L.orc_init_odometry.restype = ctypes.c_int
             L.orc_init_odometry.argtypes = [i64, i64, i32, i32, d, d, d, d]
+            L.orc_odometry_forest.restype = ctypes.c_int
+            L.orc_odometry_forest.argtypes = [i64, i64, i32, i32, i32, i32]
             L.orc_adjoint.restype = ctypes.c_int
             L.orc_adjoint.argtypes = [i64, i64, i32, i32, d, d, d, d, P(Params), i64, d, d, d, d, d, d, d, d,
                                       d, d, d, d, d, d, d]
@@ -293,6 +295,18 @@ def init_odometry(g):
     if rc != 0:
         raise MemoryError("oracle init_odometry")
     return q, t
+
+
+def odometry_forest(g):
+    """The spanning forest of init_odometry: (parent, tree-edge code) per
+    vertex, int32; parent -1 for a root; the code is e when the vertex is the
+    head of its tree edge e, -(e + 2) when it is the tail, -1 for a root."""
+    keep, a = _graph_args(g)
+    par = np.zeros(g.n, dtype=np.int32)
+    pedge = np.zeros(g.n, dtype=np.int32)
+    if lib().orc_odometry_forest(*a[:4], _i(par), _i(pedge)) != 0:
+        raise MemoryError("oracle odometry_forest")
+    return par, pedge
 
 
 def iterate(g, params: Params, state: dict, iters: int = 1):

@@ -105,8 +105,12 @@ static int64_t uf_find(int64_t* par, int64_t x) {
     return x;
 }
 
-int orc_init_odometry(int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
-                      const double* qe, const double* te, double* q, double* t) {
+/* The walk of orc_init_odometry; with q == NULL no pose is composed.  par,
+ * pedge (optional): each vertex's forest parent (-1 for a root) and the tree
+ * edge e to it, coded e when the vertex is the edge's head and -(e + 2) when
+ * it is its tail (-1 for a root). */
+static int odometry_walk(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, const double* qe,
+                         const double* te, double* q, double* t, int32_t* parent, int32_t* pedge) {
     int64_t* par = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
     int64_t* deg = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
     int64_t* tree = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
@@ -139,8 +143,11 @@ int orc_init_odometry(int64_t n, int64_t m, const int32_t* src, const int32_t* d
     for (int64_t r = 0; r < n; ++r) {
         if (done[r]) continue;
         /* r is the lowest vertex of a component not yet reached */
-        q[4 * r] = 1.0; q[4 * r + 1] = q[4 * r + 2] = q[4 * r + 3] = 0.0;
-        t[3 * r] = t[3 * r + 1] = t[3 * r + 2] = 0.0;
+        if (q) {
+            q[4 * r] = 1.0; q[4 * r + 1] = q[4 * r + 2] = q[4 * r + 3] = 0.0;
+            t[3 * r] = t[3 * r + 1] = t[3 * r + 2] = 0.0;
+        }
+        if (parent) { parent[r] = -1; pedge[r] = -1; }
         done[r] = 1;
         int64_t head = 0, tail = 0;
         queue[tail++] = r;
@@ -151,19 +158,25 @@ int orc_init_odometry(int64_t n, int64_t m, const int32_t* src, const int32_t* d
                 int64_t a = src[e], b = dst[e];
                 if (a == v && !done[b]) {
                     /* q_b = q_a q_e ; t_b = t_a + R(q_a) t_e */
-                    double rt[3];
-                    qmul(&q[4 * a], &qe[4 * e], &q[4 * b]);
-                    qrotate(&q[4 * a], &te[3 * e], rt);
-                    for (int c = 0; c < 3; ++c) t[3 * b + c] = t[3 * a + c] + rt[c];
+                    if (q) {
+                        double rt[3];
+                        qmul(&q[4 * a], &qe[4 * e], &q[4 * b]);
+                        qrotate(&q[4 * a], &te[3 * e], rt);
+                        for (int c = 0; c < 3; ++c) t[3 * b + c] = t[3 * a + c] + rt[c];
+                    }
+                    if (parent) { parent[b] = (int32_t)a; pedge[b] = (int32_t)e; }
                     done[b] = 1;
                     queue[tail++] = b;
                 } else if (b == v && !done[a]) {
                     /* q_a = q_b q_e^* ; t_a = t_b - R(q_a) t_e */
-                    double qc[4], rt[3];
-                    qconj(&qe[4 * e], qc);
-                    qmul(&q[4 * b], qc, &q[4 * a]);
-                    qrotate(&q[4 * a], &te[3 * e], rt);
-                    for (int c = 0; c < 3; ++c) t[3 * a + c] = t[3 * b + c] - rt[c];
+                    if (q) {
+                        double qc[4], rt[3];
+                        qconj(&qe[4 * e], qc);
+                        qmul(&q[4 * b], qc, &q[4 * a]);
+                        qrotate(&q[4 * a], &te[3 * e], rt);
+                        for (int c = 0; c < 3; ++c) t[3 * a + c] = t[3 * b + c] - rt[c];
+                    }
+                    if (parent) { parent[a] = (int32_t)b; pedge[a] = (int32_t)(-(e + 2)); }
                     done[a] = 1;
                     queue[tail++] = a;
                 }
@@ -172,6 +185,18 @@ int orc_init_odometry(int64_t n, int64_t m, const int32_t* src, const int32_t* d
     }
     free(par); free(deg); free(tree); free(adj); free(fill); free(done); free(queue);
     return 0;
+}
+
+int orc_init_odometry(int64_t n, int64_t m, const int32_t* src, const int32_t* dst,
+                      const double* qe, const double* te, double* q, double* t) {
+    return odometry_walk(n, m, src, dst, qe, te, q, t, NULL, NULL);
+}
+
+/* The forest of orc_init_odometry itself: parent and tree-edge code of every
+ * vertex (see odometry_walk). */
+int orc_odometry_forest(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, int32_t* parent,
+                        int32_t* pedge) {
+    return odometry_walk(n, m, src, dst, NULL, NULL, NULL, NULL, parent, pedge);
 }
 
 /* ---- objectives --------------------------------------------------------- */

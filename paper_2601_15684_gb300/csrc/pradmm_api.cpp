@@ -1750,6 +1750,14 @@ pradmm_status pradmm_init_odometry(pradmm_t h) {
     return ps;
 }
 
+pradmm_status pradmm_odometry_forest(pradmm_t h, int32_t* parent, int32_t* pedge) {
+    if (!h || !parent || !pedge) return fail(PRADMM_ERR_ARG, "NULL argument");
+    CU(cudaMemcpyAsync(parent, h->forest_par, sizeof(int32_t) * h->n, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(pedge, h->forest_pedge, sizeof(int32_t) * h->n, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return PRADMM_OK;
+}
+
 pradmm_status pradmm_step(pradmm_t h, int32_t iters, double* e_last) {
     if (!h) return fail(PRADMM_ERR_ARG, "NULL handle");
     if (iters < 0) return fail(PRADMM_ERR_ARG, "iters must be >= 0");

@@ -80,6 +80,7 @@ _SIGS = {
     "pradmm_profile_iterations": (ctypes.c_int, [_h, ctypes.c_int32, _d]),
     "pradmm_debug_set_neighbour": (ctypes.c_int, [_h, ctypes.c_int64, ctypes.c_int32]),
     "pradmm_get_trace": (ctypes.c_int, [_h, _d, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
+    "pradmm_odometry_forest": (ctypes.c_int, [_h, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "pradmm_counters": (ctypes.c_int, [_h, _i64]),
     "pradmm_bytes_per_iteration": (ctypes.c_int, [_h, _d]),
     "pradmm_profile_sweeps": (ctypes.c_int, [_h, ctypes.c_int32, _d]),
@@ -279,6 +280,16 @@ def pradmm_set_trace(h, capacity: int):
     _check(load().pradmm_set_trace(h, int(capacity)), "pradmm_set_trace")
 
 
+def pradmm_odometry_forest(h, n):
+    """(parent, tree-edge code) of every vertex, int32; see pradmm.h."""
+    par = np.zeros(n, dtype=np.int32)
+    pedge = np.zeros(n, dtype=np.int32)
+    i32 = ctypes.POINTER(ctypes.c_int32)
+    _check(load().pradmm_odometry_forest(h, par.ctypes.data_as(i32), pedge.ctypes.data_as(i32)),
+           "pradmm_odometry_forest")
+    return par, pedge
+
+
 def pradmm_get_trace(h, capacity: int):
     """(first iteration number, e^k array oldest first)."""
     out = np.zeros(max(int(capacity), 1))
@@ -438,6 +449,10 @@ class Solver:
 
     def init_odometry(self):
         pradmm_init_odometry(self.h)
+
+    def odometry_forest(self):
+        """(parent, tree-edge code) per vertex of the odometry start's forest."""
+        return pradmm_odometry_forest(self.h, self.n)
 
     def autotune(self, iters=20):
         return pradmm_autotune(self.h, iters)

@@ -3,12 +3,12 @@
 The start composes the relative measurements along the spanning forest of
 the earliest edges (an edge joins when it links two components, edges in
 input order), each component rooted at its lowest vertex with the identity
-pose.  The device finds that forest by Boruvka's rounds with the edge index
-as the weight, roots it by an Euler tour ranked by pointer jumping and
-composes the poses by pointer jumping; the oracle scans the edges in order
-and walks each tree from its root.  A wrong tree edge, parent or root moves a
-pose by O(1), so comparing the poses checks the forest, its orientation and
-the composition together.  The graphs below are chosen for the parts of the
+pose.  The device (in pradmm_create) finds that forest by Boruvka's rounds
+with the edge index as the weight and roots it by an Euler tour ranked by
+pointer jumping; the start composes the poses by pointer jumping in segments;
+the oracle scans the edges in order and walks each tree from its root.  The
+forest (index work) is compared bit for bit, parent and tree-edge code of
+every vertex; the poses within rounding.  The graphs below are chosen for the parts of the
 device path the walk workloads leave easy: many Boruvka rounds (random edge
 order), several components and isolated vertices, a chain whose hooks form
 one long list (edges numbered against the chain, half of them reversed), a
@@ -127,7 +127,7 @@ def test_device_odometry_matches_oracle(P, case):
 
 def test_device_odometry_repeated_and_after_steps(P):
     """A second start after iterations gives the same poses again (the
-    forest scratch is rebuilt every call, nothing is carried over)."""
+    composition's work space is rebuilt every call, the forest is create's)."""
     g = _components(11)
     q0, t0 = oracle.init_odometry(g)
     prm = P.pradmm_default_params()
@@ -141,3 +141,17 @@ def test_device_odometry_repeated_and_after_steps(P):
     for k in ("q", "t"):
         assert np.array_equal(a[k], b[k]), k
     assert np.abs(a["q"] - q0).max() <= 1e-11
+
+
+@pytest.mark.parametrize("case", list(CASES) + ["lattice1m"])
+def test_device_forest_equals_oracle_forest(P, case):
+    """The forest itself (index work) is compared bit for bit: every vertex's
+    parent and tree-edge code from create's device forest against
+    oracle.odometry_forest (pinned against brute force in
+    tests/test_oracle_forest.py)."""
+    g = synth.workload("lattice1m") if case == "lattice1m" else CASES[case]()
+    par_o, pe_o = oracle.odometry_forest(g)
+    with P.Solver(g) as S:
+        par_d, pe_d = S.odometry_forest()
+    bad = np.nonzero((par_d != par_o) | (pe_d != pe_o))[0]
+    assert bad.size == 0, (case, bad[:10], par_d[bad[:10]], par_o[bad[:10]])
