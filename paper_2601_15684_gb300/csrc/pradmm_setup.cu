@@ -427,17 +427,26 @@ __global__ void __launch_bounds__(256) k_seg_jump(const int32_t* __restrict__ p_
     }
 }
 
-// Head k (ordinal: hpos[v] - 1, hpos the inclusive scan of the head flags):
-// the vertex it is, the ordinal of the head above (-1 for a root) and the
-// pose step from it, C(par(s)) o step(s) (just step(s) when the parent is a
-// head itself; the identity for a root).
+// The dense head list: hv[hpos[v] - 1] = v for every head v (hpos the
+// inclusive scan of the head flags).
+__global__ void __launch_bounds__(256) k_head_list(const int32_t* __restrict__ depth, const int32_t* __restrict__ hpos,
+                                                   int64_t n, int32_t* hv) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        if (seg_head(depth, v)) hv[hpos[v] - 1] = (int32_t)v;
+}
+
+// Head k of the dense list (vertex hv[k]): the ordinal of the head above
+// (-1 for a root) and the pose step from it, C(par(s)) o step(s) (just
+// step(s) when the parent is a head itself; the identity for a root).  One
+// thread per head, so the FP64 work fills whole warps.
 __global__ void __launch_bounds__(256) k_head_init(const int32_t* __restrict__ par, const int32_t* __restrict__ seg_p,
                                                    const int32_t* __restrict__ depth, const int32_t* __restrict__ hpos,
-                                                   const double* __restrict__ q, const double* __restrict__ t, int64_t n,
+                                                   const int32_t* __restrict__ hv, const int32_t* __restrict__ count,
+                                                   const double* __restrict__ q, const double* __restrict__ t,
                                                    int32_t* hp, double* hq, double* ht) {
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        if (!seg_head(depth, v)) continue;
-        const int64_t k = hpos[v] - 1;
+    const int64_t H = *count;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < H; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = hv[k];
         const int32_t p = par[v];
         double qv[4], tv[3];
         ld_pose(q, t, v, qv, tv);
@@ -562,7 +571,7 @@ cudaError_t launch_slot_owner(const int32_t* ptr, int64_t n, int32_t* owner, cud
 }
 
 size_t odometry_scratch_bytes(int64_t n) {
-    return (size_t)n * (8 * sizeof(int32_t) + 14 * sizeof(double)) + (size_t)((n + 1023) / 1024 + 8) * sizeof(int32_t) +
+    return (size_t)n * (9 * sizeof(int32_t) + 14 * sizeof(double)) + (size_t)((n + 1023) / 1024 + 8) * sizeof(int32_t) +
            256;
 }
 
@@ -577,7 +586,8 @@ cudaError_t launch_odometry(const int32_t* pedge, const int32_t* par, const int3
     int32_t* dd[2] = {ib + 2 * n, ib + 3 * n};
     int32_t* hp[2] = {ib + 4 * n, ib + 5 * n};
     int32_t* hpos = ib + 6 * n;      // head flags, then their inclusive scan
-    int32_t* sums = ib + 7 * n;
+    int32_t* hv = ib + 7 * n;        // the dense head list
+    int32_t* sums = ib + 8 * n;
     const int g = grid_of(n);
     // smallest even r with 2^r >= x
     auto even_rounds = [](int64_t x) {
@@ -604,8 +614,9 @@ cudaError_t launch_odometry(const int32_t* pedge, const int32_t* par, const int3
     const int32_t* seg_p = pp[0];
     // the heads, packed: their chains by pointer jumping, then every vertex's pose
     if ((e = inclusive_scan_i32(hpos, n, sums, st))) return e;
-    k_head_init<<<g, 256, 0, st>>>(par, seg_p, depth, hpos, q, t, n, hp[0], hq[0], ht[0]);
     const int32_t* count = hpos + n - 1;
+    k_head_list<<<g, 256, 0, st>>>(depth, hpos, n, hv);
+    k_head_init<<<grid_of(n / kSeg + 1), 256, 0, st>>>(par, seg_p, depth, hpos, hv, count, q, t, hp[0], hq[0], ht[0]);
     const int rh = even_rounds(n / kSeg + 2);
     for (int r = 0; r < rh; ++r)
         k_head_jump<<<grid_of(n / kSeg + 1), 256, 0, st>>>(hp[r & 1], hq[r & 1], ht[r & 1], count, hp[(r + 1) & 1],
