@@ -52,17 +52,17 @@ struct CtaGroup {
         __syncthreads();
         return out;
     }
-    // the four residual parts in one CTA reduction (each with sum()'s tree),
-    // then broadcast: 4 barriers instead of 16
-    __device__ void sum4(double* v) const {
+    // e^k from the four residual parts (dlam, dz, dq, dt): one CTA reduction
+    // (each part with sum()'s tree), e formed by thread 0 and broadcast
+    __device__ double residual(double* v, double b1, double b2) const {
         block_sum_n<4>(v, sh);
-        if (threadIdx.x == 0)
-            for (int k = 0; k < 4; ++k) sh[k] = v[k];
+        if (threadIdx.x == 0) sh[0] = v[0] / b1 + v[1] / b2 + b1 * v[2] + b2 * v[3];
         __syncthreads();
-        for (int k = 0; k < 4; ++k) v[k] = sh[k];
+        const double e = sh[0];
         __syncthreads();
+        return e;
     }
-    // after sum4: its barriers already follow every write of the iteration
+    // after residual(): its barriers already follow every write of the iteration
     __device__ void sync_after_sum() const {}
 };
 
@@ -74,8 +74,13 @@ struct WarpGroup {
         v = warp_sum(v);
         return __shfl_sync(0xffffffffu, v, 0);
     }
-    __device__ void sum4(double* v) const {
-        for (int k = 0; k < 4; ++k) v[k] = sum(v[k]);
+    // e^k from the four residual parts: lane 0 holds the totals, forms e and
+    // broadcasts it
+    __device__ double residual(double* v, double b1, double b2) const {
+        for (int k = 0; k < 4; ++k) v[k] = warp_sum(v[k]);
+        double e = 0.0;
+        if ((threadIdx.x & 31) == 0) e = v[0] / b1 + v[1] / b2 + b1 * v[2] + b2 * v[3];
+        return __shfl_sync(0xffffffffu, e, 0);
     }
     // shuffles do not order memory: a warp barrier after the sums
     __device__ void sync_after_sum() const { __syncwarp(); }
@@ -96,8 +101,9 @@ struct ClusterGroup {
     }
     __device__ int size() const { return (int)cooperative_groups::this_cluster().num_blocks() * blockDim.x; }
     __device__ void sync() const { cooperative_groups::this_cluster().sync(); }
-    // four sums with one exchange
-    __device__ void sum4(double* v) const {
+    // e^k from the four residual parts with one exchange: thread 0 of every
+    // CTA adds the CTA totals in rank order, forms e and broadcasts it
+    __device__ double residual(double* v, double b1, double b2) const {
         auto cl = cooperative_groups::this_cluster();
         double cta[4] = {v[0], v[1], v[2], v[3]};
         block_sum_n<4>(cta, sh);  // thread 0 holds the CTA totals
@@ -109,16 +115,21 @@ struct ClusterGroup {
                 for (int k = 0; k < 4; ++k) dst[k] = cta[k];
             }
         cl.sync();
-        for (int k = 0; k < 4; ++k) {
-            double tot = 0.0;
-            for (unsigned r = 0; r < nb; ++r) tot += slots[(b * kMaxCluster + r) * 4 + k];
-            v[k] = tot;
+        if (threadIdx.x == 0) {
+            double tot[4];
+            for (int k = 0; k < 4; ++k) {
+                tot[k] = 0.0;
+                for (unsigned r = 0; r < nb; ++r) tot[k] += slots[(b * kMaxCluster + r) * 4 + k];
+            }
+            sh[0] = tot[0] / b1 + tot[1] / b2 + b1 * tot[2] + b2 * tot[3];
+            *bank = b ^ 1;
         }
         __syncthreads();
-        if (threadIdx.x == 0) *bank = b ^ 1;
+        const double e = sh[0];
         __syncthreads();
+        return e;
     }
-    // after sum4: its cluster barrier already follows every write of the iteration
+    // after residual(): its cluster barrier already follows every write of the iteration
     __device__ void sync_after_sum() const {}
 };
 
@@ -158,9 +169,7 @@ __device__ void solve_graph(const G& grp, const GraphDev<R>& g, const StateDev<R
         grp.sync();
         for (int64_t i = v0 + r; i < v1; i += nt) sp_vertex<R, true, false, false, INERT>(g, S, c, pcur, S.p[k & 1], i, adz, ctrl);
         double d4[4] = {adl.get(), adz.get(), adq.get(), adt.get()};
-        grp.sum4(d4);
-        const double dl = d4[0], dz = d4[1], dq = d4[2], dt = d4[3];
-        e = dl / c.b1d + dz / c.b2d + c.b1d * dq + c.b2d * dt;
+        e = grp.residual(d4, c.b1d, c.b2d);
         ++k;
         if (k == 1) e1 = e;
         grp.sync_after_sum();

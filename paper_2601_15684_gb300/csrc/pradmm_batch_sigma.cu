@@ -59,8 +59,7 @@ __device__ void solve_graph_sigma(const G& grp, const GraphDev<R>& g, const Stat
         grp.sync();
         for (int64_t i = v0 + r; i < v1; i += nt) s_sig_vertex<R, INERT>(g, S, c, sg, pn, i, adz);
         double d4[4] = {adl.get(), adz.get(), adq.get(), adt.get()};
-        grp.sum4(d4);
-        e = d4[0] / c.b1d + d4[1] / c.b2d + c.b1d * d4[2] + c.b2d * d4[3];
+        e = grp.residual(d4, c.b1d, c.b2d);
         ++k;
         if (k == 1) e1 = e;
         grp.sync_after_sum();
