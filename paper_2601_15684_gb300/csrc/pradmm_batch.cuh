@@ -37,6 +37,51 @@ namespace {
 
 using namespace dev;
 
+// Sums of four values over a warp by reduce-scatter, in FP64 with a fixed
+// tree: the first butterfly step splits the values between the half warps,
+// the second between quarter... (lanes 0-7 keep value 0, 8-15 value 1, 16-23
+// value 2, 24-31 value 3), the last three steps are a butterfly on the one
+// value a lane keeps: 6 FP64 additions per lane instead of 20 for four
+// separate trees.  Lane 0 ends with all four totals in v.
+__device__ __forceinline__ void warp_sum4(double* v) {
+    constexpr unsigned kAll = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool hi = lane >= 16, odd = (lane & 8) != 0;
+    // step 16: keep (0, 1) in the low half, (2, 3) in the high half
+    const double s0 = hi ? v[0] : v[2], s1 = hi ? v[1] : v[3];
+    const double r0 = __shfl_xor_sync(kAll, s0, 16), r1 = __shfl_xor_sync(kAll, s1, 16);
+    const double k0 = (hi ? v[2] : v[0]) + r0, k1 = (hi ? v[3] : v[1]) + r1;
+    // step 8: keep the first of the pair in lanes with bit 3 clear, else the second
+    const double s = odd ? k0 : k1;
+    double x = (odd ? k1 : k0) + __shfl_xor_sync(kAll, s, 8);
+    x += __shfl_xor_sync(kAll, x, 4);
+    x += __shfl_xor_sync(kAll, x, 2);
+    x += __shfl_xor_sync(kAll, x, 1);
+    // lanes 0, 8, 16, 24 hold the totals of values 0..3
+    const double t1 = __shfl_sync(kAll, x, 8), t2 = __shfl_sync(kAll, x, 16), t3 = __shfl_sync(kAll, x, 24);
+    v[0] = x;
+    v[1] = t1;
+    v[2] = t2;
+    v[3] = t3;
+}
+
+// Four CTA totals (thread 0 gets them) from warp_sum4 in every warp and
+// again over the warp totals; sh holds 4 x 32 doubles.
+__device__ __forceinline__ void block_sum4_rs(double* v, double* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    warp_sum4(v);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sh[32 * k + wid] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = lane < nw ? sh[32 * k + lane] : 0.0;
+        warp_sum4(v);
+    }
+    __syncthreads();
+}
+
 // Thread group that owns one graph: the whole CTA or one warp.
 struct CtaGroup {
     double* sh;  // 4 x 32 doubles of shared scratch for the reductions
@@ -55,7 +100,7 @@ struct CtaGroup {
     // e^k from the four residual parts (dlam, dz, dq, dt): one CTA reduction
     // (each part with sum()'s tree), e formed by thread 0 and broadcast
     __device__ double residual(double* v, double b1, double b2) const {
-        block_sum_n<4>(v, sh);
+        block_sum4_rs(v, sh);
         if (threadIdx.x == 0) sh[0] = v[0] / b1 + v[1] / b2 + b1 * v[2] + b2 * v[3];
         __syncthreads();
         const double e = sh[0];
@@ -77,7 +122,7 @@ struct WarpGroup {
     // e^k from the four residual parts: lane 0 holds the totals, forms e and
     // broadcasts it
     __device__ double residual(double* v, double b1, double b2) const {
-        for (int k = 0; k < 4; ++k) v[k] = warp_sum(v[k]);
+        warp_sum4(v);
         double e = 0.0;
         if ((threadIdx.x & 31) == 0) e = v[0] / b1 + v[1] / b2 + b1 * v[2] + b2 * v[3];
         return __shfl_sync(0xffffffffu, e, 0);
@@ -106,7 +151,7 @@ struct ClusterGroup {
     __device__ double residual(double* v, double b1, double b2) const {
         auto cl = cooperative_groups::this_cluster();
         double cta[4] = {v[0], v[1], v[2], v[3]};
-        block_sum_n<4>(cta, sh);  // thread 0 holds the CTA totals
+        block_sum4_rs(cta, sh);  // thread 0 holds the CTA totals
         const int b = *bank;
         const unsigned me = cl.block_rank(), nb = cl.num_blocks();
         if (threadIdx.x == 0)
