@@ -73,7 +73,6 @@ using namespace dev;
 template <typename R, bool INERT = false>
 __global__ void __launch_bounds__(256, PRADMM_MINB_Q) k_q(GraphDev<R> g, StateDev<R> S, Coef<R> c, Ctrl* ctrl, double* part,
                                            int pstride) {
-    __shared__ double sh[32];
     if (ctrl->halt) return;
     const long long k = ctrl->iter;
     const R* pn = S.p[(k + 1) & 1];
