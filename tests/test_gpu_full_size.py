@@ -14,6 +14,21 @@ printed.
   within max(1e-4, 32 x the deviation of FP32 references -- the checker's
   algorithm executed in single precision and the FP64 oracle with FP32
   storage -- at the vertex, 32 x their root mean square deviation).  The odometry start is compared first.
+- lattice1m_4m (the same walk with closures at p = 0.57: 4,002,064 edges),
+  after 1 and 10 iterations.  FP64 path, from the oracle's own start (the
+  device start, composed along the 1M-pose chain in another association, is
+  checked within 8 n unit roundoffs): p, q, t, s within 1e-10 per array and
+  every element within 1e-10 of its scale.  FP32 path: on this graph the
+  single-precision executions themselves leave 1e-5 after 10 iterations (the
+  checker's algorithm in single precision: relerr(p) 1.6e-5; the FP64 oracle
+  with FP32 storage: 9.8e-6), so each per-array bound is the larger of 1e-5
+  and twice the larger of the two references' own deviation.  A few vertices
+  carry a local mode whose error doubles every iteration; there the two
+  references differ from each other by up to about 270 times, so the
+  per-element rule takes as its factor the larger of 32 and that mutual
+  spread (computed from the references alone), and the error distribution
+  (99.9 % and 99.99 % quantiles, maximum, count above 1e-4) must stay within
+  twice the references'.
 - the 4,096-walk batch (14.0M poses, 37.4M edges), solved as the benchmark
   solves it (a first solve, the profiled schedule search, then the solve to a
   relative residual of 1e-6, at most 3,000 iterations): the stopping rule on
@@ -37,7 +52,8 @@ import pytest
 
 import oracle
 from paper_2601_15684_gb300 import synth
-from parity import check_elements_fp32, fp32_storage_run
+from parity import (ELEM_FACTOR_FP32, ELEM_FLOOR_FP32, ELEM_TOL_FP64, check_elements,
+                    check_elements_fp32, element_errors, fp32_storage_run)
 
 pytestmark = pytest.mark.gpu
 
@@ -59,24 +75,33 @@ def _oparams():
     return oracle.make_params(beta1=1.0, beta2=1.0, tau=1.5, gamma=(1.0, 1e-3, 1e-3, 1e-3))
 
 
-def _check_fp32(gpu, orc, what, orc32, tau=1.5, beta1=1.0, beta2=1.0):
+def _check_fp32(gpu, orc, what, orc32, tau=1.5, beta1=1.0, beta2=1.0, ref_factor=None,
+                elem_factor=ELEM_FACTOR_FP32):
     """p, q, t, s within 1e-5 relative.  A multiplier is a running sum of
     tau*beta*(p - q) (resp. (t - s)); on the lattice q is far from unit length
     in the first iterations (long drifted closures), so its error is measured
     against the larger of its own size and the scale of the terms it is
-    formed from."""
-    for k in ("p", "q", "t", "s"):
-        e = relerr(gpu[k], orc[k])
-        print(f"{what}: relerr({k}) = {e:.3e}")
-        assert e <= 1e-5, (what, k, e)
+    formed from.  With ref_factor every per-array bound is instead the larger
+    of 1e-5 and ref_factor times the largest error of the FP32 references
+    orc32 (a list of states) in the same measure.  elem_factor is the factor
+    of the per-element FP32 rule."""
     nl = lambda a: np.linalg.norm(a)
     scale_l = max(nl(orc["lam"]), tau * beta1 * (nl(orc["p"]) + nl(orc["q"])))
     scale_z = max(nl(orc["z"]), tau * beta2 * (nl(orc["t"]) + nl(orc["s"])))
-    el = nl(gpu["lam"] - orc["lam"]) / scale_l
-    ez = nl(gpu["z"] - orc["z"]) / scale_z
-    print(f"{what}: lam error / scale = {el:.3e}, z error / scale = {ez:.3e}")
-    assert el <= 1e-5 and ez <= 1e-5, (what, el, ez)
-    check_elements_fp32(gpu, orc, orc32, what=what, tau=tau, beta1=beta1, beta2=beta2)
+    errs = {k: (lambda x, k=k: relerr(x[k], orc[k])) for k in ("p", "q", "t", "s")}
+    errs["lam"] = lambda x: nl(x["lam"] - orc["lam"]) / scale_l
+    errs["z"] = lambda x: nl(x["z"] - orc["z"]) / scale_z
+    for k, err in errs.items():
+        e = err(gpu)
+        bound = 1e-5
+        if ref_factor is not None:
+            ex = max(err(r) for r in orc32)
+            bound = max(bound, ref_factor * ex)
+            print(f"{what}: {k}: error {e:.3e}, FP32 references {ex:.3e}, bound {bound:.3e}")
+        else:
+            print(f"{what}: {k}: error {e:.3e}")
+        assert e <= bound, (what, k, e, bound)
+    check_elements_fp32(gpu, orc, orc32, what=what, tau=tau, beta1=beta1, beta2=beta2, factor=elem_factor)
 
 
 def test_lattice1m_one_and_ten_iterations(P):
@@ -103,6 +128,97 @@ def test_lattice1m_one_and_ten_iterations(P):
         F = S.objective()
     F_ref = oracle.objective(g, orc["p"], orc["t"])
     assert abs(F - F_ref) <= 1e-5 * F_ref
+
+
+# the 4,002,064-edge lattice, FP32 path: per-array bound over the FP32
+# references' own deviation from the FP64 oracle; the error distribution
+# (upper quantiles, count above the FP32 floor) within this factor of the
+# references'
+LATTICE4M_REF_FACTOR = 2.0
+KEYS = ("p", "q", "t", "s", "lam", "z")
+
+
+def _ref_mutual_spread(orc, refs):
+    """The largest ratio, either way round, between the two FP32 references'
+    per-element errors over the elements where either exceeds the FP32 floor:
+    how far apart two FP32 executions of the method land at one vertex.  On
+    the 4,002,064-edge lattice a few vertices carry a local mode whose error
+    roughly doubles every iteration (q far from unit length); there the
+    references' own errors differ by up to about 270 times after 10
+    iterations, so the per-element factor of 32 would fail one reference
+    judged by the other."""
+    ea, eb = (element_errors(r, orc, keys=KEYS) for r in refs)
+    out = 1.0
+    for k in KEYS:
+        big = np.maximum(ea[k], eb[k]) > ELEM_FLOOR_FP32
+        if big.any():
+            a, b = ea[k][big], eb[k][big]
+            out = max(out, float(np.max(np.maximum(a, b) / np.maximum(np.minimum(a, b), 1e-300))))
+    return out
+
+
+def _check_distribution(gpu, orc, refs, what, factor=LATTICE4M_REF_FACTOR):
+    """The 99.9 % and 99.99 % quantiles and the maximum of the per-element
+    errors, and the number of elements above the FP32 floor, within factor
+    times the larger reference's (quantiles below a hundredth of the floor
+    count as that)."""
+    eg = element_errors(gpu, orc, keys=KEYS)
+    er = [element_errors(r, orc, keys=KEYS) for r in refs]
+    for k in KEYS:
+        for x in (0.999, 0.9999, 1.0):
+            vg = float(np.quantile(eg[k], x))
+            vr = max(float(np.quantile(e[k], x)) for e in er)
+            print(f"{what}: {k}: quantile {x}: {vg:.3e} (references {vr:.3e})")
+            assert vg <= factor * max(vr, 0.01 * ELEM_FLOOR_FP32), (what, k, x, vg, vr)
+        cg = int((eg[k] > ELEM_FLOOR_FP32).sum())
+        cr = max(int((e[k] > ELEM_FLOOR_FP32).sum()) for e in er)
+        print(f"{what}: {k}: {cg} elements above {ELEM_FLOOR_FP32:g} (references {cr})")
+        assert cg <= factor * cr + 10, (what, k, cg, cr)
+
+
+def test_lattice1m_4m_one_and_ten_iterations(P):
+    g = synth.workload("lattice1m_4m")
+    q0, t0 = oracle.init_odometry(g)
+    with P.Solver(g, precision=P.PRADMM_FP32) as S32, P.Solver(g, precision=P.PRADMM_FP64) as S64:
+        S32.init_odometry()
+        S64.init_odometry()
+        st0 = S64.state()
+        # the device composes the start along chains up to n poses long in
+        # another association than the oracle's walk: FP64 rounding up to
+        # about n unit roundoffs, which the first iteration amplifies; the
+        # FP64 iterations are therefore compared from the oracle's own x^0
+        d0 = max(relerr(st0["p"], q0), relerr(st0["t"], t0))
+        print(f"lattice1m_4m FP64 odometry start: relerr {d0:.3e}")
+        assert d0 <= 8 * g.n * 2.0 ** -53, d0
+        S64.set_state(q0, t0)
+        orc = oracle.init_state(q0, t0)
+        orc32, orcx = orc, orc
+        step = lambda st: oracle.iterate(g, _oparams(), st, 1)[0]
+        done = 0
+        for it in (1, 10):
+            e32 = S32.step(it - done)
+            e64 = S64.step(it - done)
+            orc, res, _ = oracle.iterate(g, _oparams(), orc, it - done)
+            orc32 = fp32_storage_run(step, orc32, it - done)
+            orcx = oracle.iterate_f32(g, _oparams(), orcx, it - done)
+            done = it
+            what = f"lattice1m_4m after {it}"
+            st64 = S64.state()
+            for k in ("p", "q", "t", "s"):
+                e = relerr(st64[k], orc[k])
+                print(f"{what} FP64: relerr({k}) = {e:.3e}")
+                assert e <= 1e-10, (what, k, e)
+            check_elements(st64, orc, ELEM_TOL_FP64, what=what + " FP64")
+            assert abs(e64 - res[0]) <= 1e-9 * res[0]
+            spread = _ref_mutual_spread(orc, [orc32, orcx])
+            assert spread <= 1e3, spread  # the references themselves stay comparable
+            elem_factor = max(ELEM_FACTOR_FP32, spread)
+            print(f"{what} FP32: references' mutual spread {spread:.1f}, element factor {elem_factor:.1f}")
+            st32 = S32.state()
+            _check_fp32(st32, orc, what + " FP32", [orc32, orcx], ref_factor=LATTICE4M_REF_FACTOR,
+                        elem_factor=elem_factor)
+            _check_distribution(st32, orc, [orc32, orcx], what + " FP32")
+            assert abs(e32 - res[0]) <= 1e-3 * res[0]
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-6), (1, 1e-3)])
