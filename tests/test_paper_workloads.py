@@ -3,15 +3,19 @@
 CPU: the generators follow the stated construction -- the ring is one loop of
 radius 2 with m = n; the cube's mean edge count matches the paper's
 E(m) = 2 (2 n^3 - 3 n^2 + 1) p + n^3 - 1 and every edge joins grid neighbours.
-GPU: the library matches the oracle on them (FP64 1e-10, FP32 1e-5 after 1 and
-10 iterations) and, with the paper's settings (tau = 1.4, tol = 1e-4,
-MaxIter = 300), its FP64 solve stops at the oracle's iteration.
+GPU: the library matches the oracle on them (FP64 1e-10, FP32 1e-5 per array
+after 1 and 10 iterations; per element, FP64 within 1e-10 of each element's
+scale and FP32 by the FP32 rule of tests/parity.py against the oracle's
+single-precision execution and its FP32-storage run) and, with the paper's
+settings (tau = 1.4, tol = 1e-4, MaxIter = 300), its FP64 solve stops at the
+oracle's iteration.
 """
 import numpy as np
 import pytest
 
 import oracle
 from paper_2601_15684_gb300 import synth
+from parity import ELEM_TOL_FP64, check_elements, check_elements_fp32, fp32_storage_run
 
 WORKLOADS = ("ring100", "ring5000", "cube7", "cube10")
 
@@ -82,17 +86,27 @@ def test_paper_workloads_match_oracle(P, name, precision):
     op = oracle.make_params(beta1=1.0, beta2=1.0, tau=1.4)
     q0, t0 = oracle.init_odometry(g)
     orc = oracle.init_state(q0, t0)
+    orc32, orcx = orc, orc
+    step = lambda st: oracle.iterate(g, op, st, 1)[0]
     with P.Solver(g, _prm(P, precision)) as S:
         S.init_odometry()
         done = 0
         for it in (1, 10):
             S.step(it - done)
             orc, _, _ = oracle.iterate(g, op, orc, it - done)
+            if precision == 1:
+                orc32 = fp32_storage_run(step, orc32, it - done)
+                orcx = oracle.iterate_f32(g, op, orcx, it - done)
             done = it
             gpu = S.state()
             tol = 1e-10 if precision == 0 else 1e-5
             for key in ("p", "q", "t", "s"):
                 assert relerr(gpu[key], orc[key]) <= tol, (name, it, key, relerr(gpu[key], orc[key]))
+            what = f"{name} after {it}"
+            if precision == 0:
+                check_elements(gpu, orc, ELEM_TOL_FP64, what=what, tau=1.4)
+            else:
+                check_elements_fp32(gpu, orc, [orc32, orcx], what=what, tau=1.4)
 
 
 @pytest.mark.gpu
