@@ -146,7 +146,7 @@ def _ref_mutual_spread(orc, refs):
     roughly doubles every iteration (q far from unit length); there the
     references' own errors differ by up to about 270 times after 10
     iterations, so the per-element factor of 32 would fail one reference
-    judged by the other."""
+    measured against the other."""
     ea, eb = (element_errors(r, orc, keys=KEYS) for r in refs)
     out = 1.0
     for k in KEYS:
